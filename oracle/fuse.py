@@ -1,0 +1,50 @@
+"""Confidence-filtered fusion of submap points into the global map: the oracle.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+The paper obtains "the global coordinates of all points in the current
+submap" from the estimated transforms (Sec. III-C "Point Correction"); each
+point of a submap carries a confidence (Sec. III-C "Feed-Forward Inference").
+Readings:
+
+* a point is kept when its confidence is strictly greater than the threshold
+  (NaN confidences are dropped);
+* kept points are emitted in ascending global flat index
+  g = index_base + ((m*F + f)*H + row)*W + col (submap-major), which makes
+  the compaction unique;
+* the global point is T_m(x) = s_m R_m x + t_m evaluated in float64 from the
+  float32 point and the float64 pose of submap m.
+
+The compaction is written as its definition: an exclusive prefix sum of the
+keep flags gives every kept point its output slot.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def fuse_points(xyz, conf, poses, threshold=1.0, index_base=0):
+    """xyz [M, F*H*W, 3] (or [M,F,H,W,3]), conf [M, ...], poses = list of (s, R, t).
+
+    Returns (out_xyz [K,3] float64, out_idx [K] int64).
+    """
+    xyz = np.asarray(xyz)
+    conf = np.asarray(conf)
+    M = xyz.shape[0]
+    xyz = xyz.reshape(M, -1, 3)
+    conf = conf.reshape(M, -1)
+    n = conf.shape[1]
+    with np.errstate(invalid="ignore"):
+        keep = (conf > threshold).reshape(-1)
+    slot = np.cumsum(keep, dtype=np.int64) - keep          # exclusive prefix sum
+    K = int(keep.sum())
+    out_idx = np.empty(K, dtype=np.int64)
+    out_xyz = np.empty((K, 3), dtype=np.float64)
+    g = np.arange(M * n, dtype=np.int64)
+    out_idx[slot[keep]] = g[keep] + index_base
+    for m in range(M):
+        s, R, t = poses[m]
+        km = keep[m * n:(m + 1) * n]
+        X = xyz[m][km].astype(np.float64)
+        out_xyz[slot[m * n:(m + 1) * n][km]] = s * (X @ np.asarray(R).T) + np.asarray(t)
+    return out_xyz, out_idx

@@ -1,0 +1,78 @@
+"""Pins of the adjoint oracle: FP64 central finite differences (h = 1e-6) of
+the forward registration loss, skipping points whose residual sits within
+1e-4 of the Huber kink (where the loss is not differentiable)."""
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+from oracle import adjoint as adj
+from oracle import register as reg
+from oracle import sim3
+
+
+def problem(seed, n=60, outliers=6):
+    rng = np.random.default_rng(seed)
+    P = rng.normal(size=(n, 3)) * np.array([2.0, 1.5, 1.0]) + 1.0
+    S = (float(rng.uniform(0.6, 1.8)), Rotation.random(random_state=rng).as_matrix(), rng.normal(size=3))
+    Q = sim3.act(S, P) + 0.02 * rng.normal(size=(n, 3))
+    Q[:outliers] += rng.normal(size=(outliers, 3))
+    cp = rng.lognormal(0, 0.5, n)
+    cq = rng.lognormal(0, 0.5, n)
+    return P, Q, cp, cq, S
+
+
+def loss(P, Q, cp, cq, S_gt, delta, iters, lam):
+    S, tape, cost = adj.irls_forward(P, Q, cp * cq, delta, iters)
+    return sim3.geodesic_sq(S_gt, S) + lam * cost
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_adjoint_matches_finite_differences(seed):
+    P, Q, cp, cq, S_gt = problem(seed)
+    delta, iters, lam = 0.05, 10, 1.0
+    w = cp * cq
+    S, tape, cost = adj.irls_forward(P, Q, w, delta, iters)
+    # forward agrees with the plain oracle
+    ref = reg.irls(P, Q, w, delta, iters)
+    assert abs(S[0] - ref["S"][0]) < 1e-12 and np.abs(S[1] - ref["S"][1]).max() < 1e-12
+    assert abs(cost - ref["cost"]) < 1e-12 * max(cost, 1e-30) + 1e-18
+    L, gs, gR, gt = adj.geodesic_loss_grad(S, S_gt)
+    gP, gQ, gw = adj.irls_backward(P, Q, w, delta, tape, S, gs, gR, gt, lam)
+    gcp, gcq = adj.weight_grads(gw, cp, cq)
+    # points near the Huber kink at any iteration are not differentiable
+    near = np.zeros(len(w), bool)
+    for rec in tape[1:]:
+        near |= np.abs(rec["r"] - delta) < 1e-4
+    h = 1e-6
+    rng = np.random.default_rng(seed)
+    idx = [i for i in rng.permutation(len(w)) if not near[i]][:12]
+    assert len(idx) >= 8
+    for i in idx:
+        for a in range(3):
+            for X, G in ((P, gP), (Q, gQ)):
+                Xp, Xm = X.copy(), X.copy()
+                Xp[i, a] += h
+                Xm[i, a] -= h
+                args_p = (Xp, Q) if X is P else (P, Xp)
+                args_m = (Xm, Q) if X is P else (P, Xm)
+                fd = (loss(*args_p, cp, cq, S_gt, delta, iters, lam)
+                      - loss(*args_m, cp, cq, S_gt, delta, iters, lam)) / (2 * h)
+                assert abs(fd - G[i, a]) <= 1e-6 * max(1.0, abs(fd)), (i, a, fd, G[i, a])
+        for c, G in ((cp, gcp), (cq, gcq)):
+            cpp, cmm = c.copy(), c.copy()
+            cpp[i] += h
+            cmm[i] -= h
+            a1 = (cpp, cq) if c is cp else (cp, cpp)
+            a2 = (cmm, cq) if c is cp else (cp, cmm)
+            fd = (loss(P, Q, *a1, S_gt, delta, iters, lam) - loss(P, Q, *a2, S_gt, delta, iters, lam)) / (2 * h)
+            assert abs(fd - G[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, G[i])
+
+
+def test_weight_gradient_orthogonal_to_weights():
+    """The loss is invariant to a global scale of w, so sum_i w_i dL/dw_i = 0."""
+    P, Q, cp, cq, S_gt = problem(11)
+    w = cp * cq
+    S, tape, cost = adj.irls_forward(P, Q, w, 0.05, 10)
+    L, gs, gR, gt = adj.geodesic_loss_grad(S, S_gt)
+    _, _, gw = adj.irls_backward(P, Q, w, 0.05, tape, S, gs, gR, gt, 1.0)
+    assert abs(float(gw @ w)) < 1e-9 * float(np.abs(gw * w).sum())

@@ -1,0 +1,56 @@
+"""The seeded generator: deterministic, shaped as stated, and its ground truth
+is what the oracle recovers from noise-free inputs."""
+import numpy as np
+import torch
+
+from oracle import register as reg
+from oracle import sim3
+from paper_2510_02080_b300 import synth
+
+
+def test_pair_deterministic_and_recoverable():
+    a = synth.make_pair(1, H=24, W=40, sigma=0.0, outlier_frac=0.0)
+    b = synth.make_pair(1, H=24, W=40, sigma=0.0, outlier_frac=0.0)
+    assert torch.equal(a.xyz, b.xyz) and torch.equal(a.conf, b.conf)
+    assert a.xyz.shape == (2, 24 * 40, 3) and a.xyz.dtype == torch.float32
+    assert torch.isfinite(a.xyz).all() and (a.conf > 0).all()
+    res = reg.align_pairs(a, delta=0.02, iters=3)[0]
+    s, R, t = [v[0] for v in a.S_gt.numpy()]
+    assert res["status"] == 0
+    assert abs(res["S"][0] / s - 1) < 1e-5 and sim3.rotation_angle(res["S"][1], R) < 1e-5
+
+
+def test_chain_pairs_share_a_keyframe():
+    ch = synth.make_chain(2, M=4, F=5, H=16, W=20, sigma=0.0, outlier_frac=0.0)
+    ps = ch.pairs()
+    assert ps.n_pairs == 3 and ch.xyz.shape == (4, 5, 320, 3)
+    truth = synth.chain_pair_truth(ch)
+    for m in range(3):
+        p = ps.xyz[int(ps.src[m])].double().numpy()
+        q = ps.xyz[int(ps.tgt[m])].double().numpy()
+        T = (float(truth.s[m]), truth.R[m].numpy(), truth.t[m].numpy())
+        assert np.abs(sim3.act(T, p) - q).max() < 1e-4 * (1 + np.abs(q).max())
+
+
+def test_loop_batch_valid_counts_follow_thresholds():
+    ps = synth.make_loop_batch(3, n_pairs=6, H=32, W=48, min_valid=300, max_valid=4000)
+    lo = ps.link_off.tolist()
+    for k in range(6):
+        f = lo[k + 1] - lo[k]
+        assert 1 <= f <= 5
+        cp = ps.conf[ps.src[lo[k]:lo[k + 1]].long()]
+        cq = ps.conf[ps.tgt[lo[k]:lo[k + 1]].long()]
+        thr = float(ps.pair_conf_min[k])
+        n_valid = int(((cp > thr) & (cq > thr)).sum())
+        expect = ps.meta["expected_valid"][k]
+        assert abs(n_valid - expect) < 6 * np.sqrt(expect) + 20
+
+
+def test_pose_graph_measurements_noise_free_are_consistent():
+    g = synth.make_pose_graph(4, 12, 3, rot_noise=0, trans_noise=0, scale_noise=0)
+    T = [(float(g.T_gt.s[v]), g.T_gt.R[v].numpy(), g.T_gt.t[v].numpy()) for v in range(12)]
+    for k in range(len(g.ei)):
+        i, j = int(g.ei[k]), int(g.ej[k])
+        M = (float(g.T_meas.s[k]), g.T_meas.R[k].numpy(), g.T_meas.t[k].numpy())
+        C = sim3.compose(T[i], M)
+        assert abs(C[0] / T[j][0] - 1) < 1e-12 and np.abs(C[1] - T[j][1]).max() < 1e-12
