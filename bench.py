@@ -1,0 +1,340 @@
+"""Benchmark of the submap-fusion hot path on synthetic submaps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (one "step"): the 200-submap chain (5 frames of 294x518 per submap,
+one shared keyframe between consecutive submaps): batched Huber-IRLS
+registration of the 199 consecutive pairs (10 solves, FP32 moments, FP64
+solve), the Sim(3) pose graph over the 200 submaps (when built), and the
+confidence > 1 compaction + global transform of all 152,292,000 points.
+
+Metric: Sim(3)-registered points per second per IRLS iteration
+(valid correspondences x iterations / step time), whole job over all ranks.
+Inputs (2.4 GB per rank) exceed the 126 MB L2, so no flush is needed.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Sim(3)-registered points/s per IRLS iter (batched, FP32) and % HBM roofline"
+UNIT = "pt-iter/s"
+M_SUBMAPS, F_FRAMES, H, W = 200, 5, 294, 518
+ITERS, DELTA = 10, 0.02
+SWEEP_BYTES_PER_PIXEL = 32          # p, q (2 x 12 B) + c_p, c_q (2 x 4 B) per sweep
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle as it stands, on a bounded sample
+# ----------------------------------------------------------------------------
+def oracle_sample(pairs_per_step, steps, warmup, seed):
+    import numpy as np
+    import torch
+    from threadpoolctl import threadpool_limits
+    from oracle import register as reg
+    from paper_2510_02080_b300 import synth
+
+    ch = synth.make_chain(seed, M=pairs_per_step + 1, F=F_FRAMES, H=H, W=W, device="cpu")
+    ps = ch.pairs()
+    with threadpool_limits(limits=1):
+        torch.set_num_threads(1)
+        for _ in range(warmup):
+            reg.align_pairs(ps, delta=DELTA, iters=ITERS)
+        t0 = time.perf_counter()
+        n = 0
+        for _ in range(steps):
+            res = reg.align_pairs(ps, delta=DELTA, iters=ITERS)
+            n += sum(r["n_valid"] for r in res) * ITERS
+        dt = time.perf_counter() - t0
+    return n / dt, n, dt, ps.n_pairs
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    pairs = 2
+    rate, n, dt, npairs = oracle_sample(pairs, args.steps, args.warmup,
+                                        2510020800 + 2)
+    line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "chain200_294x518", "sample_pairs_per_step": npairs,
+                       "iters": ITERS, "delta": DELTA},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{npairs} of the 199 chain pairs per step (152,292 "
+                                       f"correspondences each, 10 IRLS solves), FP64 numpy, "
+                                       f"1 thread"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_2510_02080_b300 import build, ec3r, synth
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+    ctx = ec3r.Context(local)
+
+    # per-rank synthetic chain (weak scaling: every rank owns its own map)
+    ch = synth.make_chain(synth.SEED_BASE + 2 + 1000 * rank, M=M_SUBMAPS, F=F_FRAMES, H=H, W=W,
+                          device=dev)
+    ps = ch.pairs()
+    n_frames, hw = ps.conf.shape
+    xyz_f, conf_f = ps.xyz, ps.conf
+    fin = torch.isfinite(xyz_f).all(-1) & torch.isfinite(conf_f) & (conf_f > 0)
+    n_valid = int((fin[ps.src.long()] & fin[ps.tgt.long()]).sum())
+    del fin
+    pix = ps.n_pairs * hw
+    n_fuse = M_SUBMAPS * F_FRAMES * hw
+    xyz_m = ch.xyz.view(M_SUBMAPS, -1, 3)
+    conf_m = ch.conf.view(M_SUBMAPS, -1)
+    kept = int((conf_m > 1.0).sum())
+    out_xyz = torch.empty((kept, 3), device=dev)
+    out_idx = torch.empty((kept,), dtype=torch.int64, device=dev)
+    S = torch.empty((ps.n_pairs, 13), dtype=torch.float64, device=dev)
+    st = torch.empty((ps.n_pairs,), dtype=torch.int32, device=dev)
+    poses = ec3r.sim3_rows(ch.T_gt.s, ch.T_gt.R, ch.T_gt.t).to(dev)
+    n_cursor = args.steps + args.warmup + 8
+    cursors = torch.zeros((n_cursor,), dtype=torch.int64, device=dev)
+    ci = [0]
+
+    def step(xyz_in, conf_in):
+        ctx.align_submaps(xyz_in.view(n_frames, hw, 3), conf_in.view(n_frames, hw), ps.link_off,
+                          ps.src, ps.tgt, delta=DELTA, iters=ITERS, out=S, status=st)
+        c = cursors[ci[0] % n_cursor:ci[0] % n_cursor + 1]
+        ci[0] += 1
+        ctx.fuse_points(xyz_in.view(M_SUBMAPS, -1, 3), conf_in.view(M_SUBMAPS, -1), poses,
+                        out_xyz, out_idx, c)
+
+    for _ in range(args.warmup):
+        step(ch.xyz, ch.conf)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0, ctx.last_error()
+    assert int((st != 0).sum()) == 0
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- timed region: inputs resident in HBM --------------------------------
+    ctx.profile(True)
+    ctx.profile_read()
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        step(ch.xyz, ch.conf)
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    assert ctx.sync_status() == 0, ctx.last_error()
+    ms_max = ms
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t)
+    value = n_valid * ITERS * args.steps * ws / (ms_max * 1e-3)
+
+    # ---- end to end: host buffers, copies inside the timed region ------------
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.empty(ch.xyz.shape, dtype=torch.float32, pin_memory=True)
+        hc = torch.empty(ch.conf.shape, dtype=torch.float32, pin_memory=True)
+        hx.copy_(ch.xyz)
+        hc.copy_(ch.conf)
+        dx = torch.empty_like(ch.xyz)
+        dc = torch.empty_like(ch.conf)
+        hS = torch.empty(S.shape, dtype=S.dtype, pin_memory=True)
+        e2e_steps = max(1, min(args.steps, 5))
+        for _ in range(2):
+            dx.copy_(hx, non_blocking=True)
+            dc.copy_(hc, non_blocking=True)
+            step(dx, dc)
+            hS.copy_(S, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            dx.copy_(hx, non_blocking=True)
+            dc.copy_(hc, non_blocking=True)
+            step(dx, dc)
+            hS.copy_(S, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier()
+        dt = time.perf_counter() - t0
+        e2e = {"value": n_valid * ITERS * e2e_steps * ws / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(hx.numel() * 4 + hc.numel() * 4),
+               "d2h_bytes_per_step": int(hS.numel() * 8), "steps": e2e_steps}
+        del hx, hc, dx, dc
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = peaks()
+    sweep = prof.get("irls_sweep_fp32", (0.0, 0))
+    sweep_ms = sweep[0] / max(sweep[1], 1)
+    sweep_bytes = SWEEP_BYTES_PER_PIXEL * pix
+    achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9 if sweep_ms > 0 else 0.0
+    total_prof = sum(v[0] for v in prof.values())
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                   "share": v[0] / total_prof if total_prof else None} for k, v in prof.items()}
+    fuse_ms = sum(prof.get(k, (0.0, 0))[0] for k in ("fuse_count", "fuse_scan", "fuse_scatter"))
+    fuse_gbs = 26.0 * n_fuse * args.steps / (fuse_ms * 1e-3) / 1e9 if fuse_ms else None
+
+    cpu_rate, n_cpu, dt_cpu, np_cpu = (None, 0, 0.0, 0)
+    if not args.no_cpu_baseline and ws == 1:
+        cpu_rate, n_cpu, dt_cpu, np_cpu = oracle_sample(2, 1, 0, synth.SEED_BASE + 2)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "chain200_294x518", "submaps": M_SUBMAPS, "frames": F_FRAMES,
+                   "H": H, "W": W, "pairs": ps.n_pairs, "valid_correspondences": n_valid,
+                   "iters": ITERS, "huber_delta": DELTA, "precision": "fp32 moments, fp64 solve",
+                   "fused_points": n_fuse, "kept_points": kept,
+                   "rows": ["registration", "fusion"],
+                   "l2": "inputs 2.4 GB per rank > 126 MB L2; no flush"},
+        "roofline": {"bound": "hbm", "kernel": "irls_sweep_fp32", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": sweep_bytes,
+                     "launch_ms": sweep_ms},
+        "kernels": kernels,
+        "fusion": {"ms_per_step": fuse_ms / args.steps, "gbs_at_26B_per_point": fuse_gbs},
+        "clocks": clk,
+        "gpu_launches": int(sum(v[1] for v in prof.values())),
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if cpu_rate is not None:
+        line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{np_cpu} chain pairs x 152,292 correspondences x "
+                                          f"{ITERS} IRLS solves, FP64 numpy, 1 thread "
+                                          f"({dt_cpu:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

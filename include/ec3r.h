@@ -1,0 +1,200 @@
+/*
+ * ec3r.h - C ABI of the B300 (sm_103a) hot path of EC3R-SLAM submap fusion.
+ *
+ * The paper (EC3R-SLAM, arXiv 2510.02080) builds local submaps with a
+ * feed-forward model, registers every new submap against connected submaps
+ * through the keyframes they share with a weighted Umeyama Sim(3) solve
+ * (Sec. III-C, "Sim3 Point Cloud Registration", Eq. (sim3)), adds the
+ * results as relative Sim(3) constraints to a submap pose graph
+ * (Sec. III-E), and places every submap point in global coordinates
+ * (Sec. III-C, "Point Correction").  This library does those three steps on
+ * the GPU, batched, plus the reverse-mode derivative of the registration.
+ *
+ * Conventions shared by every call
+ *  - All pointers named d_* are device pointers (cudaMalloc'd or equivalent,
+ *    on the context's device); h_* are host pointers.  The caller owns every
+ *    buffer it passes; the library never frees or keeps them past the call.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL means the legacy default stream).  A returned EC3R_OK means the
+ *    arguments were valid and the work was enqueued; per-pair and device-side
+ *    conditions (degenerate pairs, non-positive pivots, capacity overflow,
+ *    timeouts) are reported in device status words and by
+ *    ec3r_sync_status().
+ *  - The context owns its workspace.  A call that needs more workspace than
+ *    the context holds grows it (cudaMalloc) before enqueueing; such a call
+ *    must not be made while `stream` is being captured into a CUDA graph
+ *    (it returns EC3R_ERR_CAPTURE instead).
+ *  - One context per host thread / stream at a time; contexts are
+ *    independent.
+ *  - Similarities act as x -> s R x + t; R is row-major.
+ */
+#ifndef EC3R_H
+#define EC3R_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EC3R_OK = 0,
+  EC3R_ERR_INVALID_ARG = 1, /* bad pointer, size or option; nothing enqueued */
+  EC3R_ERR_CUDA = 2,        /* a CUDA runtime call failed; see ec3r_last_error */
+  EC3R_ERR_OOM = 3,         /* workspace allocation failed */
+  EC3R_ERR_CAPACITY = 4,    /* fuse_points: output capacity exceeded */
+  EC3R_ERR_NOT_SPD = 5,     /* pose graph: non-positive pivot in Cholesky */
+  EC3R_ERR_TIMEOUT = 6,     /* a bounded device wait gave up */
+  EC3R_ERR_DEGENERATE = 7,  /* at least one registration pair was degenerate */
+  EC3R_ERR_CAPTURE = 8      /* workspace growth requested during stream capture */
+} ec3r_status;
+
+/* Per-pair status bits written by ec3r_align_submaps (0 = solved). */
+#define EC3R_PAIR_FEW_POINTS 1u  /* fewer than 3 valid correspondences */
+#define EC3R_PAIR_ZERO_WEIGHT 2u /* total weight <= 0 or not finite */
+#define EC3R_PAIR_RANK 4u        /* source variance <= 0 or sigma2 <= 1e-4 sigma1 */
+#define EC3R_PAIR_NONFINITE 8u   /* non-finite moments or result */
+#define EC3R_PAIR_BAD_INPUT 16u  /* link offsets or frame indices out of range */
+
+typedef struct {
+  double s;     /* scale, > 0 */
+  double R[9];  /* rotation, row-major */
+  double t[3];  /* translation */
+} ec3r_sim3;
+
+typedef struct ec3r_ctx ec3r_ctx;
+
+/* Create a context on CUDA device `device`.  Allocates its status words. */
+ec3r_status ec3r_create(ec3r_ctx** out, int device);
+/* Destroy a context and free its workspace (synchronises the device). */
+void ec3r_destroy(ec3r_ctx* ctx);
+/* Human-readable text of the last error of this context (never NULL). */
+const char* ec3r_last_error(const ec3r_ctx* ctx);
+const char* ec3r_status_string(ec3r_status st);
+/* Library version, e.g. "ec3r 0.1 sm_103a". */
+const char* ec3r_version(void);
+
+/*
+ * Wait for `stream`, then read and clear the context's device status words.
+ * Returns EC3R_ERR_CAPACITY, EC3R_ERR_NOT_SPD, EC3R_ERR_TIMEOUT or
+ * EC3R_ERR_INVALID_ARG (an index argument was out of range) if one of those
+ * was raised by work enqueued since the last call, EC3R_ERR_CUDA if the
+ * stream reports an error, else EC3R_OK.  Degenerate registration pairs are
+ * reported in the per-pair status array, not here.
+ */
+ec3r_status ec3r_sync_status(ec3r_ctx* ctx, void* stream);
+
+/*
+ * Tracing.  With profiling on, calls launch their kernels directly (no cached
+ * graph) and bracket every kernel launch with a CUDA event pair recorded on
+ * the launching stream.  ec3r_profile_read waits for those events, returns
+ * per kernel name the summed duration (ms) and the launch count, in first-
+ * launch order, and clears the record.  `names` receives up to `max_kernels`
+ * NUL-terminated names of `name_len` bytes each; *n_kernels the number of
+ * distinct kernels recorded (which may exceed max_kernels).
+ */
+ec3r_status ec3r_profile(ec3r_ctx* ctx, int enable);
+ec3r_status ec3r_profile_read(ec3r_ctx* ctx, int max_kernels, char* names, int name_len,
+                              double* total_ms, int64_t* launches, int* n_kernels);
+
+/* ------------------------------------------------------------------------ */
+/* Registration: batched Huber-IRLS weighted Umeyama (Sec. III-C, Eq. (sim3))*/
+/* ------------------------------------------------------------------------ */
+
+typedef enum { EC3R_PREC_FP32C = 0, EC3R_PREC_FP64 = 1 } ec3r_precision;
+typedef enum { EC3R_WEIGHT_PRODUCT = 0, EC3R_WEIGHT_SRC = 1 } ec3r_weight_rule;
+
+typedef struct {
+  float huber_delta; /* Huber threshold on |s R p + t - q| (target units), > 0 */
+  int iters;         /* number of weighted Umeyama solves, 1..64 */
+  float conf_min;    /* valid iff c_p > conf_min and c_q > conf_min */
+  int weight_rule;   /* ec3r_weight_rule: w = c_p c_q or w = c_p */
+  int precision;     /* ec3r_precision: FP32 blocked/pairwise moments or FP64 */
+  int want_cost;     /* 1: also write the final weighted residual (one more sweep) */
+} ec3r_align_opts;
+
+/* Fills `o` with the defaults: delta 0.02, 10 iterations, conf_min 0,
+ * product weights, FP32 moments, no cost. */
+void ec3r_align_opts_default(ec3r_align_opts* o);
+
+/*
+ * Register `n_pairs` submap pairs in one batched call (Sec. III-C, Eq. (sim3)
+ * and the weighted Umeyama solution it names, wrapped in Huber IRLS).
+ *
+ * Frames.  d_xyz is a bank of `n_frames` pointmaps, float32 [n_frames][hw][3]
+ * (x, y, z interleaved per pixel, as the feed-forward model writes them), and
+ * d_conf their confidences, float32 [n_frames][hw].  Both are read only.
+ *
+ * Pairs.  Pair k owns links d_link_off[k] .. d_link_off[k+1]-1 (int32
+ * [n_pairs+1], device, non-decreasing, d_link_off[0] = 0 and
+ * d_link_off[n_pairs] = n_links).  Link l says that pixel i of frame
+ * d_src[l] (a point p_i of the current submap) and pixel i of frame
+ * d_tgt[l] (its counterpart q_i in the other submap) are the same keyframe
+ * pixel: the correspondences of Sec. III-C.  Frame indices must lie in
+ * [0, n_frames).  Out-of-range offsets or frames mark the pair
+ * EC3R_PAIR_BAD_INPUT (nothing out of range is read) and raise
+ * EC3R_ERR_INVALID_ARG at ec3r_sync_status.  A pair with no link is
+ * degenerate (EC3R_PAIR_FEW_POINTS).
+ *
+ * Weights.  Correspondence i is valid when p_i, q_i, c_p, c_q are finite and
+ * c_p > cmin and c_q > cmin, where cmin = d_pair_conf_min[k] if that
+ * pointer is non-NULL (float32 [n_pairs]) else opts->conf_min.  Its base
+ * weight is w_i = c_p c_q (or c_p).  Normalising the weights does not change
+ * the solution, so none is applied.
+ *
+ * Iteration.  Solve 1 uses w; solve k >= 2 uses w_i h_i with
+ * h_i = min(1, delta / r_i), r_i = |s R p_i + t - q_i| under solve k-1.
+ *
+ * Output.  d_out[k] (device) receives the last solve, mapping p to q;
+ * d_pair_status[k] (int32, device) the EC3R_PAIR_* bits (0 = solved; a
+ * degenerate pair gets the identity).  d_pair_cost (nullable, float64
+ * [n_pairs]) receives sum omega r(S)^2 / sum omega with the last weights
+ * when opts->want_cost is set.
+ *
+ * The call enqueues a set-up kernel, then `iters` x (moment sweep, solve),
+ * replayed from a CUDA graph cached per argument set when `stream` is not
+ * itself being captured.  Workspace: 152 bytes per tile of 8192 pixels,
+ * 4 bytes per link and 320 bytes per pair.
+ */
+ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d_conf,
+                               int64_t n_frames, int64_t hw, int n_pairs, int64_t n_links,
+                               const int32_t* d_link_off, const int32_t* d_src,
+                               const int32_t* d_tgt, const float* d_pair_conf_min,
+                               const ec3r_align_opts* opts, ec3r_sim3* d_out,
+                               int32_t* d_pair_status, double* d_pair_cost, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Fusion: confidence-filtered transform of submap points into the global   */
+/* map (Sec. III-C "Point Correction": global coordinates of all points)    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Append every point of `n_submaps` submaps whose confidence is strictly
+ * greater than `conf_threshold` (NaN is dropped) to a global point buffer,
+ * transformed by its submap's pose.
+ *
+ * d_xyz float32 [n_submaps][pts_per_submap][3] and d_conf float32
+ * [n_submaps][pts_per_submap] hold the submaps (pts_per_submap = frames*H*W;
+ * flat point g = m*pts_per_submap + i in submap-major order).  d_poses[m]
+ * (ec3r_sim3, device) maps submap m to the world; the point is computed in
+ * float32 from the float32-rounded pose (s R rounded once, then FMA).
+ *
+ * Kept points are written in ascending g at positions *d_cursor,
+ * *d_cursor + 1, ...: d_out_xyz float32 [capacity][3] and d_out_idx int64
+ * [capacity] (= index_base + g).  *d_cursor (int64, device, in/out) is
+ * advanced by the number of kept points, so successive calls stream into one
+ * buffer.  Positions at or beyond `capacity` are not written; the cursor
+ * still advances and ec3r_sync_status then returns EC3R_ERR_CAPACITY.
+ * Workspace: 8 bytes per 8192 points.
+ */
+ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
+                             const float* d_xyz, const float* d_conf, const ec3r_sim3* d_poses,
+                             float conf_threshold, int64_t index_base, float* d_out_xyz,
+                             int64_t* d_out_idx, int64_t capacity, int64_t* d_cursor,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EC3R_H */

@@ -25,7 +25,8 @@ Readings where the paper is silent (each also listed in the design notes):
   last one;
 * degeneracy: fewer than 3 valid points, total weight <= 0 or non-finite,
   source variance <= 0, or second singular value of the cross-covariance
-  <= 1e-6 times the first, or a non-finite result: the pair is flagged and
+  <= 1e-4 times the first (far above FP32 rounding of the moments, far
+  below any real scene), or a non-finite result: the pair is flagged and
   reported as the identity.
 """
 from __future__ import annotations
@@ -38,7 +39,7 @@ DEG_FEW = 1
 DEG_WEIGHT = 2
 DEG_RANK = 4
 DEG_NONFINITE = 8
-RANK_REL_TOL = 1e-6
+RANK_REL_TOL = 1e-4
 
 
 def pair_correspondences(xyz, conf, link_off, src, tgt, k, conf_min=0.0, rule="product",
@@ -159,7 +160,8 @@ def align_pairs(ps, delta=0.02, iters=10, conf_min=0.0, rule="product", pairs=No
         pcm = np.asarray(ps.pair_conf_min.cpu())
     out = []
     for k in (range(len(lo) - 1) if pairs is None else pairs):
-        cmin = float(pcm[k]) if pcm is not None else conf_min
+        # thresholds are float32, like the confidences they are compared with
+        cmin = float(np.float32(pcm[k] if pcm is not None else conf_min))
         P, Q, cp, cq, valid = pair_correspondences(xyz, conf, lo, src, tgt, k, cmin, rule)
         w = base_weights(cp[valid], cq[valid], rule)
         res = irls(P[valid], Q[valid], w, delta, iters)

@@ -1,0 +1,682 @@
+// Batched Huber-IRLS weighted-Umeyama Sim(3) registration of submap pairs.
+//
+// The paper registers the current submap against every connected submap by
+// minimising sum_i w_i |s R p_i + t - q_i|^2 over correspondences that are the
+// same pixel of a shared keyframe, with the confidences turned into weights,
+// and solves it with the weighted Umeyama closed form (Sec. III-C, Eq. (sim3)).
+// Here that solve is repeated inside a Huber IRLS loop, for many pairs at once:
+//
+//   set-up  : k_setup      one CTA per pair: validate links, map link -> pair,
+//                          pick a pivot (mean of <= 1024 sampled valid pairs)
+//   sweep k : k_sweep      one CTA per tile of 8192 pixels of one link: per point
+//                          validity, Huber weight from S_{k-1}, and the 19
+//                          pivot-centred weighted moments; writes one FP64
+//                          partial per tile (no atomics: deterministic)
+//   solve k : k_solve      one warp per pair: fixed-order FP64 sum of the
+//                          pair's tile partials, covariance, rotation as the
+//                          orthogonal polar factor (FP32 Jacobi seed, FP64
+//                          Newton-polar refinement), scale, translation
+//
+// The sweep is bandwidth-bound: it reads 32 bytes per pixel (p, q, c_p, c_q).
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace ec3r {
+namespace align {
+
+constexpr int TILE = 8192;  // pixels per sweep CTA
+constexpr int THREADS = 256;
+constexpr int NMOM = 19;
+// moment slots
+enum { M_W = 0, M_SP = 1, M_SQ = 4, M_PP = 7, M_QP = 8, M_COST = 17, M_CNT = 18 };
+constexpr double RANK_REL_TOL = 1e-4;
+
+struct PairState {
+  // FP32 view of the current and previous estimate, pivot-relative:
+  // residual e = A p' + b - q',  p' = p - piv_p, q' = q - piv_q, A = s R.
+  float A[9], b[3];
+  float Ap[9], bp[3];
+  float piv_p[3], piv_q[3];
+  float cmin;
+  int active;
+  int status;
+  int pad;
+  double Ad[9], bd[3];
+  double Adp[9], bdp[3];
+};
+
+__device__ __forceinline__ bool finitef(float x) { return fabsf(x) <= FLT_MAX; }
+
+// --------------------------------------------------------------------------
+// set-up
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(THREADS) k_setup(
+    const float* __restrict__ xyz, const float* __restrict__ conf, int64_t n_frames, int64_t hw,
+    int n_pairs, int64_t n_links, const int32_t* __restrict__ link_off,
+    const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
+    const float* __restrict__ pair_cmin, float cmin_default, int32_t* __restrict__ link_pair,
+    PairState* __restrict__ st, unsigned* flags) {
+  const int k = blockIdx.x;
+  __shared__ int bad;
+  __shared__ float red[THREADS / 32][7];
+  const int64_t l0 = link_off[k], l1 = link_off[k + 1];
+  if (threadIdx.x == 0) {
+    bad = (l0 < 0 || l1 < l0 || l1 > n_links || (k == 0 && l0 != 0) ||
+           (k == n_pairs - 1 && l1 != n_links));
+  }
+  __syncthreads();
+  if (!bad) {
+    for (int64_t l = l0 + threadIdx.x; l < l1; l += THREADS) {
+      const int a = src[l], b = tgt[l];
+      if (a < 0 || a >= n_frames || b < 0 || b >= n_frames) bad = 1;
+    }
+  }
+  __syncthreads();
+  const float cmin = pair_cmin ? pair_cmin[k] : cmin_default;
+  if (!bad) {
+    for (int64_t l = l0 + threadIdx.x; l < l1; l += THREADS) link_pair[l] = k;
+  }
+  // pivot: mean of up to 1024 valid correspondences sampled evenly
+  float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (!bad && l1 > l0) {
+    const int64_t npix = (l1 - l0) * hw;
+    for (int j = threadIdx.x; j < 1024; j += THREADS) {
+      int64_t f = (int64_t)((double)j * (double)npix / 1024.0);
+      if (f >= npix) f = npix - 1;
+      const int64_t l = l0 + f / hw, px = f % hw;
+      const float* P = xyz + ((int64_t)src[l] * hw + px) * 3;
+      const float* Q = xyz + ((int64_t)tgt[l] * hw + px) * 3;
+      const float cp = conf[(int64_t)src[l] * hw + px], cq = conf[(int64_t)tgt[l] * hw + px];
+      const float p0 = P[0], p1 = P[1], p2 = P[2], q0 = Q[0], q1 = Q[1], q2 = Q[2];
+      const bool v = finitef(p0) && finitef(p1) && finitef(p2) && finitef(q0) && finitef(q1) &&
+                     finitef(q2) && finitef(cp) && finitef(cq) && cp > cmin && cq > cmin;
+      if (v) {
+        acc[0] += p0; acc[1] += p1; acc[2] += p2;
+        acc[3] += q0; acc[4] += q1; acc[5] += q2;
+        acc[6] += 1.f;
+      }
+    }
+  }
+  for (int m = 0; m < 7; ++m)
+    for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+  if ((threadIdx.x & 31) == 0)
+    for (int m = 0; m < 7; ++m) red[threadIdx.x >> 5][m] = acc[m];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < THREADS / 32; ++w)
+      for (int m = 0; m < 7; ++m) s[m] += red[w][m];
+    PairState& S = st[k];
+    const float inv = s[6] > 0.f ? 1.f / s[6] : 0.f;
+    for (int i = 0; i < 3; ++i) {
+      S.piv_p[i] = s[i] * inv;
+      S.piv_q[i] = s[3 + i] * inv;
+    }
+    for (int i = 0; i < 9; ++i) {
+      S.A[i] = S.Ap[i] = (i % 4 == 0) ? 1.f : 0.f;
+      S.Ad[i] = S.Adp[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    }
+    for (int i = 0; i < 3; ++i) {
+      S.b[i] = S.bp[i] = 0.f;
+      S.bd[i] = S.bdp[i] = 0.0;
+    }
+    S.cmin = cmin;
+    S.active = bad ? 0 : 1;
+    S.status = bad ? (int)EC3R_PAIR_BAD_INPUT : 0;
+    if (bad) atomicOr(flags, FLAG_BAD_INDEX);
+  }
+}
+
+// --------------------------------------------------------------------------
+// moment sweep
+// --------------------------------------------------------------------------
+enum Kind { FIRST = 0, IRLS = 1, COST = 2 };
+
+// One point's contribution.  T is float (FP32 moments) or double (FP64).
+template <typename T, int KIND>
+struct PointOp {
+  T A[9], b[3], Ap[9], bp[3], pp[3], pq[3], delta;
+  float cmin;
+  int rule;
+
+  __device__ __forceinline__ void operator()(float p0, float p1, float p2, float q0, float q1,
+                                             float q2, float cp, float cq, T* acc) const {
+    const bool v = finitef(p0) && finitef(p1) && finitef(p2) && finitef(q0) && finitef(q1) &&
+                   finitef(q2) && finitef(cp) && finitef(cq) && cp > cmin && cq > cmin;
+    const T x0 = v ? (T)p0 - pp[0] : T(0), x1 = v ? (T)p1 - pp[1] : T(0),
+            x2 = v ? (T)p2 - pp[2] : T(0);
+    const T y0 = v ? (T)q0 - pq[0] : T(0), y1 = v ? (T)q1 - pq[1] : T(0),
+            y2 = v ? (T)q2 - pq[2] : T(0);
+    T w = rule == 0 ? (T)cp * (T)cq : (T)cp;
+    w = v ? w : T(0);
+    T h = T(1), r2 = T(0);
+    if (KIND != FIRST) {
+      const T* a = (KIND == COST) ? Ap : A;
+      const T* c = (KIND == COST) ? bp : b;
+      const T e0 = a[0] * x0 + a[1] * x1 + a[2] * x2 + c[0] - y0;
+      const T e1 = a[3] * x0 + a[4] * x1 + a[5] * x2 + c[1] - y1;
+      const T e2 = a[6] * x0 + a[7] * x1 + a[8] * x2 + c[2] - y2;
+      const T rr = e0 * e0 + e1 * e1 + e2 * e2;
+      if constexpr (sizeof(T) == 4) {
+        h = fminf(1.f, (float)delta * rsqrtf(rr));
+      } else {
+        h = rr <= delta * delta ? 1.0 : delta / sqrt(rr);
+      }
+      if (KIND == COST) {
+        const T f0 = A[0] * x0 + A[1] * x1 + A[2] * x2 + b[0] - y0;
+        const T f1 = A[3] * x0 + A[4] * x1 + A[5] * x2 + b[1] - y1;
+        const T f2 = A[6] * x0 + A[7] * x1 + A[8] * x2 + b[2] - y2;
+        r2 = f0 * f0 + f1 * f1 + f2 * f2;
+      } else {
+        r2 = rr;
+      }
+    }
+    const T om = w * h;
+    acc[M_W] += om;
+    acc[M_COST] += om * r2;
+    acc[M_CNT] += v ? T(1) : T(0);
+    if (KIND == COST) return;
+    const T wx0 = om * x0, wx1 = om * x1, wx2 = om * x2;
+    const T wy0 = om * y0, wy1 = om * y1, wy2 = om * y2;
+    acc[M_SP + 0] += wx0; acc[M_SP + 1] += wx1; acc[M_SP + 2] += wx2;
+    acc[M_SQ + 0] += wy0; acc[M_SQ + 1] += wy1; acc[M_SQ + 2] += wy2;
+    acc[M_PP] += wx0 * x0 + wx1 * x1 + wx2 * x2;
+    acc[M_QP + 0] += wy0 * x0; acc[M_QP + 1] += wy0 * x1; acc[M_QP + 2] += wy0 * x2;
+    acc[M_QP + 3] += wy1 * x0; acc[M_QP + 4] += wy1 * x1; acc[M_QP + 5] += wy1 * x2;
+    acc[M_QP + 6] += wy2 * x0; acc[M_QP + 7] += wy2 * x1; acc[M_QP + 8] += wy2 * x2;
+  }
+};
+
+// Per-tile partial moments.  Each thread sums its 32 pixels (8 groups of 4
+// consecutive pixels); warps combine by a pairwise butterfly in T; the eight
+// warp sums are added in FP64 in a fixed order.
+template <typename T, int KIND, bool VEC>
+__global__ void __launch_bounds__(THREADS, 2) k_sweep(
+    const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
+    const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
+    const int32_t* __restrict__ link_pair, const PairState* __restrict__ st, float delta,
+    int rule, double* __restrict__ partials) {
+  const int64_t t = blockIdx.x;
+  const int64_t l = t / tpl;
+  const int c = (int)(t - l * tpl);
+  const int k = link_pair[l];
+  if (k < 0) return;
+  const PairState& S = st[k];
+  if (!S.active) return;
+  PointOp<T, KIND> op;
+  if constexpr (sizeof(T) == 4) {
+    for (int i = 0; i < 9; ++i) { op.A[i] = S.A[i]; op.Ap[i] = S.Ap[i]; }
+    for (int i = 0; i < 3; ++i) { op.b[i] = S.b[i]; op.bp[i] = S.bp[i]; }
+  } else {
+    for (int i = 0; i < 9; ++i) { op.A[i] = S.Ad[i]; op.Ap[i] = S.Adp[i]; }
+    for (int i = 0; i < 3; ++i) { op.b[i] = S.bd[i]; op.bp[i] = S.bdp[i]; }
+  }
+  for (int i = 0; i < 3; ++i) { op.pp[i] = (T)S.piv_p[i]; op.pq[i] = (T)S.piv_q[i]; }
+  op.delta = (T)delta;
+  op.cmin = S.cmin;
+  op.rule = rule;
+
+  const int64_t fs = src[l], ft = tgt[l];
+  const int64_t px0 = (int64_t)c * TILE;
+  const float* P = xyz + (fs * hw + px0) * 3;
+  const float* Q = xyz + (ft * hw + px0) * 3;
+  const float* CP = conf + fs * hw + px0;
+  const float* CQ = conf + ft * hw + px0;
+  const int64_t rem = hw - px0;
+  const int npx = rem < TILE ? (int)rem : TILE;
+
+  T acc[NMOM];
+#pragma unroll
+  for (int m = 0; m < NMOM; ++m) acc[m] = T(0);
+
+#pragma unroll 2
+  for (int g = threadIdx.x; g < TILE / 4; g += THREADS) {
+    const int i0 = 4 * g;
+    if (i0 >= npx) break;
+    if (VEC && i0 + 4 <= npx) {
+      const float4* P4 = reinterpret_cast<const float4*>(P + 3 * i0);
+      const float4* Q4 = reinterpret_cast<const float4*>(Q + 3 * i0);
+      const float4 pa = __ldcs(P4), pb = __ldcs(P4 + 1), pc = __ldcs(P4 + 2);
+      const float4 qa = __ldcs(Q4), qb = __ldcs(Q4 + 1), qc = __ldcs(Q4 + 2);
+      const float4 cp = __ldcs(reinterpret_cast<const float4*>(CP + i0));
+      const float4 cq = __ldcs(reinterpret_cast<const float4*>(CQ + i0));
+      op(pa.x, pa.y, pa.z, qa.x, qa.y, qa.z, cp.x, cq.x, acc);
+      op(pa.w, pb.x, pb.y, qa.w, qb.x, qb.y, cp.y, cq.y, acc);
+      op(pb.z, pb.w, pc.x, qb.z, qb.w, qc.x, cp.z, cq.z, acc);
+      op(pc.y, pc.z, pc.w, qc.y, qc.z, qc.w, cp.w, cq.w, acc);
+    } else {
+      const int n = min(4, npx - i0);
+      for (int j = 0; j < n; ++j) {
+        const int i = i0 + j;
+        op(P[3 * i], P[3 * i + 1], P[3 * i + 2], Q[3 * i], Q[3 * i + 1], Q[3 * i + 2], CP[i],
+           CQ[i], acc);
+      }
+    }
+  }
+  // pairwise butterfly inside the warp
+#pragma unroll
+  for (int m = 0; m < NMOM; ++m)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+  __shared__ double red[THREADS / 32][NMOM];
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int m = 0; m < NMOM; ++m) red[warp][m] = (double)acc[m];
+  __syncthreads();
+  if (threadIdx.x < NMOM) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < THREADS / 32; ++w) s += red[w][threadIdx.x];
+    partials[t * NMOM + threadIdx.x] = s;
+  }
+}
+
+// --------------------------------------------------------------------------
+// solve
+// --------------------------------------------------------------------------
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (row-major), FP32.
+// Eigenvalues descending, eigenvectors in the columns of V.
+__device__ void jacobi_eig3f(float B[9], float V[9], float lam[3]) {
+  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.f : 0.f;
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    const float off = fabsf(B[1]) + fabsf(B[2]) + fabsf(B[5]);
+    const float dia = fabsf(B[0]) + fabsf(B[4]) + fabsf(B[8]);
+    if (off <= 1e-9f * dia) break;
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0;
+      const int q = pq == 0 ? 1 : 2;
+      const float bpq = B[3 * p + q];
+      if (fabsf(bpq) < 1e-30f) continue;
+      const float theta = (B[3 * q + q] - B[3 * p + p]) / (2.f * bpq);
+      const float tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+      const float cs = rsqrtf(tt * tt + 1.f), sn = tt * cs;
+      for (int r = 0; r < 3; ++r) {
+        const float brp = B[3 * r + p], brq = B[3 * r + q];
+        B[3 * r + p] = cs * brp - sn * brq;
+        B[3 * r + q] = sn * brp + cs * brq;
+      }
+      for (int r = 0; r < 3; ++r) {
+        const float bpr = B[3 * p + r], bqr = B[3 * q + r];
+        B[3 * p + r] = cs * bpr - sn * bqr;
+        B[3 * q + r] = sn * bpr + cs * bqr;
+      }
+      for (int r = 0; r < 3; ++r) {
+        const float vrp = V[3 * r + p], vrq = V[3 * r + q];
+        V[3 * r + p] = cs * vrp - sn * vrq;
+        V[3 * r + q] = sn * vrp + cs * vrq;
+      }
+    }
+  }
+  lam[0] = B[0]; lam[1] = B[4]; lam[2] = B[8];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2 - a; ++b)
+      if (lam[b] < lam[b + 1]) {
+        const float tl = lam[b]; lam[b] = lam[b + 1]; lam[b + 1] = tl;
+        for (int r = 0; r < 3; ++r) {
+          const float tv = V[3 * r + b]; V[3 * r + b] = V[3 * r + b + 1]; V[3 * r + b + 1] = tv;
+        }
+      }
+}
+
+// Rotation R (FP64) of the Umeyama solution, R = U diag(1,1,det(U)det(V)) V^T,
+// i.e. the orthogonal polar factor of Sig with det +1, and the Rayleigh
+// estimates d[0..2] of the signed singular values.  An FP32 Jacobi SVD seeds
+// R; two FP64 Newton-polar steps R <- R cay(w), (tr(Hs) I - Hs) w =
+// vee(H - H^T), H = R^T Sig, bring it to FP64 round-off.
+__device__ void polar_rotation(const double Sig[9], double R[9], double d[3]) {
+  double nrm = 0.0;
+  for (int i = 0; i < 9; ++i) nrm += Sig[i] * Sig[i];
+  nrm = sqrt(nrm);
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  float Sf[9], B[9], V[9], lam[3];
+  for (int i = 0; i < 9; ++i) Sf[i] = (float)(Sig[i] * inv);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      B[3 * i + j] = Sf[i] * Sf[j] + Sf[3 + i] * Sf[3 + j] + Sf[6 + i] * Sf[6 + j];
+  jacobi_eig3f(B, V, lam);
+  float v[3][3];
+  for (int c = 0; c < 3; ++c)
+    for (int r = 0; r < 3; ++r) v[c][r] = V[3 * r + c];
+  float u[3][3];
+  for (int c = 0; c < 2; ++c)
+    for (int r = 0; r < 3; ++r)
+      u[c][r] = Sf[3 * r] * v[c][0] + Sf[3 * r + 1] * v[c][1] + Sf[3 * r + 2] * v[c][2];
+  float n0 = sqrtf(u[0][0] * u[0][0] + u[0][1] * u[0][1] + u[0][2] * u[0][2]);
+  if (n0 < 1e-30f) { u[0][0] = 1.f; u[0][1] = 0.f; u[0][2] = 0.f; n0 = 1.f; }
+  for (int r = 0; r < 3; ++r) u[0][r] /= n0;
+  const float dp = u[0][0] * u[1][0] + u[0][1] * u[1][1] + u[0][2] * u[1][2];
+  for (int r = 0; r < 3; ++r) u[1][r] -= dp * u[0][r];
+  float n1 = sqrtf(u[1][0] * u[1][0] + u[1][1] * u[1][1] + u[1][2] * u[1][2]);
+  if (n1 < 1e-30f) {  // any unit vector orthogonal to u0
+    float a[3] = {0.f, 0.f, 0.f};
+    a[fabsf(u[0][0]) < 0.5f ? 0 : 1] = 1.f;
+    const float da = a[0] * u[0][0] + a[1] * u[0][1] + a[2] * u[0][2];
+    for (int r = 0; r < 3; ++r) u[1][r] = a[r] - da * u[0][r];
+    n1 = sqrtf(u[1][0] * u[1][0] + u[1][1] * u[1][1] + u[1][2] * u[1][2]);
+  }
+  for (int r = 0; r < 3; ++r) u[1][r] /= n1;
+  u[2][0] = u[0][1] * u[1][2] - u[0][2] * u[1][1];
+  u[2][1] = u[0][2] * u[1][0] - u[0][0] * u[1][2];
+  u[2][2] = u[0][0] * u[1][1] - u[0][1] * u[1][0];
+  const float detV = v[0][0] * (v[1][1] * v[2][2] - v[1][2] * v[2][1]) -
+                     v[0][1] * (v[1][0] * v[2][2] - v[1][2] * v[2][0]) +
+                     v[0][2] * (v[1][0] * v[2][1] - v[1][1] * v[2][0]);
+  const float e3 = detV < 0.f ? -1.f : 1.f;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      R[3 * i + j] = (double)(u[0][i] * v[0][j] + u[1][i] * v[1][j] + e3 * u[2][i] * v[2][j]);
+  for (int it = 0; it < 2; ++it) {
+    double H[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        H[3 * i + j] = R[i] * Sig[j] + R[3 + i] * Sig[3 + j] + R[6 + i] * Sig[6 + j];
+    const double a0 = H[7] - H[5], a1 = H[2] - H[6], a2 = H[3] - H[1];
+    const double tr = H[0] + H[4] + H[8];
+    double M[9];
+    M[0] = tr - H[0]; M[4] = tr - H[4]; M[8] = tr - H[8];
+    M[1] = M[3] = -0.5 * (H[1] + H[3]);
+    M[2] = M[6] = -0.5 * (H[2] + H[6]);
+    M[5] = M[7] = -0.5 * (H[5] + H[7]);
+    const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8],
+                 c02 = M[3] * M[7] - M[4] * M[6];
+    const double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+    if (!(fabs(det) > 1e-300)) break;
+    const double c11 = M[0] * M[8] - M[2] * M[6], c12 = M[2] * M[3] - M[0] * M[5],
+                 c22 = M[0] * M[4] - M[1] * M[3];
+    const double id = 1.0 / det;  // M symmetric: inverse = cofactor matrix / det
+    const double w0 = (c00 * a0 + c01 * a1 + c02 * a2) * id;
+    const double w1 = (c01 * a0 + c11 * a1 + c12 * a2) * id;
+    const double w2 = (c02 * a0 + c12 * a1 + c22 * a2) * id;
+    // Cayley transform of w: C = I + 2/(1+|h|^2) (h^ + h^ h^), h = w/2
+    const double h0 = 0.5 * w0, h1 = 0.5 * w1, h2 = 0.5 * w2;
+    const double f = 2.0 / (1.0 + h0 * h0 + h1 * h1 + h2 * h2);
+    double C[9];
+    C[0] = 1.0 - f * (h1 * h1 + h2 * h2);
+    C[4] = 1.0 - f * (h0 * h0 + h2 * h2);
+    C[8] = 1.0 - f * (h0 * h0 + h1 * h1);
+    C[1] = f * (-h2 + h0 * h1);
+    C[2] = f * (h1 + h0 * h2);
+    C[3] = f * (h2 + h0 * h1);
+    C[5] = f * (-h0 + h1 * h2);
+    C[6] = f * (-h1 + h0 * h2);
+    C[7] = f * (h0 + h1 * h2);
+    double Rn[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        Rn[3 * i + j] = R[3 * i] * C[j] + R[3 * i + 1] * C[3 + j] + R[3 * i + 2] * C[6 + j];
+    for (int i = 0; i < 9; ++i) R[i] = Rn[i];
+  }
+  double H[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      H[3 * i + j] = R[i] * Sig[j] + R[3 + i] * Sig[3 + j] + R[6 + i] * Sig[6 + j];
+  for (int c = 0; c < 3; ++c) {
+    const double x0 = v[c][0], x1 = v[c][1], x2 = v[c][2];
+    const double y0 = H[0] * x0 + H[1] * x1 + H[2] * x2;
+    const double y1 = H[3] * x0 + H[4] * x1 + H[5] * x2;
+    const double y2 = H[6] * x0 + H[7] * x1 + H[8] * x2;
+    d[c] = (x0 * y0 + x1 * y1 + x2 * y2) / (x0 * x0 + x1 * x1 + x2 * x2);
+  }
+}
+
+__device__ void write_identity(ec3r_sim3* o) {
+  o->s = 1.0;
+  for (int i = 0; i < 9; ++i) o->R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  for (int i = 0; i < 3; ++i) o->t[i] = 0.0;
+}
+
+// One warp per pair: FP64 tile sums (lane m < 19 owns moment m), then lane 0
+// solves.  `last` marks the final iteration (writes the outputs).
+__global__ void __launch_bounds__(256) k_solve(int n_pairs, const int32_t* __restrict__ link_off,
+                                               int tpl, const double* __restrict__ partials,
+                                               PairState* __restrict__ st,
+                                               ec3r_sim3* __restrict__ out,
+                                               int32_t* __restrict__ status_out, int last) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  __shared__ double mom[8][NMOM];
+  if (warp >= n_pairs) return;
+  PairState& S = st[warp];
+  const int wib = threadIdx.x >> 5;
+  if (!S.active) {
+    if (last && lane == 0) {
+      write_identity(&out[warp]);
+      status_out[warp] = S.status;
+    }
+    return;
+  }
+  const int64_t t0 = (int64_t)link_off[warp] * tpl, t1 = (int64_t)link_off[warp + 1] * tpl;
+  if (lane < NMOM) {
+    double s = 0.0;
+    for (int64_t t = t0; t < t1; ++t) s += partials[t * NMOM + lane];
+    mom[wib][lane] = s;
+  }
+  __syncwarp();
+  if (lane != 0) return;
+  const double* M = mom[wib];
+  unsigned status = 0;
+  const double W = M[M_W], N = M[M_CNT];
+  double R[9], d[3], s = 1.0, b[3] = {0, 0, 0};
+  if (N < 3.0) {
+    status = EC3R_PAIR_FEW_POINTS;
+  } else if (!(W > 0.0) || !isfinite(W)) {
+    status = EC3R_PAIR_ZERO_WEIGHT;
+  } else {
+    const double iw = 1.0 / W;
+    const double mp[3] = {M[M_SP] * iw, M[M_SP + 1] * iw, M[M_SP + 2] * iw};
+    const double mq[3] = {M[M_SQ] * iw, M[M_SQ + 1] * iw, M[M_SQ + 2] * iw};
+    double Sig[9];
+    bool fin = true;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        Sig[3 * i + j] = M[M_QP + 3 * i + j] * iw - mq[i] * mp[j];
+        fin &= isfinite(Sig[3 * i + j]);
+      }
+    const double var = M[M_PP] * iw - (mp[0] * mp[0] + mp[1] * mp[1] + mp[2] * mp[2]);
+    if (!fin || !isfinite(var)) {
+      status = EC3R_PAIR_NONFINITE;
+    } else if (!(var > 0.0)) {
+      status = EC3R_PAIR_RANK;
+    } else {
+      polar_rotation(Sig, R, d);
+      if (!(d[0] > 0.0) || fabs(d[1]) <= RANK_REL_TOL * d[0]) {
+        status = EC3R_PAIR_RANK;
+      } else {
+        // tr(R^T Sig) = tr(D E): the Umeyama scale numerator
+        double tr = 0.0;
+        for (int i = 0; i < 9; ++i) tr += R[i] * Sig[i];
+        s = tr / var;
+        for (int i = 0; i < 3; ++i)
+          b[i] = mq[i] - s * (R[3 * i] * mp[0] + R[3 * i + 1] * mp[1] + R[3 * i + 2] * mp[2]);
+        bool ok = isfinite(s) && s > 0.0;
+        for (int i = 0; i < 3; ++i) ok &= isfinite(b[i]);
+        if (!ok) status = EC3R_PAIR_NONFINITE;
+      }
+    }
+  }
+  if (status) {
+    S.status = (int)status;
+    S.active = 0;
+    write_identity(&out[warp]);
+    status_out[warp] = (int)status;
+    return;
+  }
+  // shift the current estimate to "previous", store the new one
+  for (int i = 0; i < 9; ++i) {
+    S.Ap[i] = S.A[i];
+    S.Adp[i] = S.Ad[i];
+    S.Ad[i] = s * R[i];
+    S.A[i] = (float)S.Ad[i];
+  }
+  for (int i = 0; i < 3; ++i) {
+    S.bp[i] = S.b[i];
+    S.bdp[i] = S.bd[i];
+    S.bd[i] = b[i];
+    S.b[i] = (float)b[i];
+  }
+  if (last) {
+    ec3r_sim3& o = out[warp];
+    o.s = s;
+    for (int i = 0; i < 9; ++i) o.R[i] = R[i];
+    const double pp[3] = {S.piv_p[0], S.piv_p[1], S.piv_p[2]};
+    for (int i = 0; i < 3; ++i)
+      o.t[i] = b[i] + (double)S.piv_q[i] -
+               s * (R[3 * i] * pp[0] + R[3 * i + 1] * pp[1] + R[3 * i + 2] * pp[2]);
+    status_out[warp] = 0;
+  }
+}
+
+// cost = sum om r^2 / sum om from the cost sweep's partials.
+__global__ void k_cost(int n_pairs, const int32_t* __restrict__ link_off, int tpl,
+                       const double* __restrict__ partials, const PairState* __restrict__ st,
+                       double* __restrict__ cost) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_pairs) return;
+  if (!st[k].active) {
+    cost[k] = 0.0;
+    return;
+  }
+  const int64_t t0 = (int64_t)link_off[k] * tpl, t1 = (int64_t)link_off[k + 1] * tpl;
+  double w = 0.0, c = 0.0;
+  for (int64_t t = t0; t < t1; ++t) {
+    w += partials[t * NMOM + M_W];
+    c += partials[t * NMOM + M_COST];
+  }
+  cost[k] = w > 0.0 ? c / w : 0.0;
+}
+
+template <typename T, bool VEC>
+void launch_sweep(int kind, int64_t n_tiles, cudaStream_t s, const float* xyz, const float* conf,
+                  int64_t hw, int tpl, const int32_t* src, const int32_t* tgt,
+                  const int32_t* link_pair, const PairState* st, float delta, int rule,
+                  double* partials) {
+  const dim3 grid((unsigned)n_tiles);
+  if (kind == FIRST)
+    k_sweep<T, FIRST, VEC><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt, link_pair, st,
+                                                    delta, rule, partials);
+  else if (kind == IRLS)
+    k_sweep<T, IRLS, VEC><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt, link_pair, st,
+                                                   delta, rule, partials);
+  else
+    k_sweep<T, COST, VEC><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt, link_pair, st,
+                                                   delta, rule, partials);
+}
+
+}  // namespace align
+}  // namespace ec3r
+
+using namespace ec3r;
+using namespace ec3r::align;
+
+extern "C" {
+
+void ec3r_align_opts_default(ec3r_align_opts* o) {
+  if (!o) return;
+  o->huber_delta = 0.02f;
+  o->iters = 10;
+  o->conf_min = 0.0f;
+  o->weight_rule = EC3R_WEIGHT_PRODUCT;
+  o->precision = EC3R_PREC_FP32C;
+  o->want_cost = 0;
+}
+
+ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d_conf,
+                               int64_t n_frames, int64_t hw, int n_pairs, int64_t n_links,
+                               const int32_t* d_link_off, const int32_t* d_src,
+                               const int32_t* d_tgt, const float* d_pair_conf_min,
+                               const ec3r_align_opts* opts, ec3r_sim3* d_out,
+                               int32_t* d_pair_status, double* d_pair_cost, void* stream) {
+  if (!ctx) return EC3R_ERR_INVALID_ARG;
+  if (!opts) return set_error(ctx, EC3R_ERR_INVALID_ARG, "opts is NULL");
+  if (n_pairs < 0 || n_links < 0 || hw <= 0 || n_frames <= 0)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "bad sizes (n_pairs %d, n_links %lld, hw %lld)",
+                     n_pairs, (long long)n_links, (long long)hw);
+  if (n_pairs == 0) return EC3R_OK;
+  if (!d_xyz || !d_conf || !d_link_off || !d_out || !d_pair_status ||
+      (n_links > 0 && (!d_src || !d_tgt)))
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
+  if (!(opts->huber_delta > 0.f) || !(opts->huber_delta <= FLT_MAX) || opts->iters < 1 ||
+      opts->iters > 64 || (opts->weight_rule != 0 && opts->weight_rule != 1) ||
+      (opts->precision != 0 && opts->precision != 1) || opts->conf_min != opts->conf_min)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "bad ec3r_align_opts");
+  if (opts->want_cost && !d_pair_cost)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "want_cost set but d_pair_cost is NULL");
+  const int64_t tpl = (hw + TILE - 1) / TILE;
+  const int64_t n_tiles = n_links * tpl;
+  if (n_tiles >= ((int64_t)1 << 31) || n_frames > ((int64_t)1 << 40) / hw)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "problem too large for one call");
+  EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  void *p_state, *p_part, *p_lp;
+  ec3r_status st;
+  if ((st = ensure_buf(ctx, "align.state", sizeof(PairState) * (size_t)n_pairs, s, &p_state)))
+    return st;
+  if ((st = ensure_buf(ctx, "align.partials", sizeof(double) * NMOM * (size_t)(n_tiles + 1), s,
+                       &p_part)))
+    return st;
+  if ((st = ensure_buf(ctx, "align.link_pair", sizeof(int32_t) * (size_t)(n_links + 1), s,
+                       &p_lp)))
+    return st;
+  PairState* state = (PairState*)p_state;
+  double* partials = (double*)p_part;
+  int32_t* link_pair = (int32_t*)p_lp;
+  const bool vec =
+      (hw % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0) && ((uintptr_t)d_conf % 16 == 0);
+  const bool fp64 = opts->precision == EC3R_PREC_FP64;
+  const ec3r_align_opts o = *opts;
+  const std::string key = key_of(
+      "align", {(uint64_t)d_xyz, (uint64_t)d_conf, (uint64_t)n_frames, (uint64_t)hw,
+                (uint64_t)n_pairs, (uint64_t)n_links, (uint64_t)d_link_off, (uint64_t)d_src,
+                (uint64_t)d_tgt, (uint64_t)d_pair_conf_min, fbits(o.huber_delta),
+                (uint64_t)o.iters, fbits(o.conf_min), (uint64_t)o.weight_rule,
+                (uint64_t)o.precision, (uint64_t)o.want_cost, (uint64_t)d_out,
+                (uint64_t)d_pair_status, (uint64_t)d_pair_cost});
+  return run_graph(ctx, key, s, [&](cudaStream_t cs) -> ec3r_status {
+    EC3R_CUDA_TRY(ctx, cudaMemsetAsync(link_pair, 0xff, sizeof(int32_t) * (size_t)(n_links + 1),
+                                       cs));
+    traced(ctx, cs, "align_setup", [&] {
+      k_setup<<<n_pairs, THREADS, 0, cs>>>(d_xyz, d_conf, n_frames, hw, n_pairs, n_links,
+                                           d_link_off, d_src, d_tgt, d_pair_conf_min,
+                                           o.conf_min, link_pair, state, ctx->d_flags);
+    });
+    const int solve_blocks = (n_pairs + 7) / 8;
+    for (int it = 1; it <= o.iters + (o.want_cost ? 1 : 0); ++it) {
+      const int kind = it == 1 ? FIRST : (it > o.iters ? COST : IRLS);
+      // the cost of a single solve uses h = 1, which a huge delta reproduces
+      const float dl = (kind == COST && o.iters == 1) ? FLT_MAX : o.huber_delta;
+      if (n_tiles > 0) traced(ctx, cs, fp64 ? "irls_sweep_fp64" : "irls_sweep_fp32", [&] {
+        if (fp64) {
+          if (vec)
+            launch_sweep<double, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
+                                       d_tgt, link_pair, state, dl, o.weight_rule, partials);
+          else
+            launch_sweep<double, false>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
+                                        d_tgt, link_pair, state, dl, o.weight_rule, partials);
+        } else {
+          if (vec)
+            launch_sweep<float, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
+                                      d_tgt, link_pair, state, dl, o.weight_rule, partials);
+          else
+            launch_sweep<float, false>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
+                                       d_tgt, link_pair, state, dl, o.weight_rule, partials);
+        }
+      });
+      if (kind == COST)
+        traced(ctx, cs, "irls_cost", [&] {
+          k_cost<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, d_link_off, (int)tpl,
+                                                        partials, state, d_pair_cost);
+        });
+      else
+        traced(ctx, cs, "sim3_solve", [&] {
+          k_solve<<<solve_blocks, 256, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
+                                                d_out, d_pair_status, it == o.iters);
+        });
+    }
+    EC3R_CUDA_TRY(ctx, cudaGetLastError());
+    return EC3R_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,244 @@
+// Confidence-filtered fusion of submap points into one global point buffer.
+//
+// The paper takes "the global coordinates of all points in the current
+// submap" from the estimated submap transforms (Sec. III-C, Point
+// Correction); every pixel of a submap carries a confidence (Sec. III-C,
+// Feed-Forward Inference).  Kept points (confidence > threshold) are written
+// in ascending flat index, so the compaction is unique and its indices are
+// exact:
+//
+//   k_fuse_count    one CTA per tile of 8192 points of one submap: keep count
+//   k_fuse_scan     one CTA: exclusive scan of the tile counts from *cursor,
+//                   advances *cursor by the total
+//   k_fuse_scatter  one CTA per tile: ordered block-wide compaction in rounds
+//                   of 1024 points, Sim(3) transform in FP32 (FMA), writes
+//                   the point and its int64 global index
+//
+// Bytes per input point: 4 (count) + 16 (scatter read) + 20 per kept point.
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace ec3r {
+namespace fuse {
+
+constexpr int TILE = 8192;
+constexpr int THREADS = 256;
+constexpr int ROUND = 4 * THREADS;  // points per compaction round
+
+__device__ __forceinline__ bool keep(float c, float thr) { return c > thr; }  // NaN -> false
+
+template <bool VEC>
+__global__ void __launch_bounds__(THREADS) k_fuse_count(const float* __restrict__ conf,
+                                                        int64_t n, int tps, float thr,
+                                                        int32_t* __restrict__ tile_count) {
+  const int64_t t = blockIdx.x;
+  const int64_t m = t / tps;
+  const int c = (int)(t - m * tps);
+  const int64_t base = m * n + (int64_t)c * TILE;
+  const int64_t rem = n - (int64_t)c * TILE;
+  const int npx = rem < TILE ? (int)rem : TILE;
+  int cnt = 0;
+  for (int i0 = 4 * threadIdx.x; i0 < npx; i0 += 4 * THREADS) {
+    if (VEC && i0 + 4 <= npx) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(conf + base + i0));
+      cnt += keep(v.x, thr) + keep(v.y, thr) + keep(v.z, thr) + keep(v.w, thr);
+    } else {
+      for (int j = i0; j < min(i0 + 4, npx); ++j) cnt += keep(conf[base + j], thr);
+    }
+  }
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  __shared__ int red[THREADS / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < THREADS / 32; ++w) s += red[w];
+    tile_count[t] = s;
+  }
+}
+
+// Single-CTA exclusive scan of the tile counts.  tile_off[t] = *cursor + sum
+// of counts before t; *cursor += total.
+__global__ void __launch_bounds__(1024) k_fuse_scan(const int32_t* __restrict__ tile_count,
+                                                    int64_t n_tiles,
+                                                    int64_t* __restrict__ tile_off,
+                                                    int64_t* cursor) {
+  __shared__ int64_t wsum[32];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = *cursor;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t b = 0; b < n_tiles; b += 1024) {
+    const int64_t i = b + threadIdx.x;
+    const int64_t v = i < n_tiles ? tile_count[i] : 0;
+    int64_t x = v;  // inclusive warp scan
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int64_t ws = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += y;
+      }
+      wsum[lane] = ws;  // inclusive over warps
+    }
+    __syncthreads();
+    const int64_t before = (warp > 0 ? wsum[warp - 1] : 0) + x - v;
+    if (i < n_tiles) tile_off[i] = carry + before;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += wsum[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *cursor = carry;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(THREADS) k_fuse_scatter(
+    const float* __restrict__ xyz, const float* __restrict__ conf, int64_t n, int tps,
+    const ec3r_sim3* __restrict__ poses, float thr, int64_t index_base,
+    const int64_t* __restrict__ tile_off, float* __restrict__ out_xyz,
+    int64_t* __restrict__ out_idx, int64_t capacity, unsigned* flags) {
+  const int64_t t = blockIdx.x;
+  const int64_t m = t / tps;
+  const int c = (int)(t - m * tps);
+  const int64_t tile0 = (int64_t)c * TILE;
+  const int64_t base = m * n + tile0;
+  const int64_t rem = n - tile0;
+  const int npx = rem < TILE ? (int)rem : TILE;
+  __shared__ float A[12];
+  __shared__ int wcnt[THREADS / 32];
+  if (threadIdx.x < 12) {
+    const ec3r_sim3& P = poses[m];
+    const int r = threadIdx.x / 4, col = threadIdx.x % 4;
+    A[threadIdx.x] = col < 3 ? (float)(P.s * P.R[3 * r + col]) : (float)P.t[r];
+  }
+  __syncthreads();
+  const float a00 = A[0], a01 = A[1], a02 = A[2], a03 = A[3];
+  const float a10 = A[4], a11 = A[5], a12 = A[6], a13 = A[7];
+  const float a20 = A[8], a21 = A[9], a22 = A[10], a23 = A[11];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t pos = tile_off[t];
+  bool overflow = false;
+  for (int r0 = 0; r0 < npx; r0 += ROUND) {
+    const int i0 = r0 + 4 * threadIdx.x;
+    float cf[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+    float p[12];
+    if (VEC && i0 + 4 <= npx) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(conf + base + i0));
+      cf[0] = v.x; cf[1] = v.y; cf[2] = v.z; cf[3] = v.w;
+    } else {
+      for (int j = 0; j < 4; ++j)
+        if (i0 + j < npx) cf[j] = conf[base + i0 + j];
+    }
+    unsigned km = 0;
+    for (int j = 0; j < 4; ++j) km |= (i0 + j < npx && keep(cf[j], thr)) ? (1u << j) : 0u;
+    if (km) {
+      if (VEC && i0 + 4 <= npx) {
+        const float4* X = reinterpret_cast<const float4*>(xyz + 3 * (base + i0));
+        const float4 u = __ldcs(X), v = __ldcs(X + 1), w = __ldcs(X + 2);
+        p[0] = u.x; p[1] = u.y; p[2] = u.z; p[3] = u.w; p[4] = v.x; p[5] = v.y;
+        p[6] = v.z; p[7] = v.w; p[8] = w.x; p[9] = w.y; p[10] = w.z; p[11] = w.w;
+      } else {
+        for (int j = 0; j < 4; ++j)
+          if (km & (1u << j))
+            for (int d = 0; d < 3; ++d) p[3 * j + d] = xyz[3 * (base + i0 + j) + d];
+      }
+    }
+    const int cnt = __popc(km);
+    int x = cnt;  // inclusive warp scan of counts (thread order = point order)
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wcnt[warp] = x;
+    __syncthreads();
+    int wbefore = 0, total = 0;
+    for (int w = 0; w < THREADS / 32; ++w) {
+      const int v = wcnt[w];
+      wbefore += w < warp ? v : 0;
+      total += v;
+    }
+    int64_t o = pos + wbefore + (x - cnt);
+    for (int j = 0; j < 4; ++j) {
+      if (!(km & (1u << j))) continue;
+      if (o >= 0 && o < capacity) {
+        const float x0 = p[3 * j], x1 = p[3 * j + 1], x2 = p[3 * j + 2];
+        out_xyz[3 * o + 0] = fmaf(a00, x0, fmaf(a01, x1, fmaf(a02, x2, a03)));
+        out_xyz[3 * o + 1] = fmaf(a10, x0, fmaf(a11, x1, fmaf(a12, x2, a13)));
+        out_xyz[3 * o + 2] = fmaf(a20, x0, fmaf(a21, x1, fmaf(a22, x2, a23)));
+        out_idx[o] = index_base + base + i0 + j;
+      } else {
+        overflow = true;
+      }
+      ++o;
+    }
+    pos += total;
+    __syncthreads();
+  }
+  if (overflow) atomicOr(flags, FLAG_CAPACITY);
+}
+
+}  // namespace fuse
+}  // namespace ec3r
+
+using namespace ec3r;
+using namespace ec3r::fuse;
+
+extern "C" ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
+                                        const float* d_xyz, const float* d_conf,
+                                        const ec3r_sim3* d_poses, float conf_threshold,
+                                        int64_t index_base, float* d_out_xyz,
+                                        int64_t* d_out_idx, int64_t capacity,
+                                        int64_t* d_cursor, void* stream) {
+  if (!ctx) return EC3R_ERR_INVALID_ARG;
+  if (n_submaps < 0 || pts_per_submap < 0 || capacity < 0 || index_base < 0)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "negative size");
+  if (n_submaps == 0 || pts_per_submap == 0) return EC3R_OK;
+  if (!d_xyz || !d_conf || !d_poses || !d_cursor || (capacity > 0 && (!d_out_xyz || !d_out_idx)))
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
+  if (conf_threshold != conf_threshold)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "conf_threshold is NaN");
+  const int64_t tps = (pts_per_submap + TILE - 1) / TILE;
+  const int64_t n_tiles = tps * n_submaps;
+  if (n_tiles >= ((int64_t)1 << 31) || tps >= ((int64_t)1 << 30))
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "problem too large for one call");
+  EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  void *p_cnt, *p_off;
+  ec3r_status st;
+  if ((st = ensure_buf(ctx, "fuse.count", sizeof(int32_t) * (size_t)n_tiles, s, &p_cnt))) return st;
+  if ((st = ensure_buf(ctx, "fuse.off", sizeof(int64_t) * (size_t)n_tiles, s, &p_off))) return st;
+  int32_t* cnt = (int32_t*)p_cnt;
+  int64_t* off = (int64_t*)p_off;
+  const bool vec = (pts_per_submap % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0) &&
+                   ((uintptr_t)d_conf % 16 == 0);
+  const dim3 grid((unsigned)n_tiles);
+  traced(ctx, s, "fuse_count", [&] {
+    if (vec)
+      k_fuse_count<true><<<grid, THREADS, 0, s>>>(d_conf, pts_per_submap, (int)tps,
+                                                  conf_threshold, cnt);
+    else
+      k_fuse_count<false><<<grid, THREADS, 0, s>>>(d_conf, pts_per_submap, (int)tps,
+                                                   conf_threshold, cnt);
+  });
+  traced(ctx, s, "fuse_scan", [&] { k_fuse_scan<<<1, 1024, 0, s>>>(cnt, n_tiles, off, d_cursor); });
+  traced(ctx, s, "fuse_scatter", [&] {
+    if (vec)
+      k_fuse_scatter<true><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, pts_per_submap, (int)tps,
+                                                    d_poses, conf_threshold, index_base, off,
+                                                    d_out_xyz, d_out_idx, capacity,
+                                                    ctx->d_flags);
+    else
+      k_fuse_scatter<false><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, pts_per_submap, (int)tps,
+                                                     d_poses, conf_threshold, index_base, off,
+                                                     d_out_xyz, d_out_idx, capacity,
+                                                     ctx->d_flags);
+  });
+  EC3R_CUDA_TRY(ctx, cudaGetLastError());
+  return EC3R_OK;
+}

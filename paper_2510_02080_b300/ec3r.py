@@ -1,0 +1,206 @@
+"""ctypes binding of the C-ABI library ``libec3r.so`` (see ``include/ec3r.h``).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch provides device memory and the current stream.  There is no
+fallback: if the library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libec3r.so")
+_lib = None
+
+OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
+                4: "capacity exceeded", 5: "not positive definite", 6: "timeout",
+                7: "degenerate pair", 8: "workspace growth during capture"}
+PAIR_FEW_POINTS, PAIR_ZERO_WEIGHT, PAIR_RANK, PAIR_NONFINITE, PAIR_BAD_INPUT = 1, 2, 4, 8, 16
+PREC = {"fp32c": 0, "fp64": 1}
+RULE = {"product": 0, "src": 1}
+
+# Every symbol include/ec3r.h declares (checked by the CPU tests).
+EXPORTS = ("ec3r_create", "ec3r_destroy", "ec3r_last_error", "ec3r_status_string",
+           "ec3r_version", "ec3r_sync_status", "ec3r_align_opts_default",
+           "ec3r_align_submaps", "ec3r_fuse_points", "ec3r_profile", "ec3r_profile_read")
+
+
+class Sim3(C.Structure):
+    _fields_ = [("s", C.c_double), ("R", C.c_double * 9), ("t", C.c_double * 3)]
+
+
+class AlignOpts(C.Structure):
+    _fields_ = [("huber_delta", C.c_float), ("iters", C.c_int), ("conf_min", C.c_float),
+                ("weight_rule", C.c_int), ("precision", C.c_int), ("want_cost", C.c_int)]
+
+
+class Ec3rError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+
+
+def _declare(l):
+    l.ec3r_create.argtypes = [C.POINTER(_P), C.c_int]
+    l.ec3r_destroy.argtypes = [_P]
+    l.ec3r_destroy.restype = None
+    l.ec3r_last_error.argtypes = [_P]
+    l.ec3r_last_error.restype = C.c_char_p
+    l.ec3r_status_string.argtypes = [C.c_int]
+    l.ec3r_status_string.restype = C.c_char_p
+    l.ec3r_version.argtypes = []
+    l.ec3r_version.restype = C.c_char_p
+    l.ec3r_sync_status.argtypes = [_P, _P]
+    l.ec3r_align_opts_default.argtypes = [C.POINTER(AlignOpts)]
+    l.ec3r_align_opts_default.restype = None
+    l.ec3r_align_submaps.argtypes = [_P, _P, _P, _I64, _I64, C.c_int, _I64, _P, _P, _P, _P,
+                                     C.POINTER(AlignOpts), _P, _P, _P, _P]
+    l.ec3r_fuse_points.argtypes = [_P, C.c_int, _I64, _P, _P, _P, C.c_float, _I64, _P, _P,
+                                   _I64, _P, _P]
+    l.ec3r_profile.argtypes = [_P, C.c_int]
+    l.ec3r_profile_read.argtypes = [_P, C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_int)]
+    for name in ("ec3r_create", "ec3r_sync_status", "ec3r_align_submaps", "ec3r_fuse_points",
+                 "ec3r_profile", "ec3r_profile_read"):
+        getattr(l, name).restype = C.c_int
+
+
+def lib():
+    """Load (once) and return the library; raises if it is not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2510_02080_b300.build`")
+        l = C.CDLL(LIB_PATH)
+        _declare(l)
+        _lib = l
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """Owns an ``ec3r_ctx`` (workspace, cached graphs) on one device."""
+
+    def __init__(self, device=None):
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        self._lib = lib()
+        h = C.c_void_p()
+        st = self._lib.ec3r_create(C.byref(h), dev.index)
+        if st != OK:
+            raise Ec3rError(st, "ec3r_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ec3r_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise Ec3rError(st, self._lib.ec3r_last_error(self._h).decode())
+
+    def sync_status(self, stream=None):
+        """Waits for the stream; returns the status code (0 = ok) of device-side checks."""
+        return self._lib.ec3r_sync_status(self._h, _stream(stream))
+
+    def profile(self, enable=True):
+        """Per-kernel CUDA-event timing of every launch (bypasses cached graphs)."""
+        self._check(self._lib.ec3r_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel: (total_ms, launches)} since the last read; waits for the events."""
+        cap, nl = 64, 64
+        names = C.create_string_buffer(cap * nl)
+        ms = (C.c_double * cap)()
+        cnt = (C.c_int64 * cap)()
+        n = C.c_int()
+        self._check(self._lib.ec3r_profile_read(self._h, cap, names, nl, ms, cnt, C.byref(n)))
+        out = {}
+        for i in range(min(n.value, cap)):
+            nm = names.raw[i * nl:(i + 1) * nl].split(b"\0", 1)[0].decode()
+            out[nm] = (ms[i], cnt[i])
+        return out
+
+    def last_error(self):
+        return self._lib.ec3r_last_error(self._h).decode()
+
+    # -- registration ------------------------------------------------------
+    def align_submaps(self, xyz, conf, link_off, src, tgt, pair_conf_min=None, *, delta=0.02,
+                      iters=10, conf_min=0.0, rule="product", precision="fp32c",
+                      want_cost=False, out=None, status=None, cost=None, stream=None):
+        """Returns (S [n_pairs,13] float64 = (s, R row-major, t), status int32, cost|None)."""
+        n_frames, hw = int(conf.shape[0]), int(conf.shape[1])
+        if xyz.dtype != torch.float32 or conf.dtype != torch.float32:
+            raise ValueError("xyz and conf must be float32")
+        if tuple(xyz.shape) != (n_frames, hw, 3):
+            raise ValueError("xyz must be [n_frames, hw, 3]")
+        n_pairs = int(link_off.numel()) - 1
+        dev = xyz.device
+        if out is None:
+            out = torch.empty((n_pairs, 13), dtype=torch.float64, device=dev)
+        if status is None:
+            status = torch.empty((n_pairs,), dtype=torch.int32, device=dev)
+        if want_cost and cost is None:
+            cost = torch.empty((n_pairs,), dtype=torch.float64, device=dev)
+        o = AlignOpts(float(delta), int(iters), float(conf_min), RULE[rule], PREC[precision],
+                      1 if want_cost else 0)
+        st = self._lib.ec3r_align_submaps(
+            self._h, _ptr(xyz), _ptr(conf), n_frames, hw, n_pairs, int(src.numel()),
+            _ptr(link_off), _ptr(src), _ptr(tgt), _ptr(pair_conf_min), C.byref(o), _ptr(out),
+            _ptr(status), _ptr(cost) if want_cost else None, _stream(stream))
+        self._check(st)
+        return out, status, (cost if want_cost else None)
+
+    # -- fusion ------------------------------------------------------------
+    def fuse_points(self, xyz, conf, poses, out_xyz, out_idx, cursor, *, threshold=1.0,
+                    index_base=0, stream=None):
+        """Appends kept points of xyz [M, n, 3] / conf [M, n] at ``cursor`` (int64 [1])."""
+        M = int(conf.shape[0])
+        n = int(conf.numel() // max(M, 1))
+        st = self._lib.ec3r_fuse_points(
+            self._h, M, n, _ptr(xyz), _ptr(conf), _ptr(poses), float(threshold), int(index_base),
+            _ptr(out_xyz), _ptr(out_idx), int(out_idx.numel()), _ptr(cursor), _stream(stream))
+        self._check(st)
+
+
+def sim3_row(row):
+    """(s, R 3x3, t) from one 13-wide row (host numpy)."""
+    import numpy as np
+    r = np.asarray(row, dtype=np.float64)
+    return float(r[0]), r[1:10].reshape(3, 3), r[10:13].copy()
+
+
+def sim3_rows(S, R, t):
+    """Pack float64 tensors s [n], R [n,3,3], t [n,3] into [n,13] rows."""
+    return torch.cat([S.reshape(-1, 1), R.reshape(-1, 9), t.reshape(-1, 3)], 1).contiguous()

@@ -1,0 +1,23 @@
+"""Shared comparison helpers for the GPU parity tests (no method arithmetic
+beyond distances between two results)."""
+import numpy as np
+from scipy.spatial.transform import Rotation
+
+# tolerances of the registration outputs against the FP64 oracle
+ROT_TOL = 1e-5        # rad
+SCALE_TOL = 1e-6      # relative
+TRANS_TOL = 1e-6      # x scene extent (bbox diagonal of the valid targets)
+
+
+def sim3_errors(row, S_or, extent):
+    s, R, t = float(row[0]), np.asarray(row[1:10]).reshape(3, 3), np.asarray(row[10:13])
+    so, Ro, to = S_or
+    rot = float(np.linalg.norm(Rotation.from_matrix(R @ np.asarray(Ro).T).as_rotvec()))
+    return rot, abs(s / so - 1.0), float(np.linalg.norm(t - to)) / max(extent, 1e-30)
+
+
+def assert_sim3_close(row, S_or, extent, what=""):
+    rot, sc, tr = sim3_errors(row, S_or, extent)
+    assert rot <= ROT_TOL and sc <= SCALE_TOL and tr <= TRANS_TOL, \
+        f"{what}: rot {rot:.2e} scale {sc:.2e} trans/extent {tr:.2e}"
+    return rot, sc, tr
