@@ -105,26 +105,34 @@ def dist_env():
 # ----------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle as it stands, on a bounded sample
 # ----------------------------------------------------------------------------
-def oracle_sample(pairs_per_step, steps, warmup, seed):
-    import numpy as np
+def _oracle_sample_inproc(pairs_per_step, steps, warmup, seed):
     import torch
-    from threadpoolctl import threadpool_limits
     from oracle import register as reg
     from paper_2510_02080_b300 import synth
 
+    torch.set_num_threads(1)
     ch = synth.make_chain(seed, M=pairs_per_step + 1, F=F_FRAMES, H=H, W=W, device="cpu")
     ps = ch.pairs()
-    with threadpool_limits(limits=1):
-        torch.set_num_threads(1)
-        for _ in range(warmup):
-            reg.align_pairs(ps, delta=DELTA, iters=ITERS)
-        t0 = time.perf_counter()
-        n = 0
-        for _ in range(steps):
-            res = reg.align_pairs(ps, delta=DELTA, iters=ITERS)
-            n += sum(r["n_valid"] for r in res) * ITERS
-        dt = time.perf_counter() - t0
+    for _ in range(warmup):
+        reg.align_pairs(ps, delta=DELTA, iters=ITERS)
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(steps):
+        res = reg.align_pairs(ps, delta=DELTA, iters=ITERS)
+        n += sum(r["n_valid"] for r in res) * ITERS
+    dt = time.perf_counter() - t0
     return n / dt, n, dt, ps.n_pairs
+
+
+def oracle_sample(pairs_per_step, steps, warmup, seed):
+    """Times the oracle in a child process pinned to one BLAS/OpenMP thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
+                          f"{pairs_per_step},{steps},{warmup},{seed}"],
+                         env=env, capture_output=True, text=True, check=True)
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    return d["rate"], d["n"], d["dt"], d["pairs"]
 
 
 def run_reference(args):
@@ -286,7 +294,7 @@ def run_ours(args):
 
     cpu_rate, n_cpu, dt_cpu, np_cpu = (None, 0, 0.0, 0)
     if not args.no_cpu_baseline and ws == 1:
-        cpu_rate, n_cpu, dt_cpu, np_cpu = oracle_sample(2, 1, 0, synth.SEED_BASE + 2)
+        cpu_rate, n_cpu, dt_cpu, np_cpu = oracle_sample(8, 3, 0, synth.SEED_BASE + 2)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -329,7 +337,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_sample:
+        p, k, w, seed = (int(v) for v in args.oracle_sample.split(","))
+        rate, n, dt, npairs = _oracle_sample_inproc(p, k, w, seed)
+        print(json.dumps({"rate": rate, "n": n, "dt": dt, "pairs": npairs}))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -46,7 +46,11 @@ def run_fuse(ctx, xyz, conf, rows, thr=1.0, index_base=0, capacity=None, cursor0
 
 
 def extent(X):
-    return float(np.linalg.norm(X.max(0) - X.min(0)))
+    """Bounding-box diagonal of the fused points (at least their magnitude,
+    so that a one-point map still has a scale)."""
+    if len(X) == 0:
+        return 1.0
+    return max(float(np.linalg.norm(X.max(0) - X.min(0))), float(np.abs(X).max()))
 
 
 @pytest.mark.parametrize("shape", [(3, 2, 33, 51), (2, 2, 64, 130), (1, 1, 1, 3)])
@@ -63,8 +67,7 @@ def test_fuse_matches_oracle(ctx, shape):
     assert st == 0 and cur == len(oi)
     assert np.array_equal(gi[:cur], oi)
     assert (gi[cur:] == -7).all()
-    ext = extent(ox) if len(ox) else 1.0
-    assert np.abs(gx[:cur] - ox).max(initial=0.0) <= POINT_TOL * ext
+    assert np.abs(gx[:cur] - ox).max(initial=0.0) <= POINT_TOL * extent(ox)
 
 
 def test_streaming_cursor_and_capacity(ctx):
