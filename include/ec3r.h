@@ -164,6 +164,41 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
                                const ec3r_align_opts* opts, ec3r_sim3* d_out,
                                int32_t* d_pair_status, double* d_pair_cost, void* stream);
 
+/*
+ * Registration without allocation.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory at all, such
+ * as code running inside a memory arena it does not own, real-time loops
+ * where an allocation's implicit synchronisation and unbounded latency are
+ * not allowed, or hosts whose allocator belongs to another framework.
+ *
+ * It computes exactly what ec3r_align_submaps computes, with the same
+ * arguments (minus the context) and the same kernels, but its scratch lives
+ * in one fixed device array inside the library (about 2.8 MB, held on every
+ * GPU that loads the library until the process exits).  It calls no
+ * cudaMalloc or cudaFree and needs no context.  Limits, checked before any
+ * work is enqueued (EC3R_ERR_INVALID_ARG when exceeded):
+ *   n_pairs <= EC3R_NOALLOC_MAX_PAIRS, n_links <= EC3R_NOALLOC_MAX_LINKS,
+ *   n_links * ceil(hw / 8192) <= EC3R_NOALLOC_MAX_TILES.
+ * It runs on the current CUDA device.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (each call resets what must start fresh): calls whose
+ * work overlaps on the GPU - on different streams, or from different
+ * threads - race and corrupt each other; serialise them.  Out-of-range
+ * offsets or frames are reported only in d_pair_status (EC3R_PAIR_BAD_INPUT).
+ */
+#define EC3R_NOALLOC_MAX_PAIRS 1024
+#define EC3R_NOALLOC_MAX_LINKS 4096
+#define EC3R_NOALLOC_MAX_TILES 16384
+ec3r_status ec3r_align_submaps_noalloc(const float* d_xyz, const float* d_conf,
+                                       int64_t n_frames, int64_t hw, int n_pairs,
+                                       int64_t n_links, const int32_t* d_link_off,
+                                       const int32_t* d_src, const int32_t* d_tgt,
+                                       const float* d_pair_conf_min,
+                                       const ec3r_align_opts* opts, ec3r_sim3* d_out,
+                                       int32_t* d_pair_status, double* d_pair_cost,
+                                       void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Fusion: confidence-filtered transform of submap points into the global   */
 /* map (Sec. III-C "Point Correction": global coordinates of all points)    */

@@ -680,3 +680,135 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Registration for callers that cannot allocate device memory.
+//
+// Some callers may not call cudaMalloc at all: code that runs inside a memory
+// pool or arena it does not own, real-time loops that forbid allocation (an
+// allocation can synchronise the device and take unbounded time), and hosts
+// whose allocator is another framework's.  ec3r_align_submaps_noalloc serves
+// them: it runs the same kernels as ec3r_align_submaps, but its scratch (pair
+// states, per-tile partial moments, link-to-pair map, a status word) lives in
+// one fixed file-scope device array, so it allocates nothing and needs no
+// context.  Every GPU that loads the library holds that array until exit.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace ec3r {
+namespace align {
+
+constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t NA_STATE_BYTES = round256(sizeof(PairState) * EC3R_NOALLOC_MAX_PAIRS);
+constexpr size_t NA_PART_BYTES = round256(sizeof(double) * NMOM * EC3R_NOALLOC_MAX_TILES);
+constexpr size_t NA_LP_BYTES = round256(sizeof(int32_t) * (EC3R_NOALLOC_MAX_LINKS + 1));
+constexpr size_t NA_FLAG_BYTES = 256;
+constexpr size_t NA_BYTES = NA_STATE_BYTES + NA_PART_BYTES + NA_LP_BYTES + NA_FLAG_BYTES;
+
+// The scratch.  In host code this name is only a stand-in for the device
+// array: kernels get its device address from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+static void* g_noalloc_addr[NA_MAX_DEVICES] = {};
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch on the current device, looked up once per
+// device (the first call on a device does the lookup).
+static ec3r_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+    cudaGetLastError();
+    return EC3R_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return EC3R_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = (unsigned char*)g_noalloc_addr[dev];
+  return EC3R_OK;
+}
+
+}  // namespace align
+}  // namespace ec3r
+
+extern "C" ec3r_status ec3r_align_submaps_noalloc(
+    const float* d_xyz, const float* d_conf, int64_t n_frames, int64_t hw, int n_pairs,
+    int64_t n_links, const int32_t* d_link_off, const int32_t* d_src, const int32_t* d_tgt,
+    const float* d_pair_conf_min, const ec3r_align_opts* opts, ec3r_sim3* d_out,
+    int32_t* d_pair_status, double* d_pair_cost, void* stream) {
+  if (!opts || n_pairs < 0 || n_links < 0 || hw <= 0 || n_frames <= 0)
+    return EC3R_ERR_INVALID_ARG;
+  if (n_pairs == 0) return EC3R_OK;
+  if (!d_xyz || !d_conf || !d_link_off || !d_out || !d_pair_status ||
+      (n_links > 0 && (!d_src || !d_tgt)))
+    return EC3R_ERR_INVALID_ARG;
+  if (!(opts->huber_delta > 0.f) || !(opts->huber_delta <= FLT_MAX) || opts->iters < 1 ||
+      opts->iters > 64 || (opts->weight_rule != 0 && opts->weight_rule != 1) ||
+      (opts->precision != 0 && opts->precision != 1) || opts->conf_min != opts->conf_min ||
+      (opts->want_cost && !d_pair_cost))
+    return EC3R_ERR_INVALID_ARG;
+  const int64_t tpl = (hw + TILE - 1) / TILE;
+  const int64_t n_tiles = n_links * tpl;
+  // the fixed scratch bounds every size
+  if (n_pairs > EC3R_NOALLOC_MAX_PAIRS || n_links > EC3R_NOALLOC_MAX_LINKS ||
+      n_tiles > EC3R_NOALLOC_MAX_TILES || n_frames > ((int64_t)1 << 40) / hw)
+    return EC3R_ERR_INVALID_ARG;
+  unsigned char* base = nullptr;
+  ec3r_status st = noalloc_scratch(&base);
+  if (st != EC3R_OK) return st;
+  PairState* state = (PairState*)base;
+  double* partials = (double*)(base + NA_STATE_BYTES);
+  int32_t* link_pair = (int32_t*)(base + NA_STATE_BYTES + NA_PART_BYTES);
+  unsigned* flags = (unsigned*)(base + NA_STATE_BYTES + NA_PART_BYTES + NA_LP_BYTES);
+  cudaStream_t cs = (cudaStream_t)stream;
+  const bool vec =
+      (hw % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0) && ((uintptr_t)d_conf % 16 == 0);
+  const bool fp64 = opts->precision == EC3R_PREC_FP64;
+  const ec3r_align_opts o = *opts;
+  // the previous call's link map and status word must not leak into this one
+  if (cudaMemsetAsync(link_pair, 0xff, sizeof(int32_t) * (size_t)(n_links + 1), cs) !=
+          cudaSuccess ||
+      cudaMemsetAsync(flags, 0, sizeof(unsigned), cs) != cudaSuccess) {
+    cudaGetLastError();
+    return EC3R_ERR_CUDA;
+  }
+  k_setup<<<n_pairs, THREADS, 0, cs>>>(d_xyz, d_conf, n_frames, hw, n_pairs, n_links,
+                                       d_link_off, d_src, d_tgt, d_pair_conf_min, o.conf_min,
+                                       link_pair, state, flags);
+  const int solve_blocks = (n_pairs + 7) / 8;
+  for (int it = 1; it <= o.iters + (o.want_cost ? 1 : 0); ++it) {
+    const int kind = it == 1 ? FIRST : (it > o.iters ? COST : IRLS);
+    const float dl = (kind == COST && o.iters == 1) ? FLT_MAX : o.huber_delta;
+    if (n_tiles > 0) {
+      if (fp64) {
+        if (vec)
+          launch_sweep<double, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
+                                     d_tgt, link_pair, state, dl, o.weight_rule, partials);
+        else
+          launch_sweep<double, false>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
+                                      d_tgt, link_pair, state, dl, o.weight_rule, partials);
+      } else {
+        if (vec)
+          launch_sweep<float, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
+                                    d_tgt, link_pair, state, dl, o.weight_rule, partials);
+        else
+          launch_sweep<float, false>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
+                                     d_tgt, link_pair, state, dl, o.weight_rule, partials);
+      }
+    }
+    if (kind == COST)
+      k_cost<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials,
+                                                    state, d_pair_cost);
+    else
+      k_solve<<<solve_blocks, 256, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
+                                            d_out, d_pair_status, it == o.iters);
+  }
+  if (cudaGetLastError() != cudaSuccess) return EC3R_ERR_CUDA;
+  return EC3R_OK;
+}

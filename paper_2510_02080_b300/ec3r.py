@@ -26,7 +26,8 @@ RULE = {"product": 0, "src": 1}
 # Every symbol include/ec3r.h declares (checked by the CPU tests).
 EXPORTS = ("ec3r_create", "ec3r_destroy", "ec3r_last_error", "ec3r_status_string",
            "ec3r_version", "ec3r_sync_status", "ec3r_align_opts_default",
-           "ec3r_align_submaps", "ec3r_fuse_points", "ec3r_profile", "ec3r_profile_read")
+           "ec3r_align_submaps", "ec3r_fuse_points", "ec3r_profile", "ec3r_profile_read",
+           "ec3r_align_submaps_noalloc")
 
 
 class Sim3(C.Structure):
