@@ -30,9 +30,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Sim(3)-registered points/s per IRLS iter (batched, FP32) and % HBM roofline"
 UNIT = "pt-iter/s"
-M_SUBMAPS, F_FRAMES, H, W = 200, 5, 294, 518
+M_SUBMAPS, F_FRAMES, H, W = 200, 5, 294, 518   # the chain workload
 ITERS, DELTA = 10, 0.02
 SWEEP_BYTES_PER_PIXEL = 32          # p, q (2 x 12 B) + c_p, c_q (2 x 4 B) per sweep
+# DRAM bytes per pixel of one sweep launch, from the ncu capture summarised in
+# profiles/irls_sweep_fp32_chain40_294x518.md (read + write / pixels); the
+# traffic scales with the pixels of a launch.  None once the kernel changes.
+SWEEP_TRAFFIC_BYTES_PER_PIXEL = 32.54
 
 
 def peaks():
@@ -174,7 +178,8 @@ def run_ours(args):
     ctx = ec3r.Context(local)
 
     # per-rank synthetic chain (weak scaling: every rank owns its own map)
-    ch = synth.make_chain(synth.SEED_BASE + 2 + 1000 * rank, M=M_SUBMAPS, F=F_FRAMES, H=H, W=W,
+    M = args.submaps
+    ch = synth.make_chain(synth.SEED_BASE + 2 + 1000 * rank, M=M, F=F_FRAMES, H=H, W=W,
                           device=dev)
     ps = ch.pairs()
     n_frames, hw = ps.conf.shape
@@ -183,9 +188,8 @@ def run_ours(args):
     n_valid = int((fin[ps.src.long()] & fin[ps.tgt.long()]).sum())
     del fin
     pix = ps.n_pairs * hw
-    n_fuse = M_SUBMAPS * F_FRAMES * hw
-    xyz_m = ch.xyz.view(M_SUBMAPS, -1, 3)
-    conf_m = ch.conf.view(M_SUBMAPS, -1)
+    n_fuse = M * F_FRAMES * hw
+    conf_m = ch.conf.view(M, -1)
     kept = int((conf_m > 1.0).sum())
     out_xyz = torch.empty((kept, 3), device=dev)
     out_idx = torch.empty((kept,), dtype=torch.int64, device=dev)
@@ -201,7 +205,7 @@ def run_ours(args):
                           ps.src, ps.tgt, delta=DELTA, iters=ITERS, out=S, status=st)
         c = cursors[ci[0] % n_cursor:ci[0] % n_cursor + 1]
         ci[0] += 1
-        ctx.fuse_points(xyz_in.view(M_SUBMAPS, -1, 3), conf_in.view(M_SUBMAPS, -1), poses,
+        ctx.fuse_points(xyz_in.view(M, -1, 3), conf_in.view(M, -1), poses,
                         out_xyz, out_idx, c)
 
     for _ in range(args.warmup):
@@ -300,7 +304,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "chain200_294x518", "submaps": M_SUBMAPS, "frames": F_FRAMES,
+        "config": {"workload": f"chain{M}_294x518", "submaps": M, "frames": F_FRAMES,
                    "H": H, "W": W, "pairs": ps.n_pairs, "valid_correspondences": n_valid,
                    "iters": ITERS, "huber_delta": DELTA, "precision": "fp32 moments, fp64 solve",
                    "fused_points": n_fuse, "kept_points": kept,
@@ -308,7 +312,9 @@ def run_ours(args):
                    "l2": "inputs 2.4 GB per rank > 126 MB L2; no flush"},
         "roofline": {"bound": "hbm", "kernel": "irls_sweep_fp32", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (SWEEP_TRAFFIC_BYTES_PER_PIXEL * pix
+                                 if SWEEP_TRAFFIC_BYTES_PER_PIXEL else None),
                      "algorithmic_bytes_per_launch": sweep_bytes,
                      "launch_ms": sweep_ms},
         "kernels": kernels,
@@ -337,6 +343,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--submaps", type=int, default=M_SUBMAPS,
+                    help="chain length (default 200); smaller values are for profiling only")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
