@@ -200,6 +200,55 @@ ec3r_status ec3r_align_submaps_noalloc(const float* d_xyz, const float* d_conf,
                                        void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Pose graph: Sim(3) submap poses refined by Gauss-Newton (Sec. III-E)     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int iters;          /* Gauss-Newton iterations, 0..1000 */
+  int fixed_node;     /* node held constant (gauge), 0 <= fixed_node < n_nodes */
+  double lm_lambda;   /* >= 0; the normal matrix is H + lm_lambda I (0: Gauss-Newton) */
+  int init_by_chaining; /* 1: first set every node by chaining relative transforms */
+} ec3r_pg_opts;
+
+/* Fills `o` with the defaults: 10 iterations, node 0 fixed, lambda 0, chaining on. */
+void ec3r_pg_opts_default(ec3r_pg_opts* o);
+
+/*
+ * Refine submap poses d_nodes (ec3r_sim3 [n_nodes], device, in/out: submap ->
+ * world) against the relative transforms of `n_edges` edges, minimising
+ * chi^2 = sum_e e_e^T Omega_e e_e with e = log_Sim3(T_ij^-1 T_i^-1 T_j)
+ * (Sec. III-E), so an edge (i, j) is satisfied when T_j = T_i T_ij.
+ *
+ * Structure.  h_i, h_j (int32 [n_edges], HOST) give each edge's endpoints,
+ * in [0, n_nodes) and distinct.  The structure is analysed on the host once
+ * (nested-dissection ordering, block fill of the Cholesky factor) and cached
+ * in the context; a call with a new structure allocates and must not be made
+ * during stream capture (EC3R_ERR_CAPTURE).  The first pose-graph call of a
+ * context also uploads a constant table.
+ *
+ * Data.  d_Tij (ec3r_sim3 [n_edges], device) are the measured T_ij; d_info
+ * (float64 [n_edges][49], row-major symmetric Omega, device) or NULL for the
+ * identity.  The tangent order is (rho, phi, sigma): translation, rotation
+ * vector, log-scale; T <- T Exp(delta) is the update.
+ *
+ * Chaining.  With init_by_chaining, every node except the fixed one is first
+ * set by composing relative transforms along a spanning tree made of the
+ * edges, in input order, that join two unconnected parts of the graph, walked
+ * from the fixed node (T_j = T_i T_ij along an edge, T_i = T_j T_ij^-1
+ * against it); nodes not connected to the fixed node become the identity.
+ *
+ * Iteration.  `iters` Gauss-Newton steps on all nodes but the fixed one, each
+ * solving (H + lambda I) delta = -g by an FP64 block Cholesky factorisation.
+ * d_chi2 (float64 [iters+1], device, nullable) receives chi^2 before each
+ * step and after the last.  A non-positive pivot skips that step's update and
+ * raises EC3R_ERR_NOT_SPD at ec3r_sync_status.
+ */
+ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nodes, int n_edges,
+                                    const int32_t* h_i, const int32_t* h_j,
+                                    const ec3r_sim3* d_Tij, const double* d_info,
+                                    const ec3r_pg_opts* opts, double* d_chi2, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Fusion: confidence-filtered transform of submap points into the global   */
 /* map (Sec. III-C "Point Correction": global coordinates of all points)    */
 /* ------------------------------------------------------------------------ */

@@ -1,0 +1,852 @@
+// Sim(3) pose-graph correction of submap poses (Sec. III-E).
+//
+// Nodes are submap poses T_t (submap -> world), an edge (i, j) carries the
+// relative transform T_ij from registration, its error is
+// e_ij = log(T_ij^-1 T_i^-1 T_j) and the energy chi^2 = sum e^T Omega e.  The
+// poses are initialised by chaining the relative transforms and refined by
+// Gauss-Newton (optionally damped: H + lambda I) with right perturbations
+// T <- T Exp(delta) and one node held fixed.
+//
+// Host (once per graph structure, cached in the context): a nested-dissection
+// ordering of the free nodes, the block fill of the Cholesky factor, its
+// elimination-tree levels, the left-looking update lists and the assembly lists.
+// Device, per Gauss-Newton iteration, all FP64:
+//   k_pg_linearize   one warp per edge: e, J_i = -Jr^-1(e) Ad(T_j^-1 T_i),
+//                    J_j = Jr^-1(e) (Jr^-1 from its Bernoulli series), and the
+//                    blocks J^T Omega J, J^T Omega e, e^T Omega e
+//   k_pg_assemble    one warp per factor block: fixed-order sums of the edge
+//                    blocks (deterministic, no atomics); g; chi^2
+//   k_pg_factor      one launch per tree level, one warp per 7x7 block column:
+//                    left-looking updates, dense 7x7 Cholesky, off-diagonal
+//                    triangular solves, forward substitution
+//   k_pg_backsolve   one launch per level, root to leaves
+//   k_pg_update      one thread per node: T <- T Exp(delta)
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <map>
+#include <set>
+#include <vector>
+
+#include "common.cuh"
+#include "sim3_math.cuh"
+
+namespace ec3r {
+namespace pg {
+
+constexpr int NB = 49;
+constexpr int NBERN = 24;
+__constant__ double c_bern[NBERN];  // B_2k / (2k)!, k = 1..24
+
+// --------------------------------------------------------------------------
+// device helpers: 7x7 blocks in shared memory, one warp
+// --------------------------------------------------------------------------
+// C = op(A) op(B); each lane computes entries lane and lane + 32.
+__device__ __forceinline__ void warp_mm7(const double* A, bool tA, const double* B, bool tB,
+                                         double* C, int lane) {
+  for (int idx = lane; idx < NB; idx += 32) {
+    const int r = idx / 7, c = idx % 7;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const double a = tA ? A[7 * k + r] : A[7 * r + k];
+      const double b = tB ? B[7 * c + k] : B[7 * k + c];
+      s = fma(a, b, s);
+    }
+    C[idx] = s;
+  }
+  __syncwarp();
+}
+
+// Adjoint of T = (s, R, t) in (rho, phi, sigma) coordinates:
+// [[sR, t^ R, -t], [0, R, 0], [0, 0, 1]].
+__device__ void adjoint7(const s3::Sim3d& T, double* A) {
+  for (int i = 0; i < NB; ++i) A[i] = 0.0;
+  const double* R = T.R;
+  const double* t = T.t;
+  const double th[9] = {0.0, -t[2], t[1], t[2], 0.0, -t[0], -t[1], t[0], 0.0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      A[7 * i + j] = T.s * R[3 * i + j];
+      A[7 * (i + 3) + (j + 3)] = R[3 * i + j];
+      double v = 0.0;
+      for (int k = 0; k < 3; ++k) v += th[3 * i + k] * R[3 * k + j];
+      A[7 * i + (j + 3)] = v;
+    }
+  for (int i = 0; i < 3; ++i) A[7 * i + 6] = -t[i];
+  A[48] = 1.0;
+}
+
+// ad of xi = (rho, phi, sigma): [[phi^ + sigma I, rho^, -rho], [0, phi^, 0], [0, 0, 0]].
+__device__ void small_ad7(const double* xi, double* A) {
+  for (int i = 0; i < NB; ++i) A[i] = 0.0;
+  const double* r = xi;
+  const double* p = xi + 3;
+  const double ph[9] = {0.0, -p[2], p[1], p[2], 0.0, -p[0], -p[1], p[0], 0.0};
+  const double rh[9] = {0.0, -r[2], r[1], r[2], 0.0, -r[0], -r[1], r[0], 0.0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      A[7 * i + j] = ph[3 * i + j] + (i == j ? xi[6] : 0.0);
+      A[7 * i + j + 3] = rh[3 * i + j];
+      A[7 * (i + 3) + j + 3] = ph[3 * i + j];
+    }
+  for (int i = 0; i < 3; ++i) A[7 * i + 6] = -r[i];
+}
+
+__device__ __forceinline__ s3::Sim3d edge_error_T(const s3::Sim3d& Ti, const s3::Sim3d& Tj,
+                                                  const s3::Sim3d& Tij) {
+  return s3::compose(s3::inverse(Tij), s3::compose(s3::inverse(Ti), Tj));
+}
+
+// --------------------------------------------------------------------------
+// chaining initialisation: pointer jumping along the spanning tree (one CTA)
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_pg_init(int n, int fixed, const int* __restrict__ parent,
+                                                  const int* __restrict__ tedge,
+                                                  const int* __restrict__ tdir,
+                                                  const ec3r_sim3* __restrict__ Tij,
+                                                  ec3r_sim3* nodes, ec3r_sim3* W0, ec3r_sim3* W1,
+                                                  int* anc0, int* anc1, int rounds) {
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    s3::Sim3d w;
+    int a = -1;
+    if (v == fixed) {
+      w = s3::load(nodes[v]);
+    } else if (parent[v] < 0) {
+      w = s3::identity();
+    } else {
+      const s3::Sim3d M = s3::load(Tij[tedge[v]]);
+      w = tdir[v] > 0 ? M : s3::inverse(M);
+      a = parent[v];
+    }
+    s3::store(w, W0[v]);
+    anc0[v] = a;
+  }
+  __syncthreads();
+  ec3r_sim3* Ws = W0;
+  ec3r_sim3* Wd = W1;
+  int* As = anc0;
+  int* Ad = anc1;
+  for (int r = 0; r < rounds; ++r) {
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+      const int a = As[v];
+      if (a >= 0) {
+        s3::store(s3::compose(s3::load(Ws[a]), s3::load(Ws[v])), Wd[v]);
+        Ad[v] = As[a];
+      } else {
+        Wd[v] = Ws[v];
+        Ad[v] = -1;
+      }
+    }
+    __syncthreads();
+    ec3r_sim3* tw = Ws; Ws = Wd; Wd = tw;
+    int* ta = As; As = Ad; Ad = ta;
+  }
+  for (int v = threadIdx.x; v < n; v += blockDim.x)
+    if (v != fixed) nodes[v] = Ws[v];
+}
+
+// --------------------------------------------------------------------------
+// linearisation: one warp per edge
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) k_pg_linearize(
+    const int* __restrict__ ei, const int* __restrict__ ej, const ec3r_sim3* __restrict__ nodes,
+    const ec3r_sim3* __restrict__ Tij, const double* __restrict__ info, double* __restrict__ contrib,
+    double* __restrict__ gvec, double* __restrict__ chi2e, int jacobians) {
+  const int e = blockIdx.x;
+  const int lane = threadIdx.x;
+  __shared__ double sA[NB], sB[NB], sC[NB], sJ[NB], sJi[NB], sO[NB], sOJ[NB], sOJj[NB];
+  __shared__ double se[7];
+  __shared__ int sK;
+  if (lane == 0) {
+    const s3::Sim3d Ti = s3::load(nodes[ei[e]]), Tj = s3::load(nodes[ej[e]]);
+    const s3::Sim3d M = s3::load(Tij[e]);
+    double xi[7];
+    s3::log(edge_error_T(Ti, Tj, M), xi);
+    for (int k = 0; k < 7; ++k) se[k] = xi[k];
+    if (jacobians) {
+      adjoint7(s3::compose(s3::inverse(Tj), Ti), sB);   // Ad(T_j^-1 T_i)
+      small_ad7(xi, sA);                                // ad(e)
+      // series length from the spectral radius of ad(e) and the size of rho
+      const double nu = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5] + xi[6] * xi[6]);
+      const double rn = 1.0 + fabs(xi[0]) + fabs(xi[1]) + fabs(xi[2]);
+      const double q = nu / (2.0 * 3.14159265358979323846);
+      int K = 1;
+      double qk = q * q;  // q^(2K)
+      while (K < NBERN && 4.0 * (K + 1) * rn * qk * q * q > 1e-18) {
+        ++K;
+        qk *= q * q;
+      }
+      sK = K;
+    }
+  }
+  __syncwarp();
+  double ev[7];
+  for (int k = 0; k < 7; ++k) ev[k] = se[k];
+  // Omega (identity unless given)
+  for (int idx = lane; idx < NB; idx += 32)
+    sO[idx] = info ? info[(size_t)e * NB + idx] : ((idx % 8 == 0) ? 1.0 : 0.0);
+  __syncwarp();
+  if (lane == 0) {
+    double v[7];
+    for (int r = 0; r < 7; ++r) {
+      double s = 0.0;
+      for (int c = 0; c < 7; ++c) s += sO[7 * r + c] * ev[c];
+      v[r] = s;
+    }
+    double x2 = 0.0;
+    for (int r = 0; r < 7; ++r) x2 += ev[r] * v[r];
+    chi2e[e] = x2;
+  }
+  if (!jacobians) return;
+  // Jr^-1(e) = I + ad/2 + sum_k c_k ad^{2k}; Horner in ad^2
+  warp_mm7(sA, false, sA, false, sC, lane);            // sC = ad^2
+  const int K = sK;
+  for (int idx = lane; idx < NB; idx += 32) sJ[idx] = (idx % 8 == 0) ? c_bern[K - 1] : 0.0;
+  __syncwarp();
+  for (int k = K - 1; k >= 1; --k) {
+    warp_mm7(sC, false, sJ, false, sOJ, lane);         // sOJ = ad^2 Q
+    for (int idx = lane; idx < NB; idx += 32)
+      sJ[idx] = sOJ[idx] + ((idx % 8 == 0) ? c_bern[k - 1] : 0.0);
+    __syncwarp();
+  }
+  warp_mm7(sC, false, sJ, false, sOJ, lane);           // sOJ = P(ad^2)
+  for (int idx = lane; idx < NB; idx += 32)
+    sJ[idx] = ((idx % 8 == 0) ? 1.0 : 0.0) + 0.5 * sA[idx] + sOJ[idx];   // sJ = Jr^-1 = J_j
+  __syncwarp();
+  warp_mm7(sJ, false, sB, false, sJi, lane);           // Jr^-1 Ad
+  for (int idx = lane; idx < NB; idx += 32) sJi[idx] = -sJi[idx];        // J_i
+  __syncwarp();
+  double* out = contrib + (size_t)e * 3 * NB;
+  warp_mm7(sO, false, sJi, false, sOJ, lane);          // Omega J_i
+  warp_mm7(sO, false, sJ, false, sOJj, lane);          // Omega J_j
+  warp_mm7(sJi, true, sOJ, false, sA, lane);           // J_i^T Omega J_i
+  warp_mm7(sJ, true, sOJj, false, sB, lane);           // J_j^T Omega J_j
+  warp_mm7(sJi, true, sOJj, false, sC, lane);          // J_i^T Omega J_j
+  for (int idx = lane; idx < NB; idx += 32) {
+    out[idx] = sA[idx];
+    out[NB + idx] = sB[idx];
+    out[2 * NB + idx] = sC[idx];
+  }
+  // g: J^T Omega e
+  if (lane < 14) {
+    const int side = lane / 7, r = lane % 7;
+    const double* OJ = side == 0 ? sOJ : sOJj;
+    double s = 0.0;
+    for (int c = 0; c < 7; ++c) s += OJ[7 * c + r] * ev[c];
+    gvec[(size_t)e * 14 + lane] = s;
+  }
+}
+
+// --------------------------------------------------------------------------
+// assembly: one warp per factor block, then one per node (g), then chi^2
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) k_pg_assemble(
+    int n_blocks, int nf, int m, const int* __restrict__ asm_ptr, const int* __restrict__ asm_it,
+    const int* __restrict__ g_ptr, const int* __restrict__ g_it, const double* __restrict__ contrib,
+    const double* __restrict__ gvec, const double* __restrict__ chi2e, double lambda, double* L,
+    double* bvec, double* chi2_out, int* fail) {
+  const int b = blockIdx.x;
+  const int lane = threadIdx.x;
+  if (b < n_blocks) {
+    const int p0 = asm_ptr[b], p1 = asm_ptr[b + 1];
+    for (int idx = lane; idx < NB; idx += 32) {
+      const int r = idx / 7, c = idx % 7;
+      double s = (b < nf && r == c) ? lambda : 0.0;
+      for (int p = p0; p < p1; ++p) {
+        const int it = asm_it[p];
+        const int edge = it >> 2, kind = it & 3;
+        const double* C = contrib + (size_t)edge * 3 * NB;
+        s += kind == 3 ? C[2 * NB + 7 * c + r] : C[kind * NB + idx];
+      }
+      L[(size_t)b * NB + idx] = s;
+    }
+  } else if (b < n_blocks + nf) {
+    const int k = b - n_blocks;
+    if (lane < 7) {
+      double s = 0.0;
+      for (int p = g_ptr[k]; p < g_ptr[k + 1]; ++p) {
+        const int it = g_it[p];
+        s += gvec[(size_t)(it >> 1) * 14 + 7 * (it & 1) + lane];
+      }
+      bvec[7 * k + lane] = -s;
+    }
+  } else {
+    double s = 0.0;
+    for (int e = lane; e < m; e += 32) s += chi2e[e];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      if (chi2_out) *chi2_out = s;
+      *fail = 0;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// factorisation + forward substitution: one warp per column of a level
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) k_pg_factor(
+    const int* __restrict__ cols, const int* __restrict__ col_ptr, const int* __restrict__ off_blk,
+    const int* __restrict__ upd_ptr, const int* __restrict__ upd, const int* __restrict__ row_ptr,
+    const int* __restrict__ row_it, double* L, double* bvec, unsigned* flags, int* fail) {
+  const int k = cols[blockIdx.x];
+  const int lane = threadIdx.x;
+  __shared__ double D[NB];
+  __shared__ double inv[7];
+  // left-looking updates of every block of column k (diagonal first, then off-diagonal)
+  for (int p = upd_ptr[k]; p < upd_ptr[k + 1]; ++p) {
+    const int dst = upd[3 * p], a = upd[3 * p + 1], bb = upd[3 * p + 2];
+    double* Dst = L + (size_t)dst * NB;
+    const double* A = L + (size_t)a * NB;
+    const double* B = L + (size_t)bb * NB;
+    for (int idx = lane; idx < NB; idx += 32) {
+      const int r = idx / 7, c = idx % 7;
+      double s = Dst[idx];
+#pragma unroll
+      for (int t = 0; t < 7; ++t) s = fma(-A[7 * r + t], B[7 * c + t], s);
+      Dst[idx] = s;
+    }
+    __syncwarp();
+  }
+  double* Lkk = L + (size_t)k * NB;
+  for (int idx = lane; idx < NB; idx += 32) D[idx] = Lkk[idx];
+  __syncwarp();
+  // dense 7x7 Cholesky (lower)
+  bool bad = false;
+  for (int c = 0; c < 7; ++c) {
+    const double d = D[8 * c];
+    if (!(d > 0.0) || !isfinite(d)) bad = true;
+    const double piv = sqrt(fmax(d, 1e-300));
+    const double ip = 1.0 / piv;
+    __syncwarp();
+    if (lane == 0) {
+      D[8 * c] = piv;
+      inv[c] = ip;
+    }
+    if (lane > c && lane < 7) D[7 * lane + c] *= ip;
+    __syncwarp();
+    // trailing update of the lower triangle
+    for (int idx = lane; idx < NB; idx += 32) {
+      const int r = idx / 7, cc = idx % 7;
+      if (r > c && cc > c && cc <= r) D[idx] -= D[7 * r + c] * D[7 * cc + c];
+    }
+    __syncwarp();
+  }
+  if (bad) {
+    if (lane == 0) {
+      atomicOr(flags, FLAG_NOT_SPD);
+      atomicExch(fail, 1);
+    }
+  }
+  for (int idx = lane; idx < NB; idx += 32) {
+    const int r = idx / 7, c = idx % 7;
+    Lkk[idx] = c <= r ? D[idx] : 0.0;
+  }
+  // off-diagonal blocks: X = H_ik Lkk^-T (row-wise forward substitution)
+  const int o0 = col_ptr[k], o1 = col_ptr[k + 1];
+  for (int base = o0 * 7; base < o1 * 7; base += 32) {
+    const int q = base + lane;
+    if (q < o1 * 7) {
+      double* X = L + (size_t)off_blk[q / 7] * NB + 7 * (q % 7);
+      double x[7];
+      for (int c = 0; c < 7; ++c) {
+        double s = X[c];
+        for (int t = 0; t < c; ++t) s -= x[t] * D[7 * c + t];
+        x[c] = s * inv[c];
+      }
+      for (int c = 0; c < 7; ++c) X[c] = x[c];
+    }
+  }
+  // forward substitution: y_k = Lkk^-1 (b_k - sum_j L_kj y_j)
+  __shared__ double y[7];
+  if (lane < 7) {
+    double s = bvec[7 * k + lane];
+    for (int p = row_ptr[k]; p < row_ptr[k + 1]; ++p) {
+      const int j = row_it[2 * p], blk = row_it[2 * p + 1];
+      const double* Lkj = L + (size_t)blk * NB + 7 * lane;
+      for (int t = 0; t < 7; ++t) s -= Lkj[t] * bvec[7 * j + t];
+    }
+    y[lane] = s;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    for (int c = 0; c < 7; ++c) {
+      double s = y[c];
+      for (int t = 0; t < c; ++t) s -= D[7 * c + t] * y[t];
+      y[c] = s * inv[c];
+    }
+  }
+  __syncwarp();
+  if (lane < 7) bvec[7 * k + lane] = y[lane];
+}
+
+// back substitution, root to leaves: x_k = Lkk^-T (y_k - sum_i L_ik^T x_i)
+__global__ void __launch_bounds__(32) k_pg_backsolve(const int* __restrict__ cols,
+                                                     const int* __restrict__ col_ptr,
+                                                     const int* __restrict__ off_row,
+                                                     const int* __restrict__ off_blk,
+                                                     const double* __restrict__ L, double* bvec) {
+  const int k = cols[blockIdx.x];
+  const int lane = threadIdx.x;
+  __shared__ double x[7];
+  if (lane < 7) {
+    double s = bvec[7 * k + lane];
+    for (int p = col_ptr[k]; p < col_ptr[k + 1]; ++p) {
+      const int i = off_row[p];
+      const double* Lik = L + (size_t)off_blk[p] * NB;
+      for (int t = 0; t < 7; ++t) s -= Lik[7 * t + lane] * bvec[7 * i + t];
+    }
+    x[lane] = s;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    const double* D = L + (size_t)k * NB;
+    for (int c = 6; c >= 0; --c) {
+      double s = x[c];
+      for (int t = c + 1; t < 7; ++t) s -= D[7 * t + c] * x[t];
+      x[c] = s / D[8 * c];
+    }
+  }
+  __syncwarp();
+  if (lane < 7) bvec[7 * k + lane] = x[lane];
+}
+
+__global__ void k_pg_update(int nf, const int* __restrict__ perm, const double* __restrict__ x,
+                            ec3r_sim3* nodes, const int* __restrict__ fail) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nf || *fail) return;
+  double d[7];
+  for (int i = 0; i < 7; ++i) d[i] = x[7 * k + i];
+  const int v = perm[k];
+  s3::store(s3::compose(s3::load(nodes[v]), s3::exp(d)), nodes[v]);
+}
+
+// --------------------------------------------------------------------------
+// host: planning
+// --------------------------------------------------------------------------
+struct Plan : Extension {
+  int n = 0, m = 0, fixed = 0, nf = 0, n_blocks = 0, rounds = 0;
+  std::vector<int> level_ptr;   // columns of level l: level_cols[level_ptr[l] .. level_ptr[l+1])
+  std::vector<void*> allocs;
+  int *d_ei = nullptr, *d_ej = nullptr, *d_perm = nullptr;
+  int *d_col_ptr = nullptr, *d_off_row = nullptr, *d_off_blk = nullptr;
+  int *d_upd_ptr = nullptr, *d_upd = nullptr, *d_row_ptr = nullptr, *d_row = nullptr;
+  int *d_level_cols = nullptr, *d_asm_ptr = nullptr, *d_asm = nullptr;
+  int *d_g_ptr = nullptr, *d_g = nullptr;
+  int *d_parent = nullptr, *d_tedge = nullptr, *d_tdir = nullptr;
+  int *d_anc0 = nullptr, *d_anc1 = nullptr, *d_fail = nullptr;
+  double *d_L = nullptr, *d_b = nullptr, *d_contrib = nullptr, *d_gvec = nullptr,
+         *d_chi2e = nullptr;
+  ec3r_sim3 *d_W0 = nullptr, *d_W1 = nullptr;
+  ~Plan() override {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+template <typename T>
+static cudaError_t upload(Plan& P, T** dst, const std::vector<T>& v) {
+  const size_t bytes = sizeof(T) * std::max<size_t>(v.size(), 1);
+  cudaError_t e = cudaMalloc((void**)dst, bytes);
+  if (e != cudaSuccess) return e;
+  P.allocs.push_back(*dst);
+  if (!v.empty()) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+template <typename T>
+static cudaError_t alloc(Plan& P, T** dst, size_t count) {
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(count, 1));
+  if (e == cudaSuccess) P.allocs.push_back(*dst);
+  return e;
+}
+
+// Nested dissection on the node order: split a set at its median node and
+// move one endpoint of every edge crossing the split into the separator.
+static void nested_dissection(std::vector<int> S, const std::vector<std::set<int>>& adj,
+                              std::vector<int>& order) {
+  if (S.size() <= 3) {
+    std::sort(S.begin(), S.end());
+    for (int v : S) order.push_back(v);
+    return;
+  }
+  std::sort(S.begin(), S.end());
+  const int mid = S[S.size() / 2];
+  std::set<int> inS(S.begin(), S.end()), sep;
+  sep.insert(mid);
+  for (int a : S) {
+    if (a >= mid) break;
+    for (int b : adj[a])
+      if (b > mid && inS.count(b) && !sep.count(a) && !sep.count(b)) sep.insert(b);
+  }
+  std::vector<int> A, B;
+  for (int v : S) {
+    if (sep.count(v)) continue;
+    (v < mid ? A : B).push_back(v);
+  }
+  nested_dissection(A, adj, order);
+  nested_dissection(B, adj, order);
+  for (int v : sep) order.push_back(v);
+}
+
+static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, const int32_t* hj,
+                              int fixed, Plan& P) {
+  P.n = n;
+  P.m = m;
+  P.fixed = fixed;
+  // free nodes and their adjacency
+  std::vector<std::set<int>> adj(n);
+  for (int e = 0; e < m; ++e) {
+    const int a = hi[e], b = hj[e];
+    if (a != fixed && b != fixed) {
+      adj[a].insert(b);
+      adj[b].insert(a);
+    }
+  }
+  std::vector<int> freev;
+  for (int v = 0; v < n; ++v)
+    if (v != fixed) freev.push_back(v);
+  std::vector<int> perm;
+  nested_dissection(freev, adj, perm);
+  const int nf = (int)perm.size();
+  P.nf = nf;
+  std::vector<int> inew(n, -1);
+  for (int k = 0; k < nf; ++k) inew[perm[k]] = k;
+  // symbolic factorisation
+  std::vector<std::vector<int>> children(nf);
+  std::vector<std::set<int>> st(nf);
+  std::vector<int> parent(nf, -1);
+  for (int k = 0; k < nf; ++k) {
+    for (int u : adj[perm[k]]) {
+      const int q = inew[u];
+      if (q > k) st[k].insert(q);
+    }
+    for (int c : children[k])
+      for (int q : st[c])
+        if (q > k) st[k].insert(q);
+    if (!st[k].empty()) {
+      parent[k] = *st[k].begin();
+      children[parent[k]].push_back(k);
+    }
+  }
+  // blocks: diagonal k -> k; off-diagonal numbered column by column
+  std::vector<int> col_ptr(nf + 1, 0), off_row, off_blk;
+  std::map<std::pair<int, int>, int> bidx;  // (row, col) -> block
+  int nb = nf;
+  for (int k = 0; k < nf; ++k) {
+    col_ptr[k] = (int)off_row.size();
+    for (int r : st[k]) {
+      off_row.push_back(r);
+      off_blk.push_back(nb);
+      bidx[{r, k}] = nb++;
+    }
+  }
+  col_ptr[nf] = (int)off_row.size();
+  P.n_blocks = nb;
+  auto blk = [&](int r, int c) { return r == c ? c : bidx.at({r, c}); };
+  // left-looking update lists and forward-substitution row lists
+  std::vector<std::vector<int>> rowstruct(nf);
+  for (int j = 0; j < nf; ++j)
+    for (int k : st[j]) rowstruct[k].push_back(j);
+  std::vector<int> upd_ptr(nf + 1, 0), upd, row_ptr(nf + 1, 0), row;
+  for (int k = 0; k < nf; ++k) {
+    upd_ptr[k] = (int)upd.size() / 3;
+    row_ptr[k] = (int)row.size() / 2;
+    std::sort(rowstruct[k].begin(), rowstruct[k].end());
+    // diagonal block first, then the off-diagonal ones, each in descendant order
+    std::vector<int> targets;
+    targets.push_back(k);
+    for (int r : st[k]) targets.push_back(r);
+    for (int i : targets)
+      for (int j : rowstruct[k]) {
+        if (i != k && !st[j].count(i)) continue;
+        upd.push_back(blk(i, k));
+        upd.push_back(blk(i, j));
+        upd.push_back(blk(k, j));
+      }
+    for (int j : rowstruct[k]) {
+      row.push_back(j);
+      row.push_back(blk(k, j));
+    }
+  }
+  upd_ptr[nf] = (int)upd.size() / 3;
+  row_ptr[nf] = (int)row.size() / 2;
+  // levels (height in the elimination tree)
+  std::vector<int> level(nf, 0);
+  int nlev = 0;
+  for (int k = 0; k < nf; ++k) {
+    for (int c : children[k]) level[k] = std::max(level[k], level[c] + 1);
+    nlev = std::max(nlev, level[k] + 1);
+  }
+  P.level_ptr.assign(nlev + 1, 0);
+  for (int k = 0; k < nf; ++k) P.level_ptr[level[k] + 1]++;
+  for (int l = 0; l < nlev; ++l) P.level_ptr[l + 1] += P.level_ptr[l];
+  std::vector<int> level_cols(nf), fill = P.level_ptr;
+  for (int k = 0; k < nf; ++k) level_cols[fill[level[k]]++] = k;
+  // assembly lists: kind 0 = Cii, 1 = Cjj, 2 = Cij, 3 = Cij^T
+  std::vector<std::vector<int>> asmv(nb), gv(nf);
+  for (int e = 0; e < m; ++e) {
+    const int a = inew[hi[e]], b = inew[hj[e]];
+    if (a >= 0) {
+      asmv[a].push_back(e << 2 | 0);
+      gv[a].push_back(e << 1 | 0);
+    }
+    if (b >= 0) {
+      asmv[b].push_back(e << 2 | 1);
+      gv[b].push_back(e << 1 | 1);
+    }
+    if (a >= 0 && b >= 0) {
+      if (a > b) asmv[blk(a, b)].push_back(e << 2 | 2);
+      else asmv[blk(b, a)].push_back(e << 2 | 3);
+    }
+  }
+  std::vector<int> asm_ptr(nb + 1, 0), asm_it, g_ptr(nf + 1, 0), g_it;
+  for (int b = 0; b < nb; ++b) {
+    asm_ptr[b] = (int)asm_it.size();
+    for (int x : asmv[b]) asm_it.push_back(x);
+  }
+  asm_ptr[nb] = (int)asm_it.size();
+  for (int k = 0; k < nf; ++k) {
+    g_ptr[k] = (int)g_it.size();
+    for (int x : gv[k]) g_it.push_back(x);
+  }
+  g_ptr[nf] = (int)g_it.size();
+  // chaining tree: edges in input order that join two components, walked from `fixed`
+  std::vector<int> uf(n);
+  for (int v = 0; v < n; ++v) uf[v] = v;
+  std::function<int(int)> find = [&](int a) {
+    while (uf[a] != a) a = uf[a] = uf[uf[a]];
+    return a;
+  };
+  std::vector<std::vector<int>> tadj(n);
+  for (int e = 0; e < m; ++e) {
+    const int a = find(hi[e]), b = find(hj[e]);
+    if (a != b) {
+      uf[a] = b;
+      tadj[hi[e]].push_back(e);
+      tadj[hj[e]].push_back(e);
+    }
+  }
+  std::vector<int> tpar(n, -1), tedge(n, -1), tdir(n, 0), depth(n, 0), q{fixed};
+  std::vector<char> seen(n, 0);
+  seen[fixed] = 1;
+  int maxd = 0;
+  for (size_t h = 0; h < q.size(); ++h) {
+    const int a = q[h];
+    for (int e : tadj[a]) {
+      const int o = hi[e] == a ? hj[e] : hi[e];
+      if (seen[o]) continue;
+      seen[o] = 1;
+      tpar[o] = a;
+      tedge[o] = e;
+      tdir[o] = hi[e] == a ? 1 : -1;
+      depth[o] = depth[a] + 1;
+      maxd = std::max(maxd, depth[o]);
+      q.push_back(o);
+    }
+  }
+  int rounds = 0;
+  while ((1 << rounds) < maxd + 1) ++rounds;
+  P.rounds = rounds;
+  std::vector<int> vi(hi, hi + m), vj(hj, hj + m);
+  cudaError_t err = cudaSuccess;
+  auto chk = [&](cudaError_t e) {
+    if (err == cudaSuccess) err = e;
+  };
+  chk(upload(P, &P.d_ei, vi));
+  chk(upload(P, &P.d_ej, vj));
+  chk(upload(P, &P.d_perm, perm));
+  chk(upload(P, &P.d_col_ptr, col_ptr));
+  chk(upload(P, &P.d_off_row, off_row));
+  chk(upload(P, &P.d_off_blk, off_blk));
+  chk(upload(P, &P.d_upd_ptr, upd_ptr));
+  chk(upload(P, &P.d_upd, upd));
+  chk(upload(P, &P.d_row_ptr, row_ptr));
+  chk(upload(P, &P.d_row, row));
+  chk(upload(P, &P.d_level_cols, level_cols));
+  chk(upload(P, &P.d_asm_ptr, asm_ptr));
+  chk(upload(P, &P.d_asm, asm_it));
+  chk(upload(P, &P.d_g_ptr, g_ptr));
+  chk(upload(P, &P.d_g, g_it));
+  chk(upload(P, &P.d_parent, tpar));
+  chk(upload(P, &P.d_tedge, tedge));
+  chk(upload(P, &P.d_tdir, tdir));
+  chk(alloc(P, &P.d_anc0, n));
+  chk(alloc(P, &P.d_anc1, n));
+  chk(alloc(P, &P.d_fail, 1));
+  chk(alloc(P, &P.d_L, (size_t)nb * NB));
+  chk(alloc(P, &P.d_b, (size_t)nf * 7));
+  chk(alloc(P, &P.d_contrib, (size_t)m * 3 * NB));
+  chk(alloc(P, &P.d_gvec, (size_t)m * 14));
+  chk(alloc(P, &P.d_chi2e, m));
+  chk(alloc(P, &P.d_W0, n));
+  chk(alloc(P, &P.d_W1, n));
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(ctx, EC3R_ERR_OOM, "pose-graph plan allocation failed: %s",
+                     cudaGetErrorString(err));
+  }
+  return EC3R_OK;
+}
+
+// B_2k/(2k)! = (-1)^{k+1} 2 zeta(2k) / (2 pi)^{2k}; zeta by direct sum plus an
+// Euler-Maclaurin tail.
+static void bernoulli_table(double* c) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = 1; k <= NBERN; ++k) {
+    const int s = 2 * k;
+    const int N = 1000;
+    long double z = 0.0L;
+    for (int i = N - 1; i >= 1; --i) z += powl((long double)i, -s);
+    const long double Nn = N;
+    z += powl(Nn, 1 - s) / (s - 1) + 0.5L * powl(Nn, -s) + (long double)s / 12.0L * powl(Nn, -s - 1) -
+         (long double)s * (s + 1) * (s + 2) / 720.0L * powl(Nn, -s - 3);
+    const long double v = 2.0L * z / powl(2.0L * pi, s);
+    c[k - 1] = (double)((k % 2 == 1) ? v : -v);
+  }
+}
+
+static uint64_t fnv(const int32_t* a, int n, uint64_t h) {
+  for (int i = 0; i < n; ++i) {
+    h ^= (uint32_t)a[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+
+}  // namespace pg
+}  // namespace ec3r
+
+using namespace ec3r;
+using namespace ec3r::pg;
+
+extern "C" {
+
+void ec3r_pg_opts_default(ec3r_pg_opts* o) {
+  if (!o) return;
+  o->iters = 10;
+  o->fixed_node = 0;
+  o->lm_lambda = 0.0;
+  o->init_by_chaining = 1;
+}
+
+ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nodes, int n_edges,
+                                    const int32_t* h_i, const int32_t* h_j,
+                                    const ec3r_sim3* d_Tij, const double* d_info,
+                                    const ec3r_pg_opts* opts, double* d_chi2, void* stream) {
+  if (!ctx) return EC3R_ERR_INVALID_ARG;
+  if (!opts || n_nodes < 1 || n_edges < 0 || !d_nodes || (n_edges > 0 && (!h_i || !h_j || !d_Tij)))
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "bad pose-graph arguments");
+  if (opts->iters < 0 || opts->iters > 1000 || opts->fixed_node < 0 ||
+      opts->fixed_node >= n_nodes || !(opts->lm_lambda >= 0.0) || n_nodes > (1 << 24) ||
+      n_edges > (1 << 28))
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "bad ec3r_pg_opts");
+  for (int e = 0; e < n_edges; ++e)
+    if (h_i[e] < 0 || h_i[e] >= n_nodes || h_j[e] < 0 || h_j[e] >= n_nodes || h_i[e] == h_j[e])
+      return set_error(ctx, EC3R_ERR_INVALID_ARG, "edge %d has invalid endpoints (%d, %d)", e,
+                       h_i[e], h_j[e]);
+  EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!ctx->ext.count("pg.bernoulli")) {  // constant table, once per context (device)
+    if (stream_capturing(s))
+      return set_error(ctx, EC3R_ERR_CAPTURE, "first pose-graph call during stream capture");
+    double c[NBERN];
+    bernoulli_table(c);
+    EC3R_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_bern, c, sizeof(c)));
+    ctx->ext["pg.bernoulli"] = new Extension();
+  }
+  // plan (host symbolic analysis), cached per graph structure
+  uint64_t h = 1469598103934665603ULL;
+  h = fnv(h_i, n_edges, h);
+  h = fnv(h_j, n_edges, h);
+  const std::string pkey = key_of("pgplan", {(uint64_t)n_nodes, (uint64_t)n_edges,
+                                             (uint64_t)opts->fixed_node, h});
+  Plan* P = nullptr;
+  auto it = ctx->ext.find(pkey);
+  if (it != ctx->ext.end()) {
+    P = static_cast<Plan*>(it->second);
+  } else {
+    if (stream_capturing(s))
+      return set_error(ctx, EC3R_ERR_CAPTURE, "new pose-graph structure during stream capture");
+    // keep at most 4 plans
+    int count = 0;
+    for (auto& kv : ctx->ext)
+      if (kv.first.rfind("pgplan", 0) == 0) ++count;
+    if (count >= 4) {
+      cudaDeviceSynchronize();
+      drop_graphs(ctx);
+      for (auto j = ctx->ext.begin(); j != ctx->ext.end();) {
+        if (j->first.rfind("pgplan", 0) == 0) {
+          delete j->second;
+          j = ctx->ext.erase(j);
+        } else {
+          ++j;
+        }
+      }
+    }
+    P = new Plan();
+    ec3r_status st = build_plan(ctx, n_nodes, n_edges, h_i, h_j, opts->fixed_node, *P);
+    if (st != EC3R_OK) {
+      delete P;
+      return st;
+    }
+    ctx->ext[pkey] = P;
+  }
+  const ec3r_pg_opts o = *opts;
+  const std::string gkey =
+      key_of("pg", {(uint64_t)P, (uint64_t)d_nodes, (uint64_t)d_Tij, (uint64_t)d_info,
+                    (uint64_t)d_chi2, (uint64_t)o.iters, dbits(o.lm_lambda),
+                    (uint64_t)o.init_by_chaining});
+  return run_graph(ctx, gkey, s, [&](cudaStream_t cs) -> ec3r_status {
+    if (o.init_by_chaining)
+      traced(ctx, cs, "pg_init", [&] {
+        k_pg_init<<<1, 1024, 0, cs>>>(n_nodes, o.fixed_node, P->d_parent, P->d_tedge, P->d_tdir,
+                                      d_Tij, d_nodes, P->d_W0, P->d_W1, P->d_anc0, P->d_anc1,
+                                      P->rounds);
+      });
+    const int nlev = (int)P->level_ptr.size() - 1;
+    for (int itn = 0; itn <= o.iters; ++itn) {
+      const bool last = itn == o.iters;  // last pass only evaluates chi^2
+      if (n_edges > 0)
+        traced(ctx, cs, "pg_linearize", [&] {
+          k_pg_linearize<<<n_edges, 32, 0, cs>>>(P->d_ei, P->d_ej, d_nodes, d_Tij, d_info,
+                                                 P->d_contrib, P->d_gvec, P->d_chi2e, last ? 0 : 1);
+        });
+      if (last) {
+        if (d_chi2)
+          traced(ctx, cs, "pg_assemble", [&] {
+            k_pg_assemble<<<1, 32, 0, cs>>>(0, 0, n_edges, P->d_asm_ptr, P->d_asm, P->d_g_ptr,
+                                            P->d_g, P->d_contrib, P->d_gvec, P->d_chi2e, 0.0,
+                                            P->d_L, P->d_b, d_chi2 + itn, P->d_fail);
+          });
+        break;
+      }
+      traced(ctx, cs, "pg_assemble", [&] {
+        k_pg_assemble<<<P->n_blocks + P->nf + 1, 32, 0, cs>>>(
+            P->n_blocks, P->nf, n_edges, P->d_asm_ptr, P->d_asm, P->d_g_ptr, P->d_g,
+            P->d_contrib, P->d_gvec, P->d_chi2e, o.lm_lambda, P->d_L, P->d_b,
+            d_chi2 ? d_chi2 + itn : nullptr, P->d_fail);
+      });
+      if (P->nf == 0) continue;
+      for (int l = 0; l < nlev; ++l)
+        traced(ctx, cs, "pg_factor", [&] {
+          k_pg_factor<<<P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs>>>(
+              P->d_level_cols + P->level_ptr[l], P->d_col_ptr, P->d_off_blk, P->d_upd_ptr,
+              P->d_upd, P->d_row_ptr, P->d_row, P->d_L, P->d_b, ctx->d_flags, P->d_fail);
+        });
+      for (int l = nlev - 1; l >= 0; --l)
+        traced(ctx, cs, "pg_backsolve", [&] {
+          k_pg_backsolve<<<P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs>>>(
+              P->d_level_cols + P->level_ptr[l], P->d_col_ptr, P->d_off_row, P->d_off_blk,
+              P->d_L, P->d_b);
+        });
+      traced(ctx, cs, "pg_update", [&] {
+        k_pg_update<<<(P->nf + 63) / 64, 64, 0, cs>>>(P->nf, P->d_perm, P->d_b, d_nodes,
+                                                      P->d_fail);
+      });
+    }
+    EC3R_CUDA_TRY(ctx, cudaGetLastError());
+    return EC3R_OK;
+  });
+}
+
+}  // extern "C"

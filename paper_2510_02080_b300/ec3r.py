@@ -27,7 +27,7 @@ RULE = {"product": 0, "src": 1}
 EXPORTS = ("ec3r_create", "ec3r_destroy", "ec3r_last_error", "ec3r_status_string",
            "ec3r_version", "ec3r_sync_status", "ec3r_align_opts_default",
            "ec3r_align_submaps", "ec3r_fuse_points", "ec3r_profile", "ec3r_profile_read",
-           "ec3r_align_submaps_noalloc")
+           "ec3r_align_submaps_noalloc", "ec3r_pg_opts_default", "ec3r_pose_graph_correct")
 
 
 class Sim3(C.Structure):
@@ -37,6 +37,11 @@ class Sim3(C.Structure):
 class AlignOpts(C.Structure):
     _fields_ = [("huber_delta", C.c_float), ("iters", C.c_int), ("conf_min", C.c_float),
                 ("weight_rule", C.c_int), ("precision", C.c_int), ("want_cost", C.c_int)]
+
+
+class PgOpts(C.Structure):
+    _fields_ = [("iters", C.c_int), ("fixed_node", C.c_int), ("lm_lambda", C.c_double),
+                ("init_by_chaining", C.c_int)]
 
 
 class Ec3rError(RuntimeError):
@@ -69,8 +74,12 @@ def _declare(l):
     l.ec3r_profile.argtypes = [_P, C.c_int]
     l.ec3r_profile_read.argtypes = [_P, C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int64), C.POINTER(C.c_int)]
+    l.ec3r_pg_opts_default.argtypes = [C.POINTER(PgOpts)]
+    l.ec3r_pg_opts_default.restype = None
+    l.ec3r_pose_graph_correct.argtypes = [_P, C.c_int, _P, C.c_int, _P, _P, _P, _P,
+                                          C.POINTER(PgOpts), _P, _P]
     for name in ("ec3r_create", "ec3r_sync_status", "ec3r_align_submaps", "ec3r_fuse_points",
-                 "ec3r_profile", "ec3r_profile_read"):
+                 "ec3r_profile", "ec3r_profile_read", "ec3r_pose_graph_correct"):
         getattr(l, name).restype = C.c_int
 
 
@@ -182,6 +191,30 @@ class Context:
             _ptr(status), _ptr(cost) if want_cost else None, _stream(stream))
         self._check(st)
         return out, status, (cost if want_cost else None)
+
+    # -- pose graph --------------------------------------------------------
+    def pose_graph_correct(self, nodes, ei, ej, Tij, info=None, *, iters=10, fixed=0,
+                           lm_lambda=0.0, init=True, chi2=None, stream=None):
+        """Refines ``nodes`` ([n,13] float64, device) in place; returns chi^2 history.
+
+        ``ei``/``ej`` are the edge endpoints on the host (the graph structure is
+        planned there); ``Tij`` [m,13] and ``info`` [m,49] live on the device.
+        """
+        import numpy as np
+        hi = np.ascontiguousarray(np.asarray(ei.cpu() if hasattr(ei, "cpu") else ei,
+                                             dtype=np.int32))
+        hj = np.ascontiguousarray(np.asarray(ej.cpu() if hasattr(ej, "cpu") else ej,
+                                             dtype=np.int32))
+        n, m = int(nodes.shape[0]), int(hi.shape[0])
+        if chi2 is None:
+            chi2 = torch.empty((iters + 1,), dtype=torch.float64, device=nodes.device)
+        o = PgOpts(int(iters), int(fixed), float(lm_lambda), 1 if init else 0)
+        st = self._lib.ec3r_pose_graph_correct(
+            self._h, n, _ptr(nodes), m, hi.ctypes.data_as(C.c_void_p),
+            hj.ctypes.data_as(C.c_void_p), _ptr(Tij) if m else None, _ptr(info), C.byref(o),
+            _ptr(chi2), _stream(stream))
+        self._check(st)
+        return chi2
 
     # -- fusion ------------------------------------------------------------
     def fuse_points(self, xyz, conf, poses, out_xyz, out_idx, cursor, *, threshold=1.0,
