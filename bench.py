@@ -5,8 +5,10 @@
 Workload (one "step"): the 200-submap chain (5 frames of 294x518 per submap,
 one shared keyframe between consecutive submaps): batched Huber-IRLS
 registration of the 199 consecutive pairs (10 solves, FP32 moments, FP64
-solve), the Sim(3) pose graph over the 200 submaps (when built), and the
-confidence > 1 compaction + global transform of all 152,292,000 points.
+solve), the FP64 Sim(3) pose graph over the 200 submaps with the 199
+registered edges (chaining + 10 Gauss-Newton iterations), and the
+confidence > 1 compaction + global transform of all 152,292,000 points under
+the corrected poses.
 
 Metric: Sim(3)-registered points per second per IRLS iteration
 (valid correspondences x iterations / step time), whole job over all ranks.
@@ -32,6 +34,7 @@ METRIC = "Sim(3)-registered points/s per IRLS iter (batched, FP32) and % HBM roo
 UNIT = "pt-iter/s"
 M_SUBMAPS, F_FRAMES, H, W = 200, 5, 294, 518   # the chain workload
 ITERS, DELTA = 10, 0.02
+PG_ITERS = 10
 SWEEP_BYTES_PER_PIXEL = 32          # p, q (2 x 12 B) + c_p, c_q (2 x 4 B) per sweep
 # DRAM bytes per pixel of one sweep launch, from the ncu capture summarised in
 # profiles/irls_sweep_fp32_chain40_294x518.md (read + write / pixels); the
@@ -195,7 +198,14 @@ def run_ours(args):
     out_idx = torch.empty((kept,), dtype=torch.int64, device=dev)
     S = torch.empty((ps.n_pairs, 13), dtype=torch.float64, device=dev)
     st = torch.empty((ps.n_pairs,), dtype=torch.int32, device=dev)
-    poses = ec3r.sim3_rows(ch.T_gt.s, ch.T_gt.R, ch.T_gt.t).to(dev)
+    # pose graph: node m = submap m, edge (m, m+1) carries pair m's estimate
+    import numpy as np
+    ei = np.arange(ps.n_pairs, dtype=np.int32)
+    ej = ei + 1
+    poses = torch.zeros((M, 13), dtype=torch.float64, device=dev)
+    poses[:, 0] = 1.0
+    poses[:, [1, 5, 9]] = 1.0          # identity; node 0 stays fixed (world = submap 0)
+    chi2 = torch.empty((PG_ITERS + 1,), dtype=torch.float64, device=dev)
     n_cursor = args.steps + args.warmup + 8
     cursors = torch.zeros((n_cursor,), dtype=torch.int64, device=dev)
     ci = [0]
@@ -203,6 +213,7 @@ def run_ours(args):
     def step(xyz_in, conf_in):
         ctx.align_submaps(xyz_in.view(n_frames, hw, 3), conf_in.view(n_frames, hw), ps.link_off,
                           ps.src, ps.tgt, delta=DELTA, iters=ITERS, out=S, status=st)
+        ctx.pose_graph_correct(poses, ei, ej, S, iters=PG_ITERS, chi2=chi2)
         c = cursors[ci[0] % n_cursor:ci[0] % n_cursor + 1]
         ci[0] += 1
         ctx.fuse_points(xyz_in.view(M, -1, 3), conf_in.view(M, -1), poses,
@@ -294,6 +305,7 @@ def run_ours(args):
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                    "share": v[0] / total_prof if total_prof else None} for k, v in prof.items()}
     fuse_ms = sum(prof.get(k, (0.0, 0))[0] for k in ("fuse_count", "fuse_scan", "fuse_scatter"))
+    pg_ms = sum(v[0] for k, v in prof.items() if k.startswith("pg_"))
     fuse_gbs = 26.0 * n_fuse * args.steps / (fuse_ms * 1e-3) / 1e9 if fuse_ms else None
 
     cpu_rate, n_cpu, dt_cpu, np_cpu = (None, 0, 0.0, 0)
@@ -308,7 +320,8 @@ def run_ours(args):
                    "H": H, "W": W, "pairs": ps.n_pairs, "valid_correspondences": n_valid,
                    "iters": ITERS, "huber_delta": DELTA, "precision": "fp32 moments, fp64 solve",
                    "fused_points": n_fuse, "kept_points": kept,
-                   "rows": ["registration", "fusion"],
+                   "pose_graph": {"nodes": M, "edges": ps.n_pairs, "gn_iters": PG_ITERS},
+                   "rows": ["registration", "pose graph", "fusion"],
                    "l2": "inputs 2.4 GB per rank > 126 MB L2; no flush"},
         "roofline": {"bound": "hbm", "kernel": "irls_sweep_fp32", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -319,6 +332,7 @@ def run_ours(args):
                      "launch_ms": sweep_ms},
         "kernels": kernels,
         "fusion": {"ms_per_step": fuse_ms / args.steps, "gbs_at_26B_per_point": fuse_gbs},
+        "pose_graph": {"ms_per_step": pg_ms / args.steps},
         "clocks": clk,
         "gpu_launches": int(sum(v[1] for v in prof.values())),
     }

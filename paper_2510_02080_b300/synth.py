@@ -123,20 +123,66 @@ def make_scene(g, device, n_planes: int = 4, n_spheres: int = 8) -> Scene:
     return Scene(torch.cat([wall_n, n]), torch.cat([wall_d, d]), c, r)
 
 
-def camera_path(g, n: int, device, step: float = 0.12, turn_deg: float = 6.0):
-    """Smooth random walk of camera centres inside the box, with small turns."""
+def _clear_of(scene, pos, clearance):
+    """True when ``pos`` is at least ``clearance`` from every surface of the scene."""
+    if scene is None:
+        return True
+    if (pos < clearance).any() or (pos > BOX - clearance).any():
+        return False
+    n_wall = 6
+    dp = (scene.plane_n[n_wall:] @ pos - scene.plane_d[n_wall:]).abs()
+    if (dp < clearance).any():
+        return False
+    ds = (scene.sph_c - pos).norm(dim=-1) - scene.sph_r
+    return bool((ds.abs() >= clearance).all())
+
+
+def _view_depth(scene, pos, R):
+    """Distance along the optical axis to the first surface."""
+    d = R[:, 2]
+    nd = scene.plane_n @ d
+    tp = (scene.plane_d - scene.plane_n @ pos) / torch.where(nd.abs() < 1e-12,
+                                                            torch.full_like(nd, 1e-12), nd)
+    tp = torch.where(tp > 1e-6, tp, torch.full_like(tp, float("inf")))
+    oc = pos - scene.sph_c
+    b = oc @ d
+    cc = (oc * oc).sum(-1) - scene.sph_r ** 2
+    disc = b * b - cc
+    sq = torch.sqrt(torch.clamp(disc, min=0.0))
+    ts = torch.where(-b - sq > 1e-6, -b - sq, -b + sq)
+    ts = torch.where((disc >= 0) & (ts > 1e-6), ts, torch.full_like(ts, float("inf")))
+    return float(torch.minimum(tp.min(), ts.min()))
+
+
+def camera_path(g, n: int, device, step: float = 0.12, turn_deg: float = 6.0, scene=None,
+                clearance: float = 0.8, min_view: float = 1.5):
+    """Smooth random walk of camera centres inside the box, with small turns.
+
+    With a scene, every centre keeps ``clearance`` from all surfaces and the
+    optical axis meets the first surface at least ``min_view`` away (a
+    keyframe never stares at a patch of a few centimetres); a rejected
+    proposal is redrawn, up to 50 times, else the camera stays put.
+    """
     c = torch.empty(n, 3, dtype=torch.float64, device=device)
     R = torch.empty(n, 3, 3, dtype=torch.float64, device=device)
-    pos0 = _uniform(g, (3,), 3.0, 7.0, device)
-    R0 = random_rotation(g, 1, device)[0]
-    steps = step * _normal(g, (n, 3), device)
-    turns = small_rotation(g, n, math.radians(turn_deg), device)
-    pos, rot = pos0, R0
+    pos = _uniform(g, (3,), 3.0, 7.0, device)
+    rot = random_rotation(g, 1, device)[0]
+    for _ in range(200):
+        if _clear_of(scene, pos, clearance) and (scene is None or
+                                                 _view_depth(scene, pos, rot) >= min_view):
+            break
+        pos = _uniform(g, (3,), 1.5, 8.5, device)
+        rot = random_rotation(g, 1, device)[0]
     for k in range(n):
         c[k] = pos
         R[k] = rot
-        pos = torch.clamp(pos + steps[k], 1.0, BOX - 1.0)
-        rot = rot @ turns[k]
+        for _ in range(50):
+            p2 = torch.clamp(pos + step * _normal(g, (3,), device), 1.0, BOX - 1.0)
+            r2 = rot @ small_rotation(g, 1, math.radians(turn_deg), device)[0]
+            if scene is None or (_clear_of(scene, p2, clearance)
+                                 and _view_depth(scene, p2, r2) >= min_view):
+                pos, rot = p2, r2
+                break
     return c, R
 
 
@@ -220,7 +266,7 @@ def make_pair(seed: int, H: int = 294, W: int = 518, sigma: float = 0.005,
     """One shared frame: p in camera coordinates, q = S_gt p, both noisy."""
     g = _gen(seed, device)
     scene = make_scene(g, device)
-    c, R = camera_path(g, 1, device)
+    c, R = camera_path(g, 1, device, scene=scene)
     fov = hfovs(g, 1, device)
     X = cast_rays(scene, c, R, fov, H, W, torch.float64)[0]        # world, float64
     p = (X - c[0]) @ R[0]                                          # camera frame
@@ -283,7 +329,7 @@ def make_chain(seed: int, M: int, F: int = 5, H: int = 294, W: int = 518, sigma:
     g = _gen(seed, device)
     scene = make_scene(g, device)
     K = (F - 1) * M + 1
-    cc, cR = camera_path(g, K, device)
+    cc, cR = camera_path(g, K, device, scene=scene)
     fov = hfovs(g, K, device)
     lam = _uniform(g, (M,), 0.5, 2.0, device)         # world -> submap scale
     n = H * W
@@ -352,7 +398,7 @@ def make_loop_batch(seed: int, n_pairs: int, H: int = 294, W: int = 518, max_fra
     fi = 0
     for k in range(n_pairs):
         f = nf_l[k]
-        c, R = camera_path(g, f, device, step=0.25, turn_deg=10.0)
+        c, R = camera_path(g, f, device, step=0.25, turn_deg=10.0, scene=scene)
         fov = hfovs(g, f, device)
         X = cast_rays(scene, c, R, fov, H, W, torch.float32).to(torch.float64)
         p = (X - c[0]) @ R[0]
