@@ -165,6 +165,37 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
                                int32_t* d_pair_status, double* d_pair_cost, void* stream);
 
 /*
+ * Reverse-mode derivative of ec3r_align_submaps (the paper has no gradient;
+ * this differentiates the registration above, for training on top of it).
+ *
+ * Same inputs and options as the forward call (FP32 moments only).  Given
+ * d_grad_S (float64 [n_pairs][13], device: dL/ds, dL/dR row-major, dL/dt of
+ * each pair's output) and d_grad_cost (float64 [n_pairs], device, nullable:
+ * dL/dcost of the weighted residual that want_cost reports), it writes the
+ * gradient with respect to every input point and confidence of the frame
+ * bank: d_grad_xyz (float32 [n_frames][hw][3]) and d_grad_conf (float32
+ * [n_frames][hw]); frames used by several links receive the sum, accumulated
+ * in link order (deterministic).  Invalid correspondences and degenerate pairs
+ * get zero.
+ *
+ * The call re-runs the forward pass with per-iteration checkpoints (estimate
+ * and moments of every solve), so it needs no state from an earlier call; it
+ * then differentiates all `iters` solves, unrolled (the Huber weights of
+ * solve k depend on solve k-1): one reduction sweep per iteration and one
+ * final sweep that writes the per-point gradients.  The rotation is
+ * differentiated in its polar form, with 1/(d_i + d_j) factors.  The Huber
+ * weight has a kink at r = delta; there the one-sided derivative of the
+ * branch taken by the FP32 forward is used.
+ */
+ec3r_status ec3r_align_submaps_backward(ec3r_ctx* ctx, const float* d_xyz, const float* d_conf,
+                                        int64_t n_frames, int64_t hw, int n_pairs,
+                                        int64_t n_links, const int32_t* d_link_off,
+                                        const int32_t* d_src, const int32_t* d_tgt,
+                                        const float* d_pair_conf_min, const ec3r_align_opts* opts,
+                                        const double* d_grad_S, const double* d_grad_cost,
+                                        float* d_grad_xyz, float* d_grad_conf, void* stream);
+
+/*
  * Registration without allocation.  The paper has no counterpart: this entry
  * point exists for callers that may not allocate device memory at all, such
  * as code running inside a memory arena it does not own, real-time loops

@@ -18,35 +18,10 @@
 //                          Newton-polar refinement), scale, translation
 //
 // The sweep is bandwidth-bound: it reads 32 bytes per pixel (p, q, c_p, c_q).
-#include <cfloat>
-
-#include "common.cuh"
+#include "align_impl.cuh"
 
 namespace ec3r {
 namespace align {
-
-constexpr int TILE = 8192;  // pixels per sweep CTA
-constexpr int THREADS = 256;
-constexpr int NMOM = 19;
-// moment slots
-enum { M_W = 0, M_SP = 1, M_SQ = 4, M_PP = 7, M_QP = 8, M_COST = 17, M_CNT = 18 };
-constexpr double RANK_REL_TOL = 1e-4;
-
-struct PairState {
-  // FP32 view of the current and previous estimate, pivot-relative:
-  // residual e = A p' + b - q',  p' = p - piv_p, q' = q - piv_q, A = s R.
-  float A[9], b[3];
-  float Ap[9], bp[3];
-  float piv_p[3], piv_q[3];
-  float cmin;
-  int active;
-  int status;
-  int pad;
-  double Ad[9], bd[3];
-  double Adp[9], bdp[3];
-};
-
-__device__ __forceinline__ bool finitef(float x) { return fabsf(x) <= FLT_MAX; }
 
 // --------------------------------------------------------------------------
 // set-up
@@ -273,154 +248,6 @@ __global__ void __launch_bounds__(THREADS, 2) k_sweep(
   }
 }
 
-// --------------------------------------------------------------------------
-// solve
-// --------------------------------------------------------------------------
-// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (row-major), FP32.
-// Eigenvalues descending, eigenvectors in the columns of V.
-__device__ void jacobi_eig3f(float B[9], float V[9], float lam[3]) {
-  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.f : 0.f;
-  for (int sweep = 0; sweep < 8; ++sweep) {
-    const float off = fabsf(B[1]) + fabsf(B[2]) + fabsf(B[5]);
-    const float dia = fabsf(B[0]) + fabsf(B[4]) + fabsf(B[8]);
-    if (off <= 1e-9f * dia) break;
-    for (int pq = 0; pq < 3; ++pq) {
-      const int p = pq == 2 ? 1 : 0;
-      const int q = pq == 0 ? 1 : 2;
-      const float bpq = B[3 * p + q];
-      if (fabsf(bpq) < 1e-30f) continue;
-      const float theta = (B[3 * q + q] - B[3 * p + p]) / (2.f * bpq);
-      const float tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-      const float cs = rsqrtf(tt * tt + 1.f), sn = tt * cs;
-      for (int r = 0; r < 3; ++r) {
-        const float brp = B[3 * r + p], brq = B[3 * r + q];
-        B[3 * r + p] = cs * brp - sn * brq;
-        B[3 * r + q] = sn * brp + cs * brq;
-      }
-      for (int r = 0; r < 3; ++r) {
-        const float bpr = B[3 * p + r], bqr = B[3 * q + r];
-        B[3 * p + r] = cs * bpr - sn * bqr;
-        B[3 * q + r] = sn * bpr + cs * bqr;
-      }
-      for (int r = 0; r < 3; ++r) {
-        const float vrp = V[3 * r + p], vrq = V[3 * r + q];
-        V[3 * r + p] = cs * vrp - sn * vrq;
-        V[3 * r + q] = sn * vrp + cs * vrq;
-      }
-    }
-  }
-  lam[0] = B[0]; lam[1] = B[4]; lam[2] = B[8];
-  for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2 - a; ++b)
-      if (lam[b] < lam[b + 1]) {
-        const float tl = lam[b]; lam[b] = lam[b + 1]; lam[b + 1] = tl;
-        for (int r = 0; r < 3; ++r) {
-          const float tv = V[3 * r + b]; V[3 * r + b] = V[3 * r + b + 1]; V[3 * r + b + 1] = tv;
-        }
-      }
-}
-
-// Rotation R (FP64) of the Umeyama solution, R = U diag(1,1,det(U)det(V)) V^T,
-// i.e. the orthogonal polar factor of Sig with det +1, and the Rayleigh
-// estimates d[0..2] of the signed singular values.  An FP32 Jacobi SVD seeds
-// R; two FP64 Newton-polar steps R <- R cay(w), (tr(Hs) I - Hs) w =
-// vee(H - H^T), H = R^T Sig, bring it to FP64 round-off.
-__device__ void polar_rotation(const double Sig[9], double R[9], double d[3]) {
-  double nrm = 0.0;
-  for (int i = 0; i < 9; ++i) nrm += Sig[i] * Sig[i];
-  nrm = sqrt(nrm);
-  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-  float Sf[9], B[9], V[9], lam[3];
-  for (int i = 0; i < 9; ++i) Sf[i] = (float)(Sig[i] * inv);
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      B[3 * i + j] = Sf[i] * Sf[j] + Sf[3 + i] * Sf[3 + j] + Sf[6 + i] * Sf[6 + j];
-  jacobi_eig3f(B, V, lam);
-  float v[3][3];
-  for (int c = 0; c < 3; ++c)
-    for (int r = 0; r < 3; ++r) v[c][r] = V[3 * r + c];
-  float u[3][3];
-  for (int c = 0; c < 2; ++c)
-    for (int r = 0; r < 3; ++r)
-      u[c][r] = Sf[3 * r] * v[c][0] + Sf[3 * r + 1] * v[c][1] + Sf[3 * r + 2] * v[c][2];
-  float n0 = sqrtf(u[0][0] * u[0][0] + u[0][1] * u[0][1] + u[0][2] * u[0][2]);
-  if (n0 < 1e-30f) { u[0][0] = 1.f; u[0][1] = 0.f; u[0][2] = 0.f; n0 = 1.f; }
-  for (int r = 0; r < 3; ++r) u[0][r] /= n0;
-  const float dp = u[0][0] * u[1][0] + u[0][1] * u[1][1] + u[0][2] * u[1][2];
-  for (int r = 0; r < 3; ++r) u[1][r] -= dp * u[0][r];
-  float n1 = sqrtf(u[1][0] * u[1][0] + u[1][1] * u[1][1] + u[1][2] * u[1][2]);
-  if (n1 < 1e-30f) {  // any unit vector orthogonal to u0
-    float a[3] = {0.f, 0.f, 0.f};
-    a[fabsf(u[0][0]) < 0.5f ? 0 : 1] = 1.f;
-    const float da = a[0] * u[0][0] + a[1] * u[0][1] + a[2] * u[0][2];
-    for (int r = 0; r < 3; ++r) u[1][r] = a[r] - da * u[0][r];
-    n1 = sqrtf(u[1][0] * u[1][0] + u[1][1] * u[1][1] + u[1][2] * u[1][2]);
-  }
-  for (int r = 0; r < 3; ++r) u[1][r] /= n1;
-  u[2][0] = u[0][1] * u[1][2] - u[0][2] * u[1][1];
-  u[2][1] = u[0][2] * u[1][0] - u[0][0] * u[1][2];
-  u[2][2] = u[0][0] * u[1][1] - u[0][1] * u[1][0];
-  const float detV = v[0][0] * (v[1][1] * v[2][2] - v[1][2] * v[2][1]) -
-                     v[0][1] * (v[1][0] * v[2][2] - v[1][2] * v[2][0]) +
-                     v[0][2] * (v[1][0] * v[2][1] - v[1][1] * v[2][0]);
-  const float e3 = detV < 0.f ? -1.f : 1.f;
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      R[3 * i + j] = (double)(u[0][i] * v[0][j] + u[1][i] * v[1][j] + e3 * u[2][i] * v[2][j]);
-  for (int it = 0; it < 2; ++it) {
-    double H[9];
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j)
-        H[3 * i + j] = R[i] * Sig[j] + R[3 + i] * Sig[3 + j] + R[6 + i] * Sig[6 + j];
-    const double a0 = H[7] - H[5], a1 = H[2] - H[6], a2 = H[3] - H[1];
-    const double tr = H[0] + H[4] + H[8];
-    double M[9];
-    M[0] = tr - H[0]; M[4] = tr - H[4]; M[8] = tr - H[8];
-    M[1] = M[3] = -0.5 * (H[1] + H[3]);
-    M[2] = M[6] = -0.5 * (H[2] + H[6]);
-    M[5] = M[7] = -0.5 * (H[5] + H[7]);
-    const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8],
-                 c02 = M[3] * M[7] - M[4] * M[6];
-    const double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
-    if (!(fabs(det) > 1e-300)) break;
-    const double c11 = M[0] * M[8] - M[2] * M[6], c12 = M[2] * M[3] - M[0] * M[5],
-                 c22 = M[0] * M[4] - M[1] * M[3];
-    const double id = 1.0 / det;  // M symmetric: inverse = cofactor matrix / det
-    const double w0 = (c00 * a0 + c01 * a1 + c02 * a2) * id;
-    const double w1 = (c01 * a0 + c11 * a1 + c12 * a2) * id;
-    const double w2 = (c02 * a0 + c12 * a1 + c22 * a2) * id;
-    // Cayley transform of w: C = I + 2/(1+|h|^2) (h^ + h^ h^), h = w/2
-    const double h0 = 0.5 * w0, h1 = 0.5 * w1, h2 = 0.5 * w2;
-    const double f = 2.0 / (1.0 + h0 * h0 + h1 * h1 + h2 * h2);
-    double C[9];
-    C[0] = 1.0 - f * (h1 * h1 + h2 * h2);
-    C[4] = 1.0 - f * (h0 * h0 + h2 * h2);
-    C[8] = 1.0 - f * (h0 * h0 + h1 * h1);
-    C[1] = f * (-h2 + h0 * h1);
-    C[2] = f * (h1 + h0 * h2);
-    C[3] = f * (h2 + h0 * h1);
-    C[5] = f * (-h0 + h1 * h2);
-    C[6] = f * (-h1 + h0 * h2);
-    C[7] = f * (h0 + h1 * h2);
-    double Rn[9];
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j)
-        Rn[3 * i + j] = R[3 * i] * C[j] + R[3 * i + 1] * C[3 + j] + R[3 * i + 2] * C[6 + j];
-    for (int i = 0; i < 9; ++i) R[i] = Rn[i];
-  }
-  double H[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      H[3 * i + j] = R[i] * Sig[j] + R[3 + i] * Sig[3 + j] + R[6 + i] * Sig[6 + j];
-  for (int c = 0; c < 3; ++c) {
-    const double x0 = v[c][0], x1 = v[c][1], x2 = v[c][2];
-    const double y0 = H[0] * x0 + H[1] * x1 + H[2] * x2;
-    const double y1 = H[3] * x0 + H[4] * x1 + H[5] * x2;
-    const double y2 = H[6] * x0 + H[7] * x1 + H[8] * x2;
-    d[c] = (x0 * y0 + x1 * y1 + x2 * y2) / (x0 * x0 + x1 * x1 + x2 * x2);
-  }
-}
-
 __device__ void write_identity(ec3r_sim3* o) {
   o->s = 1.0;
   for (int i = 0; i < 9; ++i) o->R[i] = (i % 4 == 0) ? 1.0 : 0.0;
@@ -429,11 +256,14 @@ __device__ void write_identity(ec3r_sim3* o) {
 
 // One warp per pair: FP64 tile sums (lane m < 19 owns moment m), then lane 0
 // solves.  `last` marks the final iteration (writes the outputs).
+// `ckpt` (nullable) receives, per pair and iteration `it` (1-based), the
+// moments and the new estimate for the backward pass.
 __global__ void __launch_bounds__(256) k_solve(int n_pairs, const int32_t* __restrict__ link_off,
                                                int tpl, const double* __restrict__ partials,
                                                PairState* __restrict__ st,
                                                ec3r_sim3* __restrict__ out,
-                                               int32_t* __restrict__ status_out, int last) {
+                                               int32_t* __restrict__ status_out, int last,
+                                               double* __restrict__ ckpt, int it, int iters) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   __shared__ double mom[8][NMOM];
@@ -495,6 +325,13 @@ __global__ void __launch_bounds__(256) k_solve(int n_pairs, const int32_t* __res
         if (!ok) status = EC3R_PAIR_NONFINITE;
       }
     }
+  }
+  double* ck = ckpt ? ckpt + ((size_t)warp * iters + (it - 1)) * CKPT : nullptr;
+  if (ck) {
+    for (int m = 0; m < NMOM; ++m) ck[CK_MOM + m] = M[m];
+    for (int i = 0; i < 9; ++i) ck[CK_A + i] = s * R[i];
+    for (int i = 0; i < 3; ++i) ck[CK_B + i] = b[i];
+    ck[CK_STATUS] = (double)status;
   }
   if (status) {
     S.status = (int)status;
@@ -619,9 +456,14 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
   if ((st = ensure_buf(ctx, "align.link_pair", sizeof(int32_t) * (size_t)(n_links + 1), s,
                        &p_lp)))
     return st;
-  PairState* state = (PairState*)p_state;
-  double* partials = (double*)p_part;
-  int32_t* link_pair = (int32_t*)p_lp;
+  void* p_ck;
+  if ((st = ensure_buf(ctx, "align.ckpt",
+                       sizeof(double) * CKPT * (size_t)n_pairs * (size_t)opts->iters, s, &p_ck)))
+    return st;
+  PairState* state = (PairState*)ctx->bufs["align.state"].ptr;
+  double* partials = (double*)ctx->bufs["align.partials"].ptr;
+  int32_t* link_pair = (int32_t*)ctx->bufs["align.link_pair"].ptr;
+  double* ckpt = (double*)p_ck;
   const bool vec =
       (hw % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0) && ((uintptr_t)d_conf % 16 == 0);
   const bool fp64 = opts->precision == EC3R_PREC_FP64;
@@ -671,7 +513,8 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
       else
         traced(ctx, cs, "sim3_solve", [&] {
           k_solve<<<solve_blocks, 256, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
-                                                d_out, d_pair_status, it == o.iters);
+                                                d_out, d_pair_status, it == o.iters, ckpt, it,
+                                                o.iters);
         });
     }
     EC3R_CUDA_TRY(ctx, cudaGetLastError());
@@ -807,7 +650,8 @@ extern "C" ec3r_status ec3r_align_submaps_noalloc(
                                                     state, d_pair_cost);
     else
       k_solve<<<solve_blocks, 256, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
-                                            d_out, d_pair_status, it == o.iters);
+                                            d_out, d_pair_status, it == o.iters, nullptr, it,
+                                            o.iters);
   }
   if (cudaGetLastError() != cudaSuccess) return EC3R_ERR_CUDA;
   return EC3R_OK;

@@ -1,0 +1,583 @@
+// Reverse-mode derivative (adjoint) of the batched Huber-IRLS registration.
+//
+// The forward pass (align.cu) is re-run first; its solve kernels checkpoint,
+// per pair and iteration, the 19 moments and the estimate (A = s R, b).  The
+// loss gradient then flows backwards through every iteration: the Huber
+// weights of solve k depend on estimate k-1, so each solve is differentiated
+// and the weights' dependence is carried into the previous estimate.
+//
+//   k_adj_init     per pair: upstream dL/d(s, R, t) -> pivot-relative (s, R, b)
+//   cost sweep     (dL/dcost != 0) sum om e p'^T, sum om e at the last estimate
+//   k_adj_solve    one warp per pair: back through one weighted-Umeyama solve
+//                  (covariance, polar rotation with the (d_i + d_j) form,
+//                  scale, translation) to the gradient of its moments
+//   reduce sweep   per point: the moments' gradient gives dL/d omega_i; through
+//                  h_i = min(1, delta/r_i) it gives dL/d(A, b) of the previous
+//                  estimate, reduced per pair (fixed-order FP64 partials)
+//   scatter sweep  per point, all iterations at once: dL/dp, dL/dq, dL/dc_p,
+//                  dL/dc_q of every correspondence (link layout)
+//   k_adj_frames   per pixel, links in order: accumulate into the frame bank
+//                  (deterministic: no atomics)
+#include "align_impl.cuh"
+
+namespace ec3r {
+namespace align {
+
+constexpr int NRED = 12;  // reduced values: sum g p'^T (9) + sum g (3)
+constexpr int NGM = 17;   // gradient of the moments W, Sp(3), Sq(3), Spp, Sqp(9)
+enum { G_W = 0, G_SP = 1, G_SQ = 4, G_PP = 7, G_QP = 8 };
+
+struct AdjState {
+  double gs, gR[9], gb[3];  // adjoint of the current estimate (s, R, b)
+  double gJ, gOm;           // cost = J / Om: dL/dJ and dL/dOm
+  int active;
+  int pad;
+};
+
+__device__ inline void ck_sR(const double* ck, double* s, double* R) {
+  const double* A = ck + CK_A;
+  const double sc = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+  *s = sc;
+  for (int i = 0; i < 9; ++i) R[i] = A[i] / sc;
+}
+
+__global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ckpt,
+                           const PairState* __restrict__ st, const int32_t* __restrict__ status,
+                           const double* __restrict__ cost, const double* __restrict__ gS,
+                           const double* __restrict__ gcost, AdjState* __restrict__ adj) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_pairs) return;
+  AdjState& a = adj[k];
+  a.active = (status[k] == 0 && st[k].active) ? 1 : 0;
+  a.gs = 0.0;
+  for (int i = 0; i < 9; ++i) a.gR[i] = 0.0;
+  for (int i = 0; i < 3; ++i) a.gb[i] = 0.0;
+  a.gJ = a.gOm = 0.0;
+  if (!a.active) return;
+  const double* ck = ckpt + ((size_t)k * iters + (iters - 1)) * CKPT;
+  double s, R[9];
+  ck_sR(ck, &s, R);
+  const double pp[3] = {st[k].piv_p[0], st[k].piv_p[1], st[k].piv_p[2]};
+  const double* g = gS + (size_t)k * 13;
+  // t = b + piv_q - s R piv_p
+  double Rp[3];
+  for (int i = 0; i < 3; ++i) Rp[i] = R[3 * i] * pp[0] + R[3 * i + 1] * pp[1] + R[3 * i + 2] * pp[2];
+  a.gs = g[0] - (g[10] * Rp[0] + g[11] * Rp[1] + g[12] * Rp[2]);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) a.gR[3 * i + j] = g[1 + 3 * i + j] - s * g[10 + i] * pp[j];
+  for (int i = 0; i < 3; ++i) a.gb[i] = g[10 + i];
+  if (gcost) {
+    const double W = ck[CK_MOM + M_W];
+    a.gJ = gcost[k] / W;
+    a.gOm = -gcost[k] * cost[k] / W;
+  }
+}
+
+// Per-pair data a sweep needs, staged in shared memory as float.
+struct SweepPair {
+  float pp[3], pq[3];
+  float cmin, delta;
+  int active;
+};
+
+// Reduction sweeps.  KIND 0: cost (om at S_{K-1}, e at S_K);  KIND 1: Huber
+// path of iteration k (S_{k-1} and the moments' gradient of k).
+template <int KIND, bool VEC>
+__global__ void __launch_bounds__(THREADS, 2) k_adj_reduce(
+    const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
+    const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
+    const int32_t* __restrict__ link_pair, const PairState* __restrict__ st,
+    const AdjState* __restrict__ adj, const double* __restrict__ ckpt,
+    const double* __restrict__ gM, int iters, int k_it, float delta, int rule,
+    double* __restrict__ partials) {
+  const int64_t t = blockIdx.x;
+  const int64_t l = t / tpl;
+  const int c = (int)(t - l * tpl);
+  const int k = link_pair[l];
+  if (k < 0) return;
+  if (!adj[k].active) return;
+  // estimates: "prev" = S_{k_it-1} (weights), "cur" = S_{k_it} (cost residual)
+  float Ap[9], bp[3], Ac[9], bc[3], G[NGM];
+  const double* ckb = ckpt + (size_t)k * iters * CKPT;
+  const bool first = k_it == 1;
+  for (int i = 0; i < 9; ++i) {
+    Ap[i] = first ? ((i % 4 == 0) ? 1.f : 0.f) : (float)ckb[(k_it - 2) * CKPT + CK_A + i];
+    Ac[i] = (float)ckb[(k_it - 1) * CKPT + CK_A + i];
+  }
+  for (int i = 0; i < 3; ++i) {
+    bp[i] = first ? 0.f : (float)ckb[(k_it - 2) * CKPT + CK_B + i];
+    bc[i] = (float)ckb[(k_it - 1) * CKPT + CK_B + i];
+  }
+  for (int i = 0; i < NGM; ++i)
+    G[i] = KIND == 1 ? (float)gM[((size_t)k * iters + (k_it - 1)) * NGM + i] : 0.f;
+  const float gJ = (float)adj[k].gJ, gOm = (float)adj[k].gOm;
+  const bool lastk = k_it == iters;
+  const float pp0 = st[k].piv_p[0], pp1 = st[k].piv_p[1], pp2 = st[k].piv_p[2];
+  const float pq0 = st[k].piv_q[0], pq1 = st[k].piv_q[1], pq2 = st[k].piv_q[2];
+  const float cmin = st[k].cmin;
+  const float dl = first ? FLT_MAX : delta;
+
+  const int64_t fs = src[l], ft = tgt[l];
+  const int64_t px0 = (int64_t)c * TILE;
+  const float* P = xyz + (fs * hw + px0) * 3;
+  const float* Q = xyz + (ft * hw + px0) * 3;
+  const float* CP = conf + fs * hw + px0;
+  const float* CQ = conf + ft * hw + px0;
+  const int64_t rem = hw - px0;
+  const int npx = rem < TILE ? (int)rem : TILE;
+  float acc[NRED];
+#pragma unroll
+  for (int m = 0; m < NRED; ++m) acc[m] = 0.f;
+
+  auto point = [&](float p0, float p1, float p2, float q0, float q1, float q2, float cp,
+                   float cq) {
+    const bool v = finitef(p0) && finitef(p1) && finitef(p2) && finitef(q0) && finitef(q1) &&
+                   finitef(q2) && finitef(cp) && finitef(cq) && cp > cmin && cq > cmin;
+    if (!v) return;
+    const float x0 = p0 - pp0, x1 = p1 - pp1, x2 = p2 - pp2;
+    const float y0 = q0 - pq0, y1 = q1 - pq1, y2 = q2 - pq2;
+    const float w = rule == 0 ? cp * cq : cp;
+    const float e0 = Ap[0] * x0 + Ap[1] * x1 + Ap[2] * x2 + bp[0] - y0;
+    const float e1 = Ap[3] * x0 + Ap[4] * x1 + Ap[5] * x2 + bp[1] - y1;
+    const float e2 = Ap[6] * x0 + Ap[7] * x1 + Ap[8] * x2 + bp[2] - y2;
+    const float rr = e0 * e0 + e1 * e1 + e2 * e2;
+    const float h = fminf(1.f, dl * rsqrtf(rr));
+    const float om = w * h;
+    float g0, g1, g2;
+    if (KIND == 0) {  // g = om e(S_K)
+      const float f0 = Ac[0] * x0 + Ac[1] * x1 + Ac[2] * x2 + bc[0] - y0;
+      const float f1 = Ac[3] * x0 + Ac[4] * x1 + Ac[5] * x2 + bc[1] - y1;
+      const float f2 = Ac[6] * x0 + Ac[7] * x1 + Ac[8] * x2 + bc[2] - y2;
+      g0 = om * f0; g1 = om * f1; g2 = om * f2;
+    } else {
+      float gom = G[G_W] + G[G_SP] * x0 + G[G_SP + 1] * x1 + G[G_SP + 2] * x2 +
+                  G[G_SQ] * y0 + G[G_SQ + 1] * y1 + G[G_SQ + 2] * y2 +
+                  G[G_PP] * (x0 * x0 + x1 * x1 + x2 * x2) +
+                  y0 * (G[G_QP] * x0 + G[G_QP + 1] * x1 + G[G_QP + 2] * x2) +
+                  y1 * (G[G_QP + 3] * x0 + G[G_QP + 4] * x1 + G[G_QP + 5] * x2) +
+                  y2 * (G[G_QP + 6] * x0 + G[G_QP + 7] * x1 + G[G_QP + 8] * x2);
+      if (lastk) {
+        const float f0 = Ac[0] * x0 + Ac[1] * x1 + Ac[2] * x2 + bc[0] - y0;
+        const float f1 = Ac[3] * x0 + Ac[4] * x1 + Ac[5] * x2 + bc[1] - y1;
+        const float f2 = Ac[6] * x0 + Ac[7] * x1 + Ac[8] * x2 + bc[2] - y2;
+        gom += gJ * (f0 * f0 + f1 * f1 + f2 * f2) + gOm;
+      }
+      // h = delta / r on the outer branch: dh/de = -delta e / r^3
+      const float f = rr > dl * dl ? -(gom * w) * dl * rsqrtf(rr) / rr : 0.f;
+      g0 = f * e0; g1 = f * e1; g2 = f * e2;
+    }
+    acc[0] += g0 * x0; acc[1] += g0 * x1; acc[2] += g0 * x2;
+    acc[3] += g1 * x0; acc[4] += g1 * x1; acc[5] += g1 * x2;
+    acc[6] += g2 * x0; acc[7] += g2 * x1; acc[8] += g2 * x2;
+    acc[9] += g0; acc[10] += g1; acc[11] += g2;
+  };
+
+  for (int g = threadIdx.x; g < TILE / 4; g += THREADS) {
+    const int i0 = 4 * g;
+    if (i0 >= npx) break;
+    if (VEC && i0 + 4 <= npx) {
+      const float4* P4 = reinterpret_cast<const float4*>(P + 3 * i0);
+      const float4* Q4 = reinterpret_cast<const float4*>(Q + 3 * i0);
+      const float4 pa = __ldcs(P4), pb = __ldcs(P4 + 1), pc = __ldcs(P4 + 2);
+      const float4 qa = __ldcs(Q4), qb = __ldcs(Q4 + 1), qc = __ldcs(Q4 + 2);
+      const float4 cp = __ldcs(reinterpret_cast<const float4*>(CP + i0));
+      const float4 cq = __ldcs(reinterpret_cast<const float4*>(CQ + i0));
+      point(pa.x, pa.y, pa.z, qa.x, qa.y, qa.z, cp.x, cq.x);
+      point(pa.w, pb.x, pb.y, qa.w, qb.x, qb.y, cp.y, cq.y);
+      point(pb.z, pb.w, pc.x, qb.z, qb.w, qc.x, cp.z, cq.z);
+      point(pc.y, pc.z, pc.w, qc.y, qc.z, qc.w, cp.w, cq.w);
+    } else {
+      const int n = min(4, npx - i0);
+      for (int j = 0; j < n; ++j) {
+        const int i = i0 + j;
+        point(P[3 * i], P[3 * i + 1], P[3 * i + 2], Q[3 * i], Q[3 * i + 1], Q[3 * i + 2], CP[i],
+              CQ[i]);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NRED; ++m)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+  __shared__ double red[THREADS / 32][NRED];
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int m = 0; m < NRED; ++m) red[warp][m] = (double)acc[m];
+  __syncthreads();
+  if (threadIdx.x < NRED) {
+    double s = 0.0;
+    for (int w = 0; w < THREADS / 32; ++w) s += red[w][threadIdx.x];
+    partials[t * NRED + threadIdx.x] = s;
+  }
+}
+
+// One warp per pair.  First folds the reduced sums (scaled by `scale`: 2 dL/dJ
+// for the cost sweep, 1 for a Huber sweep) into the adjoint of estimate j as
+// dL/dA and dL/db, then differentiates solve j and stores the gradient of its
+// moments in gM[j].
+__global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j,
+                                                   const int32_t* __restrict__ link_off, int tpl,
+                                                   const double* __restrict__ partials,
+                                                   int have_partials, int scale_by_gJ,
+                                                   const double* __restrict__ ckpt,
+                                                   AdjState* __restrict__ adj,
+                                                   double* __restrict__ gM) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  __shared__ double red[8][NRED];
+  if (warp >= n_pairs) return;
+  AdjState& a = adj[warp];
+  if (!a.active) return;
+  const int wib = threadIdx.x >> 5;
+  const double* ck = ckpt + ((size_t)warp * iters + (j - 1)) * CKPT;
+  if (have_partials) {
+    const int64_t t0 = (int64_t)link_off[warp] * tpl, t1 = (int64_t)link_off[warp + 1] * tpl;
+    if (lane < NRED) {
+      double s = 0.0;
+      for (int64_t t = t0; t < t1; ++t) s += partials[t * NRED + lane];
+      red[wib][lane] = s;
+    }
+  }
+  __syncwarp();
+  if (lane != 0) return;
+  double s, R[9];
+  ck_sR(ck, &s, R);
+  if (have_partials) {
+    const double f = scale_by_gJ ? 2.0 * a.gJ : 1.0;
+    // dL/dA = f X, dL/db = f y; A = s R -> dL/ds = <dL/dA, R>, dL/dR = s dL/dA
+    double gs = 0.0;
+    for (int i = 0; i < 9; ++i) {
+      const double gA = f * red[wib][i];
+      gs += gA * R[i];
+      a.gR[i] += s * gA;
+    }
+    a.gs += gs;
+    for (int i = 0; i < 3; ++i) a.gb[i] += f * red[wib][9 + i];
+  }
+  // forward quantities of solve j from its moments
+  const double* M = ck + CK_MOM;
+  const double W = M[M_W], iw = 1.0 / W;
+  const double mp[3] = {M[M_SP] * iw, M[M_SP + 1] * iw, M[M_SP + 2] * iw};
+  const double mq[3] = {M[M_SQ] * iw, M[M_SQ + 1] * iw, M[M_SQ + 2] * iw};
+  double Sig[9];
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) Sig[3 * i + k] = M[M_QP + 3 * i + k] * iw - mq[i] * mp[k];
+  const double var = M[M_PP] * iw - (mp[0] * mp[0] + mp[1] * mp[1] + mp[2] * mp[2]);
+  double Rr[9], d[3], V[9];
+  polar_rotation(Sig, Rr, d, V);
+  double tau = 0.0;
+  for (int i = 0; i < 9; ++i) tau += Rr[i] * Sig[i];
+  // b = mq - s R mp
+  double gmq[3], gmp[3], gs = a.gs, gR[9];
+  double Rmp[3];
+  for (int i = 0; i < 3; ++i)
+    Rmp[i] = Rr[3 * i] * mp[0] + Rr[3 * i + 1] * mp[1] + Rr[3 * i + 2] * mp[2];
+  for (int i = 0; i < 3; ++i) {
+    gmq[i] = a.gb[i];
+    gs -= a.gb[i] * Rmp[i];
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) gR[3 * i + k] = a.gR[3 * i + k] - s * a.gb[i] * mp[k];
+  for (int k = 0; k < 3; ++k)
+    gmp[k] = -s * (Rr[k] * a.gb[0] + Rr[3 + k] * a.gb[1] + Rr[6 + k] * a.gb[2]);
+  // s = tau / var, d tau / dSig = R
+  const double gtau = gs / var;
+  const double gvar = -gs * tau / (var * var);
+  double gSig[9];
+  for (int i = 0; i < 9; ++i) gSig[i] = gtau * Rr[i];
+  // R = U' V^T, U' = R V: dL/dSig += U' K V^T, K_ab = (G'_ab - G'_ba) / (d_a + d_b)
+  double U[9], G1[9], G2[9], Kx[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      U[3 * r + c] = Rr[3 * r] * V[c] + Rr[3 * r + 1] * V[3 + c] + Rr[3 * r + 2] * V[6 + c];
+  for (int r = 0; r < 3; ++r)  // G1 = U^T gR
+    for (int c = 0; c < 3; ++c)
+      G1[3 * r + c] = U[r] * gR[c] + U[3 + r] * gR[3 + c] + U[6 + r] * gR[6 + c];
+  for (int r = 0; r < 3; ++r)  // G2 = G1 V
+    for (int c = 0; c < 3; ++c)
+      G2[3 * r + c] = G1[3 * r] * V[c] + G1[3 * r + 1] * V[3 + c] + G1[3 * r + 2] * V[6 + c];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      Kx[3 * r + c] = r == c ? 0.0 : (G2[3 * r + c] - G2[3 * c + r]) / (d[r] + d[c]);
+  for (int r = 0; r < 3; ++r)  // G1 = U K
+    for (int c = 0; c < 3; ++c)
+      G1[3 * r + c] = U[3 * r] * Kx[c] + U[3 * r + 1] * Kx[3 + c] + U[3 * r + 2] * Kx[6 + c];
+  for (int r = 0; r < 3; ++r)  // += G1 V^T
+    for (int c = 0; c < 3; ++c)
+      gSig[3 * r + c] += G1[3 * r] * V[3 * c] + G1[3 * r + 1] * V[3 * c + 1] +
+                         G1[3 * r + 2] * V[3 * c + 2];
+  // Sig = Sqp/W - mq mp^T, var = Spp/W - |mp|^2, mp = Sp/W, mq = Sq/W
+  double* out = gM + ((size_t)warp * iters + (j - 1)) * NGM;
+  double gW = 0.0;
+  for (int i = 0; i < 9; ++i) {
+    out[G_QP + i] = gSig[i] * iw;
+    gW -= gSig[i] * M[M_QP + i] * iw * iw;
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) {
+      gmq[i] -= gSig[3 * i + k] * mp[k];
+      gmp[k] -= gSig[3 * i + k] * mq[i];
+    }
+  out[G_PP] = gvar * iw;
+  gW -= gvar * M[M_PP] * iw * iw;
+  for (int k = 0; k < 3; ++k) gmp[k] -= 2.0 * gvar * mp[k];
+  for (int k = 0; k < 3; ++k) {
+    out[G_SP + k] = gmp[k] * iw;
+    out[G_SQ + k] = gmq[k] * iw;
+    gW -= (gmp[k] * M[M_SP + k] + gmq[k] * M[M_SQ + k]) * iw * iw;
+  }
+  out[G_W] = gW;
+  // the adjoint of estimate j-1 is rebuilt by the next Huber sweep
+  a.gs = 0.0;
+  for (int i = 0; i < 9; ++i) a.gR[i] = 0.0;
+  for (int i = 0; i < 3; ++i) a.gb[i] = 0.0;
+}
+
+// Per-correspondence gradients, all iterations in one pass (link layout,
+// 8 floats per pixel: dp(3), dq(3), dc_p, dc_q).
+template <bool VEC>
+__global__ void __launch_bounds__(THREADS) k_adj_scatter(
+    const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
+    const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
+    const int32_t* __restrict__ link_pair, const PairState* __restrict__ st,
+    const AdjState* __restrict__ adj, const double* __restrict__ ckpt,
+    const double* __restrict__ gM, int iters, float delta, int rule, float* __restrict__ lg) {
+  const int64_t t = blockIdx.x;
+  const int64_t l = t / tpl;
+  const int c = (int)(t - l * tpl);
+  const int k = link_pair[l];
+  const int64_t px0 = (int64_t)c * TILE;
+  const int64_t rem = hw - px0;
+  const int npx = rem < TILE ? (int)rem : TILE;
+  float* out = lg + (l * hw + px0) * 8;
+  const bool active = k >= 0 && adj[k].active;
+  if (!active) {
+    for (int i = threadIdx.x; i < npx * 8; i += THREADS) out[i] = 0.f;
+    return;
+  }
+  extern __shared__ float sh[];  // per iteration: A(9) b(3) gM(17)
+  constexpr int PER = 29;
+  const double* ckb = ckpt + (size_t)k * iters * CKPT;
+  for (int i = threadIdx.x; i < iters * PER; i += THREADS) {
+    const int it = i / PER, f = i % PER;
+    float v;
+    if (f < 9) v = (float)ckb[it * CKPT + CK_A + f];
+    else if (f < 12) v = (float)ckb[it * CKPT + CK_B + (f - 9)];
+    else v = (float)gM[((size_t)k * iters + it) * NGM + (f - 12)];
+    sh[i] = v;
+  }
+  __syncthreads();
+  const float gJ = (float)adj[k].gJ, gOm = (float)adj[k].gOm;
+  const float pp0 = st[k].piv_p[0], pp1 = st[k].piv_p[1], pp2 = st[k].piv_p[2];
+  const float pq0 = st[k].piv_q[0], pq1 = st[k].piv_q[1], pq2 = st[k].piv_q[2];
+  const float cmin = st[k].cmin;
+  const int64_t fs = src[l], ft = tgt[l];
+  const float* P = xyz + (fs * hw + px0) * 3;
+  const float* Q = xyz + (ft * hw + px0) * 3;
+  const float* CP = conf + fs * hw + px0;
+  const float* CQ = conf + ft * hw + px0;
+  for (int i = threadIdx.x; i < npx; i += THREADS) {
+    const float p0 = P[3 * i], p1 = P[3 * i + 1], p2 = P[3 * i + 2];
+    const float q0 = Q[3 * i], q1 = Q[3 * i + 1], q2 = Q[3 * i + 2];
+    const float cp = CP[i], cq = CQ[i];
+    const bool v = finitef(p0) && finitef(p1) && finitef(p2) && finitef(q0) && finitef(q1) &&
+                   finitef(q2) && finitef(cp) && finitef(cq) && cp > cmin && cq > cmin;
+    float gp[3] = {0.f, 0.f, 0.f}, gq[3] = {0.f, 0.f, 0.f}, gw = 0.f;
+    if (v) {
+      const float x[3] = {p0 - pp0, p1 - pp1, p2 - pp2};
+      const float y[3] = {q0 - pq0, q1 - pq1, q2 - pq2};
+      const float w = rule == 0 ? cp * cq : cp;
+      for (int it = 1; it <= iters; ++it) {
+        const float* G = sh + (it - 1) * PER + 12;
+        float h = 1.f, e[3] = {0.f, 0.f, 0.f}, rr = 0.f;
+        const float* Ap = sh + (it - 2) * PER;
+        if (it > 1) {
+          for (int r = 0; r < 3; ++r)
+            e[r] = Ap[3 * r] * x[0] + Ap[3 * r + 1] * x[1] + Ap[3 * r + 2] * x[2] + Ap[9 + r] - y[r];
+          rr = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+          h = fminf(1.f, delta * rsqrtf(rr));
+        }
+        const float om = w * h;
+        float gom = G[G_W] + G[G_PP] * (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (int r = 0; r < 3; ++r) {
+          const float Gx = G[G_QP + 3 * r] * x[0] + G[G_QP + 3 * r + 1] * x[1] + G[G_QP + 3 * r + 2] * x[2];
+          gom += G[G_SP + r] * x[r] + G[G_SQ + r] * y[r] + y[r] * Gx;
+          // direct: dL/dq' += om (gSq + gSqp x)
+          gq[r] += om * (G[G_SQ + r] + Gx);
+        }
+        for (int cc = 0; cc < 3; ++cc) {
+          // dL/dp' += om (gSp + 2 gSpp x + gSqp^T y)
+          const float Gy = G[G_QP + cc] * y[0] + G[G_QP + 3 + cc] * y[1] + G[G_QP + 6 + cc] * y[2];
+          gp[cc] += om * (G[G_SP + cc] + 2.f * G[G_PP] * x[cc] + Gy);
+        }
+        if (it == iters) {
+          const float* Ac = sh + (it - 1) * PER;
+          float f[3];
+          for (int r = 0; r < 3; ++r)
+            f[r] = Ac[3 * r] * x[0] + Ac[3 * r + 1] * x[1] + Ac[3 * r + 2] * x[2] + Ac[9 + r] - y[r];
+          gom += gJ * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) + gOm;
+          // cost residual: dL/de = 2 gJ om e
+          for (int r = 0; r < 3; ++r) {
+            const float ge = 2.f * gJ * om * f[r];
+            gq[r] -= ge;
+            for (int cc = 0; cc < 3; ++cc) gp[cc] += Ac[3 * r + cc] * ge;
+          }
+        }
+        gw += gom * h;
+        if (it > 1 && rr > delta * delta) {
+          const float fct = -(gom * w) * delta * rsqrtf(rr) / rr;
+          for (int r = 0; r < 3; ++r) {
+            const float ge = fct * e[r];
+            gq[r] -= ge;
+            for (int cc = 0; cc < 3; ++cc) gp[cc] += Ap[3 * r + cc] * ge;
+          }
+        }
+      }
+    }
+    float* o = out + (size_t)i * 8;
+    o[0] = gp[0]; o[1] = gp[1]; o[2] = gp[2];
+    o[3] = gq[0]; o[4] = gq[1]; o[5] = gq[2];
+    o[6] = v ? (rule == 0 ? gw * cq : gw) : 0.f;
+    o[7] = v ? (rule == 0 ? gw * cp : 0.f) : 0.f;
+  }
+}
+
+// Frame-bank gradients: one thread per pixel index, links in order.
+__global__ void k_adj_frames(int64_t hw, int64_t n_links, const int32_t* __restrict__ src,
+                             const int32_t* __restrict__ tgt,
+                             const int32_t* __restrict__ link_pair, const float* __restrict__ lg,
+                             float* __restrict__ gxyz, float* __restrict__ gconf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= hw) return;
+  for (int64_t l = 0; l < n_links; ++l) {
+    if (link_pair[l] < 0) continue;
+    const float* g = lg + (l * hw + i) * 8;
+    const int64_t a = src[l], b = tgt[l];
+    float* ga = gxyz + (a * hw + i) * 3;
+    float* gb = gxyz + (b * hw + i) * 3;
+    ga[0] += g[0]; ga[1] += g[1]; ga[2] += g[2];
+    gb[0] += g[3]; gb[1] += g[4]; gb[2] += g[5];
+    gconf[a * hw + i] += g[6];
+    gconf[b * hw + i] += g[7];
+  }
+}
+
+}  // namespace align
+}  // namespace ec3r
+
+using namespace ec3r;
+using namespace ec3r::align;
+
+extern "C" ec3r_status ec3r_align_submaps_backward(
+    ec3r_ctx* ctx, const float* d_xyz, const float* d_conf, int64_t n_frames, int64_t hw,
+    int n_pairs, int64_t n_links, const int32_t* d_link_off, const int32_t* d_src,
+    const int32_t* d_tgt, const float* d_pair_conf_min, const ec3r_align_opts* opts,
+    const double* d_grad_S, const double* d_grad_cost, float* d_grad_xyz, float* d_grad_conf,
+    void* stream) {
+  if (!ctx) return EC3R_ERR_INVALID_ARG;
+  if (!opts || !d_grad_S || !d_grad_xyz || !d_grad_conf)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
+  if (opts->precision != EC3R_PREC_FP32C)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "the backward pass supports FP32 moments only");
+  if (n_pairs <= 0) return n_pairs == 0 ? EC3R_OK : EC3R_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // forward re-run with checkpoints and the cost
+  void *p_out, *p_st, *p_cost;
+  ec3r_status st;
+  if ((st = ensure_buf(ctx, "adj.out", sizeof(ec3r_sim3) * (size_t)n_pairs, s, &p_out))) return st;
+  if ((st = ensure_buf(ctx, "adj.status", sizeof(int32_t) * (size_t)n_pairs, s, &p_st))) return st;
+  if ((st = ensure_buf(ctx, "adj.cost", sizeof(double) * (size_t)n_pairs, s, &p_cost))) return st;
+  ec3r_align_opts fo = *opts;
+  fo.want_cost = 1;
+  if ((st = ec3r_align_submaps(ctx, d_xyz, d_conf, n_frames, hw, n_pairs, n_links, d_link_off,
+                               d_src, d_tgt, d_pair_conf_min, &fo, (ec3r_sim3*)p_out,
+                               (int32_t*)p_st, (double*)p_cost, stream)))
+    return st;
+  const int iters = opts->iters;
+  const int64_t tpl = (hw + TILE - 1) / TILE;
+  const int64_t n_tiles = n_links * tpl;
+  void *p_adj, *p_gm, *p_part, *p_lg;
+  if ((st = ensure_buf(ctx, "adj.state", sizeof(AdjState) * (size_t)n_pairs, s, &p_adj))) return st;
+  if ((st = ensure_buf(ctx, "adj.gM", sizeof(double) * NGM * (size_t)n_pairs * iters, s, &p_gm)))
+    return st;
+  if ((st = ensure_buf(ctx, "adj.partials", sizeof(double) * NRED * (size_t)(n_tiles + 1), s,
+                       &p_part)))
+    return st;
+  if ((st = ensure_buf(ctx, "adj.link_grads", sizeof(float) * 8 * (size_t)(n_links * hw + 1), s,
+                       &p_lg)))
+    return st;
+  // pointers of the forward workspace (stable: the forward call above sized them)
+  PairState* state = (PairState*)ctx->bufs["align.state"].ptr;
+  double* ckpt = (double*)ctx->bufs["align.ckpt"].ptr;
+  int32_t* link_pair = (int32_t*)ctx->bufs["align.link_pair"].ptr;
+  AdjState* adj = (AdjState*)p_adj;
+  double* gM = (double*)p_gm;
+  double* part = (double*)p_part;
+  float* lg = (float*)p_lg;
+  const bool vec =
+      (hw % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0) && ((uintptr_t)d_conf % 16 == 0);
+  const float delta = opts->huber_delta;
+  const int rule = opts->weight_rule;
+  const dim3 grid((unsigned)(n_tiles > 0 ? n_tiles : 1));
+  const int solve_blocks = (n_pairs + 7) / 8;
+  traced(ctx, s, "adj_init", [&] {
+    k_adj_init<<<(n_pairs + 127) / 128, 128, 0, s>>>(n_pairs, iters, ckpt, state,
+                                                    (const int32_t*)p_st, (const double*)p_cost,
+                                                    d_grad_S, d_grad_cost, adj);
+  });
+  const bool cost_path = d_grad_cost != nullptr;
+  if (cost_path && n_tiles > 0)
+    traced(ctx, s, "adj_reduce", [&] {
+      if (vec)
+        k_adj_reduce<0, true><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt,
+                                                       link_pair, state, adj, ckpt, gM, iters,
+                                                       iters, delta, rule, part);
+      else
+        k_adj_reduce<0, false><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src,
+                                                        d_tgt, link_pair, state, adj, ckpt, gM,
+                                                        iters, iters, delta, rule, part);
+    });
+  traced(ctx, s, "adj_solve", [&] {
+    k_adj_solve<<<solve_blocks, 256, 0, s>>>(n_pairs, iters, iters, d_link_off, (int)tpl, part,
+                                             cost_path && n_tiles > 0, 1, ckpt, adj, gM);
+  });
+  for (int k = iters; k >= 2; --k) {
+    if (n_tiles > 0)
+      traced(ctx, s, "adj_reduce", [&] {
+        if (vec)
+          k_adj_reduce<1, true><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src,
+                                                         d_tgt, link_pair, state, adj, ckpt, gM,
+                                                         iters, k, delta, rule, part);
+        else
+          k_adj_reduce<1, false><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src,
+                                                          d_tgt, link_pair, state, adj, ckpt, gM,
+                                                          iters, k, delta, rule, part);
+      });
+    traced(ctx, s, "adj_solve", [&] {
+      k_adj_solve<<<solve_blocks, 256, 0, s>>>(n_pairs, iters, k - 1, d_link_off, (int)tpl, part,
+                                               n_tiles > 0, 0, ckpt, adj, gM);
+    });
+  }
+  EC3R_CUDA_TRY(ctx, cudaMemsetAsync(d_grad_xyz, 0, sizeof(float) * 3 * (size_t)(n_frames * hw), s));
+  EC3R_CUDA_TRY(ctx, cudaMemsetAsync(d_grad_conf, 0, sizeof(float) * (size_t)(n_frames * hw), s));
+  if (n_tiles > 0) {
+    const size_t shm = sizeof(float) * 29 * (size_t)iters;
+    traced(ctx, s, "adj_scatter", [&] {
+      if (vec)
+        k_adj_scatter<true><<<grid, THREADS, shm, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt,
+                                                       link_pair, state, adj, ckpt, gM, iters,
+                                                       delta, rule, lg);
+      else
+        k_adj_scatter<false><<<grid, THREADS, shm, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src,
+                                                        d_tgt, link_pair, state, adj, ckpt, gM,
+                                                        iters, delta, rule, lg);
+    });
+    traced(ctx, s, "adj_frames", [&] {
+      k_adj_frames<<<(unsigned)((hw + 255) / 256), 256, 0, s>>>(hw, n_links, d_src, d_tgt,
+                                                                link_pair, lg, d_grad_xyz,
+                                                                d_grad_conf);
+    });
+  }
+  EC3R_CUDA_TRY(ctx, cudaGetLastError());
+  return EC3R_OK;
+}

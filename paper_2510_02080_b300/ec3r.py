@@ -27,7 +27,8 @@ RULE = {"product": 0, "src": 1}
 EXPORTS = ("ec3r_create", "ec3r_destroy", "ec3r_last_error", "ec3r_status_string",
            "ec3r_version", "ec3r_sync_status", "ec3r_align_opts_default",
            "ec3r_align_submaps", "ec3r_fuse_points", "ec3r_profile", "ec3r_profile_read",
-           "ec3r_align_submaps_noalloc", "ec3r_pg_opts_default", "ec3r_pose_graph_correct")
+           "ec3r_align_submaps_noalloc", "ec3r_pg_opts_default", "ec3r_pose_graph_correct",
+           "ec3r_align_submaps_backward")
 
 
 class Sim3(C.Structure):
@@ -74,12 +75,15 @@ def _declare(l):
     l.ec3r_profile.argtypes = [_P, C.c_int]
     l.ec3r_profile_read.argtypes = [_P, C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int64), C.POINTER(C.c_int)]
+    l.ec3r_align_submaps_backward.argtypes = [_P, _P, _P, _I64, _I64, C.c_int, _I64, _P, _P, _P,
+                                              _P, C.POINTER(AlignOpts), _P, _P, _P, _P, _P]
     l.ec3r_pg_opts_default.argtypes = [C.POINTER(PgOpts)]
     l.ec3r_pg_opts_default.restype = None
     l.ec3r_pose_graph_correct.argtypes = [_P, C.c_int, _P, C.c_int, _P, _P, _P, _P,
                                           C.POINTER(PgOpts), _P, _P]
     for name in ("ec3r_create", "ec3r_sync_status", "ec3r_align_submaps", "ec3r_fuse_points",
-                 "ec3r_profile", "ec3r_profile_read", "ec3r_pose_graph_correct"):
+                 "ec3r_profile", "ec3r_profile_read", "ec3r_pose_graph_correct",
+                 "ec3r_align_submaps_backward"):
         getattr(l, name).restype = C.c_int
 
 
@@ -192,6 +196,23 @@ class Context:
         self._check(st)
         return out, status, (cost if want_cost else None)
 
+    def align_submaps_backward(self, xyz, conf, link_off, src, tgt, grad_S, grad_cost=None,
+                               pair_conf_min=None, *, delta=0.02, iters=10, conf_min=0.0,
+                               rule="product", stream=None):
+        """Gradients (dL/dxyz [n_frames,hw,3], dL/dconf [n_frames,hw]) of the registration."""
+        n_frames, hw = int(conf.shape[0]), int(conf.shape[1])
+        n_pairs = int(link_off.numel()) - 1
+        gx = torch.empty_like(xyz)
+        gc = torch.empty_like(conf)
+        o = AlignOpts(float(delta), int(iters), float(conf_min), RULE[rule], PREC["fp32c"], 1)
+        st = self._lib.ec3r_align_submaps_backward(
+            self._h, _ptr(xyz), _ptr(conf), n_frames, hw, n_pairs, int(src.numel()),
+            _ptr(link_off), _ptr(src), _ptr(tgt), _ptr(pair_conf_min), C.byref(o),
+            _ptr(grad_S.contiguous()), _ptr(None if grad_cost is None else grad_cost.contiguous()),
+            _ptr(gx), _ptr(gc), _stream(stream))
+        self._check(st)
+        return gx, gc
+
     # -- pose graph --------------------------------------------------------
     def pose_graph_correct(self, nodes, ei, ej, Tij, info=None, *, iters=10, fixed=0,
                            lm_lambda=0.0, init=True, chi2=None, stream=None):
@@ -238,3 +259,35 @@ def sim3_row(row):
 def sim3_rows(S, R, t):
     """Pack float64 tensors s [n], R [n,3,3], t [n,3] into [n,13] rows."""
     return torch.cat([S.reshape(-1, 1), R.reshape(-1, 9), t.reshape(-1, 3)], 1).contiguous()
+
+
+class EC3RAlign(torch.autograd.Function):
+    """Differentiable batched registration: (xyz, conf) -> (S [n,13], cost [n]).
+
+    ``EC3RAlign.apply(ctx, xyz, conf, link_off, src, tgt, pair_conf_min, delta, iters,
+    conf_min, rule)``; the backward pass is the library's adjoint
+    (``ec3r_align_submaps_backward``).
+    """
+
+    @staticmethod
+    def forward(fctx, ctx, xyz, conf, link_off, src, tgt, pair_conf_min=None, delta=0.02,
+                iters=10, conf_min=0.0, rule="product"):
+        S, status, cost = ctx.align_submaps(xyz, conf, link_off, src, tgt, pair_conf_min,
+                                            delta=delta, iters=iters, conf_min=conf_min,
+                                            rule=rule, want_cost=True)
+        fctx.save_for_backward(xyz, conf, link_off, src, tgt)
+        fctx.ec3r = (ctx, pair_conf_min, delta, iters, conf_min, rule)
+        fctx.mark_non_differentiable(status)
+        return S, cost, status
+
+    @staticmethod
+    def backward(fctx, gS, gcost, _gstatus):
+        xyz, conf, link_off, src, tgt = fctx.saved_tensors
+        ctx, pcm, delta, iters, conf_min, rule = fctx.ec3r
+        if gS is None:
+            gS = torch.zeros((int(link_off.numel()) - 1, 13), dtype=torch.float64,
+                             device=xyz.device)
+        gx, gc = ctx.align_submaps_backward(xyz, conf, link_off, src, tgt,
+                                            gS.to(torch.float64), gcost, pcm, delta=delta,
+                                            iters=iters, conf_min=conf_min, rule=rule)
+        return None, gx, gc, None, None, None, None, None, None, None, None

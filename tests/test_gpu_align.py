@@ -41,6 +41,8 @@ def check_against_oracle(ps_cpu, S, st, cost, delta=0.02, iters=10, conf_min=0.0
         assert int(st[k]) == r["status"], (k, int(st[k]), r["status"])
         if r["status"] == 0:
             assert_sim3_close(S[k], r["S"], r["extent"], f"pair {k}")
+            Rg = S[k][1:10].reshape(3, 3)
+            assert np.abs(Rg.T @ Rg - np.eye(3)).max() < 1e-14 and abs(np.linalg.det(Rg) - 1) < 1e-14
             if cost is not None:
                 assert abs(cost[k] - r["cost"]) <= 1e-5 * r["cost"] + 1e-12, (k, cost[k], r["cost"])
         else:
