@@ -8,7 +8,8 @@ registration of the 199 consecutive pairs (10 solves, FP32 moments, FP64
 solve), the FP64 Sim(3) pose graph over the 200 submaps with the 199
 registered edges (chaining + 10 Gauss-Newton iterations), and the
 confidence > 1 compaction + global transform of all 152,292,000 points under
-the corrected poses.
+the corrected poses, then the adjoint of the registration for a fixed
+synthetic upstream gradient (the backward pass of a training step).
 
 Metric: Sim(3)-registered points per second per IRLS iteration
 (valid correspondences x iterations / step time), whole job over all ranks.
@@ -206,18 +207,36 @@ def run_ours(args):
     poses[:, 0] = 1.0
     poses[:, [1, 5, 9]] = 1.0          # identity; node 0 stays fixed (world = submap 0)
     chi2 = torch.empty((PG_ITERS + 1,), dtype=torch.float64, device=dev)
-    n_cursor = args.steps + args.warmup + 8
+    n_cursor = 2 * args.steps + args.warmup + 8
     cursors = torch.zeros((n_cursor,), dtype=torch.int64, device=dev)
     ci = [0]
 
+    # adjoint: a fixed synthetic upstream gradient dL/dS, dL/dcost per pair
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    gS = torch.randn((ps.n_pairs, 13), generator=gen, dtype=torch.float64, device=dev)
+    gcost = torch.ones((ps.n_pairs,), dtype=torch.float64, device=dev)
+    cost = torch.empty((ps.n_pairs,), dtype=torch.float64, device=dev)
+    gxyz = torch.empty((n_frames, hw, 3), dtype=torch.float32, device=dev)
+    gconf = torch.empty((n_frames, hw), dtype=torch.float32, device=dev)
+
     def step(xyz_in, conf_in):
         ctx.align_submaps(xyz_in.view(n_frames, hw, 3), conf_in.view(n_frames, hw), ps.link_off,
-                          ps.src, ps.tgt, delta=DELTA, iters=ITERS, out=S, status=st)
+                          ps.src, ps.tgt, delta=DELTA, iters=ITERS, out=S, status=st,
+                          want_cost=True, cost=cost)
         ctx.pose_graph_correct(poses, ei, ej, S, iters=PG_ITERS, chi2=chi2)
         c = cursors[ci[0] % n_cursor:ci[0] % n_cursor + 1]
         ci[0] += 1
         ctx.fuse_points(xyz_in.view(M, -1, 3), conf_in.view(M, -1), poses,
                         out_xyz, out_idx, c)
+        if not args.no_adjoint:
+            lib = ec3r.lib()
+            o = ec3r.AlignOpts(DELTA, ITERS, 0.0, 0, 0, 1)
+            ctx._check(lib.ec3r_align_submaps_backward(
+                ctx._h, ec3r._ptr(xyz_in), ec3r._ptr(conf_in), n_frames, hw, ps.n_pairs,
+                int(ps.src.numel()), ec3r._ptr(ps.link_off), ec3r._ptr(ps.src),
+                ec3r._ptr(ps.tgt), None, ec3r.C.byref(o), ec3r._ptr(gS), ec3r._ptr(gcost),
+                ec3r._ptr(gxyz), ec3r._ptr(gconf), ec3r._stream(None)))
 
     for _ in range(args.warmup):
         step(ch.xyz, ch.conf)
@@ -230,9 +249,8 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    # ---- timed region: inputs resident in HBM --------------------------------
-    ctx.profile(True)
-    ctx.profile_read()
+    # ---- timed region: inputs resident in HBM, every call replayed from its
+    # cached CUDA graph ------------------------------------------------------
     clocks = Clocks(local)
     clocks.start()
     barrier()
@@ -247,6 +265,19 @@ def run_ours(args):
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    assert ctx.sync_status() == 0, ctx.last_error()
+    # ---- the same K steps again with every kernel bracketed by CUDA events on
+    # its launching stream (direct launches): per-kernel durations ------------
+    ctx.profile(True)
+    ctx.profile_read()
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(s)
+    for _ in range(args.steps):
+        step(ch.xyz, ch.conf)
+    p1.record(s)
+    torch.cuda.synchronize()
+    ms_profiled = p0.elapsed_time(p1)
     prof = ctx.profile_read()
     ctx.profile(False)
     assert ctx.sync_status() == 0, ctx.last_error()
@@ -306,6 +337,9 @@ def run_ours(args):
                    "share": v[0] / total_prof if total_prof else None} for k, v in prof.items()}
     fuse_ms = sum(prof.get(k, (0.0, 0))[0] for k in ("fuse_count", "fuse_scan", "fuse_scatter"))
     pg_ms = sum(v[0] for k, v in prof.items() if k.startswith("pg_"))
+    adj_ms = sum(v[0] for k, v in prof.items() if k.startswith("adj_"))
+    reg_ms = sum(prof.get(k, (0.0, 0))[0] for k in ("align_setup", "irls_sweep_fp32",
+                                                       "sim3_solve", "irls_cost"))
     fuse_gbs = 26.0 * n_fuse * args.steps / (fuse_ms * 1e-3) / 1e9 if fuse_ms else None
 
     cpu_rate, n_cpu, dt_cpu, np_cpu = (None, 0, 0.0, 0)
@@ -321,7 +355,8 @@ def run_ours(args):
                    "iters": ITERS, "huber_delta": DELTA, "precision": "fp32 moments, fp64 solve",
                    "fused_points": n_fuse, "kept_points": kept,
                    "pose_graph": {"nodes": M, "edges": ps.n_pairs, "gn_iters": PG_ITERS},
-                   "rows": ["registration", "pose graph", "fusion"],
+                   "rows": ["registration", "pose graph", "fusion"] +
+                           ([] if args.no_adjoint else ["adjoint"]),
                    "l2": "inputs 2.4 GB per rank > 126 MB L2; no flush"},
         "roofline": {"bound": "hbm", "kernel": "irls_sweep_fp32", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -331,8 +366,14 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": sweep_bytes,
                      "launch_ms": sweep_ms},
         "kernels": kernels,
+        "profiled_pass": {"ms_per_step": ms_profiled / args.steps,
+                          "note": "same K steps, direct launches, an event pair per kernel"},
         "fusion": {"ms_per_step": fuse_ms / args.steps, "gbs_at_26B_per_point": fuse_gbs},
         "pose_graph": {"ms_per_step": pg_ms / args.steps},
+        "adjoint": {"ms_per_step": adj_ms / args.steps},
+        "registration": {"ms_per_step": reg_ms / args.steps,
+                         "pt_iter_per_s": n_valid * ITERS * args.steps / (reg_ms * 1e-3)
+                         if reg_ms else None},
         "clocks": clk,
         "gpu_launches": int(sum(v[1] for v in prof.values())),
     }
@@ -357,6 +398,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="leave the adjoint out of the step (profiling only)")
     ap.add_argument("--submaps", type=int, default=M_SUBMAPS,
                     help="chain length (default 200); smaller values are for profiling only")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)

@@ -178,9 +178,12 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
  * in link order (deterministic).  Invalid correspondences and degenerate pairs
  * get zero.
  *
- * The call re-runs the forward pass with per-iteration checkpoints (estimate
- * and moments of every solve), so it needs no state from an earlier call; it
- * then differentiates all `iters` solves, unrolled (the Huber weights of
+ * Checkpoints.  The forward call keeps, in its context, the estimate and the
+ * moments of every solve.  If the last ec3r_align_submaps call on this context
+ * had exactly these inputs and options with want_cost = 1, and its outputs
+ * (d_out, d_pair_status, d_pair_cost) are still unchanged, the backward call
+ * uses those checkpoints; otherwise it first re-runs the forward pass itself.
+ * It then differentiates all `iters` solves, unrolled (the Huber weights of
  * solve k depend on solve k-1): one reduction sweep per iteration and one
  * final sweep that writes the per-point gradients.  The rotation is
  * differentiated in its polar form, with 1/(d_i + d_j) factors.  The Huber

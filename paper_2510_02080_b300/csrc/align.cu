@@ -475,6 +475,16 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
                 (uint64_t)o.iters, fbits(o.conf_min), (uint64_t)o.weight_rule,
                 (uint64_t)o.precision, (uint64_t)o.want_cost, (uint64_t)d_out,
                 (uint64_t)d_pair_status, (uint64_t)d_pair_cost});
+  // remember this call: a backward call with the same inputs reuses its checkpoints
+  ctx->align_key = key_of("fwd", {(uint64_t)d_xyz, (uint64_t)d_conf, (uint64_t)n_frames,
+                                  (uint64_t)hw, (uint64_t)n_pairs, (uint64_t)n_links,
+                                  (uint64_t)d_link_off, (uint64_t)d_src, (uint64_t)d_tgt,
+                                  (uint64_t)d_pair_conf_min, fbits(o.huber_delta),
+                                  (uint64_t)o.iters, fbits(o.conf_min), (uint64_t)o.weight_rule,
+                                  (uint64_t)o.precision, (uint64_t)o.want_cost});
+  ctx->align_out = d_out;
+  ctx->align_status = d_pair_status;
+  ctx->align_cost = d_pair_cost;
   return run_graph(ctx, key, s, [&](cudaStream_t cs) -> ec3r_status {
     EC3R_CUDA_TRY(ctx, cudaMemsetAsync(link_pair, 0xff, sizeof(int32_t) * (size_t)(n_links + 1),
                                        cs));
@@ -483,7 +493,7 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
                                            d_link_off, d_src, d_tgt, d_pair_conf_min,
                                            o.conf_min, link_pair, state, ctx->d_flags);
     });
-    const int solve_blocks = (n_pairs + 7) / 8;
+    const int solve_blocks = n_pairs;  // one warp per CTA: pairs spread over all SMs' FP64 pipes
     for (int it = 1; it <= o.iters + (o.want_cost ? 1 : 0); ++it) {
       const int kind = it == 1 ? FIRST : (it > o.iters ? COST : IRLS);
       // the cost of a single solve uses h = 1, which a huge delta reproduces
@@ -512,7 +522,7 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
         });
       else
         traced(ctx, cs, "sim3_solve", [&] {
-          k_solve<<<solve_blocks, 256, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
+          k_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
                                                 d_out, d_pair_status, it == o.iters, ckpt, it,
                                                 o.iters);
         });
@@ -624,7 +634,7 @@ extern "C" ec3r_status ec3r_align_submaps_noalloc(
   k_setup<<<n_pairs, THREADS, 0, cs>>>(d_xyz, d_conf, n_frames, hw, n_pairs, n_links,
                                        d_link_off, d_src, d_tgt, d_pair_conf_min, o.conf_min,
                                        link_pair, state, flags);
-  const int solve_blocks = (n_pairs + 7) / 8;
+  const int solve_blocks = n_pairs;  // one warp per CTA: pairs spread over all SMs' FP64 pipes
   for (int it = 1; it <= o.iters + (o.want_cost ? 1 : 0); ++it) {
     const int kind = it == 1 ? FIRST : (it > o.iters ? COST : IRLS);
     const float dl = (kind == COST && o.iters == 1) ? FLT_MAX : o.huber_delta;
@@ -649,7 +659,7 @@ extern "C" ec3r_status ec3r_align_submaps_noalloc(
       k_cost<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials,
                                                     state, d_pair_cost);
     else
-      k_solve<<<solve_blocks, 256, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
+      k_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
                                             d_out, d_pair_status, it == o.iters, nullptr, it,
                                             o.iters);
   }

@@ -1,7 +1,8 @@
 // Reverse-mode derivative (adjoint) of the batched Huber-IRLS registration.
 //
-// The forward pass (align.cu) is re-run first; its solve kernels checkpoint,
-// per pair and iteration, the 19 moments and the estimate (A = s R, b).  The
+// The forward pass (align.cu) checkpoints, per pair and iteration, the 19
+// moments and the estimate (A = s R, b); the backward call reuses the last
+// forward call's checkpoints when its inputs match, else re-runs it.  The
 // loss gradient then flows backwards through every iteration: the Huber
 // weights of solve k depend on estimate k-1, so each solve is differentiated
 // and the weights' dependence is carried into the previous estimate.
@@ -72,13 +73,6 @@ __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ck
     a.gOm = -gcost[k] * cost[k] / W;
   }
 }
-
-// Per-pair data a sweep needs, staged in shared memory as float.
-struct SweepPair {
-  float pp[3], pq[3];
-  float cmin, delta;
-  int active;
-};
 
 // Reduction sweeps.  KIND 0: cost (om at S_{K-1}, e at S_K);  KIND 1: Huber
 // path of iteration k (S_{k-1} and the moments' gradient of k).
@@ -335,24 +329,40 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
 
 // Per-correspondence gradients, all iterations in one pass (link layout,
 // 8 floats per pixel: dp(3), dq(3), dc_p, dc_q).
+// A side whose frame no other link references writes straight into the frame
+// gradients; a shared frame's side goes to the link buffer and is summed by
+// k_adj_frames in link order.
 template <bool VEC>
 __global__ void __launch_bounds__(THREADS) k_adj_scatter(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
     const int32_t* __restrict__ link_pair, const PairState* __restrict__ st,
     const AdjState* __restrict__ adj, const double* __restrict__ ckpt,
-    const double* __restrict__ gM, int iters, float delta, int rule, float* __restrict__ lg) {
+    const double* __restrict__ gM, int iters, float delta, int rule, float* __restrict__ lg,
+    const int32_t* __restrict__ refs, float* __restrict__ gxyz, float* __restrict__ gconf) {
   const int64_t t = blockIdx.x;
   const int64_t l = t / tpl;
   const int c = (int)(t - l * tpl);
   const int k = link_pair[l];
+  if (k < 0) return;  // pair rejected at set-up: its frames were not counted
   const int64_t px0 = (int64_t)c * TILE;
   const int64_t rem = hw - px0;
   const int npx = rem < TILE ? (int)rem : TILE;
+  const int64_t fs = src[l], ft = tgt[l];
+  const bool ds = refs[fs] == 1, dt = refs[ft] == 1;  // direct writes
   float* out = lg + (l * hw + px0) * 8;
-  const bool active = k >= 0 && adj[k].active;
+  float* gxs = gxyz + (fs * hw + px0) * 3;
+  float* gxt = gxyz + (ft * hw + px0) * 3;
+  float* gcs = gconf + fs * hw + px0;
+  float* gct = gconf + ft * hw + px0;
+  const bool active = adj[k].active;
   if (!active) {
-    for (int i = threadIdx.x; i < npx * 8; i += THREADS) out[i] = 0.f;
+    for (int i = threadIdx.x; i < npx; i += THREADS) {
+      if (ds) { gxs[3 * i] = gxs[3 * i + 1] = gxs[3 * i + 2] = 0.f; gcs[i] = 0.f; }
+      else { out[8 * i] = out[8 * i + 1] = out[8 * i + 2] = out[8 * i + 6] = 0.f; }
+      if (dt) { gxt[3 * i] = gxt[3 * i + 1] = gxt[3 * i + 2] = 0.f; gct[i] = 0.f; }
+      else { out[8 * i + 3] = out[8 * i + 4] = out[8 * i + 5] = out[8 * i + 7] = 0.f; }
+    }
     return;
   }
   extern __shared__ float sh[];  // per iteration: A(9) b(3) gM(17)
@@ -371,7 +381,6 @@ __global__ void __launch_bounds__(THREADS) k_adj_scatter(
   const float pp0 = st[k].piv_p[0], pp1 = st[k].piv_p[1], pp2 = st[k].piv_p[2];
   const float pq0 = st[k].piv_q[0], pq1 = st[k].piv_q[1], pq2 = st[k].piv_q[2];
   const float cmin = st[k].cmin;
-  const int64_t fs = src[l], ft = tgt[l];
   const float* P = xyz + (fs * hw + px0) * 3;
   const float* Q = xyz + (ft * hw + px0) * 3;
   const float* CP = conf + fs * hw + px0;
@@ -434,31 +443,71 @@ __global__ void __launch_bounds__(THREADS) k_adj_scatter(
         }
       }
     }
+    const float gcp = v ? (rule == 0 ? gw * cq : gw) : 0.f;
+    const float gcq = v ? (rule == 0 ? gw * cp : 0.f) : 0.f;
     float* o = out + (size_t)i * 8;
-    o[0] = gp[0]; o[1] = gp[1]; o[2] = gp[2];
-    o[3] = gq[0]; o[4] = gq[1]; o[5] = gq[2];
-    o[6] = v ? (rule == 0 ? gw * cq : gw) : 0.f;
-    o[7] = v ? (rule == 0 ? gw * cp : 0.f) : 0.f;
+    if (ds) {
+      gxs[3 * i] = gp[0]; gxs[3 * i + 1] = gp[1]; gxs[3 * i + 2] = gp[2];
+      gcs[i] = gcp;
+    } else {
+      o[0] = gp[0]; o[1] = gp[1]; o[2] = gp[2]; o[6] = gcp;
+    }
+    if (dt) {
+      gxt[3 * i] = gq[0]; gxt[3 * i + 1] = gq[1]; gxt[3 * i + 2] = gq[2];
+      gct[i] = gcq;
+    } else {
+      o[3] = gq[0]; o[4] = gq[1]; o[5] = gq[2]; o[7] = gcq;
+    }
   }
+}
+
+// References of every frame by the links of valid pairs.
+__global__ void k_adj_refcount(int64_t n_links, int64_t n_frames,
+                               const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
+                               const int32_t* __restrict__ link_pair, int32_t* refs,
+                               int32_t* any_shared) {
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_links || link_pair[l] < 0) return;
+  const int a = src[l], b = tgt[l];
+  if (atomicAdd(&refs[a], 1) >= 1) atomicExch(any_shared, 1);
+  if (atomicAdd(&refs[b], 1) >= 1) atomicExch(any_shared, 1);
+}
+
+// Zero the gradients of frames that no scatter writes directly (references 0
+// or > 1).  One CTA per frame.
+__global__ void k_adj_zero_frames(int64_t hw, const int32_t* __restrict__ refs,
+                                  float* __restrict__ gxyz, float* __restrict__ gconf) {
+  const int64_t f = blockIdx.x;
+  if (refs[f] == 1) return;
+  float* gx = gxyz + f * hw * 3;
+  float* gc = gconf + f * hw;
+  for (int64_t i = threadIdx.x; i < hw * 3; i += blockDim.x) gx[i] = 0.f;
+  for (int64_t i = threadIdx.x; i < hw; i += blockDim.x) gc[i] = 0.f;
 }
 
 // Frame-bank gradients: one thread per pixel index, links in order.
 __global__ void k_adj_frames(int64_t hw, int64_t n_links, const int32_t* __restrict__ src,
                              const int32_t* __restrict__ tgt,
-                             const int32_t* __restrict__ link_pair, const float* __restrict__ lg,
+                             const int32_t* __restrict__ link_pair,
+                             const int32_t* __restrict__ refs,
+                             const int32_t* __restrict__ any_shared, const float* __restrict__ lg,
                              float* __restrict__ gxyz, float* __restrict__ gconf) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= hw) return;
+  if (i >= hw || !*any_shared) return;
   for (int64_t l = 0; l < n_links; ++l) {
     if (link_pair[l] < 0) continue;
     const float* g = lg + (l * hw + i) * 8;
     const int64_t a = src[l], b = tgt[l];
-    float* ga = gxyz + (a * hw + i) * 3;
-    float* gb = gxyz + (b * hw + i) * 3;
-    ga[0] += g[0]; ga[1] += g[1]; ga[2] += g[2];
-    gb[0] += g[3]; gb[1] += g[4]; gb[2] += g[5];
-    gconf[a * hw + i] += g[6];
-    gconf[b * hw + i] += g[7];
+    if (refs[a] > 1) {
+      float* ga = gxyz + (a * hw + i) * 3;
+      ga[0] += g[0]; ga[1] += g[1]; ga[2] += g[2];
+      gconf[a * hw + i] += g[6];
+    }
+    if (refs[b] > 1) {
+      float* gb = gxyz + (b * hw + i) * 3;
+      gb[0] += g[3]; gb[1] += g[4]; gb[2] += g[5];
+      gconf[b * hw + i] += g[7];
+    }
   }
 }
 
@@ -481,18 +530,34 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "the backward pass supports FP32 moments only");
   if (n_pairs <= 0) return n_pairs == 0 ? EC3R_OK : EC3R_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  // forward re-run with checkpoints and the cost
-  void *p_out, *p_st, *p_cost;
-  ec3r_status st;
-  if ((st = ensure_buf(ctx, "adj.out", sizeof(ec3r_sim3) * (size_t)n_pairs, s, &p_out))) return st;
-  if ((st = ensure_buf(ctx, "adj.status", sizeof(int32_t) * (size_t)n_pairs, s, &p_st))) return st;
-  if ((st = ensure_buf(ctx, "adj.cost", sizeof(double) * (size_t)n_pairs, s, &p_cost))) return st;
   ec3r_align_opts fo = *opts;
   fo.want_cost = 1;
-  if ((st = ec3r_align_submaps(ctx, d_xyz, d_conf, n_frames, hw, n_pairs, n_links, d_link_off,
-                               d_src, d_tgt, d_pair_conf_min, &fo, (ec3r_sim3*)p_out,
-                               (int32_t*)p_st, (double*)p_cost, stream)))
-    return st;
+  // Reuse the checkpoints of the last forward call on this context when it
+  // had these inputs and options (with the cost); otherwise re-run it.
+  const std::string want = key_of(
+      "fwd", {(uint64_t)d_xyz, (uint64_t)d_conf, (uint64_t)n_frames, (uint64_t)hw,
+              (uint64_t)n_pairs, (uint64_t)n_links, (uint64_t)d_link_off, (uint64_t)d_src,
+              (uint64_t)d_tgt, (uint64_t)d_pair_conf_min, fbits(fo.huber_delta),
+              (uint64_t)fo.iters, fbits(fo.conf_min), (uint64_t)fo.weight_rule,
+              (uint64_t)fo.precision, (uint64_t)fo.want_cost});
+  void *p_out, *p_st, *p_cost;
+  ec3r_status st;
+  if (ctx->align_key == want && ctx->bufs.count("align.ckpt")) {
+    p_out = ctx->align_out;
+    p_st = ctx->align_status;
+    p_cost = ctx->align_cost;
+  } else {
+    if ((st = ensure_buf(ctx, "adj.out", sizeof(ec3r_sim3) * (size_t)n_pairs, s, &p_out)))
+      return st;
+    if ((st = ensure_buf(ctx, "adj.status", sizeof(int32_t) * (size_t)n_pairs, s, &p_st)))
+      return st;
+    if ((st = ensure_buf(ctx, "adj.cost", sizeof(double) * (size_t)n_pairs, s, &p_cost)))
+      return st;
+    if ((st = ec3r_align_submaps(ctx, d_xyz, d_conf, n_frames, hw, n_pairs, n_links, d_link_off,
+                                 d_src, d_tgt, d_pair_conf_min, &fo, (ec3r_sim3*)p_out,
+                                 (int32_t*)p_st, (double*)p_cost, stream)))
+      return st;
+  }
   const int iters = opts->iters;
   const int64_t tpl = (hw + TILE - 1) / TILE;
   const int64_t n_tiles = n_links * tpl;
@@ -519,7 +584,7 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
   const float delta = opts->huber_delta;
   const int rule = opts->weight_rule;
   const dim3 grid((unsigned)(n_tiles > 0 ? n_tiles : 1));
-  const int solve_blocks = (n_pairs + 7) / 8;
+  const int solve_blocks = n_pairs;  // one warp per CTA: pairs spread over all SMs' FP64 pipes
   traced(ctx, s, "adj_init", [&] {
     k_adj_init<<<(n_pairs + 127) / 128, 128, 0, s>>>(n_pairs, iters, ckpt, state,
                                                     (const int32_t*)p_st, (const double*)p_cost,
@@ -538,7 +603,7 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
                                                         iters, iters, delta, rule, part);
     });
   traced(ctx, s, "adj_solve", [&] {
-    k_adj_solve<<<solve_blocks, 256, 0, s>>>(n_pairs, iters, iters, d_link_off, (int)tpl, part,
+    k_adj_solve<<<solve_blocks, 32, 0, s>>>(n_pairs, iters, iters, d_link_off, (int)tpl, part,
                                              cost_path && n_tiles > 0, 1, ckpt, adj, gM);
   });
   for (int k = iters; k >= 2; --k) {
@@ -554,28 +619,42 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
                                                           iters, k, delta, rule, part);
       });
     traced(ctx, s, "adj_solve", [&] {
-      k_adj_solve<<<solve_blocks, 256, 0, s>>>(n_pairs, iters, k - 1, d_link_off, (int)tpl, part,
+      k_adj_solve<<<solve_blocks, 32, 0, s>>>(n_pairs, iters, k - 1, d_link_off, (int)tpl, part,
                                                n_tiles > 0, 0, ckpt, adj, gM);
     });
   }
-  EC3R_CUDA_TRY(ctx, cudaMemsetAsync(d_grad_xyz, 0, sizeof(float) * 3 * (size_t)(n_frames * hw), s));
-  EC3R_CUDA_TRY(ctx, cudaMemsetAsync(d_grad_conf, 0, sizeof(float) * (size_t)(n_frames * hw), s));
+  void* p_refs;
+  if ((st = ensure_buf(ctx, "adj.refs", sizeof(int32_t) * (size_t)(n_frames + 1), s, &p_refs)))
+    return st;
+  int32_t* refs = (int32_t*)p_refs;
+  int32_t* any_shared = refs + n_frames;
+  EC3R_CUDA_TRY(ctx, cudaMemsetAsync(refs, 0, sizeof(int32_t) * (size_t)(n_frames + 1), s));
+  if (n_links > 0)
+    traced(ctx, s, "adj_refcount", [&] {
+      k_adj_refcount<<<(unsigned)((n_links + 255) / 256), 256, 0, s>>>(
+          n_links, n_frames, d_src, d_tgt, link_pair, refs, any_shared);
+    });
+  traced(ctx, s, "adj_zero_frames", [&] {
+    k_adj_zero_frames<<<(unsigned)n_frames, 512, 0, s>>>(hw, refs, d_grad_xyz, d_grad_conf);
+  });
   if (n_tiles > 0) {
     const size_t shm = sizeof(float) * 29 * (size_t)iters;
     traced(ctx, s, "adj_scatter", [&] {
       if (vec)
         k_adj_scatter<true><<<grid, THREADS, shm, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt,
                                                        link_pair, state, adj, ckpt, gM, iters,
-                                                       delta, rule, lg);
+                                                       delta, rule, lg, refs, d_grad_xyz,
+                                                       d_grad_conf);
       else
         k_adj_scatter<false><<<grid, THREADS, shm, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src,
                                                         d_tgt, link_pair, state, adj, ckpt, gM,
-                                                        iters, delta, rule, lg);
+                                                        iters, delta, rule, lg, refs, d_grad_xyz,
+                                                        d_grad_conf);
     });
     traced(ctx, s, "adj_frames", [&] {
       k_adj_frames<<<(unsigned)((hw + 255) / 256), 256, 0, s>>>(hw, n_links, d_src, d_tgt,
-                                                                link_pair, lg, d_grad_xyz,
-                                                                d_grad_conf);
+                                                                link_pair, refs, any_shared, lg,
+                                                                d_grad_xyz, d_grad_conf);
     });
   }
   EC3R_CUDA_TRY(ctx, cudaGetLastError());

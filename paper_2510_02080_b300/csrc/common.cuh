@@ -64,6 +64,11 @@ struct ec3r_ctx {
   std::map<std::string, ec3r::GraphEntry> graphs;
   std::map<std::string, ec3r::Extension*> ext;
   uint64_t clock = 0;
+  // last registration call (its checkpoints serve a following backward call)
+  std::string align_key;
+  void* align_out = nullptr;
+  void* align_status = nullptr;
+  void* align_cost = nullptr;
 };
 
 namespace ec3r {

@@ -285,17 +285,24 @@ __global__ void __launch_bounds__(32) k_pg_assemble(
 // --------------------------------------------------------------------------
 // factorisation + forward substitution: one warp per column of a level
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) k_pg_factor(
+constexpr int FWARPS = 4;  // warps per column in k_pg_factor
+
+__global__ void __launch_bounds__(32 * FWARPS) k_pg_factor(
     const int* __restrict__ cols, const int* __restrict__ col_ptr, const int* __restrict__ off_blk,
     const int* __restrict__ upd_ptr, const int* __restrict__ upd, const int* __restrict__ row_ptr,
     const int* __restrict__ row_it, double* L, double* bvec, unsigned* flags, int* fail) {
   const int k = cols[blockIdx.x];
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ double D[NB];
   __shared__ double inv[7];
-  // left-looking updates of every block of column k (diagonal first, then off-diagonal)
+  __shared__ double y[7];
+  // left-looking updates of every block of column k; warp w owns the
+  // destination blocks with index % FWARPS == w and applies their updates in
+  // list (descendant) order, so every block sees a fixed order
   for (int p = upd_ptr[k]; p < upd_ptr[k + 1]; ++p) {
-    const int dst = upd[3 * p], a = upd[3 * p + 1], bb = upd[3 * p + 2];
+    const int dst = upd[3 * p];
+    if (dst % FWARPS != warp) continue;
+    const int a = upd[3 * p + 1], bb = upd[3 * p + 2];
     double* Dst = L + (size_t)dst * NB;
     const double* A = L + (size_t)a * NB;
     const double* B = L + (size_t)bb * NB;
@@ -308,76 +315,74 @@ __global__ void __launch_bounds__(32) k_pg_factor(
     }
     __syncwarp();
   }
+  __syncthreads();
   double* Lkk = L + (size_t)k * NB;
-  for (int idx = lane; idx < NB; idx += 32) D[idx] = Lkk[idx];
-  __syncwarp();
-  // dense 7x7 Cholesky (lower)
-  bool bad = false;
-  for (int c = 0; c < 7; ++c) {
-    const double d = D[8 * c];
-    if (!(d > 0.0) || !isfinite(d)) bad = true;
-    const double piv = sqrt(fmax(d, 1e-300));
-    const double ip = 1.0 / piv;
+  if (warp == 0) {
+    for (int idx = lane; idx < NB; idx += 32) D[idx] = Lkk[idx];
     __syncwarp();
-    if (lane == 0) {
-      D[8 * c] = piv;
-      inv[c] = ip;
+    // dense 7x7 Cholesky (lower); pivots through rsqrt
+    bool bad = false;
+    for (int c = 0; c < 7; ++c) {
+      const double d = D[8 * c];
+      if (!(d > 0.0) || !isfinite(d)) bad = true;
+      const double ip = rsqrt(fmax(d, 1e-300));
+      __syncwarp();
+      if (lane == 0) {
+        D[8 * c] = d * ip;
+        inv[c] = ip;
+      }
+      if (lane > c && lane < 7) D[7 * lane + c] *= ip;
+      __syncwarp();
+      for (int idx = lane; idx < NB; idx += 32) {
+        const int r = idx / 7, cc = idx % 7;
+        if (r > c && cc > c && cc <= r) D[idx] -= D[7 * r + c] * D[7 * cc + c];
+      }
+      __syncwarp();
     }
-    if (lane > c && lane < 7) D[7 * lane + c] *= ip;
-    __syncwarp();
-    // trailing update of the lower triangle
-    for (int idx = lane; idx < NB; idx += 32) {
-      const int r = idx / 7, cc = idx % 7;
-      if (r > c && cc > c && cc <= r) D[idx] -= D[7 * r + c] * D[7 * cc + c];
-    }
-    __syncwarp();
-  }
-  if (bad) {
-    if (lane == 0) {
+    if (bad && lane == 0) {
       atomicOr(flags, FLAG_NOT_SPD);
       atomicExch(fail, 1);
     }
+    for (int idx = lane; idx < NB; idx += 32) {
+      const int r = idx / 7, c = idx % 7;
+      Lkk[idx] = c <= r ? D[idx] : 0.0;
+    }
   }
-  for (int idx = lane; idx < NB; idx += 32) {
-    const int r = idx / 7, c = idx % 7;
-    Lkk[idx] = c <= r ? D[idx] : 0.0;
-  }
+  __syncthreads();
   // off-diagonal blocks: X = H_ik Lkk^-T (row-wise forward substitution)
   const int o0 = col_ptr[k], o1 = col_ptr[k + 1];
-  for (int base = o0 * 7; base < o1 * 7; base += 32) {
-    const int q = base + lane;
-    if (q < o1 * 7) {
-      double* X = L + (size_t)off_blk[q / 7] * NB + 7 * (q % 7);
-      double x[7];
-      for (int c = 0; c < 7; ++c) {
-        double s = X[c];
-        for (int t = 0; t < c; ++t) s -= x[t] * D[7 * c + t];
-        x[c] = s * inv[c];
-      }
-      for (int c = 0; c < 7; ++c) X[c] = x[c];
+  for (int q = o0 * 7 + threadIdx.x; q < o1 * 7; q += 32 * FWARPS) {
+    double* X = L + (size_t)off_blk[q / 7] * NB + 7 * (q % 7);
+    double x[7];
+    for (int c = 0; c < 7; ++c) {
+      double s = X[c];
+      for (int t = 0; t < c; ++t) s -= x[t] * D[7 * c + t];
+      x[c] = s * inv[c];
     }
+    for (int c = 0; c < 7; ++c) X[c] = x[c];
   }
   // forward substitution: y_k = Lkk^-1 (b_k - sum_j L_kj y_j)
-  __shared__ double y[7];
-  if (lane < 7) {
-    double s = bvec[7 * k + lane];
-    for (int p = row_ptr[k]; p < row_ptr[k + 1]; ++p) {
-      const int j = row_it[2 * p], blk = row_it[2 * p + 1];
-      const double* Lkj = L + (size_t)blk * NB + 7 * lane;
-      for (int t = 0; t < 7; ++t) s -= Lkj[t] * bvec[7 * j + t];
+  if (warp == 0) {
+    if (lane < 7) {
+      double s = bvec[7 * k + lane];
+      for (int p = row_ptr[k]; p < row_ptr[k + 1]; ++p) {
+        const int j = row_it[2 * p], blk = row_it[2 * p + 1];
+        const double* Lkj = L + (size_t)blk * NB + 7 * lane;
+        for (int t = 0; t < 7; ++t) s -= Lkj[t] * bvec[7 * j + t];
+      }
+      y[lane] = s;
     }
-    y[lane] = s;
-  }
-  __syncwarp();
-  if (lane == 0) {
-    for (int c = 0; c < 7; ++c) {
-      double s = y[c];
-      for (int t = 0; t < c; ++t) s -= D[7 * c + t] * y[t];
-      y[c] = s * inv[c];
+    __syncwarp();
+    if (lane == 0) {
+      for (int c = 0; c < 7; ++c) {
+        double s = y[c];
+        for (int t = 0; t < c; ++t) s -= D[7 * c + t] * y[t];
+        y[c] = s * inv[c];
+      }
     }
+    __syncwarp();
+    if (lane < 7) bvec[7 * k + lane] = y[lane];
   }
-  __syncwarp();
-  if (lane < 7) bvec[7 * k + lane] = y[lane];
 }
 
 // back substitution, root to leaves: x_k = Lkk^-T (y_k - sum_i L_ik^T x_i)
@@ -829,7 +834,7 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
       if (P->nf == 0) continue;
       for (int l = 0; l < nlev; ++l)
         traced(ctx, cs, "pg_factor", [&] {
-          k_pg_factor<<<P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs>>>(
+          k_pg_factor<<<P->level_ptr[l + 1] - P->level_ptr[l], 32 * FWARPS, 0, cs>>>(
               P->d_level_cols + P->level_ptr[l], P->d_col_ptr, P->d_off_blk, P->d_upd_ptr,
               P->d_upd, P->d_row_ptr, P->d_row, P->d_L, P->d_b, ctx->d_flags, P->d_fail);
         });
