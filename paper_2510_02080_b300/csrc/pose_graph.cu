@@ -287,34 +287,44 @@ __global__ void __launch_bounds__(32) k_pg_assemble(
 // --------------------------------------------------------------------------
 constexpr int FWARPS = 4;  // warps per column in k_pg_factor
 
+// L[dst] -= sum over the group's updates of A B^T for the entries idx of this
+// lane; four independent partial sums break the FP64 dependency chain.
+__device__ __forceinline__ void apply_group(double* L, int dst, const int* __restrict__ ab, int n,
+                                            int lane) {
+  double* Dst = L + (size_t)dst * NB;
+  for (int idx = lane; idx < NB; idx += 32) {
+    const int r = idx / 7, c = idx % 7;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int q = 0; q < n; ++q) {
+      const double* A = L + (size_t)ab[2 * q] * NB + 7 * r;
+      const double* B = L + (size_t)ab[2 * q + 1] * NB + 7 * c;
+      s0 = fma(A[0], B[0], s0);
+      s1 = fma(A[1], B[1], s1);
+      s2 = fma(A[2], B[2], s2);
+      s3 = fma(A[3], B[3], s3);
+      s0 = fma(A[4], B[4], s0);
+      s1 = fma(A[5], B[5], s1);
+      s2 = fma(A[6], B[6], s2);
+    }
+    Dst[idx] -= (s0 + s1) + (s2 + s3);
+  }
+}
+
 __global__ void __launch_bounds__(32 * FWARPS) k_pg_factor(
     const int* __restrict__ cols, const int* __restrict__ col_ptr, const int* __restrict__ off_blk,
-    const int* __restrict__ upd_ptr, const int* __restrict__ upd, const int* __restrict__ row_ptr,
-    const int* __restrict__ row_it, double* L, double* bvec, unsigned* flags, int* fail) {
+    const int* __restrict__ grp_ptr, const int* __restrict__ grp, const int* __restrict__ upd_ab,
+    const int* __restrict__ row_ptr, const int* __restrict__ row_it, double* L, double* bvec,
+    double* idiag, unsigned* flags, int* fail) {
   const int k = cols[blockIdx.x];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ double D[NB];
   __shared__ double inv[7];
   __shared__ double y[7];
-  // left-looking updates of every block of column k; warp w owns the
-  // destination blocks with index % FWARPS == w and applies their updates in
-  // list (descendant) order, so every block sees a fixed order
-  for (int p = upd_ptr[k]; p < upd_ptr[k + 1]; ++p) {
-    const int dst = upd[3 * p];
-    if (dst % FWARPS != warp) continue;
-    const int a = upd[3 * p + 1], bb = upd[3 * p + 2];
-    double* Dst = L + (size_t)dst * NB;
-    const double* A = L + (size_t)a * NB;
-    const double* B = L + (size_t)bb * NB;
-    for (int idx = lane; idx < NB; idx += 32) {
-      const int r = idx / 7, c = idx % 7;
-      double s = Dst[idx];
-#pragma unroll
-      for (int t = 0; t < 7; ++t) s = fma(-A[7 * r + t], B[7 * c + t], s);
-      Dst[idx] = s;
-    }
-    __syncwarp();
-  }
+  // left-looking updates: warp w takes the update groups (one per destination
+  // block of column k) g with g % FWARPS == w; each group's updates are summed
+  // in a fixed order, so the result does not depend on scheduling
+  for (int g = grp_ptr[k] + warp; g < grp_ptr[k + 1]; g += FWARPS)
+    apply_group(L, grp[3 * g], upd_ab + 2 * grp[3 * g + 1], grp[3 * g + 2], lane);
   __syncthreads();
   double* Lkk = L + (size_t)k * NB;
   if (warp == 0) {
@@ -343,6 +353,7 @@ __global__ void __launch_bounds__(32 * FWARPS) k_pg_factor(
       atomicOr(flags, FLAG_NOT_SPD);
       atomicExch(fail, 1);
     }
+    if (lane < 7) idiag[7 * k + lane] = inv[lane];
     for (int idx = lane; idx < NB; idx += 32) {
       const int r = idx / 7, c = idx % 7;
       Lkk[idx] = c <= r ? D[idx] : 0.0;
@@ -390,7 +401,9 @@ __global__ void __launch_bounds__(32) k_pg_backsolve(const int* __restrict__ col
                                                      const int* __restrict__ col_ptr,
                                                      const int* __restrict__ off_row,
                                                      const int* __restrict__ off_blk,
-                                                     const double* __restrict__ L, double* bvec) {
+                                                     const double* __restrict__ L,
+                                                     const double* __restrict__ idiag,
+                                                     double* bvec) {
   const int k = cols[blockIdx.x];
   const int lane = threadIdx.x;
   __shared__ double x[7];
@@ -406,10 +419,11 @@ __global__ void __launch_bounds__(32) k_pg_backsolve(const int* __restrict__ col
   __syncwarp();
   if (lane == 0) {
     const double* D = L + (size_t)k * NB;
+    const double* id = idiag + 7 * k;
     for (int c = 6; c >= 0; --c) {
       double s = x[c];
       for (int t = c + 1; t < 7; ++t) s -= D[7 * t + c] * x[t];
-      x[c] = s / D[8 * c];
+      x[c] = s * id[c];
     }
   }
   __syncwarp();
@@ -435,13 +449,14 @@ struct Plan : Extension {
   std::vector<void*> allocs;
   int *d_ei = nullptr, *d_ej = nullptr, *d_perm = nullptr;
   int *d_col_ptr = nullptr, *d_off_row = nullptr, *d_off_blk = nullptr;
-  int *d_upd_ptr = nullptr, *d_upd = nullptr, *d_row_ptr = nullptr, *d_row = nullptr;
+  int *d_grp_ptr = nullptr, *d_grp = nullptr, *d_upd_ab = nullptr;
+  int *d_row_ptr = nullptr, *d_row = nullptr;
   int *d_level_cols = nullptr, *d_asm_ptr = nullptr, *d_asm = nullptr;
   int *d_g_ptr = nullptr, *d_g = nullptr;
   int *d_parent = nullptr, *d_tedge = nullptr, *d_tdir = nullptr;
   int *d_anc0 = nullptr, *d_anc1 = nullptr, *d_fail = nullptr;
   double *d_L = nullptr, *d_b = nullptr, *d_contrib = nullptr, *d_gvec = nullptr,
-         *d_chi2e = nullptr;
+         *d_chi2e = nullptr, *d_idiag = nullptr;
   ec3r_sim3 *d_W0 = nullptr, *d_W1 = nullptr;
   ~Plan() override {
     for (void* p : allocs) cudaFree(p);
@@ -552,28 +567,36 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   std::vector<std::vector<int>> rowstruct(nf);
   for (int j = 0; j < nf; ++j)
     for (int k : st[j]) rowstruct[k].push_back(j);
-  std::vector<int> upd_ptr(nf + 1, 0), upd, row_ptr(nf + 1, 0), row;
+  // update groups: for every block (i, k) of column k, the products
+  // L_ij L_kj^T of its descendants j, in descendant order
+  std::vector<int> grp_ptr(nf + 1, 0), grp, upd_ab, row_ptr(nf + 1, 0), row;
   for (int k = 0; k < nf; ++k) {
-    upd_ptr[k] = (int)upd.size() / 3;
+    grp_ptr[k] = (int)grp.size() / 3;
     row_ptr[k] = (int)row.size() / 2;
     std::sort(rowstruct[k].begin(), rowstruct[k].end());
-    // diagonal block first, then the off-diagonal ones, each in descendant order
     std::vector<int> targets;
     targets.push_back(k);
     for (int r : st[k]) targets.push_back(r);
-    for (int i : targets)
+    for (int i : targets) {
+      const int first = (int)upd_ab.size() / 2;
       for (int j : rowstruct[k]) {
         if (i != k && !st[j].count(i)) continue;
-        upd.push_back(blk(i, k));
-        upd.push_back(blk(i, j));
-        upd.push_back(blk(k, j));
+        upd_ab.push_back(blk(i, j));
+        upd_ab.push_back(blk(k, j));
       }
+      const int n_upd = (int)upd_ab.size() / 2 - first;
+      if (n_upd > 0) {
+        grp.push_back(blk(i, k));
+        grp.push_back(first);
+        grp.push_back(n_upd);
+      }
+    }
     for (int j : rowstruct[k]) {
       row.push_back(j);
       row.push_back(blk(k, j));
     }
   }
-  upd_ptr[nf] = (int)upd.size() / 3;
+  grp_ptr[nf] = (int)grp.size() / 3;
   row_ptr[nf] = (int)row.size() / 2;
   // levels (height in the elimination tree)
   std::vector<int> level(nf, 0);
@@ -663,8 +686,10 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   chk(upload(P, &P.d_col_ptr, col_ptr));
   chk(upload(P, &P.d_off_row, off_row));
   chk(upload(P, &P.d_off_blk, off_blk));
-  chk(upload(P, &P.d_upd_ptr, upd_ptr));
-  chk(upload(P, &P.d_upd, upd));
+  chk(upload(P, &P.d_grp_ptr, grp_ptr));
+  chk(upload(P, &P.d_grp, grp));
+  chk(upload(P, &P.d_upd_ab, upd_ab));
+  chk(alloc(P, &P.d_idiag, (size_t)nf * 7));
   chk(upload(P, &P.d_row_ptr, row_ptr));
   chk(upload(P, &P.d_row, row));
   chk(upload(P, &P.d_level_cols, level_cols));
@@ -835,14 +860,15 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
       for (int l = 0; l < nlev; ++l)
         traced(ctx, cs, "pg_factor", [&] {
           k_pg_factor<<<P->level_ptr[l + 1] - P->level_ptr[l], 32 * FWARPS, 0, cs>>>(
-              P->d_level_cols + P->level_ptr[l], P->d_col_ptr, P->d_off_blk, P->d_upd_ptr,
-              P->d_upd, P->d_row_ptr, P->d_row, P->d_L, P->d_b, ctx->d_flags, P->d_fail);
+              P->d_level_cols + P->level_ptr[l], P->d_col_ptr, P->d_off_blk, P->d_grp_ptr,
+              P->d_grp, P->d_upd_ab, P->d_row_ptr, P->d_row, P->d_L, P->d_b, P->d_idiag,
+              ctx->d_flags, P->d_fail);
         });
       for (int l = nlev - 1; l >= 0; --l)
         traced(ctx, cs, "pg_backsolve", [&] {
           k_pg_backsolve<<<P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs>>>(
               P->d_level_cols + P->level_ptr[l], P->d_col_ptr, P->d_off_row, P->d_off_blk,
-              P->d_L, P->d_b);
+              P->d_L, P->d_idiag, P->d_b);
         });
       traced(ctx, cs, "pg_update", [&] {
         k_pg_update<<<(P->nf + 63) / 64, 64, 0, cs>>>(P->nf, P->d_perm, P->d_b, d_nodes,

@@ -76,29 +76,43 @@ __device__ inline Sim3d identity() {
   return c;
 }
 
+// 1/n for n = 0..127 (entry 0 unused): FP64 division is slow on this GPU, so
+// the series below multiply by reciprocals.
+struct RecipTable {
+  double v[128];
+};
+__host__ __device__ constexpr RecipTable make_recips() {
+  RecipTable t{};
+  t.v[0] = 0.0;
+  for (int n = 1; n < 128; ++n) t.v[n] = 1.0 / (double)n;
+  return t;
+}
+__constant__ constexpr RecipTable c_recip = make_recips();
+
 // Coefficients (a, b, c) of V = a I + b phi^ + c phi^2.
 __device__ inline void v_coeffs(double sigma, double th2, double* a, double* b, double* c) {
   if (sigma * sigma + th2 < 0.25) {
     // a = sum_i s^i/(i+1)!,  b = sum_{i,j} s^i/i! (-th2)^j /(2j+1)! /(i+2j+2),
     // c = sum_{i,j} s^i/i! (-th2)^j /(2j+2)! /(i+2j+3)
+    const double* rc = c_recip.v;
     double sa = 0.0, sb = 0.0, sc = 0.0;
     double pi = 1.0;  // s^i / i!
     for (int i = 0; i < 40; ++i) {
-      sa += pi / (double)(i + 1);
+      sa += pi * rc[i + 1];
       double pj = 1.0;  // (-th2)^j
       double fb = 1.0, fc = 0.5;  // 1/(2j+1)!, 1/(2j+2)!
       double tb = 0.0, tc = 0.0;
       for (int j = 0; j < 20; ++j) {
-        tb += pj * fb / (double)(i + 2 * j + 2);
-        tc += pj * fc / (double)(i + 2 * j + 3);
+        tb += pj * fb * rc[i + 2 * j + 2];
+        tc += pj * fc * rc[i + 2 * j + 3];
         pj *= -th2;
-        fb /= (double)((2 * j + 2) * (2 * j + 3));
-        fc /= (double)((2 * j + 3) * (2 * j + 4));
+        fb *= rc[2 * j + 2] * rc[2 * j + 3];
+        fc *= rc[2 * j + 3] * rc[2 * j + 4];
         if (fabs(pj) * fb < 1e-20) break;
       }
       sb += pi * tb;
       sc += pi * tc;
-      pi *= sigma / (double)(i + 1);
+      pi *= sigma * rc[i + 1];
       if (fabs(pi) < 1e-20) break;
     }
     *a = sa;
@@ -133,9 +147,12 @@ __device__ inline void so3_exp(const double w[3], double R[9]) {
     A = 1.0 - th2 / 6.0 * (1.0 - th2 / 20.0);
     B = 0.5 - th2 / 24.0 * (1.0 - th2 / 30.0);
   } else {
-    const double th = sqrt(th2);
-    A = sin(th) / th;
-    B = (1.0 - cos(th)) / th2;
+    const double ith = rsqrt(th2);  // one rsqrt instead of sqrt and two divisions
+    const double th = th2 * ith;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    A = sn * ith;
+    B = (1.0 - cs) * ith * ith;
   }
   const double x = w[0], y = w[1], z = w[2];
   R[0] = 1.0 - B * (y * y + z * z);
@@ -154,9 +171,9 @@ __device__ inline void so3_log(const double R[9], double w[3]) {
   const double tr = R[0] + R[4] + R[8];
   double q0, q1, q2, q3;
   if (tr > R[0] && tr > R[4] && tr > R[8]) {
-    const double r = sqrt(1.0 + tr);
-    q0 = 0.5 * r;
-    const double f = 0.5 / r;
+    const double ir = rsqrt(1.0 + tr);
+    q0 = 0.5 * (1.0 + tr) * ir;
+    const double f = 0.5 * ir;
     q1 = (R[7] - R[5]) * f;
     q2 = (R[2] - R[6]) * f;
     q3 = (R[3] - R[1]) * f;
@@ -185,12 +202,13 @@ __device__ inline void so3_log(const double R[9], double w[3]) {
   if (q0 < 0.0) {
     q0 = -q0; q1 = -q1; q2 = -q2; q3 = -q3;
   }
-  const double n = sqrt(q1 * q1 + q2 * q2 + q3 * q3);
+  const double n2 = q1 * q1 + q2 * q2 + q3 * q3;
   double f;
-  if (n < 1e-8) {
-    f = 2.0 / q0 * (1.0 - n * n / (3.0 * q0 * q0));
+  if (n2 < 1e-16) {
+    f = 2.0 / q0 * (1.0 - n2 / (3.0 * q0 * q0));
   } else {
-    f = 2.0 * atan2(n, q0) / n;
+    const double in = rsqrt(n2);
+    f = 2.0 * atan2(n2 * in, q0) * in;
   }
   w[0] = f * q1;
   w[1] = f * q2;
