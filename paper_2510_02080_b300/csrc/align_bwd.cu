@@ -76,8 +76,8 @@ __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ck
 
 // Reduction sweeps.  KIND 0: cost (om at S_{K-1}, e at S_K);  KIND 1: Huber
 // path of iteration k (S_{k-1} and the moments' gradient of k).
-template <int KIND, bool VEC>
-__global__ void __launch_bounds__(THREADS, 2) k_adj_reduce(
+template <int KIND, bool LASTK, bool VEC>
+__global__ void __launch_bounds__(THREADS, 3) k_adj_reduce(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
     const int32_t* __restrict__ link_pair, const PairState* __restrict__ st,
@@ -96,16 +96,16 @@ __global__ void __launch_bounds__(THREADS, 2) k_adj_reduce(
   const bool first = k_it == 1;
   for (int i = 0; i < 9; ++i) {
     Ap[i] = first ? ((i % 4 == 0) ? 1.f : 0.f) : (float)ckb[(k_it - 2) * CKPT + CK_A + i];
-    Ac[i] = (float)ckb[(k_it - 1) * CKPT + CK_A + i];
+    Ac[i] = (KIND == 0 || LASTK) ? (float)ckb[(k_it - 1) * CKPT + CK_A + i] : 0.f;
   }
   for (int i = 0; i < 3; ++i) {
     bp[i] = first ? 0.f : (float)ckb[(k_it - 2) * CKPT + CK_B + i];
-    bc[i] = (float)ckb[(k_it - 1) * CKPT + CK_B + i];
+    bc[i] = (KIND == 0 || LASTK) ? (float)ckb[(k_it - 1) * CKPT + CK_B + i] : 0.f;
   }
   for (int i = 0; i < NGM; ++i)
     G[i] = KIND == 1 ? (float)gM[((size_t)k * iters + (k_it - 1)) * NGM + i] : 0.f;
   const float gJ = (float)adj[k].gJ, gOm = (float)adj[k].gOm;
-  const bool lastk = k_it == iters;
+  constexpr bool lastk = LASTK;  // the cost residual at S_K enters the last Huber sweep
   const float pp0 = st[k].piv_p[0], pp1 = st[k].piv_p[1], pp2 = st[k].piv_p[2];
   const float pq0 = st[k].piv_q[0], pq1 = st[k].piv_q[1], pq2 = st[k].piv_q[2];
   const float cmin = st[k].cmin;
@@ -150,14 +150,15 @@ __global__ void __launch_bounds__(THREADS, 2) k_adj_reduce(
                   y0 * (G[G_QP] * x0 + G[G_QP + 1] * x1 + G[G_QP + 2] * x2) +
                   y1 * (G[G_QP + 3] * x0 + G[G_QP + 4] * x1 + G[G_QP + 5] * x2) +
                   y2 * (G[G_QP + 6] * x0 + G[G_QP + 7] * x1 + G[G_QP + 8] * x2);
-      if (lastk) {
+      if constexpr (lastk) {
         const float f0 = Ac[0] * x0 + Ac[1] * x1 + Ac[2] * x2 + bc[0] - y0;
         const float f1 = Ac[3] * x0 + Ac[4] * x1 + Ac[5] * x2 + bc[1] - y1;
         const float f2 = Ac[6] * x0 + Ac[7] * x1 + Ac[8] * x2 + bc[2] - y2;
         gom += gJ * (f0 * f0 + f1 * f1 + f2 * f2) + gOm;
       }
       // h = delta / r on the outer branch: dh/de = -delta e / r^3
-      const float f = rr > dl * dl ? -(gom * w) * dl * rsqrtf(rr) / rr : 0.f;
+      const float rs = rsqrtf(rr);
+      const float f = rr > dl * dl ? -(gom * w) * dl * rs * rs * rs : 0.f;
       g0 = f * e0; g1 = f * e1; g2 = f * e2;
     }
     acc[0] += g0 * x0; acc[1] += g0 * x1; acc[2] += g0 * x2;
@@ -331,9 +332,11 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
 // 8 floats per pixel: dp(3), dq(3), dc_p, dc_q).
 // A side whose frame no other link references writes straight into the frame
 // gradients; a shared frame's side goes to the link buffer and is summed by
-// k_adj_frames in link order.
+// k_adj_frames in link order.  Each thread owns 4 consecutive pixels; the
+// per-iteration constants are read once per 4 pixels; invalid pixels carry
+// zero weight and zero coordinates, so every term they add is zero.
 template <bool VEC>
-__global__ void __launch_bounds__(THREADS) k_adj_scatter(
+__global__ void __launch_bounds__(THREADS, 2) k_adj_scatter(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
     const int32_t* __restrict__ link_pair, const PairState* __restrict__ st,
@@ -356,28 +359,21 @@ __global__ void __launch_bounds__(THREADS) k_adj_scatter(
   float* gcs = gconf + fs * hw + px0;
   float* gct = gconf + ft * hw + px0;
   const bool active = adj[k].active;
-  if (!active) {
-    for (int i = threadIdx.x; i < npx; i += THREADS) {
-      if (ds) { gxs[3 * i] = gxs[3 * i + 1] = gxs[3 * i + 2] = 0.f; gcs[i] = 0.f; }
-      else { out[8 * i] = out[8 * i + 1] = out[8 * i + 2] = out[8 * i + 6] = 0.f; }
-      if (dt) { gxt[3 * i] = gxt[3 * i + 1] = gxt[3 * i + 2] = 0.f; gct[i] = 0.f; }
-      else { out[8 * i + 3] = out[8 * i + 4] = out[8 * i + 5] = out[8 * i + 7] = 0.f; }
+  constexpr int PER = 29;  // per iteration: A(9) b(3) gM(17)
+  extern __shared__ float sh[];
+  if (active) {
+    const double* ckb = ckpt + (size_t)k * iters * CKPT;
+    for (int i = threadIdx.x; i < iters * PER; i += THREADS) {
+      const int it = i / PER, f = i % PER;
+      float v;
+      if (f < 9) v = (float)ckb[it * CKPT + CK_A + f];
+      else if (f < 12) v = (float)ckb[it * CKPT + CK_B + (f - 9)];
+      else v = (float)gM[((size_t)k * iters + it) * NGM + (f - 12)];
+      sh[i] = v;
     }
-    return;
-  }
-  extern __shared__ float sh[];  // per iteration: A(9) b(3) gM(17)
-  constexpr int PER = 29;
-  const double* ckb = ckpt + (size_t)k * iters * CKPT;
-  for (int i = threadIdx.x; i < iters * PER; i += THREADS) {
-    const int it = i / PER, f = i % PER;
-    float v;
-    if (f < 9) v = (float)ckb[it * CKPT + CK_A + f];
-    else if (f < 12) v = (float)ckb[it * CKPT + CK_B + (f - 9)];
-    else v = (float)gM[((size_t)k * iters + it) * NGM + (f - 12)];
-    sh[i] = v;
   }
   __syncthreads();
-  const float gJ = (float)adj[k].gJ, gOm = (float)adj[k].gOm;
+  const float gJ = active ? (float)adj[k].gJ : 0.f, gOm = active ? (float)adj[k].gOm : 0.f;
   const float pp0 = st[k].piv_p[0], pp1 = st[k].piv_p[1], pp2 = st[k].piv_p[2];
   const float pq0 = st[k].piv_q[0], pq1 = st[k].piv_q[1], pq2 = st[k].piv_q[2];
   const float cmin = st[k].cmin;
@@ -385,78 +381,158 @@ __global__ void __launch_bounds__(THREADS) k_adj_scatter(
   const float* Q = xyz + (ft * hw + px0) * 3;
   const float* CP = conf + fs * hw + px0;
   const float* CQ = conf + ft * hw + px0;
-  for (int i = threadIdx.x; i < npx; i += THREADS) {
-    const float p0 = P[3 * i], p1 = P[3 * i + 1], p2 = P[3 * i + 2];
-    const float q0 = Q[3 * i], q1 = Q[3 * i + 1], q2 = Q[3 * i + 2];
-    const float cp = CP[i], cq = CQ[i];
-    const bool v = finitef(p0) && finitef(p1) && finitef(p2) && finitef(q0) && finitef(q1) &&
-                   finitef(q2) && finitef(cp) && finitef(cq) && cp > cmin && cq > cmin;
-    float gp[3] = {0.f, 0.f, 0.f}, gq[3] = {0.f, 0.f, 0.f}, gw = 0.f;
-    if (v) {
-      const float x[3] = {p0 - pp0, p1 - pp1, p2 - pp2};
-      const float y[3] = {q0 - pq0, q1 - pq1, q2 - pq2};
-      const float w = rule == 0 ? cp * cq : cp;
+  for (int g = threadIdx.x; g < TILE / 4; g += THREADS) {
+    const int i0 = 4 * g;
+    if (i0 >= npx) break;
+    const int n = min(4, npx - i0);
+    float pr[12], qr[12], cpr[4], cqr[4];
+    if (VEC && n == 4) {
+      const float4* P4 = reinterpret_cast<const float4*>(P + 3 * i0);
+      const float4* Q4 = reinterpret_cast<const float4*>(Q + 3 * i0);
+      const float4 a = __ldcs(P4), b = __ldcs(P4 + 1), cc = __ldcs(P4 + 2);
+      const float4 d = __ldcs(Q4), e = __ldcs(Q4 + 1), f = __ldcs(Q4 + 2);
+      const float4 u = __ldcs(reinterpret_cast<const float4*>(CP + i0));
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(CQ + i0));
+      pr[0] = a.x; pr[1] = a.y; pr[2] = a.z; pr[3] = a.w; pr[4] = b.x; pr[5] = b.y;
+      pr[6] = b.z; pr[7] = b.w; pr[8] = cc.x; pr[9] = cc.y; pr[10] = cc.z; pr[11] = cc.w;
+      qr[0] = d.x; qr[1] = d.y; qr[2] = d.z; qr[3] = d.w; qr[4] = e.x; qr[5] = e.y;
+      qr[6] = e.z; qr[7] = e.w; qr[8] = f.x; qr[9] = f.y; qr[10] = f.z; qr[11] = f.w;
+      cpr[0] = u.x; cpr[1] = u.y; cpr[2] = u.z; cpr[3] = u.w;
+      cqr[0] = v.x; cqr[1] = v.y; cqr[2] = v.z; cqr[3] = v.w;
+    } else {
+      for (int j = 0; j < 4; ++j) {
+        const bool in = j < n;
+        for (int dd = 0; dd < 3; ++dd) {
+          pr[3 * j + dd] = in ? P[3 * (i0 + j) + dd] : 0.f;
+          qr[3 * j + dd] = in ? Q[3 * (i0 + j) + dd] : 0.f;
+        }
+        cpr[j] = in ? CP[i0 + j] : 0.f;
+        cqr[j] = in ? CQ[i0 + j] : 0.f;
+      }
+    }
+    float x[4][3], y[4][3], w[4], gp[4][3], gq[4][3], gw[4];
+    bool val[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool v = active && j < n && finitef(pr[3 * j]) && finitef(pr[3 * j + 1]) &&
+                     finitef(pr[3 * j + 2]) && finitef(qr[3 * j]) && finitef(qr[3 * j + 1]) &&
+                     finitef(qr[3 * j + 2]) && finitef(cpr[j]) && finitef(cqr[j]) &&
+                     cpr[j] > cmin && cqr[j] > cmin;
+      val[j] = v;
+      x[j][0] = v ? pr[3 * j] - pp0 : 0.f;
+      x[j][1] = v ? pr[3 * j + 1] - pp1 : 0.f;
+      x[j][2] = v ? pr[3 * j + 2] - pp2 : 0.f;
+      y[j][0] = v ? qr[3 * j] - pq0 : 0.f;
+      y[j][1] = v ? qr[3 * j + 1] - pq1 : 0.f;
+      y[j][2] = v ? qr[3 * j + 2] - pq2 : 0.f;
+      w[j] = v ? (rule == 0 ? cpr[j] * cqr[j] : cpr[j]) : 0.f;
+      gp[j][0] = gp[j][1] = gp[j][2] = 0.f;
+      gq[j][0] = gq[j][1] = gq[j][2] = 0.f;
+      gw[j] = 0.f;
+    }
+    if (active) {
       for (int it = 1; it <= iters; ++it) {
         const float* G = sh + (it - 1) * PER + 12;
-        float h = 1.f, e[3] = {0.f, 0.f, 0.f}, rr = 0.f;
-        const float* Ap = sh + (it - 2) * PER;
-        if (it > 1) {
-          for (int r = 0; r < 3; ++r)
-            e[r] = Ap[3 * r] * x[0] + Ap[3 * r + 1] * x[1] + Ap[3 * r + 2] * x[2] + Ap[9 + r] - y[r];
-          rr = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
-          h = fminf(1.f, delta * rsqrtf(rr));
+        float gW = G[G_W], gPP = G[G_PP], gSp[3], gSq[3], gQP[9];
+        for (int i = 0; i < 3; ++i) {
+          gSp[i] = G[G_SP + i];
+          gSq[i] = G[G_SQ + i];
         }
-        const float om = w * h;
-        float gom = G[G_W] + G[G_PP] * (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-        for (int r = 0; r < 3; ++r) {
-          const float Gx = G[G_QP + 3 * r] * x[0] + G[G_QP + 3 * r + 1] * x[1] + G[G_QP + 3 * r + 2] * x[2];
-          gom += G[G_SP + r] * x[r] + G[G_SQ + r] * y[r] + y[r] * Gx;
-          // direct: dL/dq' += om (gSq + gSqp x)
-          gq[r] += om * (G[G_SQ + r] + Gx);
-        }
-        for (int cc = 0; cc < 3; ++cc) {
-          // dL/dp' += om (gSp + 2 gSpp x + gSqp^T y)
-          const float Gy = G[G_QP + cc] * y[0] + G[G_QP + 3 + cc] * y[1] + G[G_QP + 6 + cc] * y[2];
-          gp[cc] += om * (G[G_SP + cc] + 2.f * G[G_PP] * x[cc] + Gy);
-        }
-        if (it == iters) {
-          const float* Ac = sh + (it - 1) * PER;
-          float f[3];
-          for (int r = 0; r < 3; ++r)
-            f[r] = Ac[3 * r] * x[0] + Ac[3 * r + 1] * x[1] + Ac[3 * r + 2] * x[2] + Ac[9 + r] - y[r];
-          gom += gJ * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) + gOm;
-          // cost residual: dL/de = 2 gJ om e
-          for (int r = 0; r < 3; ++r) {
-            const float ge = 2.f * gJ * om * f[r];
-            gq[r] -= ge;
-            for (int cc = 0; cc < 3; ++cc) gp[cc] += Ac[3 * r + cc] * ge;
+        for (int i = 0; i < 9; ++i) gQP[i] = G[G_QP + i];
+        float Ap[12];
+        if (it > 1)
+          for (int i = 0; i < 12; ++i) Ap[i] = sh[(it - 2) * PER + i];
+        float Ac[12];
+        if (it == iters)
+          for (int i = 0; i < 12; ++i) Ac[i] = sh[(it - 1) * PER + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float* X = x[j];
+          const float* Y = y[j];
+          float h = 1.f, e[3] = {0.f, 0.f, 0.f}, rr = 0.f, rs = 0.f;
+          if (it > 1) {
+            for (int r = 0; r < 3; ++r)
+              e[r] = Ap[3 * r] * X[0] + Ap[3 * r + 1] * X[1] + Ap[3 * r + 2] * X[2] + Ap[9 + r] - Y[r];
+            rr = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+            rs = rsqrtf(rr);
+            h = fminf(1.f, delta * rs);
           }
-        }
-        gw += gom * h;
-        if (it > 1 && rr > delta * delta) {
-          const float fct = -(gom * w) * delta * rsqrtf(rr) / rr;
+          const float om = w[j] * h;
+          float gom = gW + gPP * (X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
           for (int r = 0; r < 3; ++r) {
-            const float ge = fct * e[r];
-            gq[r] -= ge;
-            for (int cc = 0; cc < 3; ++cc) gp[cc] += Ap[3 * r + cc] * ge;
+            const float Gx = gQP[3 * r] * X[0] + gQP[3 * r + 1] * X[1] + gQP[3 * r + 2] * X[2];
+            gom += gSp[r] * X[r] + gSq[r] * Y[r] + Y[r] * Gx;
+            gq[j][r] += om * (gSq[r] + Gx);
+          }
+          for (int cc = 0; cc < 3; ++cc) {
+            const float Gy = gQP[cc] * Y[0] + gQP[3 + cc] * Y[1] + gQP[6 + cc] * Y[2];
+            gp[j][cc] += om * (gSp[cc] + 2.f * gPP * X[cc] + Gy);
+          }
+          if (it == iters) {
+            float f[3];
+            for (int r = 0; r < 3; ++r)
+              f[r] = Ac[3 * r] * X[0] + Ac[3 * r + 1] * X[1] + Ac[3 * r + 2] * X[2] + Ac[9 + r] - Y[r];
+            gom += gJ * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) + gOm;
+            const float s2 = 2.f * gJ * om;
+            for (int r = 0; r < 3; ++r) {
+              const float ge = s2 * f[r];
+              gq[j][r] -= ge;
+              for (int cc = 0; cc < 3; ++cc) gp[j][cc] += Ac[3 * r + cc] * ge;
+            }
+          }
+          gw[j] += gom * h;
+          if (it > 1 && rr > delta * delta) {
+            const float fct = -(gom * w[j]) * delta * rs * rs * rs;
+            for (int r = 0; r < 3; ++r) {
+              const float ge = fct * e[r];
+              gq[j][r] -= ge;
+              for (int cc = 0; cc < 3; ++cc) gp[j][cc] += Ap[3 * r + cc] * ge;
+            }
           }
         }
       }
     }
-    const float gcp = v ? (rule == 0 ? gw * cq : gw) : 0.f;
-    const float gcq = v ? (rule == 0 ? gw * cp : 0.f) : 0.f;
-    float* o = out + (size_t)i * 8;
-    if (ds) {
-      gxs[3 * i] = gp[0]; gxs[3 * i + 1] = gp[1]; gxs[3 * i + 2] = gp[2];
-      gcs[i] = gcp;
-    } else {
-      o[0] = gp[0]; o[1] = gp[1]; o[2] = gp[2]; o[6] = gcp;
+    float gcp[4], gcq[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      gcp[j] = val[j] ? (rule == 0 ? gw[j] * cqr[j] : gw[j]) : 0.f;
+      gcq[j] = val[j] ? (rule == 0 ? gw[j] * cpr[j] : 0.f) : 0.f;
     }
-    if (dt) {
-      gxt[3 * i] = gq[0]; gxt[3 * i + 1] = gq[1]; gxt[3 * i + 2] = gq[2];
-      gct[i] = gcq;
+    if (VEC && n == 4 && ds) {
+      float4* o = reinterpret_cast<float4*>(gxs + 3 * i0);
+      o[0] = make_float4(gp[0][0], gp[0][1], gp[0][2], gp[1][0]);
+      o[1] = make_float4(gp[1][1], gp[1][2], gp[2][0], gp[2][1]);
+      o[2] = make_float4(gp[2][2], gp[3][0], gp[3][1], gp[3][2]);
+      *reinterpret_cast<float4*>(gcs + i0) = make_float4(gcp[0], gcp[1], gcp[2], gcp[3]);
     } else {
-      o[3] = gq[0]; o[4] = gq[1]; o[5] = gq[2]; o[7] = gcq;
+      for (int j = 0; j < n; ++j) {
+        const int i = i0 + j;
+        if (ds) {
+          gxs[3 * i] = gp[j][0]; gxs[3 * i + 1] = gp[j][1]; gxs[3 * i + 2] = gp[j][2];
+          gcs[i] = gcp[j];
+        } else {
+          out[8 * i] = gp[j][0]; out[8 * i + 1] = gp[j][1]; out[8 * i + 2] = gp[j][2];
+          out[8 * i + 6] = gcp[j];
+        }
+      }
+    }
+    if (VEC && n == 4 && dt) {
+      float4* o = reinterpret_cast<float4*>(gxt + 3 * i0);
+      o[0] = make_float4(gq[0][0], gq[0][1], gq[0][2], gq[1][0]);
+      o[1] = make_float4(gq[1][1], gq[1][2], gq[2][0], gq[2][1]);
+      o[2] = make_float4(gq[2][2], gq[3][0], gq[3][1], gq[3][2]);
+      *reinterpret_cast<float4*>(gct + i0) = make_float4(gcq[0], gcq[1], gcq[2], gcq[3]);
+    } else {
+      for (int j = 0; j < n; ++j) {
+        const int i = i0 + j;
+        if (dt) {
+          gxt[3 * i] = gq[j][0]; gxt[3 * i + 1] = gq[j][1]; gxt[3 * i + 2] = gq[j][2];
+          gct[i] = gcq[j];
+        } else {
+          out[8 * i + 3] = gq[j][0]; out[8 * i + 4] = gq[j][1]; out[8 * i + 5] = gq[j][2];
+          out[8 * i + 7] = gcq[j];
+        }
+      }
     }
   }
 }
@@ -594,13 +670,13 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
   if (cost_path && n_tiles > 0)
     traced(ctx, s, "adj_reduce", [&] {
       if (vec)
-        k_adj_reduce<0, true><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt,
-                                                       link_pair, state, adj, ckpt, gM, iters,
-                                                       iters, delta, rule, part);
+        k_adj_reduce<0, false, true><<<grid, THREADS, 0, s>>>(
+            d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
+            iters, delta, rule, part);
       else
-        k_adj_reduce<0, false><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src,
-                                                        d_tgt, link_pair, state, adj, ckpt, gM,
-                                                        iters, iters, delta, rule, part);
+        k_adj_reduce<0, false, false><<<grid, THREADS, 0, s>>>(
+            d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
+            iters, delta, rule, part);
     });
   traced(ctx, s, "adj_solve", [&] {
     k_adj_solve<<<solve_blocks, 32, 0, s>>>(n_pairs, iters, iters, d_link_off, (int)tpl, part,
@@ -609,14 +685,23 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
   for (int k = iters; k >= 2; --k) {
     if (n_tiles > 0)
       traced(ctx, s, "adj_reduce", [&] {
-        if (vec)
-          k_adj_reduce<1, true><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src,
-                                                         d_tgt, link_pair, state, adj, ckpt, gM,
-                                                         iters, k, delta, rule, part);
+        const bool last = k == iters;
+        if (vec && last)
+          k_adj_reduce<1, true, true><<<grid, THREADS, 0, s>>>(
+              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
+              k, delta, rule, part);
+        else if (vec)
+          k_adj_reduce<1, false, true><<<grid, THREADS, 0, s>>>(
+              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
+              k, delta, rule, part);
+        else if (last)
+          k_adj_reduce<1, true, false><<<grid, THREADS, 0, s>>>(
+              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
+              k, delta, rule, part);
         else
-          k_adj_reduce<1, false><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src,
-                                                          d_tgt, link_pair, state, adj, ckpt, gM,
-                                                          iters, k, delta, rule, part);
+          k_adj_reduce<1, false, false><<<grid, THREADS, 0, s>>>(
+              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
+              k, delta, rule, part);
       });
     traced(ctx, s, "adj_solve", [&] {
       k_adj_solve<<<solve_blocks, 32, 0, s>>>(n_pairs, iters, k - 1, d_link_off, (int)tpl, part,

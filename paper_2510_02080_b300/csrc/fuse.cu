@@ -97,6 +97,10 @@ __global__ void __launch_bounds__(1024) k_fuse_scan(const int32_t* __restrict__ 
   if (threadIdx.x == 0) *cursor = carry;
 }
 
+// One CTA per tile, rounds of 1024 points (4 per thread).  The confidences and
+// the points of a round are loaded together, the next round's loads are in
+// flight while the current one is compacted, and each round's kept points are
+// staged in shared memory and written with coalesced stores.
 template <bool VEC>
 __global__ void __launch_bounds__(THREADS) k_fuse_scatter(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t n, int tps,
@@ -112,6 +116,8 @@ __global__ void __launch_bounds__(THREADS) k_fuse_scatter(
   const int npx = rem < TILE ? (int)rem : TILE;
   __shared__ float A[12];
   __shared__ int wcnt[THREADS / 32];
+  __shared__ float sx[3 * ROUND];
+  __shared__ int64_t sidx[ROUND];
   if (threadIdx.x < 12) {
     const ec3r_sim3& P = poses[m];
     const int r = threadIdx.x / 4, col = threadIdx.x % 4;
@@ -124,31 +130,34 @@ __global__ void __launch_bounds__(THREADS) k_fuse_scatter(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t pos = tile_off[t];
   bool overflow = false;
-  for (int r0 = 0; r0 < npx; r0 += ROUND) {
+
+  float cf[4], p[12];
+  auto load = [&](int r0) {
     const int i0 = r0 + 4 * threadIdx.x;
-    float cf[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
-    float p[12];
     if (VEC && i0 + 4 <= npx) {
       const float4 v = __ldcs(reinterpret_cast<const float4*>(conf + base + i0));
+      const float4* X = reinterpret_cast<const float4*>(xyz + 3 * (base + i0));
+      const float4 u = __ldcs(X), w = __ldcs(X + 1), z = __ldcs(X + 2);
       cf[0] = v.x; cf[1] = v.y; cf[2] = v.z; cf[3] = v.w;
+      p[0] = u.x; p[1] = u.y; p[2] = u.z; p[3] = u.w; p[4] = w.x; p[5] = w.y;
+      p[6] = w.z; p[7] = w.w; p[8] = z.x; p[9] = z.y; p[10] = z.z; p[11] = z.w;
     } else {
-      for (int j = 0; j < 4; ++j)
-        if (i0 + j < npx) cf[j] = conf[base + i0 + j];
-    }
-    unsigned km = 0;
-    for (int j = 0; j < 4; ++j) km |= (i0 + j < npx && keep(cf[j], thr)) ? (1u << j) : 0u;
-    if (km) {
-      if (VEC && i0 + 4 <= npx) {
-        const float4* X = reinterpret_cast<const float4*>(xyz + 3 * (base + i0));
-        const float4 u = __ldcs(X), v = __ldcs(X + 1), w = __ldcs(X + 2);
-        p[0] = u.x; p[1] = u.y; p[2] = u.z; p[3] = u.w; p[4] = v.x; p[5] = v.y;
-        p[6] = v.z; p[7] = v.w; p[8] = w.x; p[9] = w.y; p[10] = w.z; p[11] = w.w;
-      } else {
-        for (int j = 0; j < 4; ++j)
-          if (km & (1u << j))
-            for (int d = 0; d < 3; ++d) p[3 * j + d] = xyz[3 * (base + i0 + j) + d];
+      for (int j = 0; j < 4; ++j) {
+        const bool in = i0 + j < npx;
+        cf[j] = in ? conf[base + i0 + j] : -FLT_MAX;
+        for (int d = 0; d < 3; ++d) p[3 * j + d] = in ? xyz[3 * (base + i0 + j) + d] : 0.f;
       }
     }
+  };
+  if (npx > 0) load(0);
+  for (int r0 = 0; r0 < npx; r0 += ROUND) {
+    const int i0 = r0 + 4 * threadIdx.x;
+    float ccf[4], cp[12];
+    for (int j = 0; j < 4; ++j) ccf[j] = cf[j];
+    for (int j = 0; j < 12; ++j) cp[j] = p[j];
+    if (r0 + ROUND < npx) load(r0 + ROUND);  // next round in flight
+    unsigned km = 0;
+    for (int j = 0; j < 4; ++j) km |= (i0 + j < npx && keep(ccf[j], thr)) ? (1u << j) : 0u;
     const int cnt = __popc(km);
     int x = cnt;  // inclusive warp scan of counts (thread order = point order)
     for (int o = 1; o < 32; o <<= 1) {
@@ -163,24 +172,29 @@ __global__ void __launch_bounds__(THREADS) k_fuse_scatter(
       wbefore += w < warp ? v : 0;
       total += v;
     }
-    int64_t o = pos + wbefore + (x - cnt);
+    int q = wbefore + (x - cnt);  // slot of this thread's first kept point in the round
     for (int j = 0; j < 4; ++j) {
       if (!(km & (1u << j))) continue;
-      if (o >= 0 && o < capacity) {
-        const float x0 = p[3 * j], x1 = p[3 * j + 1], x2 = p[3 * j + 2];
-        out_xyz[3 * o + 0] = fmaf(a00, x0, fmaf(a01, x1, fmaf(a02, x2, a03)));
-        out_xyz[3 * o + 1] = fmaf(a10, x0, fmaf(a11, x1, fmaf(a12, x2, a13)));
-        out_xyz[3 * o + 2] = fmaf(a20, x0, fmaf(a21, x1, fmaf(a22, x2, a23)));
-        out_idx[o] = index_base + base + i0 + j;
-      } else {
-        overflow = true;
-      }
-      ++o;
+      const float x0 = cp[3 * j], x1 = cp[3 * j + 1], x2 = cp[3 * j + 2];
+      sx[3 * q + 0] = fmaf(a00, x0, fmaf(a01, x1, fmaf(a02, x2, a03)));
+      sx[3 * q + 1] = fmaf(a10, x0, fmaf(a11, x1, fmaf(a12, x2, a13)));
+      sx[3 * q + 2] = fmaf(a20, x0, fmaf(a21, x1, fmaf(a22, x2, a23)));
+      sidx[q] = index_base + base + i0 + j;
+      ++q;
     }
+    __syncthreads();
+    // coalesced write-out of the round's kept points at [pos, pos + total)
+    int64_t lim = pos < 0 ? 0 : capacity - pos;  // points that still fit (none past a bad cursor)
+    if (lim < 0) lim = 0;
+    const int nw = (int)(total < lim ? total : lim);
+    if (nw < total) overflow = true;
+    float* ox = out_xyz + 3 * pos;
+    for (int i = threadIdx.x; i < 3 * nw; i += THREADS) ox[i] = sx[i];
+    for (int i = threadIdx.x; i < nw; i += THREADS) out_idx[pos + i] = sidx[i];
     pos += total;
     __syncthreads();
   }
-  if (overflow) atomicOr(flags, FLAG_CAPACITY);
+  if (overflow && threadIdx.x == 0) atomicOr(flags, FLAG_CAPACITY);
 }
 
 }  // namespace fuse
