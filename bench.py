@@ -281,12 +281,37 @@ def run_ours(args):
     prof = ctx.profile_read()
     ctx.profile(False)
     assert ctx.sync_status() == 0, ctx.last_error()
+    # ---- comparator: the plain single-pair FP64-accumulation path, looped over
+    # the same pairs (one call per pair, direct launches) ----------------------
+    comparator = None
+    if not args.no_comparator and rank == 0:
+        one = torch.tensor([0, 1], dtype=torch.int32, device=dev)
+        S1 = torch.empty((1, 13), dtype=torch.float64, device=dev)
+        st1 = torch.empty((1,), dtype=torch.int32, device=dev)
+        xyz_b, conf_b = ch.xyz.view(n_frames, hw, 3), ch.conf.view(n_frames, hw)
+        ctx.profile(True)
+
+        def loop_pairs():
+            for k in range(ps.n_pairs):
+                ctx.align_submaps(xyz_b, conf_b, one, ps.src[k:k + 1], ps.tgt[k:k + 1],
+                                  delta=DELTA, iters=ITERS, precision="fp64", out=S1, status=st1)
+        loop_pairs()
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(s)
+        loop_pairs()
+        c1.record(s)
+        torch.cuda.synchronize()
+        ctx.profile_read()
+        ctx.profile(False)
+        cms = c0.elapsed_time(c1)
+        comparator = {"impl": "single-pair FP64-accumulation registration, looped over the "
+                              "199 pairs (same inputs, same kernels' FP64 mode)",
+                      "pt_iter_per_s": n_valid * ITERS / (cms * 1e-3), "ms": cms}
     ms_max = ms
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t)
+        from paper_2510_02080_b300 import shard
+        ms_max = shard.max_over_ranks(ms)
     value = n_valid * ITERS * args.steps * ws / (ms_max * 1e-3)
 
     # ---- end to end: host buffers, copies inside the timed region ------------
@@ -375,6 +400,7 @@ def run_ours(args):
                          "pt_iter_per_s": n_valid * ITERS * args.steps / (reg_ms * 1e-3)
                          if reg_ms else None},
         "clocks": clk,
+        "comparator": comparator,
         "gpu_launches": int(sum(v[1] for v in prof.values())),
     }
     if e2e:
@@ -390,6 +416,146 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------
+# the other workloads (one JSON line each; not the benchmark line)
+# ----------------------------------------------------------------------------
+def _time(fn, reps, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(reps):
+        fn()
+    b.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _valid_count(ps, pcm=None):
+    import torch
+    fin = torch.isfinite(ps.xyz).all(-1) & torch.isfinite(ps.conf)
+    lo = ps.link_off.cpu().tolist()
+    n = 0
+    for k in range(ps.n_pairs):
+        thr = 0.0 if pcm is None else float(pcm[k])
+        for l in range(lo[k], lo[k + 1]):
+            a, b = int(ps.src[l]), int(ps.tgt[l])
+            n += int((fin[a] & fin[b] & (ps.conf[a] > thr) & (ps.conf[b] > thr)).sum())
+    return n
+
+
+def run_workload(args):
+    import numpy as np
+    import torch
+    from paper_2510_02080_b300 import build, ec3r, synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    ctx = ec3r.Context(0)
+    peak, peak_kind = peaks()
+    out = {"workload": args.workload, "unit": UNIT, "data": "synthetic"}
+
+    def reg_rate(ps, precision="fp32c", reps=5):
+        n_valid = _valid_count(ps, ps.pair_conf_min)
+        S = torch.empty((ps.n_pairs, 13), dtype=torch.float64, device=dev)
+        st = torch.empty((ps.n_pairs,), dtype=torch.int32, device=dev)
+        ms = _time(lambda: ctx.align_submaps(ps.xyz, ps.conf, ps.link_off, ps.src, ps.tgt,
+                                             ps.pair_conf_min, delta=DELTA, iters=ITERS,
+                                             precision=precision, out=S, status=st), reps)
+        assert ctx.sync_status() == 0, ctx.last_error()
+        return n_valid, ms, S, st
+
+    if args.workload == "pair1":
+        ps = synth.make_pair(synth.SEED_BASE + 1, H=294, W=518, sigma=0.005, device=dev)
+        for prec in ("fp64", "fp32c"):
+            n, ms, S, st = reg_rate(ps, prec, reps=50)
+            out[prec] = {"pt_iter_per_s": n * ITERS / (ms * 1e-3), "ms_per_call": ms,
+                         "valid": n}
+        out["note"] = "one 294x518 pair, 10 IRLS solves: latency-bound (4.9 MB, L2-resident)"
+    elif args.workload == "adjoint1":
+        ps = synth.make_pair(synth.SEED_BASE + 4, H=294, W=518, sigma=0.005, device=dev)
+        n, ms_f, S, st = reg_rate(ps, reps=50)
+        gS = torch.randn((1, 13), dtype=torch.float64, device=dev)
+        gc = torch.ones((1,), dtype=torch.float64, device=dev)
+        cost = torch.empty((1,), dtype=torch.float64, device=dev)
+
+        def fwd_bwd():
+            ctx.align_submaps(ps.xyz, ps.conf, ps.link_off, ps.src, ps.tgt, want_cost=True,
+                              out=S, status=st, cost=cost)
+            ctx.align_submaps_backward(ps.xyz, ps.conf, ps.link_off, ps.src, ps.tgt, gS, gc)
+        ms = _time(fwd_bwd, 20)
+        out.update({"forward_ms": ms_f, "forward_backward_ms": ms, "valid": n,
+                    "note": "config-1 pair, 10 checkpointed IRLS iterations differentiated"})
+    elif args.workload == "loops512":
+        ps = synth.make_loop_batch(synth.SEED_BASE + 3, n_pairs=512, H=294, W=518, device=dev)
+        n, ms, S, st = reg_rate(ps, reps=5)
+        px = int(ps.link_off[-1]) * ps.hw
+        out["registration"] = {"pairs": 512, "valid": n, "ms": ms,
+                               "pt_iter_per_s": n * ITERS / (ms * 1e-3),
+                               "gbs_at_32B_per_pixel": 32.0 * px * ITERS / (ms * 1e-3) / 1e9}
+        g = synth.make_pose_graph(synth.SEED_BASE + 3, 200, 40, device="cpu")
+        Tij = ec3r.sim3_rows(g.T_meas.s, g.T_meas.R, g.T_meas.t).to(dev)
+        nodes = torch.zeros((200, 13), dtype=torch.float64, device=dev)
+        nodes[:, 0] = 1.0
+        nodes[:, [1, 5, 9]] = 1.0
+        pg_ms = _time(lambda: ctx.pose_graph_correct(nodes, g.ei.numpy(), g.ej.numpy(), Tij,
+                                                     iters=10), 5)
+        out["pose_graph"] = {"nodes": 200, "edges": len(g.ei), "gn_iters": 10, "ms": pg_ms}
+    elif args.workload == "map1000":
+        M = 1000
+        ch = synth.make_chain(synth.SEED_BASE + 5, M=M, F=5, H=392, W=518, device=dev)
+        lb = synth.make_loop_batch(synth.SEED_BASE + 55, n_pairs=300, H=392, W=518,
+                                   max_valid=760_000, device=dev)
+        cp = ch.pairs()
+        nf = cp.xyz.shape[0]
+        bank = synth.PairSet(torch.cat([cp.xyz, lb.xyz]), torch.cat([cp.conf, lb.conf]),
+                             torch.cat([cp.link_off[:-1], lb.link_off + int(cp.link_off[-1])]),
+                             torch.cat([cp.src, lb.src + nf]), torch.cat([cp.tgt, lb.tgt + nf]),
+                             392, 518,
+                             pair_conf_min=torch.cat([torch.zeros(cp.n_pairs, device=dev),
+                                                      lb.pair_conf_min]))
+        del lb
+        n, ms, S, st = reg_rate(bank, reps=3)
+        px = int(bank.link_off[-1]) * bank.hw
+        out["registration"] = {"pairs": bank.n_pairs, "valid": n, "ms": ms,
+                               "pt_iter_per_s": n * ITERS / (ms * 1e-3),
+                               "gbs_at_32B_per_pixel": 32.0 * px * ITERS / (ms * 1e-3) / 1e9}
+        del bank
+        g = synth.make_pose_graph(synth.SEED_BASE + 5, M, 300, device="cpu")
+        Tij = ec3r.sim3_rows(g.T_meas.s, g.T_meas.R, g.T_meas.t).to(dev)
+        nodes = torch.zeros((M, 13), dtype=torch.float64, device=dev)
+        nodes[:, 0] = 1.0
+        nodes[:, [1, 5, 9]] = 1.0
+        pg_ms = _time(lambda: ctx.pose_graph_correct(nodes, g.ei.numpy(), g.ej.numpy(), Tij,
+                                                     iters=10), 1, warm=1)
+        out["pose_graph"] = {"nodes": M, "edges": len(g.ei), "gn_iters": 10, "ms": pg_ms}
+        xyz = ch.xyz.view(M, -1, 3)
+        conf = ch.conf.view(M, -1)
+        kept = int((conf > 1.0).sum())
+        ox = torch.empty((kept, 3), device=dev)
+        oi = torch.empty((kept,), dtype=torch.int64, device=dev)
+        cur = torch.zeros((1,), dtype=torch.int64, device=dev)
+        poses = torch.zeros((M, 13), dtype=torch.float64, device=dev)
+        poses[:, 0] = 1.0
+        poses[:, [1, 5, 9]] = 1.0
+
+        def fuse():
+            cur.zero_()
+            ctx.fuse_points(xyz, conf, poses, ox, oi, cur)
+        fms = _time(fuse, 3)
+        assert ctx.sync_status() == 0 and int(cur) == kept
+        npts = conf.numel()
+        out["fusion"] = {"points": npts, "kept": kept, "ms": fms,
+                         "gbs_at_26B_per_point": 26.0 * npts / (fms * 1e-3) / 1e9}
+    out["peak_gbs"] = peak
+    out["peak_kind"] = peak_kind
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -398,6 +564,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--workload", default="chain200",
+                    choices=["chain200", "pair1", "loops512", "adjoint1", "map1000"],
+                    help="chain200 is the benchmark; the others measure the other workloads")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="leave the adjoint out of the step (profiling only)")
     ap.add_argument("--submaps", type=int, default=M_SUBMAPS,
@@ -411,6 +581,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "chain200":
+        run_workload(args)
     else:
         run_ours(args)
 

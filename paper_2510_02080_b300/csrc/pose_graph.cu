@@ -46,14 +46,16 @@ __device__ __forceinline__ void warp_mm7(const double* A, bool tA, const double*
                                          double* C, int lane) {
   for (int idx = lane; idx < NB; idx += 32) {
     const int r = idx / 7, c = idx % 7;
-    double s = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;  // independent partial sums: short FP64 chains
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
       const double a = tA ? A[7 * k + r] : A[7 * r + k];
       const double b = tB ? B[7 * c + k] : B[7 * k + c];
-      s = fma(a, b, s);
+      if (k % 3 == 0) s0 = fma(a, b, s0);
+      else if (k % 3 == 1) s1 = fma(a, b, s1);
+      else s2 = fma(a, b, s2);
     }
-    C[idx] = s;
+    C[idx] = (s0 + s1) + s2;
   }
   __syncwarp();
 }
@@ -408,13 +410,15 @@ __global__ void __launch_bounds__(32) k_pg_backsolve(const int* __restrict__ col
   const int lane = threadIdx.x;
   __shared__ double x[7];
   if (lane < 7) {
-    double s = bvec[7 * k + lane];
+    double s0 = bvec[7 * k + lane], s1 = 0.0;
     for (int p = col_ptr[k]; p < col_ptr[k + 1]; ++p) {
       const int i = off_row[p];
-      const double* Lik = L + (size_t)off_blk[p] * NB;
-      for (int t = 0; t < 7; ++t) s -= Lik[7 * t + lane] * bvec[7 * i + t];
+      const double* Lik = L + (size_t)off_blk[p] * NB + lane;
+      const double* xi = bvec + 7 * i;
+      s0 -= Lik[0] * xi[0] + Lik[14] * xi[2] + Lik[28] * xi[4] + Lik[42] * xi[6];
+      s1 -= Lik[7] * xi[1] + Lik[21] * xi[3] + Lik[35] * xi[5];
     }
-    x[lane] = s;
+    x[lane] = s0 + s1;
   }
   __syncwarp();
   if (lane == 0) {
