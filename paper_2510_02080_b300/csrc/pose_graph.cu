@@ -36,6 +36,7 @@ namespace pg {
 
 constexpr int NB = 49;
 constexpr int NBERN = 24;
+constexpr int SN_MIN = 8;  // smallest trailing supernode factored right-looking
 __constant__ double c_bern[NBERN];  // B_2k / (2k)!, k = 1..24
 
 // --------------------------------------------------------------------------
@@ -398,6 +399,176 @@ __global__ void __launch_bounds__(32 * FWARPS) k_pg_factor(
   }
 }
 
+// --------------------------------------------------------------------------
+// trailing dense supernode (the last ns columns, whose factor columns are full)
+// --------------------------------------------------------------------------
+// Updates of the supernode's blocks by the sparse columns below it: one warp
+// per destination block.
+__global__ void __launch_bounds__(32) k_pg_sn_assemble(const int* __restrict__ grp,
+                                                       const int* __restrict__ upd_ab, double* L) {
+  const int g = blockIdx.x;
+  apply_group(L, grp[3 * g], upd_ab + 2 * grp[3 * g + 1], grp[3 * g + 2], threadIdx.x);
+}
+
+__device__ __forceinline__ int sn_block(const int* col_ptr, const int* off_blk, int i, int j) {
+  return i == j ? j : off_blk[col_ptr[j] + (i - j - 1)];
+}
+
+// Panel k of the supernode: 7x7 Cholesky of the diagonal block, then the
+// triangular solve of every block below it (one block row per thread).
+__global__ void __launch_bounds__(256) k_pg_sn_panel(int k, int nf, const int* __restrict__ col_ptr,
+                                                     const int* __restrict__ off_blk, double* L,
+                                                     double* idiag, unsigned* flags, int* fail) {
+  __shared__ double D[NB];
+  __shared__ double inv[7];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* Lkk = L + (size_t)k * NB;
+  if (warp == 0) {
+    for (int idx = lane; idx < NB; idx += 32) D[idx] = Lkk[idx];
+    __syncwarp();
+    bool bad = false;
+    for (int c = 0; c < 7; ++c) {
+      const double d = D[8 * c];
+      if (!(d > 0.0) || !isfinite(d)) bad = true;
+      const double ip = rsqrt(fmax(d, 1e-300));
+      __syncwarp();
+      if (lane == 0) {
+        D[8 * c] = d * ip;
+        inv[c] = ip;
+      }
+      if (lane > c && lane < 7) D[7 * lane + c] *= ip;
+      __syncwarp();
+      for (int idx = lane; idx < NB; idx += 32) {
+        const int r = idx / 7, cc = idx % 7;
+        if (r > c && cc > c && cc <= r) D[idx] -= D[7 * r + c] * D[7 * cc + c];
+      }
+      __syncwarp();
+    }
+    if (bad && lane == 0) {
+      atomicOr(flags, FLAG_NOT_SPD);
+      atomicExch(fail, 1);
+    }
+    for (int idx = lane; idx < NB; idx += 32) Lkk[idx] = (idx % 7 <= idx / 7) ? D[idx] : 0.0;
+    if (lane < 7) idiag[7 * k + lane] = inv[lane];
+  }
+  __syncthreads();
+  const int nrows = (nf - 1 - k) * 7;
+  for (int q = threadIdx.x; q < nrows; q += blockDim.x) {
+    double* X = L + (size_t)off_blk[col_ptr[k] + q / 7] * NB + 7 * (q % 7);
+    double x[7];
+    for (int c = 0; c < 7; ++c) {
+      double s = X[c];
+      for (int t = 0; t < c; ++t) s -= x[t] * D[7 * c + t];
+      x[c] = s * inv[c];
+    }
+    for (int c = 0; c < 7; ++c) X[c] = x[c];
+  }
+}
+
+// Trailing update after panel k: L_ij -= L_ik L_jk^T for k < j <= i < nf, one
+// warp per block (triangular index).
+__global__ void __launch_bounds__(32) k_pg_sn_update(int k, const int* __restrict__ col_ptr,
+                                                     const int* __restrict__ off_blk, double* L) {
+  const int64_t t = blockIdx.x;
+  int ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
+  while ((int64_t)ii * (ii + 1) / 2 > t) --ii;
+  const int jj = (int)(t - (int64_t)ii * (ii + 1) / 2);
+  const int i = k + 1 + ii, j = k + 1 + jj;
+  double* Dst = L + (size_t)sn_block(col_ptr, off_blk, i, j) * NB;
+  const double* A = L + (size_t)off_blk[col_ptr[k] + (i - k - 1)] * NB;
+  const double* B = L + (size_t)off_blk[col_ptr[k] + (j - k - 1)] * NB;
+  for (int idx = threadIdx.x; idx < NB; idx += 32) {
+    const int r = idx / 7, c = idx % 7;
+    double s0 = 0.0, s1 = 0.0;
+    s0 = fma(A[7 * r + 0], B[7 * c + 0], s0);
+    s1 = fma(A[7 * r + 1], B[7 * c + 1], s1);
+    s0 = fma(A[7 * r + 2], B[7 * c + 2], s0);
+    s1 = fma(A[7 * r + 3], B[7 * c + 3], s1);
+    s0 = fma(A[7 * r + 4], B[7 * c + 4], s0);
+    s1 = fma(A[7 * r + 5], B[7 * c + 5], s1);
+    s0 = fma(A[7 * r + 6], B[7 * c + 6], s0);
+    Dst[idx] -= s0 + s1;
+  }
+}
+
+// Forward substitution over the supernode columns (one CTA, in column order):
+// y_k = Lkk^-1 (b_k - sum_j L_kj y_j) over every earlier column j.
+__global__ void __launch_bounds__(256) k_pg_sn_forward(int sn0, int nf,
+                                                       const int* __restrict__ row_ptr,
+                                                       const int* __restrict__ row_it,
+                                                       const double* __restrict__ L,
+                                                       const double* __restrict__ idiag,
+                                                       double* bvec) {
+  __shared__ double red[8][7];
+  __shared__ double y[7];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = sn0; k < nf; ++k) {
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int p = row_ptr[k] + threadIdx.x; p < row_ptr[k + 1]; p += blockDim.x) {
+      const int j = row_it[2 * p];
+      const double* Lkj = L + (size_t)row_it[2 * p + 1] * NB;
+      const double* yj = bvec + 7 * j;
+      for (int r = 0; r < 7; ++r)
+        for (int t = 0; t < 7; ++t) acc[r] = fma(Lkj[7 * r + t], yj[t], acc[r]);
+    }
+    for (int r = 0; r < 7; ++r)
+      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (lane == 0)
+      for (int r = 0; r < 7; ++r) red[warp][r] = acc[r];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double* D = L + (size_t)k * NB;
+      for (int c = 0; c < 7; ++c) {
+        double s = bvec[7 * k + c];
+        for (int w = 0; w < 8; ++w) s -= red[w][c];
+        for (int t = 0; t < c; ++t) s -= D[7 * c + t] * y[t];
+        y[c] = s * idiag[7 * k + c];
+      }
+      for (int c = 0; c < 7; ++c) bvec[7 * k + c] = y[c];
+    }
+    __syncthreads();
+  }
+}
+
+// Back substitution over the supernode (one CTA, last column first):
+// x_k = Lkk^-T (y_k - sum_{i > k} L_ik^T x_i).
+__global__ void __launch_bounds__(256) k_pg_sn_backward(int sn0, int nf,
+                                                        const int* __restrict__ col_ptr,
+                                                        const int* __restrict__ off_blk,
+                                                        const double* __restrict__ L,
+                                                        const double* __restrict__ idiag,
+                                                        double* bvec) {
+  __shared__ double red[8][7];
+  __shared__ double x[7];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = nf - 1; k >= sn0; --k) {
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int i = k + 1 + threadIdx.x; i < nf; i += blockDim.x) {
+      const double* Lik = L + (size_t)off_blk[col_ptr[k] + (i - k - 1)] * NB;
+      const double* xi = bvec + 7 * i;
+      for (int r = 0; r < 7; ++r)
+        for (int t = 0; t < 7; ++t) acc[r] = fma(Lik[7 * t + r], xi[t], acc[r]);
+    }
+    for (int r = 0; r < 7; ++r)
+      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (lane == 0)
+      for (int r = 0; r < 7; ++r) red[warp][r] = acc[r];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double* D = L + (size_t)k * NB;
+      for (int c = 6; c >= 0; --c) {
+        double s = bvec[7 * k + c];
+        for (int w = 0; w < 8; ++w) s -= red[w][c];
+        for (int t = c + 1; t < 7; ++t) s -= D[7 * t + c] * x[t];
+        x[c] = s * idiag[7 * k + c];
+      }
+      for (int c = 0; c < 7; ++c) bvec[7 * k + c] = x[c];
+    }
+    __syncthreads();
+  }
+}
+
 // back substitution, root to leaves: x_k = Lkk^-T (y_k - sum_i L_ik^T x_i)
 __global__ void __launch_bounds__(32) k_pg_backsolve(const int* __restrict__ cols,
                                                      const int* __restrict__ col_ptr,
@@ -453,7 +624,8 @@ struct Plan : Extension {
   std::vector<void*> allocs;
   int *d_ei = nullptr, *d_ej = nullptr, *d_perm = nullptr;
   int *d_col_ptr = nullptr, *d_off_row = nullptr, *d_off_blk = nullptr;
-  int *d_grp_ptr = nullptr, *d_grp = nullptr, *d_upd_ab = nullptr;
+  int *d_grp_ptr = nullptr, *d_grp = nullptr, *d_upd_ab = nullptr, *d_sn_grp = nullptr;
+  int sn0 = 0, n_sn_groups = 0;  // columns >= sn0 form the dense trailing supernode
   int *d_row_ptr = nullptr, *d_row = nullptr;
   int *d_level_cols = nullptr, *d_asm_ptr = nullptr, *d_asm = nullptr;
   int *d_g_ptr = nullptr, *d_g = nullptr;
@@ -535,21 +707,56 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   P.nf = nf;
   std::vector<int> inew(n, -1);
   for (int k = 0; k < nf; ++k) inew[perm[k]] = k;
-  // symbolic factorisation
-  std::vector<std::vector<int>> children(nf);
-  std::vector<std::set<int>> st(nf);
-  std::vector<int> parent(nf, -1);
-  for (int k = 0; k < nf; ++k) {
-    for (int u : adj[perm[k]]) {
-      const int q = inew[u];
-      if (q > k) st[k].insert(q);
-    }
-    for (int c : children[k])
-      for (int q : st[c])
+  // symbolic factorisation of the order `perm`: structure of every column,
+  // elimination tree
+  std::vector<std::vector<int>> children;
+  std::vector<std::set<int>> st;
+  std::vector<int> parent;
+  auto symbolic = [&]() {
+    for (int k = 0; k < nf; ++k) inew[perm[k]] = k;
+    children.assign(nf, {});
+    st.assign(nf, {});
+    parent.assign(nf, -1);
+    for (int k = 0; k < nf; ++k) {
+      for (int u : adj[perm[k]]) {
+        const int q = inew[u];
         if (q > k) st[k].insert(q);
-    if (!st[k].empty()) {
-      parent[k] = *st[k].begin();
-      children[parent[k]].push_back(k);
+      }
+      for (int c : children[k])
+        for (int q : st[c])
+          if (q > k) st[k].insert(q);
+      if (!st[k].empty()) {
+        parent[k] = *st[k].begin();
+        children[parent[k]].push_back(k);
+      }
+    }
+  };
+  symbolic();
+  // Columns at the top of the elimination tree that are alone in their level
+  // form a chain that would be factored one CTA at a time.  They are moved to
+  // the end of the order (eliminating these separator-like nodes last adds no
+  // fill elsewhere) and, with the root clique, become one dense supernode
+  // (explicit zero fill) factored right-looking across all SMs.
+  {
+    std::vector<int> lv(nf, 0), cnt(nf + 1, 0);
+    for (int k = 0; k < nf; ++k)
+      for (int c : children[k]) lv[k] = std::max(lv[k], lv[c] + 1);
+    for (int k = 0; k < nf; ++k) cnt[lv[k]]++;
+    std::vector<int> chain, rest;
+    for (int k = 0; k < nf; ++k) (cnt[lv[k]] == 1 ? chain : rest).push_back(k);
+    if ((int)chain.size() >= SN_MIN) {
+      const bool suffix = chain.front() == nf - (int)chain.size();
+      if (!suffix) {
+        std::vector<int> np;
+        for (int k : rest) np.push_back(perm[k]);
+        for (int k : chain) np.push_back(perm[k]);
+        perm = np;
+        symbolic();
+      }
+      for (int k = nf - (int)chain.size(); k < nf; ++k) {
+        st[k].clear();
+        for (int q = k + 1; q < nf; ++q) st[k].insert(q);
+      }
     }
   }
   // blocks: diagonal k -> k; off-diagonal numbered column by column
@@ -571,9 +778,18 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   std::vector<std::vector<int>> rowstruct(nf);
   for (int j = 0; j < nf; ++j)
     for (int k : st[j]) rowstruct[k].push_back(j);
+  // trailing dense supernode: the longest suffix of columns whose structure is
+  // every later column; it is factored right-looking across all SMs
+  int s0 = nf;
+  for (int k = nf - 1; k >= 0; --k) {
+    if ((int)st[k].size() != nf - 1 - k) break;
+    s0 = k;
+  }
+  P.sn0 = (nf - s0 >= SN_MIN) ? s0 : nf;
   // update groups: for every block (i, k) of column k, the products
-  // L_ij L_kj^T of its descendants j, in descendant order
-  std::vector<int> grp_ptr(nf + 1, 0), grp, upd_ab, row_ptr(nf + 1, 0), row;
+  // L_ij L_kj^T of its descendants j, in descendant order (for supernode
+  // columns only the descendants below the supernode, gathered in sn_grp)
+  std::vector<int> grp_ptr(nf + 1, 0), grp, upd_ab, row_ptr(nf + 1, 0), row, sn_grp;
   for (int k = 0; k < nf; ++k) {
     grp_ptr[k] = (int)grp.size() / 3;
     row_ptr[k] = (int)row.size() / 2;
@@ -581,18 +797,21 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
     std::vector<int> targets;
     targets.push_back(k);
     for (int r : st[k]) targets.push_back(r);
+    const bool in_sn = k >= P.sn0;
     for (int i : targets) {
       const int first = (int)upd_ab.size() / 2;
       for (int j : rowstruct[k]) {
+        if (in_sn && j >= P.sn0) continue;  // supernode columns update right-looking
         if (i != k && !st[j].count(i)) continue;
         upd_ab.push_back(blk(i, j));
         upd_ab.push_back(blk(k, j));
       }
       const int n_upd = (int)upd_ab.size() / 2 - first;
       if (n_upd > 0) {
-        grp.push_back(blk(i, k));
-        grp.push_back(first);
-        grp.push_back(n_upd);
+        std::vector<int>& G = in_sn ? sn_grp : grp;
+        G.push_back(blk(i, k));
+        G.push_back(first);
+        G.push_back(n_upd);
       }
     }
     for (int j : rowstruct[k]) {
@@ -602,18 +821,20 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   }
   grp_ptr[nf] = (int)grp.size() / 3;
   row_ptr[nf] = (int)row.size() / 2;
-  // levels (height in the elimination tree)
+  // levels (height in the elimination tree) of the columns below the supernode
+  const int nsp = P.sn0;
   std::vector<int> level(nf, 0);
   int nlev = 0;
-  for (int k = 0; k < nf; ++k) {
+  for (int k = 0; k < nsp; ++k) {
     for (int c : children[k]) level[k] = std::max(level[k], level[c] + 1);
     nlev = std::max(nlev, level[k] + 1);
   }
   P.level_ptr.assign(nlev + 1, 0);
-  for (int k = 0; k < nf; ++k) P.level_ptr[level[k] + 1]++;
+  for (int k = 0; k < nsp; ++k) P.level_ptr[level[k] + 1]++;
   for (int l = 0; l < nlev; ++l) P.level_ptr[l + 1] += P.level_ptr[l];
-  std::vector<int> level_cols(nf), fill = P.level_ptr;
-  for (int k = 0; k < nf; ++k) level_cols[fill[level[k]]++] = k;
+  std::vector<int> level_cols(std::max(nsp, 1)), fill = P.level_ptr;
+  for (int k = 0; k < nsp; ++k) level_cols[fill[level[k]]++] = k;
+  P.n_sn_groups = (int)sn_grp.size() / 3;
   // assembly lists: kind 0 = Cii, 1 = Cjj, 2 = Cij, 3 = Cij^T
   std::vector<std::vector<int>> asmv(nb), gv(nf);
   for (int e = 0; e < m; ++e) {
@@ -692,6 +913,7 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   chk(upload(P, &P.d_off_blk, off_blk));
   chk(upload(P, &P.d_grp_ptr, grp_ptr));
   chk(upload(P, &P.d_grp, grp));
+  chk(upload(P, &P.d_sn_grp, sn_grp));
   chk(upload(P, &P.d_upd_ab, upd_ab));
   chk(alloc(P, &P.d_idiag, (size_t)nf * 7));
   chk(upload(P, &P.d_row_ptr, row_ptr));
@@ -868,6 +1090,31 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
               P->d_grp, P->d_upd_ab, P->d_row_ptr, P->d_row, P->d_L, P->d_b, P->d_idiag,
               ctx->d_flags, P->d_fail);
         });
+      if (P->sn0 < P->nf) {
+        const int nf = P->nf;
+        if (P->n_sn_groups > 0)
+          traced(ctx, cs, "pg_sn_assemble", [&] {
+            k_pg_sn_assemble<<<P->n_sn_groups, 32, 0, cs>>>(P->d_sn_grp, P->d_upd_ab, P->d_L);
+          });
+        for (int k = P->sn0; k < nf; ++k) {
+          traced(ctx, cs, "pg_sn_panel", [&] {
+            k_pg_sn_panel<<<1, 256, 0, cs>>>(k, nf, P->d_col_ptr, P->d_off_blk, P->d_L,
+                                             P->d_idiag, ctx->d_flags, P->d_fail);
+          });
+          const int64_t mrem = nf - 1 - k;
+          if (mrem > 0)
+            traced(ctx, cs, "pg_sn_update", [&] {
+              k_pg_sn_update<<<(unsigned)(mrem * (mrem + 1) / 2), 32, 0, cs>>>(
+                  k, P->d_col_ptr, P->d_off_blk, P->d_L);
+            });
+        }
+        traced(ctx, cs, "pg_sn_solve", [&] {
+          k_pg_sn_forward<<<1, 256, 0, cs>>>(P->sn0, nf, P->d_row_ptr, P->d_row, P->d_L,
+                                             P->d_idiag, P->d_b);
+          k_pg_sn_backward<<<1, 256, 0, cs>>>(P->sn0, nf, P->d_col_ptr, P->d_off_blk, P->d_L,
+                                              P->d_idiag, P->d_b);
+        });
+      }
       for (int l = nlev - 1; l >= 0; --l)
         traced(ctx, cs, "pg_backsolve", [&] {
           k_pg_backsolve<<<P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs>>>(
