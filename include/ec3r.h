@@ -255,7 +255,8 @@ void ec3r_pg_opts_default(ec3r_pg_opts* o);
  *
  * Structure.  h_i, h_j (int32 [n_edges], HOST) give each edge's endpoints,
  * in [0, n_nodes) and distinct.  The structure is analysed on the host once
- * (nested-dissection ordering, block fill of the Cholesky factor) and cached
+ * (nested-dissection or minimum-degree ordering, whichever is estimated
+ * cheaper; block fill of the Cholesky factor) and cached
  * in the context; a call with a new structure allocates and must not be made
  * during stream capture (EC3R_ERR_CAPTURE).  The first pose-graph call of a
  * context also uploads a constant table.

@@ -332,9 +332,28 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
 // 8 floats per pixel: dp(3), dq(3), dc_p, dc_q).
 // A side whose frame no other link references writes straight into the frame
 // gradients; a shared frame's side goes to the link buffer and is summed by
-// k_adj_frames in link order.  Each thread owns 4 consecutive pixels; the
-// per-iteration constants are read once per 4 pixels; invalid pixels carry
-// zero weight and zero coordinates, so every term they add is zero.
+// k_adj_frames in link order.  Invalid pixels carry zero weight and zero
+// coordinates, so every term they add is zero.
+//
+// Iteration k's moments are sums of om_k phi(p, q) with phi = (1, p, q, |p|^2,
+// q p^T) and om_k = w h_k(r_k).  The part of the gradient that holds om_k fixed
+// is linear in the moment adjoints, so it is accumulated as one 17-vector
+// Gt = sum_k om_k gM_k and differentiated once at the end; per iteration a
+// pixel only evaluates gom_k = <gM_k, phi> (for the weight and the Huber
+// branch) and adds om_k gM_k to Gt.
+//
+// Each thread owns 2 consecutive pixels and carries them as the two lanes of
+// packed FP32 pairs (one f32x2 instruction does both pixels' multiply-adds, each
+// lane rounded exactly like the scalar operation).  The per-iteration constants
+// sit in shared memory as duplicated pairs, so a 16-byte load yields two
+// broadcast operands.
+constexpr int SC_PAIRS = 32;  // float2 per iteration: A 9, b 3, gM 17, 3 pad
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
 template <bool VEC>
 __global__ void __launch_bounds__(THREADS, 2) k_adj_scatter(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
@@ -359,48 +378,47 @@ __global__ void __launch_bounds__(THREADS, 2) k_adj_scatter(
   float* gcs = gconf + fs * hw + px0;
   float* gct = gconf + ft * hw + px0;
   const bool active = adj[k].active;
-  constexpr int PER = 29;  // per iteration: A(9) b(3) gM(17)
-  extern __shared__ float sh[];
+  extern __shared__ float4 sh4[];
+  float2* sh2 = reinterpret_cast<float2*>(sh4);
   if (active) {
     const double* ckb = ckpt + (size_t)k * iters * CKPT;
-    for (int i = threadIdx.x; i < iters * PER; i += THREADS) {
-      const int it = i / PER, f = i % PER;
-      float v;
+    for (int i = threadIdx.x; i < iters * SC_PAIRS; i += THREADS) {
+      const int it = i / SC_PAIRS, f = i % SC_PAIRS;
+      float v = 0.f;
       if (f < 9) v = (float)ckb[it * CKPT + CK_A + f];
       else if (f < 12) v = (float)ckb[it * CKPT + CK_B + (f - 9)];
-      else v = (float)gM[((size_t)k * iters + it) * NGM + (f - 12)];
-      sh[i] = v;
+      else if (f < 12 + NGM) v = (float)gM[((size_t)k * iters + it) * NGM + (f - 12)];
+      sh2[i] = f2(v);
     }
   }
   __syncthreads();
   const float gJ = active ? (float)adj[k].gJ : 0.f, gOm = active ? (float)adj[k].gOm : 0.f;
-  const float pp0 = st[k].piv_p[0], pp1 = st[k].piv_p[1], pp2 = st[k].piv_p[2];
-  const float pq0 = st[k].piv_q[0], pq1 = st[k].piv_q[1], pq2 = st[k].piv_q[2];
+  const float piv[6] = {st[k].piv_p[0], st[k].piv_p[1], st[k].piv_p[2],
+                        st[k].piv_q[0], st[k].piv_q[1], st[k].piv_q[2]};
   const float cmin = st[k].cmin;
+  const float d2 = delta * delta;
   const float* P = xyz + (fs * hw + px0) * 3;
   const float* Q = xyz + (ft * hw + px0) * 3;
   const float* CP = conf + fs * hw + px0;
   const float* CQ = conf + ft * hw + px0;
-  for (int g = threadIdx.x; g < TILE / 4; g += THREADS) {
-    const int i0 = 4 * g;
+  for (int g = threadIdx.x; g < TILE / 2; g += THREADS) {
+    const int i0 = 2 * g;
     if (i0 >= npx) break;
-    const int n = min(4, npx - i0);
-    float pr[12], qr[12], cpr[4], cqr[4];
-    if (VEC && n == 4) {
-      const float4* P4 = reinterpret_cast<const float4*>(P + 3 * i0);
-      const float4* Q4 = reinterpret_cast<const float4*>(Q + 3 * i0);
-      const float4 a = __ldcs(P4), b = __ldcs(P4 + 1), cc = __ldcs(P4 + 2);
-      const float4 d = __ldcs(Q4), e = __ldcs(Q4 + 1), f = __ldcs(Q4 + 2);
-      const float4 u = __ldcs(reinterpret_cast<const float4*>(CP + i0));
-      const float4 v = __ldcs(reinterpret_cast<const float4*>(CQ + i0));
-      pr[0] = a.x; pr[1] = a.y; pr[2] = a.z; pr[3] = a.w; pr[4] = b.x; pr[5] = b.y;
-      pr[6] = b.z; pr[7] = b.w; pr[8] = cc.x; pr[9] = cc.y; pr[10] = cc.z; pr[11] = cc.w;
-      qr[0] = d.x; qr[1] = d.y; qr[2] = d.z; qr[3] = d.w; qr[4] = e.x; qr[5] = e.y;
-      qr[6] = e.z; qr[7] = e.w; qr[8] = f.x; qr[9] = f.y; qr[10] = f.z; qr[11] = f.w;
-      cpr[0] = u.x; cpr[1] = u.y; cpr[2] = u.z; cpr[3] = u.w;
-      cqr[0] = v.x; cqr[1] = v.y; cqr[2] = v.z; cqr[3] = v.w;
+    const int n = min(2, npx - i0);
+    float pr[6], qr[6], cpr[2], cqr[2];
+    if (VEC && n == 2) {
+      const float2* P2 = reinterpret_cast<const float2*>(P + 3 * i0);
+      const float2* Q2 = reinterpret_cast<const float2*>(Q + 3 * i0);
+      const float2 a = __ldcs(P2), b = __ldcs(P2 + 1), cc = __ldcs(P2 + 2);
+      const float2 d = __ldcs(Q2), e = __ldcs(Q2 + 1), f = __ldcs(Q2 + 2);
+      const float2 u = __ldcs(reinterpret_cast<const float2*>(CP + i0));
+      const float2 v = __ldcs(reinterpret_cast<const float2*>(CQ + i0));
+      pr[0] = a.x; pr[1] = a.y; pr[2] = b.x; pr[3] = b.y; pr[4] = cc.x; pr[5] = cc.y;
+      qr[0] = d.x; qr[1] = d.y; qr[2] = e.x; qr[3] = e.y; qr[4] = f.x; qr[5] = f.y;
+      cpr[0] = u.x; cpr[1] = u.y;
+      cqr[0] = v.x; cqr[1] = v.y;
     } else {
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < 2; ++j) {
         const bool in = j < n;
         for (int dd = 0; dd < 3; ++dd) {
           pr[3 * j + dd] = in ? P[3 * (i0 + j) + dd] : 0.f;
@@ -410,126 +428,155 @@ __global__ void __launch_bounds__(THREADS, 2) k_adj_scatter(
         cqr[j] = in ? CQ[i0 + j] : 0.f;
       }
     }
-    float x[4][3], y[4][3], w[4], gp[4][3], gq[4][3], gw[4];
-    bool val[4];
+    // lane j of every pair is pixel i0 + j
+    float2 X[3], Y[3], W, XX;
+    bool val[2];
+    {
+      float xs[2][3], ys[2][3], ws[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const bool v = active && j < n && finitef(pr[3 * j]) && finitef(pr[3 * j + 1]) &&
-                     finitef(pr[3 * j + 2]) && finitef(qr[3 * j]) && finitef(qr[3 * j + 1]) &&
-                     finitef(qr[3 * j + 2]) && finitef(cpr[j]) && finitef(cqr[j]) &&
-                     cpr[j] > cmin && cqr[j] > cmin;
-      val[j] = v;
-      x[j][0] = v ? pr[3 * j] - pp0 : 0.f;
-      x[j][1] = v ? pr[3 * j + 1] - pp1 : 0.f;
-      x[j][2] = v ? pr[3 * j + 2] - pp2 : 0.f;
-      y[j][0] = v ? qr[3 * j] - pq0 : 0.f;
-      y[j][1] = v ? qr[3 * j + 1] - pq1 : 0.f;
-      y[j][2] = v ? qr[3 * j + 2] - pq2 : 0.f;
-      w[j] = v ? (rule == 0 ? cpr[j] * cqr[j] : cpr[j]) : 0.f;
-      gp[j][0] = gp[j][1] = gp[j][2] = 0.f;
-      gq[j][0] = gq[j][1] = gq[j][2] = 0.f;
-      gw[j] = 0.f;
+      for (int j = 0; j < 2; ++j) {
+        const bool v = active && j < n && finitef(pr[3 * j]) && finitef(pr[3 * j + 1]) &&
+                       finitef(pr[3 * j + 2]) && finitef(qr[3 * j]) && finitef(qr[3 * j + 1]) &&
+                       finitef(qr[3 * j + 2]) && finitef(cpr[j]) && finitef(cqr[j]) &&
+                       cpr[j] > cmin && cqr[j] > cmin;
+        val[j] = v;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          xs[j][r] = v ? pr[3 * j + r] - piv[r] : 0.f;
+          ys[j][r] = v ? qr[3 * j + r] - piv[3 + r] : 0.f;
+        }
+        ws[j] = v ? (rule == 0 ? cpr[j] * cqr[j] : cpr[j]) : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        X[r] = make_float2(xs[0][r], xs[1][r]);
+        Y[r] = make_float2(ys[0][r], ys[1][r]);
+      }
+      W = make_float2(ws[0], ws[1]);
+      XX = fma2(X[0], X[0], fma2(X[1], X[1], mul2(X[2], X[2])));
     }
+    const float2 nY[3] = {make_float2(-Y[0].x, -Y[0].y), make_float2(-Y[1].x, -Y[1].y),
+                          make_float2(-Y[2].x, -Y[2].y)};
+    float2 gp[3] = {f2(0.f), f2(0.f), f2(0.f)}, gq[3] = {f2(0.f), f2(0.f), f2(0.f)};
+    float2 gw = f2(0.f), Gt[NGM];
+#pragma unroll
+    for (int i = 0; i < NGM; ++i) Gt[i] = f2(0.f);
     if (active) {
       for (int it = 1; it <= iters; ++it) {
-        const float* G = sh + (it - 1) * PER + 12;
-        float gW = G[G_W], gPP = G[G_PP], gSp[3], gSq[3], gQP[9];
-        for (int i = 0; i < 3; ++i) {
-          gSp[i] = G[G_SP + i];
-          gSq[i] = G[G_SQ + i];
-        }
-        for (int i = 0; i < 9; ++i) gQP[i] = G[G_QP + i];
-        float Ap[12];
-        if (it > 1)
-          for (int i = 0; i < 12; ++i) Ap[i] = sh[(it - 2) * PER + i];
-        float Ac[12];
-        if (it == iters)
-          for (int i = 0; i < 12; ++i) Ac[i] = sh[(it - 1) * PER + i];
+        const float2* S = sh2 + (it - 1) * SC_PAIRS;  // estimate it-1 (A, b) and gM of it
+        const float2* Sp = S - (it > 1 ? SC_PAIRS : 0);  // estimate the weights of it use
+        float2 h = f2(1.f), e[3] = {f2(0.f), f2(0.f), f2(0.f)}, rr = f2(0.f), rs = f2(0.f);
+        if (it > 1) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float* X = x[j];
-          const float* Y = y[j];
-          float h = 1.f, e[3] = {0.f, 0.f, 0.f}, rr = 0.f, rs = 0.f;
-          if (it > 1) {
-            for (int r = 0; r < 3; ++r)
-              e[r] = Ap[3 * r] * X[0] + Ap[3 * r + 1] * X[1] + Ap[3 * r + 2] * X[2] + Ap[9 + r] - Y[r];
-            rr = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
-            rs = rsqrtf(rr);
-            h = fminf(1.f, delta * rs);
-          }
-          const float om = w[j] * h;
-          float gom = gW + gPP * (X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+          for (int r = 0; r < 3; ++r)
+            e[r] = fma2(Sp[3 * r], X[0],
+                        fma2(Sp[3 * r + 1], X[1], fma2(Sp[3 * r + 2], X[2], add2(Sp[9 + r], nY[r]))));
+          rr = fma2(e[0], e[0], fma2(e[1], e[1], mul2(e[2], e[2])));
+          rs = make_float2(rsqrtf(rr.x), rsqrtf(rr.y));
+          const float2 dr = mul2(f2(delta), rs);
+          h = make_float2(fminf(1.f, dr.x), fminf(1.f, dr.y));
+        }
+        const float2 om = mul2(W, h);
+        const float2* G = S + 12;
+        float2 gom = fma2(G[G_PP], XX, G[G_W]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const float2 Gx = fma2(G[G_QP + 3 * r], X[0],
+                                 fma2(G[G_QP + 3 * r + 1], X[1],
+                                      fma2(G[G_QP + 3 * r + 2], X[2], G[G_SQ + r])));
+          gom = fma2(G[G_SP + r], X[r], gom);
+          gom = fma2(Y[r], Gx, gom);
+        }
+#pragma unroll
+        for (int i = 0; i < NGM; ++i) Gt[i] = fma2(om, G[i], Gt[i]);
+        if (it == iters) {  // cost terms of the returned estimate
+          float2 f[3];
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+            f[r] = fma2(S[3 * r], X[0],
+                        fma2(S[3 * r + 1], X[1], fma2(S[3 * r + 2], X[2], add2(S[9 + r], nY[r]))));
+          const float2 ff = fma2(f[0], f[0], fma2(f[1], f[1], mul2(f[2], f[2])));
+          gom = add2(gom, fma2(f2(gJ), ff, f2(gOm)));
+          const float2 s2 = mul2(f2(2.f * gJ), om);
+#pragma unroll
           for (int r = 0; r < 3; ++r) {
-            const float Gx = gQP[3 * r] * X[0] + gQP[3 * r + 1] * X[1] + gQP[3 * r + 2] * X[2];
-            gom += gSp[r] * X[r] + gSq[r] * Y[r] + Y[r] * Gx;
-            gq[j][r] += om * (gSq[r] + Gx);
+            const float2 ge = mul2(s2, f[r]);
+            gq[r] = fma2(f2(-1.f), ge, gq[r]);
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) gp[cc] = fma2(S[3 * r + cc], ge, gp[cc]);
           }
-          for (int cc = 0; cc < 3; ++cc) {
-            const float Gy = gQP[cc] * Y[0] + gQP[3 + cc] * Y[1] + gQP[6 + cc] * Y[2];
-            gp[j][cc] += om * (gSp[cc] + 2.f * gPP * X[cc] + Gy);
-          }
-          if (it == iters) {
-            float f[3];
-            for (int r = 0; r < 3; ++r)
-              f[r] = Ac[3 * r] * X[0] + Ac[3 * r + 1] * X[1] + Ac[3 * r + 2] * X[2] + Ac[9 + r] - Y[r];
-            gom += gJ * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) + gOm;
-            const float s2 = 2.f * gJ * om;
-            for (int r = 0; r < 3; ++r) {
-              const float ge = s2 * f[r];
-              gq[j][r] -= ge;
-              for (int cc = 0; cc < 3; ++cc) gp[j][cc] += Ac[3 * r + cc] * ge;
-            }
-          }
-          gw[j] += gom * h;
-          if (it > 1 && rr > delta * delta) {
-            const float fct = -(gom * w[j]) * delta * rs * rs * rs;
-            for (int r = 0; r < 3; ++r) {
-              const float ge = fct * e[r];
-              gq[j][r] -= ge;
-              for (int cc = 0; cc < 3; ++cc) gp[j][cc] += Ap[3 * r + cc] * ge;
-            }
+        }
+        gw = fma2(gom, h, gw);
+        if (it > 1) {
+          // Huber branch (|r| > delta): d h / d e = -delta e / |r|^3
+          float2 u = mul2(mul2(gom, W), mul2(f2(-delta), mul2(rs, mul2(rs, rs))));
+          u.x = rr.x > d2 ? u.x : 0.f;
+          u.y = rr.y > d2 ? u.y : 0.f;
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const float2 ge = mul2(u, e[r]);
+            gq[r] = fma2(f2(-1.f), ge, gq[r]);
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) gp[cc] = fma2(Sp[3 * r + cc], ge, gp[cc]);
           }
         }
       }
-    }
-    float gcp[4], gcq[4];
+      // the fixed-weight part: d<Gt, phi>/dp and d<Gt, phi>/dq
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      gcp[j] = val[j] ? (rule == 0 ? gw[j] * cqr[j] : gw[j]) : 0.f;
-      gcq[j] = val[j] ? (rule == 0 ? gw[j] * cpr[j] : 0.f) : 0.f;
+      for (int r = 0; r < 3; ++r) {
+        gq[r] = add2(gq[r], fma2(Gt[G_QP + 3 * r], X[0],
+                                 fma2(Gt[G_QP + 3 * r + 1], X[1],
+                                      fma2(Gt[G_QP + 3 * r + 2], X[2], Gt[G_SQ + r]))));
+        gp[r] = add2(gp[r], fma2(mul2(f2(2.f), Gt[G_PP]), X[r],
+                                 fma2(Gt[G_QP + r], Y[0],
+                                      fma2(Gt[G_QP + 3 + r], Y[1],
+                                           fma2(Gt[G_QP + 6 + r], Y[2], Gt[G_SP + r])))));
+      }
     }
-    if (VEC && n == 4 && ds) {
-      float4* o = reinterpret_cast<float4*>(gxs + 3 * i0);
-      o[0] = make_float4(gp[0][0], gp[0][1], gp[0][2], gp[1][0]);
-      o[1] = make_float4(gp[1][1], gp[1][2], gp[2][0], gp[2][1]);
-      o[2] = make_float4(gp[2][2], gp[3][0], gp[3][1], gp[3][2]);
-      *reinterpret_cast<float4*>(gcs + i0) = make_float4(gcp[0], gcp[1], gcp[2], gcp[3]);
+    float gpo[2][3], gqo[2][3], gcp[2], gcq[2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      gpo[0][r] = gp[r].x; gpo[1][r] = gp[r].y;
+      gqo[0][r] = gq[r].x; gqo[1][r] = gq[r].y;
+    }
+    const float gws[2] = {gw.x, gw.y};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      gcp[j] = val[j] ? (rule == 0 ? gws[j] * cqr[j] : gws[j]) : 0.f;
+      gcq[j] = val[j] ? (rule == 0 ? gws[j] * cpr[j] : 0.f) : 0.f;
+    }
+    if (VEC && n == 2 && ds) {
+      float2* o = reinterpret_cast<float2*>(gxs + 3 * i0);
+      o[0] = make_float2(gpo[0][0], gpo[0][1]);
+      o[1] = make_float2(gpo[0][2], gpo[1][0]);
+      o[2] = make_float2(gpo[1][1], gpo[1][2]);
+      *reinterpret_cast<float2*>(gcs + i0) = make_float2(gcp[0], gcp[1]);
     } else {
       for (int j = 0; j < n; ++j) {
         const int i = i0 + j;
         if (ds) {
-          gxs[3 * i] = gp[j][0]; gxs[3 * i + 1] = gp[j][1]; gxs[3 * i + 2] = gp[j][2];
+          gxs[3 * i] = gpo[j][0]; gxs[3 * i + 1] = gpo[j][1]; gxs[3 * i + 2] = gpo[j][2];
           gcs[i] = gcp[j];
         } else {
-          out[8 * i] = gp[j][0]; out[8 * i + 1] = gp[j][1]; out[8 * i + 2] = gp[j][2];
+          out[8 * i] = gpo[j][0]; out[8 * i + 1] = gpo[j][1]; out[8 * i + 2] = gpo[j][2];
           out[8 * i + 6] = gcp[j];
         }
       }
     }
-    if (VEC && n == 4 && dt) {
-      float4* o = reinterpret_cast<float4*>(gxt + 3 * i0);
-      o[0] = make_float4(gq[0][0], gq[0][1], gq[0][2], gq[1][0]);
-      o[1] = make_float4(gq[1][1], gq[1][2], gq[2][0], gq[2][1]);
-      o[2] = make_float4(gq[2][2], gq[3][0], gq[3][1], gq[3][2]);
-      *reinterpret_cast<float4*>(gct + i0) = make_float4(gcq[0], gcq[1], gcq[2], gcq[3]);
+    if (VEC && n == 2 && dt) {
+      float2* o = reinterpret_cast<float2*>(gxt + 3 * i0);
+      o[0] = make_float2(gqo[0][0], gqo[0][1]);
+      o[1] = make_float2(gqo[0][2], gqo[1][0]);
+      o[2] = make_float2(gqo[1][1], gqo[1][2]);
+      *reinterpret_cast<float2*>(gct + i0) = make_float2(gcq[0], gcq[1]);
     } else {
       for (int j = 0; j < n; ++j) {
         const int i = i0 + j;
         if (dt) {
-          gxt[3 * i] = gq[j][0]; gxt[3 * i + 1] = gq[j][1]; gxt[3 * i + 2] = gq[j][2];
+          gxt[3 * i] = gqo[j][0]; gxt[3 * i + 1] = gqo[j][1]; gxt[3 * i + 2] = gqo[j][2];
           gct[i] = gcq[j];
         } else {
-          out[8 * i + 3] = gq[j][0]; out[8 * i + 4] = gq[j][1]; out[8 * i + 5] = gq[j][2];
+          out[8 * i + 3] = gqo[j][0]; out[8 * i + 4] = gqo[j][1]; out[8 * i + 5] = gqo[j][2];
           out[8 * i + 7] = gcq[j];
         }
       }
@@ -723,7 +770,7 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
     k_adj_zero_frames<<<(unsigned)n_frames, 512, 0, s>>>(hw, refs, d_grad_xyz, d_grad_conf);
   });
   if (n_tiles > 0) {
-    const size_t shm = sizeof(float) * 29 * (size_t)iters;
+    const size_t shm = sizeof(float2) * SC_PAIRS * (size_t)iters;
     traced(ctx, s, "adj_scatter", [&] {
       if (vec)
         k_adj_scatter<true><<<grid, THREADS, shm, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt,

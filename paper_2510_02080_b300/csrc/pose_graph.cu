@@ -7,9 +7,11 @@
 // Gauss-Newton (optionally damped: H + lambda I) with right perturbations
 // T <- T Exp(delta) and one node held fixed.
 //
-// Host (once per graph structure, cached in the context): a nested-dissection
-// ordering of the free nodes, the block fill of the Cholesky factor, its
-// elimination-tree levels, the left-looking update lists and the assembly lists.
+// Host (once per graph structure, cached in the context): an ordering of the
+// free nodes (nested dissection or minimum degree, whichever a cost estimate
+// prefers), the block fill of the Cholesky factor, its elimination-tree
+// levels, the trailing dense supernode, the left-looking update lists and the
+// assembly lists.
 // Device, per Gauss-Newton iteration, all FP64:
 //   k_pg_linearize   one warp per edge: e, J_i = -Jr^-1(e) Ad(T_j^-1 T_i),
 //                    J_j = Jr^-1(e) (Jr^-1 from its Bernoulli series), and the
@@ -25,6 +27,7 @@
 #include <cmath>
 #include <functional>
 #include <map>
+#include <queue>
 #include <set>
 #include <vector>
 
@@ -150,26 +153,48 @@ __global__ void __launch_bounds__(1024) k_pg_init(int n, int fixed, const int* _
 }
 
 // --------------------------------------------------------------------------
-// linearisation: one warp per edge
+// device view of a plan and of one call's data
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) k_pg_linearize(
-    const int* __restrict__ ei, const int* __restrict__ ej, const ec3r_sim3* __restrict__ nodes,
-    const ec3r_sim3* __restrict__ Tij, const double* __restrict__ info, double* __restrict__ contrib,
-    double* __restrict__ gvec, double* __restrict__ chi2e, int jacobians) {
-  const int e = blockIdx.x;
-  const int lane = threadIdx.x;
-  __shared__ double sA[NB], sB[NB], sC[NB], sJ[NB], sJi[NB], sO[NB], sOJ[NB], sOJj[NB];
-  __shared__ double se[7];
-  __shared__ int sK;
+struct PgDev {
+  int n, m, nf, n_blocks, sn0, nlev, n_sn_groups, iters;
+  double lambda;
+  const int *ei, *ej, *perm, *col_ptr, *off_row, *off_blk, *grp_ptr, *grp, *upd_ab, *sn_grp,
+      *row_ptr, *row, *level_ptr, *level_cols, *asm_ptr, *asm_it, *g_ptr, *g_it;
+  double *L, *b, *contrib, *gvec, *chi2e, *idiag, *chi2;
+  int* fail;
+  unsigned* flags;
+  const ec3r_sim3* Tij;
+  const double* info;
+  ec3r_sim3* nodes;
+};
+
+// Loads of values written by an earlier launch of the same solve: plain
+// coherent loads, never the read-only data path.
+__device__ __forceinline__ double ldc(const double* p) { return *p; }
+__device__ __forceinline__ int ldc(const int* p) { return *p; }
+
+__device__ __forceinline__ s3::Sim3d load_cg(const ec3r_sim3* a) { return s3::load(*a); }
+
+// Shared-memory scratch of one warp.
+struct WarpScratch {
+  double A[NB], B[NB], C[NB], J[NB], Ji[NB], O[NB], OJ[NB], OJj[NB];
+  double e[7], inv[7], y[7];
+  int K;
+};
+
+// --------------------------------------------------------------------------
+// linearisation of one edge (one warp)
+// --------------------------------------------------------------------------
+__device__ void linearize_edge(int e, int lane, WarpScratch& w, const PgDev& p, int jacobians) {
   if (lane == 0) {
-    const s3::Sim3d Ti = s3::load(nodes[ei[e]]), Tj = s3::load(nodes[ej[e]]);
-    const s3::Sim3d M = s3::load(Tij[e]);
+    const s3::Sim3d Ti = load_cg(p.nodes + p.ei[e]), Tj = load_cg(p.nodes + p.ej[e]);
+    const s3::Sim3d M = s3::load(p.Tij[e]);
     double xi[7];
     s3::log(edge_error_T(Ti, Tj, M), xi);
-    for (int k = 0; k < 7; ++k) se[k] = xi[k];
+    for (int k = 0; k < 7; ++k) w.e[k] = xi[k];
     if (jacobians) {
-      adjoint7(s3::compose(s3::inverse(Tj), Ti), sB);   // Ad(T_j^-1 T_i)
-      small_ad7(xi, sA);                                // ad(e)
+      adjoint7(s3::compose(s3::inverse(Tj), Ti), w.B);   // Ad(T_j^-1 T_i)
+      small_ad7(xi, w.A);                                // ad(e)
       // series length from the spectral radius of ad(e) and the size of rho
       const double nu = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5] + xi[6] * xi[6]);
       const double rn = 1.0 + fabs(xi[0]) + fabs(xi[1]) + fabs(xi[2]);
@@ -180,116 +205,114 @@ __global__ void __launch_bounds__(32) k_pg_linearize(
         ++K;
         qk *= q * q;
       }
-      sK = K;
+      w.K = K;
     }
   }
   __syncwarp();
   double ev[7];
-  for (int k = 0; k < 7; ++k) ev[k] = se[k];
+  for (int k = 0; k < 7; ++k) ev[k] = w.e[k];
   // Omega (identity unless given)
   for (int idx = lane; idx < NB; idx += 32)
-    sO[idx] = info ? info[(size_t)e * NB + idx] : ((idx % 8 == 0) ? 1.0 : 0.0);
+    w.O[idx] = p.info ? p.info[(size_t)e * NB + idx] : ((idx % 8 == 0) ? 1.0 : 0.0);
   __syncwarp();
   if (lane == 0) {
     double v[7];
     for (int r = 0; r < 7; ++r) {
       double s = 0.0;
-      for (int c = 0; c < 7; ++c) s += sO[7 * r + c] * ev[c];
+      for (int c = 0; c < 7; ++c) s += w.O[7 * r + c] * ev[c];
       v[r] = s;
     }
     double x2 = 0.0;
     for (int r = 0; r < 7; ++r) x2 += ev[r] * v[r];
-    chi2e[e] = x2;
+    p.chi2e[e] = x2;
   }
-  if (!jacobians) return;
+  if (!jacobians) {
+    __syncwarp();
+    return;
+  }
   // Jr^-1(e) = I + ad/2 + sum_k c_k ad^{2k}; Horner in ad^2
-  warp_mm7(sA, false, sA, false, sC, lane);            // sC = ad^2
-  const int K = sK;
-  for (int idx = lane; idx < NB; idx += 32) sJ[idx] = (idx % 8 == 0) ? c_bern[K - 1] : 0.0;
+  warp_mm7(w.A, false, w.A, false, w.C, lane);          // C = ad^2
+  const int K = w.K;
+  for (int idx = lane; idx < NB; idx += 32) w.J[idx] = (idx % 8 == 0) ? c_bern[K - 1] : 0.0;
   __syncwarp();
   for (int k = K - 1; k >= 1; --k) {
-    warp_mm7(sC, false, sJ, false, sOJ, lane);         // sOJ = ad^2 Q
+    warp_mm7(w.C, false, w.J, false, w.OJ, lane);       // OJ = ad^2 Q
     for (int idx = lane; idx < NB; idx += 32)
-      sJ[idx] = sOJ[idx] + ((idx % 8 == 0) ? c_bern[k - 1] : 0.0);
+      w.J[idx] = w.OJ[idx] + ((idx % 8 == 0) ? c_bern[k - 1] : 0.0);
     __syncwarp();
   }
-  warp_mm7(sC, false, sJ, false, sOJ, lane);           // sOJ = P(ad^2)
+  warp_mm7(w.C, false, w.J, false, w.OJ, lane);         // OJ = P(ad^2)
   for (int idx = lane; idx < NB; idx += 32)
-    sJ[idx] = ((idx % 8 == 0) ? 1.0 : 0.0) + 0.5 * sA[idx] + sOJ[idx];   // sJ = Jr^-1 = J_j
+    w.J[idx] = ((idx % 8 == 0) ? 1.0 : 0.0) + 0.5 * w.A[idx] + w.OJ[idx];  // J = Jr^-1 = J_j
   __syncwarp();
-  warp_mm7(sJ, false, sB, false, sJi, lane);           // Jr^-1 Ad
-  for (int idx = lane; idx < NB; idx += 32) sJi[idx] = -sJi[idx];        // J_i
+  warp_mm7(w.J, false, w.B, false, w.Ji, lane);         // Jr^-1 Ad
+  for (int idx = lane; idx < NB; idx += 32) w.Ji[idx] = -w.Ji[idx];     // J_i
   __syncwarp();
-  double* out = contrib + (size_t)e * 3 * NB;
-  warp_mm7(sO, false, sJi, false, sOJ, lane);          // Omega J_i
-  warp_mm7(sO, false, sJ, false, sOJj, lane);          // Omega J_j
-  warp_mm7(sJi, true, sOJ, false, sA, lane);           // J_i^T Omega J_i
-  warp_mm7(sJ, true, sOJj, false, sB, lane);           // J_j^T Omega J_j
-  warp_mm7(sJi, true, sOJj, false, sC, lane);          // J_i^T Omega J_j
+  double* out = p.contrib + (size_t)e * 3 * NB;
+  warp_mm7(w.O, false, w.Ji, false, w.OJ, lane);        // Omega J_i
+  warp_mm7(w.O, false, w.J, false, w.OJj, lane);        // Omega J_j
+  warp_mm7(w.Ji, true, w.OJ, false, w.A, lane);         // J_i^T Omega J_i
+  warp_mm7(w.J, true, w.OJj, false, w.B, lane);         // J_j^T Omega J_j
+  warp_mm7(w.Ji, true, w.OJj, false, w.C, lane);        // J_i^T Omega J_j
   for (int idx = lane; idx < NB; idx += 32) {
-    out[idx] = sA[idx];
-    out[NB + idx] = sB[idx];
-    out[2 * NB + idx] = sC[idx];
+    out[idx] = w.A[idx];
+    out[NB + idx] = w.B[idx];
+    out[2 * NB + idx] = w.C[idx];
   }
   // g: J^T Omega e
   if (lane < 14) {
     const int side = lane / 7, r = lane % 7;
-    const double* OJ = side == 0 ? sOJ : sOJj;
+    const double* OJ = side == 0 ? w.OJ : w.OJj;
     double s = 0.0;
     for (int c = 0; c < 7; ++c) s += OJ[7 * c + r] * ev[c];
-    gvec[(size_t)e * 14 + lane] = s;
+    p.gvec[(size_t)e * 14 + lane] = s;
   }
+  __syncwarp();
 }
 
 // --------------------------------------------------------------------------
-// assembly: one warp per factor block, then one per node (g), then chi^2
+// assembly unit b (one warp): a factor block (b < n_blocks), a right-hand
+// side block (then nf of them), or chi^2 (the last unit)
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) k_pg_assemble(
-    int n_blocks, int nf, int m, const int* __restrict__ asm_ptr, const int* __restrict__ asm_it,
-    const int* __restrict__ g_ptr, const int* __restrict__ g_it, const double* __restrict__ contrib,
-    const double* __restrict__ gvec, const double* __restrict__ chi2e, double lambda, double* L,
-    double* bvec, double* chi2_out, int* fail) {
-  const int b = blockIdx.x;
-  const int lane = threadIdx.x;
+__device__ void assemble_unit(int b, int lane, int n_blocks, int nf, const PgDev& p,
+                              double* chi2_out) {
   if (b < n_blocks) {
-    const int p0 = asm_ptr[b], p1 = asm_ptr[b + 1];
+    const int p0 = p.asm_ptr[b], p1 = p.asm_ptr[b + 1];
     for (int idx = lane; idx < NB; idx += 32) {
       const int r = idx / 7, c = idx % 7;
-      double s = (b < nf && r == c) ? lambda : 0.0;
-      for (int p = p0; p < p1; ++p) {
-        const int it = asm_it[p];
+      double s = (b < nf && r == c) ? p.lambda : 0.0;
+      for (int q = p0; q < p1; ++q) {
+        const int it = p.asm_it[q];
         const int edge = it >> 2, kind = it & 3;
-        const double* C = contrib + (size_t)edge * 3 * NB;
-        s += kind == 3 ? C[2 * NB + 7 * c + r] : C[kind * NB + idx];
+        const double* C = p.contrib + (size_t)edge * 3 * NB;
+        s += kind == 3 ? ldc(C + 2 * NB + 7 * c + r) : ldc(C + kind * NB + idx);
       }
-      L[(size_t)b * NB + idx] = s;
+      p.L[(size_t)b * NB + idx] = s;
     }
   } else if (b < n_blocks + nf) {
     const int k = b - n_blocks;
     if (lane < 7) {
       double s = 0.0;
-      for (int p = g_ptr[k]; p < g_ptr[k + 1]; ++p) {
-        const int it = g_it[p];
-        s += gvec[(size_t)(it >> 1) * 14 + 7 * (it & 1) + lane];
+      for (int q = p.g_ptr[k]; q < p.g_ptr[k + 1]; ++q) {
+        const int it = p.g_it[q];
+        s += ldc(p.gvec + (size_t)(it >> 1) * 14 + 7 * (it & 1) + lane);
       }
-      bvec[7 * k + lane] = -s;
+      p.b[7 * k + lane] = -s;
     }
   } else {
     double s = 0.0;
-    for (int e = lane; e < m; e += 32) s += chi2e[e];
+    for (int e = lane; e < p.m; e += 32) s += ldc(p.chi2e + e);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
       if (chi2_out) *chi2_out = s;
-      *fail = 0;
+      *p.fail = 0;
     }
   }
 }
 
 // --------------------------------------------------------------------------
-// factorisation + forward substitution: one warp per column of a level
+// numeric factorisation helpers
 // --------------------------------------------------------------------------
-constexpr int FWARPS = 4;  // warps per column in k_pg_factor
-
 // L[dst] -= sum over the group's updates of A B^T for the entries idx of this
 // lane; four independent partial sums break the FP64 dependency chain.
 __device__ __forceinline__ void apply_group(double* L, int dst, const int* __restrict__ ab, int n,
@@ -301,102 +324,183 @@ __device__ __forceinline__ void apply_group(double* L, int dst, const int* __res
     for (int q = 0; q < n; ++q) {
       const double* A = L + (size_t)ab[2 * q] * NB + 7 * r;
       const double* B = L + (size_t)ab[2 * q + 1] * NB + 7 * c;
-      s0 = fma(A[0], B[0], s0);
-      s1 = fma(A[1], B[1], s1);
-      s2 = fma(A[2], B[2], s2);
-      s3 = fma(A[3], B[3], s3);
-      s0 = fma(A[4], B[4], s0);
-      s1 = fma(A[5], B[5], s1);
-      s2 = fma(A[6], B[6], s2);
+      s0 = fma(ldc(A + 0), ldc(B + 0), s0);
+      s1 = fma(ldc(A + 1), ldc(B + 1), s1);
+      s2 = fma(ldc(A + 2), ldc(B + 2), s2);
+      s3 = fma(ldc(A + 3), ldc(B + 3), s3);
+      s0 = fma(ldc(A + 4), ldc(B + 4), s0);
+      s1 = fma(ldc(A + 5), ldc(B + 5), s1);
+      s2 = fma(ldc(A + 6), ldc(B + 6), s2);
     }
-    Dst[idx] -= (s0 + s1) + (s2 + s3);
+    Dst[idx] = ldc(Dst + idx) - ((s0 + s1) + (s2 + s3));
   }
 }
 
-__global__ void __launch_bounds__(32 * FWARPS) k_pg_factor(
-    const int* __restrict__ cols, const int* __restrict__ col_ptr, const int* __restrict__ off_blk,
-    const int* __restrict__ grp_ptr, const int* __restrict__ grp, const int* __restrict__ upd_ab,
-    const int* __restrict__ row_ptr, const int* __restrict__ row_it, double* L, double* bvec,
-    double* idiag, unsigned* flags, int* fail) {
-  const int k = cols[blockIdx.x];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ double D[NB];
-  __shared__ double inv[7];
-  __shared__ double y[7];
-  // left-looking updates: warp w takes the update groups (one per destination
-  // block of column k) g with g % FWARPS == w; each group's updates are summed
-  // in a fixed order, so the result does not depend on scheduling
-  for (int g = grp_ptr[k] + warp; g < grp_ptr[k + 1]; g += FWARPS)
-    apply_group(L, grp[3 * g], upd_ab + 2 * grp[3 * g + 1], grp[3 * g + 2], lane);
-  __syncthreads();
-  double* Lkk = L + (size_t)k * NB;
-  if (warp == 0) {
-    for (int idx = lane; idx < NB; idx += 32) D[idx] = Lkk[idx];
+// Dense 7x7 Cholesky (lower) of the block at Lkk into D (shared), reciprocal
+// pivots (through rsqrt) into inv; writes the factor back and the reciprocal
+// pivots to id.  One warp.  A non-positive or non-finite pivot raises NOT_SPD.
+__device__ void chol7(double* Lkk, double* id, double* D, double* inv, int lane, const PgDev& p) {
+  for (int idx = lane; idx < NB; idx += 32) D[idx] = ldc(Lkk + idx);
+  __syncwarp();
+  bool bad = false;
+  for (int c = 0; c < 7; ++c) {
+    const double d = D[8 * c];
+    if (!(d > 0.0) || !isfinite(d)) bad = true;
+    const double ip = rsqrt(fmax(d, 1e-300));
     __syncwarp();
-    // dense 7x7 Cholesky (lower); pivots through rsqrt
-    bool bad = false;
-    for (int c = 0; c < 7; ++c) {
-      const double d = D[8 * c];
-      if (!(d > 0.0) || !isfinite(d)) bad = true;
-      const double ip = rsqrt(fmax(d, 1e-300));
-      __syncwarp();
-      if (lane == 0) {
-        D[8 * c] = d * ip;
-        inv[c] = ip;
-      }
-      if (lane > c && lane < 7) D[7 * lane + c] *= ip;
-      __syncwarp();
-      for (int idx = lane; idx < NB; idx += 32) {
-        const int r = idx / 7, cc = idx % 7;
-        if (r > c && cc > c && cc <= r) D[idx] -= D[7 * r + c] * D[7 * cc + c];
-      }
-      __syncwarp();
+    if (lane == 0) {
+      D[8 * c] = d * ip;
+      inv[c] = ip;
     }
-    if (bad && lane == 0) {
-      atomicOr(flags, FLAG_NOT_SPD);
-      atomicExch(fail, 1);
-    }
-    if (lane < 7) idiag[7 * k + lane] = inv[lane];
+    if (lane > c && lane < 7) D[7 * lane + c] *= ip;
+    __syncwarp();
     for (int idx = lane; idx < NB; idx += 32) {
-      const int r = idx / 7, c = idx % 7;
-      Lkk[idx] = c <= r ? D[idx] : 0.0;
+      const int r = idx / 7, cc = idx % 7;
+      if (r > c && cc > c && cc <= r) D[idx] -= D[7 * r + c] * D[7 * cc + c];
     }
+    __syncwarp();
   }
-  __syncthreads();
-  // off-diagonal blocks: X = H_ik Lkk^-T (row-wise forward substitution)
-  const int o0 = col_ptr[k], o1 = col_ptr[k + 1];
-  for (int q = o0 * 7 + threadIdx.x; q < o1 * 7; q += 32 * FWARPS) {
-    double* X = L + (size_t)off_blk[q / 7] * NB + 7 * (q % 7);
-    double x[7];
-    for (int c = 0; c < 7; ++c) {
-      double s = X[c];
-      for (int t = 0; t < c; ++t) s -= x[t] * D[7 * c + t];
-      x[c] = s * inv[c];
-    }
-    for (int c = 0; c < 7; ++c) X[c] = x[c];
+  if (bad && lane == 0) {
+    atomicOr(p.flags, FLAG_NOT_SPD);
+    atomicExch(p.fail, 1);
   }
-  // forward substitution: y_k = Lkk^-1 (b_k - sum_j L_kj y_j)
+  for (int idx = lane; idx < NB; idx += 32) Lkk[idx] = (idx % 7 <= idx / 7) ? D[idx] : 0.0;
+  if (lane < 7) id[lane] = inv[lane];
+  __syncwarp();
+}
+
+// One row of an off-diagonal block, in place: x <- x Lkk^-T.
+__device__ __forceinline__ void row_solve7(double* X, const double* D, const double* inv) {
+  double x[7];
+  for (int c = 0; c < 7; ++c) {
+    double s = ldc(X + c);
+    for (int t = 0; t < c; ++t) s -= x[t] * D[7 * c + t];
+    x[c] = s * inv[c];
+  }
+  for (int c = 0; c < 7; ++c) X[c] = x[c];
+}
+
+// y <- Lkk^-1 y and x <- Lkk^-T x on 7-vectors in shared memory (one thread).
+__device__ __forceinline__ void lower_solve7(double* y, const double* D, const double* inv) {
+  for (int c = 0; c < 7; ++c) {
+    double s = y[c];
+    for (int t = 0; t < c; ++t) s -= D[7 * c + t] * y[t];
+    y[c] = s * inv[c];
+  }
+}
+__device__ __forceinline__ void upper_solve7(double* x, const double* D, const double* inv) {
+  for (int c = 6; c >= 0; --c) {
+    double s = x[c];
+    for (int t = c + 1; t < 7; ++t) s -= D[7 * t + c] * x[t];
+    x[c] = s * inv[c];
+  }
+}
+
+template <int TW>
+__device__ __forceinline__ void team_sync() {
+  if constexpr (TW == 1) __syncwarp();
+  else __syncthreads();
+}
+
+// Column k of the sparse part, by a team of TW warps (tid in [0, 32 TW)):
+// left-looking updates (each destination block's group summed in a fixed
+// order, so the result does not depend on scheduling), dense 7x7 Cholesky,
+// off-diagonal triangular solves, forward substitution
+// y_k = Lkk^-1 (b_k - sum_j L_kj y_j) over its descendants j.
+template <int TW>
+__device__ void factor_column(int k, int tid, double* D, double* inv, double* y, const PgDev& p) {
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int g = p.grp_ptr[k] + warp; g < p.grp_ptr[k + 1]; g += TW)
+    apply_group(p.L, p.grp[3 * g], p.upd_ab + 2 * p.grp[3 * g + 1], p.grp[3 * g + 2], lane);
+  team_sync<TW>();
+  if (warp == 0) chol7(p.L + (size_t)k * NB, p.idiag + 7 * k, D, inv, lane, p);
+  team_sync<TW>();
+  const int o0 = p.col_ptr[k], o1 = p.col_ptr[k + 1];
+  for (int q = o0 * 7 + tid; q < o1 * 7; q += 32 * TW)
+    row_solve7(p.L + (size_t)p.off_blk[q / 7] * NB + 7 * (q % 7), D, inv);
   if (warp == 0) {
     if (lane < 7) {
-      double s = bvec[7 * k + lane];
-      for (int p = row_ptr[k]; p < row_ptr[k + 1]; ++p) {
-        const int j = row_it[2 * p], blk = row_it[2 * p + 1];
-        const double* Lkj = L + (size_t)blk * NB + 7 * lane;
-        for (int t = 0; t < 7; ++t) s -= Lkj[t] * bvec[7 * j + t];
+      double s = ldc(p.b + 7 * k + lane);
+      for (int q = p.row_ptr[k]; q < p.row_ptr[k + 1]; ++q) {
+        const int j = p.row[2 * q], blk = p.row[2 * q + 1];
+        const double* Lkj = p.L + (size_t)blk * NB + 7 * lane;
+        for (int t = 0; t < 7; ++t) s -= ldc(Lkj + t) * ldc(p.b + 7 * j + t);
       }
       y[lane] = s;
     }
     __syncwarp();
-    if (lane == 0) {
-      for (int c = 0; c < 7; ++c) {
-        double s = y[c];
-        for (int t = 0; t < c; ++t) s -= D[7 * c + t] * y[t];
-        y[c] = s * inv[c];
-      }
-    }
+    if (lane == 0) lower_solve7(y, D, inv);
     __syncwarp();
-    if (lane < 7) bvec[7 * k + lane] = y[lane];
+    if (lane < 7) p.b[7 * k + lane] = y[lane];
   }
+  team_sync<TW>();
+}
+
+// Back substitution of column k (one warp): x_k = Lkk^-T (y_k - sum_i L_ik^T x_i).
+__device__ void backsolve_column(int k, int lane, double* x, const PgDev& p) {
+  if (lane < 7) {
+    double s0 = ldc(p.b + 7 * k + lane), s1 = 0.0;
+    for (int q = p.col_ptr[k]; q < p.col_ptr[k + 1]; ++q) {
+      const int i = p.off_row[q];
+      const double* Lik = p.L + (size_t)p.off_blk[q] * NB + lane;
+      const double* xi = p.b + 7 * i;
+      s0 -= ldc(Lik + 0) * ldc(xi + 0) + ldc(Lik + 14) * ldc(xi + 2) +
+            ldc(Lik + 28) * ldc(xi + 4) + ldc(Lik + 42) * ldc(xi + 6);
+      s1 -= ldc(Lik + 7) * ldc(xi + 1) + ldc(Lik + 21) * ldc(xi + 3) + ldc(Lik + 35) * ldc(xi + 5);
+    }
+    x[lane] = s0 + s1;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    const double* D = p.L + (size_t)k * NB;
+    const double* id = p.idiag + 7 * k;
+    for (int c = 6; c >= 0; --c) {
+      double s = x[c];
+      for (int t = c + 1; t < 7; ++t) s -= ldc(D + 7 * t + c) * x[t];
+      x[c] = s * ldc(id + c);
+    }
+  }
+  __syncwarp();
+  if (lane < 7) p.b[7 * k + lane] = x[lane];
+  __syncwarp();
+}
+
+__device__ __forceinline__ void update_node(int k, const PgDev& p) {
+  double d[7];
+  for (int i = 0; i < 7; ++i) d[i] = ldc(p.b + 7 * k + i);
+  const int v = p.perm[k];
+  s3::store(s3::compose(load_cg(p.nodes + v), s3::exp(d)), p.nodes[v]);
+}
+
+// --------------------------------------------------------------------------
+// multi-launch schedule: one launch per phase and per tree level
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) k_pg_linearize(PgDev p, int jacobians) {
+  __shared__ WarpScratch w;
+  linearize_edge(blockIdx.x, threadIdx.x, w, p, jacobians);
+}
+
+__global__ void __launch_bounds__(32) k_pg_assemble(PgDev p, int n_blocks, int nf,
+                                                    double* chi2_out) {
+  assemble_unit(blockIdx.x, threadIdx.x, n_blocks, nf, p, chi2_out);
+}
+
+constexpr int FWARPS = 4;  // warps per column in k_pg_factor
+
+__global__ void __launch_bounds__(32 * FWARPS) k_pg_factor(PgDev p, int level) {
+  __shared__ double D[NB], inv[7], y[7];
+  factor_column<FWARPS>(p.level_cols[p.level_ptr[level] + blockIdx.x], threadIdx.x, D, inv, y, p);
+}
+
+__global__ void __launch_bounds__(32) k_pg_backsolve(PgDev p, int level) {
+  __shared__ double x[7];
+  backsolve_column(p.level_cols[p.level_ptr[level] + blockIdx.x], threadIdx.x, x, p);
+}
+
+__global__ void k_pg_update(PgDev p) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= p.nf || ldc(p.fail)) return;
+  update_node(k, p);
 }
 
 // --------------------------------------------------------------------------
@@ -569,51 +673,6 @@ __global__ void __launch_bounds__(256) k_pg_sn_backward(int sn0, int nf,
   }
 }
 
-// back substitution, root to leaves: x_k = Lkk^-T (y_k - sum_i L_ik^T x_i)
-__global__ void __launch_bounds__(32) k_pg_backsolve(const int* __restrict__ cols,
-                                                     const int* __restrict__ col_ptr,
-                                                     const int* __restrict__ off_row,
-                                                     const int* __restrict__ off_blk,
-                                                     const double* __restrict__ L,
-                                                     const double* __restrict__ idiag,
-                                                     double* bvec) {
-  const int k = cols[blockIdx.x];
-  const int lane = threadIdx.x;
-  __shared__ double x[7];
-  if (lane < 7) {
-    double s0 = bvec[7 * k + lane], s1 = 0.0;
-    for (int p = col_ptr[k]; p < col_ptr[k + 1]; ++p) {
-      const int i = off_row[p];
-      const double* Lik = L + (size_t)off_blk[p] * NB + lane;
-      const double* xi = bvec + 7 * i;
-      s0 -= Lik[0] * xi[0] + Lik[14] * xi[2] + Lik[28] * xi[4] + Lik[42] * xi[6];
-      s1 -= Lik[7] * xi[1] + Lik[21] * xi[3] + Lik[35] * xi[5];
-    }
-    x[lane] = s0 + s1;
-  }
-  __syncwarp();
-  if (lane == 0) {
-    const double* D = L + (size_t)k * NB;
-    const double* id = idiag + 7 * k;
-    for (int c = 6; c >= 0; --c) {
-      double s = x[c];
-      for (int t = c + 1; t < 7; ++t) s -= D[7 * t + c] * x[t];
-      x[c] = s * id[c];
-    }
-  }
-  __syncwarp();
-  if (lane < 7) bvec[7 * k + lane] = x[lane];
-}
-
-__global__ void k_pg_update(int nf, const int* __restrict__ perm, const double* __restrict__ x,
-                            ec3r_sim3* nodes, const int* __restrict__ fail) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nf || *fail) return;
-  double d[7];
-  for (int i = 0; i < 7; ++i) d[i] = x[7 * k + i];
-  const int v = perm[k];
-  s3::store(s3::compose(s3::load(nodes[v]), s3::exp(d)), nodes[v]);
-}
 
 // --------------------------------------------------------------------------
 // host: planning
@@ -625,9 +684,10 @@ struct Plan : Extension {
   int *d_ei = nullptr, *d_ej = nullptr, *d_perm = nullptr;
   int *d_col_ptr = nullptr, *d_off_row = nullptr, *d_off_blk = nullptr;
   int *d_grp_ptr = nullptr, *d_grp = nullptr, *d_upd_ab = nullptr, *d_sn_grp = nullptr;
-  int sn0 = 0, n_sn_groups = 0;  // columns >= sn0 form the dense trailing supernode
+  int sn0 = 0, n_sn_groups = 0, ordering = 0;  // ordering: 0 nested dissection, 1 min degree  // columns >= sn0 form the dense trailing supernode
   int *d_row_ptr = nullptr, *d_row = nullptr;
-  int *d_level_cols = nullptr, *d_asm_ptr = nullptr, *d_asm = nullptr;
+  int *d_level_cols = nullptr, *d_level_ptr = nullptr, *d_asm_ptr = nullptr, *d_asm = nullptr;
+  int nlev = 0;
   int *d_g_ptr = nullptr, *d_g = nullptr;
   int *d_parent = nullptr, *d_tedge = nullptr, *d_tdir = nullptr;
   int *d_anc0 = nullptr, *d_anc1 = nullptr, *d_fail = nullptr;
@@ -684,6 +744,126 @@ static void nested_dissection(std::vector<int> S, const std::vector<std::set<int
   for (int v : sep) order.push_back(v);
 }
 
+// Minimum degree on the exact elimination graph: repeatedly eliminate the node
+// of fewest neighbours (ties by index), joining its neighbours into a clique.
+// Fewer fill blocks than nested dissection on graphs with many long loops, but
+// on a chain it eliminates from the ends inward (a deep elimination tree).
+static void minimum_degree(const std::vector<int>& freev, const std::vector<std::set<int>>& adj,
+                           std::vector<int>& order) {
+  const int n = (int)adj.size();
+  std::vector<std::set<int>> G(n);
+  std::vector<char> gone(n, 1);
+  using Item = std::pair<int, int>;
+  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
+  for (int v : freev) {
+    G[v] = adj[v];
+    gone[v] = 0;
+    pq.push({(int)G[v].size(), v});
+  }
+  while (!pq.empty()) {
+    const auto [d, v] = pq.top();
+    pq.pop();
+    if (gone[v] || d != (int)G[v].size()) continue;  // stale entry
+    gone[v] = 1;
+    order.push_back(v);
+    const std::vector<int> nb(G[v].begin(), G[v].end());
+    for (int a : nb) {
+      G[a].erase(v);
+      for (int b : nb)
+        if (b != a) G[a].insert(b);
+      pq.push({(int)G[a].size(), a});
+    }
+    G[v].clear();
+  }
+}
+
+// Symbolic factorisation of one elimination order: the block structure of
+// every factor column, the elimination tree, the trailing dense supernode and
+// an estimate of the numeric cost per Gauss-Newton iteration.
+struct Symbolic {
+  std::vector<int> perm, inew, parent;
+  std::vector<std::vector<int>> children;
+  std::vector<std::set<int>> st;
+  int sn0 = 0, nlev = 0;
+  double pairs = 0.0, cost = 0.0;
+};
+
+static void symbolic(const std::vector<std::set<int>>& adj, Symbolic& S) {
+  const int nf = (int)S.perm.size();
+  S.inew.assign(adj.size(), -1);
+  for (int k = 0; k < nf; ++k) S.inew[S.perm[k]] = k;
+  S.children.assign(nf, {});
+  S.st.assign(nf, {});
+  S.parent.assign(nf, -1);
+  for (int k = 0; k < nf; ++k) {
+    for (int u : adj[S.perm[k]]) {
+      const int q = S.inew[u];
+      if (q > k) S.st[k].insert(q);
+    }
+    for (int c : S.children[k])
+      for (int q : S.st[c])
+        if (q > k) S.st[k].insert(q);
+    if (!S.st[k].empty()) {
+      S.parent[k] = *S.st[k].begin();
+      S.children[S.parent[k]].push_back(k);
+    }
+  }
+}
+
+static Symbolic analyse(const std::vector<int>& order, const std::vector<std::set<int>>& adj) {
+  Symbolic S;
+  S.perm = order;
+  symbolic(adj, S);
+  const int nf = (int)S.perm.size();
+  // Columns at the top of the elimination tree that are alone in their level
+  // form a chain that would be factored one launch at a time.  They are moved
+  // to the end of the order (eliminating these separator-like nodes last adds
+  // no fill elsewhere) and, with the root clique, become one dense supernode
+  // (explicit zero fill) factored right-looking across many warps.
+  {
+    std::vector<int> lv(nf, 0), cnt(nf + 1, 0);
+    for (int k = 0; k < nf; ++k)
+      for (int c : S.children[k]) lv[k] = std::max(lv[k], lv[c] + 1);
+    for (int k = 0; k < nf; ++k) cnt[lv[k]]++;
+    std::vector<int> chain, rest;
+    for (int k = 0; k < nf; ++k) (cnt[lv[k]] == 1 ? chain : rest).push_back(k);
+    if ((int)chain.size() >= SN_MIN) {
+      if (chain.front() != nf - (int)chain.size()) {
+        std::vector<int> np;
+        for (int k : rest) np.push_back(S.perm[k]);
+        for (int k : chain) np.push_back(S.perm[k]);
+        S.perm = np;
+        symbolic(adj, S);
+      }
+      for (int k = nf - (int)chain.size(); k < nf; ++k) {
+        S.st[k].clear();
+        for (int q = k + 1; q < nf; ++q) S.st[k].insert(q);
+      }
+    }
+  }
+  // trailing dense supernode: the longest suffix of columns whose structure is
+  // every later column
+  int s0 = nf;
+  for (int k = nf - 1; k >= 0; --k) {
+    if ((int)S.st[k].size() != nf - 1 - k) break;
+    s0 = k;
+  }
+  S.sn0 = (nf - s0 >= SN_MIN) ? s0 : nf;
+  std::vector<int> level(nf, 0);
+  for (int k = 0; k < S.sn0; ++k) {
+    for (int c : S.children[k]) level[k] = std::max(level[k], level[c] + 1);
+    S.nlev = std::max(S.nlev, level[k] + 1);
+  }
+  for (int k = 0; k < nf; ++k) {
+    const double c = (double)S.st[k].size() + 1.0;
+    S.pairs += c * (c + 1.0) * 0.5;  // 7x7 block products of column k's updates
+  }
+  // seconds per iteration: a launch-latency term per sparse level and per
+  // supernode column, plus the block products at an effective FP64 rate
+  S.cost = 8e-6 * S.nlev + 25e-6 * (nf - S.sn0) + S.pairs * 686.0 / 1e11;
+  return S;
+}
+
 static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, const int32_t* hj,
                               int fixed, Plan& P) {
   P.n = n;
@@ -701,64 +881,18 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   std::vector<int> freev;
   for (int v = 0; v < n; ++v)
     if (v != fixed) freev.push_back(v);
-  std::vector<int> perm;
-  nested_dissection(freev, adj, perm);
-  const int nf = (int)perm.size();
+  std::vector<int> nd_order, md_order;
+  nested_dissection(freev, adj, nd_order);
+  minimum_degree(freev, adj, md_order);
+  Symbolic A = analyse(nd_order, adj), B = analyse(md_order, adj);
+  Symbolic& S = B.cost < A.cost ? B : A;
+  const int nf = (int)S.perm.size();
   P.nf = nf;
-  std::vector<int> inew(n, -1);
-  for (int k = 0; k < nf; ++k) inew[perm[k]] = k;
-  // symbolic factorisation of the order `perm`: structure of every column,
-  // elimination tree
-  std::vector<std::vector<int>> children;
-  std::vector<std::set<int>> st;
-  std::vector<int> parent;
-  auto symbolic = [&]() {
-    for (int k = 0; k < nf; ++k) inew[perm[k]] = k;
-    children.assign(nf, {});
-    st.assign(nf, {});
-    parent.assign(nf, -1);
-    for (int k = 0; k < nf; ++k) {
-      for (int u : adj[perm[k]]) {
-        const int q = inew[u];
-        if (q > k) st[k].insert(q);
-      }
-      for (int c : children[k])
-        for (int q : st[c])
-          if (q > k) st[k].insert(q);
-      if (!st[k].empty()) {
-        parent[k] = *st[k].begin();
-        children[parent[k]].push_back(k);
-      }
-    }
-  };
-  symbolic();
-  // Columns at the top of the elimination tree that are alone in their level
-  // form a chain that would be factored one CTA at a time.  They are moved to
-  // the end of the order (eliminating these separator-like nodes last adds no
-  // fill elsewhere) and, with the root clique, become one dense supernode
-  // (explicit zero fill) factored right-looking across all SMs.
-  {
-    std::vector<int> lv(nf, 0), cnt(nf + 1, 0);
-    for (int k = 0; k < nf; ++k)
-      for (int c : children[k]) lv[k] = std::max(lv[k], lv[c] + 1);
-    for (int k = 0; k < nf; ++k) cnt[lv[k]]++;
-    std::vector<int> chain, rest;
-    for (int k = 0; k < nf; ++k) (cnt[lv[k]] == 1 ? chain : rest).push_back(k);
-    if ((int)chain.size() >= SN_MIN) {
-      const bool suffix = chain.front() == nf - (int)chain.size();
-      if (!suffix) {
-        std::vector<int> np;
-        for (int k : rest) np.push_back(perm[k]);
-        for (int k : chain) np.push_back(perm[k]);
-        perm = np;
-        symbolic();
-      }
-      for (int k = nf - (int)chain.size(); k < nf; ++k) {
-        st[k].clear();
-        for (int q = k + 1; q < nf; ++q) st[k].insert(q);
-      }
-    }
-  }
+  P.ordering = &S == &B ? 1 : 0;
+  std::vector<int>& perm = S.perm;
+  std::vector<int>& inew = S.inew;
+  std::vector<std::vector<int>>& children = S.children;
+  std::vector<std::set<int>>& st = S.st;
   // blocks: diagonal k -> k; off-diagonal numbered column by column
   std::vector<int> col_ptr(nf + 1, 0), off_row, off_blk;
   std::map<std::pair<int, int>, int> bidx;  // (row, col) -> block
@@ -780,12 +914,7 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
     for (int k : st[j]) rowstruct[k].push_back(j);
   // trailing dense supernode: the longest suffix of columns whose structure is
   // every later column; it is factored right-looking across all SMs
-  int s0 = nf;
-  for (int k = nf - 1; k >= 0; --k) {
-    if ((int)st[k].size() != nf - 1 - k) break;
-    s0 = k;
-  }
-  P.sn0 = (nf - s0 >= SN_MIN) ? s0 : nf;
+  P.sn0 = S.sn0;
   // update groups: for every block (i, k) of column k, the products
   // L_ij L_kj^T of its descendants j, in descendant order (for supernode
   // columns only the descendants below the supernode, gathered in sn_grp)
@@ -835,6 +964,7 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   std::vector<int> level_cols(std::max(nsp, 1)), fill = P.level_ptr;
   for (int k = 0; k < nsp; ++k) level_cols[fill[level[k]]++] = k;
   P.n_sn_groups = (int)sn_grp.size() / 3;
+  P.nlev = nlev;
   // assembly lists: kind 0 = Cii, 1 = Cjj, 2 = Cij, 3 = Cij^T
   std::vector<std::vector<int>> asmv(nb), gv(nf);
   for (int e = 0; e < m; ++e) {
@@ -919,6 +1049,7 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   chk(upload(P, &P.d_row_ptr, row_ptr));
   chk(upload(P, &P.d_row, row));
   chk(upload(P, &P.d_level_cols, level_cols));
+  chk(upload(P, &P.d_level_ptr, P.level_ptr));
   chk(upload(P, &P.d_asm_ptr, asm_ptr));
   chk(upload(P, &P.d_asm, asm_it));
   chk(upload(P, &P.d_g_ptr, g_ptr));
@@ -1048,6 +1179,46 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
     ctx->ext[pkey] = P;
   }
   const ec3r_pg_opts o = *opts;
+  PgDev dv{};
+  dv.n = n_nodes;
+  dv.m = n_edges;
+  dv.nf = P->nf;
+  dv.n_blocks = P->n_blocks;
+  dv.sn0 = P->sn0;
+  dv.nlev = P->nlev;
+  dv.n_sn_groups = P->n_sn_groups;
+  dv.iters = o.iters;
+  dv.lambda = o.lm_lambda;
+  dv.ei = P->d_ei;
+  dv.ej = P->d_ej;
+  dv.perm = P->d_perm;
+  dv.col_ptr = P->d_col_ptr;
+  dv.off_row = P->d_off_row;
+  dv.off_blk = P->d_off_blk;
+  dv.grp_ptr = P->d_grp_ptr;
+  dv.grp = P->d_grp;
+  dv.upd_ab = P->d_upd_ab;
+  dv.sn_grp = P->d_sn_grp;
+  dv.row_ptr = P->d_row_ptr;
+  dv.row = P->d_row;
+  dv.level_ptr = P->d_level_ptr;
+  dv.level_cols = P->d_level_cols;
+  dv.asm_ptr = P->d_asm_ptr;
+  dv.asm_it = P->d_asm;
+  dv.g_ptr = P->d_g_ptr;
+  dv.g_it = P->d_g;
+  dv.L = P->d_L;
+  dv.b = P->d_b;
+  dv.contrib = P->d_contrib;
+  dv.gvec = P->d_gvec;
+  dv.chi2e = P->d_chi2e;
+  dv.idiag = P->d_idiag;
+  dv.chi2 = d_chi2;
+  dv.fail = P->d_fail;
+  dv.flags = ctx->d_flags;
+  dv.Tij = d_Tij;
+  dv.info = d_info;
+  dv.nodes = d_nodes;
   const std::string gkey =
       key_of("pg", {(uint64_t)P, (uint64_t)d_nodes, (uint64_t)d_Tij, (uint64_t)d_info,
                     (uint64_t)d_chi2, (uint64_t)o.iters, dbits(o.lm_lambda),
@@ -1059,36 +1230,28 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
                                       d_Tij, d_nodes, P->d_W0, P->d_W1, P->d_anc0, P->d_anc1,
                                       P->rounds);
       });
-    const int nlev = (int)P->level_ptr.size() - 1;
+    const int nlev = P->nlev;
     for (int itn = 0; itn <= o.iters; ++itn) {
       const bool last = itn == o.iters;  // last pass only evaluates chi^2
       if (n_edges > 0)
         traced(ctx, cs, "pg_linearize", [&] {
-          k_pg_linearize<<<n_edges, 32, 0, cs>>>(P->d_ei, P->d_ej, d_nodes, d_Tij, d_info,
-                                                 P->d_contrib, P->d_gvec, P->d_chi2e, last ? 0 : 1);
+          k_pg_linearize<<<n_edges, 32, 0, cs>>>(dv, last ? 0 : 1);
         });
       if (last) {
         if (d_chi2)
           traced(ctx, cs, "pg_assemble", [&] {
-            k_pg_assemble<<<1, 32, 0, cs>>>(0, 0, n_edges, P->d_asm_ptr, P->d_asm, P->d_g_ptr,
-                                            P->d_g, P->d_contrib, P->d_gvec, P->d_chi2e, 0.0,
-                                            P->d_L, P->d_b, d_chi2 + itn, P->d_fail);
+            k_pg_assemble<<<1, 32, 0, cs>>>(dv, 0, 0, d_chi2 + itn);
           });
         break;
       }
       traced(ctx, cs, "pg_assemble", [&] {
-        k_pg_assemble<<<P->n_blocks + P->nf + 1, 32, 0, cs>>>(
-            P->n_blocks, P->nf, n_edges, P->d_asm_ptr, P->d_asm, P->d_g_ptr, P->d_g,
-            P->d_contrib, P->d_gvec, P->d_chi2e, o.lm_lambda, P->d_L, P->d_b,
-            d_chi2 ? d_chi2 + itn : nullptr, P->d_fail);
+        k_pg_assemble<<<P->n_blocks + P->nf + 1, 32, 0, cs>>>(dv, P->n_blocks, P->nf,
+                                                              d_chi2 ? d_chi2 + itn : nullptr);
       });
       if (P->nf == 0) continue;
       for (int l = 0; l < nlev; ++l)
         traced(ctx, cs, "pg_factor", [&] {
-          k_pg_factor<<<P->level_ptr[l + 1] - P->level_ptr[l], 32 * FWARPS, 0, cs>>>(
-              P->d_level_cols + P->level_ptr[l], P->d_col_ptr, P->d_off_blk, P->d_grp_ptr,
-              P->d_grp, P->d_upd_ab, P->d_row_ptr, P->d_row, P->d_L, P->d_b, P->d_idiag,
-              ctx->d_flags, P->d_fail);
+          k_pg_factor<<<P->level_ptr[l + 1] - P->level_ptr[l], 32 * FWARPS, 0, cs>>>(dv, l);
         });
       if (P->sn0 < P->nf) {
         const int nf = P->nf;
@@ -1117,13 +1280,10 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
       }
       for (int l = nlev - 1; l >= 0; --l)
         traced(ctx, cs, "pg_backsolve", [&] {
-          k_pg_backsolve<<<P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs>>>(
-              P->d_level_cols + P->level_ptr[l], P->d_col_ptr, P->d_off_row, P->d_off_blk,
-              P->d_L, P->d_idiag, P->d_b);
+          k_pg_backsolve<<<P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs>>>(dv, l);
         });
       traced(ctx, cs, "pg_update", [&] {
-        k_pg_update<<<(P->nf + 63) / 64, 64, 0, cs>>>(P->nf, P->d_perm, P->d_b, d_nodes,
-                                                      P->d_fail);
+        k_pg_update<<<(P->nf + 63) / 64, 64, 0, cs>>>(dv);
       });
     }
     EC3R_CUDA_TRY(ctx, cudaGetLastError());

@@ -118,3 +118,20 @@ def test_invalid_edges_rejected(ctx):
         ctx.pose_graph_correct(nodes, [1], [1], T)
     with pytest.raises(ec3r.Ec3rError):
         ctx.pose_graph_correct(nodes, [0], [3], T)
+
+
+@pytest.mark.timeout(900)
+def test_large_loop_graph_one_iteration_matches_oracle(ctx):
+    """1000 nodes, 300 random loops (minimum-degree ordering, a dense trailing
+    supernode in the factor): one Gauss-Newton step against the oracle's dense
+    FP64 solve."""
+    n = 1000
+    g = synth.make_pose_graph(synth.SEED_BASE + 5, n, 300)
+    ei, ej, Tij = graph_from_synth(g)
+    init = opg.chain_init(n, ei, ej, Tij)
+    ref, hist, _ = opg.gauss_newton(init, ei, ej, Tij, iters=1)
+    nodes = rows([sim3.identity()] * n)
+    chi2 = ctx.pose_graph_correct(nodes, ei, ej, rows(Tij), iters=1)
+    assert ctx.sync_status() == 0
+    np.testing.assert_allclose(chi2.cpu().numpy(), np.array(hist), rtol=TOL)
+    assert_poses_close(tuples(nodes), ref)
