@@ -470,7 +470,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_adj_scatter(
 #pragma unroll
           for (int r = 0; r < 3; ++r)
             e[r] = fma2(Sp[3 * r], X[0],
-                        fma2(Sp[3 * r + 1], X[1], fma2(Sp[3 * r + 2], X[2], add2(Sp[9 + r], nY[r]))));
+                        fma2(Sp[3 * r + 1], X[1],
+                             fma2(Sp[3 * r + 2], X[2], add2(Sp[9 + r], nY[r]))));
           rr = fma2(e[0], e[0], fma2(e[1], e[1], mul2(e[2], e[2])));
           rs = make_float2(rsqrtf(rr.x), rsqrtf(rr.y));
           const float2 dr = mul2(f2(delta), rs);
@@ -708,87 +709,103 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
   const int rule = opts->weight_rule;
   const dim3 grid((unsigned)(n_tiles > 0 ? n_tiles : 1));
   const int solve_blocks = n_pairs;  // one warp per CTA: pairs spread over all SMs' FP64 pipes
-  traced(ctx, s, "adj_init", [&] {
-    k_adj_init<<<(n_pairs + 127) / 128, 128, 0, s>>>(n_pairs, iters, ckpt, state,
-                                                    (const int32_t*)p_st, (const double*)p_cost,
-                                                    d_grad_S, d_grad_cost, adj);
-  });
-  const bool cost_path = d_grad_cost != nullptr;
-  if (cost_path && n_tiles > 0)
-    traced(ctx, s, "adj_reduce", [&] {
-      if (vec)
-        k_adj_reduce<0, false, true><<<grid, THREADS, 0, s>>>(
-            d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
-            iters, delta, rule, part);
-      else
-        k_adj_reduce<0, false, false><<<grid, THREADS, 0, s>>>(
-            d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
-            iters, delta, rule, part);
-    });
-  traced(ctx, s, "adj_solve", [&] {
-    k_adj_solve<<<solve_blocks, 32, 0, s>>>(n_pairs, iters, iters, d_link_off, (int)tpl, part,
-                                             cost_path && n_tiles > 0, 1, ckpt, adj, gM);
-  });
-  for (int k = iters; k >= 2; --k) {
-    if (n_tiles > 0)
-      traced(ctx, s, "adj_reduce", [&] {
-        const bool last = k == iters;
-        if (vec && last)
-          k_adj_reduce<1, true, true><<<grid, THREADS, 0, s>>>(
-              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
-              k, delta, rule, part);
-        else if (vec)
-          k_adj_reduce<1, false, true><<<grid, THREADS, 0, s>>>(
-              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
-              k, delta, rule, part);
-        else if (last)
-          k_adj_reduce<1, true, false><<<grid, THREADS, 0, s>>>(
-              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
-              k, delta, rule, part);
-        else
-          k_adj_reduce<1, false, false><<<grid, THREADS, 0, s>>>(
-              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
-              k, delta, rule, part);
-      });
-    traced(ctx, s, "adj_solve", [&] {
-      k_adj_solve<<<solve_blocks, 32, 0, s>>>(n_pairs, iters, k - 1, d_link_off, (int)tpl, part,
-                                               n_tiles > 0, 0, ckpt, adj, gM);
-    });
-  }
   void* p_refs;
   if ((st = ensure_buf(ctx, "adj.refs", sizeof(int32_t) * (size_t)(n_frames + 1), s, &p_refs)))
     return st;
   int32_t* refs = (int32_t*)p_refs;
   int32_t* any_shared = refs + n_frames;
-  EC3R_CUDA_TRY(ctx, cudaMemsetAsync(refs, 0, sizeof(int32_t) * (size_t)(n_frames + 1), s));
-  if (n_links > 0)
-    traced(ctx, s, "adj_refcount", [&] {
-      k_adj_refcount<<<(unsigned)((n_links + 255) / 256), 256, 0, s>>>(
-          n_links, n_frames, d_src, d_tgt, link_pair, refs, any_shared);
+  const double* gcost = d_grad_cost;
+  const std::string gkey =
+      key_of("adj", {(uint64_t)d_xyz, (uint64_t)d_conf, (uint64_t)n_frames, (uint64_t)hw,
+                     (uint64_t)n_pairs, (uint64_t)n_links, (uint64_t)d_link_off, (uint64_t)d_src,
+                     (uint64_t)d_tgt, fbits(delta), (uint64_t)iters, (uint64_t)rule,
+                     (uint64_t)d_grad_S, (uint64_t)gcost, (uint64_t)d_grad_xyz,
+                     (uint64_t)d_grad_conf, (uint64_t)p_st, (uint64_t)p_cost, (uint64_t)vec});
+  return run_graph(ctx, gkey, s, [&](cudaStream_t cs) -> ec3r_status {
+    // Branch: the frames' reference counts and the zeroing of every frame that
+    // the scatter does not write directly depend only on the link structure, so
+    // they run beside the reduction sweeps and solves (filling the HBM-idle
+    // time of the FP64 solves) and join before the scatter.
+    cudaStream_t side = ctx->side_stream;
+    EC3R_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, cs));
+    EC3R_CUDA_TRY(ctx, cudaStreamWaitEvent(side, ctx->ev_fork, 0));
+    EC3R_CUDA_TRY(ctx, cudaMemsetAsync(refs, 0, sizeof(int32_t) * (size_t)(n_frames + 1), side));
+    if (n_links > 0)
+      traced(ctx, side, "adj_refcount", [&] {
+        k_adj_refcount<<<(unsigned)((n_links + 255) / 256), 256, 0, side>>>(
+            n_links, n_frames, d_src, d_tgt, link_pair, refs, any_shared);
+      });
+    traced(ctx, side, "adj_zero_frames", [&] {
+      k_adj_zero_frames<<<(unsigned)n_frames, 512, 0, side>>>(hw, refs, d_grad_xyz, d_grad_conf);
     });
-  traced(ctx, s, "adj_zero_frames", [&] {
-    k_adj_zero_frames<<<(unsigned)n_frames, 512, 0, s>>>(hw, refs, d_grad_xyz, d_grad_conf);
+    EC3R_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, side));
+    traced(ctx, cs, "adj_init", [&] {
+      k_adj_init<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, iters, ckpt, state,
+                                                      (const int32_t*)p_st, (const double*)p_cost,
+                                                      d_grad_S, d_grad_cost, adj);
+    });
+    const bool cost_path = d_grad_cost != nullptr;
+    if (cost_path && n_tiles > 0)
+      traced(ctx, cs, "adj_reduce", [&] {
+        if (vec)
+          k_adj_reduce<0, false, true><<<grid, THREADS, 0, cs>>>(
+              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
+              iters, delta, rule, part);
+        else
+          k_adj_reduce<0, false, false><<<grid, THREADS, 0, cs>>>(
+              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
+              iters, delta, rule, part);
+      });
+    traced(ctx, cs, "adj_solve", [&] {
+      k_adj_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, iters, iters, d_link_off, (int)tpl, part,
+                                               cost_path && n_tiles > 0, 1, ckpt, adj, gM);
+    });
+    for (int k = iters; k >= 2; --k) {
+      if (n_tiles > 0)
+        traced(ctx, cs, "adj_reduce", [&] {
+          const bool last = k == iters;
+          if (vec && last)
+            k_adj_reduce<1, true, true><<<grid, THREADS, 0, cs>>>(
+                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM,
+                iters, k, delta, rule, part);
+          else if (vec)
+            k_adj_reduce<1, false, true><<<grid, THREADS, 0, cs>>>(
+                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM,
+                iters, k, delta, rule, part);
+          else if (last)
+            k_adj_reduce<1, true, false><<<grid, THREADS, 0, cs>>>(
+                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM,
+                iters, k, delta, rule, part);
+          else
+            k_adj_reduce<1, false, false><<<grid, THREADS, 0, cs>>>(
+                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM,
+                iters, k, delta, rule, part);
+        });
+      traced(ctx, cs, "adj_solve", [&] {
+        k_adj_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, iters, k - 1, d_link_off, (int)tpl,
+                                                 part, n_tiles > 0, 0, ckpt, adj, gM);
+      });
+    }
+    EC3R_CUDA_TRY(ctx, cudaStreamWaitEvent(cs, ctx->ev_join, 0));  // frame references, zeroing
+    if (n_tiles > 0) {
+      const size_t shm = sizeof(float2) * SC_PAIRS * (size_t)iters;
+      traced(ctx, cs, "adj_scatter", [&] {
+        if (vec)
+          k_adj_scatter<true><<<grid, THREADS, shm, cs>>>(
+              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
+              delta, rule, lg, refs, d_grad_xyz, d_grad_conf);
+        else
+          k_adj_scatter<false><<<grid, THREADS, shm, cs>>>(
+              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
+              delta, rule, lg, refs, d_grad_xyz, d_grad_conf);
+      });
+      traced(ctx, cs, "adj_frames", [&] {
+        k_adj_frames<<<(unsigned)((hw + 255) / 256), 256, 0, cs>>>(hw, n_links, d_src, d_tgt,
+                                                                  link_pair, refs, any_shared, lg,
+                                                                  d_grad_xyz, d_grad_conf);
+      });
+    }
+    EC3R_CUDA_TRY(ctx, cudaGetLastError());
+    return EC3R_OK;
   });
-  if (n_tiles > 0) {
-    const size_t shm = sizeof(float2) * SC_PAIRS * (size_t)iters;
-    traced(ctx, s, "adj_scatter", [&] {
-      if (vec)
-        k_adj_scatter<true><<<grid, THREADS, shm, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt,
-                                                       link_pair, state, adj, ckpt, gM, iters,
-                                                       delta, rule, lg, refs, d_grad_xyz,
-                                                       d_grad_conf);
-      else
-        k_adj_scatter<false><<<grid, THREADS, shm, s>>>(d_xyz, d_conf, hw, (int)tpl, d_src,
-                                                        d_tgt, link_pair, state, adj, ckpt, gM,
-                                                        iters, delta, rule, lg, refs, d_grad_xyz,
-                                                        d_grad_conf);
-    });
-    traced(ctx, s, "adj_frames", [&] {
-      k_adj_frames<<<(unsigned)((hw + 255) / 256), 256, 0, s>>>(hw, n_links, d_src, d_tgt,
-                                                                link_pair, refs, any_shared, lg,
-                                                                d_grad_xyz, d_grad_conf);
-    });
-  }
-  EC3R_CUDA_TRY(ctx, cudaGetLastError());
-  return EC3R_OK;
 }

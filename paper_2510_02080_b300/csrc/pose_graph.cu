@@ -684,7 +684,8 @@ struct Plan : Extension {
   int *d_ei = nullptr, *d_ej = nullptr, *d_perm = nullptr;
   int *d_col_ptr = nullptr, *d_off_row = nullptr, *d_off_blk = nullptr;
   int *d_grp_ptr = nullptr, *d_grp = nullptr, *d_upd_ab = nullptr, *d_sn_grp = nullptr;
-  int sn0 = 0, n_sn_groups = 0, ordering = 0;  // ordering: 0 nested dissection, 1 min degree  // columns >= sn0 form the dense trailing supernode
+  int sn0 = 0, n_sn_groups = 0;  // columns >= sn0 form the dense trailing supernode
+  int ordering = 0;              // 0 nested dissection, 1 minimum degree
   int *d_row_ptr = nullptr, *d_row = nullptr;
   int *d_level_cols = nullptr, *d_level_ptr = nullptr, *d_asm_ptr = nullptr, *d_asm = nullptr;
   int nlev = 0;
