@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_adj_reduce(
     acc[9] += g0; acc[10] += g1; acc[11] += g2;
   };
 
+#pragma unroll 2
   for (int g = threadIdx.x; g < TILE / 4; g += THREADS) {
     const int i0 = 4 * g;
     if (i0 >= npx) break;
@@ -722,23 +723,6 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
                      (uint64_t)d_grad_S, (uint64_t)gcost, (uint64_t)d_grad_xyz,
                      (uint64_t)d_grad_conf, (uint64_t)p_st, (uint64_t)p_cost, (uint64_t)vec});
   return run_graph(ctx, gkey, s, [&](cudaStream_t cs) -> ec3r_status {
-    // Branch: the frames' reference counts and the zeroing of every frame that
-    // the scatter does not write directly depend only on the link structure, so
-    // they run beside the reduction sweeps and solves (filling the HBM-idle
-    // time of the FP64 solves) and join before the scatter.
-    cudaStream_t side = ctx->side_stream;
-    EC3R_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, cs));
-    EC3R_CUDA_TRY(ctx, cudaStreamWaitEvent(side, ctx->ev_fork, 0));
-    EC3R_CUDA_TRY(ctx, cudaMemsetAsync(refs, 0, sizeof(int32_t) * (size_t)(n_frames + 1), side));
-    if (n_links > 0)
-      traced(ctx, side, "adj_refcount", [&] {
-        k_adj_refcount<<<(unsigned)((n_links + 255) / 256), 256, 0, side>>>(
-            n_links, n_frames, d_src, d_tgt, link_pair, refs, any_shared);
-      });
-    traced(ctx, side, "adj_zero_frames", [&] {
-      k_adj_zero_frames<<<(unsigned)n_frames, 512, 0, side>>>(hw, refs, d_grad_xyz, d_grad_conf);
-    });
-    EC3R_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, side));
     traced(ctx, cs, "adj_init", [&] {
       k_adj_init<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, iters, ckpt, state,
                                                       (const int32_t*)p_st, (const double*)p_cost,
@@ -786,7 +770,25 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
                                                  part, n_tiles > 0, 0, ckpt, adj, gM);
       });
     }
-    EC3R_CUDA_TRY(ctx, cudaStreamWaitEvent(cs, ctx->ev_join, 0));  // frame references, zeroing
+    EC3R_CUDA_TRY(ctx, cudaMemsetAsync(refs, 0, sizeof(int32_t) * (size_t)(n_frames + 1), cs));
+    if (n_links > 0)
+      traced(ctx, cs, "adj_refcount", [&] {
+        k_adj_refcount<<<(unsigned)((n_links + 255) / 256), 256, 0, cs>>>(
+            n_links, n_frames, d_src, d_tgt, link_pair, refs, any_shared);
+      });
+    // Branch: zeroing every frame that the scatter does not write directly
+    // (HBM-bound) runs beside the ALU-bound scatter, which writes only the
+    // other frames; both join before the shared frames are summed.
+    // (Under per-kernel profiling everything stays on one stream.)
+    cudaStream_t side = ctx->profiling ? cs : ctx->side_stream;
+    if (side != cs) {
+      EC3R_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, cs));
+      EC3R_CUDA_TRY(ctx, cudaStreamWaitEvent(side, ctx->ev_fork, 0));
+    }
+    traced(ctx, side, "adj_zero_frames", [&] {
+      k_adj_zero_frames<<<(unsigned)n_frames, 512, 0, side>>>(hw, refs, d_grad_xyz, d_grad_conf);
+    });
+    if (side != cs) EC3R_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, side));
     if (n_tiles > 0) {
       const size_t shm = sizeof(float2) * SC_PAIRS * (size_t)iters;
       traced(ctx, cs, "adj_scatter", [&] {
@@ -799,12 +801,14 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
               d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
               delta, rule, lg, refs, d_grad_xyz, d_grad_conf);
       });
+    }
+    if (side != cs) EC3R_CUDA_TRY(ctx, cudaStreamWaitEvent(cs, ctx->ev_join, 0));
+    if (n_tiles > 0)
       traced(ctx, cs, "adj_frames", [&] {
         k_adj_frames<<<(unsigned)((hw + 255) / 256), 256, 0, cs>>>(hw, n_links, d_src, d_tgt,
                                                                   link_pair, refs, any_shared, lg,
                                                                   d_grad_xyz, d_grad_conf);
       });
-    }
     EC3R_CUDA_TRY(ctx, cudaGetLastError());
     return EC3R_OK;
   });
