@@ -587,6 +587,38 @@ def run_workload(args):
         npts = conf.numel()
         out["fusion"] = {"points": npts, "kept": kept, "ms": fms,
                          "gbs_at_26B_per_point": 26.0 * npts / (fms * 1e-3) / 1e9}
+    elif args.workload == "depth200":
+        # the 200-submap chain given as depth maps + cameras (the paper's submaps
+        # are unprojected depths): registration straight from depth, 16 B per
+        # correspondence and sweep instead of 32
+        M = args.submaps
+        ch = synth.make_depth_chain(synth.SEED_BASE + 46, M=M, F=5, H=294, W=518, device=dev)
+        dps = ch.pairs()
+        fin = (torch.isfinite(dps.depth) & (dps.depth > 0) & torch.isfinite(dps.conf) &
+               (dps.conf > 0)).view(dps.depth.shape[0], -1)
+        n = int((fin[dps.src.long()] & fin[dps.tgt.long()]).sum())
+        del fin
+        S = torch.empty((dps.n_pairs, 13), dtype=torch.float64, device=dev)
+        st = torch.empty((dps.n_pairs,), dtype=torch.int32, device=dev)
+        ms = _time(lambda: ctx.align_submaps_depth(dps.depth, dps.conf, dps.cams, dps.link_off,
+                                                   dps.src, dps.tgt, delta=DELTA, iters=ITERS,
+                                                   out=S, status=st), 10)
+        assert ctx.sync_status() == 0 and int((st != 0).sum()) == 0
+        ctx.profile(True)
+        ctx.profile_read()
+        ctx.align_submaps_depth(dps.depth, dps.conf, dps.cams, dps.link_off, dps.src, dps.tgt,
+                                delta=DELTA, iters=ITERS, out=S, status=st)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        sw = prof["depth_sweep"]
+        sweep_ms = sw[0] / sw[1]
+        px = int(dps.link_off[-1]) * dps.H * dps.W
+        achieved = 16.0 * px / (sweep_ms * 1e-3) / 1e9
+        out["registration"] = {"pairs": dps.n_pairs, "valid": n, "ms": ms,
+                               "pt_iter_per_s": n * ITERS / (ms * 1e-3),
+                               "sweep_ms": sweep_ms, "sweep_gbs_at_16B_per_pixel": achieved,
+                               "sweep_frac_of_peak": achieved / peak,
+                               "kernels": {k: v[0] for k, v in prof.items()}}
     out["peak_gbs"] = peak
     out["peak_kind"] = peak_kind
     print(json.dumps(out), flush=True)
@@ -602,7 +634,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--workload", default="chain200",
-                    choices=["chain200", "pair1", "loops512", "adjoint1", "map1000"],
+                    choices=["chain200", "pair1", "loops512", "adjoint1", "map1000",
+                             "depth200"],
                     help="chain200 is the benchmark; the others measure the other workloads")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="leave the adjoint out of the step (profiling only)")

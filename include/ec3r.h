@@ -234,6 +234,45 @@ ec3r_status ec3r_align_submaps_noalloc(const float* d_xyz, const float* d_conf,
                                        void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Registration straight from depth maps and cameras (Sec. III-C: a submap   */
+/* is the inverse projection of the predicted depths through the predicted   */
+/* cameras, one point per keyframe pixel)                                    */
+/* ------------------------------------------------------------------------ */
+
+/* A frame's pinhole camera and its pose in its submap. */
+typedef struct {
+  float fx, fy, cx, cy; /* focal lengths and principal point, pixels */
+  float R[9];           /* camera -> submap rotation, row-major */
+  float t[3];           /* camera -> submap translation */
+} ec3r_camera;          /* 64 bytes */
+
+/*
+ * The registration of ec3r_align_submaps applied to the pointmaps
+ *   X(v, u) = R (d(v, u) * ((u - cx) / fx, (v - cy) / fy, 1)) + t
+ * of every frame (pixel row v, column u; u, v integers; d the depth along the
+ * optical axis), without forming them: each link is swept in its two cameras'
+ * frames and reads 4-byte depths (16 bytes per correspondence with the
+ * confidences instead of 32).  A pixel whose depth is not finite or not > 0
+ * is invalid (like a non-finite point).
+ *
+ * d_depth and d_conf: float32 [n_frames][H][W], device.  d_cams: ec3r_camera
+ * [n_frames], device.  Pairs, links, pair thresholds, options, outputs,
+ * statuses and the cost are as for ec3r_align_submaps (the output Sim(3) maps
+ * src-submap coordinates to tgt-submap coordinates), except that only FP32
+ * moments are offered (opts->precision must be EC3R_PREC_FP32C) and the call
+ * keeps no checkpoints for ec3r_align_submaps_backward.  H * W < 2^31.
+ * Workspace is context-owned; first calls (and calls with larger problems)
+ * allocate and must not be captured.
+ */
+ec3r_status ec3r_align_submaps_depth(ec3r_ctx* ctx, const float* d_depth, const float* d_conf,
+                                     const ec3r_camera* d_cams, int64_t n_frames, int H, int W,
+                                     int n_pairs, int64_t n_links, const int32_t* d_link_off,
+                                     const int32_t* d_src, const int32_t* d_tgt,
+                                     const float* d_pair_conf_min, const ec3r_align_opts* opts,
+                                     ec3r_sim3* d_out, int32_t* d_pair_status,
+                                     double* d_pair_cost, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Pose graph: Sim(3) submap poses refined by Gauss-Newton (Sec. III-E)     */
 /* ------------------------------------------------------------------------ */
 

@@ -15,6 +15,9 @@ in float64 numpy, written from the paper:
                     Huber-IRLS loop around it.
 * ``pose_graph``  - edge error e_ij = log(T_ij^-1 T_i^-1 T_j), chi^2,
                     chaining initialisation and Gauss-Newton (Sec. III-E).
+* ``unproject``   - inverse projection of depth maps through pinhole cameras
+                    (Sec. III-C "Feed-Forward Inference": submaps from the
+                    predicted depths and cameras).
 * ``fuse``        - confidence-filtered compaction and transform of submap
                     points into the global frame (Sec. III-C "Point
                     Correction": global coordinates of all submap points).

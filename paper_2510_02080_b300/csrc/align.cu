@@ -106,63 +106,6 @@ __global__ void __launch_bounds__(THREADS) k_setup(
 // --------------------------------------------------------------------------
 // moment sweep
 // --------------------------------------------------------------------------
-enum Kind { FIRST = 0, IRLS = 1, COST = 2 };
-
-// One point's contribution.  T is float (FP32 moments) or double (FP64).
-template <typename T, int KIND>
-struct PointOp {
-  T A[9], b[3], Ap[9], bp[3], pp[3], pq[3], delta;
-  float cmin;
-  int rule;
-
-  __device__ __forceinline__ void operator()(float p0, float p1, float p2, float q0, float q1,
-                                             float q2, float cp, float cq, T* acc) const {
-    const bool v = finitef(p0) && finitef(p1) && finitef(p2) && finitef(q0) && finitef(q1) &&
-                   finitef(q2) && finitef(cp) && finitef(cq) && cp > cmin && cq > cmin;
-    const T x0 = v ? (T)p0 - pp[0] : T(0), x1 = v ? (T)p1 - pp[1] : T(0),
-            x2 = v ? (T)p2 - pp[2] : T(0);
-    const T y0 = v ? (T)q0 - pq[0] : T(0), y1 = v ? (T)q1 - pq[1] : T(0),
-            y2 = v ? (T)q2 - pq[2] : T(0);
-    T w = rule == 0 ? (T)cp * (T)cq : (T)cp;
-    w = v ? w : T(0);
-    T h = T(1), r2 = T(0);
-    if (KIND != FIRST) {
-      const T* a = (KIND == COST) ? Ap : A;
-      const T* c = (KIND == COST) ? bp : b;
-      const T e0 = a[0] * x0 + a[1] * x1 + a[2] * x2 + c[0] - y0;
-      const T e1 = a[3] * x0 + a[4] * x1 + a[5] * x2 + c[1] - y1;
-      const T e2 = a[6] * x0 + a[7] * x1 + a[8] * x2 + c[2] - y2;
-      const T rr = e0 * e0 + e1 * e1 + e2 * e2;
-      if constexpr (sizeof(T) == 4) {
-        h = fminf(1.f, (float)delta * rsqrtf(rr));
-      } else {
-        h = rr <= delta * delta ? 1.0 : delta / sqrt(rr);
-      }
-      if (KIND == COST) {
-        const T f0 = A[0] * x0 + A[1] * x1 + A[2] * x2 + b[0] - y0;
-        const T f1 = A[3] * x0 + A[4] * x1 + A[5] * x2 + b[1] - y1;
-        const T f2 = A[6] * x0 + A[7] * x1 + A[8] * x2 + b[2] - y2;
-        r2 = f0 * f0 + f1 * f1 + f2 * f2;
-      } else {
-        r2 = rr;
-      }
-    }
-    const T om = w * h;
-    acc[M_W] += om;
-    acc[M_COST] += om * r2;
-    acc[M_CNT] += v ? T(1) : T(0);
-    if (KIND == COST) return;
-    const T wx0 = om * x0, wx1 = om * x1, wx2 = om * x2;
-    const T wy0 = om * y0, wy1 = om * y1, wy2 = om * y2;
-    acc[M_SP + 0] += wx0; acc[M_SP + 1] += wx1; acc[M_SP + 2] += wx2;
-    acc[M_SQ + 0] += wy0; acc[M_SQ + 1] += wy1; acc[M_SQ + 2] += wy2;
-    acc[M_PP] += wx0 * x0 + wx1 * x1 + wx2 * x2;
-    acc[M_QP + 0] += wy0 * x0; acc[M_QP + 1] += wy0 * x1; acc[M_QP + 2] += wy0 * x2;
-    acc[M_QP + 3] += wy1 * x0; acc[M_QP + 4] += wy1 * x1; acc[M_QP + 5] += wy1 * x2;
-    acc[M_QP + 6] += wy2 * x0; acc[M_QP + 7] += wy2 * x1; acc[M_QP + 8] += wy2 * x2;
-  }
-};
-
 // Per-tile partial moments.  Each thread sums its 32 pixels (8 groups of 4
 // consecutive pixels); warps combine by a pairwise butterfly in T; the eight
 // warp sums are added in FP64 in a fixed order.
@@ -248,11 +191,6 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 3 : 2) k_sweep(
   }
 }
 
-__device__ void write_identity(ec3r_sim3* o) {
-  o->s = 1.0;
-  for (int i = 0; i < 9; ++i) o->R[i] = (i % 4 == 0) ? 1.0 : 0.0;
-  for (int i = 0; i < 3; ++i) o->t[i] = 0.0;
-}
 
 // One warp per pair: FP64 tile sums (lane m < 19 owns moment m), then lane 0
 // solves.  `last` marks the final iteration (writes the outputs).
@@ -286,46 +224,8 @@ __global__ void __launch_bounds__(256) k_solve(int n_pairs, const int32_t* __res
   __syncwarp();
   if (lane != 0) return;
   const double* M = mom[wib];
-  unsigned status = 0;
-  const double W = M[M_W], N = M[M_CNT];
-  double R[9], d[3], s = 1.0, b[3] = {0, 0, 0};
-  if (N < 3.0) {
-    status = EC3R_PAIR_FEW_POINTS;
-  } else if (!(W > 0.0) || !isfinite(W)) {
-    status = EC3R_PAIR_ZERO_WEIGHT;
-  } else {
-    const double iw = 1.0 / W;
-    const double mp[3] = {M[M_SP] * iw, M[M_SP + 1] * iw, M[M_SP + 2] * iw};
-    const double mq[3] = {M[M_SQ] * iw, M[M_SQ + 1] * iw, M[M_SQ + 2] * iw};
-    double Sig[9];
-    bool fin = true;
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) {
-        Sig[3 * i + j] = M[M_QP + 3 * i + j] * iw - mq[i] * mp[j];
-        fin &= isfinite(Sig[3 * i + j]);
-      }
-    const double var = M[M_PP] * iw - (mp[0] * mp[0] + mp[1] * mp[1] + mp[2] * mp[2]);
-    if (!fin || !isfinite(var)) {
-      status = EC3R_PAIR_NONFINITE;
-    } else if (!(var > 0.0)) {
-      status = EC3R_PAIR_RANK;
-    } else {
-      polar_rotation(Sig, R, d);
-      if (!(d[0] > 0.0) || fabs(d[1]) <= RANK_REL_TOL * d[0]) {
-        status = EC3R_PAIR_RANK;
-      } else {
-        // tr(R^T Sig) = tr(D E): the Umeyama scale numerator
-        double tr = 0.0;
-        for (int i = 0; i < 9; ++i) tr += R[i] * Sig[i];
-        s = tr / var;
-        for (int i = 0; i < 3; ++i)
-          b[i] = mq[i] - s * (R[3 * i] * mp[0] + R[3 * i + 1] * mp[1] + R[3 * i + 2] * mp[2]);
-        bool ok = isfinite(s) && s > 0.0;
-        for (int i = 0; i < 3; ++i) ok &= isfinite(b[i]);
-        if (!ok) status = EC3R_PAIR_NONFINITE;
-      }
-    }
-  }
+  double R[9], s = 1.0, b[3] = {0, 0, 0};
+  const unsigned status = umeyama_from_moments(M, R, s, b);
   double* ck = ckpt ? ckpt + ((size_t)warp * iters + (it - 1)) * CKPT : nullptr;
   if (ck) {
     for (int m = 0; m < NMOM; ++m) ck[CK_MOM + m] = M[m];
@@ -333,55 +233,7 @@ __global__ void __launch_bounds__(256) k_solve(int n_pairs, const int32_t* __res
     for (int i = 0; i < 3; ++i) ck[CK_B + i] = b[i];
     ck[CK_STATUS] = (double)status;
   }
-  if (status) {
-    S.status = (int)status;
-    S.active = 0;
-    write_identity(&out[warp]);
-    status_out[warp] = (int)status;
-    return;
-  }
-  // shift the current estimate to "previous", store the new one
-  for (int i = 0; i < 9; ++i) {
-    S.Ap[i] = S.A[i];
-    S.Adp[i] = S.Ad[i];
-    S.Ad[i] = s * R[i];
-    S.A[i] = (float)S.Ad[i];
-  }
-  for (int i = 0; i < 3; ++i) {
-    S.bp[i] = S.b[i];
-    S.bdp[i] = S.bd[i];
-    S.bd[i] = b[i];
-    S.b[i] = (float)b[i];
-  }
-  if (last) {
-    ec3r_sim3& o = out[warp];
-    o.s = s;
-    for (int i = 0; i < 9; ++i) o.R[i] = R[i];
-    const double pp[3] = {S.piv_p[0], S.piv_p[1], S.piv_p[2]};
-    for (int i = 0; i < 3; ++i)
-      o.t[i] = b[i] + (double)S.piv_q[i] -
-               s * (R[3 * i] * pp[0] + R[3 * i + 1] * pp[1] + R[3 * i + 2] * pp[2]);
-    status_out[warp] = 0;
-  }
-}
-
-// cost = sum om r^2 / sum om from the cost sweep's partials.
-__global__ void k_cost(int n_pairs, const int32_t* __restrict__ link_off, int tpl,
-                       const double* __restrict__ partials, const PairState* __restrict__ st,
-                       double* __restrict__ cost) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_pairs) return;
-  if (!st[k].active) {
-    cost[k] = 0.0;
-    return;
-  }
-  const int64_t t0 = (int64_t)link_off[k] * tpl, t1 = (int64_t)link_off[k + 1] * tpl;
-  double w = 0.0, c = 0.0;
-  for (int64_t t = t0; t < t1; ++t) {
-    w += partials[t * NMOM + M_W];
-    c += partials[t * NMOM + M_COST];
-  }
-  cost[k] = w > 0.0 ? c / w : 0.0;
+  commit_estimate(S, status, R, s, b, last, out[warp], status_out[warp]);
 }
 
 template <typename T, bool VEC>

@@ -28,7 +28,7 @@ EXPORTS = ("ec3r_create", "ec3r_destroy", "ec3r_last_error", "ec3r_status_string
            "ec3r_version", "ec3r_sync_status", "ec3r_align_opts_default",
            "ec3r_align_submaps", "ec3r_fuse_points", "ec3r_profile", "ec3r_profile_read",
            "ec3r_align_submaps_noalloc", "ec3r_pg_opts_default", "ec3r_pose_graph_correct",
-           "ec3r_align_submaps_backward")
+           "ec3r_align_submaps_backward", "ec3r_align_submaps_depth")
 
 
 class Sim3(C.Structure):
@@ -77,13 +77,16 @@ def _declare(l):
                                     C.POINTER(C.c_int64), C.POINTER(C.c_int)]
     l.ec3r_align_submaps_backward.argtypes = [_P, _P, _P, _I64, _I64, C.c_int, _I64, _P, _P, _P,
                                               _P, C.POINTER(AlignOpts), _P, _P, _P, _P, _P]
+    l.ec3r_align_submaps_depth.argtypes = [_P, _P, _P, _P, _I64, C.c_int, C.c_int, C.c_int,
+                                           _I64, _P, _P, _P, _P, C.POINTER(AlignOpts), _P, _P,
+                                           _P, _P]
     l.ec3r_pg_opts_default.argtypes = [C.POINTER(PgOpts)]
     l.ec3r_pg_opts_default.restype = None
     l.ec3r_pose_graph_correct.argtypes = [_P, C.c_int, _P, C.c_int, _P, _P, _P, _P,
                                           C.POINTER(PgOpts), _P, _P]
     for name in ("ec3r_create", "ec3r_sync_status", "ec3r_align_submaps", "ec3r_fuse_points",
                  "ec3r_profile", "ec3r_profile_read", "ec3r_pose_graph_correct",
-                 "ec3r_align_submaps_backward"):
+                 "ec3r_align_submaps_backward", "ec3r_align_submaps_depth"):
         getattr(l, name).restype = C.c_int
 
 
@@ -193,6 +196,38 @@ class Context:
             self._h, _ptr(xyz), _ptr(conf), n_frames, hw, n_pairs, int(src.numel()),
             _ptr(link_off), _ptr(src), _ptr(tgt), _ptr(pair_conf_min), C.byref(o), _ptr(out),
             _ptr(status), _ptr(cost) if want_cost else None, _stream(stream))
+        self._check(st)
+        return out, status, (cost if want_cost else None)
+
+    def align_submaps_depth(self, depth, conf, cams, link_off, src, tgt, pair_conf_min=None, *,
+                            delta=0.02, iters=10, conf_min=0.0, rule="product", want_cost=False,
+                            out=None, status=None, cost=None, stream=None):
+        """Registration from depth [n_frames, H, W] float32, conf (same shape) and cameras
+        [n_frames, 16] float32 (fx, fy, cx, cy, R row-major, t: camera -> submap).
+        Returns (S [n_pairs,13] float64, status int32, cost|None)."""
+        if depth.dim() != 3 or tuple(conf.shape) != tuple(depth.shape):
+            raise ValueError("depth and conf must be [n_frames, H, W]")
+        n_frames, H, W = (int(v) for v in depth.shape)
+        if depth.dtype != torch.float32 or conf.dtype != torch.float32 or \
+                cams.dtype != torch.float32:
+            raise ValueError("depth, conf and cams must be float32")
+        if tuple(cams.shape) != (n_frames, 16):
+            raise ValueError("cams must be [n_frames, 16]")
+        n_pairs = int(link_off.numel()) - 1
+        dev = depth.device
+        if out is None:
+            out = torch.empty((n_pairs, 13), dtype=torch.float64, device=dev)
+        if status is None:
+            status = torch.empty((n_pairs,), dtype=torch.int32, device=dev)
+        if want_cost and cost is None:
+            cost = torch.empty((n_pairs,), dtype=torch.float64, device=dev)
+        o = AlignOpts(float(delta), int(iters), float(conf_min), RULE[rule], PREC["fp32c"],
+                      1 if want_cost else 0)
+        st = self._lib.ec3r_align_submaps_depth(
+            self._h, _ptr(depth), _ptr(conf), _ptr(cams), n_frames, H, W, n_pairs,
+            int(src.numel()), _ptr(link_off), _ptr(src), _ptr(tgt), _ptr(pair_conf_min),
+            C.byref(o), _ptr(out), _ptr(status), _ptr(cost) if want_cost else None,
+            _stream(stream))
         self._check(st)
         return out, status, (cost if want_cost else None)
 

@@ -350,6 +350,115 @@ def make_chain(seed: int, M: int, F: int = 5, H: int = 294, W: int = 518, sigma:
                  meta=dict(kind="chain", sigma=sigma, outlier_frac=outlier_frac, seed=seed))
 
 
+@dataclass
+class DepthPairSet:
+    """Frames as depth maps with their cameras, plus correspondence links.
+
+    ``depth[n_frames, H, W]`` and ``conf[n_frames, H, W]`` (float32);
+    ``cams[n_frames, 16]`` (float32) = (fx, fy, cx, cy, R row-major, t) with
+    camera -> submap pose (R, t).  Links as in ``PairSet``.
+    """
+    depth: torch.Tensor
+    conf: torch.Tensor
+    cams: torch.Tensor
+    link_off: torch.Tensor
+    src: torch.Tensor
+    tgt: torch.Tensor
+    H: int
+    W: int
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_pairs(self):
+        return int(self.link_off.numel()) - 1
+
+
+@dataclass
+class DepthChain:
+    """Submaps of ``F`` frames given as depth maps and cameras, consecutive
+    submaps sharing ``overlap`` keyframes (the last ``overlap`` frames of
+    submap m are the first ``overlap`` frames of submap m+1).
+
+    Pair ``m`` registers submap ``m+1`` (source) onto submap ``m`` (target)
+    through ``overlap`` links; its ground truth is ``T_gt[m]^-1 T_gt[m+1]``.
+    """
+    depth: torch.Tensor   # [M, F, H, W]
+    conf: torch.Tensor    # [M, F, H, W]
+    cams: torch.Tensor    # [M, F, 16]
+    T_gt: Sim3
+    H: int
+    W: int
+    F: int
+    overlap: int
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def M(self):
+        return int(self.depth.shape[0])
+
+    def pairs(self) -> DepthPairSet:
+        M, F, ov = self.M, self.F, self.overlap
+        dev = self.depth.device
+        m = torch.arange(M - 1, device=dev, dtype=torch.int64)
+        j = torch.arange(ov, device=dev, dtype=torch.int64)
+        src = ((m[:, None] + 1) * F + j[None, :]).reshape(-1).to(torch.int32)
+        tgt = (m[:, None] * F + (F - ov) + j[None, :]).reshape(-1).to(torch.int32)
+        off = (torch.arange(M, device=dev, dtype=torch.int32) * ov)
+        return DepthPairSet(self.depth.view(M * F, self.H, self.W),
+                            self.conf.view(M * F, self.H, self.W),
+                            self.cams.view(M * F, 16), off, src, tgt, self.H, self.W,
+                            meta=dict(kind="depth_chain", overlap=ov))
+
+
+def make_depth_chain(seed: int, M: int, F: int = 5, H: int = 294, W: int = 518,
+                     overlap: int = 1, sigma: float = 0.01, outlier_frac: float = 0.1,
+                     device="cpu", cast_dtype=torch.float32) -> DepthChain:
+    """Like ``make_chain`` but each frame is a depth map (along the optical
+    axis, in submap units) with its pinhole camera and camera -> submap pose.
+
+    Intrinsics: fx = fy = (W/2)/tan(hfov/2), cx = W/2 - 1/2, cy = H/2 - 1/2
+    (the ray-casting camera).  Noise is N(0, sigma^2) on the depth; a fraction
+    ``outlier_frac`` of the pixels get a depth uniform in (0, 2 x the frame's
+    largest depth).
+    """
+    if not 1 <= overlap < F:
+        raise ValueError("need 1 <= overlap < F")
+    g = _gen(seed, device)
+    scene = make_scene(g, device)
+    step = F - overlap
+    K = step * M + overlap
+    cc, cR = camera_path(g, K, device, scene=scene)
+    fov = hfovs(g, K, device)
+    lam = _uniform(g, (M,), 0.5, 2.0, device)         # world -> submap scale
+    n = H * W
+    depth = torch.empty(M, F, H, W, dtype=torch.float32, device=device)
+    conf = torch.empty(M, F, H, W, dtype=torch.float32, device=device)
+    cams = torch.empty(M, F, 16, dtype=torch.float32, device=device)
+    first = torch.arange(M, device=device) * step
+    Ts, TR, Tt = 1.0 / lam, cR[first].clone(), cc[first].clone()
+    for m in range(M):
+        kf = torch.arange(step * m, step * m + F, device=device)
+        X = cast_rays(scene, cc[kf], cR[kf], fov[kf], H, W, cast_dtype).to(torch.float64)
+        z = torch.einsum("fnk,fk->fn", X - cc[kf][:, None, :], cR[kf][:, :, 2])  # optical axis
+        d = lam[m] * z + sigma * _normal(g, (F, n), device)
+        om = torch.rand((F, n), generator=g, device=device) < outlier_frac
+        du = _uniform(g, (F, n), 0.0, 1.0, device) * 2.0 * d.max(dim=1, keepdim=True).values
+        depth[m] = torch.where(om, du, d).to(torch.float32).view(F, H, W)
+        conf[m] = _lognormal_conf(g, (F, n), device).view(F, H, W)
+        f = (W / 2.0) / torch.tan(fov[kf] / 2.0)
+        Rc = TR[m].T[None] @ cR[kf]                                  # camera -> submap
+        tc = lam[m] * ((cc[kf] - Tt[m]) @ TR[m])
+        cams[m, :, 0] = f.to(torch.float32)
+        cams[m, :, 1] = f.to(torch.float32)
+        cams[m, :, 2] = W / 2.0 - 0.5
+        cams[m, :, 3] = H / 2.0 - 0.5
+        cams[m, :, 4:13] = Rc.reshape(F, 9).to(torch.float32)
+        cams[m, :, 13:16] = tc.to(torch.float32)
+    return DepthChain(depth, conf, cams, Sim3(Ts, TR, Tt), H, W, F, overlap,
+                      meta=dict(kind="depth_chain", sigma=sigma, outlier_frac=outlier_frac,
+                                seed=seed))
+
+
 def chain_pair_truth(chain: Chain) -> Sim3:
     """Ground truth of pair m (submap m+1 -> submap m): T_m^-1 T_{m+1}."""
     s, R, t = chain.T_gt.s, chain.T_gt.R, chain.T_gt.t
