@@ -36,6 +36,7 @@ UNIT = "pt-iter/s"
 M_SUBMAPS, F_FRAMES, H, W = 200, 5, 294, 518   # the chain workload
 ITERS, DELTA = 10, 0.02
 PG_ITERS = 10
+SEED_CORRECT = 2510020800 + 56
 SWEEP_BYTES_PER_PIXEL = 32          # p, q (2 x 12 B) + c_p, c_q (2 x 4 B) per sweep
 # DRAM bytes per pixel of one sweep launch, from the ncu capture summarised in
 # profiles/irls_sweep_fp32_chain40_294x518.md (read + write / pixels); the
@@ -587,6 +588,19 @@ def run_workload(args):
         npts = conf.numel()
         out["fusion"] = {"points": npts, "kept": kept, "ms": fms,
                          "gbs_at_26B_per_point": 26.0 * npts / (fms * 1e-3) / 1e9}
+        # point correction: 2M sparse-map points, each referencing a random pixel
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(SEED_CORRECT)
+        n_sp = 2_000_000
+        refs = torch.randint(0, npts, (n_sp,), generator=gen, device=dev, dtype=torch.int64)
+        pts = torch.zeros((n_sp, 3), device=dev)
+        ncor = torch.zeros((1,), dtype=torch.int64, device=dev)
+        cms = _time(lambda: ctx.correct_points(pts, refs, xyz, conf, poses, threshold=1.0,
+                                               n_corrected=ncor), 5)
+        assert ctx.sync_status() == 0
+        out["point_correction"] = {"points": n_sp, "ms": cms,
+                                   "points_per_s": n_sp / (cms * 1e-3),
+                                   "note": "random references: 16 B gathered per point"}
     elif args.workload == "depth200":
         # the 200-submap chain given as depth maps + cameras (the paper's submaps
         # are unprojected depths): registration straight from depth, 16 B per

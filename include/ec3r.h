@@ -352,6 +352,31 @@ ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_subma
                              int64_t* d_out_idx, int64_t capacity, int64_t* d_cursor,
                              void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Point correction (Sec. III-C "Point Correction"): sparse-map points that  */
+/* correspond to submap pixels take those pixels' global coordinates         */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * For every sparse-map point i (d_points float32 [n_points][3], device,
+ * in/out) with a reference d_refs[i] = g (int64, device: the flat submap point
+ * g = m*pts_per_submap + k of ec3r_fuse_points, or -1 for none), replace the
+ * point by T_m(X_g) when the submap point is valid: its confidence is
+ * strictly greater than conf_threshold and its coordinates are finite; the
+ * point is computed exactly as ec3r_fuse_points computes the fused point of
+ * g (float32 from the float32-rounded pose, same FMA order).  Other points are
+ * left unchanged.  d_xyz / d_conf / d_poses as for ec3r_fuse_points.
+ * d_n_corrected (int64, device, nullable) is incremented by the number of
+ * corrected points.  A reference < -1 or >= n_submaps*pts_per_submap leaves
+ * its point unchanged and makes ec3r_sync_status return EC3R_ERR_INVALID_ARG.
+ * No workspace; one launch.
+ */
+ec3r_status ec3r_correct_points(ec3r_ctx* ctx, int64_t n_points, float* d_points,
+                                const int64_t* d_refs, int n_submaps, int64_t pts_per_submap,
+                                const float* d_xyz, const float* d_conf,
+                                const ec3r_sim3* d_poses, float conf_threshold,
+                                int64_t* d_n_corrected, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,3 +48,36 @@ def fuse_points(xyz, conf, poses, threshold=1.0, index_base=0):
         X = xyz[m][km].astype(np.float64)
         out_xyz[slot[m * n:(m + 1) * n][km]] = s * (X @ np.asarray(R).T) + np.asarray(t)
     return out_xyz, out_idx
+
+
+def correct_points(points, refs, xyz, conf, poses, threshold=1.0):
+    """Point correction (Sec. III-C "Point Correction"): a sparse-map point
+    that corresponds to a submap pixel takes that pixel's global coordinates.
+
+    Readings: the correspondence is given as the flat submap point g of
+    ``fuse_points`` (-1: none); the replacement happens only when the submap
+    point is valid (confidence strictly above the threshold, finite
+    coordinates), the other points keep their coordinates; the global point is
+    T_m(x) in float64 as in ``fuse_points``.
+
+    Returns (points [n, 3] float64, number corrected).
+    """
+    out = np.asarray(points, dtype=np.float64).copy()
+    xyz = np.asarray(xyz)
+    conf = np.asarray(conf)
+    M = xyz.shape[0]
+    xyz = xyz.reshape(M, -1, 3)
+    conf = conf.reshape(M, -1)
+    n = conf.shape[1]
+    count = 0
+    for i, g in enumerate(np.asarray(refs, dtype=np.int64)):
+        if g < 0:
+            continue
+        m, k = divmod(int(g), n)
+        x = xyz[m, k].astype(np.float64)
+        if not (conf[m, k] > threshold) or not np.all(np.isfinite(x)):
+            continue
+        s, R, t = poses[m]
+        out[i] = s * (np.asarray(R) @ x) + np.asarray(t)
+        count += 1
+    return out, count

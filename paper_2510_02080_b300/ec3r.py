@@ -28,7 +28,7 @@ EXPORTS = ("ec3r_create", "ec3r_destroy", "ec3r_last_error", "ec3r_status_string
            "ec3r_version", "ec3r_sync_status", "ec3r_align_opts_default",
            "ec3r_align_submaps", "ec3r_fuse_points", "ec3r_profile", "ec3r_profile_read",
            "ec3r_align_submaps_noalloc", "ec3r_pg_opts_default", "ec3r_pose_graph_correct",
-           "ec3r_align_submaps_backward", "ec3r_align_submaps_depth")
+           "ec3r_align_submaps_backward", "ec3r_align_submaps_depth", "ec3r_correct_points")
 
 
 class Sim3(C.Structure):
@@ -80,13 +80,15 @@ def _declare(l):
     l.ec3r_align_submaps_depth.argtypes = [_P, _P, _P, _P, _I64, C.c_int, C.c_int, C.c_int,
                                            _I64, _P, _P, _P, _P, C.POINTER(AlignOpts), _P, _P,
                                            _P, _P]
+    l.ec3r_correct_points.argtypes = [_P, _I64, _P, _P, C.c_int, _I64, _P, _P, _P, C.c_float,
+                                      _P, _P]
     l.ec3r_pg_opts_default.argtypes = [C.POINTER(PgOpts)]
     l.ec3r_pg_opts_default.restype = None
     l.ec3r_pose_graph_correct.argtypes = [_P, C.c_int, _P, C.c_int, _P, _P, _P, _P,
                                           C.POINTER(PgOpts), _P, _P]
     for name in ("ec3r_create", "ec3r_sync_status", "ec3r_align_submaps", "ec3r_fuse_points",
                  "ec3r_profile", "ec3r_profile_read", "ec3r_pose_graph_correct",
-                 "ec3r_align_submaps_backward", "ec3r_align_submaps_depth"):
+                 "ec3r_align_submaps_backward", "ec3r_align_submaps_depth", "ec3r_correct_points"):
         getattr(l, name).restype = C.c_int
 
 
@@ -281,6 +283,21 @@ class Context:
         st = self._lib.ec3r_fuse_points(
             self._h, M, n, _ptr(xyz), _ptr(conf), _ptr(poses), float(threshold), int(index_base),
             _ptr(out_xyz), _ptr(out_idx), int(out_idx.numel()), _ptr(cursor), _stream(stream))
+        self._check(st)
+
+
+    # -- point correction --------------------------------------------------
+    def correct_points(self, points, refs, xyz, conf, poses, *, threshold=1.0, n_corrected=None,
+                       stream=None):
+        """Sparse-map points [n, 3] (float32, in place) take the global coordinates of
+        their referenced submap points (refs int64 [n], -1 = none); xyz [M, n_sub, 3]."""
+        M = int(conf.shape[0])
+        n = int(conf.numel() // max(M, 1))
+        if points.dtype != torch.float32 or refs.dtype != torch.int64:
+            raise ValueError("points must be float32 and refs int64")
+        st = self._lib.ec3r_correct_points(
+            self._h, int(refs.numel()), _ptr(points), _ptr(refs), M, n, _ptr(xyz), _ptr(conf),
+            _ptr(poses), float(threshold), _ptr(n_corrected), _stream(stream))
         self._check(st)
 
 

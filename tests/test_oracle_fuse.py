@@ -34,3 +34,33 @@ def test_fuse_empty():
     conf = np.zeros((2, 3), np.float32)
     out_xyz, out_idx = fuse.fuse_points(xyz, conf, [(1.0, np.eye(3), np.zeros(3))] * 2)
     assert out_xyz.shape == (0, 3) and out_idx.shape == (0,)
+
+
+def test_point_correction_closed_forms():
+    """Point correction (Sec. III-C): identity pose copies the submap point;
+    translation / scale poses add t / multiply by s; invalid or missing
+    correspondences leave the sparse point unchanged."""
+    rng = np.random.default_rng(7)
+    M, n = 3, 50
+    xyz = rng.normal(size=(M, n, 3)).astype(np.float32)
+    conf = rng.uniform(0.5, 2.0, (M, n)).astype(np.float32)
+    xyz[1, 4, 2] = np.nan
+    conf[2, 9] = np.nan
+    t = np.array([1.0, -2.0, 0.5])
+    poses = [(1.0, np.eye(3), np.zeros(3)), (1.0, np.eye(3), t), (2.5, np.eye(3), np.zeros(3))]
+    refs = np.array([-1, 3, n + 7, n + 4, 2 * n + 9, 2 * n + 11, 0])
+    pts = rng.normal(size=(len(refs), 3))
+    out, cnt = fuse.correct_points(pts, refs, xyz, conf, poses, threshold=1.0)
+    for i, g in enumerate(refs):
+        m, k = divmod(int(g), n) if g >= 0 else (None, None)
+        valid = g >= 0 and conf[m, k] > 1.0 and np.all(np.isfinite(xyz[m, k]))
+        if not valid:
+            np.testing.assert_array_equal(out[i], pts[i])
+        elif m == 0:
+            np.testing.assert_array_equal(out[i], xyz[0, k].astype(np.float64))
+        elif m == 1:
+            np.testing.assert_allclose(out[i], xyz[1, k] + t, rtol=0, atol=1e-15)
+        else:
+            np.testing.assert_allclose(out[i], 2.5 * xyz[2, k].astype(np.float64), rtol=1e-15)
+    assert cnt == sum(1 for g in refs if g >= 0 and conf.reshape(-1)[g] > 1.0 and
+                      np.all(np.isfinite(xyz.reshape(-1, 3)[g])))
