@@ -633,6 +633,24 @@ def run_workload(args):
                                "sweep_ms": sweep_ms, "sweep_gbs_at_16B_per_pixel": achieved,
                                "sweep_frac_of_peak": achieved / peak,
                                "kernels": {k: v[0] for k, v in prof.items()}}
+        # fusion of every frame straight from depth (identity poses)
+        npts = dps.depth.numel()
+        kept = int(((dps.conf > 1.0) & (dps.depth > 0) & torch.isfinite(dps.depth)).sum())
+        ox = torch.empty((kept, 3), device=dev)
+        oi = torch.empty((kept,), dtype=torch.int64, device=dev)
+        cur = torch.zeros((1,), dtype=torch.int64, device=dev)
+        poses = torch.zeros((M, 13), dtype=torch.float64, device=dev)
+        poses[:, 0] = 1.0
+        poses[:, [1, 5, 9]] = 1.0
+
+        def fuse():
+            cur.zero_()
+            ctx.fuse_points_depth(dps.depth, dps.conf, dps.cams, poses, ox, oi, cur, frames=5)
+        fms = _time(fuse, 5)
+        assert ctx.sync_status() == 0 and int(cur) == kept
+        out["fusion"] = {"points": npts, "kept": kept, "ms": fms,
+                         "gbs_at_16B_plus_20B_per_kept":
+                             (16.0 * npts + 20.0 * kept) / (fms * 1e-3) / 1e9}
     out["peak_gbs"] = peak
     out["peak_kind"] = peak_kind
     print(json.dumps(out), flush=True)

@@ -352,6 +352,28 @@ ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_subma
                              int64_t* d_out_idx, int64_t capacity, int64_t* d_cursor,
                              void* stream);
 
+/*
+ * ec3r_fuse_points on the pointmaps of depth frames (Sec. III-C: submaps are
+ * the inverse projection of the predicted depths through the predicted
+ * cameras), without forming them.  Frame f of submap m is d_depth / d_conf
+ * float32 [n_submaps*frames][H][W] entry m*frames + f with camera
+ * d_cams[m*frames + f] (ec3r_camera, device; pixel and camera conventions of
+ * ec3r_align_submaps_depth).  A pixel has a point when its frame's camera is
+ * finite with nonzero focal lengths and its depth is finite and > 0; it is kept
+ * when, in addition, its confidence is strictly greater than conf_threshold.
+ * The kept point is s_m R_m (R_f x + t_f) + t_m with x the camera-frame point,
+ * evaluated in float32 from the composite pose rounded once to float32.
+ * Outputs, flat indices (g = index_base + (m*frames + f)*H*W + v*W + u),
+ * cursor and capacity behave exactly as in ec3r_fuse_points.  H * W < 2^31.
+ * Reads 8 bytes per pixel twice (count and scatter) instead of 4 + 16.
+ */
+ec3r_status ec3r_fuse_points_depth(ec3r_ctx* ctx, int n_submaps, int frames, int H, int W,
+                                   const float* d_depth, const float* d_conf,
+                                   const ec3r_camera* d_cams, const ec3r_sim3* d_poses,
+                                   float conf_threshold, int64_t index_base, float* d_out_xyz,
+                                   int64_t* d_out_idx, int64_t capacity, int64_t* d_cursor,
+                                   void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Point correction (Sec. III-C "Point Correction"): sparse-map points that  */
 /* correspond to submap pixels take those pixels' global coordinates         */

@@ -81,3 +81,32 @@ def correct_points(points, refs, xyz, conf, poses, threshold=1.0):
         out[i] = s * (np.asarray(R) @ x) + np.asarray(t)
         count += 1
     return out, count
+
+
+def fuse_points_depth(depth, conf, cams, poses, frames, threshold=1.0, index_base=0):
+    """Fusion of depth frames (Sec. III-C: submaps are unprojected depths):
+    ``unproject`` gives every pixel's submap point (none where the depth or the
+    camera is invalid); a pixel is kept when it has a point and its confidence
+    is strictly above the threshold; kept points go out in ascending flat
+    index as in ``fuse_points``.  depth / conf [M*frames, H, W], cams
+    [M*frames, 16], poses: list of M (s, R, t).
+
+    Returns (out_xyz [K, 3] float64, out_idx [K] int64).
+    """
+    from . import unproject as up
+    d = np.asarray(depth)
+    nfr = d.shape[0]
+    M = nfr // frames
+    X = up.unproject(d, cams).reshape(M, -1, 3)              # [M, frames*H*W, 3]
+    c = np.asarray(conf, dtype=np.float64).reshape(M, -1)
+    with np.errstate(invalid="ignore"):
+        keep = (c > threshold) & np.all(np.isfinite(X), axis=-1)
+    flat_keep = keep.reshape(-1)
+    n = c.shape[1]
+    g = np.nonzero(flat_keep)[0].astype(np.int64)
+    out = np.empty((len(g), 3))
+    for m in range(M):
+        sel = (g >= m * n) & (g < (m + 1) * n)
+        s, R, t = poses[m]
+        out[sel] = s * (X[m][g[sel] - m * n] @ np.asarray(R).T) + np.asarray(t)
+    return out, g + index_base

@@ -97,6 +97,52 @@ __global__ void __launch_bounds__(1024) k_fuse_scan(const int32_t* __restrict__ 
   if (threadIdx.x == 0) *cursor = carry;
 }
 
+// One compaction round of a scatter CTA: this thread's kept points (mask km
+// over its 4 points i0..i0+3 of the tile) get consecutive slots in point order
+// (warp scan, then across warps), `point(j, dst)` writes point j's three
+// global coordinates into shared memory, and the round's kept points are
+// written with coalesced stores at [pos, pos + total) (nothing at or past
+// `capacity`); pos advances by the round's total.
+template <class Point>
+__device__ __forceinline__ void emit_round(unsigned km, int i0, int64_t gbase, int64_t& pos,
+                                           int64_t capacity, bool& overflow,
+                                           float* __restrict__ out_xyz,
+                                           int64_t* __restrict__ out_idx, int* wcnt, float* sx,
+                                           int64_t* sidx, Point&& point) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cnt = __popc(km);
+  int x = cnt;  // inclusive warp scan of counts (thread order = point order)
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wcnt[warp] = x;
+  __syncthreads();
+  int wbefore = 0, total = 0;
+  for (int w = 0; w < THREADS / 32; ++w) {
+    const int v = wcnt[w];
+    wbefore += w < warp ? v : 0;
+    total += v;
+  }
+  int q = wbefore + (x - cnt);  // slot of this thread's first kept point in the round
+  for (int j = 0; j < 4; ++j) {
+    if (!(km & (1u << j))) continue;
+    point(j, sx + 3 * q);
+    sidx[q] = gbase + i0 + j;
+    ++q;
+  }
+  __syncthreads();
+  int64_t lim = pos < 0 ? 0 : capacity - pos;  // points that still fit (none past a bad cursor)
+  if (lim < 0) lim = 0;
+  const int nw = (int)(total < lim ? total : lim);
+  if (nw < total) overflow = true;
+  float* ox = out_xyz + 3 * pos;
+  for (int i = threadIdx.x; i < 3 * nw; i += THREADS) ox[i] = sx[i];
+  for (int i = threadIdx.x; i < nw; i += THREADS) out_idx[pos + i] = sidx[i];
+  pos += total;
+  __syncthreads();
+}
+
 // One CTA per tile, rounds of 1024 points (4 per thread).  The confidences and
 // the points of a round are loaded together, the next round's loads are in
 // flight while the current one is compacted, and each round's kept points are
@@ -127,7 +173,6 @@ __global__ void __launch_bounds__(THREADS) k_fuse_scatter(
   const float a00 = A[0], a01 = A[1], a02 = A[2], a03 = A[3];
   const float a10 = A[4], a11 = A[5], a12 = A[6], a13 = A[7];
   const float a20 = A[8], a21 = A[9], a22 = A[10], a23 = A[11];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t pos = tile_off[t];
   bool overflow = false;
 
@@ -158,41 +203,161 @@ __global__ void __launch_bounds__(THREADS) k_fuse_scatter(
     if (r0 + ROUND < npx) load(r0 + ROUND);  // next round in flight
     unsigned km = 0;
     for (int j = 0; j < 4; ++j) km |= (i0 + j < npx && keep(ccf[j], thr)) ? (1u << j) : 0u;
-    const int cnt = __popc(km);
-    int x = cnt;  // inclusive warp scan of counts (thread order = point order)
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+    emit_round(km, i0, index_base + base, pos, capacity, overflow, out_xyz, out_idx, wcnt, sx,
+               sidx, [&](int j, float* dst) {
+                 const float x0 = cp[3 * j], x1 = cp[3 * j + 1], x2 = cp[3 * j + 2];
+                 dst[0] = fmaf(a00, x0, fmaf(a01, x1, fmaf(a02, x2, a03)));
+                 dst[1] = fmaf(a10, x0, fmaf(a11, x1, fmaf(a12, x2, a13)));
+                 dst[2] = fmaf(a20, x0, fmaf(a21, x1, fmaf(a22, x2, a23)));
+               });
+  }
+  if (overflow && threadIdx.x == 0) atomicOr(flags, FLAG_CAPACITY);
+}
+
+// --------------------------------------------------------------------------
+// fusion straight from depth maps and cameras
+// --------------------------------------------------------------------------
+// A point exists where the frame's camera is usable (finite, fx, fy != 0) and
+// the depth is finite and > 0; it is kept when, in addition, its confidence is
+// strictly above the threshold.  Tiles are 8192 pixels of one frame, so the
+// flat index of every point is g = frame * H * W + pixel, the same as the
+// pointmap fusion's (submap-major, then frame, row, column).
+__device__ __forceinline__ bool cam_usable(const ec3r_camera& c) {
+  bool ok = c.fx != 0.f && c.fy != 0.f;
+  const float* f = &c.fx;
+  for (int i = 0; i < 16; ++i) ok &= fabsf(f[i]) <= FLT_MAX;
+  return ok;
+}
+
+__device__ __forceinline__ bool keepz(float d, float c, float thr) {
+  return d > 0.f && d <= FLT_MAX && c > thr;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(THREADS) k_fusez_count(const float* __restrict__ depth,
+                                                         const float* __restrict__ conf,
+                                                         const ec3r_camera* __restrict__ cams,
+                                                         int64_t hw, int tpf, float thr,
+                                                         int32_t* __restrict__ tile_count) {
+  const int64_t t = blockIdx.x;
+  const int64_t fr = t / tpf;
+  const int c = (int)(t - fr * tpf);
+  const int64_t base = fr * hw + (int64_t)c * TILE;
+  const int64_t rem = hw - (int64_t)c * TILE;
+  const int npx = rem < TILE ? (int)rem : TILE;
+  const bool usable = cam_usable(cams[fr]);
+  int cnt = 0;
+  if (usable) {
+    for (int i0 = 4 * threadIdx.x; i0 < npx; i0 += 4 * THREADS) {
+      if (VEC && i0 + 4 <= npx) {
+        const float4 d = __ldcs(reinterpret_cast<const float4*>(depth + base + i0));
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(conf + base + i0));
+        cnt += keepz(d.x, v.x, thr) + keepz(d.y, v.y, thr) + keepz(d.z, v.z, thr) +
+               keepz(d.w, v.w, thr);
+      } else {
+        for (int j = i0; j < min(i0 + 4, npx); ++j)
+          cnt += keepz(depth[base + j], conf[base + j], thr);
+      }
     }
-    if (lane == 31) wcnt[warp] = x;
-    __syncthreads();
-    int wbefore = 0, total = 0;
-    for (int w = 0; w < THREADS / 32; ++w) {
-      const int v = wcnt[w];
-      wbefore += w < warp ? v : 0;
-      total += v;
+  }
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  __shared__ int red[THREADS / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < THREADS / 32; ++w) s += red[w];
+    tile_count[t] = s;
+  }
+}
+
+// As k_fuse_scatter, the point of a kept pixel (row v, column u) being
+// A (d (u - cx)/fx, d (v - cy)/fy, d) + a with (A, a) = the submap pose composed
+// with the camera pose, formed in FP64 and rounded to FP32 once per CTA.
+template <bool VEC>
+__global__ void __launch_bounds__(THREADS) k_fusez_scatter(
+    const float* __restrict__ depth, const float* __restrict__ conf,
+    const ec3r_camera* __restrict__ cams, int W, int64_t hw, int tpf, int frames,
+    const ec3r_sim3* __restrict__ poses, float thr, int64_t index_base,
+    const int64_t* __restrict__ tile_off, float* __restrict__ out_xyz,
+    int64_t* __restrict__ out_idx, int64_t capacity, unsigned* flags) {
+  const int64_t t = blockIdx.x;
+  const int64_t fr = t / tpf;
+  const int c = (int)(t - fr * tpf);
+  const int64_t tile0 = (int64_t)c * TILE;
+  const int64_t base = fr * hw + tile0;
+  const int64_t rem = hw - tile0;
+  const int npx = rem < TILE ? (int)rem : TILE;
+  __shared__ float A[16];
+  __shared__ int usable;
+  __shared__ int wcnt[THREADS / 32];
+  __shared__ float sx[3 * ROUND];
+  __shared__ int64_t sidx[ROUND];
+  const ec3r_camera& cam = cams[fr];
+  if (threadIdx.x < 12) {
+    const ec3r_sim3& P = poses[fr / frames];
+    const int r = threadIdx.x / 4, col = threadIdx.x % 4;
+    double v = 0.0;  // (s R_m [R_f | t_f]) + [0 | t_m], row r, column col
+    for (int k = 0; k < 3; ++k)
+      v += P.s * P.R[3 * r + k] * (col < 3 ? (double)cam.R[3 * k + col] : (double)cam.t[k]);
+    A[threadIdx.x] = (float)(col < 3 ? v : v + P.t[r]);
+  } else if (threadIdx.x == 12) {
+    A[12] = 1.f / cam.fx;
+    A[13] = 1.f / cam.fy;
+    A[14] = cam.cx;
+    A[15] = cam.cy;
+    usable = cam_usable(cam);
+  }
+  __syncthreads();
+  const float a00 = A[0], a01 = A[1], a02 = A[2], a03 = A[3];
+  const float a10 = A[4], a11 = A[5], a12 = A[6], a13 = A[7];
+  const float a20 = A[8], a21 = A[9], a22 = A[10], a23 = A[11];
+  const float ifx = A[12], ify = A[13], cx = A[14], cy = A[15];
+  const bool ok = usable != 0;
+  int64_t pos = tile_off[t];
+  bool overflow = false;
+
+  float cf[4], dd[4];
+  auto load = [&](int r0) {
+    const int i0 = r0 + 4 * threadIdx.x;
+    if (VEC && i0 + 4 <= npx) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(conf + base + i0));
+      const float4 d = __ldcs(reinterpret_cast<const float4*>(depth + base + i0));
+      cf[0] = v.x; cf[1] = v.y; cf[2] = v.z; cf[3] = v.w;
+      dd[0] = d.x; dd[1] = d.y; dd[2] = d.z; dd[3] = d.w;
+    } else {
+      for (int j = 0; j < 4; ++j) {
+        const bool in = i0 + j < npx;
+        cf[j] = in ? conf[base + i0 + j] : -FLT_MAX;
+        dd[j] = in ? depth[base + i0 + j] : 0.f;
+      }
     }
-    int q = wbefore + (x - cnt);  // slot of this thread's first kept point in the round
+  };
+  if (npx > 0) load(0);
+  for (int r0 = 0; r0 < npx; r0 += ROUND) {
+    const int i0 = r0 + 4 * threadIdx.x;
+    float ccf[4], cd[4];
     for (int j = 0; j < 4; ++j) {
-      if (!(km & (1u << j))) continue;
-      const float x0 = cp[3 * j], x1 = cp[3 * j + 1], x2 = cp[3 * j + 2];
-      sx[3 * q + 0] = fmaf(a00, x0, fmaf(a01, x1, fmaf(a02, x2, a03)));
-      sx[3 * q + 1] = fmaf(a10, x0, fmaf(a11, x1, fmaf(a12, x2, a13)));
-      sx[3 * q + 2] = fmaf(a20, x0, fmaf(a21, x1, fmaf(a22, x2, a23)));
-      sidx[q] = index_base + base + i0 + j;
-      ++q;
+      ccf[j] = cf[j];
+      cd[j] = dd[j];
     }
-    __syncthreads();
-    // coalesced write-out of the round's kept points at [pos, pos + total)
-    int64_t lim = pos < 0 ? 0 : capacity - pos;  // points that still fit (none past a bad cursor)
-    if (lim < 0) lim = 0;
-    const int nw = (int)(total < lim ? total : lim);
-    if (nw < total) overflow = true;
-    float* ox = out_xyz + 3 * pos;
-    for (int i = threadIdx.x; i < 3 * nw; i += THREADS) ox[i] = sx[i];
-    for (int i = threadIdx.x; i < nw; i += THREADS) out_idx[pos + i] = sidx[i];
-    pos += total;
-    __syncthreads();
+    if (r0 + ROUND < npx) load(r0 + ROUND);  // next round in flight
+    unsigned km = 0;
+    for (int j = 0; j < 4; ++j)
+      km |= (ok && i0 + j < npx && keepz(cd[j], ccf[j], thr)) ? (1u << j) : 0u;
+    const unsigned pix0 = (unsigned)(tile0 + i0);  // < 2^31
+    const unsigned v0 = pix0 / (unsigned)W;
+    const unsigned u0 = pix0 - v0 * (unsigned)W;
+    emit_round(km, i0, index_base + base, pos, capacity, overflow, out_xyz, out_idx, wcnt, sx,
+               sidx, [&](int j, float* dst) {
+                 unsigned u = u0 + j, v = v0;
+                 while (u >= (unsigned)W) { u -= (unsigned)W; ++v; }  // at most 3 steps
+                 const float d = cd[j];
+                 const float x0 = d * (((float)u - cx) * ifx), x1 = d * (((float)v - cy) * ify);
+                 dst[0] = fmaf(a00, x0, fmaf(a01, x1, fmaf(a02, d, a03)));
+                 dst[1] = fmaf(a10, x0, fmaf(a11, x1, fmaf(a12, d, a13)));
+                 dst[2] = fmaf(a20, x0, fmaf(a21, x1, fmaf(a22, d, a23)));
+               });
   }
   if (overflow && threadIdx.x == 0) atomicOr(flags, FLAG_CAPACITY);
 }
@@ -252,6 +417,62 @@ extern "C" ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pt
                                                      d_poses, conf_threshold, index_base, off,
                                                      d_out_xyz, d_out_idx, capacity,
                                                      ctx->d_flags);
+  });
+  EC3R_CUDA_TRY(ctx, cudaGetLastError());
+  return EC3R_OK;
+}
+
+extern "C" ec3r_status ec3r_fuse_points_depth(ec3r_ctx* ctx, int n_submaps, int frames, int H,
+                                              int W, const float* d_depth, const float* d_conf,
+                                              const ec3r_camera* d_cams,
+                                              const ec3r_sim3* d_poses, float conf_threshold,
+                                              int64_t index_base, float* d_out_xyz,
+                                              int64_t* d_out_idx, int64_t capacity,
+                                              int64_t* d_cursor, void* stream) {
+  if (!ctx) return EC3R_ERR_INVALID_ARG;
+  if (n_submaps < 0 || frames < 0 || H < 0 || W < 0 || capacity < 0 || index_base < 0)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "negative size");
+  if (n_submaps == 0 || frames == 0 || H == 0 || W == 0) return EC3R_OK;
+  if (!d_depth || !d_conf || !d_cams || !d_poses || !d_cursor ||
+      (capacity > 0 && (!d_out_xyz || !d_out_idx)))
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
+  if (conf_threshold != conf_threshold)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "conf_threshold is NaN");
+  const int64_t hw = (int64_t)H * W;
+  const int64_t tpf = (hw + TILE - 1) / TILE;
+  const int64_t n_frames = (int64_t)n_submaps * frames;
+  const int64_t n_tiles = tpf * n_frames;
+  if (hw >= ((int64_t)1 << 31) || n_tiles >= ((int64_t)1 << 31))
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "problem too large for one call");
+  EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  void *p_cnt, *p_off;
+  ec3r_status st;
+  if ((st = ensure_buf(ctx, "fuse.count", sizeof(int32_t) * (size_t)n_tiles, s, &p_cnt))) return st;
+  if ((st = ensure_buf(ctx, "fuse.off", sizeof(int64_t) * (size_t)n_tiles, s, &p_off))) return st;
+  int32_t* cnt = (int32_t*)p_cnt;
+  int64_t* off = (int64_t*)p_off;
+  const bool vec = (hw % 4 == 0) && ((uintptr_t)d_depth % 16 == 0) &&
+                   ((uintptr_t)d_conf % 16 == 0);
+  const dim3 grid((unsigned)n_tiles);
+  traced(ctx, s, "fusez_count", [&] {
+    if (vec)
+      k_fusez_count<true><<<grid, THREADS, 0, s>>>(d_depth, d_conf, d_cams, hw, (int)tpf,
+                                                   conf_threshold, cnt);
+    else
+      k_fusez_count<false><<<grid, THREADS, 0, s>>>(d_depth, d_conf, d_cams, hw, (int)tpf,
+                                                    conf_threshold, cnt);
+  });
+  traced(ctx, s, "fuse_scan", [&] { k_fuse_scan<<<1, 1024, 0, s>>>(cnt, n_tiles, off, d_cursor); });
+  traced(ctx, s, "fusez_scatter", [&] {
+    if (vec)
+      k_fusez_scatter<true><<<grid, THREADS, 0, s>>>(
+          d_depth, d_conf, d_cams, W, hw, (int)tpf, frames, d_poses, conf_threshold, index_base,
+          off, d_out_xyz, d_out_idx, capacity, ctx->d_flags);
+    else
+      k_fusez_scatter<false><<<grid, THREADS, 0, s>>>(
+          d_depth, d_conf, d_cams, W, hw, (int)tpf, frames, d_poses, conf_threshold, index_base,
+          off, d_out_xyz, d_out_idx, capacity, ctx->d_flags);
   });
   EC3R_CUDA_TRY(ctx, cudaGetLastError());
   return EC3R_OK;

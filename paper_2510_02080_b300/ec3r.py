@@ -28,7 +28,8 @@ EXPORTS = ("ec3r_create", "ec3r_destroy", "ec3r_last_error", "ec3r_status_string
            "ec3r_version", "ec3r_sync_status", "ec3r_align_opts_default",
            "ec3r_align_submaps", "ec3r_fuse_points", "ec3r_profile", "ec3r_profile_read",
            "ec3r_align_submaps_noalloc", "ec3r_pg_opts_default", "ec3r_pose_graph_correct",
-           "ec3r_align_submaps_backward", "ec3r_align_submaps_depth", "ec3r_correct_points")
+           "ec3r_align_submaps_backward", "ec3r_align_submaps_depth", "ec3r_correct_points",
+           "ec3r_fuse_points_depth")
 
 
 class Sim3(C.Structure):
@@ -80,6 +81,8 @@ def _declare(l):
     l.ec3r_align_submaps_depth.argtypes = [_P, _P, _P, _P, _I64, C.c_int, C.c_int, C.c_int,
                                            _I64, _P, _P, _P, _P, C.POINTER(AlignOpts), _P, _P,
                                            _P, _P]
+    l.ec3r_fuse_points_depth.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P,
+                                         _P, C.c_float, _I64, _P, _P, _I64, _P, _P]
     l.ec3r_correct_points.argtypes = [_P, _I64, _P, _P, C.c_int, _I64, _P, _P, _P, C.c_float,
                                       _P, _P]
     l.ec3r_pg_opts_default.argtypes = [C.POINTER(PgOpts)]
@@ -88,7 +91,8 @@ def _declare(l):
                                           C.POINTER(PgOpts), _P, _P]
     for name in ("ec3r_create", "ec3r_sync_status", "ec3r_align_submaps", "ec3r_fuse_points",
                  "ec3r_profile", "ec3r_profile_read", "ec3r_pose_graph_correct",
-                 "ec3r_align_submaps_backward", "ec3r_align_submaps_depth", "ec3r_correct_points"):
+                 "ec3r_align_submaps_backward", "ec3r_align_submaps_depth", "ec3r_correct_points",
+           "ec3r_fuse_points_depth"):
         getattr(l, name).restype = C.c_int
 
 
@@ -285,6 +289,23 @@ class Context:
             _ptr(out_xyz), _ptr(out_idx), int(out_idx.numel()), _ptr(cursor), _stream(stream))
         self._check(st)
 
+
+    def fuse_points_depth(self, depth, conf, cams, poses, out_xyz, out_idx, cursor, *,
+                          frames, threshold=1.0, index_base=0, stream=None):
+        """Appends kept points of depth / conf [M*frames, H, W] with cameras
+        [M*frames, 16] at ``cursor`` (int64 [1])."""
+        if depth.dim() != 3 or tuple(conf.shape) != tuple(depth.shape):
+            raise ValueError("depth and conf must be [n_frames, H, W]")
+        nfr, H, W = (int(v) for v in depth.shape)
+        if nfr % frames:
+            raise ValueError("the frame count must be a multiple of frames")
+        if tuple(cams.shape) != (nfr, 16) or cams.dtype != torch.float32:
+            raise ValueError("cams must be float32 [n_frames, 16]")
+        st = self._lib.ec3r_fuse_points_depth(
+            self._h, nfr // frames, int(frames), H, W, _ptr(depth), _ptr(conf), _ptr(cams),
+            _ptr(poses), float(threshold), int(index_base), _ptr(out_xyz), _ptr(out_idx),
+            int(out_idx.numel()), _ptr(cursor), _stream(stream))
+        self._check(st)
 
     # -- point correction --------------------------------------------------
     def correct_points(self, points, refs, xyz, conf, poses, *, threshold=1.0, n_corrected=None,

@@ -162,3 +162,57 @@ def test_full_size_depth_chain_sampled_pairs(ctx):
     cpu = synth.DepthPairSet(dps.depth.cpu(), dps.conf.cpu(), dps.cams.cpu(), dps.link_off.cpu(),
                              dps.src.cpu(), dps.tgt.cpu(), dps.H, dps.W)
     check(oracle_pairset(cpu, frames), S, st, cost, pairs=pairs)
+
+
+def _rand_pose_rows(rng, M):
+    from scipy.spatial.transform import Rotation
+    s = rng.uniform(0.5, 2.0, M)
+    R = Rotation.random(M, random_state=rng).as_matrix()
+    t = rng.normal(size=(M, 3)) * 3
+    rows = np.concatenate([s[:, None], R.reshape(M, 9), t], 1)
+    return rows, [(s[m], R[m], t[m]) for m in range(M)]
+
+
+def test_depth_fusion_matches_oracle(ctx):
+    """ec3r_fuse_points_depth against the oracle's unprojection + fusion: flat
+    indices bit-exact, points within 1e-6 x extent; invalid depths and an
+    unusable camera drop their pixels; two calls stream into one buffer and a
+    short buffer reports the overflow."""
+    from oracle import fuse as ofuse
+    ch = synth.make_depth_chain(synth.SEED_BASE + 48, M=4, F=3, H=100, W=180, overlap=1)
+    dps = ch.pairs()
+    d = dps.depth.clone()
+    rng = np.random.default_rng(5)
+    flat = d.view(-1)
+    for val in (0.0, -1.0, float("nan"), float("inf")):
+        flat[torch.from_numpy(rng.choice(flat.numel(), 500, replace=False))] = val
+    cams = dps.cams.clone()
+    cams[4, 9] = float("nan")                        # frame 4 (submap 1): no points
+    rows, poses = _rand_pose_rows(rng, ch.M)
+    ref_x, ref_i = ofuse.fuse_points_depth(d.numpy(), dps.conf.numpy(), cams.numpy(), poses,
+                                           frames=3, threshold=1.0, index_base=7)
+    K = len(ref_i)
+    out_x = torch.full((K + 5, 3), -3.0, device="cuda")
+    out_i = torch.full((K + 5,), -3, dtype=torch.int64, device="cuda")
+    cur = torch.zeros((1,), dtype=torch.int64, device="cuda")
+    d_d, c_d, k_d = d.cuda(), dps.conf.cuda(), cams.cuda()
+    P = torch.tensor(rows, dtype=torch.float64, device="cuda")
+    ctx.fuse_points_depth(d_d[:6], c_d[:6], k_d[:6], P[:2], out_x, out_i, cur, frames=3,
+                          index_base=7)
+    ctx.fuse_points_depth(d_d[6:], c_d[6:], k_d[6:], P[2:], out_x, out_i, cur, frames=3,
+                          index_base=7 + 6 * dps.H * dps.W)
+    assert ctx.sync_status() == 0 and int(cur) == K
+    gi = out_i[:K].cpu().numpy()
+    gx = out_x[:K].cpu().numpy()
+    np.testing.assert_array_equal(gi, ref_i)
+    ext = float(np.linalg.norm(np.ptp(ref_x, axis=0)))
+    assert np.abs(gx - ref_x).max() <= 1e-6 * ext
+    assert not np.any((gi >= 7 + 4 * dps.H * dps.W) & (gi < 7 + 5 * dps.H * dps.W))
+    # a buffer one point short: everything but the last point, then CAPACITY
+    cur.zero_()
+    short_x = torch.zeros((K - 1, 3), device="cuda")
+    short_i = torch.zeros((K - 1,), dtype=torch.int64, device="cuda")
+    ctx.fuse_points_depth(d_d, c_d, k_d, P, short_x, short_i, cur, frames=3, index_base=7)
+    assert ctx.sync_status() == 4                     # EC3R_ERR_CAPACITY
+    assert int(cur) == K
+    np.testing.assert_array_equal(short_i.cpu().numpy(), ref_i[:K - 1])

@@ -64,3 +64,29 @@ def test_point_correction_closed_forms():
             np.testing.assert_allclose(out[i], 2.5 * xyz[2, k].astype(np.float64), rtol=1e-15)
     assert cnt == sum(1 for g in refs if g >= 0 and conf.reshape(-1)[g] > 1.0 and
                       np.all(np.isfinite(xyz.reshape(-1, 3)[g])))
+
+
+def test_depth_fusion_closed_forms():
+    """Fusion of depth frames: with identity camera and pose, a constant-depth
+    plane fuses to the pinhole grid; a pixel without a point (depth <= 0, NaN,
+    or a frame whose camera has a zero focal length) is dropped even when its
+    confidence passes; a pose maps the kept points."""
+    H, W, Z = 4, 6, 2.0
+    cam = np.concatenate([[100.0, 80.0, 2.0, 1.0], np.eye(3).ravel(), np.zeros(3)])
+    cams = np.stack([cam, cam.copy()])
+    cams[1, 0] = 0.0                                     # frame 1: fx = 0, no points
+    depth = np.full((2, H, W), Z)
+    depth[0, 0, 0] = 0.0
+    depth[0, 1, 2] = np.nan
+    conf = np.full((2, H, W), 2.0)
+    conf[0, 3, 5] = 0.5                                  # below the threshold
+    s, t = 1.5, np.array([0.0, 1.0, -2.0])
+    out, idx = fuse.fuse_points_depth(depth, conf, cams, [(s, np.eye(3), t)], frames=2,
+                                      threshold=1.0, index_base=10)
+    expect = [r * W + c for r in range(H) for c in range(W)
+              if (r, c) not in ((0, 0), (1, 2), (3, 5))]
+    np.testing.assert_array_equal(idx, np.asarray(expect) + 10)
+    for k, g in enumerate(expect):
+        r, c = divmod(g, W)
+        x = np.array([(c - 2.0) / 100.0 * Z, (r - 1.0) / 80.0 * Z, Z])
+        np.testing.assert_allclose(out[k], s * x + t, rtol=0, atol=1e-14)
