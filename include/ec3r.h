@@ -281,9 +281,11 @@ typedef struct {
   int fixed_node;     /* node held constant (gauge), 0 <= fixed_node < n_nodes */
   double lm_lambda;   /* >= 0; the normal matrix is H + lm_lambda I (0: Gauss-Newton) */
   int init_by_chaining; /* 1: first set every node by chaining relative transforms */
+  int lm_adaptive;    /* 1: Levenberg-Marquardt with adaptive damping from lm_lambda > 0 */
 } ec3r_pg_opts;
 
-/* Fills `o` with the defaults: 10 iterations, node 0 fixed, lambda 0, chaining on. */
+/* Fills `o` with the defaults: 10 iterations, node 0 fixed, lambda 0, chaining on,
+ * fixed damping. */
 void ec3r_pg_opts_default(ec3r_pg_opts* o);
 
 /*
@@ -316,6 +318,12 @@ void ec3r_pg_opts_default(ec3r_pg_opts* o);
  * d_chi2 (float64 [iters+1], device, nullable) receives chi^2 before each
  * step and after the last.  A non-positive pivot skips that step's update and
  * raises EC3R_ERR_NOT_SPD at ec3r_sync_status.
+ *
+ * With lm_adaptive = 1 the iterations are Levenberg-Marquardt (the paper's
+ * choice): lambda starts at lm_lambda (0 < lm_lambda <= 1e10); a step is kept
+ * when its factorisation succeeds and chi^2 decreases, and lambda is divided by
+ * 10 (not below 1e-10); otherwise the poses are restored and lambda is
+ * multiplied by 10 (not above 1e10).  A rejected step is not an error.
  */
 ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nodes, int n_edges,
                                     const int32_t* h_i, const int32_t* h_j,

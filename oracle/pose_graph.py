@@ -116,6 +116,66 @@ def numeric_jacobians(Ti, Tj, Tij, h=1e-3):
     return Ji, Jj
 
 
+def normal_equations(nodes, ei, ej, Tij, info, fixed, h=1e-3):
+    """H = sum J^T Omega J and g = sum J^T Omega e over the free nodes."""
+    n = len(nodes)
+    free = [v for v in range(n) if v != fixed]
+    col = {v: 7 * q for q, v in enumerate(free)}
+    H = np.zeros((7 * len(free), 7 * len(free)))
+    g = np.zeros(7 * len(free))
+    for k in range(len(ei)):
+        i, j = int(ei[k]), int(ej[k])
+        e = edge_error(nodes[i], nodes[j], Tij[k])
+        Ji, Jj = numeric_jacobians(nodes[i], nodes[j], Tij[k], h)
+        Om = np.eye(7) if info is None else np.asarray(info[k]).reshape(7, 7)
+        for a, Ja in ((i, Ji), (j, Jj)):
+            if a == fixed:
+                continue
+            g[col[a]:col[a] + 7] += Ja.T @ Om @ e
+            for b, Jb in ((i, Ji), (j, Jj)):
+                if b == fixed:
+                    continue
+                H[col[a]:col[a] + 7, col[b]:col[b] + 7] += Ja.T @ Om @ Jb
+    return H, g, free, col
+
+
+LM_MIN, LM_MAX = 1e-10, 1e10
+
+
+def levenberg_marquardt(nodes, ei, ej, Tij, info=None, iters=10, fixed=0, lambda0=1e-3,
+                        h=1e-3):
+    """Levenberg-Marquardt (Sec. III-E: the paper optimises with LM): each step
+    solves (H + lambda I) delta = -g; it is kept when the Cholesky
+    factorisation exists and chi^2 decreases (lambda / 10, not below 1e-10),
+    else discarded (lambda x 10, not above 1e10).
+
+    Returns (nodes, chi2 history of length iters+1: before each step and after
+    the last, lambdas used)."""
+    nodes = list(nodes)
+    lam = float(lambda0)
+    hist = [chi2(nodes, ei, ej, Tij, info)]
+    lams = []
+    for _ in range(iters):
+        lams.append(lam)
+        H, g, free, col = normal_equations(nodes, ei, ej, Tij, info, fixed, h)
+        trial = None
+        try:
+            L = np.linalg.cholesky(H + lam * np.eye(H.shape[0]))
+            delta = np.linalg.solve(L.T, np.linalg.solve(L, -g))
+            trial = list(nodes)
+            for v in free:
+                trial[v] = sim3.compose(nodes[v], sim3.exp(delta[col[v]:col[v] + 7]))
+        except np.linalg.LinAlgError:
+            pass
+        if trial is not None and chi2(trial, ei, ej, Tij, info) < hist[-1]:
+            nodes = trial
+            lam = max(lam * 0.1, LM_MIN)
+        else:
+            lam = min(lam * 10.0, LM_MAX)
+        hist.append(chi2(nodes, ei, ej, Tij, info))
+    return nodes, hist, lams
+
+
 def gauss_newton(nodes, ei, ej, Tij, info=None, iters=10, fixed=0, lm_lambda=0.0, h=1e-3):
     """Returns (nodes, chi2 history of length iters+1, last step norms)."""
     n = len(nodes)

@@ -161,6 +161,8 @@ struct PgDev {
   const int *ei, *ej, *perm, *col_ptr, *off_row, *off_blk, *grp_ptr, *grp, *upd_ab, *sn_grp,
       *row_ptr, *row, *level_ptr, *level_cols, *asm_ptr, *asm_it, *g_ptr, *g_it;
   double *L, *b, *contrib, *gvec, *chi2e, *idiag, *chi2;
+  double* lm;           // adaptive LM: lambda, chi^2 at the step's start, after it (else null)
+  ec3r_sim3* backup;    // adaptive LM: poses before the tentative step
   int* fail;
   unsigned* flags;
   const ec3r_sim3* Tij;
@@ -275,12 +277,13 @@ __device__ void linearize_edge(int e, int lane, WarpScratch& w, const PgDev& p, 
 // side block (then nf of them), or chi^2 (the last unit)
 // --------------------------------------------------------------------------
 __device__ void assemble_unit(int b, int lane, int n_blocks, int nf, const PgDev& p,
-                              double* chi2_out) {
+                              double* chi2_out, int trial) {
   if (b < n_blocks) {
     const int p0 = p.asm_ptr[b], p1 = p.asm_ptr[b + 1];
+    const double lambda = p.lm ? ldc(p.lm) : p.lambda;
     for (int idx = lane; idx < NB; idx += 32) {
       const int r = idx / 7, c = idx % 7;
-      double s = (b < nf && r == c) ? p.lambda : 0.0;
+      double s = (b < nf && r == c) ? lambda : 0.0;
       for (int q = p0; q < p1; ++q) {
         const int it = p.asm_it[q];
         const int edge = it >> 2, kind = it & 3;
@@ -304,8 +307,13 @@ __device__ void assemble_unit(int b, int lane, int n_blocks, int nf, const PgDev
     for (int e = lane; e < p.m; e += 32) s += ldc(p.chi2e + e);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
-      if (chi2_out) *chi2_out = s;
-      *p.fail = 0;
+      if (trial) {  // chi^2 after a tentative LM step; the step's fail flag stays
+        p.lm[2] = s;
+      } else {
+        if (chi2_out) *chi2_out = s;
+        if (p.lm) p.lm[1] = s;
+        *p.fail = 0;
+      }
     }
   }
 }
@@ -481,8 +489,28 @@ __global__ void __launch_bounds__(32) k_pg_linearize(PgDev p, int jacobians) {
 }
 
 __global__ void __launch_bounds__(32) k_pg_assemble(PgDev p, int n_blocks, int nf,
-                                                    double* chi2_out) {
-  assemble_unit(blockIdx.x, threadIdx.x, n_blocks, nf, p, chi2_out);
+                                                    double* chi2_out, int trial) {
+  assemble_unit(blockIdx.x, threadIdx.x, n_blocks, nf, p, chi2_out, trial);
+}
+
+// Adaptive Levenberg-Marquardt (Sec. III-E names LM): the damping starts at
+// lambda0; a step is kept when the factorisation succeeded and chi^2 went
+// down (lambda / 10), else the poses before it are restored (lambda x 10);
+// lambda stays in [LM_MIN, LM_MAX].
+constexpr double LM_MIN = 1e-10, LM_MAX = 1e10;
+
+__global__ void k_pg_lm_start(PgDev p, double lambda0) { p.lm[0] = lambda0; }
+
+__global__ void k_pg_backup(PgDev p) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < p.n) p.backup[k] = p.nodes[k];
+}
+
+__global__ void k_pg_decide(PgDev p) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool accept = !ldc(p.fail) && ldc(p.lm + 2) < ldc(p.lm + 1);
+  if (!accept && k < p.n) p.nodes[k] = p.backup[k];
+  if (k == 0) p.lm[0] = accept ? fmax(ldc(p.lm) * 0.1, LM_MIN) : fmin(ldc(p.lm) * 10.0, LM_MAX);
 }
 
 constexpr int FWARPS = 4;  // warps per column in k_pg_factor
@@ -694,7 +722,9 @@ struct Plan : Extension {
   int *d_anc0 = nullptr, *d_anc1 = nullptr, *d_fail = nullptr;
   double *d_L = nullptr, *d_b = nullptr, *d_contrib = nullptr, *d_gvec = nullptr,
          *d_chi2e = nullptr, *d_idiag = nullptr;
-  ec3r_sim3 *d_W0 = nullptr, *d_W1 = nullptr;
+  ec3r_sim3 *d_W0 = nullptr, *d_W1 = nullptr, *d_backup = nullptr;
+  double* d_lm = nullptr;      // adaptive LM state
+  unsigned* d_lm_flags = nullptr;  // absorbs non-SPD reports of rejected LM steps
   ~Plan() override {
     for (void* p : allocs) cudaFree(p);
   }
@@ -1068,6 +1098,9 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   chk(alloc(P, &P.d_chi2e, m));
   chk(alloc(P, &P.d_W0, n));
   chk(alloc(P, &P.d_W1, n));
+  chk(alloc(P, &P.d_backup, n));
+  chk(alloc(P, &P.d_lm, 4));
+  chk(alloc(P, &P.d_lm_flags, 1));
   if (err != cudaSuccess) {
     cudaGetLastError();
     return set_error(ctx, EC3R_ERR_OOM, "pose-graph plan allocation failed: %s",
@@ -1115,6 +1148,7 @@ void ec3r_pg_opts_default(ec3r_pg_opts* o) {
   o->fixed_node = 0;
   o->lm_lambda = 0.0;
   o->init_by_chaining = 1;
+  o->lm_adaptive = 0;
 }
 
 ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nodes, int n_edges,
@@ -1126,6 +1160,8 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "bad pose-graph arguments");
   if (opts->iters < 0 || opts->iters > 1000 || opts->fixed_node < 0 ||
       opts->fixed_node >= n_nodes || !(opts->lm_lambda >= 0.0) || n_nodes > (1 << 24) ||
+      (opts->lm_adaptive != 0 && opts->lm_adaptive != 1) ||
+      (opts->lm_adaptive && !(opts->lm_lambda > 0.0 && opts->lm_lambda <= 1e10)) ||
       n_edges > (1 << 28))
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "bad ec3r_pg_opts");
   for (int e = 0; e < n_edges; ++e)
@@ -1216,14 +1252,17 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
   dv.idiag = P->d_idiag;
   dv.chi2 = d_chi2;
   dv.fail = P->d_fail;
-  dv.flags = ctx->d_flags;
+  const bool lm = o.lm_adaptive != 0;
+  dv.flags = lm ? P->d_lm_flags : ctx->d_flags;  // a rejected LM step is not an error
+  dv.lm = lm ? P->d_lm : nullptr;
+  dv.backup = P->d_backup;
   dv.Tij = d_Tij;
   dv.info = d_info;
   dv.nodes = d_nodes;
   const std::string gkey =
       key_of("pg", {(uint64_t)P, (uint64_t)d_nodes, (uint64_t)d_Tij, (uint64_t)d_info,
                     (uint64_t)d_chi2, (uint64_t)o.iters, dbits(o.lm_lambda),
-                    (uint64_t)o.init_by_chaining});
+                    (uint64_t)o.init_by_chaining, (uint64_t)o.lm_adaptive});
   return run_graph(ctx, gkey, s, [&](cudaStream_t cs) -> ec3r_status {
     if (o.init_by_chaining)
       traced(ctx, cs, "pg_init", [&] {
@@ -1232,6 +1271,8 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
                                       P->rounds);
       });
     const int nlev = P->nlev;
+    if (lm)
+      traced(ctx, cs, "pg_lm", [&] { k_pg_lm_start<<<1, 1, 0, cs>>>(dv, o.lm_lambda); });
     for (int itn = 0; itn <= o.iters; ++itn) {
       const bool last = itn == o.iters;  // last pass only evaluates chi^2
       if (n_edges > 0)
@@ -1241,13 +1282,13 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
       if (last) {
         if (d_chi2)
           traced(ctx, cs, "pg_assemble", [&] {
-            k_pg_assemble<<<1, 32, 0, cs>>>(dv, 0, 0, d_chi2 + itn);
+            k_pg_assemble<<<1, 32, 0, cs>>>(dv, 0, 0, d_chi2 + itn, 0);
           });
         break;
       }
       traced(ctx, cs, "pg_assemble", [&] {
-        k_pg_assemble<<<P->n_blocks + P->nf + 1, 32, 0, cs>>>(dv, P->n_blocks, P->nf,
-                                                              d_chi2 ? d_chi2 + itn : nullptr);
+        k_pg_assemble<<<P->n_blocks + P->nf + 1, 32, 0, cs>>>(
+            dv, P->n_blocks, P->nf, d_chi2 ? d_chi2 + itn : nullptr, 0);
       });
       if (P->nf == 0) continue;
       for (int l = 0; l < nlev; ++l)
@@ -1263,7 +1304,7 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
         for (int k = P->sn0; k < nf; ++k) {
           traced(ctx, cs, "pg_sn_panel", [&] {
             k_pg_sn_panel<<<1, 256, 0, cs>>>(k, nf, P->d_col_ptr, P->d_off_blk, P->d_L,
-                                             P->d_idiag, ctx->d_flags, P->d_fail);
+                                             P->d_idiag, dv.flags, P->d_fail);
           });
           const int64_t mrem = nf - 1 - k;
           if (mrem > 0)
@@ -1283,9 +1324,25 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
         traced(ctx, cs, "pg_backsolve", [&] {
           k_pg_backsolve<<<P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs>>>(dv, l);
         });
+      if (lm)
+        traced(ctx, cs, "pg_lm", [&] {
+          k_pg_backup<<<(n_nodes + 127) / 128, 128, 0, cs>>>(dv);
+        });
       traced(ctx, cs, "pg_update", [&] {
         k_pg_update<<<(P->nf + 63) / 64, 64, 0, cs>>>(dv);
       });
+      if (lm) {  // chi^2 of the tentative step, then keep it or restore
+        if (n_edges > 0)
+          traced(ctx, cs, "pg_linearize", [&] {
+            k_pg_linearize<<<n_edges, 32, 0, cs>>>(dv, 0);
+          });
+        traced(ctx, cs, "pg_assemble", [&] {
+          k_pg_assemble<<<1, 32, 0, cs>>>(dv, 0, 0, nullptr, 1);
+        });
+        traced(ctx, cs, "pg_lm", [&] {
+          k_pg_decide<<<(n_nodes + 127) / 128, 128, 0, cs>>>(dv);
+        });
+      }
     }
     EC3R_CUDA_TRY(ctx, cudaGetLastError());
     return EC3R_OK;

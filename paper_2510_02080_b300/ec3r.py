@@ -43,7 +43,7 @@ class AlignOpts(C.Structure):
 
 class PgOpts(C.Structure):
     _fields_ = [("iters", C.c_int), ("fixed_node", C.c_int), ("lm_lambda", C.c_double),
-                ("init_by_chaining", C.c_int)]
+                ("init_by_chaining", C.c_int), ("lm_adaptive", C.c_int)]
 
 
 class Ec3rError(RuntimeError):
@@ -256,7 +256,8 @@ class Context:
 
     # -- pose graph --------------------------------------------------------
     def pose_graph_correct(self, nodes, ei, ej, Tij, info=None, *, iters=10, fixed=0,
-                           lm_lambda=0.0, init=True, chi2=None, stream=None):
+                           lm_lambda=0.0, init=True, chi2=None, lm_adaptive=False,
+                           stream=None):
         """Refines ``nodes`` ([n,13] float64, device) in place; returns chi^2 history.
 
         ``ei``/``ej`` are the edge endpoints on the host (the graph structure is
@@ -270,7 +271,8 @@ class Context:
         n, m = int(nodes.shape[0]), int(hi.shape[0])
         if chi2 is None:
             chi2 = torch.empty((iters + 1,), dtype=torch.float64, device=nodes.device)
-        o = PgOpts(int(iters), int(fixed), float(lm_lambda), 1 if init else 0)
+        o = PgOpts(int(iters), int(fixed), float(lm_lambda), 1 if init else 0,
+                   1 if lm_adaptive else 0)
         st = self._lib.ec3r_pose_graph_correct(
             self._h, n, _ptr(nodes), m, hi.ctypes.data_as(C.c_void_p),
             hj.ctypes.data_as(C.c_void_p), _ptr(Tij) if m else None, _ptr(info), C.byref(o),

@@ -135,3 +135,38 @@ def test_large_loop_graph_one_iteration_matches_oracle(ctx):
     assert ctx.sync_status() == 0
     np.testing.assert_allclose(chi2.cpu().numpy(), np.array(hist), rtol=TOL)
     assert_poses_close(tuples(nodes), ref)
+
+
+@pytest.mark.parametrize("n,loops,seed", [(30, 8, 1), (200, 40, 3)])
+def test_levenberg_marquardt_matches_oracle(ctx, n, loops, seed):
+    """Adaptive LM (the paper's optimiser) from the chained start: the chi^2
+    history (kept and discarded steps alike) and the final poses."""
+    g = synth.make_pose_graph(synth.SEED_BASE + seed, n, loops)
+    ei, ej, Tij = graph_from_synth(g)
+    nodes = rows([sim3.identity()] * n)
+    chi2 = ctx.pose_graph_correct(nodes, ei, ej, rows(Tij), iters=10, lm_lambda=1e-3,
+                                  lm_adaptive=True)
+    assert ctx.sync_status() == 0
+    init = opg.chain_init(n, ei, ej, Tij)
+    ref, hist, lams = opg.levenberg_marquardt(init, ei, ej, Tij, iters=10, lambda0=1e-3)
+    np.testing.assert_allclose(chi2.cpu().numpy(), np.array(hist), rtol=TOL)
+    assert_poses_close(tuples(nodes), ref)
+
+
+def test_levenberg_marquardt_discards_an_overshooting_step(ctx):
+    """Strongly inconsistent loops from the identity: the first undamped step
+    raises chi^2, is discarded (poses restored, no error) and later damped
+    steps are kept, as in the oracle."""
+    from test_oracle_pose_graph import random_graph
+    rng = np.random.default_rng(32)
+    T, ei, ej, Tij = random_graph(rng, 6, 4, noise=0.6)
+    nodes = rows([sim3.identity()] * 6)
+    chi2 = ctx.pose_graph_correct(nodes, np.array(ei), np.array(ej), rows(Tij), iters=12,
+                                  init=False, lm_lambda=1e-6, lm_adaptive=True)
+    assert ctx.sync_status() == 0
+    ref, hist, _ = opg.levenberg_marquardt([sim3.identity()] * 6, ei, ej, Tij, iters=12,
+                                           lambda0=1e-6)
+    got = chi2.cpu().numpy()
+    assert got[1] == got[0] and got[-1] < got[0]
+    np.testing.assert_allclose(got, np.array(hist), rtol=TOL)
+    assert_poses_close(tuples(nodes), ref)

@@ -147,3 +147,47 @@ def test_information_matrix_scales_energy():
     e = [pg.edge_error(T[i], T[j], M) for i, j, M in zip(ei, ej, Tij)]
     ref = sum(float(x @ np.asarray(I).reshape(7, 7) @ x) for x, I in zip(e, info))
     assert abs(pg.chi2(T, ei, ej, Tij, info) - ref) < 1e-14 * max(ref, 1)
+
+
+def test_lm_is_monotone_and_reaches_the_truth():
+    """Levenberg-Marquardt (Sec. III-E): chi^2 never increases along the kept
+    steps and a consistent graph is recovered from a far start."""
+    rng = np.random.default_rng(11)
+    T, ei, ej, Tij = random_graph(rng, 7, 3)
+    start = [T[0]] + [sim3.compose(t, sim3.exp(0.4 * rng.normal(size=7))) for t in T[1:]]
+    nodes, hist, lams = pg.levenberg_marquardt(start, ei, ej, Tij, iters=40, lambda0=1e-2)
+    assert all(b <= a for a, b in zip(hist, hist[1:]))
+    assert hist[-1] < 1e-18
+    for a, b in zip(nodes, T):
+        assert close(a, b, 1e-8)
+
+
+def test_lm_rejects_a_step_that_raises_the_energy():
+    """From the identity, an undamped step overshoots: LM discards it, raises
+    lambda tenfold and keeps the poses; a later, damped step is kept."""
+    rng = np.random.default_rng(32)
+    T, ei, ej, Tij = random_graph(rng, 6, 4, noise=0.6)   # strongly inconsistent loops
+    start = [sim3.identity()] * 6
+    _, gn_hist, _ = pg.gauss_newton(start, ei, ej, Tij, iters=1)
+    assert gn_hist[1] > gn_hist[0]                   # the plain step raises chi^2
+    nodes, hist, lams = pg.levenberg_marquardt(start, ei, ej, Tij, iters=12, lambda0=1e-6)
+    assert hist[1] == hist[0] and lams[1] == lams[0] * 10.0
+    assert hist[-1] < hist[0]
+    assert all(b <= a for a, b in zip(hist, hist[1:]))
+
+
+def test_lm_fixed_point_is_stationary():
+    rng = np.random.default_rng(13)
+    T, ei, ej, Tij = random_graph(rng, 6, 2, noise=0.02)
+    init = pg.chain_init(6, ei, ej, Tij)
+    nodes, hist, lams = pg.levenberg_marquardt(init, ei, ej, Tij, iters=40, lambda0=1e-3)
+    h = 1e-6
+    for v in range(1, 6):
+        for a in range(7):
+            d = np.zeros(7)
+            d[a] = h
+            up, dn = list(nodes), list(nodes)
+            up[v] = sim3.compose(nodes[v], sim3.exp(d))
+            dn[v] = sim3.compose(nodes[v], sim3.exp(-d))
+            g = (pg.chi2(up, ei, ej, Tij) - pg.chi2(dn, ei, ej, Tij)) / (2 * h)
+            assert abs(g) < 1e-7, (v, a, g)
