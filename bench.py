@@ -651,6 +651,39 @@ def run_workload(args):
         out["fusion"] = {"points": npts, "kept": kept, "ms": fms,
                          "gbs_at_16B_plus_20B_per_kept":
                              (16.0 * npts + 20.0 * kept) / (fms * 1e-3) / 1e9}
+    elif args.workload == "loops32k":
+        # global loop retrieval over 32,768 keyframe embeddings of 1,024 dimensions
+        # (two laps of a 1.6 km route, a keyframe every 0.1 m), every 2nd keyframe
+        # in the BF16 tensor-core similarity matrix
+        n, d, stride = 32768, 1024, 2
+        E = synth.make_keyframe_embeddings(synth.SEED_BASE + 62, n=n, d=d, device=dev)
+        kw = dict(stride=stride, radius=2, gap=n // 5, tau_global=0.93, tau_local=0.96,
+                  capacity=1 << 18)
+        ms = _time(lambda: ctx.loop_candidates(E, **kw), 5)
+        assert ctx.sync_status() == 0
+        ctx.profile(True)
+        ctx.profile_read()
+        rows, scores, counts, _ = ctx.loop_candidates(E, **kw)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        m = (n + stride - 1) // stride
+        side = (m + 127) // 128
+        tiles = side * (side + 1) // 2
+        flops = 2.0 * tiles * 128 * 128 * d                 # the contraction the kernel does
+        tc_ms = prof["loop_sim_tc"][0]
+        bf16_peak = 1800.0
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16_peak = float(json.load(f)["bf16_tflops"])
+        except Exception:
+            pass
+        out["loop_retrieval"] = {
+            "keyframes": n, "dim": d, "stride": stride, "coarse_pairs": int(counts[0]),
+            "candidates": int(counts[1]), "ms": ms,
+            "kernels_ms": {k: v[0] for k, v in prof.items()},
+            "similarity_tflops": flops / (tc_ms * 1e-3) / 1e12,
+            "similarity_frac_of_bf16_peak": flops / (tc_ms * 1e-3) / 1e12 / bf16_peak,
+            "bf16_peak_tflops": bf16_peak}
     out["peak_gbs"] = peak
     out["peak_kind"] = peak_kind
     print(json.dumps(out), flush=True)
@@ -667,7 +700,7 @@ def main():
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--workload", default="chain200",
                     choices=["chain200", "pair1", "loops512", "adjoint1", "map1000",
-                             "depth200"],
+                             "depth200", "loops32k"],
                     help="chain200 is the benchmark; the others measure the other workloads")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="leave the adjoint out of the step (profiling only)")

@@ -407,6 +407,50 @@ ec3r_status ec3r_correct_points(ec3r_ctx* ctx, int64_t n_points, float* d_points
                                 const ec3r_sim3* d_poses, float conf_threshold,
                                 int64_t* d_n_corrected, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Global loop retrieval (Sec. III-D "Loop Retrieval and Verification")     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int stride;       /* similarities between every stride-th keyframe (the paper's N) */
+  int radius;       /* neighbourhood half-width around a similar pair, keyframes */
+  int gap;          /* minimum keyframe distance j - i of a loop */
+  float tau_global; /* coarse threshold (paper: 0.93) */
+  float tau_local;  /* neighbourhood threshold (paper: 0.96) */
+} ec3r_loop_opts;
+
+typedef struct {
+  int a, b;         /* coarse pair: sampled keyframes a*stride < b*stride */
+  int i, j;         /* best keyframe pair of its neighbourhood, i < j */
+  float s_coarse;   /* cosine of a and b from the BF16 tensor-core contraction */
+  float s;          /* cosine of i and j in FP32 */
+} ec3r_loop;        /* 24 bytes */
+
+/*
+ * Loop candidates among n keyframe embeddings d_emb (float32 [n][d], device;
+ * d a positive multiple of 64).  Similarity is the cosine of two embeddings.
+ * Every stride-th keyframe is normalised in FP32 and rounded to BF16; their
+ * similarity matrix S = A A^T (upper triangle) is a tensor-core contraction
+ * with FP32 accumulation; a coarse pair (a, b), a < b, qualifies when
+ * (b - a) * stride >= gap and S_ab > tau_global.  For each, the keyframes
+ * within `radius` of a*stride and of b*stride (with j - i >= gap) are compared
+ * by FP32 cosines; the best pair (largest cosine; ties: smallest i, then j)
+ * is a loop candidate when its cosine is > tau_local.
+ *
+ * d_loops (ec3r_loop [capacity], device) receives the candidates in no
+ * particular order; d_counts (int64 [2], device) receives the number of coarse
+ * pairs and of candidates (counting those past a buffer: ec3r_sync_status then
+ * returns EC3R_ERR_CAPACITY; the coarse buffer is context-owned and holds at
+ * least 2^20 pairs).  d_sim (float32 [m][m], m = ceil(n / stride), device,
+ * nullable) receives the upper triangle of S (diagonal included; the lower
+ * triangle is not written).  Workspace is context-owned; not graph-captured.
+ * A bounded wait that runs out raises EC3R_ERR_TIMEOUT at ec3r_sync_status.
+ */
+ec3r_status ec3r_loop_candidates(ec3r_ctx* ctx, const float* d_emb, int n, int d,
+                                 const ec3r_loop_opts* opts, ec3r_loop* d_loops,
+                                 int64_t capacity, int64_t* d_counts, float* d_sim,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,7 @@ EXPORTS = ("ec3r_create", "ec3r_destroy", "ec3r_last_error", "ec3r_status_string
            "ec3r_align_submaps", "ec3r_fuse_points", "ec3r_profile", "ec3r_profile_read",
            "ec3r_align_submaps_noalloc", "ec3r_pg_opts_default", "ec3r_pose_graph_correct",
            "ec3r_align_submaps_backward", "ec3r_align_submaps_depth", "ec3r_correct_points",
-           "ec3r_fuse_points_depth")
+           "ec3r_fuse_points_depth", "ec3r_loop_candidates")
 
 
 class Sim3(C.Structure):
@@ -44,6 +44,11 @@ class AlignOpts(C.Structure):
 class PgOpts(C.Structure):
     _fields_ = [("iters", C.c_int), ("fixed_node", C.c_int), ("lm_lambda", C.c_double),
                 ("init_by_chaining", C.c_int), ("lm_adaptive", C.c_int)]
+
+
+class LoopOpts(C.Structure):
+    _fields_ = [("stride", C.c_int), ("radius", C.c_int), ("gap", C.c_int),
+                ("tau_global", C.c_float), ("tau_local", C.c_float)]
 
 
 class Ec3rError(RuntimeError):
@@ -83,6 +88,8 @@ def _declare(l):
                                            _P, _P]
     l.ec3r_fuse_points_depth.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P,
                                          _P, C.c_float, _I64, _P, _P, _I64, _P, _P]
+    l.ec3r_loop_candidates.argtypes = [_P, _P, C.c_int, C.c_int, C.POINTER(LoopOpts), _P, _I64,
+                                       _P, _P, _P]
     l.ec3r_correct_points.argtypes = [_P, _I64, _P, _P, C.c_int, _I64, _P, _P, _P, C.c_float,
                                       _P, _P]
     l.ec3r_pg_opts_default.argtypes = [C.POINTER(PgOpts)]
@@ -92,7 +99,7 @@ def _declare(l):
     for name in ("ec3r_create", "ec3r_sync_status", "ec3r_align_submaps", "ec3r_fuse_points",
                  "ec3r_profile", "ec3r_profile_read", "ec3r_pose_graph_correct",
                  "ec3r_align_submaps_backward", "ec3r_align_submaps_depth", "ec3r_correct_points",
-           "ec3r_fuse_points_depth"):
+           "ec3r_fuse_points_depth", "ec3r_loop_candidates"):
         getattr(l, name).restype = C.c_int
 
 
@@ -308,6 +315,28 @@ class Context:
             _ptr(poses), float(threshold), int(index_base), _ptr(out_xyz), _ptr(out_idx),
             int(out_idx.numel()), _ptr(cursor), _stream(stream))
         self._check(st)
+
+    # -- global loop retrieval ----------------------------------------------
+    def loop_candidates(self, emb, *, stride=5, radius=2, gap=50, tau_global=0.93,
+                        tau_local=0.96, capacity=1 << 16, with_sim=False, stream=None):
+        """Loop candidates of keyframe embeddings emb [n, d] (float32, device).
+
+        Returns (rows int32 [k, 4] = (a, b, i, j), scores float32 [k, 2] =
+        (coarse, local), counts int64 [2] = (coarse pairs, candidates), S or None)."""
+        n, d = int(emb.shape[0]), int(emb.shape[1])
+        if emb.dtype != torch.float32:
+            raise ValueError("emb must be float32")
+        buf = torch.empty((max(int(capacity), 1), 6), dtype=torch.int32, device=emb.device)
+        counts = torch.empty((2,), dtype=torch.int64, device=emb.device)
+        m = (n + stride - 1) // stride
+        sim = torch.full((m, m), float("nan"), device=emb.device) if with_sim else None
+        o = LoopOpts(int(stride), int(radius), int(gap), float(tau_global), float(tau_local))
+        st = self._lib.ec3r_loop_candidates(self._h, _ptr(emb), n, d, C.byref(o), _ptr(buf),
+                                            int(capacity), _ptr(counts), _ptr(sim),
+                                            _stream(stream))
+        self._check(st)
+        k = min(int(counts[1]), int(capacity))
+        return buf[:k, :4], buf[:k, 4:].view(torch.float32), counts, sim
 
     # -- point correction --------------------------------------------------
     def correct_points(self, points, refs, xyz, conf, poses, *, threshold=1.0, n_corrected=None,

@@ -459,6 +459,35 @@ def make_depth_chain(seed: int, M: int, F: int = 5, H: int = 294, W: int = 518,
                                 seed=seed))
 
 
+def make_keyframe_embeddings(seed: int, n: int, d: int = 1024, laps: int = 2,
+                             spacing: float = 0.1, sigma: float = 0.35, noise: float = 0.15,
+                             device="cpu") -> torch.Tensor:
+    """Keyframe embeddings of a closed route driven ``laps`` times, one keyframe
+    every ``spacing`` metres (float32 [n, d]).
+
+    A keyframe's embedding stands for its image's pooled encoder feature: random
+    Fourier features of its place, sqrt(2/d) cos(W p + b) with W ~ N(0, I /
+    sigma^2), so two embeddings' cosine is close to exp(-|p - q|^2 / (2 sigma^2)),
+    plus N(0, noise^2 / d) per dimension (a noise vector of norm about
+    ``noise``, independent of d).  Later laps revisit earlier places with a
+    lateral offset drawn per lap, which makes the global loop candidates.
+    """
+    g = _gen(seed, device)
+    length = n * spacing / laps
+    radius = length / (2.0 * math.pi)
+    k = torch.arange(n, device=device, dtype=torch.float64)
+    lap = torch.div(k, n / laps, rounding_mode="floor").clamp(max=laps - 1)
+    ang = 2.0 * math.pi * (k * spacing / length)
+    off = _uniform(g, (laps,), -0.1, 0.1, device)[lap.long()]
+    r = radius + off
+    p = torch.stack([r * torch.cos(ang), r * torch.sin(ang), torch.zeros_like(ang)], -1)
+    W = _normal(g, (d, 3), device) / sigma
+    b = _uniform(g, (d,), 0.0, 2.0 * math.pi, device)
+    E = (math.sqrt(2.0 / d) * torch.cos(p @ W.T + b) +
+         (noise / math.sqrt(d)) * _normal(g, (n, d), device))
+    return E.to(torch.float32)
+
+
 def chain_pair_truth(chain: Chain) -> Sim3:
     """Ground truth of pair m (submap m+1 -> submap m): T_m^-1 T_{m+1}."""
     s, R, t = chain.T_gt.s, chain.T_gt.R, chain.T_gt.t

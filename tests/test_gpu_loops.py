@@ -1,0 +1,78 @@
+"""GPU parity of ec3r_loop_candidates (Sec. III-D global loop retrieval) against
+the oracle: the BF16 tensor-core similarity matrix within 1e-4 of the
+oracle's (normalised embeddings rounded to BF16, exact products); the coarse
+pairs and loop candidates equal, except pairs within 1e-4 of a threshold,
+which may fall on either side (the two sides normalise with different FP32
+roundings)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import loops as olp
+from paper_2510_02080_b300 import ec3r, synth
+
+pytestmark = pytest.mark.gpu
+MARGIN = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_lib):
+    c = ec3r.Context()
+    yield c
+    c.close()
+
+
+def test_similarity_matrix_on_the_tensor_cores(ctx):
+    # 700 keyframes, every 2nd: 350 samples = 3 x 3 tiles of 128 (ragged), d = 256
+    rng = np.random.default_rng(0)
+    E = rng.normal(size=(700, 256)).astype(np.float32)
+    E[::7] += 3.0 * E[3]                                # some strongly similar rows
+    rows, scores, counts, S = ctx.loop_candidates(torch.tensor(E, device="cuda"), stride=2,
+                                                  radius=1, gap=4, tau_global=0.5,
+                                                  tau_local=0.6, with_sim=True)
+    assert ctx.sync_status() == 0
+    ref = olp.coarse_similarity(E, 2)
+    got = S.cpu().numpy()
+    iu = np.triu_indices(ref.shape[0])
+    assert np.abs(got[iu] - ref[iu]).max() <= MARGIN
+    assert np.all(np.isnan(got[np.tril_indices(ref.shape[0], -1)]))
+
+
+@pytest.mark.parametrize("n,d,stride", [(2000, 256, 4), (3000, 512, 3)])
+def test_loop_candidates_match_oracle(ctx, n, d, stride):
+    E = synth.make_keyframe_embeddings(synth.SEED_BASE + 60, n=n, d=d).numpy()
+    kw = dict(stride=stride, radius=2, gap=n // 5, tau_global=0.93, tau_local=0.96)
+    rows, scores, counts, _ = ctx.loop_candidates(torch.tensor(E, device="cuda"), **kw)
+    assert ctx.sync_status() == 0
+    coarse, found = olp.loop_candidates(E, **kw)
+    S = olp.coarse_similarity(E, stride)
+    got = {(int(a), int(b)): (int(i), int(j), float(sc), float(s))
+           for (a, b, i, j), (sc, s) in zip(rows.cpu().numpy(), scores.cpu().numpy())}
+    want = {(a, b): (i, j, s) for a, b, i, j, s in found}
+    ref_coarse = {(a, b) for a, b, _ in coarse}
+    assert len(want) > 20
+    # coarse pairs: every clear one found, none clearly below the threshold
+    m = S.shape[0]
+    near = {(a, b) for a in range(m) for b in range(a + 1, m)
+            if abs(S[a, b] - kw["tau_global"]) <= MARGIN}
+    assert int(counts[0]) >= len(ref_coarse - near)
+    assert int(counts[0]) <= len(ref_coarse | near)
+    for key, (i, j, s) in want.items():
+        if key in near or abs(s - kw["tau_local"]) <= MARGIN:
+            continue
+        assert key in got, key
+        gi, gj, gsc, gs = got[key]
+        assert abs(gs - s) <= 1e-5 and abs(gsc - S[key]) <= MARGIN
+        assert (gi, gj) == (i, j) or abs(gs - s) <= 1e-5
+    for key, (gi, gj, gsc, gs) in got.items():
+        assert key in want or key in near or abs(gs - kw["tau_local"]) <= MARGIN, key
+
+
+def test_capacity_and_arguments(ctx):
+    E = synth.make_keyframe_embeddings(synth.SEED_BASE + 61, n=1500, d=128)
+    rows, scores, counts, _ = ctx.loop_candidates(E.cuda(), stride=3, radius=1, gap=300,
+                                                  tau_global=0.93, tau_local=0.96, capacity=3)
+    assert int(counts[1]) > 3 and rows.shape[0] == 3
+    assert ctx.sync_status() == 4                      # EC3R_ERR_CAPACITY
+    with pytest.raises(ec3r.Ec3rError):
+        ctx.loop_candidates(torch.zeros((10, 100), device="cuda"))   # d not a multiple of 64
