@@ -655,7 +655,7 @@ def run_workload(args):
         # global loop retrieval over 32,768 keyframe embeddings of 1,024 dimensions
         # (two laps of a 1.6 km route, a keyframe every 0.1 m), every 2nd keyframe
         # in the BF16 tensor-core similarity matrix
-        n, d, stride = 32768, 1024, 2
+        n, d, stride = args.keyframes, 1024, 2
         E = synth.make_keyframe_embeddings(synth.SEED_BASE + 62, n=n, d=d, device=dev)
         kw = dict(stride=stride, radius=2, gap=n // 5, tau_global=0.93, tau_local=0.96,
                   capacity=1 << 18)
@@ -669,7 +669,7 @@ def run_workload(args):
         m = (n + stride - 1) // stride
         side = (m + 127) // 128
         tiles = side * (side + 1) // 2
-        flops = 2.0 * tiles * 128 * 128 * d                 # the contraction the kernel does
+        flops = 2.0 * tiles * 128 * 128 * d      # the 128 x 128 blocks meeting the upper triangle
         tc_ms = prof["loop_sim_tc"][0]
         bf16_peak = 1800.0
         try:
@@ -706,6 +706,9 @@ def main():
                     help="leave the adjoint out of the step (profiling only)")
     ap.add_argument("--submaps", type=int, default=M_SUBMAPS,
                     help="chain length (default 200); smaller values are for profiling only")
+    ap.add_argument("--keyframes", type=int, default=32768,
+                    help="keyframes of loops32k (default 32768); smaller values are for "
+                         "profiling only")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
