@@ -224,14 +224,17 @@ __global__ void __launch_bounds__(256) k_solve(int n_pairs, const int32_t* __res
   __syncwarp();
   if (lane != 0) return;
   const double* M = mom[wib];
-  double R[9], s = 1.0, b[3] = {0, 0, 0};
-  const unsigned status = umeyama_from_moments(M, R, s, b);
+  double R[9], s = 1.0, b[3] = {0, 0, 0}, dV[12];
   double* ck = ckpt ? ckpt + ((size_t)warp * iters + (it - 1)) * CKPT : nullptr;
+  const unsigned status = umeyama_from_moments(M, R, s, b, ck ? dV : nullptr);
   if (ck) {
     for (int m = 0; m < NMOM; ++m) ck[CK_MOM + m] = M[m];
     for (int i = 0; i < 9; ++i) ck[CK_A + i] = s * R[i];
     for (int i = 0; i < 3; ++i) ck[CK_B + i] = b[i];
     ck[CK_STATUS] = (double)status;
+    ck[CK_S] = s;
+    for (int i = 0; i < 9; ++i) ck[CK_R + i] = R[i];
+    for (int i = 0; i < 12; ++i) ck[CK_D + i] = status ? 0.0 : dV[i];
   }
   commit_estimate(S, status, R, s, b, last, out[warp], status_out[warp]);
 }

@@ -35,21 +35,54 @@ struct AdjState {
   int pad;
 };
 
+// FP32 parameters of one pair for the next reduction sweep, written once per
+// pair by the kernel before it (so that no sweep thread converts FP64
+// checkpoints): "prev" estimate (weights), "cur" estimate (cost residual),
+// the moments' gradient, dL/dJ, dL/dOm, pivots, confidence floor and the
+// Huber threshold of that iteration.
+struct RedParams {
+  float Ap[9], bp[3], Ac[9], bc[3], G[NGM];
+  float gJ, gOm, pp[3], pq[3], cmin, dl;
+  int active;
+  int pad[3];
+};
+
+__device__ inline void write_red_params(RedParams& P, const double* ckb, int k_it, bool cur,
+                                        const double* G, const AdjState& a, const PairState& S,
+                                        float delta) {
+  const bool first = k_it == 1;
+  for (int i = 0; i < 9; ++i) {
+    P.Ap[i] = first ? ((i % 4 == 0) ? 1.f : 0.f) : (float)ckb[(k_it - 2) * CKPT + CK_A + i];
+    P.Ac[i] = cur ? (float)ckb[(k_it - 1) * CKPT + CK_A + i] : 0.f;
+  }
+  for (int i = 0; i < 3; ++i) {
+    P.bp[i] = first ? 0.f : (float)ckb[(k_it - 2) * CKPT + CK_B + i];
+    P.bc[i] = cur ? (float)ckb[(k_it - 1) * CKPT + CK_B + i] : 0.f;
+    P.pp[i] = S.piv_p[i];
+    P.pq[i] = S.piv_q[i];
+  }
+  for (int i = 0; i < NGM; ++i) P.G[i] = G ? (float)G[i] : 0.f;
+  P.gJ = (float)a.gJ;
+  P.gOm = (float)a.gOm;
+  P.cmin = S.cmin;
+  P.dl = first ? FLT_MAX : delta;
+}
+
 __device__ inline void ck_sR(const double* ck, double* s, double* R) {
-  const double* A = ck + CK_A;
-  const double sc = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
-  *s = sc;
-  for (int i = 0; i < 9; ++i) R[i] = A[i] / sc;
+  *s = ck[CK_S];
+  for (int i = 0; i < 9; ++i) R[i] = ck[CK_R + i];
 }
 
 __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ckpt,
                            const PairState* __restrict__ st, const int32_t* __restrict__ status,
                            const double* __restrict__ cost, const double* __restrict__ gS,
-                           const double* __restrict__ gcost, AdjState* __restrict__ adj) {
+                           const double* __restrict__ gcost, AdjState* __restrict__ adj,
+                           float delta, RedParams* __restrict__ rp) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_pairs) return;
   AdjState& a = adj[k];
   a.active = (status[k] == 0 && st[k].active) ? 1 : 0;
+  rp[k].active = a.active;
   a.gs = 0.0;
   for (int i = 0; i < 9; ++i) a.gR[i] = 0.0;
   for (int i = 0; i < 3; ++i) a.gb[i] = 0.0;
@@ -72,6 +105,8 @@ __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ck
     a.gJ = gcost[k] / W;
     a.gOm = -gcost[k] * cost[k] / W;
   }
+  // the cost sweep: om at S_{K-1}, residual at S_K
+  write_red_params(rp[k], ckpt + (size_t)k * iters * CKPT, iters, true, nullptr, a, st[k], delta);
 }
 
 // Reduction sweeps.  KIND 0: cost (om at S_{K-1}, e at S_K);  KIND 1: Huber
@@ -80,36 +115,32 @@ template <int KIND, bool LASTK, bool VEC>
 __global__ void __launch_bounds__(THREADS, 3) k_adj_reduce(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
-    const int32_t* __restrict__ link_pair, const PairState* __restrict__ st,
-    const AdjState* __restrict__ adj, const double* __restrict__ ckpt,
-    const double* __restrict__ gM, int iters, int k_it, float delta, int rule,
+    const int32_t* __restrict__ link_pair, const RedParams* __restrict__ rp, int rule,
     double* __restrict__ partials) {
   const int64_t t = blockIdx.x;
   const int64_t l = t / tpl;
   const int c = (int)(t - l * tpl);
   const int k = link_pair[l];
   if (k < 0) return;
-  if (!adj[k].active) return;
+  const RedParams& RP = rp[k];
+  if (!RP.active) return;
   // estimates: "prev" = S_{k_it-1} (weights), "cur" = S_{k_it} (cost residual)
   float Ap[9], bp[3], Ac[9], bc[3], G[NGM];
-  const double* ckb = ckpt + (size_t)k * iters * CKPT;
-  const bool first = k_it == 1;
   for (int i = 0; i < 9; ++i) {
-    Ap[i] = first ? ((i % 4 == 0) ? 1.f : 0.f) : (float)ckb[(k_it - 2) * CKPT + CK_A + i];
-    Ac[i] = (KIND == 0 || LASTK) ? (float)ckb[(k_it - 1) * CKPT + CK_A + i] : 0.f;
+    Ap[i] = RP.Ap[i];
+    Ac[i] = (KIND == 0 || LASTK) ? RP.Ac[i] : 0.f;
   }
   for (int i = 0; i < 3; ++i) {
-    bp[i] = first ? 0.f : (float)ckb[(k_it - 2) * CKPT + CK_B + i];
-    bc[i] = (KIND == 0 || LASTK) ? (float)ckb[(k_it - 1) * CKPT + CK_B + i] : 0.f;
+    bp[i] = RP.bp[i];
+    bc[i] = (KIND == 0 || LASTK) ? RP.bc[i] : 0.f;
   }
-  for (int i = 0; i < NGM; ++i)
-    G[i] = KIND == 1 ? (float)gM[((size_t)k * iters + (k_it - 1)) * NGM + i] : 0.f;
-  const float gJ = (float)adj[k].gJ, gOm = (float)adj[k].gOm;
+  for (int i = 0; i < NGM; ++i) G[i] = KIND == 1 ? RP.G[i] : 0.f;
+  const float gJ = RP.gJ, gOm = RP.gOm;
   constexpr bool lastk = LASTK;  // the cost residual at S_K enters the last Huber sweep
-  const float pp0 = st[k].piv_p[0], pp1 = st[k].piv_p[1], pp2 = st[k].piv_p[2];
-  const float pq0 = st[k].piv_q[0], pq1 = st[k].piv_q[1], pq2 = st[k].piv_q[2];
-  const float cmin = st[k].cmin;
-  const float dl = first ? FLT_MAX : delta;
+  const float pp0 = RP.pp[0], pp1 = RP.pp[1], pp2 = RP.pp[2];
+  const float pq0 = RP.pq[0], pq1 = RP.pq[1], pq2 = RP.pq[2];
+  const float cmin = RP.cmin;
+  const float dl = RP.dl;
 
   const int64_t fs = src[l], ft = tgt[l];
   const int64_t px0 = (int64_t)c * TILE;
@@ -217,7 +248,9 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
                                                    int have_partials, int scale_by_gJ,
                                                    const double* __restrict__ ckpt,
                                                    AdjState* __restrict__ adj,
-                                                   double* __restrict__ gM) {
+                                                   double* __restrict__ gM,
+                                                   const PairState* __restrict__ st,
+                                                   float delta, RedParams* __restrict__ rp) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   __shared__ double red[8][NRED];
@@ -259,8 +292,11 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
   for (int i = 0; i < 3; ++i)
     for (int k = 0; k < 3; ++k) Sig[3 * i + k] = M[M_QP + 3 * i + k] * iw - mq[i] * mp[k];
   const double var = M[M_PP] * iw - (mp[0] * mp[0] + mp[1] * mp[1] + mp[2] * mp[2]);
-  double Rr[9], d[3], V[9];
-  polar_rotation(Sig, Rr, d, V);
+  // the forward solve's polar factor R = U' V^T of Sig and its d, V
+  const double* Rr = R;
+  double d[3], V[9];
+  for (int i = 0; i < 3; ++i) d[i] = ck[CK_D + i];
+  for (int i = 0; i < 9; ++i) V[i] = ck[CK_V + i];
   double tau = 0.0;
   for (int i = 0; i < 9; ++i) tau += Rr[i] * Sig[i];
   // b = mq - s R mp
@@ -323,6 +359,12 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
     gW -= (gmp[k] * M[M_SP + k] + gmq[k] * M[M_SQ + k]) * iw * iw;
   }
   out[G_W] = gW;
+  // parameters of the Huber sweep of iteration j (it rebuilds the adjoint of
+  // estimate j-1); iteration 1 starts from the identity with unit weights and
+  // has none
+  if (j >= 2)
+    write_red_params(rp[warp], ckpt + (size_t)warp * iters * CKPT, j, j == iters, out, a,
+                     st[warp], delta);
   // the adjoint of estimate j-1 is rebuilt by the next Huber sweep
   a.gs = 0.0;
   for (int i = 0; i < 9; ++i) a.gR[i] = 0.0;
@@ -688,6 +730,9 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
   const int64_t n_tiles = n_links * tpl;
   void *p_adj, *p_gm, *p_part, *p_lg;
   if ((st = ensure_buf(ctx, "adj.state", sizeof(AdjState) * (size_t)n_pairs, s, &p_adj))) return st;
+  void* p_rp;
+  if ((st = ensure_buf(ctx, "adj.red_params", sizeof(RedParams) * (size_t)n_pairs, s, &p_rp)))
+    return st;
   if ((st = ensure_buf(ctx, "adj.gM", sizeof(double) * NGM * (size_t)n_pairs * iters, s, &p_gm)))
     return st;
   if ((st = ensure_buf(ctx, "adj.partials", sizeof(double) * NRED * (size_t)(n_tiles + 1), s,
@@ -701,6 +746,7 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
   double* ckpt = (double*)ctx->bufs["align.ckpt"].ptr;
   int32_t* link_pair = (int32_t*)ctx->bufs["align.link_pair"].ptr;
   AdjState* adj = (AdjState*)p_adj;
+  RedParams* rp = (RedParams*)p_rp;
   double* gM = (double*)p_gm;
   double* part = (double*)p_part;
   float* lg = (float*)p_lg;
@@ -726,23 +772,22 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
     traced(ctx, cs, "adj_init", [&] {
       k_adj_init<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, iters, ckpt, state,
                                                       (const int32_t*)p_st, (const double*)p_cost,
-                                                      d_grad_S, d_grad_cost, adj);
+                                                      d_grad_S, d_grad_cost, adj, delta, rp);
     });
     const bool cost_path = d_grad_cost != nullptr;
     if (cost_path && n_tiles > 0)
       traced(ctx, cs, "adj_reduce", [&] {
         if (vec)
           k_adj_reduce<0, false, true><<<grid, THREADS, 0, cs>>>(
-              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
-              iters, delta, rule, part);
+              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
         else
           k_adj_reduce<0, false, false><<<grid, THREADS, 0, cs>>>(
-              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
-              iters, delta, rule, part);
+              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
       });
     traced(ctx, cs, "adj_solve", [&] {
       k_adj_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, iters, iters, d_link_off, (int)tpl, part,
-                                               cost_path && n_tiles > 0, 1, ckpt, adj, gM);
+                                               cost_path && n_tiles > 0, 1, ckpt, adj, gM, state,
+                                               delta, rp);
     });
     for (int k = iters; k >= 2; --k) {
       if (n_tiles > 0)
@@ -750,24 +795,21 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
           const bool last = k == iters;
           if (vec && last)
             k_adj_reduce<1, true, true><<<grid, THREADS, 0, cs>>>(
-                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM,
-                iters, k, delta, rule, part);
+                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
           else if (vec)
             k_adj_reduce<1, false, true><<<grid, THREADS, 0, cs>>>(
-                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM,
-                iters, k, delta, rule, part);
+                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
           else if (last)
             k_adj_reduce<1, true, false><<<grid, THREADS, 0, cs>>>(
-                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM,
-                iters, k, delta, rule, part);
+                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
           else
             k_adj_reduce<1, false, false><<<grid, THREADS, 0, cs>>>(
-                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM,
-                iters, k, delta, rule, part);
+                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
         });
       traced(ctx, cs, "adj_solve", [&] {
         k_adj_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, iters, k - 1, d_link_off, (int)tpl,
-                                                 part, n_tiles > 0, 0, ckpt, adj, gM);
+                                                 part, n_tiles > 0, 0, ckpt, adj, gM, state,
+                                                 delta, rp);
       });
     }
     EC3R_CUDA_TRY(ctx, cudaMemsetAsync(refs, 0, sizeof(int32_t) * (size_t)(n_frames + 1), cs));

@@ -33,9 +33,13 @@ struct PairState {
 __device__ __forceinline__ bool finitef(float x) { return fabsf(x) <= FLT_MAX; }
 
 // Per pair and iteration, the forward solve keeps (for the backward pass) the
-// 19 moments, A = s R (9) and b (3) of its estimate, and its status.
-constexpr int CKPT = 32;
-enum { CK_MOM = 0, CK_A = 19, CK_B = 28, CK_STATUS = 31 };
+// 19 moments, A = s R (9) and b (3) of its estimate, its status, s and R
+// themselves, and the singular values d (3) and right singular vectors V (9)
+// of its cross-covariance (the pieces of the polar factor's derivative).
+constexpr int CKPT = 56;
+enum {
+  CK_MOM = 0, CK_A = 19, CK_B = 28, CK_STATUS = 31, CK_S = 32, CK_R = 33, CK_D = 42, CK_V = 45
+};
 
 // --------------------------------------------------------------------------
 // solve
@@ -277,7 +281,7 @@ __device__ inline void write_identity(ec3r_sim3* o) {
 // the new estimate (R, s, b) with b the pivot-relative translation, or a
 // status bit (R = I, s = 1, b = 0) for a degenerate pair.
 __device__ inline unsigned umeyama_from_moments(const double* M, double R[9], double& s,
-                                                double b[3]) {
+                                                double b[3], double* dV = nullptr) {
   for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
   s = 1.0;
   b[0] = b[1] = b[2] = 0.0;
@@ -297,8 +301,8 @@ __device__ inline unsigned umeyama_from_moments(const double* M, double R[9], do
   const double var = M[M_PP] * iw - (mp[0] * mp[0] + mp[1] * mp[1] + mp[2] * mp[2]);
   if (!fin || !isfinite(var)) return EC3R_PAIR_NONFINITE;
   if (!(var > 0.0)) return EC3R_PAIR_RANK;
-  double d[3], Rn[9];
-  polar_rotation(Sig, Rn, d);
+  double d[3], Rn[9], V[9];
+  polar_rotation(Sig, Rn, d, V);
   if (!(d[0] > 0.0) || fabs(d[1]) <= RANK_REL_TOL * d[0]) return EC3R_PAIR_RANK;
   // tr(R^T Sig) = tr(D E): the Umeyama scale numerator
   double tr = 0.0;
@@ -313,6 +317,10 @@ __device__ inline unsigned umeyama_from_moments(const double* M, double R[9], do
   for (int i = 0; i < 9; ++i) R[i] = Rn[i];
   s = sn;
   for (int i = 0; i < 3; ++i) b[i] = bn[i];
+  if (dV) {
+    for (int i = 0; i < 3; ++i) dV[i] = d[i];
+    for (int i = 0; i < 9; ++i) dV[3 + i] = V[i];
+  }
   return 0;
 }
 

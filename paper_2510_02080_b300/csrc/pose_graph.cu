@@ -18,10 +18,12 @@
 //                    blocks J^T Omega J, J^T Omega e, e^T Omega e
 //   k_pg_assemble    one warp per factor block: fixed-order sums of the edge
 //                    blocks (deterministic, no atomics); g; chi^2
-//   k_pg_factor      one launch per tree level, one warp per 7x7 block column:
-//                    left-looking updates, dense 7x7 Cholesky, off-diagonal
-//                    triangular solves, forward substitution
-//   k_pg_backsolve   one launch per level, root to leaves
+//   k_pg_factor      one launch per tree level, four warps per 7x7 block
+//                    column: left-looking updates into the column staged in
+//                    shared memory, dense 7x7 Cholesky, off-diagonal triangular
+//                    solves, forward substitution (its products formed in
+//                    parallel with the updates)
+//   k_pg_backsolve   one launch per level, root to leaves, one warp per column
 //   k_pg_update      one thread per node: T <- T Exp(delta)
 #include <algorithm>
 #include <cmath>
@@ -160,6 +162,8 @@ struct PgDev {
   double lambda;
   const int *ei, *ej, *perm, *col_ptr, *off_row, *off_blk, *grp_ptr, *grp, *upd_ab, *sn_grp,
       *row_ptr, *row, *level_ptr, *level_cols, *asm_ptr, *asm_it, *g_ptr, *g_it;
+  const int4* col_meta;  // per column in level order: ColMeta as two int4
+  const int* grp_slot;   // per update group: its block's slot in the column (0: diagonal)
   double *L, *b, *contrib, *gvec, *chi2e, *idiag, *chi2;
   double* lm;           // adaptive LM: lambda, chi^2 at the step's start, after it (else null)
   ec3r_sim3* backup;    // adaptive LM: poses before the tentative step
@@ -344,12 +348,31 @@ __device__ __forceinline__ void apply_group(double* L, int dst, const int* __res
   }
 }
 
+// Entry idx of block dst after its group's updates (the arithmetic of
+// apply_group), returned instead of stored.
+__device__ __forceinline__ double group_entry(const double* L, int dst, const int* __restrict__ ab,
+                                              int n, int idx) {
+  const int r = idx / 7, c = idx % 7;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int q = 0; q < n; ++q) {
+    const double* A = L + (size_t)ab[2 * q] * NB + 7 * r;
+    const double* B = L + (size_t)ab[2 * q + 1] * NB + 7 * c;
+    s0 = fma(ldc(A + 0), ldc(B + 0), s0);
+    s1 = fma(ldc(A + 1), ldc(B + 1), s1);
+    s2 = fma(ldc(A + 2), ldc(B + 2), s2);
+    s3 = fma(ldc(A + 3), ldc(B + 3), s3);
+    s0 = fma(ldc(A + 4), ldc(B + 4), s0);
+    s1 = fma(ldc(A + 5), ldc(B + 5), s1);
+    s2 = fma(ldc(A + 6), ldc(B + 6), s2);
+  }
+  return ldc(L + (size_t)dst * NB + idx) - ((s0 + s1) + (s2 + s3));
+}
+
 // Dense 7x7 Cholesky (lower) of the block at Lkk into D (shared), reciprocal
 // pivots (through rsqrt) into inv; writes the factor back and the reciprocal
 // pivots to id.  One warp.  A non-positive or non-finite pivot raises NOT_SPD.
-__device__ void chol7(double* Lkk, double* id, double* D, double* inv, int lane, const PgDev& p) {
-  for (int idx = lane; idx < NB; idx += 32) D[idx] = ldc(Lkk + idx);
-  __syncwarp();
+__device__ void chol7_core(double* Lkk, double* id, double* D, double* inv, int lane,
+                           const PgDev& p) {
   bool bad = false;
   for (int c = 0; c < 7; ++c) {
     const double d = D[8 * c];
@@ -372,9 +395,18 @@ __device__ void chol7(double* Lkk, double* id, double* D, double* inv, int lane,
     atomicOr(p.flags, FLAG_NOT_SPD);
     atomicExch(p.fail, 1);
   }
-  for (int idx = lane; idx < NB; idx += 32) Lkk[idx] = (idx % 7 <= idx / 7) ? D[idx] : 0.0;
+  for (int idx = lane; idx < NB; idx += 32) {
+    if (idx % 7 > idx / 7) D[idx] = 0.0;
+    Lkk[idx] = D[idx];
+  }
   if (lane < 7) id[lane] = inv[lane];
   __syncwarp();
+}
+
+__device__ void chol7(double* Lkk, double* id, double* D, double* inv, int lane, const PgDev& p) {
+  for (int idx = lane; idx < NB; idx += 32) D[idx] = ldc(Lkk + idx);
+  __syncwarp();
+  chol7_core(Lkk, id, D, inv, lane, p);
 }
 
 // One row of an off-diagonal block, in place: x <- x Lkk^-T.
@@ -397,9 +429,9 @@ __device__ __forceinline__ void lower_solve7(double* y, const double* D, const d
   }
 }
 __device__ __forceinline__ void upper_solve7(double* x, const double* D, const double* inv) {
-  for (int c = 6; c >= 0; --c) {
+  for (int c = 6; c >= 0; --c) {  // x[c + 1], the latest, enters last: a short chain
     double s = x[c];
-    for (int t = c + 1; t < 7; ++t) s -= D[7 * t + c] * x[t];
+    for (int t = 6; t > c; --t) s -= D[7 * t + c] * x[t];
     x[c] = s * inv[c];
   }
 }
@@ -513,16 +545,152 @@ __global__ void k_pg_decide(PgDev p) {
   if (k == 0) p.lm[0] = accept ? fmax(ldc(p.lm) * 0.1, LM_MIN) : fmin(ldc(p.lm) * 10.0, LM_MAX);
 }
 
-constexpr int FWARPS = 4;  // warps per column in k_pg_factor
+constexpr int FWARPS = 4;   // warps per column in k_pg_factor
+constexpr int CB_MAX = 31;  // staged blocks of a column: the diagonal + up to 30 below it
+constexpr int FS_MAX = 64;  // staged forward-substitution terms of a column
 
-__global__ void __launch_bounds__(32 * FWARPS) k_pg_factor(PgDev p, int level) {
-  __shared__ double D[NB], inv[7], y[7];
-  factor_column<FWARPS>(p.level_cols[p.level_ptr[level] + blockIdx.x], threadIdx.x, D, inv, y, p);
+// Per column (in level order), built on the host: the column, its update
+// groups [g0, g1), its off-diagonal blocks [o0, o1), its forward-substitution
+// terms [r0, r1), the slots filled by groups (bit s), and whether the column
+// fits the staged schedule.
+struct ColMeta {
+  int k, g0, g1, o0, o1, r0, r1, mask_fast;  // mask_fast: slot mask << 1 | fits
+};
+
+__device__ __forceinline__ ColMeta load_meta(const int4* m, int pos) {
+  const int4 a = m[2 * pos], b = m[2 * pos + 1];
+  return ColMeta{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 }
 
-__global__ void __launch_bounds__(32) k_pg_backsolve(PgDev p, int level) {
-  __shared__ double x[7];
-  backsolve_column(p.level_cols[p.level_ptr[level] + blockIdx.x], threadIdx.x, x, p);
+// Column c by a CTA of four warps (tid in [0, 128)), staged schedule (a
+// column with at most 30 blocks below the diagonal and 64 forward-substitution
+// terms), every dependent step spread over the team:
+//   1. the column's blocks enter shared memory, either as stored or through
+//      their update group (left-looking, group_entry); the products
+//      L_kj y_j of the forward substitution are formed meanwhile, one row of
+//      one term per thread;
+//   2. warp 0 factors the diagonal block; warp 1 sums b_k - sum_j L_kj y_j;
+//   3. warps 0..2 solve the rows of the off-diagonal blocks, warp 3 the
+//      diagonal system of the forward substitution.
+__device__ void factor_staged(const ColMeta& c, int tid, double* CB, double* fpart, double* inv,
+                              double* y, const PgDev& p) {
+  const int lane = tid & 31, warp = tid >> 5;
+  const int k = c.k;
+  const unsigned filled = (unsigned)c.mask_fast >> 1;
+  const int nblk = c.o1 - c.o0, nrow = c.r1 - c.r0;
+  for (int it = tid; it < (1 + nblk) * NB; it += 32 * FWARPS) {
+    const int sl = it / NB;
+    if ((filled >> sl) & 1u) continue;
+    const int blk = sl == 0 ? k : p.off_blk[c.o0 + sl - 1];
+    CB[it] = ldc(p.L + (size_t)blk * NB + it % NB);
+  }
+  for (int it = tid; it < (c.g1 - c.g0) * NB; it += 32 * FWARPS) {
+    const int g = c.g0 + it / NB, idx = it % NB;
+    CB[p.grp_slot[g] * NB + idx] =
+        group_entry(p.L, p.grp[3 * g], p.upd_ab + 2 * p.grp[3 * g + 1], p.grp[3 * g + 2], idx);
+  }
+  for (int it = tid; it < nrow * 7; it += 32 * FWARPS) {
+    const int q = c.r0 + it / 7, r = it % 7;
+    const double* Lkj = p.L + (size_t)p.row[2 * q + 1] * NB + 7 * r;
+    const double* yj = p.b + 7 * p.row[2 * q];
+    double s0 = ldc(Lkj) * ldc(yj), s1 = ldc(Lkj + 1) * ldc(yj + 1);
+    double s2 = ldc(Lkj + 2) * ldc(yj + 2);
+    s0 = fma(ldc(Lkj + 3), ldc(yj + 3), s0);
+    s1 = fma(ldc(Lkj + 4), ldc(yj + 4), s1);
+    s2 = fma(ldc(Lkj + 5), ldc(yj + 5), s2);
+    s0 = fma(ldc(Lkj + 6), ldc(yj + 6), s0);
+    fpart[it] = (s0 + s1) + s2;
+  }
+  if (tid >= 64 && tid < 71) y[tid - 64] = ldc(p.b + 7 * k + tid - 64);
+  __syncthreads();
+  if (warp == 0) {
+    chol7_core(p.L + (size_t)k * NB, p.idiag + 7 * k, CB, inv, lane, p);
+  } else if (warp == 1 && lane < 7) {
+    double s = y[lane];
+    for (int q = 0; q < nrow; ++q) s -= fpart[7 * q + lane];
+    y[lane] = s;
+  }
+  __syncthreads();
+  if (warp == FWARPS - 1) {
+    if (lane == 0) lower_solve7(y, CB, inv);
+    __syncwarp();
+    if (lane < 7) p.b[7 * k + lane] = y[lane];
+  } else {
+    for (int it = tid; it < nblk * 7; it += 32 * (FWARPS - 1)) {
+      const int sl = 1 + it / 7, r = it % 7;
+      const double* X = CB + sl * NB + 7 * r;
+      double x[7];
+      for (int cc = 0; cc < 7; ++cc) {
+        double v = X[cc];
+        for (int t = 0; t < cc; ++t) v -= x[t] * CB[7 * cc + t];
+        x[cc] = v * inv[cc];
+      }
+      double* out = p.L + (size_t)p.off_blk[c.o0 + sl - 1] * NB + 7 * r;
+      for (int cc = 0; cc < 7; ++cc) out[cc] = x[cc];
+    }
+  }
+}
+
+// One column per CTA: the staged schedule, else factor_column.
+__global__ void __launch_bounds__(32 * FWARPS) k_pg_factor(PgDev p, int lstart) {
+  __shared__ double CB[CB_MAX * NB], fpart[FS_MAX * 7], inv[7], y[7];
+  const ColMeta c = load_meta(p.col_meta, lstart + blockIdx.x);
+  if (c.mask_fast & 1) factor_staged(c, threadIdx.x, CB, fpart, inv, y, p);
+  else factor_column<FWARPS>(c.k, threadIdx.x, CB, inv, y, p);
+}
+
+constexpr int BS_MAX = 64;  // staged back-substitution terms of a column (x 7 rows)
+
+// Column c by one warp: x_k = Lkk^-T (y_k - sum_i L_ik^T x_i).  The terms
+// L_ik^T x_i (one row of one block per lane) are formed in parallel while the
+// diagonal block is staged; a column with more than BS_MAX blocks below the
+// diagonal takes backsolve_column.
+__device__ void backsolve_staged(const ColMeta& c, int lane, double* D, double* part, double* id,
+                                 double* x, const PgDev& p) {
+  const int k = c.k, nblk = c.o1 - c.o0;
+  if (nblk > BS_MAX) {
+    backsolve_column(k, lane, x, p);
+    return;
+  }
+  for (int it = lane; it < nblk * 7; it += 32) {
+    const int q = c.o0 + it / 7, r = it % 7;
+    const double* Lik = p.L + (size_t)p.off_blk[q] * NB + r;
+    const double* xi = p.b + 7 * p.off_row[q];
+    double s0 = ldc(Lik) * ldc(xi), s1 = ldc(Lik + 7) * ldc(xi + 1);
+    double s2 = ldc(Lik + 14) * ldc(xi + 2);
+    s0 = fma(ldc(Lik + 21), ldc(xi + 3), s0);
+    s1 = fma(ldc(Lik + 28), ldc(xi + 4), s1);
+    s2 = fma(ldc(Lik + 35), ldc(xi + 5), s2);
+    s0 = fma(ldc(Lik + 42), ldc(xi + 6), s0);
+    part[it] = (s0 + s1) + s2;
+  }
+  for (int idx = lane; idx < NB; idx += 32) D[idx] = ldc(p.L + (size_t)k * NB + idx);
+  if (lane < 7) {
+    id[lane] = ldc(p.idiag + 7 * k + lane);
+    x[lane] = ldc(p.b + 7 * k + lane);
+  }
+  __syncwarp();
+  if (lane < 7) {
+    double s = x[lane];
+    for (int q = 0; q < nblk; ++q) s -= part[7 * q + lane];
+    x[lane] = s;
+  }
+  __syncwarp();
+  if (lane == 0) upper_solve7(x, D, id);
+  __syncwarp();
+  if (lane < 7) p.b[7 * k + lane] = x[lane];
+  __syncwarp();
+}
+
+struct WarpSolve {
+  double D[NB], part[BS_MAX * 7], id[7], x[7];
+};
+
+// One column per warp (one warp per CTA).
+__global__ void __launch_bounds__(32) k_pg_backsolve(PgDev p, int lstart) {
+  __shared__ WarpSolve w;
+  backsolve_staged(load_meta(p.col_meta, lstart + blockIdx.x), threadIdx.x, w.D, w.part, w.id,
+                   w.x, p);
 }
 
 __global__ void k_pg_update(PgDev p) {
@@ -716,6 +884,7 @@ struct Plan : Extension {
   int ordering = 0;              // 0 nested dissection, 1 minimum degree
   int *d_row_ptr = nullptr, *d_row = nullptr;
   int *d_level_cols = nullptr, *d_level_ptr = nullptr, *d_asm_ptr = nullptr, *d_asm = nullptr;
+  int *d_col_meta = nullptr, *d_grp_slot = nullptr;
   int nlev = 0;
   int *d_g_ptr = nullptr, *d_g = nullptr;
   int *d_parent = nullptr, *d_tedge = nullptr, *d_tdir = nullptr;
@@ -949,7 +1118,7 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   // update groups: for every block (i, k) of column k, the products
   // L_ij L_kj^T of its descendants j, in descendant order (for supernode
   // columns only the descendants below the supernode, gathered in sn_grp)
-  std::vector<int> grp_ptr(nf + 1, 0), grp, upd_ab, row_ptr(nf + 1, 0), row, sn_grp;
+  std::vector<int> grp_ptr(nf + 1, 0), grp, upd_ab, row_ptr(nf + 1, 0), row, sn_grp, grp_slot;
   for (int k = 0; k < nf; ++k) {
     grp_ptr[k] = (int)grp.size() / 3;
     row_ptr[k] = (int)row.size() / 2;
@@ -958,7 +1127,8 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
     targets.push_back(k);
     for (int r : st[k]) targets.push_back(r);
     const bool in_sn = k >= P.sn0;
-    for (int i : targets) {
+    for (size_t ti = 0; ti < targets.size(); ++ti) {
+      const int i = targets[ti];
       const int first = (int)upd_ab.size() / 2;
       for (int j : rowstruct[k]) {
         if (in_sn && j >= P.sn0) continue;  // supernode columns update right-looking
@@ -972,6 +1142,7 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
         G.push_back(blk(i, k));
         G.push_back(first);
         G.push_back(n_upd);
+        if (!in_sn) grp_slot.push_back((int)ti);  // 0: diagonal, t: t-th block below it
       }
     }
     for (int j : rowstruct[k]) {
@@ -994,6 +1165,26 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   for (int l = 0; l < nlev; ++l) P.level_ptr[l + 1] += P.level_ptr[l];
   std::vector<int> level_cols(std::max(nsp, 1)), fill = P.level_ptr;
   for (int k = 0; k < nsp; ++k) level_cols[fill[level[k]]++] = k;
+  // per column in level order: ColMeta (k, groups, blocks below the diagonal,
+  // forward-substitution terms, slots filled by groups << 1 | staged)
+  std::vector<int> col_meta(8 * (size_t)std::max(nsp, 1), 0);
+  for (int pos = 0; pos < nsp; ++pos) {
+    const int k = level_cols[pos];
+    int* cm = &col_meta[8 * (size_t)pos];
+    cm[0] = k;
+    cm[1] = grp_ptr[k];
+    cm[2] = grp_ptr[k + 1];
+    cm[3] = col_ptr[k];
+    cm[4] = col_ptr[k + 1];
+    cm[5] = row_ptr[k];
+    cm[6] = row_ptr[k + 1];
+    const bool fits = 1 + (col_ptr[k + 1] - col_ptr[k]) <= CB_MAX &&
+                      row_ptr[k + 1] - row_ptr[k] <= FS_MAX;
+    unsigned mask = 0;
+    if (fits)
+      for (int g = grp_ptr[k]; g < grp_ptr[k + 1]; ++g) mask |= 1u << grp_slot[g];
+    cm[7] = fits ? (int)(mask << 1 | 1u) : 0;
+  }
   P.n_sn_groups = (int)sn_grp.size() / 3;
   P.nlev = nlev;
   // assembly lists: kind 0 = Cii, 1 = Cjj, 2 = Cij, 3 = Cij^T
@@ -1080,6 +1271,8 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   chk(upload(P, &P.d_row_ptr, row_ptr));
   chk(upload(P, &P.d_row, row));
   chk(upload(P, &P.d_level_cols, level_cols));
+  chk(upload(P, &P.d_col_meta, col_meta));
+  chk(upload(P, &P.d_grp_slot, grp_slot));
   chk(upload(P, &P.d_level_ptr, P.level_ptr));
   chk(upload(P, &P.d_asm_ptr, asm_ptr));
   chk(upload(P, &P.d_asm, asm_it));
@@ -1240,6 +1433,8 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
   dv.row = P->d_row;
   dv.level_ptr = P->d_level_ptr;
   dv.level_cols = P->d_level_cols;
+  dv.col_meta = reinterpret_cast<const int4*>(P->d_col_meta);
+  dv.grp_slot = P->d_grp_slot;
   dv.asm_ptr = P->d_asm_ptr;
   dv.asm_it = P->d_asm;
   dv.g_ptr = P->d_g_ptr;
@@ -1293,7 +1488,8 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
       if (P->nf == 0) continue;
       for (int l = 0; l < nlev; ++l)
         traced(ctx, cs, "pg_factor", [&] {
-          k_pg_factor<<<P->level_ptr[l + 1] - P->level_ptr[l], 32 * FWARPS, 0, cs>>>(dv, l);
+          k_pg_factor<<<P->level_ptr[l + 1] - P->level_ptr[l], 32 * FWARPS, 0, cs>>>(
+              dv, P->level_ptr[l]);
         });
       if (P->sn0 < P->nf) {
         const int nf = P->nf;
@@ -1322,7 +1518,8 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
       }
       for (int l = nlev - 1; l >= 0; --l)
         traced(ctx, cs, "pg_backsolve", [&] {
-          k_pg_backsolve<<<P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs>>>(dv, l);
+          k_pg_backsolve<<<P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs>>>(
+              dv, P->level_ptr[l]);
         });
       if (lm)
         traced(ctx, cs, "pg_lm", [&] {
