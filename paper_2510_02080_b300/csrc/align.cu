@@ -216,11 +216,7 @@ __global__ void __launch_bounds__(256) k_solve(int n_pairs, const int32_t* __res
     return;
   }
   const int64_t t0 = (int64_t)link_off[warp] * tpl, t1 = (int64_t)link_off[warp + 1] * tpl;
-  if (lane < NMOM) {
-    double s = 0.0;
-    for (int64_t t = t0; t < t1; ++t) s += partials[t * NMOM + lane];
-    mom[wib][lane] = s;
-  }
+  if (lane < NMOM) mom[wib][lane] = tile_sum<NMOM>(partials, t0, t1, lane);
   __syncwarp();
   if (lane != 0) return;
   const double* M = mom[wib];

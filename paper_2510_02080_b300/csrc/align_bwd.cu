@@ -261,11 +261,7 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
   const double* ck = ckpt + ((size_t)warp * iters + (j - 1)) * CKPT;
   if (have_partials) {
     const int64_t t0 = (int64_t)link_off[warp] * tpl, t1 = (int64_t)link_off[warp + 1] * tpl;
-    if (lane < NRED) {
-      double s = 0.0;
-      for (int64_t t = t0; t < t1; ++t) s += partials[t * NRED + lane];
-      red[wib][lane] = s;
-    }
+    if (lane < NRED) red[wib][lane] = tile_sum<NRED>(partials, t0, t1, lane);
   }
   __syncwarp();
   if (lane != 0) return;

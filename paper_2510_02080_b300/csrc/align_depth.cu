@@ -362,12 +362,8 @@ __global__ void __launch_bounds__(256) k_solve_depth(
   double acc = 0.0;  // lane m < NMOM: pair moment m
   for (int l = l0; l < l1; ++l) {
     if (!ls[l].ok) continue;  // no valid pixel (and possibly a non-finite camera)
-    if (lane < NMOM) {
-      double s = 0.0;
-      for (int64_t t = (int64_t)l * tpl; t < (int64_t)(l + 1) * tpl; ++t)
-        s += partials[t * NMOM + lane];
-      lm[wib][lane] = s;
-    }
+    if (lane < NMOM)
+      lm[wib][lane] = tile_sum<NMOM>(partials, (int64_t)l * tpl, (int64_t)(l + 1) * tpl, lane);
     if (lane < 9) {
       rot[wib][lane] = (double)cams[src[l]].R[lane];
       rot[wib][9 + lane] = (double)cams[tgt[l]].R[lane];

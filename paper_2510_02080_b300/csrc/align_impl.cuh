@@ -268,6 +268,26 @@ struct PointOp {
   }
 };
 
+// FP64 sum of partials[t * NV + v] over the tiles t in [t0, t1) for one v:
+// four accumulators over consecutive tiles, so that eight loads are in flight
+// at once instead of one dependent load per tile; fixed order (it depends
+// only on the tile count).
+template <int NV>
+__device__ __forceinline__ double tile_sum(const double* __restrict__ partials, int64_t t0,
+                                           int64_t t1, int v) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t t = t0;
+#pragma unroll 2
+  for (; t + 4 <= t1; t += 4) {
+    s0 += partials[t * NV + v];
+    s1 += partials[(t + 1) * NV + v];
+    s2 += partials[(t + 2) * NV + v];
+    s3 += partials[(t + 3) * NV + v];
+  }
+  for (; t < t1; ++t) s0 += partials[t * NV + v];
+  return (s0 + s1) + (s2 + s3);
+}
+
 // --------------------------------------------------------------------------
 // per-pair solve from the 19 moments (shared by the pointmap and depth paths)
 // --------------------------------------------------------------------------

@@ -792,6 +792,127 @@ __global__ void __launch_bounds__(32) k_pg_sn_update(int k, const int* __restric
   }
 }
 
+// Right-hand side of the supernode's forward substitution: b_k -= sum_j
+// L_kj y_j over the sparse columns j < sn0 (final once the levels are done),
+// one warp per supernode column k (lanes over terms, fixed shuffle tree).
+__global__ void __launch_bounds__(32) k_pg_sn_rhs(int sn0, const int* __restrict__ row_ptr,
+                                                  const int* __restrict__ row_it,
+                                                  const double* __restrict__ L, double* bvec) {
+  const int k = sn0 + blockIdx.x, lane = threadIdx.x;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int p = row_ptr[k] + lane; p < row_ptr[k + 1]; p += 32) {
+    const int j = row_it[2 * p];
+    if (j >= sn0) continue;  // supernode columns: right-looking in k_pg_sn_dense_forward
+    const double* Lkj = L + (size_t)row_it[2 * p + 1] * NB;
+    const double* yj = bvec + 7 * j;
+    double yv[7];
+    for (int t = 0; t < 7; ++t) yv[t] = ldc(yj + t);
+    for (int r = 0; r < 7; ++r)
+      for (int t = 0; t < 7; ++t) acc[r] = fma(ldc(Lkj + 7 * r + t), yv[t], acc[r]);
+  }
+  for (int r = 0; r < 7; ++r)
+    for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  if (lane < 7) {
+    double a = acc[0];
+    for (int r = 1; r < 7; ++r) a = lane == r ? acc[r] : a;
+    bvec[7 * k + lane] -= a;
+  }
+}
+
+constexpr int SN_THREADS = 512;
+
+// Dense forward and back substitution over the supernode (one CTA,
+// right-looking, the supernode's right-hand side in shared memory):
+//   forward, k ascending:  y_k = Lkk^-1 b_k, then b_i -= L_ik y_k for i > k;
+//   backward, k descending: x_k = Lkk^-T y_k, then y_i -= L_ki^T x_k for i < k.
+// One thread per row of each update; the next diagonal block is staged while
+// the current update runs.
+__device__ __forceinline__ void sn_stage_diag(int kk, const double* L, const double* idiag,
+                                              double* D, double* inv, int tid) {
+  if (tid < NB) D[tid] = ldc(L + (size_t)kk * NB + tid);
+  else if (tid < NB + 7) inv[tid - NB] = ldc(idiag + 7 * kk + tid - NB);
+}
+
+__global__ void __launch_bounds__(SN_THREADS) k_pg_sn_dense_solve(int sn0, int nf,
+                                                                 const int* __restrict__ col_ptr,
+                                                                 const int* __restrict__ off_blk,
+                                                                 const double* __restrict__ L,
+                                                                 const double* __restrict__ idiag,
+                                                                 double* bvec) {
+  extern __shared__ double sn_b[];  // [ns * 7]
+  __shared__ double D[2][NB], inv[2][7], v[7];
+  const int ns = nf - sn0, tid = threadIdx.x;
+  for (int i = tid; i < ns * 7; i += SN_THREADS) sn_b[i] = ldc(bvec + 7 * sn0 + i);
+  sn_stage_diag(sn0, L, idiag, D[0], inv[0], tid);
+  __syncthreads();
+  // forward
+  for (int k = 0; k < ns; ++k) {
+    const int cur = k & 1;
+    if (tid == 0) {
+      double y[7];
+#pragma unroll
+      for (int c = 0; c < 7; ++c) {
+        double a = sn_b[7 * k + c];
+#pragma unroll
+        for (int t = 0; t < c; ++t) a -= D[cur][7 * c + t] * y[t];
+        y[c] = a * inv[cur][c];
+      }
+#pragma unroll
+      for (int c = 0; c < 7; ++c) v[c] = sn_b[7 * k + c] = y[c];
+    } else if (tid >= 32 && k + 1 < ns) {
+      sn_stage_diag(sn0 + k + 1, L, idiag, D[cur ^ 1], inv[cur ^ 1], tid - 32);
+    }
+    __syncthreads();
+    const int kk = sn0 + k;
+    for (int it = tid; it < (ns - 1 - k) * 7; it += SN_THREADS) {
+      const int i = k + 1 + it / 7, r = it % 7;
+      const double* Lik = L + (size_t)off_blk[col_ptr[kk] + (i - k - 1)] * NB + 7 * r;
+      double s0 = ldc(Lik) * v[0], s1 = ldc(Lik + 1) * v[1], s2 = ldc(Lik + 2) * v[2];
+      s0 = fma(ldc(Lik + 3), v[3], s0);
+      s1 = fma(ldc(Lik + 4), v[4], s1);
+      s2 = fma(ldc(Lik + 5), v[5], s2);
+      s0 = fma(ldc(Lik + 6), v[6], s0);
+      sn_b[7 * i + r] -= (s0 + s1) + s2;
+    }
+    __syncthreads();
+  }
+  // backward (the last diagonal block is staged: ns - 1 has parity (ns - 1) & 1)
+  for (int k = ns - 1; k >= 0; --k) {
+    const int cur = k & 1;
+    if (tid == 0) {
+      double x[7];
+#pragma unroll
+      for (int c = 6; c >= 0; --c) {
+        double a = sn_b[7 * k + c];
+#pragma unroll
+        for (int t = 6; t > c; --t) a -= D[cur][7 * t + c] * x[t];
+        x[c] = a * inv[cur][c];
+      }
+#pragma unroll
+      for (int c = 0; c < 7; ++c) v[c] = sn_b[7 * k + c] = x[c];
+    } else if (tid >= 32 && k > 0) {
+      sn_stage_diag(sn0 + k - 1, L, idiag, D[cur ^ 1], inv[cur ^ 1], tid - 32);
+    }
+    __syncthreads();
+    for (int it = tid; it < k * 7; it += SN_THREADS) {
+      const int i = it / 7, r = it % 7;  // block (k, i) of column i, its column r
+      const double* Lki = L + (size_t)off_blk[col_ptr[sn0 + i] + (k - i - 1)] * NB + r;
+      double s0 = ldc(Lki) * v[0], s1 = ldc(Lki + 7) * v[1], s2 = ldc(Lki + 14) * v[2];
+      s0 = fma(ldc(Lki + 21), v[3], s0);
+      s1 = fma(ldc(Lki + 28), v[4], s1);
+      s2 = fma(ldc(Lki + 35), v[5], s2);
+      s0 = fma(ldc(Lki + 42), v[6], s0);
+      sn_b[7 * i + r] -= (s0 + s1) + s2;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < ns * 7; i += SN_THREADS) bvec[7 * sn0 + i] = sn_b[i];
+}
+
+// Supernodes whose right-hand side does not fit in shared memory take the two
+// kernels below.
+constexpr int SN_DENSE_MAX = 3200;  // 3200 x 7 doubles = 175 KB
+
 // Forward substitution over the supernode columns (one CTA, in column order):
 // y_k = Lkk^-1 (b_k - sum_j L_kj y_j) over every earlier column j.
 __global__ void __launch_bounds__(256) k_pg_sn_forward(int sn0, int nf,
@@ -1458,6 +1579,13 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
       key_of("pg", {(uint64_t)P, (uint64_t)d_nodes, (uint64_t)d_Tij, (uint64_t)d_info,
                     (uint64_t)d_chi2, (uint64_t)o.iters, dbits(o.lm_lambda),
                     (uint64_t)o.init_by_chaining, (uint64_t)o.lm_adaptive});
+  static bool attr_set[64] = {};
+  if (ctx->device < 64 && !attr_set[ctx->device]) {
+    EC3R_CUDA_TRY(ctx, cudaFuncSetAttribute(k_pg_sn_dense_solve,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sizeof(double) * 7 * SN_DENSE_MAX)));
+    attr_set[ctx->device] = true;
+  }
   return run_graph(ctx, gkey, s, [&](cudaStream_t cs) -> ec3r_status {
     if (o.init_by_chaining)
       traced(ctx, cs, "pg_init", [&] {
@@ -1510,10 +1638,17 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
             });
         }
         traced(ctx, cs, "pg_sn_solve", [&] {
-          k_pg_sn_forward<<<1, 256, 0, cs>>>(P->sn0, nf, P->d_row_ptr, P->d_row, P->d_L,
-                                             P->d_idiag, P->d_b);
-          k_pg_sn_backward<<<1, 256, 0, cs>>>(P->sn0, nf, P->d_col_ptr, P->d_off_blk, P->d_L,
-                                              P->d_idiag, P->d_b);
+          const int ns = nf - P->sn0;
+          if (ns <= SN_DENSE_MAX) {
+            k_pg_sn_rhs<<<ns, 32, 0, cs>>>(P->sn0, P->d_row_ptr, P->d_row, P->d_L, P->d_b);
+            k_pg_sn_dense_solve<<<1, SN_THREADS, sizeof(double) * 7 * ns, cs>>>(
+                P->sn0, nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, P->d_b);
+          } else {
+            k_pg_sn_forward<<<1, 256, 0, cs>>>(P->sn0, nf, P->d_row_ptr, P->d_row, P->d_L,
+                                               P->d_idiag, P->d_b);
+            k_pg_sn_backward<<<1, 256, 0, cs>>>(P->sn0, nf, P->d_col_ptr, P->d_off_blk, P->d_L,
+                                                P->d_idiag, P->d_b);
+          }
         });
       }
       for (int l = nlev - 1; l >= 0; --l)
