@@ -714,17 +714,18 @@ __device__ __forceinline__ int sn_block(const int* col_ptr, const int* off_blk, 
   return i == j ? j : off_blk[col_ptr[j] + (i - j - 1)];
 }
 
-// Panel k of the supernode: 7x7 Cholesky of the diagonal block, then the
-// triangular solve of every block below it (one block row per thread).
-__global__ void __launch_bounds__(256) k_pg_sn_panel(int k, int nf, const int* __restrict__ col_ptr,
-                                                     const int* __restrict__ off_blk, double* L,
-                                                     double* idiag, unsigned* flags, int* fail) {
-  __shared__ double D[NB];
-  __shared__ double inv[7];
+// Panel work of supernode column k by a CTA of SN_UPD_THREADS threads: 7x7
+// Cholesky of the diagonal block (warp 0), then the triangular solve of every
+// block below it (one block row per thread).  The column was written by other
+// CTAs of the same launch: its loads bypass L1.
+constexpr int SN_UPD_THREADS = 256;
+__device__ void sn_panel_cta(int k, int nf, const int* __restrict__ col_ptr,
+                             const int* __restrict__ off_blk, double* L, double* idiag,
+                             unsigned* flags, int* fail, double* D, double* inv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* Lkk = L + (size_t)k * NB;
   if (warp == 0) {
-    for (int idx = lane; idx < NB; idx += 32) D[idx] = Lkk[idx];
+    for (int idx = lane; idx < NB; idx += 32) D[idx] = __ldcg(Lkk + idx);
     __syncwarp();
     bool bad = false;
     for (int c = 0; c < 7; ++c) {
@@ -753,43 +754,78 @@ __global__ void __launch_bounds__(256) k_pg_sn_panel(int k, int nf, const int* _
   }
   __syncthreads();
   const int nrows = (nf - 1 - k) * 7;
-  for (int q = threadIdx.x; q < nrows; q += blockDim.x) {
+  for (int q = threadIdx.x; q < nrows; q += SN_UPD_THREADS) {
     double* X = L + (size_t)off_blk[col_ptr[k] + q / 7] * NB + 7 * (q % 7);
     double x[7];
+#pragma unroll
     for (int c = 0; c < 7; ++c) {
-      double s = X[c];
-      for (int t = 0; t < c; ++t) s -= x[t] * D[7 * c + t];
-      x[c] = s * inv[c];
+      double v = __ldcg(X + c);
+#pragma unroll
+      for (int t = 0; t < c; ++t) v -= x[t] * D[7 * c + t];
+      x[c] = v * inv[c];
     }
+#pragma unroll
     for (int c = 0; c < 7; ++c) X[c] = x[c];
   }
 }
 
-// Trailing update after panel k: L_ij -= L_ik L_jk^T for k < j <= i < nf, one
-// warp per block (triangular index).
-__global__ void __launch_bounds__(32) k_pg_sn_update(int k, const int* __restrict__ col_ptr,
-                                                     const int* __restrict__ off_blk, double* L) {
-  const int64_t t = blockIdx.x;
-  int ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while ((int64_t)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
-  while ((int64_t)ii * (ii + 1) / 2 > t) --ii;
-  const int jj = (int)(t - (int64_t)ii * (ii + 1) / 2);
-  const int i = k + 1 + ii, j = k + 1 + jj;
-  double* Dst = L + (size_t)sn_block(col_ptr, off_blk, i, j) * NB;
-  const double* A = L + (size_t)off_blk[col_ptr[k] + (i - k - 1)] * NB;
-  const double* B = L + (size_t)off_blk[col_ptr[k] + (j - k - 1)] * NB;
-  for (int idx = threadIdx.x; idx < NB; idx += 32) {
-    const int r = idx / 7, c = idx % 7;
-    double s0 = 0.0, s1 = 0.0;
-    s0 = fma(A[7 * r + 0], B[7 * c + 0], s0);
-    s1 = fma(A[7 * r + 1], B[7 * c + 1], s1);
-    s0 = fma(A[7 * r + 2], B[7 * c + 2], s0);
-    s1 = fma(A[7 * r + 3], B[7 * c + 3], s1);
-    s0 = fma(A[7 * r + 4], B[7 * c + 4], s0);
-    s1 = fma(A[7 * r + 5], B[7 * c + 5], s1);
-    s0 = fma(A[7 * r + 6], B[7 * c + 6], s0);
-    Dst[idx] -= s0 + s1;
+// First panel of the supernode.
+__global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_panel_first(
+    int k, int nf, const int* __restrict__ col_ptr, const int* __restrict__ off_blk, double* L,
+    double* idiag, unsigned* flags, int* fail) {
+  __shared__ double D[NB], inv[7];
+  sn_panel_cta(k, nf, col_ptr, off_blk, L, idiag, flags, fail, D, inv);
+}
+
+// Trailing update after panel k, L_ij -= L_ik L_jk^T for k < j <= i < nf (one
+// warp per block, blocks in triangular order), fused with panel k + 1: every
+// CTA adds the number of its blocks in column k + 1 to cnt[k] after a fence;
+// the CTA that completes the count (all of column k + 1 updated) factors
+// column k + 1.  No CTA waits on another.
+__global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_update_panel(
+    int k, int nf, const int* __restrict__ col_ptr, const int* __restrict__ off_blk, double* L,
+    double* idiag, unsigned* flags, int* fail, int* cnt) {
+  __shared__ double D[NB], inv[7];
+  __shared__ int mine, last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mrem = nf - 1 - k;
+  const int64_t nblk = (int64_t)mrem * (mrem + 1) / 2;
+  const int64_t t = (int64_t)blockIdx.x * (SN_UPD_THREADS / 32) + warp;
+  if (threadIdx.x == 0) mine = 0;
+  __syncthreads();
+  if (t < nblk) {
+    int ii = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while ((int64_t)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
+    while ((int64_t)ii * (ii + 1) / 2 > t) --ii;
+    const int jj = (int)(t - (int64_t)ii * (ii + 1) / 2);
+    const int i = k + 1 + ii, j = k + 1 + jj;
+    double* Dst = L + (size_t)sn_block(col_ptr, off_blk, i, j) * NB;
+    const double* A = L + (size_t)off_blk[col_ptr[k] + (i - k - 1)] * NB;
+    const double* B = L + (size_t)off_blk[col_ptr[k] + (j - k - 1)] * NB;
+    for (int idx = lane; idx < NB; idx += 32) {
+      const int r = idx / 7, c = idx % 7;
+      double s0 = 0.0, s1 = 0.0;
+      s0 = fma(ldc(A + 7 * r + 0), ldc(B + 7 * c + 0), s0);
+      s1 = fma(ldc(A + 7 * r + 1), ldc(B + 7 * c + 1), s1);
+      s0 = fma(ldc(A + 7 * r + 2), ldc(B + 7 * c + 2), s0);
+      s1 = fma(ldc(A + 7 * r + 3), ldc(B + 7 * c + 3), s1);
+      s0 = fma(ldc(A + 7 * r + 4), ldc(B + 7 * c + 4), s0);
+      s1 = fma(ldc(A + 7 * r + 5), ldc(B + 7 * c + 5), s1);
+      s0 = fma(ldc(A + 7 * r + 6), ldc(B + 7 * c + 6), s0);
+      Dst[idx] = ldc(Dst + idx) - (s0 + s1);
+    }
+    if (jj == 0 && lane == 0) atomicAdd(&mine, 1);
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    last = 0;
+    if (mine > 0) last = atomicAdd(cnt + k, mine) + mine == mrem;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  sn_panel_cta(k + 1, nf, col_ptr, off_blk, L, idiag, flags, fail, D, inv);
 }
 
 // Right-hand side of the supernode's forward substitution: b_k -= sum_j
@@ -1006,6 +1042,7 @@ struct Plan : Extension {
   int *d_row_ptr = nullptr, *d_row = nullptr;
   int *d_level_cols = nullptr, *d_level_ptr = nullptr, *d_asm_ptr = nullptr, *d_asm = nullptr;
   int *d_col_meta = nullptr, *d_grp_slot = nullptr;
+  int* d_sn_cnt = nullptr;  // per supernode column: its blocks updated so far
   int nlev = 0;
   int *d_g_ptr = nullptr, *d_g = nullptr;
   int *d_parent = nullptr, *d_tedge = nullptr, *d_tdir = nullptr;
@@ -1394,6 +1431,7 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   chk(upload(P, &P.d_level_cols, level_cols));
   chk(upload(P, &P.d_col_meta, col_meta));
   chk(upload(P, &P.d_grp_slot, grp_slot));
+  chk(alloc(P, &P.d_sn_cnt, (size_t)nf));
   chk(upload(P, &P.d_level_ptr, P.level_ptr));
   chk(upload(P, &P.d_asm_ptr, asm_ptr));
   chk(upload(P, &P.d_asm, asm_it));
@@ -1625,17 +1663,22 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
           traced(ctx, cs, "pg_sn_assemble", [&] {
             k_pg_sn_assemble<<<P->n_sn_groups, 32, 0, cs>>>(P->d_sn_grp, P->d_upd_ab, P->d_L);
           });
-        for (int k = P->sn0; k < nf; ++k) {
-          traced(ctx, cs, "pg_sn_panel", [&] {
-            k_pg_sn_panel<<<1, 256, 0, cs>>>(k, nf, P->d_col_ptr, P->d_off_blk, P->d_L,
-                                             P->d_idiag, dv.flags, P->d_fail);
-          });
+        // panel sn0, then per column k one launch: its trailing update and,
+        // in the CTA that completes column k + 1, panel k + 1
+        EC3R_CUDA_TRY(ctx, cudaMemsetAsync(P->d_sn_cnt, 0, sizeof(int) * (size_t)nf, cs));
+        traced(ctx, cs, "pg_sn_panel", [&] {
+          k_pg_sn_panel_first<<<1, SN_UPD_THREADS, 0, cs>>>(
+              P->sn0, nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, dv.flags, P->d_fail);
+        });
+        for (int k = P->sn0; k + 1 < nf; ++k) {
           const int64_t mrem = nf - 1 - k;
-          if (mrem > 0)
-            traced(ctx, cs, "pg_sn_update", [&] {
-              k_pg_sn_update<<<(unsigned)(mrem * (mrem + 1) / 2), 32, 0, cs>>>(
-                  k, P->d_col_ptr, P->d_off_blk, P->d_L);
-            });
+          const int64_t blocks = (mrem * (mrem + 1) / 2 + SN_UPD_THREADS / 32 - 1) /
+                                 (SN_UPD_THREADS / 32);
+          traced(ctx, cs, "pg_sn_update", [&] {
+            k_pg_sn_update_panel<<<(unsigned)blocks, SN_UPD_THREADS, 0, cs>>>(
+                k, nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, dv.flags, P->d_fail,
+                P->d_sn_cnt);
+          });
         }
         traced(ctx, cs, "pg_sn_solve", [&] {
           const int ns = nf - P->sn0;
