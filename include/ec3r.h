@@ -300,7 +300,8 @@ void ec3r_pg_opts_default(ec3r_pg_opts* o);
  * cheaper; block fill of the Cholesky factor) and cached
  * in the context; a call with a new structure allocates and must not be made
  * during stream capture (EC3R_ERR_CAPTURE).  The first pose-graph call of a
- * context also uploads a constant table.
+ * context also uploads a constant table.  A structure whose factor ends in a
+ * dense block of more than 3200 nodes is rejected (EC3R_ERR_INVALID_ARG).
  *
  * Data.  d_Tij (ec3r_sim3 [n_edges], device) are the measured T_ij; d_info
  * (float64 [n_edges][49], row-major symmetric Omega, device) or NULL for the

@@ -945,87 +945,9 @@ __global__ void __launch_bounds__(SN_THREADS) k_pg_sn_dense_solve(int sn0, int n
   for (int i = tid; i < ns * 7; i += SN_THREADS) bvec[7 * sn0 + i] = sn_b[i];
 }
 
-// Supernodes whose right-hand side does not fit in shared memory take the two
-// kernels below.
+// Largest supernode: its right-hand side (7 doubles per column) stays in
+// shared memory during the substitution.
 constexpr int SN_DENSE_MAX = 3200;  // 3200 x 7 doubles = 175 KB
-
-// Forward substitution over the supernode columns (one CTA, in column order):
-// y_k = Lkk^-1 (b_k - sum_j L_kj y_j) over every earlier column j.
-__global__ void __launch_bounds__(256) k_pg_sn_forward(int sn0, int nf,
-                                                       const int* __restrict__ row_ptr,
-                                                       const int* __restrict__ row_it,
-                                                       const double* __restrict__ L,
-                                                       const double* __restrict__ idiag,
-                                                       double* bvec) {
-  __shared__ double red[8][7];
-  __shared__ double y[7];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = sn0; k < nf; ++k) {
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int p = row_ptr[k] + threadIdx.x; p < row_ptr[k + 1]; p += blockDim.x) {
-      const int j = row_it[2 * p];
-      const double* Lkj = L + (size_t)row_it[2 * p + 1] * NB;
-      const double* yj = bvec + 7 * j;
-      for (int r = 0; r < 7; ++r)
-        for (int t = 0; t < 7; ++t) acc[r] = fma(Lkj[7 * r + t], yj[t], acc[r]);
-    }
-    for (int r = 0; r < 7; ++r)
-      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-    if (lane == 0)
-      for (int r = 0; r < 7; ++r) red[warp][r] = acc[r];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const double* D = L + (size_t)k * NB;
-      for (int c = 0; c < 7; ++c) {
-        double s = bvec[7 * k + c];
-        for (int w = 0; w < 8; ++w) s -= red[w][c];
-        for (int t = 0; t < c; ++t) s -= D[7 * c + t] * y[t];
-        y[c] = s * idiag[7 * k + c];
-      }
-      for (int c = 0; c < 7; ++c) bvec[7 * k + c] = y[c];
-    }
-    __syncthreads();
-  }
-}
-
-// Back substitution over the supernode (one CTA, last column first):
-// x_k = Lkk^-T (y_k - sum_{i > k} L_ik^T x_i).
-__global__ void __launch_bounds__(256) k_pg_sn_backward(int sn0, int nf,
-                                                        const int* __restrict__ col_ptr,
-                                                        const int* __restrict__ off_blk,
-                                                        const double* __restrict__ L,
-                                                        const double* __restrict__ idiag,
-                                                        double* bvec) {
-  __shared__ double red[8][7];
-  __shared__ double x[7];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = nf - 1; k >= sn0; --k) {
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int i = k + 1 + threadIdx.x; i < nf; i += blockDim.x) {
-      const double* Lik = L + (size_t)off_blk[col_ptr[k] + (i - k - 1)] * NB;
-      const double* xi = bvec + 7 * i;
-      for (int r = 0; r < 7; ++r)
-        for (int t = 0; t < 7; ++t) acc[r] = fma(Lik[7 * t + r], xi[t], acc[r]);
-    }
-    for (int r = 0; r < 7; ++r)
-      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-    if (lane == 0)
-      for (int r = 0; r < 7; ++r) red[warp][r] = acc[r];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const double* D = L + (size_t)k * NB;
-      for (int c = 6; c >= 0; --c) {
-        double s = bvec[7 * k + c];
-        for (int w = 0; w < 8; ++w) s -= red[w][c];
-        for (int t = c + 1; t < 7; ++t) s -= D[7 * t + c] * x[t];
-        x[c] = s * idiag[7 * k + c];
-      }
-      for (int c = 0; c < 7; ++c) bvec[7 * k + c] = x[c];
-    }
-    __syncthreads();
-  }
-}
-
 
 // --------------------------------------------------------------------------
 // host: planning
@@ -1273,6 +1195,10 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   // trailing dense supernode: the longest suffix of columns whose structure is
   // every later column; it is factored right-looking across all SMs
   P.sn0 = S.sn0;
+  if (nf - P.sn0 > SN_DENSE_MAX)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG,
+                     "the factor's dense trailing block has %d nodes (at most %d)", nf - P.sn0,
+                     SN_DENSE_MAX);
   // update groups: for every block (i, k) of column k, the products
   // L_ij L_kj^T of its descendants j, in descendant order (for supernode
   // columns only the descendants below the supernode, gathered in sn_grp)
@@ -1682,16 +1608,9 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
         }
         traced(ctx, cs, "pg_sn_solve", [&] {
           const int ns = nf - P->sn0;
-          if (ns <= SN_DENSE_MAX) {
-            k_pg_sn_rhs<<<ns, 32, 0, cs>>>(P->sn0, P->d_row_ptr, P->d_row, P->d_L, P->d_b);
-            k_pg_sn_dense_solve<<<1, SN_THREADS, sizeof(double) * 7 * ns, cs>>>(
-                P->sn0, nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, P->d_b);
-          } else {
-            k_pg_sn_forward<<<1, 256, 0, cs>>>(P->sn0, nf, P->d_row_ptr, P->d_row, P->d_L,
-                                               P->d_idiag, P->d_b);
-            k_pg_sn_backward<<<1, 256, 0, cs>>>(P->sn0, nf, P->d_col_ptr, P->d_off_blk, P->d_L,
-                                                P->d_idiag, P->d_b);
-          }
+          k_pg_sn_rhs<<<ns, 32, 0, cs>>>(P->sn0, P->d_row_ptr, P->d_row, P->d_L, P->d_b);
+          k_pg_sn_dense_solve<<<1, SN_THREADS, sizeof(double) * 7 * ns, cs>>>(
+              P->sn0, nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, P->d_b);
         });
       }
       for (int l = nlev - 1; l >= 0; --l)
