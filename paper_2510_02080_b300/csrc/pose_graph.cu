@@ -546,24 +546,27 @@ __global__ void k_pg_decide(PgDev p) {
 }
 
 constexpr int FWARPS = 4;   // warps per column in k_pg_factor
-constexpr int CB_MAX = 31;  // staged blocks of a column: the diagonal + up to 30 below it
+constexpr int CB_MAX = 96;  // staged blocks of a column: the diagonal + up to 95 below it
 constexpr int FS_MAX = 64;  // staged forward-substitution terms of a column
 
 // Per column (in level order), built on the host: the column, its update
 // groups [g0, g1), its off-diagonal blocks [o0, o1), its forward-substitution
-// terms [r0, r1), the slots filled by groups (bit s), and whether the column
-// fits the staged schedule.
+// terms [r0, r1), whether the column fits the staged schedule, and the slots
+// filled by groups (slot s: bit s % 32 of filled[s / 32]).
 struct ColMeta {
-  int k, g0, g1, o0, o1, r0, r1, mask_fast;  // mask_fast: slot mask << 1 | fits
+  int k, g0, g1, o0, o1, r0, r1, fast;
+  unsigned filled[3];
 };
+constexpr int META_INTS = 12;  // three int4 per column
 
 __device__ __forceinline__ ColMeta load_meta(const int4* m, int pos) {
-  const int4 a = m[2 * pos], b = m[2 * pos + 1];
-  return ColMeta{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  const int4 a = m[3 * pos], b = m[3 * pos + 1], c = m[3 * pos + 2];
+  return ColMeta{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w,
+                 {(unsigned)c.x, (unsigned)c.y, (unsigned)c.z}};
 }
 
 // Column c by a CTA of four warps (tid in [0, 128)), staged schedule (a
-// column with at most 30 blocks below the diagonal and 64 forward-substitution
+// column with at most 95 blocks below the diagonal and 64 forward-substitution
 // terms), every dependent step spread over the team:
 //   1. the column's blocks enter shared memory, either as stored or through
 //      their update group (left-looking, group_entry); the products
@@ -576,11 +579,10 @@ __device__ void factor_staged(const ColMeta& c, int tid, double* CB, double* fpa
                               double* y, const PgDev& p) {
   const int lane = tid & 31, warp = tid >> 5;
   const int k = c.k;
-  const unsigned filled = (unsigned)c.mask_fast >> 1;
   const int nblk = c.o1 - c.o0, nrow = c.r1 - c.r0;
   for (int it = tid; it < (1 + nblk) * NB; it += 32 * FWARPS) {
     const int sl = it / NB;
-    if ((filled >> sl) & 1u) continue;
+    if ((c.filled[sl >> 5] >> (sl & 31)) & 1u) continue;
     const int blk = sl == 0 ? k : p.off_blk[c.o0 + sl - 1];
     CB[it] = ldc(p.L + (size_t)blk * NB + it % NB);
   }
@@ -635,7 +637,7 @@ __device__ void factor_staged(const ColMeta& c, int tid, double* CB, double* fpa
 __global__ void __launch_bounds__(32 * FWARPS) k_pg_factor(PgDev p, int lstart) {
   __shared__ double CB[CB_MAX * NB], fpart[FS_MAX * 7], inv[7], y[7];
   const ColMeta c = load_meta(p.col_meta, lstart + blockIdx.x);
-  if (c.mask_fast & 1) factor_staged(c, threadIdx.x, CB, fpart, inv, y, p);
+  if (c.fast) factor_staged(c, threadIdx.x, CB, fpart, inv, y, p);
   else factor_column<FWARPS>(c.k, threadIdx.x, CB, inv, y, p);
 }
 
@@ -1250,11 +1252,11 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   std::vector<int> level_cols(std::max(nsp, 1)), fill = P.level_ptr;
   for (int k = 0; k < nsp; ++k) level_cols[fill[level[k]]++] = k;
   // per column in level order: ColMeta (k, groups, blocks below the diagonal,
-  // forward-substitution terms, slots filled by groups << 1 | staged)
-  std::vector<int> col_meta(8 * (size_t)std::max(nsp, 1), 0);
+  // forward-substitution terms, staged, slots filled by groups)
+  std::vector<int> col_meta(META_INTS * (size_t)std::max(nsp, 1), 0);
   for (int pos = 0; pos < nsp; ++pos) {
     const int k = level_cols[pos];
-    int* cm = &col_meta[8 * (size_t)pos];
+    int* cm = &col_meta[META_INTS * (size_t)pos];
     cm[0] = k;
     cm[1] = grp_ptr[k];
     cm[2] = grp_ptr[k + 1];
@@ -1264,10 +1266,10 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
     cm[6] = row_ptr[k + 1];
     const bool fits = 1 + (col_ptr[k + 1] - col_ptr[k]) <= CB_MAX &&
                       row_ptr[k + 1] - row_ptr[k] <= FS_MAX;
-    unsigned mask = 0;
+    cm[7] = fits ? 1 : 0;
     if (fits)
-      for (int g = grp_ptr[k]; g < grp_ptr[k + 1]; ++g) mask |= 1u << grp_slot[g];
-    cm[7] = fits ? (int)(mask << 1 | 1u) : 0;
+      for (int g = grp_ptr[k]; g < grp_ptr[k + 1]; ++g)
+        cm[8 + grp_slot[g] / 32] |= (int)(1u << (grp_slot[g] % 32));
   }
   P.n_sn_groups = (int)sn_grp.size() / 3;
   P.nlev = nlev;
