@@ -780,10 +780,11 @@ __global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_panel_first(
 }
 
 // Trailing update after panel k, L_ij -= L_ik L_jk^T for k < j <= i < nf (one
-// warp per block, blocks in triangular order), fused with panel k + 1: every
-// CTA adds the number of its blocks in column k + 1 to cnt[k] after a fence;
-// the CTA that completes the count (all of column k + 1 updated) factors
-// column k + 1.  No CTA waits on another.
+// warp per block, blocks numbered column by column so that column k + 1 comes
+// first), fused with panel k + 1: every CTA adds the number of its blocks in
+// column k + 1 to cnt[k] after a fence; the CTA that completes the count (all
+// of column k + 1 updated) factors column k + 1 while the later columns are
+// still being updated.  No CTA waits on another.
 __global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_update_panel(
     int k, int nf, const int* __restrict__ col_ptr, const int* __restrict__ off_blk, double* L,
     double* idiag, unsigned* flags, int* fail, int* cnt) {
@@ -796,10 +797,14 @@ __global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_update_panel(
   if (threadIdx.x == 0) mine = 0;
   __syncthreads();
   if (t < nblk) {
-    int ii = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-    while ((int64_t)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
-    while ((int64_t)ii * (ii + 1) / 2 > t) --ii;
-    const int jj = (int)(t - (int64_t)ii * (ii + 1) / 2);
+    // column jj holds mrem - jj blocks and starts at off(jj) = jj (2 mrem - jj + 1) / 2
+    auto off = [mrem](int64_t c) { return c * (2 * (int64_t)mrem - c + 1) / 2; };
+    const float b2 = 2.f * (float)mrem + 1.f;
+    int jj = (int)((b2 - sqrtf(fmaxf(b2 * b2 - 8.f * (float)t, 0.f))) * 0.5f);
+    jj = min(max(jj, 0), mrem - 1);
+    while (jj + 1 < mrem && off(jj + 1) <= t) ++jj;
+    while (jj > 0 && off(jj) > t) --jj;
+    const int ii = jj + (int)(t - off(jj));
     const int i = k + 1 + ii, j = k + 1 + jj;
     double* Dst = L + (size_t)sn_block(col_ptr, off_blk, i, j) * NB;
     const double* A = L + (size_t)off_blk[col_ptr[k] + (i - k - 1)] * NB;
