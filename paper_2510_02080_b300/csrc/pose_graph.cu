@@ -603,7 +603,7 @@ __device__ void factor_staged(const ColMeta& c, int tid, double* CB, double* fpa
     s0 = fma(ldc(Lkj + 6), ldc(yj + 6), s0);
     fpart[it] = (s0 + s1) + s2;
   }
-  if (tid >= 64 && tid < 71) y[tid - 64] = ldc(p.b + 7 * k + tid - 64);
+  if (tid >= 32 && tid < 39) y[tid - 32] = ldc(p.b + 7 * k + tid - 32);
   __syncthreads();
   if (warp == 0) {
     chol7_core(p.L + (size_t)k * NB, p.idiag + 7 * k, CB, inv, lane, p);
