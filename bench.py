@@ -222,10 +222,11 @@ def run_ours(args):
     gconf = torch.empty((n_frames, hw), dtype=torch.float32, device=dev)
 
     # The adjoint needs only the registration's checkpoints, so the pose graph
-    # and the fusion (which need the registered edges) run on a second,
-    # high-priority stream while the adjoint runs on the main one; the
-    # latency-bound pose-graph launches then fill the gaps of the HBM-bound
-    # adjoint sweeps.  The step ends when both streams are done.
+    # (which needs the registered edges) runs on a second, high-priority
+    # stream while the adjoint runs on the main one; the latency-bound
+    # pose-graph launches then fill the gaps of the HBM-bound adjoint sweeps.
+    # The fusion (HBM-bound, it needs the corrected poses) follows the adjoint
+    # on the main stream once the pose graph is done.
     side = torch.cuda.Stream(device=dev, priority=-1)
     ev_reg, ev_side = torch.cuda.Event(), torch.cuda.Event()
 
@@ -238,10 +239,6 @@ def run_ours(args):
         ev_reg.record(main)
         sec.wait_event(ev_reg)
         ctx.pose_graph_correct(poses, ei, ej, S, iters=PG_ITERS, chi2=chi2, stream=sec)
-        c = cursors[ci[0] % n_cursor:ci[0] % n_cursor + 1]
-        ci[0] += 1
-        ctx.fuse_points(xyz_in.view(M, -1, 3), conf_in.view(M, -1), poses,
-                        out_xyz, out_idx, c, stream=sec)
         ev_side.record(sec)
         if not args.no_adjoint:
             lib = ec3r.lib()
@@ -252,6 +249,10 @@ def run_ours(args):
                 ec3r._ptr(ps.tgt), None, ec3r.C.byref(o), ec3r._ptr(gS), ec3r._ptr(gcost),
                 ec3r._ptr(gxyz), ec3r._ptr(gconf), ec3r._stream(main)))
         main.wait_event(ev_side)
+        c = cursors[ci[0] % n_cursor:ci[0] % n_cursor + 1]
+        ci[0] += 1
+        ctx.fuse_points(xyz_in.view(M, -1, 3), conf_in.view(M, -1), poses,
+                        out_xyz, out_idx, c, stream=main)
 
     for _ in range(args.warmup):
         step(ch.xyz, ch.conf)
