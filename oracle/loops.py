@@ -53,14 +53,41 @@ def coarse_similarity(E, stride):
     return A @ A.T
 
 
+def coarse_similarity_rows(E, stride, rows):
+    """The rows `rows` (sample indices) of coarse_similarity(E, stride), for
+    sizes whose whole matrix is too large to form."""
+    A = bf16_round(normalise32(np.asarray(E)[::stride])).astype(np.float64)
+    return A[np.asarray(rows)] @ A.T
+
+
+def unit_rows(E):
+    """Embeddings normalised in float64 (the neighbourhood similarities)."""
+    En = np.asarray(E, dtype=np.float32).astype(np.float64)
+    return En / np.linalg.norm(En, axis=1, keepdims=True)
+
+
+def best_neighbour(En, ka, kb, radius, gap):
+    """The neighbourhood search of one coarse pair with keyframes ka < kb over
+    unit embeddings En: (best similarity, i, j), ties to the smallest i, then
+    j; (-inf, -1, -1) when no pair of the neighbourhood is `gap` apart."""
+    n = En.shape[0]
+    best = (-np.inf, -1, -1)
+    for i in range(max(ka - radius, 0), min(ka + radius, n - 1) + 1):
+        for j in range(max(kb - radius, 0), min(kb + radius, n - 1) + 1):
+            if j - i < gap:
+                continue
+            s = float(En[i] @ En[j])
+            if s > best[0]:
+                best = (s, i, j)
+    return best
+
+
 def loop_candidates(E, stride, radius, gap, tau_global, tau_local):
     """Returns (coarse pairs [(a, b, s)], loops [(a, b, i, j, s)])."""
     E = np.asarray(E, dtype=np.float32)
-    n = E.shape[0]
     S = coarse_similarity(E, stride)
     m = S.shape[0]
-    En = E.astype(np.float64)
-    En = En / np.linalg.norm(En, axis=1, keepdims=True)
+    En = unit_rows(E)
     coarse, loops = [], []
     for a in range(m):
         for b in range(a + 1, m):
@@ -68,14 +95,7 @@ def loop_candidates(E, stride, radius, gap, tau_global, tau_local):
             if kb - ka < gap or not S[a, b] > tau_global:
                 continue
             coarse.append((a, b, float(S[a, b])))
-            best = (-np.inf, -1, -1)
-            for i in range(max(ka - radius, 0), min(ka + radius, n - 1) + 1):
-                for j in range(max(kb - radius, 0), min(kb + radius, n - 1) + 1):
-                    if j - i < gap:
-                        continue
-                    s = float(En[i] @ En[j])
-                    if s > best[0]:
-                        best = (s, i, j)
+            best = best_neighbour(En, ka, kb, radius, gap)
             if best[0] > tau_local:
                 loops.append((a, b, best[1], best[2], best[0]))
     return coarse, loops

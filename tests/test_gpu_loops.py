@@ -76,3 +76,37 @@ def test_capacity_and_arguments(ctx):
     assert ctx.sync_status() == 4                      # EC3R_ERR_CAPACITY
     with pytest.raises(ec3r.Ec3rError):
         ctx.loop_candidates(torch.zeros((10, 100), device="cuda"))   # d not a multiple of 64
+
+
+@pytest.mark.timeout(900)
+def test_full_size_sampled_rows_and_candidates(ctx):
+    """The benchmarked size (32,768 keyframes x 1024, every 2nd sampled: a
+    16,384^2 similarity matrix, the same launch as the timed call): sampled
+    rows of the tensor-core matrix against the oracle's rows, and sampled
+    loop candidates against the oracle's neighbourhood search."""
+    n, d, stride = 32768, 1024, 2
+    E = synth.make_keyframe_embeddings(synth.SEED_BASE + 62, n=n, d=d)
+    kw = dict(stride=stride, radius=2, gap=n // 5, tau_global=0.93, tau_local=0.96)
+    rows, scores, counts, S = ctx.loop_candidates(E.cuda(), capacity=1 << 18, with_sim=True,
+                                                  **kw)
+    assert ctx.sync_status() == 0
+    En = E.numpy()
+    m = S.shape[0]
+    rng = np.random.default_rng(5)
+    sample = np.concatenate([[0, m - 1], rng.choice(m, 10, replace=False)])
+    ref = olp.coarse_similarity_rows(En, stride, sample)
+    got = S[torch.as_tensor(sample, device="cuda")].cpu().numpy()
+    for r, a in enumerate(sample):
+        assert np.abs(got[r, a:] - ref[r, a:]).max() <= MARGIN, a
+    assert int(counts[0]) > 1000 and int(counts[1]) > 100
+    # sampled candidates: the coarse score is the matrix entry, the best
+    # neighbour is the oracle's (or ties it within FP32 rounding)
+    U = olp.unit_rows(En)
+    R, SC = rows.cpu().numpy(), scores.cpu().numpy()
+    for q in rng.choice(len(R), 40, replace=False):
+        a, b, i, j = (int(v) for v in R[q])
+        sc, s = float(SC[q, 0]), float(SC[q, 1])
+        assert abs(sc - olp.coarse_similarity_rows(En, stride, [a])[0, b]) <= MARGIN
+        best, bi, bj = olp.best_neighbour(U, a * stride, b * stride, kw["radius"], kw["gap"])
+        assert abs(s - best) <= 1e-5
+        assert (bi, bj) == (i, j) or abs(float(U[i] @ U[j]) - best) <= 1e-5

@@ -47,3 +47,23 @@ def test_thresholds_gap_and_best_neighbour():
         assert (i, j) == (-best[1], -best[2]) and abs(s - best[0]) < 1e-6 and s > 0.999
     # (0, 5): theta 0 vs 0.02 -> cos 0.9998 passes both thresholds
     assert any((a, b) == (0, 5) for a, b, *_ in found)
+
+
+def test_sampled_rows_and_neighbourhood_helpers_agree_with_the_whole_matrix():
+    """The row-sampled similarities (for sizes whose matrix is too large) are
+    the rows of the whole matrix; the neighbourhood search of one pair
+    reproduces the candidates of the full search."""
+    rng = np.random.default_rng(4)
+    E = rng.normal(size=(90, 64)).astype(np.float32)
+    E[42:52] = E[0:10] + 0.05 * rng.normal(size=(10, 64)).astype(np.float32)  # a revisit
+    S = loops.coarse_similarity(E, 3)
+    rows = [0, 5, S.shape[0] - 1]
+    np.testing.assert_array_equal(loops.coarse_similarity_rows(E, 3, rows), S[rows])
+    coarse, found = loops.loop_candidates(E, stride=3, radius=1, gap=20, tau_global=0.9,
+                                          tau_local=0.95)
+    assert found
+    En = loops.unit_rows(E)
+    for a, b, i, j, s in found:
+        assert loops.best_neighbour(En, 3 * a, 3 * b, 1, 20) == (s, i, j)
+    # a neighbourhood with no pair far enough apart
+    assert loops.best_neighbour(En, 0, 3, 1, 20) == (-np.inf, -1, -1)
