@@ -343,27 +343,18 @@ def run_ours(args):
         # inputs from pinned host memory and reads its result back)
         dxs = [torch.empty(hx.shape, dtype=torch.float32, device=dev) for _ in range(2)]
         dcs = [torch.empty(hc.shape, dtype=torch.float32, device=dev) for _ in range(2)]
-        ready = [[torch.cuda.Event() for _ in range(2)] for _ in range(2)]
+        ready = [torch.cuda.Event() for _ in range(2)]
         free = [torch.cuda.Event() for _ in range(2)]
-        # two copy streams, each with half of the step's bytes: the host link
-        # sustains about 2 % more with two copies in flight than with one
-        copy_streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
-        hxf, hcf = hx.view(-1), hc.view(-1)
-        half = (hxf.numel() + hcf.numel()) // 2  # stream 0: xyz[:half]; 1: the rest + conf
+        copy_stream = torch.cuda.Stream(device=dev)
         hS = torch.empty(S.shape, dtype=S.dtype, pin_memory=True)
         e2e_steps = max(1, min(args.steps, 5))
 
         def upload(b):
-            dxf, dcf = dxs[b].view(-1), dcs[b].view(-1)
-            for j, cs in enumerate(copy_streams):
-                cs.wait_event(free[b])
-                with torch.cuda.stream(cs):
-                    if j == 0:
-                        dxf[:half].copy_(hxf[:half], non_blocking=True)
-                    else:
-                        dxf[half:].copy_(hxf[half:], non_blocking=True)
-                        dcf.copy_(hcf, non_blocking=True)
-                ready[b][j].record(cs)
+            copy_stream.wait_event(free[b])
+            with torch.cuda.stream(copy_stream):
+                dxs[b].copy_(hx, non_blocking=True)
+                dcs[b].copy_(hc, non_blocking=True)
+            ready[b].record(copy_stream)
 
         def run(n):
             main = torch.cuda.current_stream()
@@ -374,8 +365,7 @@ def run_ours(args):
                 b = i % 2
                 if i + 1 < n:
                     upload(1 - b)
-                main.wait_event(ready[b][0])
-                main.wait_event(ready[b][1])
+                main.wait_event(ready[b])
                 step(dxs[b], dcs[b])
                 free[b].record(main)
                 hS.copy_(S, non_blocking=True)
