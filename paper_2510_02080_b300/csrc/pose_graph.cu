@@ -13,7 +13,8 @@
 // levels, the trailing dense supernode, the left-looking update lists and the
 // assembly lists.
 // Device, per Gauss-Newton iteration, all FP64:
-//   k_pg_linearize   one warp per edge: e, J_i = -Jr^-1(e) Ad(T_j^-1 T_i),
+//   k_pg_linearize   two warps per edge (the adjoint beside the logarithm):
+//                    e, J_i = -Jr^-1(e) Ad(T_j^-1 T_i),
 //                    J_j = Jr^-1(e) (Jr^-1 from its Bernoulli series), and the
 //                    blocks J^T Omega J, J^T Omega e, e^T Omega e
 //   k_pg_assemble    one warp per factor block: fixed-order sums of the edge
@@ -47,22 +48,35 @@ __constant__ double c_bern[NBERN];  // B_2k / (2k)!, k = 1..24
 // --------------------------------------------------------------------------
 // device helpers: 7x7 blocks in shared memory, one warp
 // --------------------------------------------------------------------------
-// C = op(A) op(B); each lane computes entries lane and lane + 32.
+// C = op(A) op(B) (C distinct from A and B); each lane computes entries lane
+// and lane + 32, their FMA chains interleaved.
 __device__ __forceinline__ void warp_mm7(const double* A, bool tA, const double* B, bool tB,
                                          double* C, int lane) {
-  for (int idx = lane; idx < NB; idx += 32) {
-    const int r = idx / 7, c = idx % 7;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;  // independent partial sums: short FP64 chains
+  const int i1 = lane + 32;
+  const bool two = i1 < NB;
+  const int r0 = lane / 7, c0 = lane % 7;
+  const int r1 = two ? i1 / 7 : 0, c1 = two ? i1 % 7 : 0;  // lanes >= 17: a dummy entry
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;  // independent partial sums: short FP64 chains
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      const double a = tA ? A[7 * k + r] : A[7 * r + k];
-      const double b = tB ? B[7 * c + k] : B[7 * k + c];
-      if (k % 3 == 0) s0 = fma(a, b, s0);
-      else if (k % 3 == 1) s1 = fma(a, b, s1);
-      else s2 = fma(a, b, s2);
+  for (int k = 0; k < 7; ++k) {
+    const double a0 = tA ? A[7 * k + r0] : A[7 * r0 + k];
+    const double b0 = tB ? B[7 * c0 + k] : B[7 * k + c0];
+    const double a1 = tA ? A[7 * k + r1] : A[7 * r1 + k];
+    const double b1 = tB ? B[7 * c1 + k] : B[7 * k + c1];
+    if (k % 3 == 0) {
+      s0 = fma(a0, b0, s0);
+      t0 = fma(a1, b1, t0);
+    } else if (k % 3 == 1) {
+      s1 = fma(a0, b0, s1);
+      t1 = fma(a1, b1, t1);
+    } else {
+      s2 = fma(a0, b0, s2);
+      t2 = fma(a1, b1, t2);
     }
-    C[idx] = (s0 + s1) + s2;
   }
+  C[lane] = (s0 + s1) + s2;
+  if (two) C[i1] = (t0 + t1) + t2;
   __syncwarp();
 }
 
@@ -191,6 +205,18 @@ struct WarpScratch {
 // --------------------------------------------------------------------------
 // linearisation of one edge (one warp)
 // --------------------------------------------------------------------------
+// Warp 1 of the edge's CTA: Ad(T_j^-1 T_i) into w.B, independent of the error,
+// while warp 0 takes the logarithm; barrier 1 joins the two warps.
+__device__ __forceinline__ void pair_barrier() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+__device__ void linearize_adjoint(int e, int lane, WarpScratch& w, const PgDev& p, int jacobians) {
+  if (lane == 0 && jacobians) {
+    const s3::Sim3d Ti = load_cg(p.nodes + p.ei[e]), Tj = load_cg(p.nodes + p.ej[e]);
+    adjoint7(s3::compose(s3::inverse(Tj), Ti), w.B);
+  }
+  pair_barrier();
+}
+
 __device__ void linearize_edge(int e, int lane, WarpScratch& w, const PgDev& p, int jacobians) {
   if (lane == 0) {
     const s3::Sim3d Ti = load_cg(p.nodes + p.ei[e]), Tj = load_cg(p.nodes + p.ej[e]);
@@ -199,7 +225,6 @@ __device__ void linearize_edge(int e, int lane, WarpScratch& w, const PgDev& p, 
     s3::log(edge_error_T(Ti, Tj, M), xi);
     for (int k = 0; k < 7; ++k) w.e[k] = xi[k];
     if (jacobians) {
-      adjoint7(s3::compose(s3::inverse(Tj), Ti), w.B);   // Ad(T_j^-1 T_i)
       small_ad7(xi, w.A);                                // ad(e)
       // series length from the spectral radius of ad(e) and the size of rho
       const double nu = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5] + xi[6] * xi[6]);
@@ -214,7 +239,7 @@ __device__ void linearize_edge(int e, int lane, WarpScratch& w, const PgDev& p, 
       w.K = K;
     }
   }
-  __syncwarp();
+  pair_barrier();  // w.e, w.A, w.K (warp 0) and w.B (warp 1)
   double ev[7];
   for (int k = 0; k < 7; ++k) ev[k] = w.e[k];
   // Omega (identity unless given)
@@ -255,11 +280,17 @@ __device__ void linearize_edge(int e, int lane, WarpScratch& w, const PgDev& p, 
   for (int idx = lane; idx < NB; idx += 32) w.Ji[idx] = -w.Ji[idx];     // J_i
   __syncwarp();
   double* out = p.contrib + (size_t)e * 3 * NB;
-  warp_mm7(w.O, false, w.Ji, false, w.OJ, lane);        // Omega J_i
-  warp_mm7(w.O, false, w.J, false, w.OJj, lane);        // Omega J_j
-  warp_mm7(w.Ji, true, w.OJ, false, w.A, lane);         // J_i^T Omega J_i
-  warp_mm7(w.J, true, w.OJj, false, w.B, lane);         // J_j^T Omega J_j
-  warp_mm7(w.Ji, true, w.OJj, false, w.C, lane);        // J_i^T Omega J_j
+  const double* OJi = w.Ji;  // Omega J_i, Omega J_j (Omega = I unless given)
+  const double* OJj = w.J;
+  if (p.info) {
+    warp_mm7(w.O, false, w.Ji, false, w.OJ, lane);
+    warp_mm7(w.O, false, w.J, false, w.OJj, lane);
+    OJi = w.OJ;
+    OJj = w.OJj;
+  }
+  warp_mm7(w.Ji, true, OJi, false, w.A, lane);          // J_i^T Omega J_i
+  warp_mm7(w.J, true, OJj, false, w.B, lane);           // J_j^T Omega J_j
+  warp_mm7(w.Ji, true, OJj, false, w.C, lane);          // J_i^T Omega J_j
   for (int idx = lane; idx < NB; idx += 32) {
     out[idx] = w.A[idx];
     out[NB + idx] = w.B[idx];
@@ -268,7 +299,7 @@ __device__ void linearize_edge(int e, int lane, WarpScratch& w, const PgDev& p, 
   // g: J^T Omega e
   if (lane < 14) {
     const int side = lane / 7, r = lane % 7;
-    const double* OJ = side == 0 ? w.OJ : w.OJj;
+    const double* OJ = side == 0 ? OJi : OJj;
     double s = 0.0;
     for (int c = 0; c < 7; ++c) s += OJ[7 * c + r] * ev[c];
     p.gvec[(size_t)e * 14 + lane] = s;
@@ -515,9 +546,10 @@ __device__ __forceinline__ void update_node(int k, const PgDev& p) {
 // --------------------------------------------------------------------------
 // multi-launch schedule: one launch per phase and per tree level
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) k_pg_linearize(PgDev p, int jacobians) {
+__global__ void __launch_bounds__(64) k_pg_linearize(PgDev p, int jacobians) {
   __shared__ WarpScratch w;
-  linearize_edge(blockIdx.x, threadIdx.x, w, p, jacobians);
+  if (threadIdx.x < 32) linearize_edge(blockIdx.x, threadIdx.x, w, p, jacobians);
+  else linearize_adjoint(blockIdx.x, threadIdx.x - 32, w, p, jacobians);
 }
 
 __global__ void __launch_bounds__(32) k_pg_assemble(PgDev p, int n_blocks, int nf,
@@ -1571,7 +1603,7 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
       const bool last = itn == o.iters;  // last pass only evaluates chi^2
       if (n_edges > 0)
         traced(ctx, cs, "pg_linearize", [&] {
-          k_pg_linearize<<<n_edges, 32, 0, cs>>>(dv, last ? 0 : 1);
+          k_pg_linearize<<<n_edges, 64, 0, cs>>>(dv, last ? 0 : 1);
         });
       if (last) {
         if (d_chi2)
@@ -1635,7 +1667,7 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
       if (lm) {  // chi^2 of the tentative step, then keep it or restore
         if (n_edges > 0)
           traced(ctx, cs, "pg_linearize", [&] {
-            k_pg_linearize<<<n_edges, 32, 0, cs>>>(dv, 0);
+            k_pg_linearize<<<n_edges, 64, 0, cs>>>(dv, 0);
           });
         traced(ctx, cs, "pg_assemble", [&] {
           k_pg_assemble<<<1, 32, 0, cs>>>(dv, 0, 0, nullptr, 1);
