@@ -38,10 +38,10 @@ ITERS, DELTA = 10, 0.02
 PG_ITERS = 10
 SEED_CORRECT = 2510020800 + 56
 SWEEP_BYTES_PER_PIXEL = 32          # p, q (2 x 12 B) + c_p, c_q (2 x 4 B) per sweep
-# DRAM bytes per pixel of one sweep launch, from the ncu capture summarised in
-# profiles/irls_sweep_fp32_chain40_294x518.md (read + write / pixels); the
-# traffic scales with the pixels of a launch.  None once the kernel changes.
-SWEEP_TRAFFIC_BYTES_PER_PIXEL = 32.54
+# DRAM bytes per pixel of one sweep launch (read + write / pixels), from an ncu
+# capture of k_sweep on the 40-submap chain; the traffic scales with the
+# pixels of a launch.  None once the kernel changes.
+SWEEP_TRAFFIC_BYTES_PER_PIXEL = 32.53
 
 
 def peaks():

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(THREADS) k_setup(
 // consecutive pixels); warps combine by a pairwise butterfly in T; the eight
 // warp sums are added in FP64 in a fixed order.
 template <typename T, int KIND, bool VEC>
-__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 3 : 2) k_sweep(
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2) k_sweep(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
     const int32_t* __restrict__ link_pair, const PairState* __restrict__ st, float delta,

@@ -112,7 +112,7 @@ __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ck
 // Reduction sweeps.  KIND 0: cost (om at S_{K-1}, e at S_K);  KIND 1: Huber
 // path of iteration k (S_{k-1} and the moments' gradient of k).
 template <int KIND, bool LASTK, bool VEC>
-__global__ void __launch_bounds__(THREADS, 3) k_adj_reduce(
+__global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
     const int32_t* __restrict__ link_pair, const RedParams* __restrict__ rp, int rule,

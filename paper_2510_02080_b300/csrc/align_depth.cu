@@ -247,7 +247,7 @@ struct DepthOp {
 };
 
 template <int KIND, bool VEC>
-__global__ void __launch_bounds__(THREADS, 3) k_sweep_depth(
+__global__ void __launch_bounds__(THREADS, 4) k_sweep_depth(
     const float* __restrict__ depth, const float* __restrict__ conf, int W, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
     const int32_t* __restrict__ link_pair, const PairState* __restrict__ st,
