@@ -133,6 +133,116 @@ def _oracle_sample_inproc(pairs_per_step, steps, warmup, seed):
     return n / dt, n, dt, ps.n_pairs
 
 
+def _oracle_workload_inproc(name):
+    """The oracle timed on a bounded sample of one of the other workloads (one
+    thread); returns {"value", "unit", "sample", "seconds"} and, for some,
+    further timed parts."""
+    import numpy as np
+    import torch
+    from oracle import adjoint as oadj
+    from oracle import fuse as ofuse
+    from oracle import loops as olp
+    from oracle import pose_graph as opg
+    from oracle import register as reg
+    from oracle import unproject as oup
+    from oracle import sim3 as osim3
+    from paper_2510_02080_b300 import synth
+
+    torch.set_num_threads(1)
+
+    def reg_rate(ps):
+        t0 = time.perf_counter()
+        res = reg.align_pairs(ps, delta=DELTA, iters=ITERS)
+        dt = time.perf_counter() - t0
+        return sum(r["n_valid"] for r in res) * ITERS / dt, dt
+
+    def pg_iteration_ms(seed, n, loops):
+        g = synth.make_pose_graph(seed, n, loops, device="cpu")
+        Tij = [(float(g.T_meas.s[k]), g.T_meas.R[k].numpy(), g.T_meas.t[k].numpy())
+               for k in range(len(g.ei))]
+        ei, ej = g.ei.numpy(), g.ej.numpy()
+        init = opg.chain_init(n, ei, ej, Tij)
+        t0 = time.perf_counter()
+        opg.gauss_newton(init, ei, ej, Tij, iters=1)
+        return 1e3 * (time.perf_counter() - t0)
+
+    out = {"unit": UNIT, "cores": 1, "kind": "oracle"}
+    if name == "pair1":
+        ps = synth.make_pair(synth.SEED_BASE + 1, H=294, W=518, sigma=0.005, device="cpu")
+        rate, dt = reg_rate(ps)
+        out.update(value=rate, seconds=dt, sample="the whole pair (FP64 numpy, 10 IRLS solves)")
+    elif name == "adjoint1":
+        ps = synth.make_pair(synth.SEED_BASE + 4, H=294, W=518, sigma=0.005, device="cpu")
+        xyz, conf = ps.xyz.double().numpy(), ps.conf.double().numpy()
+        lo, src, tgt = ps.link_off.numpy(), ps.src.numpy(), ps.tgt.numpy()
+        P, Q, cp, cq, valid = reg.pair_correspondences(xyz, conf, lo, src, tgt, 0, 0.0)
+        w = cp[valid] * cq[valid]
+        t0 = time.perf_counter()
+        S, tape, cost = oadj.irls_forward(P[valid], Q[valid], w, DELTA, ITERS)
+        L, gs, gR, gt = oadj.geodesic_loss_grad(S, osim3.identity())
+        oadj.irls_backward(P[valid], Q[valid], w, DELTA, tape, S, gs, gR, gt, 1.0)
+        dt = time.perf_counter() - t0
+        out.update(value=1e3 * dt, unit="ms per forward + backward", seconds=dt,
+                   sample="the whole pair, FP64 numpy reverse mode")
+    elif name == "loops512":
+        ps = synth.make_loop_batch(synth.SEED_BASE + 3, n_pairs=2, H=294, W=518, device="cpu")
+        rate, dt = reg_rate(ps)
+        out.update(value=rate, seconds=dt,
+                   sample="2 loop pairs of the same recipe (1-5 shared frames, per-pair "
+                          "thresholds), 10 IRLS solves",
+                   pose_graph_ms_per_iteration=pg_iteration_ms(synth.SEED_BASE + 3, 200, 40))
+    elif name == "map1000":
+        ch = synth.make_chain(synth.SEED_BASE + 5, M=3, F=5, H=392, W=518, device="cpu")
+        rate, dt = reg_rate(ch.pairs())
+        xyz = ch.xyz.view(3, -1, 3)[:1].double().numpy()
+        conf = ch.conf.view(3, -1)[:1].double().numpy()
+        pose = [osim3.identity()]
+        t0 = time.perf_counter()
+        ofuse.fuse_points(xyz, conf, pose)
+        fdt = time.perf_counter() - t0
+        out.update(value=rate, seconds=dt,
+                   sample="2 chain pairs at 392x518, 10 IRLS solves; fusion of one submap "
+                          "(5 x 392 x 518 points); one Gauss-Newton iteration of a "
+                          "200-node / 40-loop graph",
+                   fusion_points_per_s=xyz.shape[1] / fdt,
+                   pose_graph_ms_per_iteration_200_nodes=pg_iteration_ms(
+                       synth.SEED_BASE + 3, 200, 40))
+    elif name == "depth200":
+        ch = synth.make_depth_chain(synth.SEED_BASE + 46, M=3, F=5, H=294, W=518, device="cpu")
+        dps = ch.pairs()
+        t0 = time.perf_counter()
+        xyz = oup.unproject(dps.depth.double().numpy(), dps.cams.numpy())
+        dt_un = time.perf_counter() - t0
+        nf, H_, W_ = dps.depth.shape
+        ps = synth.PairSet(torch.as_tensor(xyz, dtype=torch.float32),
+                           dps.conf.reshape(nf, H_ * W_), dps.link_off, dps.src, dps.tgt, H_, W_)
+        rate, dt = reg_rate(ps)
+        out.update(value=rate * dt / (dt + dt_un), seconds=dt + dt_un,
+                   sample="2 depth pairs: FP64 unprojection of their frames, then 10 IRLS "
+                          "solves")
+    elif name == "loops32k":
+        E = synth.make_keyframe_embeddings(synth.SEED_BASE + 62, n=32768, d=1024).numpy()
+        rows = np.arange(0, 16384, 128)
+        t0 = time.perf_counter()
+        olp.coarse_similarity_rows(E, 2, rows)
+        dt = time.perf_counter() - t0
+        m, d = 16384, 1024
+        flops = 2.0 * len(rows) * m * d
+        out.update(value=flops / dt / 1e12, unit="TFLOP/s", seconds=dt,
+                   sample="128 of the 16,384 rows of the similarity matrix (BF16-rounded "
+                          "embeddings, FP64 products)")
+    return out
+
+
+def oracle_workload(name):
+    """_oracle_workload_inproc in a child process pinned to one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-workload",
+                          name], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def oracle_sample(pairs_per_step, steps, warmup, seed):
     """Times the oracle in a child process pinned to one BLAS/OpenMP thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
@@ -687,6 +797,8 @@ def run_workload(args):
             "bf16_peak_tflops": bf16_peak}
     out["peak_gbs"] = peak
     out["peak_kind"] = peak_kind
+    if not args.no_oracle:
+        out["cpu_baseline"] = oracle_workload(args.workload)
     print(json.dumps(out), flush=True)
 
 
@@ -711,7 +823,13 @@ def main():
                     help="keyframes of loops32k (default 32768); smaller values are for "
                          "profiling only")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-workload", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="other workloads: leave out the oracle timing on a sample")
     args = ap.parse_args()
+    if args.oracle_workload:
+        print(json.dumps(_oracle_workload_inproc(args.oracle_workload)))
+        return
     if args.oracle_sample:
         p, k, w, seed = (int(v) for v in args.oracle_sample.split(","))
         rate, n, dt, npairs = _oracle_sample_inproc(p, k, w, seed)
