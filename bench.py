@@ -335,9 +335,13 @@ def run_ours(args):
     # (which needs the registered edges) runs on a second, high-priority
     # stream while the adjoint runs on the main one; the latency-bound
     # pose-graph launches then fill the gaps of the HBM-bound adjoint sweeps.
-    # The fusion (HBM-bound, it needs the corrected poses) follows the adjoint
-    # on the main stream once the pose graph is done.
+    # The fusion's keep counts (no pose needed) run on the second stream
+    # before the pose graph; its scan and scatter (HBM-bound, they need the
+    # corrected poses) follow the adjoint on the main stream once the pose
+    # graph is done.
     side = torch.cuda.Stream(device=dev, priority=-1)
+    tile_counts = torch.empty((M * ((n_frames // M * hw + 8191) // 8192),), dtype=torch.int32,
+                              device=dev)
     ev_reg, ev_side = torch.cuda.Event(), torch.cuda.Event()
 
     def step(xyz_in, conf_in, overlap=True):
@@ -348,6 +352,8 @@ def run_ours(args):
                           want_cost=True, cost=cost, stream=main)
         ev_reg.record(main)
         sec.wait_event(ev_reg)
+        # the fusion's keep counts need no pose: beside the pose graph
+        ctx.fuse_count(conf_in.view(M, -1), tile_counts, stream=sec)
         ctx.pose_graph_correct(poses, ei, ej, S, iters=PG_ITERS, chi2=chi2, stream=sec)
         ev_side.record(sec)
         if not args.no_adjoint:
@@ -361,8 +367,8 @@ def run_ours(args):
         main.wait_event(ev_side)
         c = cursors[ci[0] % n_cursor:ci[0] % n_cursor + 1]
         ci[0] += 1
-        ctx.fuse_points(xyz_in.view(M, -1, 3), conf_in.view(M, -1), poses,
-                        out_xyz, out_idx, c, stream=main)
+        ctx.fuse_points_counted(xyz_in.view(M, -1, 3), conf_in.view(M, -1), tile_counts,
+                                poses, out_xyz, out_idx, c, stream=main)
 
     for _ in range(args.warmup):
         step(ch.xyz, ch.conf)

@@ -362,6 +362,30 @@ ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_subma
                              void* stream);
 
 /*
+ * The same fusion in two calls, for callers that know the confidences before
+ * the poses (the count needs no pose, so it can run while the poses are
+ * still being corrected).
+ *
+ * ec3r_fuse_count writes, for every tile of 8192 consecutive points of every
+ * submap, its number of kept points to d_tile_counts (int32
+ * [n_submaps * ceil(pts_per_submap / 8192)], device, caller-owned).
+ * ec3r_fuse_points_counted then takes those counts instead of counting again
+ * and produces exactly the output of ec3r_fuse_points (same arguments
+ * otherwise).  d_conf and conf_threshold must be the same in both calls and
+ * d_conf must not change between them; the counts are not checked against
+ * the confidences.
+ */
+ec3r_status ec3r_fuse_count(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
+                            const float* d_conf, float conf_threshold, int32_t* d_tile_counts,
+                            void* stream);
+ec3r_status ec3r_fuse_points_counted(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
+                                     const float* d_xyz, const float* d_conf,
+                                     const int32_t* d_tile_counts, const ec3r_sim3* d_poses,
+                                     float conf_threshold, int64_t index_base, float* d_out_xyz,
+                                     int64_t* d_out_idx, int64_t capacity, int64_t* d_cursor,
+                                     void* stream);
+
+/*
  * ec3r_fuse_points on the pointmaps of depth frames (Sec. III-C: submaps are
  * the inverse projection of the predicted depths through the predicted
  * cameras), without forming them.  Frame f of submap m is d_depth / d_conf

@@ -368,43 +368,51 @@ __global__ void __launch_bounds__(THREADS) k_fusez_scatter(
 using namespace ec3r;
 using namespace ec3r::fuse;
 
-extern "C" ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
-                                        const float* d_xyz, const float* d_conf,
-                                        const ec3r_sim3* d_poses, float conf_threshold,
-                                        int64_t index_base, float* d_out_xyz,
-                                        int64_t* d_out_idx, int64_t capacity,
-                                        int64_t* d_cursor, void* stream) {
-  if (!ctx) return EC3R_ERR_INVALID_ARG;
-  if (n_submaps < 0 || pts_per_submap < 0 || capacity < 0 || index_base < 0)
+// Argument checks shared by the pointmap fusion entries; *tps and *n_tiles
+// receive the tiling.  EC3R_OK with n_tiles = 0 means nothing to do.
+static ec3r_status fuse_args(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
+                             float conf_threshold, int64_t* tps, int64_t* n_tiles) {
+  *tps = *n_tiles = 0;
+  if (n_submaps < 0 || pts_per_submap < 0)
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "negative size");
   if (n_submaps == 0 || pts_per_submap == 0) return EC3R_OK;
-  if (!d_xyz || !d_conf || !d_poses || !d_cursor || (capacity > 0 && (!d_out_xyz || !d_out_idx)))
-    return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
   if (conf_threshold != conf_threshold)
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "conf_threshold is NaN");
-  const int64_t tps = (pts_per_submap + TILE - 1) / TILE;
-  const int64_t n_tiles = tps * n_submaps;
-  if (n_tiles >= ((int64_t)1 << 31) || tps >= ((int64_t)1 << 30))
+  *tps = (pts_per_submap + TILE - 1) / TILE;
+  *n_tiles = *tps * n_submaps;
+  if (*n_tiles >= ((int64_t)1 << 31) || *tps >= ((int64_t)1 << 30))
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "problem too large for one call");
-  EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  cudaStream_t s = (cudaStream_t)stream;
-  void *p_cnt, *p_off;
+  return EC3R_OK;
+}
+
+static void launch_count(ec3r_ctx* ctx, cudaStream_t s, const float* d_conf,
+                         int64_t pts_per_submap, int64_t tps, int64_t n_tiles,
+                         float conf_threshold, int32_t* cnt) {
+  const bool vec = (pts_per_submap % 4 == 0) && ((uintptr_t)d_conf % 16 == 0);
+  traced(ctx, s, "fuse_count", [&] {
+    if (vec)
+      k_fuse_count<true><<<(unsigned)n_tiles, THREADS, 0, s>>>(d_conf, pts_per_submap, (int)tps,
+                                                               conf_threshold, cnt);
+    else
+      k_fuse_count<false><<<(unsigned)n_tiles, THREADS, 0, s>>>(d_conf, pts_per_submap,
+                                                                (int)tps, conf_threshold, cnt);
+  });
+}
+
+// Scan of the tile counts (after the running cursor) and the ordered scatter.
+static ec3r_status scan_scatter(ec3r_ctx* ctx, cudaStream_t s, int64_t pts_per_submap,
+                                int64_t tps, int64_t n_tiles, const float* d_xyz,
+                                const float* d_conf, const int32_t* cnt,
+                                const ec3r_sim3* d_poses, float conf_threshold,
+                                int64_t index_base, float* d_out_xyz, int64_t* d_out_idx,
+                                int64_t capacity, int64_t* d_cursor) {
+  void* p_off;
   ec3r_status st;
-  if ((st = ensure_buf(ctx, "fuse.count", sizeof(int32_t) * (size_t)n_tiles, s, &p_cnt))) return st;
   if ((st = ensure_buf(ctx, "fuse.off", sizeof(int64_t) * (size_t)n_tiles, s, &p_off))) return st;
-  int32_t* cnt = (int32_t*)p_cnt;
   int64_t* off = (int64_t*)p_off;
   const bool vec = (pts_per_submap % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0) &&
                    ((uintptr_t)d_conf % 16 == 0);
   const dim3 grid((unsigned)n_tiles);
-  traced(ctx, s, "fuse_count", [&] {
-    if (vec)
-      k_fuse_count<true><<<grid, THREADS, 0, s>>>(d_conf, pts_per_submap, (int)tps,
-                                                  conf_threshold, cnt);
-    else
-      k_fuse_count<false><<<grid, THREADS, 0, s>>>(d_conf, pts_per_submap, (int)tps,
-                                                   conf_threshold, cnt);
-  });
   traced(ctx, s, "fuse_scan", [&] { k_fuse_scan<<<1, 1024, 0, s>>>(cnt, n_tiles, off, d_cursor); });
   traced(ctx, s, "fuse_scatter", [&] {
     if (vec)
@@ -420,6 +428,67 @@ extern "C" ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pt
   });
   EC3R_CUDA_TRY(ctx, cudaGetLastError());
   return EC3R_OK;
+}
+
+extern "C" ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
+                                        const float* d_xyz, const float* d_conf,
+                                        const ec3r_sim3* d_poses, float conf_threshold,
+                                        int64_t index_base, float* d_out_xyz,
+                                        int64_t* d_out_idx, int64_t capacity,
+                                        int64_t* d_cursor, void* stream) {
+  if (!ctx) return EC3R_ERR_INVALID_ARG;
+  if (capacity < 0 || index_base < 0)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "negative size");
+  int64_t tps, n_tiles;
+  ec3r_status st = fuse_args(ctx, n_submaps, pts_per_submap, conf_threshold, &tps, &n_tiles);
+  if (st != EC3R_OK || n_tiles == 0) return st;
+  if (!d_xyz || !d_conf || !d_poses || !d_cursor || (capacity > 0 && (!d_out_xyz || !d_out_idx)))
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
+  EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  void* p_cnt;
+  if ((st = ensure_buf(ctx, "fuse.count", sizeof(int32_t) * (size_t)n_tiles, s, &p_cnt)))
+    return st;
+  int32_t* cnt = (int32_t*)p_cnt;
+  launch_count(ctx, s, d_conf, pts_per_submap, tps, n_tiles, conf_threshold, cnt);
+  return scan_scatter(ctx, s, pts_per_submap, tps, n_tiles, d_xyz, d_conf, cnt, d_poses,
+                      conf_threshold, index_base, d_out_xyz, d_out_idx, capacity, d_cursor);
+}
+
+extern "C" ec3r_status ec3r_fuse_count(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
+                                       const float* d_conf, float conf_threshold,
+                                       int32_t* d_tile_counts, void* stream) {
+  if (!ctx) return EC3R_ERR_INVALID_ARG;
+  int64_t tps, n_tiles;
+  ec3r_status st = fuse_args(ctx, n_submaps, pts_per_submap, conf_threshold, &tps, &n_tiles);
+  if (st != EC3R_OK || n_tiles == 0) return st;
+  if (!d_conf || !d_tile_counts)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
+  EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  launch_count(ctx, (cudaStream_t)stream, d_conf, pts_per_submap, tps, n_tiles, conf_threshold,
+               d_tile_counts);
+  EC3R_CUDA_TRY(ctx, cudaGetLastError());
+  return EC3R_OK;
+}
+
+extern "C" ec3r_status ec3r_fuse_points_counted(
+    ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap, const float* d_xyz, const float* d_conf,
+    const int32_t* d_tile_counts, const ec3r_sim3* d_poses, float conf_threshold,
+    int64_t index_base, float* d_out_xyz, int64_t* d_out_idx, int64_t capacity,
+    int64_t* d_cursor, void* stream) {
+  if (!ctx) return EC3R_ERR_INVALID_ARG;
+  if (capacity < 0 || index_base < 0)
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "negative size");
+  int64_t tps, n_tiles;
+  ec3r_status st = fuse_args(ctx, n_submaps, pts_per_submap, conf_threshold, &tps, &n_tiles);
+  if (st != EC3R_OK || n_tiles == 0) return st;
+  if (!d_xyz || !d_conf || !d_tile_counts || !d_poses || !d_cursor ||
+      (capacity > 0 && (!d_out_xyz || !d_out_idx)))
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
+  EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return scan_scatter(ctx, (cudaStream_t)stream, pts_per_submap, tps, n_tiles, d_xyz, d_conf,
+                      d_tile_counts, d_poses, conf_threshold, index_base, d_out_xyz, d_out_idx,
+                      capacity, d_cursor);
 }
 
 extern "C" ec3r_status ec3r_fuse_points_depth(ec3r_ctx* ctx, int n_submaps, int frames, int H,

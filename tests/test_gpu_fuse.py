@@ -124,3 +124,47 @@ def test_full_size_chain_sampled_submaps(ctx):
         gx = out_xyz[start:start + len(oi)].cpu().numpy()
         assert np.array_equal(gi, oi)
         assert np.abs(gx - ox).max() <= POINT_TOL * extent(ox)
+
+
+@pytest.mark.parametrize("shape", [(3, 2, 33, 51), (2, 5, 294, 62)])
+def test_count_then_scatter_equals_one_call(ctx, shape):
+    """ec3r_fuse_count + ec3r_fuse_points_counted produce exactly what one
+    ec3r_fuse_points call produces (points, indices, cursor), several tiles
+    and a ragged last tile per submap, streaming after a non-zero cursor;
+    and exactly the oracle's indices."""
+    M, F, H, W = shape
+    rng = np.random.default_rng(11)
+    xyz = rng.normal(size=(M, F * H * W, 3)).astype(np.float32)
+    conf = rng.lognormal(0.0, 0.5, size=(M, F * H * W)).astype(np.float32)
+    conf[0, :5] = np.nan
+    rows, Ts = rand_poses(rng, M)
+    ref_xyz, ref_idx, ref_cur, st = run_fuse(ctx, xyz, conf, rows, index_base=3, cursor0=17)
+    assert st == 0
+    xyz_d = torch.tensor(xyz, device="cuda")
+    conf_d = torch.tensor(conf, device="cuda")
+    poses = torch.tensor(rows, dtype=torch.float64, device="cuda")
+    out_xyz = torch.full((conf.size, 3), -7.0, device="cuda")
+    out_idx = torch.full((conf.size,), -7, dtype=torch.int64, device="cuda")
+    cursor = torch.tensor([17], dtype=torch.int64, device="cuda")
+    counts = ctx.fuse_count(conf_d)
+    assert counts.numel() == M * ((F * H * W + 8191) // 8192)
+    ctx.fuse_points_counted(xyz_d, conf_d, counts, poses, out_xyz, out_idx, cursor,
+                            index_base=3)
+    assert ctx.sync_status() == 0
+    assert int(cursor.item()) == ref_cur
+    np.testing.assert_array_equal(out_idx.cpu().numpy(), ref_idx)
+    np.testing.assert_array_equal(out_xyz.cpu().numpy(), ref_xyz)
+    _, idx = ofuse.fuse_points(xyz.astype(np.float64), conf.astype(np.float64), Ts,
+                               index_base=3)
+    np.testing.assert_array_equal(out_idx.cpu().numpy()[17:ref_cur], idx)
+
+
+def test_count_arguments(ctx):
+    conf = torch.ones((2, 100), device="cuda")
+    with pytest.raises(ValueError):
+        ctx.fuse_count(conf, torch.empty((1,), dtype=torch.int32, device="cuda"))
+    with pytest.raises(ec3r.Ec3rError):
+        ctx.fuse_count(conf, threshold=float("nan"))
+    st = ctx._lib.ec3r_fuse_count(ctx._h, 2, 100, ec3r._ptr(conf), 1.0, None,
+                                  ec3r._stream(None))
+    assert st == 1  # EC3R_ERR_INVALID_ARG: no count buffer
