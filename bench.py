@@ -342,6 +342,7 @@ def run_ours(args):
     side = torch.cuda.Stream(device=dev, priority=-1)
     tile_counts = torch.empty((M * ((n_frames // M * hw + 8191) // 8192),), dtype=torch.int32,
                               device=dev)
+    keep_mask = torch.empty((tile_counts.numel() * 256,), dtype=torch.int32, device=dev)
     ev_reg, ev_side = torch.cuda.Event(), torch.cuda.Event()
 
     def step(xyz_in, conf_in, overlap=True):
@@ -353,7 +354,7 @@ def run_ours(args):
         ev_reg.record(main)
         sec.wait_event(ev_reg)
         # the fusion's keep counts need no pose: beside the pose graph
-        ctx.fuse_count(conf_in.view(M, -1), tile_counts, stream=sec)
+        ctx.fuse_count(conf_in.view(M, -1), tile_counts, keep_mask, stream=sec)
         ctx.pose_graph_correct(poses, ei, ej, S, iters=PG_ITERS, chi2=chi2, stream=sec)
         ev_side.record(sec)
         if not args.no_adjoint:
@@ -367,8 +368,8 @@ def run_ours(args):
         main.wait_event(ev_side)
         c = cursors[ci[0] % n_cursor:ci[0] % n_cursor + 1]
         ci[0] += 1
-        ctx.fuse_points_counted(xyz_in.view(M, -1, 3), conf_in.view(M, -1), tile_counts,
-                                poses, out_xyz, out_idx, c, stream=main)
+        ctx.fuse_points_counted(xyz_in.view(M, -1, 3), tile_counts, keep_mask, poses,
+                                out_xyz, out_idx, c, stream=main)
 
     for _ in range(args.warmup):
         step(ch.xyz, ch.conf)

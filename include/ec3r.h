@@ -353,7 +353,7 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
  * advanced by the number of kept points, so successive calls stream into one
  * buffer.  Positions at or beyond `capacity` are not written; the cursor
  * still advances and ec3r_sync_status then returns EC3R_ERR_CAPACITY.
- * Workspace: 8 bytes per 8192 points.
+ * Workspace: 1036 bytes per 8192 points (tile counts, offsets, keep mask).
  */
 ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
                              const float* d_xyz, const float* d_conf, const ec3r_sim3* d_poses,
@@ -367,23 +367,24 @@ ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_subma
  * still being corrected).
  *
  * ec3r_fuse_count writes, for every tile of 8192 consecutive points of every
- * submap, its number of kept points to d_tile_counts (int32
- * [n_submaps * ceil(pts_per_submap / 8192)], device, caller-owned).
- * ec3r_fuse_points_counted then takes those counts instead of counting again
- * and produces exactly the output of ec3r_fuse_points (same arguments
- * otherwise).  d_conf and conf_threshold must be the same in both calls and
- * d_conf must not change between them; the counts are not checked against
- * the confidences.
+ * submap (tile t = m * ceil(pts_per_submap / 8192) + i / 8192 for point i of
+ * submap m), its number of kept points to d_tile_counts[t] (int32
+ * [n_tiles], device, caller-owned) and its keep mask to d_keep_mask (uint32
+ * [n_tiles * 256], device, caller-owned: bit j % 32 of word t * 256 + j / 32
+ * says whether point j of tile t is kept; bits past a tile's last point are
+ * 0).  ec3r_fuse_points_counted then scans the counts and scatters the points
+ * the mask keeps, without reading the confidences, and produces exactly the
+ * output of ec3r_fuse_points with the same d_conf and conf_threshold (the
+ * other arguments as there).  The counts and the mask are not checked.
  */
 ec3r_status ec3r_fuse_count(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
                             const float* d_conf, float conf_threshold, int32_t* d_tile_counts,
-                            void* stream);
+                            uint32_t* d_keep_mask, void* stream);
 ec3r_status ec3r_fuse_points_counted(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
-                                     const float* d_xyz, const float* d_conf,
-                                     const int32_t* d_tile_counts, const ec3r_sim3* d_poses,
-                                     float conf_threshold, int64_t index_base, float* d_out_xyz,
-                                     int64_t* d_out_idx, int64_t capacity, int64_t* d_cursor,
-                                     void* stream);
+                                     const float* d_xyz, const int32_t* d_tile_counts,
+                                     const uint32_t* d_keep_mask, const ec3r_sim3* d_poses,
+                                     int64_t index_base, float* d_out_xyz, int64_t* d_out_idx,
+                                     int64_t capacity, int64_t* d_cursor, void* stream);
 
 /*
  * ec3r_fuse_points on the pointmaps of depth frames (Sec. III-C: submaps are

@@ -28,25 +28,47 @@ constexpr int ROUND = 4 * THREADS;  // points per compaction round
 
 __device__ __forceinline__ bool keep(float c, float thr) { return c > thr; }  // NaN -> false
 
+constexpr int MASK_WORDS = TILE / 32;  // keep-mask words per tile
+
+// Kept points per tile and the tile's keep mask: bit i % 32 of word
+// t * MASK_WORDS + i / 32 is point i of tile t (bits past the tile's end are
+// 0).  A round covers 1024 points, 4 per thread, so 8 consecutive lanes fill
+// one word.
 template <bool VEC>
 __global__ void __launch_bounds__(THREADS) k_fuse_count(const float* __restrict__ conf,
                                                         int64_t n, int tps, float thr,
-                                                        int32_t* __restrict__ tile_count) {
+                                                        int32_t* __restrict__ tile_count,
+                                                        uint32_t* __restrict__ mask) {
   const int64_t t = blockIdx.x;
   const int64_t m = t / tps;
   const int c = (int)(t - m * tps);
   const int64_t base = m * n + (int64_t)c * TILE;
   const int64_t rem = n - (int64_t)c * TILE;
   const int npx = rem < TILE ? (int)rem : TILE;
+  const int lane = threadIdx.x & 31;
   int cnt = 0;
-  for (int i0 = 4 * threadIdx.x; i0 < npx; i0 += 4 * THREADS) {
+  for (int r0 = 0; r0 < npx; r0 += 4 * THREADS) {  // every lane takes every round
+    const int i0 = r0 + 4 * threadIdx.x;
+    unsigned nib = 0;
     if (VEC && i0 + 4 <= npx) {
       const float4 v = __ldcs(reinterpret_cast<const float4*>(conf + base + i0));
-      cnt += keep(v.x, thr) + keep(v.y, thr) + keep(v.z, thr) + keep(v.w, thr);
+      nib = (unsigned)keep(v.x, thr) | (unsigned)keep(v.y, thr) << 1 |
+            (unsigned)keep(v.z, thr) << 2 | (unsigned)keep(v.w, thr) << 3;
     } else {
-      for (int j = i0; j < min(i0 + 4, npx); ++j) cnt += keep(conf[base + j], thr);
+      for (int j = 0; j < 4; ++j)
+        if (i0 + j < npx && keep(conf[base + i0 + j], thr)) nib |= 1u << j;
     }
+    cnt += __popc(nib);
+    unsigned w = nib << (4 * (lane & 7));
+    w |= __shfl_xor_sync(0xffffffffu, w, 1);
+    w |= __shfl_xor_sync(0xffffffffu, w, 2);
+    w |= __shfl_xor_sync(0xffffffffu, w, 4);
+    if ((lane & 7) == 0) mask[t * MASK_WORDS + (r0 >> 5) + (threadIdx.x >> 3)] = w;
   }
+  // words past the last round of a short tile
+  for (int w = ((npx + 4 * THREADS - 1) / (4 * THREADS)) * (4 * THREADS / 32) + threadIdx.x;
+       w < MASK_WORDS; w += THREADS)
+    mask[t * MASK_WORDS + w] = 0u;
   cnt = __reduce_add_sync(0xffffffffu, cnt);
   __shared__ int red[THREADS / 32];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
@@ -143,14 +165,15 @@ __device__ __forceinline__ void emit_round(unsigned km, int i0, int64_t gbase, i
   __syncthreads();
 }
 
-// One CTA per tile, rounds of 1024 points (4 per thread).  The confidences and
-// the points of a round are loaded together, the next round's loads are in
-// flight while the current one is compacted, and each round's kept points are
-// staged in shared memory and written with coalesced stores.
+// One CTA per tile, rounds of 1024 points (4 per thread).  The keep decision
+// comes from the count pass's mask (1 bit per point instead of a 4-byte
+// confidence); the next round's loads are in flight while the current one is
+// compacted, and each round's kept points are staged in shared memory and
+// written with coalesced stores.
 template <bool VEC>
 __global__ void __launch_bounds__(THREADS) k_fuse_scatter(
-    const float* __restrict__ xyz, const float* __restrict__ conf, int64_t n, int tps,
-    const ec3r_sim3* __restrict__ poses, float thr, int64_t index_base,
+    const float* __restrict__ xyz, const uint32_t* __restrict__ mask, int64_t n, int tps,
+    const ec3r_sim3* __restrict__ poses, int64_t index_base,
     const int64_t* __restrict__ tile_off, float* __restrict__ out_xyz,
     int64_t* __restrict__ out_idx, int64_t capacity, unsigned* flags) {
   const int64_t t = blockIdx.x;
@@ -176,20 +199,20 @@ __global__ void __launch_bounds__(THREADS) k_fuse_scatter(
   int64_t pos = tile_off[t];
   bool overflow = false;
 
-  float cf[4], p[12];
+  const uint32_t* tmask = mask + t * MASK_WORDS;
+  unsigned nb;
+  float p[12];
   auto load = [&](int r0) {
     const int i0 = r0 + 4 * threadIdx.x;
+    nb = (tmask[(r0 >> 5) + (threadIdx.x >> 3)] >> (4 * (threadIdx.x & 7))) & 0xFu;
     if (VEC && i0 + 4 <= npx) {
-      const float4 v = __ldcs(reinterpret_cast<const float4*>(conf + base + i0));
       const float4* X = reinterpret_cast<const float4*>(xyz + 3 * (base + i0));
       const float4 u = __ldcs(X), w = __ldcs(X + 1), z = __ldcs(X + 2);
-      cf[0] = v.x; cf[1] = v.y; cf[2] = v.z; cf[3] = v.w;
       p[0] = u.x; p[1] = u.y; p[2] = u.z; p[3] = u.w; p[4] = w.x; p[5] = w.y;
       p[6] = w.z; p[7] = w.w; p[8] = z.x; p[9] = z.y; p[10] = z.z; p[11] = z.w;
     } else {
       for (int j = 0; j < 4; ++j) {
         const bool in = i0 + j < npx;
-        cf[j] = in ? conf[base + i0 + j] : -FLT_MAX;
         for (int d = 0; d < 3; ++d) p[3 * j + d] = in ? xyz[3 * (base + i0 + j) + d] : 0.f;
       }
     }
@@ -197,12 +220,12 @@ __global__ void __launch_bounds__(THREADS) k_fuse_scatter(
   if (npx > 0) load(0);
   for (int r0 = 0; r0 < npx; r0 += ROUND) {
     const int i0 = r0 + 4 * threadIdx.x;
-    float ccf[4], cp[12];
-    for (int j = 0; j < 4; ++j) ccf[j] = cf[j];
+    float cp[12];
+    const unsigned cnb = nb;
     for (int j = 0; j < 12; ++j) cp[j] = p[j];
     if (r0 + ROUND < npx) load(r0 + ROUND);  // next round in flight
     unsigned km = 0;
-    for (int j = 0; j < 4; ++j) km |= (i0 + j < npx && keep(ccf[j], thr)) ? (1u << j) : 0u;
+    for (int j = 0; j < 4; ++j) km |= (i0 + j < npx && ((cnb >> j) & 1u)) ? (1u << j) : 0u;
     emit_round(km, i0, index_base + base, pos, capacity, overflow, out_xyz, out_idx, wcnt, sx,
                sidx, [&](int j, float* dst) {
                  const float x0 = cp[3 * j], x1 = cp[3 * j + 1], x2 = cp[3 * j + 2];
@@ -387,44 +410,40 @@ static ec3r_status fuse_args(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_subma
 
 static void launch_count(ec3r_ctx* ctx, cudaStream_t s, const float* d_conf,
                          int64_t pts_per_submap, int64_t tps, int64_t n_tiles,
-                         float conf_threshold, int32_t* cnt) {
+                         float conf_threshold, int32_t* cnt, uint32_t* mask) {
   const bool vec = (pts_per_submap % 4 == 0) && ((uintptr_t)d_conf % 16 == 0);
   traced(ctx, s, "fuse_count", [&] {
     if (vec)
       k_fuse_count<true><<<(unsigned)n_tiles, THREADS, 0, s>>>(d_conf, pts_per_submap, (int)tps,
-                                                               conf_threshold, cnt);
+                                                               conf_threshold, cnt, mask);
     else
-      k_fuse_count<false><<<(unsigned)n_tiles, THREADS, 0, s>>>(d_conf, pts_per_submap,
-                                                                (int)tps, conf_threshold, cnt);
+      k_fuse_count<false><<<(unsigned)n_tiles, THREADS, 0, s>>>(
+          d_conf, pts_per_submap, (int)tps, conf_threshold, cnt, mask);
   });
 }
 
 // Scan of the tile counts (after the running cursor) and the ordered scatter.
 static ec3r_status scan_scatter(ec3r_ctx* ctx, cudaStream_t s, int64_t pts_per_submap,
                                 int64_t tps, int64_t n_tiles, const float* d_xyz,
-                                const float* d_conf, const int32_t* cnt,
-                                const ec3r_sim3* d_poses, float conf_threshold,
-                                int64_t index_base, float* d_out_xyz, int64_t* d_out_idx,
-                                int64_t capacity, int64_t* d_cursor) {
+                                const int32_t* cnt, const uint32_t* mask,
+                                const ec3r_sim3* d_poses, int64_t index_base, float* d_out_xyz,
+                                int64_t* d_out_idx, int64_t capacity, int64_t* d_cursor) {
   void* p_off;
   ec3r_status st;
   if ((st = ensure_buf(ctx, "fuse.off", sizeof(int64_t) * (size_t)n_tiles, s, &p_off))) return st;
   int64_t* off = (int64_t*)p_off;
-  const bool vec = (pts_per_submap % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0) &&
-                   ((uintptr_t)d_conf % 16 == 0);
+  const bool vec = (pts_per_submap % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0);
   const dim3 grid((unsigned)n_tiles);
   traced(ctx, s, "fuse_scan", [&] { k_fuse_scan<<<1, 1024, 0, s>>>(cnt, n_tiles, off, d_cursor); });
   traced(ctx, s, "fuse_scatter", [&] {
     if (vec)
-      k_fuse_scatter<true><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, pts_per_submap, (int)tps,
-                                                    d_poses, conf_threshold, index_base, off,
-                                                    d_out_xyz, d_out_idx, capacity,
-                                                    ctx->d_flags);
+      k_fuse_scatter<true><<<grid, THREADS, 0, s>>>(d_xyz, mask, pts_per_submap, (int)tps,
+                                                    d_poses, index_base, off, d_out_xyz,
+                                                    d_out_idx, capacity, ctx->d_flags);
     else
-      k_fuse_scatter<false><<<grid, THREADS, 0, s>>>(d_xyz, d_conf, pts_per_submap, (int)tps,
-                                                     d_poses, conf_threshold, index_base, off,
-                                                     d_out_xyz, d_out_idx, capacity,
-                                                     ctx->d_flags);
+      k_fuse_scatter<false><<<grid, THREADS, 0, s>>>(d_xyz, mask, pts_per_submap, (int)tps,
+                                                     d_poses, index_base, off, d_out_xyz,
+                                                     d_out_idx, capacity, ctx->d_flags);
   });
   EC3R_CUDA_TRY(ctx, cudaGetLastError());
   return EC3R_OK;
@@ -446,48 +465,53 @@ extern "C" ec3r_status ec3r_fuse_points(ec3r_ctx* ctx, int n_submaps, int64_t pt
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
   EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  void* p_cnt;
+  void *p_cnt, *p_mask;
   if ((st = ensure_buf(ctx, "fuse.count", sizeof(int32_t) * (size_t)n_tiles, s, &p_cnt)))
     return st;
+  if ((st = ensure_buf(ctx, "fuse.mask", sizeof(uint32_t) * MASK_WORDS * (size_t)n_tiles, s,
+                       &p_mask)))
+    return st;
   int32_t* cnt = (int32_t*)p_cnt;
-  launch_count(ctx, s, d_conf, pts_per_submap, tps, n_tiles, conf_threshold, cnt);
-  return scan_scatter(ctx, s, pts_per_submap, tps, n_tiles, d_xyz, d_conf, cnt, d_poses,
-                      conf_threshold, index_base, d_out_xyz, d_out_idx, capacity, d_cursor);
+  uint32_t* mask = (uint32_t*)p_mask;
+  launch_count(ctx, s, d_conf, pts_per_submap, tps, n_tiles, conf_threshold, cnt, mask);
+  return scan_scatter(ctx, s, pts_per_submap, tps, n_tiles, d_xyz, cnt, mask, d_poses,
+                      index_base, d_out_xyz, d_out_idx, capacity, d_cursor);
 }
 
 extern "C" ec3r_status ec3r_fuse_count(ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap,
                                        const float* d_conf, float conf_threshold,
-                                       int32_t* d_tile_counts, void* stream) {
+                                       int32_t* d_tile_counts, uint32_t* d_keep_mask,
+                                       void* stream) {
   if (!ctx) return EC3R_ERR_INVALID_ARG;
   int64_t tps, n_tiles;
   ec3r_status st = fuse_args(ctx, n_submaps, pts_per_submap, conf_threshold, &tps, &n_tiles);
   if (st != EC3R_OK || n_tiles == 0) return st;
-  if (!d_conf || !d_tile_counts)
+  if (!d_conf || !d_tile_counts || !d_keep_mask)
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
   EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   launch_count(ctx, (cudaStream_t)stream, d_conf, pts_per_submap, tps, n_tiles, conf_threshold,
-               d_tile_counts);
+               d_tile_counts, d_keep_mask);
   EC3R_CUDA_TRY(ctx, cudaGetLastError());
   return EC3R_OK;
 }
 
 extern "C" ec3r_status ec3r_fuse_points_counted(
-    ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap, const float* d_xyz, const float* d_conf,
-    const int32_t* d_tile_counts, const ec3r_sim3* d_poses, float conf_threshold,
+    ec3r_ctx* ctx, int n_submaps, int64_t pts_per_submap, const float* d_xyz,
+    const int32_t* d_tile_counts, const uint32_t* d_keep_mask, const ec3r_sim3* d_poses,
     int64_t index_base, float* d_out_xyz, int64_t* d_out_idx, int64_t capacity,
     int64_t* d_cursor, void* stream) {
   if (!ctx) return EC3R_ERR_INVALID_ARG;
   if (capacity < 0 || index_base < 0)
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "negative size");
   int64_t tps, n_tiles;
-  ec3r_status st = fuse_args(ctx, n_submaps, pts_per_submap, conf_threshold, &tps, &n_tiles);
+  ec3r_status st = fuse_args(ctx, n_submaps, pts_per_submap, 0.f, &tps, &n_tiles);
   if (st != EC3R_OK || n_tiles == 0) return st;
-  if (!d_xyz || !d_conf || !d_tile_counts || !d_poses || !d_cursor ||
+  if (!d_xyz || !d_tile_counts || !d_keep_mask || !d_poses || !d_cursor ||
       (capacity > 0 && (!d_out_xyz || !d_out_idx)))
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
   EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  return scan_scatter(ctx, (cudaStream_t)stream, pts_per_submap, tps, n_tiles, d_xyz, d_conf,
-                      d_tile_counts, d_poses, conf_threshold, index_base, d_out_xyz, d_out_idx,
+  return scan_scatter(ctx, (cudaStream_t)stream, pts_per_submap, tps, n_tiles, d_xyz,
+                      d_tile_counts, d_keep_mask, d_poses, index_base, d_out_xyz, d_out_idx,
                       capacity, d_cursor);
 }
 

@@ -91,9 +91,9 @@ def _declare(l):
                                          _P, C.c_float, _I64, _P, _P, _I64, _P, _P]
     l.ec3r_loop_candidates.argtypes = [_P, _P, C.c_int, C.c_int, C.POINTER(LoopOpts), _P, _I64,
                                        _P, _P, _P]
-    l.ec3r_fuse_count.argtypes = [_P, C.c_int, _I64, _P, C.c_float, _P, _P]
-    l.ec3r_fuse_points_counted.argtypes = [_P, C.c_int, _I64, _P, _P, _P, _P, C.c_float, _I64,
-                                           _P, _P, _I64, _P, _P]
+    l.ec3r_fuse_count.argtypes = [_P, C.c_int, _I64, _P, C.c_float, _P, _P, _P]
+    l.ec3r_fuse_points_counted.argtypes = [_P, C.c_int, _I64, _P, _P, _P, _P, _I64, _P, _P,
+                                           _I64, _P, _P]
     l.ec3r_correct_points.argtypes = [_P, _I64, _P, _P, C.c_int, _I64, _P, _P, _P, C.c_float,
                                       _P, _P]
     l.ec3r_pg_opts_default.argtypes = [C.POINTER(PgOpts)]
@@ -304,32 +304,38 @@ class Context:
         self._check(st)
 
 
-    def fuse_count(self, conf, counts=None, *, threshold=1.0, stream=None):
-        """Kept points of every 8192-point tile of conf [M, n] (int32 counts,
-        returned); the first half of fuse_points, needing no pose."""
+    def fuse_count(self, conf, counts=None, mask=None, *, threshold=1.0, stream=None):
+        """Kept points of every 8192-point tile of conf [M, n] and the keep mask
+        (int32 counts [n_tiles], int32 mask words [n_tiles * 256], returned);
+        the first half of fuse_points, needing no pose."""
         M = int(conf.shape[0])
         n = int(conf.numel() // max(M, 1))
         n_tiles = M * ((n + 8191) // 8192)
         if counts is None:
             counts = torch.empty((max(n_tiles, 1),), dtype=torch.int32, device=conf.device)
-        elif counts.dtype != torch.int32 or counts.numel() < n_tiles:
+        if mask is None:
+            mask = torch.empty((max(n_tiles, 1) * 256,), dtype=torch.int32, device=conf.device)
+        if counts.dtype != torch.int32 or counts.numel() < n_tiles:
             raise ValueError(f"counts must be int32 with at least {n_tiles} entries")
+        if mask.dtype != torch.int32 or mask.numel() < 256 * n_tiles:
+            raise ValueError(f"mask must be int32 with at least {256 * n_tiles} entries")
         st = self._lib.ec3r_fuse_count(self._h, M, n, _ptr(conf), float(threshold),
-                                       _ptr(counts), _stream(stream))
+                                       _ptr(counts), _ptr(mask), _stream(stream))
         self._check(st)
-        return counts
+        return counts, mask
 
-    def fuse_points_counted(self, xyz, conf, counts, poses, out_xyz, out_idx, cursor, *,
-                            threshold=1.0, index_base=0, stream=None):
-        """fuse_points with the tile counts of fuse_count (same conf and threshold)."""
-        M = int(conf.shape[0])
-        n = int(conf.numel() // max(M, 1))
-        if counts.dtype != torch.int32 or counts.numel() < M * ((n + 8191) // 8192):
-            raise ValueError("counts must be the int32 tile counts of fuse_count")
+    def fuse_points_counted(self, xyz, counts, mask, poses, out_xyz, out_idx, cursor, *,
+                            index_base=0, stream=None):
+        """fuse_points from the tile counts and keep mask of fuse_count."""
+        M = int(xyz.shape[0])
+        n = int(xyz.numel() // max(3 * M, 1))
+        n_tiles = M * ((n + 8191) // 8192)
+        if counts.dtype != torch.int32 or counts.numel() < n_tiles or \
+                mask.dtype != torch.int32 or mask.numel() < 256 * n_tiles:
+            raise ValueError("counts and mask must be those of fuse_count")
         st = self._lib.ec3r_fuse_points_counted(
-            self._h, M, n, _ptr(xyz), _ptr(conf), _ptr(counts), _ptr(poses), float(threshold),
-            int(index_base), _ptr(out_xyz), _ptr(out_idx), int(out_idx.numel()), _ptr(cursor),
-            _stream(stream))
+            self._h, M, n, _ptr(xyz), _ptr(counts), _ptr(mask), _ptr(poses), int(index_base),
+            _ptr(out_xyz), _ptr(out_idx), int(out_idx.numel()), _ptr(cursor), _stream(stream))
         self._check(st)
 
     def fuse_points_depth(self, depth, conf, cams, poses, out_xyz, out_idx, cursor, *,

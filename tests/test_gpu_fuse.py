@@ -146,10 +146,19 @@ def test_count_then_scatter_equals_one_call(ctx, shape):
     out_xyz = torch.full((conf.size, 3), -7.0, device="cuda")
     out_idx = torch.full((conf.size,), -7, dtype=torch.int64, device="cuda")
     cursor = torch.tensor([17], dtype=torch.int64, device="cuda")
-    counts = ctx.fuse_count(conf_d)
-    assert counts.numel() == M * ((F * H * W + 8191) // 8192)
-    ctx.fuse_points_counted(xyz_d, conf_d, counts, poses, out_xyz, out_idx, cursor,
-                            index_base=3)
+    counts, mask = ctx.fuse_count(conf_d)
+    n = F * H * W
+    tps = (n + 8191) // 8192
+    assert counts.numel() == M * tps
+    # the mask is the keep predicate, bit by bit, zero past each tile's end
+    words = mask.cpu().numpy().view(np.uint32).reshape(M, tps, 256)
+    bits = ((words[..., None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(M, tps * 8192)
+    with np.errstate(invalid="ignore"):
+        np.testing.assert_array_equal(bits[:, :n], (conf > 1.0).astype(np.uint32))
+    assert not bits[:, n:].any()
+    np.testing.assert_array_equal(counts.cpu().numpy().reshape(M, tps).sum(1),
+                                  bits.sum(1))
+    ctx.fuse_points_counted(xyz_d, counts, mask, poses, out_xyz, out_idx, cursor, index_base=3)
     assert ctx.sync_status() == 0
     assert int(cursor.item()) == ref_cur
     np.testing.assert_array_equal(out_idx.cpu().numpy(), ref_idx)
@@ -165,6 +174,7 @@ def test_count_arguments(ctx):
         ctx.fuse_count(conf, torch.empty((1,), dtype=torch.int32, device="cuda"))
     with pytest.raises(ec3r.Ec3rError):
         ctx.fuse_count(conf, threshold=float("nan"))
-    st = ctx._lib.ec3r_fuse_count(ctx._h, 2, 100, ec3r._ptr(conf), 1.0, None,
+    counts = torch.empty((2,), dtype=torch.int32, device="cuda")
+    st = ctx._lib.ec3r_fuse_count(ctx._h, 2, 100, ec3r._ptr(conf), 1.0, ec3r._ptr(counts), None,
                                   ec3r._stream(None))
-    assert st == 1  # EC3R_ERR_INVALID_ARG: no count buffer
+    assert st == 1  # EC3R_ERR_INVALID_ARG: no mask buffer
