@@ -1129,6 +1129,44 @@ static void symbolic(const std::vector<std::set<int>>& adj, Symbolic& S) {
   }
 }
 
+// Cost model of one Gauss-Newton iteration (seconds), from measurements on
+// this GPU: a sparse tree level costs a factor and a back-substitution launch
+// (about 22 us together) plus its heaviest column's left-looking updates at
+// one SM's FP64 rate; a supernode column costs about 25 us (its update and
+// panel launch, its share of the two substitutions) plus the dense updates
+// at the whole GPU's FP64 rate.  A 7x7 block product is 686 FLOP.
+constexpr double LEVEL_S = 22e-6, SN_COL_S = 25e-6;
+constexpr double SM_FP64 = 6.3e9, GPU_FP64 = 148 * 6.3e9, BLOCK_FLOP = 686.0;
+
+// Per level l < n_levels (columns k < k_end at level lv[k]): LEVEL_S plus the
+// block products that update its heaviest column (sum over the descendants j
+// of column k of the entries of st[j] at or after k).
+static std::vector<double> level_times(const Symbolic& S, const std::vector<int>& lv,
+                                       int n_levels, int k_end = -1) {
+  const int nf = (int)S.perm.size();
+  if (k_end < 0) k_end = nf;
+  std::vector<double> work(nf, 0.0);
+  for (int j = 0; j < nf; ++j) {
+    int idx = 0;
+    const int len = (int)S.st[j].size();
+    for (int k : S.st[j]) work[k] += (double)(len - idx++);  // entries of st[j] >= k
+  }
+  std::vector<double> worst(std::max(n_levels, 0), 0.0), t(std::max(n_levels, 0), 0.0);
+  std::vector<char> any(std::max(n_levels, 0), 0);
+  for (int k = 0; k < k_end; ++k) {
+    worst[lv[k]] = std::max(worst[lv[k]], work[k]);
+    any[lv[k]] = 1;
+  }
+  for (int l = 0; l < n_levels; ++l)
+    t[l] = any[l] ? LEVEL_S + worst[l] * BLOCK_FLOP / SM_FP64 : 0.0;
+  return t;
+}
+
+static double sn_time(int n) {
+  const double d = (double)n;
+  return n <= 0 ? 0.0 : SN_COL_S * d + d * d * d / 6.0 * BLOCK_FLOP / GPU_FP64;
+}
+
 static Symbolic analyse(const std::vector<int>& order, const std::vector<std::set<int>>& adj) {
   Symbolic S;
   S.perm = order;
@@ -1160,6 +1198,58 @@ static Symbolic analyse(const std::vector<int>& order, const std::vector<std::se
       }
     }
   }
+  // Likewise the top of the tree from a cut level on, when the cost model
+  // below prefers it: a narrow level runs on a few CTAs, its (possibly large)
+  // left-looking updates at one SM's FP64 rate, while as supernode columns
+  // the updates spread over every SM.  The set is closed under parents, so
+  // moving it last (in its own order) adds no fill: a column adjacent to one
+  // of its columns later in the order is its ancestor.
+  {
+    std::vector<int> lv(nf, 0);
+    int top = -1;
+    for (int k = 0; k < nf; ++k) {
+      for (int c : S.children[k]) lv[k] = std::max(lv[k], lv[c] + 1);
+      top = std::max(top, lv[k]);
+    }
+    const std::vector<double> ltime = level_times(S, lv, top + 1);
+    // the columns already dense at the end (from the rule above) stay there
+    int s_old = nf;
+    for (int k = nf - 1; k >= 0; --k) {
+      if ((int)S.st[k].size() != nf - 1 - k) break;
+      s_old = k;
+    }
+    std::vector<int> cnt_below(top + 2, 0);  // columns of level l below s_old
+    for (int k = 0; k < s_old; ++k) cnt_below[lv[k]]++;
+    double best = 1e300;
+    int cut = top + 1;
+    int n_up = nf - s_old;
+    double sparse = 0.0;
+    for (int l = 0; l <= top; ++l) sparse += cnt_below[l] > 0 ? ltime[l] : 0.0;
+    for (int L = top + 1; L >= 0; --L) {
+      if (L <= top) {  // level L joins the supernode
+        sparse -= cnt_below[L] > 0 ? ltime[L] : 0.0;
+        n_up += cnt_below[L];
+      }
+      const double c = sparse + sn_time(n_up);
+      if (c < best - 1e-12) {
+        best = c;
+        cut = L;
+      }
+    }
+    std::vector<int> upper, rest;
+    for (int k = 0; k < nf; ++k) (k >= s_old || lv[k] >= cut ? upper : rest).push_back(k);
+    if ((int)upper.size() >= SN_MIN && (int)upper.size() > nf - s_old) {
+      std::vector<int> np;
+      for (int k : rest) np.push_back(S.perm[k]);
+      for (int k : upper) np.push_back(S.perm[k]);
+      S.perm = np;
+      symbolic(adj, S);
+      for (int k = nf - (int)upper.size(); k < nf; ++k) {
+        S.st[k].clear();
+        for (int q = k + 1; q < nf; ++q) S.st[k].insert(q);
+      }
+    }
+  }
   // trailing dense supernode: the longest suffix of columns whose structure is
   // every later column
   int s0 = nf;
@@ -1177,9 +1267,17 @@ static Symbolic analyse(const std::vector<int>& order, const std::vector<std::se
     const double c = (double)S.st[k].size() + 1.0;
     S.pairs += c * (c + 1.0) * 0.5;  // 7x7 block products of column k's updates
   }
-  // seconds per iteration: a launch-latency term per sparse level and per
-  // supernode column, plus the block products at an effective FP64 rate
-  S.cost = 8e-6 * S.nlev + 25e-6 * (nf - S.sn0) + S.pairs * 686.0 / 1e11;
+  {
+    std::vector<int> lv2(nf, 0);
+    int top = -1;
+    for (int k = 0; k < S.sn0; ++k) {
+      for (int c : S.children[k]) lv2[k] = std::max(lv2[k], lv2[c] + 1);
+      top = std::max(top, lv2[k]);
+    }
+    const std::vector<double> lt = level_times(S, lv2, top + 1, S.sn0);
+    S.cost = sn_time(nf - S.sn0);
+    for (double t : lt) S.cost += t;
+  }
   return S;
 }
 
