@@ -76,46 +76,62 @@ __device__ inline Sim3d identity() {
   return c;
 }
 
-// 1/n for n = 0..127 (entry 0 unused): FP64 division is slow on this GPU, so
-// the series below multiply by reciprocals.
-struct RecipTable {
-  double v[128];
+// Coefficients of the small-argument series of (a, b, c) below, as
+// polynomials in sigma (Horner) for each power of -th2:
+//   a = sum_i s^i / (i+1)!,
+//   b = sum_j (-th2)^j sum_i s^i / ((2j+1)! i! (i+2j+2)),
+//   c = sum_j (-th2)^j sum_i s^i / ((2j+2)! i! (i+2j+3)).
+// For s^2 + th2 < 1/4 (|s| < 1/2, th2 < 1/4) 18 powers of s and 9 of th2 leave
+// a truncation below 1e-19.
+constexpr int VS_I = 18, VS_J = 9;
+struct VSeries {
+  double a[VS_I], b[VS_J][VS_I], c[VS_J][VS_I];
 };
-__host__ __device__ constexpr RecipTable make_recips() {
-  RecipTable t{};
-  t.v[0] = 0.0;
-  for (int n = 1; n < 128; ++n) t.v[n] = 1.0 / (double)n;
+__host__ __device__ constexpr double factorial(int n) {
+  double f = 1.0;
+  for (int k = 2; k <= n; ++k) f *= (double)k;
+  return f;
+}
+__host__ __device__ constexpr VSeries make_vseries() {
+  VSeries t{};
+  for (int i = 0; i < VS_I; ++i) {
+    t.a[i] = 1.0 / factorial(i + 1);
+    for (int j = 0; j < VS_J; ++j) {
+      t.b[j][i] = 1.0 / (factorial(2 * j + 1) * factorial(i) * (double)(i + 2 * j + 2));
+      t.c[j][i] = 1.0 / (factorial(2 * j + 2) * factorial(i) * (double)(i + 2 * j + 3));
+    }
+  }
   return t;
 }
-__constant__ constexpr RecipTable c_recip = make_recips();
+__constant__ constexpr VSeries c_vseries = make_vseries();
 
 // Coefficients (a, b, c) of V = a I + b phi^ + c phi^2.
 __device__ inline void v_coeffs(double sigma, double th2, double* a, double* b, double* c) {
   if (sigma * sigma + th2 < 0.25) {
-    // a = sum_i s^i/(i+1)!,  b = sum_{i,j} s^i/i! (-th2)^j /(2j+1)! /(i+2j+2),
-    // c = sum_{i,j} s^i/i! (-th2)^j /(2j+2)! /(i+2j+3)
-    const double* rc = c_recip.v;
-    double sa = 0.0, sb = 0.0, sc = 0.0;
-    double pi = 1.0;  // s^i / i!
-    for (int i = 0; i < 40; ++i) {
-      sa += pi * rc[i + 1];
-      double pj = 1.0;  // (-th2)^j
-      double fb = 1.0, fc = 0.5;  // 1/(2j+1)!, 1/(2j+2)!
-      double tb = 0.0, tc = 0.0;
-      for (int j = 0; j < 20; ++j) {
-        tb += pj * fb * rc[i + 2 * j + 2];
-        tc += pj * fc * rc[i + 2 * j + 3];
-        pj *= -th2;
-        fb *= rc[2 * j + 2] * rc[2 * j + 3];
-        fc *= rc[2 * j + 3] * rc[2 * j + 4];
-        if (fabs(pj) * fb < 1e-20) break;
+    // Horner in sigma for every power of -th2 at once (independent chains),
+    // then Horner in -th2; fewer powers of sigma when |sigma| is small
+    const double as = fabs(sigma);
+    const int ni = as < 1e-9 ? 2 : as < 1e-4 ? 5 : as < 1e-2 ? 8 : as < 0.1 ? 12 : VS_I;
+    const VSeries& V = c_vseries;
+    double pa = 0.0, pb[VS_J], pc[VS_J];
+#pragma unroll
+    for (int j = 0; j < VS_J; ++j) pb[j] = pc[j] = 0.0;
+    for (int i = ni - 1; i >= 0; --i) {
+      pa = fma(pa, sigma, V.a[i]);
+#pragma unroll
+      for (int j = 0; j < VS_J; ++j) {
+        pb[j] = fma(pb[j], sigma, V.b[j][i]);
+        pc[j] = fma(pc[j], sigma, V.c[j][i]);
       }
-      sb += pi * tb;
-      sc += pi * tc;
-      pi *= sigma * rc[i + 1];
-      if (fabs(pi) < 1e-20) break;
     }
-    *a = sa;
+    const double u = -th2;
+    double sb = pb[VS_J - 1], sc = pc[VS_J - 1];
+#pragma unroll
+    for (int j = VS_J - 2; j >= 0; --j) {
+      sb = fma(sb, u, pb[j]);
+      sc = fma(sc, u, pc[j]);
+    }
+    *a = pa;
     *b = sb;
     *c = sc;
     return;
