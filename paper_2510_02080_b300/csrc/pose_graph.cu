@@ -26,6 +26,15 @@
 //                    parallel with the updates)
 //   k_pg_backsolve   one launch per level, root to leaves, one warp per column
 //   k_pg_update      one thread per node: T <- T Exp(delta)
+// The trailing dense supernode (the top of the elimination tree):
+//   k_pg_sn_assemble      updates of its blocks by the sparse columns
+//   k_pg_sn_panel_first   7x7 Cholesky and triangular solves of its first column
+//   k_pg_sn_update_panel  per column: the right-looking update of the
+//                         remaining blocks over all SMs, and the next column's
+//                         panel in the CTA that completes that column
+//   k_pg_sn_rhs           the sparse columns' terms of its right-hand side
+//   k_pg_sn_dense_solve   one CTA: forward and back substitution, right-looking
+// Adaptive LM (lm_adaptive): k_pg_lm_start, k_pg_backup, k_pg_decide.
 #include <algorithm>
 #include <cmath>
 #include <functional>
