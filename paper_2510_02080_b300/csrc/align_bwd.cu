@@ -1,7 +1,8 @@
 // Reverse-mode derivative (adjoint) of the batched Huber-IRLS registration.
 //
 // The forward pass (align.cu) checkpoints, per pair and iteration, the 19
-// moments and the estimate (A = s R, b); the backward call reuses the last
+// moments, the estimate (A = s R, b), s and R, and the singular values and
+// right singular vectors of the cross-covariance; the backward call reuses the last
 // forward call's checkpoints when its inputs match, else re-runs it.  The
 // loss gradient then flows backwards through every iteration: the Huber
 // weights of solve k depend on estimate k-1, so each solve is differentiated
@@ -10,8 +11,10 @@
 //   k_adj_init     per pair: upstream dL/d(s, R, t) -> pivot-relative (s, R, b)
 //   cost sweep     (dL/dcost != 0) sum om e p'^T, sum om e at the last estimate
 //   k_adj_solve    one warp per pair: back through one weighted-Umeyama solve
-//                  (covariance, polar rotation with the (d_i + d_j) form,
-//                  scale, translation) to the gradient of its moments
+//                  (covariance, polar rotation with the (d_i + d_j) form from
+//                  the checkpointed d, V, scale, translation) to the gradient
+//                  of its moments; writes the pair's FP32 parameters of the
+//                  next reduce sweep
 //   reduce sweep   per point: the moments' gradient gives dL/d omega_i; through
 //                  h_i = min(1, delta/r_i) it gives dL/d(A, b) of the previous
 //                  estimate, reduced per pair (fixed-order FP64 partials)

@@ -8,13 +8,16 @@
 // exact:
 //
 //   k_fuse_count    one CTA per tile of 8192 points of one submap: keep count
+//                   and the tile's 1-bit keep mask
 //   k_fuse_scan     one CTA: exclusive scan of the tile counts from *cursor,
 //                   advances *cursor by the total
 //   k_fuse_scatter  one CTA per tile: ordered block-wide compaction in rounds
-//                   of 1024 points, Sim(3) transform in FP32 (FMA), writes
-//                   the point and its int64 global index
+//                   of 1024 points (the keep bits from the mask), Sim(3)
+//                   transform in FP32 (FMA), writes the point and its int64
+//                   global index
 //
-// Bytes per input point: 4 (count) + 16 (scatter read) + 20 per kept point.
+// Bytes per input point: 4 + 1/8 (count) + 12 + 1/8 (scatter read) + 20 per
+// kept point.
 #include <cfloat>
 
 #include "common.cuh"
