@@ -315,6 +315,11 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
   double* partials = (double*)ctx->bufs["align.partials"].ptr;
   int32_t* link_pair = (int32_t*)ctx->bufs["align.link_pair"].ptr;
   double* ckpt = (double*)p_ck;
+  void* p_cs;
+  if ((st = ensure_buf(ctx, "align.cost_sums", sizeof(double) * NCS * (size_t)n_pairs, s,
+                       &p_cs)))
+    return st;
+  double* cost_sums = (double*)p_cs;
   const bool vec =
       (hw % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0) && ((uintptr_t)d_conf % 16 == 0);
   const bool fp64 = opts->precision == EC3R_PREC_FP64;
@@ -368,8 +373,8 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
       });
       if (kind == COST)
         traced(ctx, cs, "irls_cost", [&] {
-          k_cost<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, d_link_off, (int)tpl,
-                                                        partials, state, d_pair_cost);
+          k_cost<<<n_pairs, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
+                                         d_pair_cost, cost_sums);
         });
       else
         traced(ctx, cs, "sim3_solve", [&] {
@@ -507,8 +512,8 @@ extern "C" ec3r_status ec3r_align_submaps_noalloc(
       }
     }
     if (kind == COST)
-      k_cost<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials,
-                                                    state, d_pair_cost);
+      k_cost<<<n_pairs, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
+                                     d_pair_cost, nullptr);
     else
       k_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
                                             d_out, d_pair_status, it == o.iters, nullptr, it,

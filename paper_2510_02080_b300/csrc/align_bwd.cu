@@ -9,7 +9,8 @@
 // and the weights' dependence is carried into the previous estimate.
 //
 //   k_adj_init     per pair: upstream dL/d(s, R, t) -> pivot-relative (s, R, b)
-//   cost sweep     (dL/dcost != 0) sum om e p'^T, sum om e at the last estimate
+//   cost term      (dL/dcost != 0) sum om e p'^T, sum om e at the last
+//                  estimate: accumulated by the forward's cost sweep
 //   k_adj_solve    one warp per pair: back through one weighted-Umeyama solve
 //                  (covariance, polar rotation with the (d_i + d_j) form from
 //                  the checkpointed d, V, scale, translation) to the gradient
@@ -80,7 +81,7 @@ __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ck
                            const PairState* __restrict__ st, const int32_t* __restrict__ status,
                            const double* __restrict__ cost, const double* __restrict__ gS,
                            const double* __restrict__ gcost, AdjState* __restrict__ adj,
-                           float delta, RedParams* __restrict__ rp) {
+                           RedParams* __restrict__ rp) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_pairs) return;
   AdjState& a = adj[k];
@@ -108,13 +109,12 @@ __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ck
     a.gJ = gcost[k] / W;
     a.gOm = -gcost[k] * cost[k] / W;
   }
-  // the cost sweep: om at S_{K-1}, residual at S_K
-  write_red_params(rp[k], ckpt + (size_t)k * iters * CKPT, iters, true, nullptr, a, st[k], delta);
 }
 
-// Reduction sweeps.  KIND 0: cost (om at S_{K-1}, e at S_K);  KIND 1: Huber
-// path of iteration k (S_{k-1} and the moments' gradient of k).
-template <int KIND, bool LASTK, bool VEC>
+// Reduction sweep of the Huber path of iteration k (S_{k-1} and the
+// moments' gradient of k).  (The cost term's sums come from the forward's
+// cost sweep.)
+template <bool LASTK, bool VEC>
 __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
@@ -131,13 +131,13 @@ __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
   float Ap[9], bp[3], Ac[9], bc[3], G[NGM];
   for (int i = 0; i < 9; ++i) {
     Ap[i] = RP.Ap[i];
-    Ac[i] = (KIND == 0 || LASTK) ? RP.Ac[i] : 0.f;
+    Ac[i] = LASTK ? RP.Ac[i] : 0.f;
   }
   for (int i = 0; i < 3; ++i) {
     bp[i] = RP.bp[i];
-    bc[i] = (KIND == 0 || LASTK) ? RP.bc[i] : 0.f;
+    bc[i] = LASTK ? RP.bc[i] : 0.f;
   }
-  for (int i = 0; i < NGM; ++i) G[i] = KIND == 1 ? RP.G[i] : 0.f;
+  for (int i = 0; i < NGM; ++i) G[i] = RP.G[i];
   const float gJ = RP.gJ, gOm = RP.gOm;
   constexpr bool lastk = LASTK;  // the cost residual at S_K enters the last Huber sweep
   const float pp0 = RP.pp[0], pp1 = RP.pp[1], pp2 = RP.pp[2];
@@ -169,15 +169,8 @@ __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
     const float e1 = Ap[3] * x0 + Ap[4] * x1 + Ap[5] * x2 + bp[1] - y1;
     const float e2 = Ap[6] * x0 + Ap[7] * x1 + Ap[8] * x2 + bp[2] - y2;
     const float rr = e0 * e0 + e1 * e1 + e2 * e2;
-    const float h = fminf(1.f, dl * rsqrtf(rr));
-    const float om = w * h;
     float g0, g1, g2;
-    if (KIND == 0) {  // g = om e(S_K)
-      const float f0 = Ac[0] * x0 + Ac[1] * x1 + Ac[2] * x2 + bc[0] - y0;
-      const float f1 = Ac[3] * x0 + Ac[4] * x1 + Ac[5] * x2 + bc[1] - y1;
-      const float f2 = Ac[6] * x0 + Ac[7] * x1 + Ac[8] * x2 + bc[2] - y2;
-      g0 = om * f0; g1 = om * f1; g2 = om * f2;
-    } else {
+    {
       float gom = G[G_W] + G[G_SP] * x0 + G[G_SP + 1] * x1 + G[G_SP + 2] * x2 +
                   G[G_SQ] * y0 + G[G_SQ + 1] * y1 + G[G_SQ + 2] * y2 +
                   G[G_PP] * (x0 * x0 + x1 * x1 + x2 * x2) +
@@ -253,7 +246,8 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
                                                    AdjState* __restrict__ adj,
                                                    double* __restrict__ gM,
                                                    const PairState* __restrict__ st,
-                                                   float delta, RedParams* __restrict__ rp) {
+                                                   float delta, RedParams* __restrict__ rp,
+                                                   const double* __restrict__ pair_sums) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   __shared__ double red[8][NRED];
@@ -262,9 +256,13 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
   if (!a.active) return;
   const int wib = threadIdx.x >> 5;
   const double* ck = ckpt + ((size_t)warp * iters + (j - 1)) * CKPT;
-  if (have_partials) {
-    const int64_t t0 = (int64_t)link_off[warp] * tpl, t1 = (int64_t)link_off[warp + 1] * tpl;
-    if (lane < NRED) red[wib][lane] = tile_sum<NRED>(partials, t0, t1, lane);
+  if (have_partials && lane < NRED) {
+    if (pair_sums) {  // summed per pair already (the forward's cost sweep)
+      red[wib][lane] = pair_sums[(size_t)warp * NRED + lane];
+    } else {
+      const int64_t t0 = (int64_t)link_off[warp] * tpl, t1 = (int64_t)link_off[warp + 1] * tpl;
+      red[wib][lane] = tile_sum<NRED>(partials, t0, t1, lane);
+    }
   }
   __syncwarp();
   if (lane != 0) return;
@@ -771,44 +769,38 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
     traced(ctx, cs, "adj_init", [&] {
       k_adj_init<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, iters, ckpt, state,
                                                       (const int32_t*)p_st, (const double*)p_cost,
-                                                      d_grad_S, d_grad_cost, adj, delta, rp);
+                                                      d_grad_S, d_grad_cost, adj, rp);
     });
+    // the cost term's sums (sum g p'^T, sum g at the returned estimate with
+    // the last weights) come from the forward's cost sweep, per pair
     const bool cost_path = d_grad_cost != nullptr;
-    if (cost_path && n_tiles > 0)
-      traced(ctx, cs, "adj_reduce", [&] {
-        if (vec)
-          k_adj_reduce<0, false, true><<<grid, THREADS, 0, cs>>>(
-              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
-        else
-          k_adj_reduce<0, false, false><<<grid, THREADS, 0, cs>>>(
-              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
-      });
+    const double* cost_sums = (const double*)ctx->bufs["align.cost_sums"].ptr;
     traced(ctx, cs, "adj_solve", [&] {
       k_adj_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, iters, iters, d_link_off, (int)tpl, part,
                                                cost_path && n_tiles > 0, 1, ckpt, adj, gM, state,
-                                               delta, rp);
+                                               delta, rp, cost_sums);
     });
     for (int k = iters; k >= 2; --k) {
       if (n_tiles > 0)
         traced(ctx, cs, "adj_reduce", [&] {
           const bool last = k == iters;
           if (vec && last)
-            k_adj_reduce<1, true, true><<<grid, THREADS, 0, cs>>>(
+            k_adj_reduce<true, true><<<grid, THREADS, 0, cs>>>(
                 d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
           else if (vec)
-            k_adj_reduce<1, false, true><<<grid, THREADS, 0, cs>>>(
+            k_adj_reduce<false, true><<<grid, THREADS, 0, cs>>>(
                 d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
           else if (last)
-            k_adj_reduce<1, true, false><<<grid, THREADS, 0, cs>>>(
+            k_adj_reduce<true, false><<<grid, THREADS, 0, cs>>>(
                 d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
           else
-            k_adj_reduce<1, false, false><<<grid, THREADS, 0, cs>>>(
+            k_adj_reduce<false, false><<<grid, THREADS, 0, cs>>>(
                 d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
         });
       traced(ctx, cs, "adj_solve", [&] {
         k_adj_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, iters, k - 1, d_link_off, (int)tpl,
                                                  part, n_tiles > 0, 0, ckpt, adj, gM, state,
-                                                 delta, rp);
+                                                 delta, rp, nullptr);
       });
     }
     EC3R_CUDA_TRY(ctx, cudaMemsetAsync(refs, 0, sizeof(int32_t) * (size_t)(n_frames + 1), cs));

@@ -536,8 +536,8 @@ extern "C" ec3r_status ec3r_align_submaps_depth(
         });
       if (kind == COST)
         traced(ctx, cs, "depth_cost", [&] {
-          k_cost<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials,
-                                                        state, d_pair_cost);
+          k_cost<<<n_pairs, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
+                                         d_pair_cost, nullptr);
         });
       else
         traced(ctx, cs, "depth_solve", [&] {

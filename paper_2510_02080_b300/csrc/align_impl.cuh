@@ -14,6 +14,9 @@ constexpr int THREADS = 256;
 constexpr int NMOM = 19;
 // moment slots
 enum { M_W = 0, M_SP = 1, M_SQ = 4, M_PP = 7, M_QP = 8, M_COST = 17, M_CNT = 18 };
+// The cost sweep leaves slots 1..16 free and stores there, from CS_SLOT on,
+// the 12 sums of the adjoint's cost term (sum g p'^T row-major, sum g).
+constexpr int CS_SLOT = 1, NCS = 12;
 constexpr double RANK_REL_TOL = 1e-4;
 
 struct PairState {
@@ -230,7 +233,7 @@ struct PointOp {
             y2 = v ? (T)q2 - pq[2] : T(0);
     T w = rule == 0 ? (T)cp * (T)cq : (T)cp;
     w = v ? w : T(0);
-    T h = T(1), r2 = T(0);
+    T h = T(1), r2 = T(0), f0 = T(0), f1 = T(0), f2 = T(0);
     if (KIND != FIRST) {
       const T* a = (KIND == COST) ? Ap : A;
       const T* c = (KIND == COST) ? bp : b;
@@ -244,9 +247,9 @@ struct PointOp {
         h = rr <= delta * delta ? 1.0 : delta / sqrt(rr);
       }
       if (KIND == COST) {
-        const T f0 = A[0] * x0 + A[1] * x1 + A[2] * x2 + b[0] - y0;
-        const T f1 = A[3] * x0 + A[4] * x1 + A[5] * x2 + b[1] - y1;
-        const T f2 = A[6] * x0 + A[7] * x1 + A[8] * x2 + b[2] - y2;
+        f0 = A[0] * x0 + A[1] * x1 + A[2] * x2 + b[0] - y0;
+        f1 = A[3] * x0 + A[4] * x1 + A[5] * x2 + b[1] - y1;
+        f2 = A[6] * x0 + A[7] * x1 + A[8] * x2 + b[2] - y2;
         r2 = f0 * f0 + f1 * f1 + f2 * f2;
       } else {
         r2 = rr;
@@ -256,7 +259,16 @@ struct PointOp {
     acc[M_W] += om;
     acc[M_COST] += om * r2;
     acc[M_CNT] += v ? T(1) : T(0);
-    if (KIND == COST) return;
+    if (KIND == COST) {
+      // for the adjoint's cost term: sum g p'^T and sum g with g = om e(S_K),
+      // in moment slots the cost sweep does not otherwise use
+      const T g0 = om * f0, g1 = om * f1, g2 = om * f2;
+      acc[CS_SLOT + 0] += g0 * x0; acc[CS_SLOT + 1] += g0 * x1; acc[CS_SLOT + 2] += g0 * x2;
+      acc[CS_SLOT + 3] += g1 * x0; acc[CS_SLOT + 4] += g1 * x1; acc[CS_SLOT + 5] += g1 * x2;
+      acc[CS_SLOT + 6] += g2 * x0; acc[CS_SLOT + 7] += g2 * x1; acc[CS_SLOT + 8] += g2 * x2;
+      acc[CS_SLOT + 9] += g0; acc[CS_SLOT + 10] += g1; acc[CS_SLOT + 11] += g2;
+      return;
+    }
     const T wx0 = om * x0, wx1 = om * x1, wx2 = om * x2;
     const T wy0 = om * y0, wy1 = om * y1, wy2 = om * y2;
     acc[M_SP + 0] += wx0; acc[M_SP + 1] += wx1; acc[M_SP + 2] += wx2;
@@ -381,24 +393,30 @@ __device__ inline void commit_estimate(PairState& S, unsigned status, const doub
 }
 
 // cost = sum om r^2 / sum om from the cost sweep's partials.
-static __global__ void k_cost(int n_pairs, const int32_t* __restrict__ link_off, int tpl,
-                       const double* __restrict__ partials, const PairState* __restrict__ st,
-                       double* __restrict__ cost) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_pairs) return;
+// One warp per pair: the cost sum W^-1 sum om r^2 of the last estimate and,
+// when cost_sums is given, the pair's 12 sums of the adjoint's cost term
+// (fixed-order tile sums, lane m owns slot m).
+static __global__ void __launch_bounds__(32) k_cost(int n_pairs,
+                                                    const int32_t* __restrict__ link_off,
+                                                    int tpl, const double* __restrict__ partials,
+                                                    const PairState* __restrict__ st,
+                                                    double* __restrict__ cost,
+                                                    double* __restrict__ cost_sums) {
+  const int k = blockIdx.x, lane = threadIdx.x;
+  __shared__ double red[NMOM];
   if (!st[k].active) {
-    cost[k] = 0.0;
+    if (lane == 0) cost[k] = 0.0;
     return;
   }
   const int64_t t0 = (int64_t)link_off[k] * tpl, t1 = (int64_t)link_off[k + 1] * tpl;
-  double w = 0.0, c = 0.0;
-  for (int64_t t = t0; t < t1; ++t) {
-    w += partials[t * NMOM + M_W];
-    c += partials[t * NMOM + M_COST];
+  if (lane < NMOM) red[lane] = tile_sum<NMOM>(partials, t0, t1, lane);
+  __syncwarp();
+  if (lane == 0) {
+    const double w = red[M_W], c = red[M_COST];
+    cost[k] = w > 0.0 ? c / w : 0.0;
   }
-  cost[k] = w > 0.0 ? c / w : 0.0;
+  if (cost_sums && lane < NCS) cost_sums[(size_t)k * NCS + lane] = red[CS_SLOT + lane];
 }
-
 
 }  // namespace align
 }  // namespace ec3r
