@@ -131,6 +131,33 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _want(t, name, dtype, numel=None, at_least=None):
+    """Check a tensor's dtype and element count before its pointer crosses the
+    C ABI, which sees only the pointer: a mistyped buffer would be misread and a
+    short one read or written past its end by the kernels."""
+    if t is None:
+        return
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+    if at_least is not None and t.numel() < at_least:
+        raise ValueError(f"{name} needs at least {at_least} elements, has {t.numel()}")
+
+
+def _want_links(link_off, src, tgt, pair_conf_min, n_pairs):
+    _want(link_off, "link_off", torch.int32)
+    _want(src, "src", torch.int32)
+    _want(tgt, "tgt", torch.int32, numel=int(src.numel()))
+    _want(pair_conf_min, "pair_conf_min", torch.float32, at_least=n_pairs)
+
+
+def _want_outputs(out_xyz, out_idx, cursor):
+    _want(out_idx, "out_idx", torch.int64)
+    _want(out_xyz, "out_xyz", torch.float32, at_least=3 * int(out_idx.numel()))
+    _want(cursor, "cursor", torch.int64, at_least=1)
+
+
 def _stream(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -201,6 +228,7 @@ class Context:
         if tuple(xyz.shape) != (n_frames, hw, 3):
             raise ValueError("xyz must be [n_frames, hw, 3]")
         n_pairs = int(link_off.numel()) - 1
+        _want_links(link_off, src, tgt, pair_conf_min, n_pairs)
         dev = xyz.device
         if out is None:
             out = torch.empty((n_pairs, 13), dtype=torch.float64, device=dev)
@@ -208,6 +236,9 @@ class Context:
             status = torch.empty((n_pairs,), dtype=torch.int32, device=dev)
         if want_cost and cost is None:
             cost = torch.empty((n_pairs,), dtype=torch.float64, device=dev)
+        _want(out, "out", torch.float64, at_least=13 * n_pairs)
+        _want(status, "status", torch.int32, at_least=n_pairs)
+        _want(cost if want_cost else None, "cost", torch.float64, at_least=n_pairs)
         o = AlignOpts(float(delta), int(iters), float(conf_min), RULE[rule], PREC[precision],
                       1 if want_cost else 0)
         st = self._lib.ec3r_align_submaps(
@@ -232,6 +263,7 @@ class Context:
         if tuple(cams.shape) != (n_frames, 16):
             raise ValueError("cams must be [n_frames, 16]")
         n_pairs = int(link_off.numel()) - 1
+        _want_links(link_off, src, tgt, pair_conf_min, n_pairs)
         dev = depth.device
         if out is None:
             out = torch.empty((n_pairs, 13), dtype=torch.float64, device=dev)
@@ -239,6 +271,9 @@ class Context:
             status = torch.empty((n_pairs,), dtype=torch.int32, device=dev)
         if want_cost and cost is None:
             cost = torch.empty((n_pairs,), dtype=torch.float64, device=dev)
+        _want(out, "out", torch.float64, at_least=13 * n_pairs)
+        _want(status, "status", torch.int32, at_least=n_pairs)
+        _want(cost if want_cost else None, "cost", torch.float64, at_least=n_pairs)
         o = AlignOpts(float(delta), int(iters), float(conf_min), RULE[rule], PREC["fp32c"],
                       1 if want_cost else 0)
         st = self._lib.ec3r_align_submaps_depth(
@@ -254,7 +289,14 @@ class Context:
                                rule="product", stream=None):
         """Gradients (dL/dxyz [n_frames,hw,3], dL/dconf [n_frames,hw]) of the registration."""
         n_frames, hw = int(conf.shape[0]), int(conf.shape[1])
+        if xyz.dtype != torch.float32 or conf.dtype != torch.float32:
+            raise ValueError("xyz and conf must be float32")
+        if tuple(xyz.shape) != (n_frames, hw, 3):
+            raise ValueError("xyz must be [n_frames, hw, 3]")
         n_pairs = int(link_off.numel()) - 1
+        _want_links(link_off, src, tgt, pair_conf_min, n_pairs)
+        _want(grad_S, "grad_S", torch.float64, numel=13 * n_pairs)
+        _want(grad_cost, "grad_cost", torch.float64, numel=n_pairs)
         gx = torch.empty_like(xyz)
         gc = torch.empty_like(conf)
         o = AlignOpts(float(delta), int(iters), float(conf_min), RULE[rule], PREC["fp32c"], 1)
@@ -281,8 +323,14 @@ class Context:
         hj = np.ascontiguousarray(np.asarray(ej.cpu() if hasattr(ej, "cpu") else ej,
                                              dtype=np.int32))
         n, m = int(nodes.shape[0]), int(hi.shape[0])
+        if hi.ndim != 1 or hj.shape != hi.shape:
+            raise ValueError("ei and ej must be 1-D and of the same length")
+        _want(nodes, "nodes", torch.float64, numel=13 * n)
+        _want(Tij, "Tij", torch.float64, at_least=13 * m)
+        _want(info, "info", torch.float64, at_least=49 * m)
         if chi2 is None:
             chi2 = torch.empty((iters + 1,), dtype=torch.float64, device=nodes.device)
+        _want(chi2, "chi2", torch.float64, at_least=int(iters) + 1)
         o = PgOpts(int(iters), int(fixed), float(lm_lambda), 1 if init else 0,
                    1 if lm_adaptive else 0)
         st = self._lib.ec3r_pose_graph_correct(
@@ -298,6 +346,10 @@ class Context:
         """Appends kept points of xyz [M, n, 3] / conf [M, n] at ``cursor`` (int64 [1])."""
         M = int(conf.shape[0])
         n = int(conf.numel() // max(M, 1))
+        _want(conf, "conf", torch.float32, numel=M * n)
+        _want(xyz, "xyz", torch.float32, numel=3 * M * n)
+        _want(poses, "poses", torch.float64, at_least=13 * M)
+        _want_outputs(out_xyz, out_idx, cursor)
         st = self._lib.ec3r_fuse_points(
             self._h, M, n, _ptr(xyz), _ptr(conf), _ptr(poses), float(threshold), int(index_base),
             _ptr(out_xyz), _ptr(out_idx), int(out_idx.numel()), _ptr(cursor), _stream(stream))
@@ -311,6 +363,7 @@ class Context:
         M = int(conf.shape[0])
         n = int(conf.numel() // max(M, 1))
         n_tiles = M * ((n + 8191) // 8192)
+        _want(conf, "conf", torch.float32, numel=M * n)
         if counts is None:
             counts = torch.empty((max(n_tiles, 1),), dtype=torch.int32, device=conf.device)
         if mask is None:
@@ -333,6 +386,9 @@ class Context:
         if counts.dtype != torch.int32 or counts.numel() < n_tiles or \
                 mask.dtype != torch.int32 or mask.numel() < 256 * n_tiles:
             raise ValueError("counts and mask must be those of fuse_count")
+        _want(xyz, "xyz", torch.float32, numel=3 * M * n)
+        _want(poses, "poses", torch.float64, at_least=13 * M)
+        _want_outputs(out_xyz, out_idx, cursor)
         st = self._lib.ec3r_fuse_points_counted(
             self._h, M, n, _ptr(xyz), _ptr(counts), _ptr(mask), _ptr(poses), int(index_base),
             _ptr(out_xyz), _ptr(out_idx), int(out_idx.numel()), _ptr(cursor), _stream(stream))
@@ -349,6 +405,10 @@ class Context:
             raise ValueError("the frame count must be a multiple of frames")
         if tuple(cams.shape) != (nfr, 16) or cams.dtype != torch.float32:
             raise ValueError("cams must be float32 [n_frames, 16]")
+        _want(depth, "depth", torch.float32)
+        _want(conf, "conf", torch.float32)
+        _want(poses, "poses", torch.float64, at_least=13 * (nfr // frames))
+        _want_outputs(out_xyz, out_idx, cursor)
         st = self._lib.ec3r_fuse_points_depth(
             self._h, nfr // frames, int(frames), H, W, _ptr(depth), _ptr(conf), _ptr(cams),
             _ptr(poses), float(threshold), int(index_base), _ptr(out_xyz), _ptr(out_idx),
@@ -386,6 +446,11 @@ class Context:
         n = int(conf.numel() // max(M, 1))
         if points.dtype != torch.float32 or refs.dtype != torch.int64:
             raise ValueError("points must be float32 and refs int64")
+        _want(points, "points", torch.float32, at_least=3 * int(refs.numel()))
+        _want(conf, "conf", torch.float32, numel=M * n)
+        _want(xyz, "xyz", torch.float32, numel=3 * M * n)
+        _want(poses, "poses", torch.float64, at_least=13 * M)
+        _want(n_corrected, "n_corrected", torch.int64, at_least=1)
         st = self._lib.ec3r_correct_points(
             self._h, int(refs.numel()), _ptr(points), _ptr(refs), M, n, _ptr(xyz), _ptr(conf),
             _ptr(poses), float(threshold), _ptr(n_corrected), _stream(stream))
