@@ -76,3 +76,32 @@ def test_weight_gradient_orthogonal_to_weights():
     L, gs, gR, gt = adj.geodesic_loss_grad(S, S_gt)
     _, _, gw = adj.irls_backward(P, Q, w, 0.05, tape, S, gs, gR, gt, 1.0)
     assert abs(float(gw @ w)) < 1e-9 * float(np.abs(gw * w).sum())
+
+
+def test_source_weight_rule_matches_finite_differences():
+    """With the source-confidence rule (w = c_p) the gradient reaches c_p only:
+    dL/dc_p matches central differences and dL/dc_q is zero."""
+    P, Q, cp, cq, S_gt = problem(21)
+    delta, iters, lam = 0.05, 10, 1.0
+    S, tape, cost = adj.irls_forward(P, Q, cp, delta, iters)
+    L, gs, gR, gt = adj.geodesic_loss_grad(S, S_gt)
+    _, _, gw = adj.irls_backward(P, Q, cp, delta, tape, S, gs, gR, gt, lam)
+    gcp, gcq = adj.weight_grads(gw, cp, cq, rule="src")
+    assert np.all(gcq == 0.0)
+
+    def loss_src(c):
+        S_, _, cost_ = adj.irls_forward(P, Q, c, delta, iters)
+        return sim3.geodesic_sq(S_gt, S_) + lam * cost_
+
+    near = np.zeros(len(cp), bool)
+    for rec in tape[1:]:
+        near |= np.abs(rec["r"] - delta) < 1e-4
+    h = 1e-6
+    idx = [i for i in range(len(cp)) if not near[i]][:10]
+    assert len(idx) >= 8
+    for i in idx:
+        cpp, cmm = cp.copy(), cp.copy()
+        cpp[i] += h
+        cmm[i] -= h
+        fd = (loss_src(cpp) - loss_src(cmm)) / (2 * h)
+        assert abs(fd - gcp[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, gcp[i])

@@ -140,6 +140,27 @@ def test_noisy_loop_first_order_optimality():
             assert abs(g) < 1e-7, (v, a, g)
 
 
+def test_fixed_node_only_chooses_the_gauge():
+    """The edge error is left-invariant (T_v -> G T_v for every node leaves it
+    unchanged), so holding a different node changes only the gauge: chi^2 and
+    every relative pose T_i^-1 T_j of the optimum agree, and the held node
+    keeps its initial pose."""
+    rng = np.random.default_rng(9)
+    T, ei, ej, Tij = random_graph(rng, 6, 2, noise=0.02)
+    a, ha, sa = pg.gauss_newton(pg.chain_init(6, ei, ej, Tij), ei, ej, Tij, iters=30, fixed=0)
+    start = pg.chain_init(6, ei, ej, Tij, root=3, T_root=rand_sim3(rng))
+    b, hb, sb = pg.gauss_newton(start, ei, ej, Tij, iters=30, fixed=3)
+    assert sa[-1] < 1e-11 and sb[-1] < 1e-11
+    assert hb[-1] < hb[0] and abs(ha[-1] - hb[-1]) <= 1e-10 * ha[-1]
+    assert b[3][0] == start[3][0] and np.array_equal(b[3][1], start[3][1]) \
+        and np.array_equal(b[3][2], start[3][2])
+    for i in range(6):
+        for j in range(6):
+            ra = sim3.compose(sim3.inverse(a[i]), a[j])
+            rb = sim3.compose(sim3.inverse(b[i]), b[j])
+            assert close(rb, ra, 1e-9), (i, j)
+
+
 def test_information_matrix_scales_energy():
     rng = np.random.default_rng(8)
     T, ei, ej, Tij = random_graph(rng, 5, 1, noise=0.03)

@@ -174,6 +174,48 @@ def test_irls_large_delta_is_umeyama():
     assert abs(res["S"][0] - S[0]) < 1e-13 and np.abs(res["S"][1] - S[1]).max() < 1e-13
 
 
+def umeyama_min_error(P, Q, w):
+    """Umeyama (1991): the minimum over (s, R, t) of (1/W) sum w |s R p + t - q|^2
+    is sigma_q^2 - (d1 + d2 + e d3)^2 / sigma_p^2, with d1 >= d2 >= d3 the
+    singular values of the weighted cross-covariance and e the sign of its
+    determinant.  No residual is evaluated; the singular values come from the
+    eigenvalues of C^T C."""
+    W = w.sum()
+    mp, mq = (w[:, None] * P).sum(0) / W, (w[:, None] * Q).sum(0) / W
+    Pc, Qc = P - mp, Q - mq
+    vp = (w * (Pc * Pc).sum(1)).sum() / W
+    vq = (w * (Qc * Qc).sum(1)).sum() / W
+    C = (w[:, None] * Qc).T @ Pc / W
+    d = np.sqrt(np.clip(np.linalg.eigvalsh(C.T @ C), 0.0, None))[::-1]
+    e = 1.0 if np.linalg.det(C) >= 0 else -1.0
+    return vq - (d[0] + d[1] + e * d[2]) ** 2 / vp
+
+
+@pytest.mark.parametrize("iters", [1, 4])
+def test_cost_is_umeyamas_minimum_error_for_the_last_weights(iters):
+    """The reported cost is sum omega r(S_K)^2 / sum omega with the weights of
+    the last solve, omega = w min(1, delta / r(S_{K-1})); S_K minimises that
+    weighted error, so the cost is Umeyama's closed-form minimum for omega."""
+    rng = np.random.default_rng(500 + iters)
+    n, delta = 400, 0.05
+    P = cloud(rng, n)
+    Q = sim3.act(rand_sim3(rng), P) + 0.01 * rng.normal(size=(n, 3))
+    out = rng.random(n) < 0.2
+    Q[out] += rng.normal(size=(int(out.sum()), 3))          # outliers far past delta
+    w = rng.uniform(0.1, 2.0, n)
+    res = reg.irls(P, Q, w, delta, iters)
+    assert res["status"] == 0 and len(res["history"]) == iters
+    om = w
+    if iters > 1:
+        s, R, t = res["history"][-2]
+        r = np.linalg.norm(P @ (s * R).T + t - Q, axis=1)
+        assert (r > delta).sum() > 50                        # the Huber branch is taken
+        om = w * np.minimum(1.0, delta / r)
+    ref = umeyama_min_error(P, Q, om)
+    assert ref > 0
+    assert abs(res["cost"] - ref) <= 1e-10 * ref
+
+
 def huber_rho(r, d):
     return np.where(r <= d, 0.5 * r * r, d * r - 0.5 * d * d)
 
