@@ -39,3 +39,37 @@ def test_struct_layouts_match_header():
     o = ec3r.AlignOpts()
     ec3r.lib().ec3r_align_opts_default(ctypes.byref(o))
     assert abs(o.huber_delta - 0.02) < 1e-9 and o.iters == 10 and o.precision == 0
+
+
+def test_noalloc_limits_are_enforced_before_any_device_work():
+    """ec3r_align_submaps_noalloc checks its sizes against the fixed scratch
+    before touching the device, so each limit the header states can be checked
+    on the host: the pointers below are placeholders that are never used."""
+    l = ec3r.lib()
+    f = l.ec3r_align_submaps_noalloc
+    P, I64 = ctypes.c_void_p, ctypes.c_int64
+    f.argtypes = [P, P, I64, I64, ctypes.c_int, I64, P, P, P, P,
+                  ctypes.POINTER(ec3r.AlignOpts), P, P, P, P]
+    f.restype = ctypes.c_int
+    text = open(os.path.join(ROOT, "include", "ec3r.h")).read()
+    lim = {k: int(v) for k, v in re.findall(r"#define EC3R_NOALLOC_(MAX_\w+) (\d+)", text)}
+    assert set(lim) == {"MAX_PAIRS", "MAX_LINKS", "MAX_TILES"}
+    o = ec3r.AlignOpts()
+    l.ec3r_align_opts_default(ctypes.byref(o))
+    x = P(256)
+
+    def call(n_pairs, n_links, hw, opts=o):
+        return f(x, x, 4, hw, n_pairs, n_links, x, x, x, None, ctypes.byref(opts), x, x, None,
+                 None)
+
+    assert call(0, 0, 64) == 0                                     # nothing to do
+    assert call(lim["MAX_PAIRS"] + 1, 1, 64) == 1
+    assert call(1, lim["MAX_LINKS"] + 1, 64) == 1
+    tiles_per_link = lim["MAX_TILES"] // lim["MAX_LINKS"] + 1     # one link more than fits
+    assert call(1, lim["MAX_LINKS"], tiles_per_link * 8192) == 1
+    bad = ec3r.AlignOpts()
+    l.ec3r_align_opts_default(ctypes.byref(bad))
+    bad.iters = 0
+    assert call(1, 1, 64, bad) == 1
+    bad.iters, bad.want_cost = 10, 1                               # cost wanted, no buffer
+    assert call(1, 1, 64, bad) == 1
