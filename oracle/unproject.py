@@ -56,3 +56,27 @@ def project(X, cam):
     x = (np.asarray(X, dtype=np.float64) - t) @ R      # R^T (X - t), row-wise
     z = x[:, 2]
     return fx * x[:, 0] / z + cx, fy * x[:, 1] / z + cy, z
+
+
+def unproject_backward(gX, depth, cams):
+    """Gradient with respect to the depths, given dL/dX of the unprojected points.
+
+    X = R (d r) + t with the pixel's ray r = ((u - cx)/fx, (v - cy)/fy, 1), so
+    dX/dd = R r and dL/dd = (R r) . dL/dX.  A pixel without a point (its depth
+    not finite or not > 0) gets 0.  gX [n, H*W, 3], depth [n, H, W] ->
+    [n, H, W] (float64).  This is the chain rule that carries the registration's
+    adjoint (``oracle.adjoint``) from points back to depth maps.
+    """
+    d = np.asarray(depth, dtype=np.float64)
+    n, H, W = d.shape
+    g = np.asarray(gX, dtype=np.float64).reshape(n, H * W, 3)
+    v, u = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64),
+                       indexing="ij")
+    out = np.zeros((n, H, W))
+    for f in range(n):
+        fx, fy, cx, cy, R, t = camera(cams[f])
+        r = np.stack([(u - cx) / fx, (v - cy) / fy, np.ones_like(u)], -1).reshape(-1, 3)
+        gd = ((r @ R.T) * g[f]).sum(1)
+        ok = (np.isfinite(d[f]) & (d[f] > 0)).reshape(-1)
+        out[f] = np.where(ok, gd, 0.0).reshape(H, W)
+    return out

@@ -105,3 +105,76 @@ def test_source_weight_rule_matches_finite_differences():
         cmm[i] -= h
         fd = (loss_src(cpp) - loss_src(cmm)) / (2 * h)
         assert abs(fd - gcp[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, gcp[i])
+
+
+def depth_problem(seed, H=6, W=10):
+    """Two depth frames of one surface seen from two camera poses (same
+    intrinsics), 1 % depth noise and a few outlier depths."""
+    from oracle import unproject as unp
+    rng = np.random.default_rng(seed)
+    fx, cx, cy = 8.0, (W - 1) / 2.0, (H - 1) / 2.0
+
+    def cam(R, t):
+        return np.concatenate([[fx, fx, cx, cy], R.ravel(), t])[None]
+
+    Rp, Rq = (Rotation.random(random_state=rng).as_matrix() for _ in range(2))
+    tp, tq = rng.normal(size=3), rng.normal(size=3)
+    dp = rng.uniform(1.5, 3.0, (1, H, W))
+    dq = dp * (1 + 0.01 * rng.normal(size=dp.shape))
+    dq[0, 0, :4] *= 1.5
+    cp, cq = rng.lognormal(0, 0.5, H * W), rng.lognormal(0, 0.5, H * W)
+    R_gt = Rq @ Rp.T
+    S_gt = (1.0, R_gt, tq - R_gt @ tp)                  # q = R_gt (p - t_p) + t_q
+    return unp, dp, dq, cam(Rp, tp), cam(Rq, tq), cp, cq, S_gt
+
+
+def test_depth_gradient_matches_finite_differences():
+    """The registration's adjoint carried to the depth maps (dL/dd = (R r) .
+    dL/dX) matches FP64 central differences of the whole chain: unprojection
+    of both frames, Huber-IRLS registration, geodesic loss plus cost."""
+    unp, dp, dq, camp, camq, cp, cq, S_gt = depth_problem(31)
+    delta, iters, lam = 0.05, 10, 1.0
+    w = cp * cq
+
+    def loss_depth(a, b):
+        P, Q = unp.unproject(a, camp)[0], unp.unproject(b, camq)[0]
+        S_, _, cost_ = adj.irls_forward(P, Q, w, delta, iters)
+        return sim3.geodesic_sq(S_gt, S_) + lam * cost_
+
+    P, Q = unp.unproject(dp, camp)[0], unp.unproject(dq, camq)[0]
+    S, tape, cost = adj.irls_forward(P, Q, w, delta, iters)
+    L, gs, gR, gt = adj.geodesic_loss_grad(S, S_gt)
+    gP, gQ, _ = adj.irls_backward(P, Q, w, delta, tape, S, gs, gR, gt, lam)
+    gdp = unp.unproject_backward(gP[None], dp, camp)
+    gdq = unp.unproject_backward(gQ[None], dq, camq)
+    assert np.abs(gdp).max() > 1e-3 and np.abs(gdq).max() > 1e-3
+    near = np.zeros(len(w), bool)
+    for rec in tape[1:]:
+        near |= np.abs(rec["r"] - delta) < 1e-4
+    assert (np.abs(tape[-1]["r"]) > delta).sum() >= 2          # both Huber branches taken
+    h = 1e-6
+    W_ = dp.shape[2]
+    idx = [i for i in range(len(w)) if not near[i]][::4]
+    assert len(idx) >= 10
+    for i in idx:
+        v, u = divmod(i, W_)
+        for which, G in (("p", gdp), ("q", gdq)):
+            a_p, a_m = dp.copy(), dp.copy()
+            b_p, b_m = dq.copy(), dq.copy()
+            if which == "p":
+                a_p[0, v, u] += h
+                a_m[0, v, u] -= h
+            else:
+                b_p[0, v, u] += h
+                b_m[0, v, u] -= h
+            fd = (loss_depth(a_p, b_p) - loss_depth(a_m, b_m)) / (2 * h)
+            assert abs(fd - G[0, v, u]) <= 1e-6 * max(1.0, abs(fd)), (which, v, u, fd, G[0, v, u])
+
+
+def test_depth_gradient_is_zero_where_a_pixel_has_no_point():
+    unp, dp, dq, camp, camq, cp, cq, S_gt = depth_problem(32)
+    d = dp.copy()
+    d[0, 1, 2], d[0, 3, 4], d[0, 5, 9] = 0.0, -1.0, np.nan
+    g = unp.unproject_backward(np.ones((1, d[0].size, 3)), d, camp)
+    assert g[0, 1, 2] == 0.0 and g[0, 3, 4] == 0.0 and g[0, 5, 9] == 0.0
+    assert np.count_nonzero(g) == d[0].size - 3
