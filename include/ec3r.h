@@ -155,7 +155,8 @@ void ec3r_align_opts_default(ec3r_align_opts* o);
  * The call enqueues a set-up kernel, then `iters` x (moment sweep, solve),
  * replayed from a CUDA graph cached per argument set when `stream` is not
  * itself being captured.  Workspace: 152 bytes per tile of 8192 pixels,
- * 4 bytes per link and 320 bytes per pair.
+ * 4 bytes per link, and per pair 424 bytes plus 448 bytes per iteration (the
+ * checkpoints that ec3r_align_submaps_backward reuses).
  */
 ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d_conf,
                                int64_t n_frames, int64_t hw, int n_pairs, int64_t n_links,
@@ -184,11 +185,21 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
  * (d_out, d_pair_status, d_pair_cost) are still unchanged, the backward call
  * uses those checkpoints; otherwise it first re-runs the forward pass itself.
  * It then differentiates all `iters` solves, unrolled (the Huber weights of
- * solve k depend on solve k-1): one reduction sweep per iteration and one
- * final sweep that writes the per-point gradients.  The rotation is
+ * solve k depend on solve k-1): one reduction sweep per Huber iteration
+ * (iters - 1 of them; the sums of the cost term come from the forward's cost
+ * sweep) and one final sweep that writes the per-point gradients.  The rotation is
  * differentiated in its polar form, with 1/(d_i + d_j) factors.  The Huber
  * weight has a kink at r = delta; there the one-sided derivative of the
  * branch taken by the FP32 forward is used.
+ *
+ * Errors: EC3R_ERR_INVALID_ARG (nothing enqueued) for a NULL context, opts,
+ * d_grad_S, d_grad_xyz or d_grad_conf, n_pairs < 0, or opts->precision other
+ * than EC3R_PREC_FP32C; n_pairs = 0 does nothing.  The forward call's own
+ * checks apply when it is re-run.
+ * Workspace (context-owned, beyond the forward's): 96 bytes per tile of 8192
+ * pixels, 32 bytes per link pixel (per-link gradients, summed into frames
+ * that several links share), 348 bytes per pair plus 136 bytes per pair and
+ * iteration, and 4 bytes per frame.
  */
 ec3r_status ec3r_align_submaps_backward(ec3r_ctx* ctx, const float* d_xyz, const float* d_conf,
                                         int64_t n_frames, int64_t hw, int n_pairs,
