@@ -31,6 +31,8 @@ def fuse_points(xyz, conf, poses, threshold=1.0, index_base=0):
     xyz = np.asarray(xyz)
     conf = np.asarray(conf)
     M = xyz.shape[0]
+    if M == 0:                                  # no submap: no point
+        return np.empty((0, 3), dtype=np.float64), np.empty(0, dtype=np.int64)
     xyz = xyz.reshape(M, -1, 3)
     conf = conf.reshape(M, -1)
     n = conf.shape[1]
@@ -66,12 +68,12 @@ def correct_points(points, refs, xyz, conf, poses, threshold=1.0):
     xyz = np.asarray(xyz)
     conf = np.asarray(conf)
     M = xyz.shape[0]
-    xyz = xyz.reshape(M, -1, 3)
-    conf = conf.reshape(M, -1)
-    n = conf.shape[1]
+    n = conf.size // M if M else 0
+    xyz = xyz.reshape(M, n, 3)
+    conf = conf.reshape(M, n)
     count = 0
     for i, g in enumerate(np.asarray(refs, dtype=np.int64)):
-        if g < 0:
+        if g < 0 or g >= M * n:      # none (-1), or no such submap point: unchanged
             continue
         m, k = divmod(int(g), n)
         x = xyz[m, k].astype(np.float64)
@@ -97,6 +99,8 @@ def fuse_points_depth(depth, conf, cams, poses, frames, threshold=1.0, index_bas
     d = np.asarray(depth)
     nfr = d.shape[0]
     M = nfr // frames
+    if M == 0:                                                # no submap: no point
+        return np.empty((0, 3)), np.empty(0, dtype=np.int64)
     X = up.unproject(d, cams).reshape(M, -1, 3)              # [M, frames*H*W, 3]
     c = np.asarray(conf, dtype=np.float64).reshape(M, -1)
     with np.errstate(invalid="ignore"):

@@ -34,6 +34,9 @@ def test_fuse_empty():
     conf = np.zeros((2, 3), np.float32)
     out_xyz, out_idx = fuse.fuse_points(xyz, conf, [(1.0, np.eye(3), np.zeros(3))] * 2)
     assert out_xyz.shape == (0, 3) and out_idx.shape == (0,)
+    out_xyz, out_idx = fuse.fuse_points(np.zeros((0, 3, 3), np.float32),
+                                        np.zeros((0, 3), np.float32), [], index_base=9)
+    assert out_xyz.shape == (0, 3) and out_idx.shape == (0,)
 
 
 def test_point_correction_closed_forms():
@@ -64,6 +67,29 @@ def test_point_correction_closed_forms():
             np.testing.assert_allclose(out[i], 2.5 * xyz[2, k].astype(np.float64), rtol=1e-15)
     assert cnt == sum(1 for g in refs if g >= 0 and conf.reshape(-1)[g] > 1.0 and
                       np.all(np.isfinite(xyz.reshape(-1, 3)[g])))
+
+
+def test_point_correction_out_of_range_and_no_submaps():
+    """A reference below -1 or past the last submap point leaves its point
+    unchanged and is not counted; with no submap every reference is such."""
+    rng = np.random.default_rng(8)
+    M, n = 2, 10
+    xyz = rng.normal(size=(M, n, 3)).astype(np.float32)
+    conf = np.full((M, n), 2.0, np.float32)
+    poses = [(1.0, np.eye(3), np.zeros(3))] * M
+    refs = np.array([-5, M * n, M * n + 3, 7])
+    pts = rng.normal(size=(4, 3))
+    out, cnt = fuse.correct_points(pts, refs, xyz, conf, poses)
+    np.testing.assert_array_equal(out[:3], pts[:3])
+    np.testing.assert_array_equal(out[3], xyz[0, 7].astype(np.float64))
+    assert cnt == 1
+    out, cnt = fuse.correct_points(pts, refs, np.zeros((0, n, 3), np.float32),
+                                   np.zeros((0, n), np.float32), [])
+    np.testing.assert_array_equal(out, pts)
+    assert cnt == 0
+    ox, oi = fuse.fuse_points_depth(np.zeros((0, 2, 3)), np.zeros((0, 2, 3)), np.zeros((0, 16)),
+                                    [], frames=1)
+    assert ox.shape == (0, 3) and oi.shape == (0,)
 
 
 def test_depth_fusion_closed_forms():

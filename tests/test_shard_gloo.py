@@ -1,4 +1,4 @@
-"""Two gloo ranks on CPU run the sharded path's host logic: balanced pair
+"""Gloo ranks on CPU (2, 3 and 7) run the sharded path's host logic: balanced pair
 partition, registration of each shard (the FP64 oracle stands in for the
 GPU, which this host lacks), gather of the Sim(3) rows on rank 0, fusion of
 each rank's submaps with offsets from one all-gathered count, and the
@@ -68,12 +68,14 @@ def _worker(rank, world, port, result_path):
 
 
 @pytest.mark.timeout(300)
-def test_two_gloo_ranks_match_single_process(tmp_path):
+@pytest.mark.parametrize("world", [2, 3, 7])
+def test_gloo_ranks_match_single_process(tmp_path, world):
+    """2 ranks: even shares; 3: uneven (5 pairs, 6 submaps); 7: more ranks than
+    submaps, so one rank registers and fuses nothing."""
     from oracle import fuse as ofuse
     from oracle import register as reg
     from paper_2510_02080_b300 import synth
 
-    world = 2
     path = str(tmp_path / "res.pt")
     mp.start_processes(_worker, args=(world, _free_port(), path), nprocs=world, join=True,
                        start_method="spawn")
@@ -86,4 +88,4 @@ def test_two_gloo_ranks_match_single_process(tmp_path):
     _, ref_idx = ofuse.fuse_points(ch.xyz.view(ch.M, -1, 3).numpy(), ch.conf.view(ch.M, -1).numpy(),
                                    [(1.0, np.eye(3), np.zeros(3))] * ch.M, 1.0)
     assert np.array_equal(got["idx"].numpy(), ref_idx)
-    assert got["t"] == 2.0
+    assert got["t"] == float(world)
