@@ -54,3 +54,32 @@ def test_pose_graph_measurements_noise_free_are_consistent():
         M = (float(g.T_meas.s[k]), g.T_meas.R[k].numpy(), g.T_meas.t[k].numpy())
         C = sim3.compose(T[i], M)
         assert abs(C[0] / T[j][0] - 1) < 1e-12 and np.abs(C[1] - T[j][1]).max() < 1e-12
+
+
+def test_chain_follows_the_stated_recipe():
+    """Confidences log-normal(0, 0.5); every frame's points replaced by uniform
+    box points with probability 0.1, so a correspondence (two frames) is an
+    outlier with probability 1 - 0.9^2 = 0.19 under the true transform; inlier
+    residuals are the N(0, sigma^2) noise of both points (the source's scaled by
+    s); submap scales in [0.5, 2]."""
+    sigma = 0.01
+    ch = synth.make_chain(5, M=4, F=5, H=40, W=60, sigma=sigma, outlier_frac=0.1)
+    lc = torch.log(ch.conf.double()).reshape(-1)
+    assert abs(float(lc.mean())) < 0.02 and abs(float(lc.std()) - 0.5) < 0.02
+    lam = 1.0 / ch.T_gt.s.double()
+    assert float(lam.min()) >= 0.5 and float(lam.max()) <= 2.0
+    ps = ch.pairs()
+    truth = synth.chain_pair_truth(ch)
+    out, inl = [], []
+    for m in range(ps.n_pairs):
+        p = ps.xyz[int(ps.src[m])].double().numpy()
+        q = ps.xyz[int(ps.tgt[m])].double().numpy()
+        s = float(truth.s[m])
+        r = sim3.act((s, truth.R[m].numpy(), truth.t[m].numpy()), p) - q
+        d = np.linalg.norm(r, axis=1)
+        far = d > 20 * sigma * (1 + s)
+        out.append(far.mean())
+        inl.append(r[~far] / (sigma * np.sqrt(1 + s * s)))    # unit normal per coordinate
+    assert abs(float(np.mean(out)) - 0.19) < 0.02
+    z = np.concatenate(inl).reshape(-1)
+    assert abs(z.mean()) < 0.02 and abs(z.std() - 1.0) < 0.03
