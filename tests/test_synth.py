@@ -83,3 +83,30 @@ def test_chain_follows_the_stated_recipe():
     assert abs(float(np.mean(out)) - 0.19) < 0.02
     z = np.concatenate(inl).reshape(-1)
     assert abs(z.mean()) < 0.02 and abs(z.std() - 1.0) < 0.03
+
+
+def test_depth_chain_follows_the_stated_recipe():
+    """Depth frames: pinhole intrinsics fx = fy, cx = W/2 - 1/2, cy = H/2 - 1/2
+    and an orthonormal camera -> submap rotation; the shared keyframe,
+    unprojected in both submaps, agrees under the true transform except where a
+    depth was replaced by an outlier (probability 0.1 per frame, so about 0.19
+    of the correspondences)."""
+    from oracle import unproject as unp
+    H, W, sigma = 30, 48, 0.01
+    ch = synth.make_depth_chain(6, M=4, F=5, H=H, W=W, sigma=sigma, outlier_frac=0.1)
+    cams = ch.cams.double().reshape(-1, 16).numpy()
+    assert np.all(cams[:, 0] == cams[:, 1]) and np.all(cams[:, 0] > 0)
+    assert np.all(cams[:, 2] == W / 2 - 0.5) and np.all(cams[:, 3] == H / 2 - 0.5)
+    R = cams[:, 4:13].reshape(-1, 3, 3)
+    assert np.abs(R @ R.transpose(0, 2, 1) - np.eye(3)).max() < 1e-6
+    dps = ch.pairs()
+    truth = synth.chain_pair_truth(ch)
+    far = []
+    for m in range(dps.n_pairs):
+        a, b = int(dps.src[m]), int(dps.tgt[m])
+        p = unp.unproject(dps.depth[a:a + 1].numpy(), dps.cams[a:a + 1].numpy())[0]
+        q = unp.unproject(dps.depth[b:b + 1].numpy(), dps.cams[b:b + 1].numpy())[0]
+        s = float(truth.s[m])
+        d = np.linalg.norm(sim3.act((s, truth.R[m].numpy(), truth.t[m].numpy()), p) - q, axis=1)
+        far.append(np.mean(d > 0.2 * (1 + s)))
+    assert abs(float(np.mean(far)) - 0.19) < 0.03
