@@ -110,3 +110,19 @@ def test_depth_chain_follows_the_stated_recipe():
         d = np.linalg.norm(sim3.act((s, truth.R[m].numpy(), truth.t[m].numpy()), p) - q, axis=1)
         far.append(np.mean(d > 0.2 * (1 + s)))
     assert abs(float(np.mean(far)) - 0.19) < 0.03
+
+
+def test_keyframe_embeddings_follow_the_stated_kernel():
+    """Random Fourier features average to the Gaussian kernel and the noise
+    adds noise^2 to each squared norm, so keyframes j apart on the route
+    (distance 0.1 j) have mean cosine exp(-(0.1 j)^2 / (2 x 0.35^2)) /
+    (1 + 0.15^2); the second lap passes the first lap's places again."""
+    n = 2048
+    E = synth.make_keyframe_embeddings(9, n=n, d=1024).double()
+    U = E / E.norm(dim=1, keepdim=True)
+    for j in (1, 3, 6, 12):
+        got = float((U[:-j] * U[j:]).sum(1).mean())
+        want = np.exp(-(0.1 * j) ** 2 / (2 * 0.35 ** 2)) / (1 + 0.15 ** 2)
+        assert abs(got - want) < 0.02, (j, got, want)
+    same_place = (U[: n // 2] * U[n // 2:]).sum(1)           # lap 1 vs lap 2
+    assert float(same_place.mean()) > 0.75
