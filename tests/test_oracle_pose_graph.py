@@ -61,6 +61,19 @@ def test_exp_log_round_trip_and_group_laws():
     assert close(sim3.compose(sim3.exp(0.3 * xi), sim3.exp(0.7 * xi)), sim3.exp(xi), 1e-12)
 
 
+@pytest.mark.parametrize("angle", [1e-9, 1e-4, 1.0, 3.0, np.pi - 1e-6])
+@pytest.mark.parametrize("sigma", [0.0, 1e-9, 0.7, -1.2])
+def test_exp_log_round_trip_at_extreme_angles_and_scales(angle, sigma):
+    """Log(Exp(xi)) = xi from a vanishing rotation to one just short of pi, and
+    from unit scale (sigma = 0, where the translation series degenerates) to
+    strong shrinking and growth."""
+    rng = np.random.default_rng(int(angle * 1e3) + int(sigma * 10) + 50)
+    axis = rng.normal(size=3)
+    axis /= np.linalg.norm(axis)
+    xi = np.concatenate([2.0 * rng.normal(size=3), angle * axis, [sigma]])
+    assert np.abs(sim3.log(sim3.exp(xi)) - xi).max() < 1e-12
+
+
 def random_graph(rng, n, loops, noise=0.0):
     T = [sim3.identity()] + [rand_sim3(rng, 2.0) for _ in range(n - 1)]
     ei = list(range(n - 1))
