@@ -166,7 +166,7 @@ def _oracle_workload_inproc(name):
         opg.gauss_newton(init, ei, ej, Tij, iters=1)
         return 1e3 * (time.perf_counter() - t0)
 
-    out = {"unit": UNIT, "cores": 1, "kind": "oracle"}
+    out = {"unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle"}
     if name == "pair1":
         ps = synth.make_pair(synth.SEED_BASE + 1, H=294, W=518, sigma=0.005, device="cpu")
         rate, dt = reg_rate(ps)
@@ -267,7 +267,8 @@ def run_reference(args):
             "data": "synthetic", "impl": "reference",
             "config": {"workload": "chain200_294x518", "sample_pairs_per_step": npairs,
                        "iters": ITERS, "delta": DELTA},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1,
+                             "host_cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{npairs} of the 199 chain pairs per step (152,292 "
                                        f"correspondences each, 10 IRLS solves), FP64 numpy, "
                                        f"1 thread"},
@@ -561,7 +562,8 @@ def run_ours(args):
     if e2e:
         line["e2e"] = e2e
     if cpu_rate is not None:
-        line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": 1,
+                                "host_cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{np_cpu} chain pairs x 152,292 correspondences x "
                                           f"{ITERS} IRLS solves, FP64 numpy, 1 thread "
                                           f"({dt_cpu:.1f} s)"}
