@@ -1,0 +1,49 @@
+"""The reference arm of bench.py (the FP64 oracle timed on the host) keeps the
+one-JSON-line contract: the keys, their types and the ones fixed by the
+contract (impl, cpu_baseline, an e2e with zero copies), on the same metric and
+workload as the GPU arm; under a multi-rank launch only rank 0 prints."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def run_bench(*args, env=None):
+    e = dict(os.environ)
+    e.update(env or {})
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args],
+                       cwd=ROOT, env=e, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+@pytest.mark.timeout(600)
+def test_reference_arm_prints_one_contract_line():
+    lines = run_bench("--impl", "reference", "--steps", "1", "--warmup", "0")
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key, typ in (("metric", str), ("value", float), ("unit", str), ("n_gpus", int),
+                     ("steps", int), ("warmup", int), ("ms_per_step", float),
+                     ("higher_is_better", bool), ("scaling", str), ("dtype", str),
+                     ("data", str), ("config", dict), ("cpu_baseline", dict), ("e2e", dict)):
+        assert isinstance(d[key], typ), key
+    assert d["impl"] == "reference" and d["vs_baseline"] is None
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["unit"] == "pt-iter/s" and d["value"] > 0
+    assert d["config"]["workload"] == "chain200_294x518"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] == 1
+    assert cb["host_cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+@pytest.mark.timeout(600)
+def test_reference_arm_other_ranks_print_nothing():
+    lines = run_bench("--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
+                      env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert lines == []
