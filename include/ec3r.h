@@ -86,6 +86,27 @@ const char* ec3r_version(void);
 ec3r_status ec3r_sync_status(ec3r_ctx* ctx, void* stream);
 
 /*
+ * Bounded waits.  A kernel that waits on work of other CTAs or on its own
+ * asynchronous copies (the persistent registration's per-pair solves, the
+ * tensor-core similarity's mbarriers) gives up after a limit, raises
+ * EC3R_ERR_TIMEOUT at ec3r_sync_status and returns; the context stays usable.
+ * ec3r_set_wait_limit sets that limit in seconds (0: the default of two
+ * seconds; at most 3600) for later calls of this context.
+ *
+ * ec3r_inject makes such a wait run out on purpose, for tests of that path
+ * (no fault, trap or unbounded wait is involved): EC3R_INJECT_LOOPS_NO_COPY -
+ * the similarity kernel's producer starts no copy, so its MMA thread's first
+ * wait gives up; EC3R_INJECT_ALIGN_NO_EPOCH - the registration's solves publish
+ * no epoch, so the next sweep's waits give up.  0 turns injection off.  Both
+ * calls drop the context's cached graphs.  EC3R_ERR_INVALID_ARG for a bad
+ * value.
+ */
+#define EC3R_INJECT_LOOPS_NO_COPY 1u
+#define EC3R_INJECT_ALIGN_NO_EPOCH 2u
+ec3r_status ec3r_set_wait_limit(ec3r_ctx* ctx, double seconds);
+ec3r_status ec3r_inject(ec3r_ctx* ctx, unsigned what);
+
+/*
  * Tracing.  With profiling on, calls launch their kernels directly (no cached
  * graph) and bracket every kernel launch with a CUDA event pair recorded on
  * the launching stream.  ec3r_profile_read waits for those events, returns
@@ -132,10 +153,11 @@ void ec3r_align_opts_default(ec3r_align_opts* o);
  * d_src[l] (a point p_i of the current submap) and pixel i of frame
  * d_tgt[l] (its counterpart q_i in the other submap) are the same keyframe
  * pixel: the correspondences of Sec. III-C.  Frame indices must lie in
- * [0, n_frames).  Out-of-range offsets or frames mark the pair
- * EC3R_PAIR_BAD_INPUT (nothing out of range is read) and raise
- * EC3R_ERR_INVALID_ARG at ec3r_sync_status.  A pair with no link is
- * degenerate (EC3R_PAIR_FEW_POINTS).
+ * [0, n_frames).  Offsets that do not form such an array (out of range,
+ * decreasing anywhere, wrong first or last value) mark every pair of the call
+ * EC3R_PAIR_BAD_INPUT; a link with an out-of-range frame marks its pair.
+ * Nothing out of range is read, and either case raises EC3R_ERR_INVALID_ARG at
+ * ec3r_sync_status.  A pair with no link is degenerate (EC3R_PAIR_FEW_POINTS).
  *
  * Weights.  Correspondence i is valid when p_i, q_i, c_p, c_q are finite and
  * c_p > cmin and c_q > cmin, where cmin = d_pair_conf_min[k] if that
@@ -152,11 +174,30 @@ void ec3r_align_opts_default(ec3r_align_opts* o);
  * [n_pairs]) receives sum omega r(S)^2 / sum omega with the last weights
  * when opts->want_cost is set.
  *
- * The call enqueues a set-up kernel, then `iters` x (moment sweep, solve),
- * replayed from a CUDA graph cached per argument set when `stream` is not
- * itself being captured.  Workspace: 152 bytes per tile of 8192 pixels,
- * 4 bytes per link, and per pair 424 bytes plus 448 bytes per iteration (the
- * checkpoints that ec3r_align_submaps_backward reuses).
+ * Launches.  A set-up kernel, then, with FP32 moments, one persistent launch
+ * that runs every sweep and solve: tiles of pixels are handed out iteration
+ * by iteration to resident CTAs, the CTA that completes a pair's tiles of an
+ * iteration solves that pair, and a pair's next sweep waits only for its own
+ * solve (a bounded wait: one that runs out raises EC3R_ERR_TIMEOUT at
+ * ec3r_sync_status).  With FP64 accumulation, `iters` x (sweep, solve) grids.
+ * Replayed from a CUDA graph cached per argument set when `stream` is not
+ * itself being captured.
+ *
+ * Variants.  The FP32 launch has variants (pixels per tile x CTAs per SM,
+ * ec3r_align_variant_info).  The tile size groups the FP32 sums, so results
+ * of different variants differ at FP32 rounding level; each variant is
+ * deterministic.  Unless one is forced (ec3r_align_set_variant), the first
+ * call of each problem-size bucket (the power of two of the link pixels and
+ * of the pair count) on 16-byte aligned pointmaps with hw a multiple of 4
+ * times every variant on its own inputs - three runs each after a warm-up,
+ * synchronising with `stream` - and the fastest serves the bucket from then
+ * on; such a first call must not be made while `stream` is captured (a
+ * captured first call uses variant 0 untimed).  Other pointmaps use one fixed
+ * configuration.
+ *
+ * Workspace: 152 bytes per 4096 link pixels, 4 bytes per link, and per pair
+ * 444 bytes plus 448 bytes per iteration (the checkpoints that
+ * ec3r_align_submaps_backward reuses).
  */
 ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d_conf,
                                int64_t n_frames, int64_t hw, int n_pairs, int64_t n_links,
@@ -179,11 +220,19 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
  * in link order (deterministic).  Invalid correspondences and degenerate pairs
  * get zero.
  *
- * Checkpoints.  The forward call keeps, in its context, the estimate and the
- * moments of every solve.  If the last ec3r_align_submaps call on this context
- * had exactly these inputs and options with want_cost = 1, and its outputs
- * (d_out, d_pair_status, d_pair_cost) are still unchanged, the backward call
- * uses those checkpoints; otherwise it first re-runs the forward pass itself.
+ * Checkpoints.  Every ec3r_align_submaps call keeps, in its context, the
+ * estimate and the moments of every solve, each pair's final status and its
+ * cost, and issues a new token (ec3r_align_token).  With fwd_token = 0 the
+ * backward call first runs the forward pass itself (into context-owned
+ * outputs) and uses its checkpoints: always correct.  With fwd_token = the
+ * token of the last ec3r_align_submaps call on this context, the backward
+ * call reuses that call's checkpoints instead; that call must have had the
+ * same inputs (pointers and sizes) and options, and want_cost = 1 if
+ * d_grad_cost is given, else EC3R_ERR_INVALID_ARG (nothing enqueued).  By
+ * passing a token the caller asserts that the frames, confidences, links and
+ * thresholds have not been modified since that call (the library cannot see
+ * an in-place rewrite); that call's output buffers are never read, so they
+ * may have been freed or reused.
  * It then differentiates all `iters` solves, unrolled (the Huber weights of
  * solve k depend on solve k-1): one reduction sweep per Huber iteration
  * (iters - 1 of them; the sums of the cost term come from the forward's cost
@@ -193,9 +242,10 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
  * branch taken by the FP32 forward is used.
  *
  * Errors: EC3R_ERR_INVALID_ARG (nothing enqueued) for a NULL context, opts,
- * d_grad_S, d_grad_xyz or d_grad_conf, n_pairs < 0, or opts->precision other
- * than EC3R_PREC_FP32C; n_pairs = 0 does nothing.  The forward call's own
- * checks apply when it is re-run.
+ * d_grad_S, d_grad_xyz or d_grad_conf, n_pairs < 0, opts->precision other
+ * than EC3R_PREC_FP32C, or a fwd_token that does not qualify (above);
+ * n_pairs = 0 does nothing.  The forward call's own checks apply when it is
+ * run with fwd_token = 0.
  * Workspace (context-owned, beyond the forward's): 96 bytes per tile of 8192
  * pixels, 32 bytes per link pixel (per-link gradients, summed into frames
  * that several links share), 348 bytes per pair plus 136 bytes per pair and
@@ -206,8 +256,31 @@ ec3r_status ec3r_align_submaps_backward(ec3r_ctx* ctx, const float* d_xyz, const
                                         int64_t n_links, const int32_t* d_link_off,
                                         const int32_t* d_src, const int32_t* d_tgt,
                                         const float* d_pair_conf_min, const ec3r_align_opts* opts,
-                                        const double* d_grad_S, const double* d_grad_cost,
-                                        float* d_grad_xyz, float* d_grad_conf, void* stream);
+                                        uint64_t fwd_token, const double* d_grad_S,
+                                        const double* d_grad_cost, float* d_grad_xyz,
+                                        float* d_grad_conf, void* stream);
+
+/*
+ * Sweep variants of ec3r_align_submaps (FP32 moments): their count, and for
+ * variant v its tile size (pixels) and CTAs per SM (EC3R_ERR_INVALID_ARG for v
+ * out of range).  ec3r_align_set_variant forces variant v for every later
+ * call on the context, or, with v = -1 (the default), lets each size bucket
+ * use the variant its first call timed fastest.  ec3r_align_last_variant gives
+ * the variant of the last call (-1: a mode without variants) and, if ms is not
+ * NULL (float [ec3r_align_variant_count()]), every variant's median time in ms
+ * from the timing of that call's bucket (-1 where none was measured).
+ */
+int ec3r_align_variant_count(void);
+ec3r_status ec3r_align_variant_info(int v, int* tile_pixels, int* ctas_per_sm);
+ec3r_status ec3r_align_set_variant(ec3r_ctx* ctx, int v);
+ec3r_status ec3r_align_last_variant(const ec3r_ctx* ctx, int* variant, float* ms);
+
+/*
+ * Token of the last successful ec3r_align_submaps call on this context (a new
+ * nonzero value per call; 0 if there is none, or if the last call failed),
+ * for ec3r_align_submaps_backward.  NULL context: 0.
+ */
+uint64_t ec3r_align_token(const ec3r_ctx* ctx);
 
 /*
  * Registration without allocation.  The paper has no counterpart: this entry

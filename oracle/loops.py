@@ -66,6 +66,16 @@ def unit_rows(E):
     return En / np.linalg.norm(En, axis=1, keepdims=True)
 
 
+def cosine_rows(E, stride, rows):
+    """The exact cosines of the sampled keyframes (the similarity Sec. III-D
+    thresholds), rows `rows` (sample indices) against every sample: the
+    float32 embeddings taken as they are, everything else in float64.  The
+    tensor-core contraction approximates this in BF16 (coarse_similarity_rows
+    gives its exact value)."""
+    U = unit_rows(np.asarray(E)[::stride])
+    return U[np.asarray(rows)] @ U.T
+
+
 def best_neighbour(En, ka, kb, radius, gap):
     """The neighbourhood search of one coarse pair with keyframes ka < kb over
     unit embeddings En: (best similarity, i, j), ties to the smallest i, then

@@ -18,6 +18,9 @@
 //                          Newton-polar refinement), scale, translation
 //
 // The sweep is bandwidth-bound: it reads 32 bytes per pixel (p, q, c_p, c_q).
+#include <algorithm>
+#include <vector>
+
 #include "align_impl.cuh"
 
 namespace ec3r {
@@ -31,15 +34,15 @@ __global__ void __launch_bounds__(THREADS) k_setup(
     int n_pairs, int64_t n_links, const int32_t* __restrict__ link_off,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
     const float* __restrict__ pair_cmin, float cmin_default, int32_t* __restrict__ link_pair,
-    PairState* __restrict__ st, unsigned* flags) {
+    const int32_t* __restrict__ malformed, PairState* __restrict__ st, unsigned* flags,
+    ec3r_sim3* __restrict__ out, int32_t* __restrict__ status_out, double* __restrict__ cost,
+    double* __restrict__ cost_sums) {
   const int k = blockIdx.x;
   __shared__ int bad;
   __shared__ float red[THREADS / 32][7];
-  const int64_t l0 = link_off[k], l1 = link_off[k + 1];
-  if (threadIdx.x == 0) {
-    bad = (l0 < 0 || l1 < l0 || l1 > n_links || (k == 0 && l0 != 0) ||
-           (k == n_pairs - 1 && l1 != n_links));
-  }
+  // a malformed offset array (k_check_offsets) marks every pair of the batch
+  const int64_t l0 = *malformed ? 0 : link_off[k], l1 = *malformed ? 0 : link_off[k + 1];
+  if (threadIdx.x == 0) bad = *malformed;
   __syncthreads();
   if (!bad) {
     for (int64_t l = l0 + threadIdx.x; l < l1; l += THREADS) {
@@ -97,9 +100,19 @@ __global__ void __launch_bounds__(THREADS) k_setup(
       S.bd[i] = S.bdp[i] = 0.0;
     }
     S.cmin = cmin;
-    S.active = bad ? 0 : 1;
-    S.status = bad ? (int)EC3R_PAIR_BAD_INPUT : 0;
+    // A pair without links is degenerate before any solve: with a bad one it
+    // is final here (identity, status, zero cost), since no solve runs for it.
+    const int status = bad ? (int)EC3R_PAIR_BAD_INPUT : (l1 == l0 ? (int)EC3R_PAIR_FEW_POINTS : 0);
+    S.active = status ? 0 : 1;
+    S.status = status;
     if (bad) atomicOr(flags, FLAG_BAD_INDEX);
+    if (status) {
+      write_identity(&out[k]);
+      status_out[k] = status;
+      if (cost) cost[k] = 0.0;
+      if (cost_sums)
+        for (int i = 0; i < CS_STRIDE; ++i) cost_sums[(size_t)k * CS_STRIDE + i] = 0.0;
+    }
   }
 }
 
@@ -291,102 +304,219 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "bad ec3r_align_opts");
   if (opts->want_cost && !d_pair_cost)
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "want_cost set but d_pair_cost is NULL");
-  const int64_t tpl = (hw + TILE - 1) / TILE;
-  const int64_t n_tiles = n_links * tpl;
-  if (n_tiles >= ((int64_t)1 << 31) || n_frames > ((int64_t)1 << 40) / hw)
+  // the smallest tile of any variant bounds the tile count
+  const int64_t tpl_max = (hw + reg_min_tile() - 1) / reg_min_tile();
+  const int64_t n_tiles_max = n_links * tpl_max;
+  if (n_tiles_max >= ((int64_t)1 << 31) || n_frames > ((int64_t)1 << 40) / hw)
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "problem too large for one call");
   EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  void *p_state, *p_part, *p_lp;
+  void *p_state, *p_part, *p_lp, *p_ck, *p_cs, *p_ctl;
   ec3r_status st;
-  if ((st = ensure_buf(ctx, "align.state", sizeof(PairState) * (size_t)n_pairs, s, &p_state)))
+  const size_t ctl_bytes = reg_ctl_bytes(n_pairs);
+  if ((st = ensure_buf(ctx, "align.state", sizeof(PairState) * (size_t)n_pairs, s, &p_state)) ||
+      (st = ensure_buf(ctx, "align.partials", sizeof(double) * NMOM * (size_t)(n_tiles_max + 1),
+                       s, &p_part)) ||
+      // link -> pair map, then one word for the verdict of k_check_offsets
+      (st = ensure_buf(ctx, "align.link_pair", sizeof(int32_t) * (size_t)(n_links + 2), s,
+                       &p_lp)) ||
+      (st = ensure_buf(ctx, "align.ckpt",
+                       sizeof(double) * CKPT * (size_t)n_pairs * (size_t)opts->iters, s, &p_ck)) ||
+      (st = ensure_buf(ctx, "align.cost_sums", sizeof(double) * CS_STRIDE * (size_t)n_pairs, s,
+                       &p_cs)) ||
+      (st = ensure_buf(ctx, "align.ctl", ctl_bytes, s, &p_ctl)))
     return st;
-  if ((st = ensure_buf(ctx, "align.partials", sizeof(double) * NMOM * (size_t)(n_tiles + 1), s,
-                       &p_part)))
-    return st;
-  if ((st = ensure_buf(ctx, "align.link_pair", sizeof(int32_t) * (size_t)(n_links + 1), s,
-                       &p_lp)))
-    return st;
-  void* p_ck;
-  if ((st = ensure_buf(ctx, "align.ckpt",
-                       sizeof(double) * CKPT * (size_t)n_pairs * (size_t)opts->iters, s, &p_ck)))
-    return st;
+  // (buffers that grew dropped the graphs holding older ones; re-read them all)
   PairState* state = (PairState*)ctx->bufs["align.state"].ptr;
   double* partials = (double*)ctx->bufs["align.partials"].ptr;
   int32_t* link_pair = (int32_t*)ctx->bufs["align.link_pair"].ptr;
-  double* ckpt = (double*)p_ck;
-  void* p_cs;
-  if ((st = ensure_buf(ctx, "align.cost_sums", sizeof(double) * NCS * (size_t)n_pairs, s,
-                       &p_cs)))
-    return st;
-  double* cost_sums = (double*)p_cs;
+  double* ckpt = (double*)ctx->bufs["align.ckpt"].ptr;
+  double* cost_sums = (double*)ctx->bufs["align.cost_sums"].ptr;
+  void* ctl = ctx->bufs["align.ctl"].ptr;
   const bool vec =
       (hw % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0) && ((uintptr_t)d_conf % 16 == 0);
   const bool fp64 = opts->precision == EC3R_PREC_FP64;
   const ec3r_align_opts o = *opts;
-  const std::string key = key_of(
-      "align", {(uint64_t)d_xyz, (uint64_t)d_conf, (uint64_t)n_frames, (uint64_t)hw,
-                (uint64_t)n_pairs, (uint64_t)n_links, (uint64_t)d_link_off, (uint64_t)d_src,
-                (uint64_t)d_tgt, (uint64_t)d_pair_conf_min, fbits(o.huber_delta),
-                (uint64_t)o.iters, fbits(o.conf_min), (uint64_t)o.weight_rule,
-                (uint64_t)o.precision, (uint64_t)o.want_cost, (uint64_t)d_out,
-                (uint64_t)d_pair_status, (uint64_t)d_pair_cost});
-  // remember this call: a backward call with the same inputs reuses its checkpoints
-  ctx->align_key = key_of("fwd", {(uint64_t)d_xyz, (uint64_t)d_conf, (uint64_t)n_frames,
-                                  (uint64_t)hw, (uint64_t)n_pairs, (uint64_t)n_links,
-                                  (uint64_t)d_link_off, (uint64_t)d_src, (uint64_t)d_tgt,
-                                  (uint64_t)d_pair_conf_min, fbits(o.huber_delta),
-                                  (uint64_t)o.iters, fbits(o.conf_min), (uint64_t)o.weight_rule,
-                                  (uint64_t)o.precision, (uint64_t)o.want_cost});
-  ctx->align_out = d_out;
-  ctx->align_status = d_pair_status;
-  ctx->align_cost = d_pair_cost;
-  return run_graph(ctx, key, s, [&](cudaStream_t cs) -> ec3r_status {
+  int32_t* malformed = link_pair + n_links + 1;
+  // This call overwrites the workspace that an earlier token refers to.
+  ctx->align_token = 0;
+
+  // set-up, then every sweep and solve in one persistent launch
+  auto enqueue = [&](cudaStream_t cs, int v) -> ec3r_status {
     EC3R_CUDA_TRY(ctx, cudaMemsetAsync(link_pair, 0xff, sizeof(int32_t) * (size_t)(n_links + 1),
                                        cs));
     traced(ctx, cs, "align_setup", [&] {
+      k_check_offsets<<<1, 1024, 0, cs>>>(d_link_off, n_pairs, n_links, malformed);
       k_setup<<<n_pairs, THREADS, 0, cs>>>(d_xyz, d_conf, n_frames, hw, n_pairs, n_links,
                                            d_link_off, d_src, d_tgt, d_pair_conf_min,
-                                           o.conf_min, link_pair, state, ctx->d_flags);
+                                           o.conf_min, link_pair, malformed, state,
+                                           ctx->d_flags, d_out, d_pair_status,
+                                           o.want_cost ? d_pair_cost : nullptr, cost_sums);
     });
-    const int solve_blocks = n_pairs;  // one warp per CTA: pairs spread over all SMs' FP64 pipes
-    for (int it = 1; it <= o.iters + (o.want_cost ? 1 : 0); ++it) {
-      const int kind = it == 1 ? FIRST : (it > o.iters ? COST : IRLS);
-      // the cost of a single solve uses h = 1, which a huge delta reproduces
-      const float dl = (kind == COST && o.iters == 1) ? FLT_MAX : o.huber_delta;
-      if (n_tiles > 0) traced(ctx, cs, fp64 ? "irls_sweep_fp64" : "irls_sweep_fp32", [&] {
-        if (fp64) {
+    if (!fp64) {
+      ec3r_status r = EC3R_OK;
+      traced(ctx, cs, "irls_register", [&] {
+        r = launch_register(ctx, cs, v, vec, d_xyz, d_conf, hw, n_pairs, n_links, d_link_off,
+                            d_src, d_tgt, link_pair, state, partials, o.huber_delta,
+                            o.weight_rule, o.iters, d_out, d_pair_status,
+                            o.want_cost ? d_pair_cost : nullptr, cost_sums, ckpt, ctl,
+                            ctl_bytes);
+      });
+      if (r != EC3R_OK) return r;
+      if (o.want_cost) {
+        // the cost sweep (weights of S_{K-1}, residuals under S_K) as its own
+        // grid, then the cost and the adjoint's cost-term sums per pair
+        const int64_t tpl = (hw + TILE - 1) / TILE;
+        const int64_t n_tiles = n_links * tpl;
+        const float dl = o.iters == 1 ? FLT_MAX : o.huber_delta;
+        if (n_tiles > 0) traced(ctx, cs, "irls_cost_sweep", [&] {
+          if (vec)
+            launch_sweep<float, true>(COST, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
+                                      d_tgt, link_pair, state, dl, o.weight_rule, partials);
+          else
+            launch_sweep<float, false>(COST, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
+                                       d_tgt, link_pair, state, dl, o.weight_rule, partials);
+        });
+        traced(ctx, cs, "irls_cost", [&] {
+          k_cost<<<n_pairs, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
+                                         d_pair_cost, cost_sums);
+        });
+      }
+    } else {
+      // FP64 accumulation (the plain baseline): one grid per sweep and per solve
+      const int64_t tpl = (hw + TILE - 1) / TILE;
+      const int64_t n_tiles = n_links * tpl;
+      for (int it = 1; it <= o.iters + (o.want_cost ? 1 : 0); ++it) {
+        const int kind = it == 1 ? FIRST : (it > o.iters ? COST : IRLS);
+        // the cost of a single solve uses h = 1, which a huge delta reproduces
+        const float dl = (kind == COST && o.iters == 1) ? FLT_MAX : o.huber_delta;
+        if (n_tiles > 0) traced(ctx, cs, "irls_sweep_fp64", [&] {
           if (vec)
             launch_sweep<double, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
                                        d_tgt, link_pair, state, dl, o.weight_rule, partials);
           else
             launch_sweep<double, false>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
                                         d_tgt, link_pair, state, dl, o.weight_rule, partials);
-        } else {
-          if (vec)
-            launch_sweep<float, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
-                                      d_tgt, link_pair, state, dl, o.weight_rule, partials);
-          else
-            launch_sweep<float, false>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
-                                       d_tgt, link_pair, state, dl, o.weight_rule, partials);
-        }
-      });
-      if (kind == COST)
-        traced(ctx, cs, "irls_cost", [&] {
-          k_cost<<<n_pairs, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
-                                         d_pair_cost, cost_sums);
         });
-      else
-        traced(ctx, cs, "sim3_solve", [&] {
-          k_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
-                                                d_out, d_pair_status, it == o.iters, ckpt, it,
-                                                o.iters);
-        });
+        if (kind == COST)
+          traced(ctx, cs, "irls_cost", [&] {
+            k_cost<<<n_pairs, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
+                                           d_pair_cost, cost_sums);
+          });
+        else
+          traced(ctx, cs, "sim3_solve", [&] {
+            k_solve<<<n_pairs, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
+                                            d_out, d_pair_status, it == o.iters, ckpt, it,
+                                            o.iters);
+          });
+      }
     }
     EC3R_CUDA_TRY(ctx, cudaGetLastError());
     return EC3R_OK;
-  });
+  };
+
+  // Variant: forced, or the one timed fastest for this size bucket (FP32
+  // moments on aligned pointmaps; the other modes have one configuration).
+  int v = 0;
+  ctx->align_last_ms.clear();
+  if (!fp64 && vec) {
+    if (ctx->align_force >= 0) {
+      v = ctx->align_force;
+    } else {
+      const int64_t px = n_links * hw;
+      const uint64_t bucket = (uint64_t)(63 - __builtin_clzll((unsigned long long)px)) * 64 +
+                              (uint64_t)(31 - __builtin_clz((unsigned)n_pairs));
+      auto it = ctx->align_tune.find(bucket);
+      if (it != ctx->align_tune.end()) {
+        v = it->second.first;
+        ctx->align_last_ms = it->second.second;
+      } else if (!ctx->profiling && !stream_capturing(s)) {
+        // first call of this size: time every variant on these inputs (this
+        // call therefore synchronises with `stream`)
+        const int nv = reg_variant_count();
+        std::vector<float> ms(nv, 0.f);
+        cudaEvent_t e0, e1;
+        EC3R_CUDA_TRY(ctx, cudaEventCreate(&e0));
+        EC3R_CUDA_TRY(ctx, cudaEventCreate(&e1));
+        ec3r_status tr = EC3R_OK;
+        for (int c = 0; c < nv && tr == EC3R_OK; ++c) {
+          if ((tr = enqueue(s, c))) break;       // warm-up
+          std::vector<float> reps;
+          for (int r = 0; r < 3 && tr == EC3R_OK; ++r) {
+            cudaEventRecord(e0, s);
+            tr = enqueue(s, c);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) tr = EC3R_ERR_CUDA;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            reps.push_back(t);
+          }
+          std::sort(reps.begin(), reps.end());
+          ms[c] = reps.empty() ? 0.f : reps[reps.size() / 2];
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (tr != EC3R_OK) {
+          cudaGetLastError();
+          return set_error(ctx, tr == EC3R_ERR_CUDA ? EC3R_ERR_CUDA : tr,
+                           "timing the registration variants failed");
+        }
+        v = (int)(std::min_element(ms.begin(), ms.end()) - ms.begin());
+        ctx->align_tune[bucket] = {v, ms};
+        ctx->align_last_ms = ms;
+      }
+    }
+  }
+  ctx->align_last_variant = (!fp64 && vec) ? v : -1;
+  const std::string key = key_of(
+      "align", {(uint64_t)d_xyz, (uint64_t)d_conf, (uint64_t)n_frames, (uint64_t)hw,
+                (uint64_t)n_pairs, (uint64_t)n_links, (uint64_t)d_link_off, (uint64_t)d_src,
+                (uint64_t)d_tgt, (uint64_t)d_pair_conf_min, fbits(o.huber_delta),
+                (uint64_t)o.iters, fbits(o.conf_min), (uint64_t)o.weight_rule,
+                (uint64_t)o.precision, (uint64_t)o.want_cost, (uint64_t)d_out,
+                (uint64_t)d_pair_status, (uint64_t)d_pair_cost, (uint64_t)v});
+  const ec3r_status rs = run_graph(ctx, key, s, [&](cudaStream_t cs) { return enqueue(cs, v); });
+  if (rs != EC3R_OK) return rs;
+  // Remember this call: a backward call given its token reuses its checkpoints.
+  ctx->align_args = key_of("fwd", {(uint64_t)d_xyz, (uint64_t)d_conf, (uint64_t)n_frames,
+                                   (uint64_t)hw, (uint64_t)n_pairs, (uint64_t)n_links,
+                                   (uint64_t)d_link_off, (uint64_t)d_src, (uint64_t)d_tgt,
+                                   (uint64_t)d_pair_conf_min, fbits(o.huber_delta),
+                                   (uint64_t)o.iters, fbits(o.conf_min), (uint64_t)o.weight_rule,
+                                   (uint64_t)o.precision});
+  ctx->align_had_cost = o.want_cost != 0;
+  ctx->align_token = ++ctx->align_tokens_issued;
+  return EC3R_OK;
 }
+
+ec3r_status ec3r_align_set_variant(ec3r_ctx* ctx, int v) {
+  if (!ctx) return EC3R_ERR_INVALID_ARG;
+  if (v < -1 || v >= reg_variant_count())
+    return set_error(ctx, EC3R_ERR_INVALID_ARG, "variant %d out of range", v);
+  ctx->align_force = v;
+  return EC3R_OK;
+}
+
+int ec3r_align_variant_count(void) { return reg_variant_count(); }
+
+ec3r_status ec3r_align_variant_info(int v, int* tile_pixels, int* ctas_per_sm) {
+  if (!tile_pixels || !ctas_per_sm || !reg_variant_info(v, tile_pixels, ctas_per_sm))
+    return EC3R_ERR_INVALID_ARG;
+  return EC3R_OK;
+}
+
+ec3r_status ec3r_align_last_variant(const ec3r_ctx* ctx, int* variant, float* ms) {
+  if (!ctx || !variant) return EC3R_ERR_INVALID_ARG;
+  *variant = ctx->align_last_variant;
+  if (ms) {
+    const int nv = reg_variant_count();
+    for (int i = 0; i < nv; ++i)
+      ms[i] = i < (int)ctx->align_last_ms.size() ? ctx->align_last_ms[i] : -1.f;
+  }
+  return EC3R_OK;
+}
+
+uint64_t ec3r_align_token(const ec3r_ctx* ctx) { return ctx ? ctx->align_token : 0; }
 
 }  // extern "C"
 
@@ -410,7 +540,7 @@ namespace align {
 constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t NA_STATE_BYTES = round256(sizeof(PairState) * EC3R_NOALLOC_MAX_PAIRS);
 constexpr size_t NA_PART_BYTES = round256(sizeof(double) * NMOM * EC3R_NOALLOC_MAX_TILES);
-constexpr size_t NA_LP_BYTES = round256(sizeof(int32_t) * (EC3R_NOALLOC_MAX_LINKS + 1));
+constexpr size_t NA_LP_BYTES = round256(sizeof(int32_t) * (EC3R_NOALLOC_MAX_LINKS + 2));
 constexpr size_t NA_FLAG_BYTES = 256;
 constexpr size_t NA_BYTES = NA_STATE_BYTES + NA_PART_BYTES + NA_LP_BYTES + NA_FLAG_BYTES;
 
@@ -487,9 +617,12 @@ extern "C" ec3r_status ec3r_align_submaps_noalloc(
     cudaGetLastError();
     return EC3R_ERR_CUDA;
   }
+  int32_t* malformed = link_pair + n_links + 1;
+  k_check_offsets<<<1, 1024, 0, cs>>>(d_link_off, n_pairs, n_links, malformed);
   k_setup<<<n_pairs, THREADS, 0, cs>>>(d_xyz, d_conf, n_frames, hw, n_pairs, n_links,
                                        d_link_off, d_src, d_tgt, d_pair_conf_min, o.conf_min,
-                                       link_pair, state, flags);
+                                       link_pair, malformed, state, flags, d_out, d_pair_status,
+                                       o.want_cost ? d_pair_cost : nullptr, nullptr);
   const int solve_blocks = n_pairs;  // one warp per CTA: pairs spread over all SMs' FP64 pipes
   for (int it = 1; it <= o.iters + (o.want_cost ? 1 : 0); ++it) {
     const int kind = it == 1 ? FIRST : (it > o.iters ? COST : IRLS);

@@ -77,15 +77,18 @@ __device__ inline void ck_sR(const double* ck, double* s, double* R) {
   for (int i = 0; i < 9; ++i) R[i] = ck[CK_R + i];
 }
 
+// Everything the forward left for the backward is context-owned: a pair was
+// solved iff its state is still active after the last solve, and its cost sits
+// in its cost record (never the caller's output buffers, which may be gone).
 __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ckpt,
-                           const PairState* __restrict__ st, const int32_t* __restrict__ status,
-                           const double* __restrict__ cost, const double* __restrict__ gS,
+                           const PairState* __restrict__ st,
+                           const double* __restrict__ cost_rec, const double* __restrict__ gS,
                            const double* __restrict__ gcost, AdjState* __restrict__ adj,
                            RedParams* __restrict__ rp) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_pairs) return;
   AdjState& a = adj[k];
-  a.active = (status[k] == 0 && st[k].active) ? 1 : 0;
+  a.active = st[k].active ? 1 : 0;
   rp[k].active = a.active;
   a.gs = 0.0;
   for (int i = 0; i < 9; ++i) a.gR[i] = 0.0;
@@ -107,7 +110,7 @@ __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ck
   if (gcost) {
     const double W = ck[CK_MOM + M_W];
     a.gJ = gcost[k] / W;
-    a.gOm = -gcost[k] * cost[k] / W;
+    a.gOm = -gcost[k] * cost_rec[(size_t)k * CS_STRIDE + CS_COST] / W;
   }
 }
 
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
   const double* ck = ckpt + ((size_t)warp * iters + (j - 1)) * CKPT;
   if (have_partials && lane < NRED) {
     if (pair_sums) {  // summed per pair already (the forward's cost sweep)
-      red[wib][lane] = pair_sums[(size_t)warp * NRED + lane];
+      red[wib][lane] = pair_sums[(size_t)warp * CS_STRIDE + lane];
     } else {
       const int64_t t0 = (int64_t)link_off[warp] * tpl, t1 = (int64_t)link_off[warp + 1] * tpl;
       red[wib][lane] = tile_sum<NRED>(partials, t0, t1, lane);
@@ -685,8 +688,8 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
     ec3r_ctx* ctx, const float* d_xyz, const float* d_conf, int64_t n_frames, int64_t hw,
     int n_pairs, int64_t n_links, const int32_t* d_link_off, const int32_t* d_src,
     const int32_t* d_tgt, const float* d_pair_conf_min, const ec3r_align_opts* opts,
-    const double* d_grad_S, const double* d_grad_cost, float* d_grad_xyz, float* d_grad_conf,
-    void* stream) {
+    uint64_t fwd_token, const double* d_grad_S, const double* d_grad_cost, float* d_grad_xyz,
+    float* d_grad_conf, void* stream) {
   if (!ctx) return EC3R_ERR_INVALID_ARG;
   if (!opts || !d_grad_S || !d_grad_xyz || !d_grad_conf)
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
@@ -696,21 +699,30 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
   cudaStream_t s = (cudaStream_t)stream;
   ec3r_align_opts fo = *opts;
   fo.want_cost = 1;
-  // Reuse the checkpoints of the last forward call on this context when it
-  // had these inputs and options (with the cost); otherwise re-run it.
-  const std::string want = key_of(
-      "fwd", {(uint64_t)d_xyz, (uint64_t)d_conf, (uint64_t)n_frames, (uint64_t)hw,
-              (uint64_t)n_pairs, (uint64_t)n_links, (uint64_t)d_link_off, (uint64_t)d_src,
-              (uint64_t)d_tgt, (uint64_t)d_pair_conf_min, fbits(fo.huber_delta),
-              (uint64_t)fo.iters, fbits(fo.conf_min), (uint64_t)fo.weight_rule,
-              (uint64_t)fo.precision, (uint64_t)fo.want_cost});
-  void *p_out, *p_st, *p_cost;
   ec3r_status st;
-  if (ctx->align_key == want && ctx->bufs.count("align.ckpt")) {
-    p_out = ctx->align_out;
-    p_st = ctx->align_status;
-    p_cost = ctx->align_cost;
+  if (fwd_token != 0) {
+    // Reuse the checkpoints of the forward call that issued this token: it must
+    // be the last registration call on this context, with these inputs and
+    // options, and with the cost sweep if the cost has a gradient.
+    const std::string want = key_of(
+        "fwd", {(uint64_t)d_xyz, (uint64_t)d_conf, (uint64_t)n_frames, (uint64_t)hw,
+                (uint64_t)n_pairs, (uint64_t)n_links, (uint64_t)d_link_off, (uint64_t)d_src,
+                (uint64_t)d_tgt, (uint64_t)d_pair_conf_min, fbits(fo.huber_delta),
+                (uint64_t)fo.iters, fbits(fo.conf_min), (uint64_t)fo.weight_rule,
+                (uint64_t)fo.precision});
+    if (fwd_token != ctx->align_token)
+      return set_error(ctx, EC3R_ERR_INVALID_ARG,
+                       "fwd_token %llu is not the token of the last registration call (%llu)",
+                       (unsigned long long)fwd_token, (unsigned long long)ctx->align_token);
+    if (ctx->align_args != want)
+      return set_error(ctx, EC3R_ERR_INVALID_ARG,
+                       "fwd_token's registration call had other inputs or options");
+    if (d_grad_cost && !ctx->align_had_cost)
+      return set_error(ctx, EC3R_ERR_INVALID_ARG,
+                       "d_grad_cost given but fwd_token's call ran without want_cost");
   } else {
+    // No token: run the forward pass here, into context-owned outputs.
+    void *p_out, *p_st, *p_cost;
     if ((st = ensure_buf(ctx, "adj.out", sizeof(ec3r_sim3) * (size_t)n_pairs, s, &p_out)))
       return st;
     if ((st = ensure_buf(ctx, "adj.status", sizeof(int32_t) * (size_t)n_pairs, s, &p_st)))
@@ -764,17 +776,16 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
                      (uint64_t)n_pairs, (uint64_t)n_links, (uint64_t)d_link_off, (uint64_t)d_src,
                      (uint64_t)d_tgt, fbits(delta), (uint64_t)iters, (uint64_t)rule,
                      (uint64_t)d_grad_S, (uint64_t)gcost, (uint64_t)d_grad_xyz,
-                     (uint64_t)d_grad_conf, (uint64_t)p_st, (uint64_t)p_cost, (uint64_t)vec});
+                     (uint64_t)d_grad_conf, (uint64_t)vec});
+  // the cost term's sums (sum g p'^T, sum g at the returned estimate with the
+  // last weights) and the cost come from the forward's cost sweep, per pair
+  const double* cost_sums = (const double*)ctx->bufs["align.cost_sums"].ptr;
   return run_graph(ctx, gkey, s, [&](cudaStream_t cs) -> ec3r_status {
     traced(ctx, cs, "adj_init", [&] {
-      k_adj_init<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, iters, ckpt, state,
-                                                      (const int32_t*)p_st, (const double*)p_cost,
+      k_adj_init<<<(n_pairs + 127) / 128, 128, 0, cs>>>(n_pairs, iters, ckpt, state, cost_sums,
                                                       d_grad_S, d_grad_cost, adj, rp);
     });
-    // the cost term's sums (sum g p'^T, sum g at the returned estimate with
-    // the last weights) come from the forward's cost sweep, per pair
     const bool cost_path = d_grad_cost != nullptr;
-    const double* cost_sums = (const double*)ctx->bufs["align.cost_sums"].ptr;
     traced(ctx, cs, "adj_solve", [&] {
       k_adj_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, iters, iters, d_link_off, (int)tpl, part,
                                                cost_path && n_tiles > 0, 1, ckpt, adj, gM, state,

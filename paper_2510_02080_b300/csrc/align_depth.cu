@@ -65,17 +65,15 @@ __global__ void __launch_bounds__(THREADS) k_setup_depth(
     const ec3r_camera* __restrict__ cams, int64_t n_frames, int W, int64_t hw, int n_pairs,
     int64_t n_links, const int32_t* __restrict__ link_off, const int32_t* __restrict__ src,
     const int32_t* __restrict__ tgt, const float* __restrict__ pair_cmin, float cmin_default,
-    int32_t* __restrict__ link_pair, PairState* __restrict__ st, LinkState* __restrict__ ls,
-    unsigned* flags) {
+    int32_t* __restrict__ link_pair, const int32_t* __restrict__ malformed,
+    PairState* __restrict__ st, LinkState* __restrict__ ls, unsigned* flags) {
   const int k = blockIdx.x;
   __shared__ int bad;
   __shared__ float red[THREADS / 32][7];
   __shared__ float piv[6];
-  const int64_t l0 = link_off[k], l1 = link_off[k + 1];
-  if (threadIdx.x == 0) {
-    bad = (l0 < 0 || l1 < l0 || l1 > n_links || (k == 0 && l0 != 0) ||
-           (k == n_pairs - 1 && l1 != n_links));
-  }
+  // a malformed offset array (k_check_offsets) marks every pair of the batch
+  const int64_t l0 = *malformed ? 0 : link_off[k], l1 = *malformed ? 0 : link_off[k + 1];
+  if (threadIdx.x == 0) bad = *malformed;
   __syncthreads();
   if (!bad) {
     for (int64_t l = l0 + threadIdx.x; l < l1; l += THREADS) {
@@ -489,7 +487,8 @@ extern "C" ec3r_status ec3r_align_submaps_depth(
   if ((st = ensure_buf(ctx, "depth.partials", sizeof(double) * NMOM * (size_t)(n_tiles + 1), s,
                        &p_part)))
     return st;
-  if ((st = ensure_buf(ctx, "depth.link_pair", sizeof(int32_t) * (size_t)(n_links + 1), s,
+  // link -> pair map, then one word for the verdict of k_check_offsets
+  if ((st = ensure_buf(ctx, "depth.link_pair", sizeof(int32_t) * (size_t)(n_links + 2), s,
                        &p_lp)))
     return st;
   if ((st = ensure_buf(ctx, "depth.links", sizeof(LinkState) * (size_t)(n_links + 1), s,
@@ -513,11 +512,13 @@ extern "C" ec3r_status ec3r_align_submaps_depth(
   return run_graph(ctx, key, s, [&](cudaStream_t cs) -> ec3r_status {
     EC3R_CUDA_TRY(ctx, cudaMemsetAsync(link_pair, 0xff, sizeof(int32_t) * (size_t)(n_links + 1),
                                        cs));
+    int32_t* malformed = link_pair + n_links + 1;
     traced(ctx, cs, "depth_setup", [&] {
+      k_check_offsets<<<1, 1024, 0, cs>>>(d_link_off, n_pairs, n_links, malformed);
       k_setup_depth<<<n_pairs, THREADS, 0, cs>>>(d_depth, d_conf, d_cams, n_frames, W, hw,
                                                  n_pairs, n_links, d_link_off, d_src, d_tgt,
-                                                 d_pair_conf_min, o.conf_min, link_pair, state,
-                                                 links, ctx->d_flags);
+                                                 d_pair_conf_min, o.conf_min, link_pair,
+                                                 malformed, state, links, ctx->d_flags);
     });
     for (int it = 1; it <= o.iters + (o.want_cost ? 1 : 0); ++it) {
       const int kind = it == 1 ? FIRST : (it > o.iters ? COST : IRLS);

@@ -16,7 +16,9 @@ constexpr int NMOM = 19;
 enum { M_W = 0, M_SP = 1, M_SQ = 4, M_PP = 7, M_QP = 8, M_COST = 17, M_CNT = 18 };
 // The cost sweep leaves slots 1..16 free and stores there, from CS_SLOT on,
 // the 12 sums of the adjoint's cost term (sum g p'^T row-major, sum g).
-constexpr int CS_SLOT = 1, NCS = 12;
+// Per pair the context keeps those 12 sums and then the cost itself
+// (CS_STRIDE doubles), so the backward never reads the caller's outputs.
+constexpr int CS_SLOT = 1, NCS = 12, CS_COST = NCS, CS_STRIDE = NCS + 1;
 constexpr double RANK_REL_TOL = 1e-4;
 
 struct PairState {
@@ -406,6 +408,7 @@ static __global__ void __launch_bounds__(32) k_cost(int n_pairs,
   __shared__ double red[NMOM];
   if (!st[k].active) {
     if (lane == 0) cost[k] = 0.0;
+    if (cost_sums && lane <= NCS) cost_sums[(size_t)k * CS_STRIDE + lane] = 0.0;
     return;
   }
   const int64_t t0 = (int64_t)link_off[k] * tpl, t1 = (int64_t)link_off[k + 1] * tpl;
@@ -413,10 +416,45 @@ static __global__ void __launch_bounds__(32) k_cost(int n_pairs,
   __syncwarp();
   if (lane == 0) {
     const double w = red[M_W], c = red[M_COST];
-    cost[k] = w > 0.0 ? c / w : 0.0;
+    const double v = w > 0.0 ? c / w : 0.0;
+    cost[k] = v;
+    if (cost_sums) cost_sums[(size_t)k * CS_STRIDE + CS_COST] = v;
   }
-  if (cost_sums && lane < NCS) cost_sums[(size_t)k * NCS + lane] = red[CS_SLOT + lane];
+  if (cost_sums && lane < NCS) cost_sums[(size_t)k * CS_STRIDE + lane] = red[CS_SLOT + lane];
 }
+
+// Checks the link offsets as one CSR array (link_off[0] = 0, non-decreasing,
+// link_off[n_pairs] = n_links) and writes 1 to *malformed if they are not, else
+// 0.  One CTA reads every offset, so that the set-up of every pair sees the
+// same verdict: a malformed batch marks all its pairs, and no two pairs of an
+// accepted batch can claim the same link.
+static __global__ void __launch_bounds__(1024) k_check_offsets(
+    const int32_t* __restrict__ link_off, int n_pairs, int64_t n_links, int32_t* malformed) {
+  int bad = 0;
+  for (int j = threadIdx.x; j < n_pairs; j += blockDim.x) {
+    const int64_t a = link_off[j], b = link_off[j + 1];
+    bad |= (a > b) | (a < 0) | (b > n_links);
+  }
+  if (threadIdx.x == 0) bad |= (link_off[0] != 0) | ((int64_t)link_off[n_pairs] != n_links);
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) *malformed = bad ? 1 : 0;
+}
+
+// The persistent registration with FP32 moments (align_persist.cu): the
+// autotuner's variants and the launch.  Variant v < 0 or out of range means
+// the first (8192-pixel tiles, four CTAs per SM); unaligned pointmaps have one
+// fixed configuration.
+int reg_variant_count();
+bool reg_variant_info(int v, int* tile, int* ctas);
+int reg_min_tile();
+size_t reg_ctl_bytes(int n_pairs);
+ec3r_status launch_register(ec3r_ctx* ctx, cudaStream_t s, int v, bool vec,
+                            const float* xyz, const float* conf, int64_t hw, int n_pairs,
+                            int64_t n_links, const int32_t* link_off, const int32_t* src,
+                            const int32_t* tgt, const int32_t* link_pair, PairState* st,
+                            double* partials, float delta, int rule, int iters,
+                            ec3r_sim3* out, int32_t* status_out, double* cost,
+                            double* cost_sums, double* ckpt, void* ctl, size_t ctl_bytes);
 
 }  // namespace align
 }  // namespace ec3r

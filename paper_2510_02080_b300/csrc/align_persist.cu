@@ -1,0 +1,434 @@
+// Batched Huber-IRLS registration as one persistent launch.
+//
+// The registration of Sec. III-C (Eq. (sim3), weighted Umeyama in Huber IRLS)
+// alternates an HBM-bound moment sweep over every correspondence with a
+// latency-bound FP64 solve per pair.  Launched as separate grids, every solve
+// is a barrier across all pairs: the whole GPU waits for the slowest pair's
+// FP64 solve ten times per call.  Here the sweeps of all iterations are one
+// stream of work items (iteration j, tile t), handed out in that order by an
+// atomic counter to a grid of resident CTAs:
+//
+//   * a CTA sweeps its tile with the pair's current estimate and writes the
+//     tile's 19 FP64 partial moments (fixed slots: deterministic);
+//   * it counts the tile in the pair's completion counter; the CTA that
+//     completes the pair's last tile of iteration j sums the pair's partials
+//     in fixed order and solves (FP64 polar factor, scale, translation), then
+//     publishes the pair's epoch j with a release store;
+//   * a tile of iteration j + 1 first waits (acquire) for its own pair's epoch
+//     j, which its pair's tiles of iteration j - all handed out earlier, to
+//     running CTAs - complete; no CTA ever waits for a CTA that has not started.
+//
+// So each pair's solve runs while other pairs' tiles stream, and only the
+// last pair's last solve is exposed.  Every wait is bounded: past the limit
+// the CTA raises FLAG_TIMEOUT and skips its tile.  The cost sweep (weights
+// from one estimate, residuals under another: twelve more live registers than
+// a Huber sweep) runs after this launch as its own grid, so that the
+// persistent loop fits the register budget of four CTAs per SM.
+//
+// Variants (tile pixels x CTAs per SM) are instantiated for the autotuner;
+// the tile size groups the FP32 sums, so variants differ at FP32 rounding
+// level; each is deterministic (tile partials have fixed slots and are summed
+// in a fixed order, whichever CTA computed them).
+#include "align_impl.cuh"
+
+namespace ec3r {
+namespace align {
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Epoch of a pair that no later sweep works on (degenerate): every wait passes.
+constexpr unsigned EPOCH_DONE = 0xffffffffu;
+
+// Waits until *ep >= want.  Gives up after `limit` cycles or 2^22 polls,
+// whichever comes first, or as soon as another CTA has given up (*abort):
+// then raises FLAG_TIMEOUT, sets *abort so that every other CTA stops too, and
+// returns false.
+__device__ __noinline__ bool wait_epoch(const unsigned* ep, unsigned want, unsigned* abort,
+                                        unsigned* flags, long long limit) {
+  if (ld_acquire_u32(ep) >= want) return true;
+  const long long t0 = clock64();
+  unsigned ns = 32;
+  for (int poll = 0; poll < (1 << 22); ++poll) {
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+    if (ld_acquire_u32(ep) >= want) return true;
+    if (ld_acquire_u32(abort) || clock64() - t0 > limit) break;
+  }
+  atomicOr(flags, FLAG_TIMEOUT);
+  atomicExch(abort, 1u);
+  return false;
+}
+
+// One point's contribution to the moments of Huber-IRLS sweep j: weights
+// from the current estimate S_{j-1} (A, b) around the pair's pivots; moments
+// W, Sp, Sq, Spp, Sqp and the count (the solve uses no cost moment).
+// delta = +inf gives h = 1 exactly (the first sweep: plain weighted moments).
+struct HuberOp {
+  float A[9], b[3], pp[3], pq[3], delta, cmin;
+  int rule;
+
+  __device__ __forceinline__ void operator()(float p0, float p1, float p2, float q0, float q1,
+                                             float q2, float cp, float cq, float* acc) const {
+    const bool v = finitef(p0) && finitef(p1) && finitef(p2) && finitef(q0) && finitef(q1) &&
+                   finitef(q2) && finitef(cp) && finitef(cq) && cp > cmin && cq > cmin;
+    const float x0 = v ? p0 - pp[0] : 0.f, x1 = v ? p1 - pp[1] : 0.f, x2 = v ? p2 - pp[2] : 0.f;
+    const float y0 = v ? q0 - pq[0] : 0.f, y1 = v ? q1 - pq[1] : 0.f, y2 = v ? q2 - pq[2] : 0.f;
+    float w = rule == 0 ? cp * cq : cp;
+    w = v ? w : 0.f;
+    const float e0 = A[0] * x0 + A[1] * x1 + A[2] * x2 + b[0] - y0;
+    const float e1 = A[3] * x0 + A[4] * x1 + A[5] * x2 + b[1] - y1;
+    const float e2 = A[6] * x0 + A[7] * x1 + A[8] * x2 + b[2] - y2;
+    const float rr = e0 * e0 + e1 * e1 + e2 * e2;
+    const float om = w * fminf(1.f, delta * rsqrtf(rr));
+    acc[M_W] += om;
+    acc[M_CNT] += v ? 1.f : 0.f;
+    const float wx0 = om * x0, wx1 = om * x1, wx2 = om * x2;
+    const float wy0 = om * y0, wy1 = om * y1, wy2 = om * y2;
+    acc[M_SP + 0] += wx0; acc[M_SP + 1] += wx1; acc[M_SP + 2] += wx2;
+    acc[M_SQ + 0] += wy0; acc[M_SQ + 1] += wy1; acc[M_SQ + 2] += wy2;
+    acc[M_PP] += wx0 * x0 + wx1 * x1 + wx2 * x2;
+    acc[M_QP + 0] += wy0 * x0; acc[M_QP + 1] += wy0 * x1; acc[M_QP + 2] += wy0 * x2;
+    acc[M_QP + 3] += wy1 * x0; acc[M_QP + 4] += wy1 * x1; acc[M_QP + 5] += wy1 * x2;
+    acc[M_QP + 6] += wy2 * x0; acc[M_QP + 7] += wy2 * x1; acc[M_QP + 8] += wy2 * x2;
+  }
+};
+
+// The pair's estimate as the operator of sweep j.  The state changes during
+// the launch (other CTAs solve), so it is read from L2 (ld.global.cg), never
+// from a possibly stale L1 line.
+__device__ __forceinline__ void load_op(const PairState* S, int j, float delta, int rule,
+                                        HuberOp& op) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) op.A[i] = __ldcg(&S->A[i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    op.b[i] = __ldcg(&S->b[i]);
+    op.pp[i] = __ldcg(&S->piv_p[i]);
+    op.pq[i] = __ldcg(&S->piv_q[i]);
+  }
+  op.delta = j == 1 ? INFINITY : delta;
+  op.cmin = __ldcg(&S->cmin);
+  op.rule = rule;
+}
+
+// One tile of TP pixels of one link: per-thread sums of 4 consecutive pixels
+// at a time, then a pairwise warp butterfly; lane 0 of warp w leaves the warp's
+// sums in red[w] (the caller adds the warps in FP64).
+template <bool VEC, int TP>
+__device__ __forceinline__ void sweep_tile(const HuberOp& op, const float* __restrict__ P,
+                                           const float* __restrict__ Q,
+                                           const float* __restrict__ CP,
+                                           const float* __restrict__ CQ, int npx,
+                                           double (*red)[NMOM]) {
+  float acc[NMOM];
+#pragma unroll
+  for (int m = 0; m < NMOM; ++m) acc[m] = 0.f;
+#pragma unroll 2
+  for (int g = threadIdx.x; g < TP / 4; g += THREADS) {
+    const int i0 = 4 * g;
+    if (i0 >= npx) break;
+    if (VEC && i0 + 4 <= npx) {
+      const float4* P4 = reinterpret_cast<const float4*>(P + 3 * i0);
+      const float4* Q4 = reinterpret_cast<const float4*>(Q + 3 * i0);
+      const float4 pa = __ldcs(P4), pb = __ldcs(P4 + 1), pc = __ldcs(P4 + 2);
+      const float4 qa = __ldcs(Q4), qb = __ldcs(Q4 + 1), qc = __ldcs(Q4 + 2);
+      const float4 cp = __ldcs(reinterpret_cast<const float4*>(CP + i0));
+      const float4 cq = __ldcs(reinterpret_cast<const float4*>(CQ + i0));
+      op(pa.x, pa.y, pa.z, qa.x, qa.y, qa.z, cp.x, cq.x, acc);
+      op(pa.w, pb.x, pb.y, qa.w, qb.x, qb.y, cp.y, cq.y, acc);
+      op(pb.z, pb.w, pc.x, qb.z, qb.w, qc.x, cp.z, cq.z, acc);
+      op(pc.y, pc.z, pc.w, qc.y, qc.z, qc.w, cp.w, cq.w, acc);
+    } else {
+      const int n = min(4, npx - i0);
+      for (int j = 0; j < n; ++j) {
+        const int i = i0 + j;
+        op(P[3 * i], P[3 * i + 1], P[3 * i + 2], Q[3 * i], Q[3 * i + 1], Q[3 * i + 2], CP[i],
+           CQ[i], acc);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NMOM; ++m)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int m = 0; m < NMOM; ++m) red[warp][m] = (double)acc[m];
+}
+
+struct RegArgs {
+  const float* xyz;
+  const float* conf;
+  int64_t hw;
+  int tpl;             // tiles per link
+  int64_t n_tiles;     // tiles per sweep
+  const int32_t* link_off;
+  const int32_t* src;
+  const int32_t* tgt;
+  const int32_t* link_pair;
+  PairState* st;
+  double* partials;    // [n_tiles][NMOM]
+  float delta;
+  int rule;
+  int iters;           // Huber-IRLS solves (= sweeps)
+  ec3r_sim3* out;
+  int32_t* status_out;
+  double* cost;        // nullable: zeroed for pairs that turn degenerate
+  double* cost_sums;   // [n_pairs][CS_STRIDE], zeroed likewise
+  double* ckpt;        // [n_pairs][iters][CKPT]
+  unsigned long long* next;   // work items handed out
+  unsigned* abort;            // set when a wait gave up: every CTA stops
+  unsigned long long* done;   // per pair: tiles completed, over all sweeps
+  unsigned* epoch;            // per pair: solves completed (EPOCH_DONE: degenerate)
+  unsigned* flags;
+  long long wait_cycles;
+  int no_epoch;        // test injection: solves publish no epoch
+};
+
+// FP64 tile sums from L2 (the partials were written by other CTAs during
+// this launch): four accumulators, fixed order, as tile_sum.
+template <int NV>
+__device__ __forceinline__ double tile_sum_cg(const double* partials, int64_t t0, int64_t t1,
+                                              int v) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t t = t0;
+#pragma unroll 2
+  for (; t + 4 <= t1; t += 4) {
+    s0 += __ldcg(&partials[t * NV + v]);
+    s1 += __ldcg(&partials[(t + 1) * NV + v]);
+    s2 += __ldcg(&partials[(t + 2) * NV + v]);
+    s3 += __ldcg(&partials[(t + 3) * NV + v]);
+  }
+  for (; t < t1; ++t) s0 += __ldcg(&partials[t * NV + v]);
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Warp 0 of the CTA that completed pair k's sweep j: the solve of iteration j,
+// then the pair's epoch j (EPOCH_DONE if the pair turned degenerate).
+__device__ __noinline__ void finish_pair(const RegArgs& a, int k, int j, double* mom) {
+  const int lane = threadIdx.x & 31;
+  __threadfence();
+  const int64_t t0 = (int64_t)a.link_off[k] * a.tpl, t1 = (int64_t)a.link_off[k + 1] * a.tpl;
+  if (lane < NMOM) mom[lane] = tile_sum_cg<NMOM>(a.partials, t0, t1, lane);
+  __syncwarp();
+  if (lane == 0) {
+    double R[9], s = 1.0, b[3] = {0, 0, 0}, dV[12];
+    const unsigned status = umeyama_from_moments(mom, R, s, b, dV);
+    double* ck = a.ckpt + ((size_t)k * a.iters + (j - 1)) * CKPT;
+    for (int m = 0; m < NMOM; ++m) ck[CK_MOM + m] = mom[m];
+    for (int i = 0; i < 9; ++i) ck[CK_A + i] = s * R[i];
+    for (int i = 0; i < 3; ++i) ck[CK_B + i] = b[i];
+    ck[CK_STATUS] = (double)status;
+    ck[CK_S] = s;
+    for (int i = 0; i < 9; ++i) ck[CK_R + i] = R[i];
+    for (int i = 0; i < 12; ++i) ck[CK_D + i] = status ? 0.0 : dV[i];
+    commit_estimate(a.st[k], status, R, s, b, j == a.iters, a.out[k], a.status_out[k]);
+    if (status && a.cost) {  // a degenerate pair reports no cost
+      a.cost[k] = 0.0;
+      double* cs = a.cost_sums + (size_t)k * CS_STRIDE;
+      for (int i = 0; i < CS_STRIDE; ++i) cs[i] = 0.0;
+    }
+    __threadfence();
+    // a pair that turned degenerate is skipped by every later sweep
+    if (!a.no_epoch) st_release_u32(a.epoch + k, status ? EPOCH_DONE : (unsigned)j);
+  }
+}
+
+template <bool VEC, int TP, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_register(const __grid_constant__ RegArgs a) {
+  __shared__ double red[THREADS / 32][NMOM];
+  __shared__ double mom[NMOM];
+  __shared__ long long s_item;
+  __shared__ int s_k, s_go, s_last;
+  __shared__ long long s_pre;  // the next item, fetched while this one is reduced
+  const long long total = (long long)a.iters * a.n_tiles;
+  if (threadIdx.x == 0) s_pre = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      // after a timeout anywhere, hand out nothing more
+      const long long item = ld_acquire_u32(a.abort) ? total
+                             : s_pre >= 0            ? s_pre
+                                                     : (long long)atomicAdd(a.next, 1ull);
+      s_pre = -1;
+      int k = -1, go = 0;
+      if (item < total) {
+        const int j = (int)(item / a.n_tiles) + 1;
+        const int64_t t = item - (long long)(j - 1) * a.n_tiles;
+        k = a.link_pair[t / a.tpl];
+        if (k >= 0) {
+          go = j == 1 ? 1 : (int)wait_epoch(a.epoch + k, (unsigned)(j - 1), a.abort, a.flags,
+                                            a.wait_cycles);
+          if (go) go = __ldcg(&a.st[k].active);
+        }
+      }
+      s_item = item;
+      s_k = k;
+      s_go = go;
+    }
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= total) break;
+    if (s_go) {
+      {
+        const int k = s_k;
+        const int j = (int)(item / a.n_tiles) + 1;
+        const int64_t t = item - (long long)(j - 1) * a.n_tiles;
+        const int64_t l = t / a.tpl;
+        const int c = (int)(t - l * a.tpl);
+        const int64_t fs = a.src[l], ft = a.tgt[l];
+        const int64_t px0 = (int64_t)c * TP;
+        const int64_t rem = a.hw - px0;
+        HuberOp op;
+        load_op(a.st + k, j, a.delta, a.rule, op);
+        sweep_tile<VEC, TP>(op, a.xyz + (fs * a.hw + px0) * 3, a.xyz + (ft * a.hw + px0) * 3,
+                            a.conf + fs * a.hw + px0, a.conf + ft * a.hw + px0,
+                            rem < TP ? (int)rem : TP, red);
+      }
+      // the next item's round trip to the counter overlaps this one's reduction
+      if (threadIdx.x == 0) s_pre = (long long)atomicAdd(a.next, 1ull);
+      __syncthreads();
+      // the item again from shared memory, so that nothing of it stays live
+      // across the sweep (registers)
+      const long long it = *(volatile long long*)&s_item;
+      const int k = *(volatile int*)&s_k;
+      const int j = (int)(it / a.n_tiles) + 1;
+      const int64_t t = it - (long long)(j - 1) * a.n_tiles;
+      if (threadIdx.x < NMOM) {  // the tile's moments: FP64 over the warps, fixed order
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < THREADS / 32; ++w) sum += red[w][threadIdx.x];
+        a.partials[t * NMOM + threadIdx.x] = sum;
+        __threadfence();
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long nt =
+            (unsigned long long)(a.link_off[k + 1] - a.link_off[k]) * (unsigned long long)a.tpl;
+        const unsigned long long old = atomicAdd(a.done + k, 1ull);
+        s_last = old + 1ull == (unsigned long long)j * nt;
+        if (s_last) __threadfence();
+      }
+      __syncthreads();
+      if (s_last && threadIdx.x < 32) finish_pair(a, k, j, mom);
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
+// host side: variants, occupancy, launch
+// --------------------------------------------------------------------------
+typedef void (*RegKernel)(const RegArgs);
+
+struct RegVariant {
+  int tile, ctas;
+  RegKernel fn;
+};
+
+// 16-byte aligned pointmaps: the autotuner's candidates (tile pixels, CTAs
+// per SM; 64, 80 and 128 registers per thread).
+static const RegVariant kTuned[] = {
+    {8192, 4, k_register<true, 8192, 4>},   {8192, 3, k_register<true, 8192, 3>},
+    {8192, 2, k_register<true, 8192, 2>},   {4096, 4, k_register<true, 4096, 4>},
+    {4096, 3, k_register<true, 4096, 3>},   {4096, 2, k_register<true, 4096, 2>},
+    {16384, 4, k_register<true, 16384, 4>}, {16384, 3, k_register<true, 16384, 3>},
+    {16384, 2, k_register<true, 16384, 2>},
+};
+constexpr int N_TUNED = sizeof(kTuned) / sizeof(kTuned[0]);
+// Unaligned pointmaps or hw not a multiple of 4: scalar loads, one configuration.
+static const RegVariant kScalar = {8192, 3, k_register<false, 8192, 3>};
+
+int reg_variant_count() { return N_TUNED; }
+
+bool reg_variant_info(int v, int* tile, int* ctas) {
+  if (v < 0 || v >= N_TUNED) return false;
+  *tile = kTuned[v].tile;
+  *ctas = kTuned[v].ctas;
+  return true;
+}
+
+int reg_min_tile() { return 4096; }
+
+static const RegVariant& pick(int v, bool vec) {
+  if (!vec) return kScalar;
+  return kTuned[(v >= 0 && v < N_TUNED) ? v : 0];
+}
+
+// Resident CTAs of a variant on this device (the persistent grid's size).
+static int resident_ctas(const RegVariant& rv, int sm_count) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rv.fn, THREADS, 0) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return per_sm * sm_count;
+}
+
+// Enqueues the persistent launch of variant v on `s`.  `ctl` holds the work
+// counter, then the per-pair completion counters and epochs; it is cleared
+// here (inside the caller's graph), so every call starts from zero.
+ec3r_status launch_register(ec3r_ctx* ctx, cudaStream_t s, int v, bool vec,
+                            const float* xyz, const float* conf, int64_t hw, int n_pairs,
+                            int64_t n_links, const int32_t* link_off, const int32_t* src,
+                            const int32_t* tgt, const int32_t* link_pair, PairState* st,
+                            double* partials, float delta, int rule, int iters,
+                            ec3r_sim3* out, int32_t* status_out, double* cost,
+                            double* cost_sums, double* ckpt, void* ctl, size_t ctl_bytes) {
+  const RegVariant& rv = pick(v, vec);
+  const int64_t tpl = (hw + rv.tile - 1) / rv.tile;
+  RegArgs a;
+  a.xyz = xyz;
+  a.conf = conf;
+  a.hw = hw;
+  a.tpl = (int)tpl;
+  a.n_tiles = n_links * tpl;
+  a.link_off = link_off;
+  a.src = src;
+  a.tgt = tgt;
+  a.link_pair = link_pair;
+  a.st = st;
+  a.partials = partials;
+  a.delta = delta;
+  a.rule = rule;
+  a.iters = iters;
+  a.out = out;
+  a.status_out = status_out;
+  a.cost = cost;
+  a.cost_sums = cost_sums;
+  a.ckpt = ckpt;
+  unsigned long long* c = (unsigned long long*)ctl;
+  a.next = c;
+  a.abort = (unsigned*)(c + 1);
+  a.done = c + 2;
+  a.epoch = (unsigned*)(c + 2 + n_pairs);
+  a.flags = ctx->d_flags;
+  a.wait_cycles = wait_limit_cycles(ctx);
+  a.no_epoch = (ctx->inject & EC3R_INJECT_ALIGN_NO_EPOCH) ? 1 : 0;
+  EC3R_CUDA_TRY(ctx, cudaMemsetAsync(ctl, 0, ctl_bytes, s));
+  if (a.n_tiles == 0) return EC3R_OK;
+  const long long total = (long long)a.iters * a.n_tiles;
+  long long grid = resident_ctas(rv, ctx->sm_count);
+  if (grid > total) grid = total;
+  rv.fn<<<(unsigned)grid, THREADS, 0, s>>>(a);
+  EC3R_CUDA_TRY(ctx, cudaGetLastError());
+  return EC3R_OK;
+}
+
+// Work counter, abort word, per-pair completion counters and epochs.
+size_t reg_ctl_bytes(int n_pairs) {
+  return sizeof(unsigned long long) * (2 + (size_t)n_pairs) + sizeof(unsigned) * (size_t)n_pairs;
+}
+
+}  // namespace align
+}  // namespace ec3r

@@ -35,6 +35,7 @@ ec3r_status ec3r_create(ec3r_ctx** out, int device) {
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) !=
           cudaSuccess ||
+      cudaDeviceGetAttribute(&c->clock_khz, cudaDevAttrClockRate, device) != cudaSuccess ||
       cudaMalloc(&c->d_flags, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(c->d_flags, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&c->h_flags, sizeof(unsigned)) != cudaSuccess ||
@@ -92,6 +93,21 @@ ec3r_status ec3r_sync_status(ec3r_ctx* c, void* stream) {
     return set_error(c, EC3R_ERR_CAPACITY, "fuse_points output capacity exceeded");
   if (f & FLAG_BAD_INDEX)
     return set_error(c, EC3R_ERR_INVALID_ARG, "an index argument was out of range");
+  return EC3R_OK;
+}
+
+ec3r_status ec3r_set_wait_limit(ec3r_ctx* c, double seconds) {
+  if (!c || !(seconds >= 0.0) || seconds > 3600.0) return EC3R_ERR_INVALID_ARG;
+  c->wait_limit_s = seconds;
+  drop_graphs(c);  // cached graphs hold the old limit as a launch argument
+  return EC3R_OK;
+}
+
+ec3r_status ec3r_inject(ec3r_ctx* c, unsigned what) {
+  if (!c || (what & ~(unsigned)(EC3R_INJECT_LOOPS_NO_COPY | EC3R_INJECT_ALIGN_NO_EPOCH)))
+    return EC3R_ERR_INVALID_ARG;
+  c->inject = what;
+  drop_graphs(c);
   return EC3R_OK;
 }
 

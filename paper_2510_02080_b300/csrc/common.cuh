@@ -67,11 +67,27 @@ struct ec3r_ctx {
   std::map<std::string, ec3r::GraphEntry> graphs;
   std::map<std::string, ec3r::Extension*> ext;
   uint64_t clock = 0;
-  // last registration call (its checkpoints serve a following backward call)
-  std::string align_key;
-  void* align_out = nullptr;
-  void* align_status = nullptr;
-  void* align_cost = nullptr;
+  // The last registration call: its token (0: none, or it failed), the key of
+  // its inputs and options, and whether it ran the cost sweep.  Its
+  // checkpoints, per-pair activity and cost live in the align.* workspace;
+  // a backward call given this token reuses them.
+  uint64_t align_token = 0;
+  uint64_t align_tokens_issued = 0;
+  std::string align_args;
+  bool align_had_cost = false;
+  // Registration sweep variants: a forced choice (-1: choose by timing), per
+  // size bucket the chosen variant and every variant's measured time (ms),
+  // and the variant and times of the last call.
+  int align_force = -1;
+  int align_last_variant = -1;
+  std::vector<float> align_last_ms;
+  std::map<uint64_t, std::pair<int, std::vector<float>>> align_tune;
+  // Bounded device waits: the limit (seconds; 0 = the default of two
+  // seconds), the SM clock that converts it to cycles, and test-only
+  // injections that make a wait run out (EC3R_INJECT_*).
+  double wait_limit_s = 0.0;
+  int clock_khz = 0;
+  unsigned inject = 0;
 };
 
 namespace ec3r {
@@ -205,6 +221,14 @@ inline void traced(ec3r_ctx* ctx, cudaStream_t s, const char* name, F&& launch) 
   launch();
   if (b) cudaEventRecord(b, s);
   if (a && b) ctx->prof.push_back(ProfRec{name, a, b});
+}
+
+// The wait limit in SM cycles (clock64 counts at the SM clock, at most the
+// peak clock, so the limit in seconds is an upper bound of the real wait).
+inline long long wait_limit_cycles(const ec3r_ctx* ctx) {
+  const double s = ctx->wait_limit_s > 0.0 ? ctx->wait_limit_s : 2.0;
+  const double khz = ctx->clock_khz > 0 ? (double)ctx->clock_khz : 2.0e6;
+  return (long long)(s * khz * 1e3);
 }
 
 inline std::string key_of(const char* tag, std::initializer_list<uint64_t> vals) {

@@ -59,9 +59,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
 }
 
-// true when the barrier completed the phase of parity `parity` within the limit
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// true when the barrier completed the phase of parity `parity` within the
+// limits: WAIT_LIMIT polls and `limit` SM cycles
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit) {
   const unsigned a = smem_addr(bar);
+  const long long t0 = clock64();
   for (long long i = 0; i < WAIT_LIMIT; ++i) {
     unsigned ok;
     asm volatile(
@@ -72,6 +74,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
+    if (clock64() - t0 > limit) break;
   }
   return false;
 }
@@ -183,7 +186,8 @@ __device__ __forceinline__ uint64_t sw128_desc(unsigned addr) {
 __global__ void __launch_bounds__(SIM_THREADS, 2) k_sim_tc(
     const __grid_constant__ CUtensorMap tmap, int m, int d, int stride, int gap, float tau,
     int side_m, int side_n, Coarse* __restrict__ out, int64_t capacity,
-    unsigned long long* __restrict__ count, float* __restrict__ S_out, unsigned* flags) {
+    unsigned long long* __restrict__ count, float* __restrict__ S_out, unsigned* flags,
+    long long limit, int no_copy) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ unsigned tmem_base;
@@ -222,10 +226,10 @@ __global__ void __launch_bounds__(SIM_THREADS, 2) k_sim_tc(
   const int nk = d / TK;
   const uint64_t tmap_addr = reinterpret_cast<uint64_t>(&tmap);
   int issued = 0;  // chunks whose copies the producer started
-  if (threadIdx.x == 0) {  // producer
-    for (int kc = 0; kc < nk; ++kc) {
+  if (threadIdx.x == 0) {  // producer (with no_copy, a test injection, it starts nothing)
+    for (int kc = 0; kc < (no_copy ? 0 : nk); ++kc) {
       const int st = kc % STAGES;
-      if (kc >= STAGES && !mbar_wait(&empty[st], (unsigned)((kc / STAGES - 1) & 1))) {
+      if (kc >= STAGES && !mbar_wait(&empty[st], (unsigned)((kc / STAGES - 1) & 1), limit)) {
         atomicOr(flags, FLAG_TIMEOUT);
         bad = 1;
         break;
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(SIM_THREADS, 2) k_sim_tc(
     bool ok = true;
     for (int kc = 0; kc < nk && ok; ++kc) {
       const int st = kc % STAGES;
-      if (!mbar_wait(&full[st], (unsigned)((kc / STAGES) & 1))) {
+      if (!mbar_wait(&full[st], (unsigned)((kc / STAGES) & 1), limit)) {
         atomicOr(flags, FLAG_TIMEOUT);
         bad = 1;
         ok = false;
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(SIM_THREADS, 2) k_sim_tc(
     mma_commit(&done);  // completion of every MMA issued
   }
   __syncwarp();
-  if (!mbar_wait(&done, 0)) {
+  if (!mbar_wait(&done, 0, limit)) {
     if (threadIdx.x == 0) atomicOr(flags, FLAG_TIMEOUT);
     bad = 1;
   }
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(SIM_THREADS, 2) k_sim_tc(
   __syncthreads();
   if (bad && threadIdx.x == 0)  // the copies still in flight land before the CTA exits
     for (int kc = max(issued - STAGES, 0); kc < issued; ++kc)
-      mbar_wait(&full[kc % STAGES], (unsigned)((kc / STAGES) & 1));
+      mbar_wait(&full[kc % STAGES], (unsigned)((kc / STAGES) & 1), limit);
   if (!bad) {
     const int a = bm * TM + 32 * warp + lane;
     for (int c0 = 0; c0 < TN; c0 += 32) {
@@ -484,7 +488,7 @@ extern "C" ec3r_status ec3r_loop_candidates(ec3r_ctx* ctx, const float* d_emb, i
   traced(ctx, s, "loop_sim_tc", [&] {
     k_sim_tc<<<(unsigned)n_tiles, SIM_THREADS, SMEM_BYTES, s>>>(
         tmap, m, d, o.stride, o.gap, o.tau_global, side_m, side_n, coarse, coarse_cap, cnt, d_sim,
-        ctx->d_flags);
+        ctx->d_flags, wait_limit_cycles(ctx), (ctx->inject & EC3R_INJECT_LOOPS_NO_COPY) ? 1 : 0);
   });
   // the number of coarse pairs is on the device: a fixed grid of warps
   // strides over them

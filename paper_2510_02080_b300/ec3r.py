@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memo
                 4: "capacity exceeded", 5: "not positive definite", 6: "timeout",
                 7: "degenerate pair", 8: "workspace growth during capture"}
 PAIR_FEW_POINTS, PAIR_ZERO_WEIGHT, PAIR_RANK, PAIR_NONFINITE, PAIR_BAD_INPUT = 1, 2, 4, 8, 16
+INJECT_LOOPS_NO_COPY, INJECT_ALIGN_NO_EPOCH = 1, 2
 PREC = {"fp32c": 0, "fp64": 1}
 RULE = {"product": 0, "src": 1}
 
@@ -30,7 +31,9 @@ EXPORTS = ("ec3r_create", "ec3r_destroy", "ec3r_last_error", "ec3r_status_string
            "ec3r_align_submaps_noalloc", "ec3r_pg_opts_default", "ec3r_pose_graph_correct",
            "ec3r_align_submaps_backward", "ec3r_align_submaps_depth", "ec3r_correct_points",
            "ec3r_fuse_points_depth", "ec3r_loop_candidates", "ec3r_fuse_count",
-           "ec3r_fuse_points_counted")
+           "ec3r_fuse_points_counted", "ec3r_align_token", "ec3r_align_variant_count",
+           "ec3r_align_variant_info", "ec3r_align_set_variant", "ec3r_align_last_variant",
+           "ec3r_set_wait_limit", "ec3r_inject")
 
 
 class Sim3(C.Structure):
@@ -83,7 +86,17 @@ def _declare(l):
     l.ec3r_profile_read.argtypes = [_P, C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int64), C.POINTER(C.c_int)]
     l.ec3r_align_submaps_backward.argtypes = [_P, _P, _P, _I64, _I64, C.c_int, _I64, _P, _P, _P,
-                                              _P, C.POINTER(AlignOpts), _P, _P, _P, _P, _P]
+                                              _P, C.POINTER(AlignOpts), C.c_uint64, _P, _P, _P,
+                                              _P, _P]
+    l.ec3r_align_token.argtypes = [_P]
+    l.ec3r_align_token.restype = C.c_uint64
+    l.ec3r_align_variant_count.argtypes = []
+    l.ec3r_align_variant_count.restype = C.c_int
+    l.ec3r_align_variant_info.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    l.ec3r_align_set_variant.argtypes = [_P, C.c_int]
+    l.ec3r_align_last_variant.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_float)]
+    l.ec3r_set_wait_limit.argtypes = [_P, C.c_double]
+    l.ec3r_inject.argtypes = [_P, C.c_uint]
     l.ec3r_align_submaps_depth.argtypes = [_P, _P, _P, _P, _I64, C.c_int, C.c_int, C.c_int,
                                            _I64, _P, _P, _P, _P, C.POINTER(AlignOpts), _P, _P,
                                            _P, _P]
@@ -104,7 +117,8 @@ def _declare(l):
                  "ec3r_profile", "ec3r_profile_read", "ec3r_pose_graph_correct",
                  "ec3r_align_submaps_backward", "ec3r_align_submaps_depth", "ec3r_correct_points",
                  "ec3r_fuse_points_depth", "ec3r_loop_candidates", "ec3r_fuse_count",
-                 "ec3r_fuse_points_counted"):
+                 "ec3r_fuse_points_counted", "ec3r_align_variant_info", "ec3r_align_set_variant",
+                 "ec3r_align_last_variant", "ec3r_set_wait_limit", "ec3r_inject"):
         getattr(l, name).restype = C.c_int
 
 
@@ -196,6 +210,14 @@ class Context:
         """Waits for the stream; returns the status code (0 = ok) of device-side checks."""
         return self._lib.ec3r_sync_status(self._h, _stream(stream))
 
+    def set_wait_limit(self, seconds):
+        """Limit of the kernels' bounded waits in seconds (0: the default, 2 s)."""
+        self._check(self._lib.ec3r_set_wait_limit(self._h, float(seconds)))
+
+    def inject(self, what):
+        """Test-only: make a bounded wait run out (INJECT_* bits; 0 = off)."""
+        self._check(self._lib.ec3r_inject(self._h, int(what)))
+
     def profile(self, enable=True):
         """Per-kernel CUDA-event timing of every launch (bypasses cached graphs)."""
         self._check(self._lib.ec3r_profile(self._h, 1 if enable else 0))
@@ -216,6 +238,23 @@ class Context:
 
     def last_error(self):
         return self._lib.ec3r_last_error(self._h).decode()
+
+    def align_token(self):
+        """Token of the last align_submaps call (0: none); see align_submaps_backward."""
+        return int(self._lib.ec3r_align_token(self._h))
+
+    def set_align_variant(self, v):
+        """Force registration sweep variant v for later calls (-1: choose by timing)."""
+        self._check(self._lib.ec3r_align_set_variant(self._h, int(v)))
+
+    def last_align_variant(self):
+        """(variant of the last align_submaps call or -1, {variant: median ms} of its
+        size bucket's timing, empty if it was not timed)."""
+        v = C.c_int()
+        n = align_variant_count()
+        ms = (C.c_float * n)()
+        self._check(self._lib.ec3r_align_last_variant(self._h, C.byref(v), ms))
+        return v.value, {i: float(ms[i]) for i in range(n) if ms[i] >= 0.0}
 
     # -- registration ------------------------------------------------------
     def align_submaps(self, xyz, conf, link_off, src, tgt, pair_conf_min=None, *, delta=0.02,
@@ -286,8 +325,12 @@ class Context:
 
     def align_submaps_backward(self, xyz, conf, link_off, src, tgt, grad_S, grad_cost=None,
                                pair_conf_min=None, *, delta=0.02, iters=10, conf_min=0.0,
-                               rule="product", stream=None):
-        """Gradients (dL/dxyz [n_frames,hw,3], dL/dconf [n_frames,hw]) of the registration."""
+                               rule="product", fwd_token=0, stream=None):
+        """Gradients (dL/dxyz [n_frames,hw,3], dL/dconf [n_frames,hw]) of the registration.
+
+        ``fwd_token`` = 0 runs the forward pass first; the token of the last
+        ``align_submaps`` call (``align_token()``) with the same inputs reuses its
+        checkpoints, asserting that the inputs were not modified since."""
         n_frames, hw = int(conf.shape[0]), int(conf.shape[1])
         if xyz.dtype != torch.float32 or conf.dtype != torch.float32:
             raise ValueError("xyz and conf must be float32")
@@ -303,7 +346,8 @@ class Context:
         st = self._lib.ec3r_align_submaps_backward(
             self._h, _ptr(xyz), _ptr(conf), n_frames, hw, n_pairs, int(src.numel()),
             _ptr(link_off), _ptr(src), _ptr(tgt), _ptr(pair_conf_min), C.byref(o),
-            _ptr(grad_S.contiguous()), _ptr(None if grad_cost is None else grad_cost.contiguous()),
+            int(fwd_token), _ptr(grad_S.contiguous()),
+            _ptr(None if grad_cost is None else grad_cost.contiguous()),
             _ptr(gx), _ptr(gc), _stream(stream))
         self._check(st)
         return gx, gc
@@ -457,6 +501,20 @@ class Context:
         self._check(st)
 
 
+def align_variant_count():
+    """Number of registration sweep variants (FP32 moments)."""
+    return int(lib().ec3r_align_variant_count())
+
+
+def align_variant_info(v):
+    """(pixels per tile, CTAs per SM) of registration sweep variant v."""
+    t, c = C.c_int(), C.c_int()
+    st = lib().ec3r_align_variant_info(int(v), C.byref(t), C.byref(c))
+    if st != OK:
+        raise Ec3rError(st, f"no variant {v}")
+    return t.value, c.value
+
+
 def sim3_row(row):
     """(s, R 3x3, t) from one 13-wide row (host numpy)."""
     import numpy as np
@@ -474,7 +532,11 @@ class EC3RAlign(torch.autograd.Function):
 
     ``EC3RAlign.apply(ctx, xyz, conf, link_off, src, tgt, pair_conf_min, delta, iters,
     conf_min, rule)``; the backward pass is the library's adjoint
-    (``ec3r_align_submaps_backward``).
+    (``ec3r_align_submaps_backward``).  It reuses the forward call's checkpoints
+    when that call is still the context's last registration (its token), else
+    it recomputes them; autograd's saved-tensor version check rejects inputs
+    modified in place in between.  The returned status and cost tensors are the
+    caller's: the backward never reads them.
     """
 
     @staticmethod
@@ -483,19 +545,22 @@ class EC3RAlign(torch.autograd.Function):
         S, status, cost = ctx.align_submaps(xyz, conf, link_off, src, tgt, pair_conf_min,
                                             delta=delta, iters=iters, conf_min=conf_min,
                                             rule=rule, want_cost=True)
-        fctx.save_for_backward(xyz, conf, link_off, src, tgt)
-        fctx.ec3r = (ctx, pair_conf_min, delta, iters, conf_min, rule)
+        fctx.save_for_backward(xyz, conf, link_off, src, tgt, pair_conf_min)
+        fctx.ec3r = (ctx, delta, iters, conf_min, rule, ctx.align_token())
         fctx.mark_non_differentiable(status)
         return S, cost, status
 
     @staticmethod
     def backward(fctx, gS, gcost, _gstatus):
-        xyz, conf, link_off, src, tgt = fctx.saved_tensors
-        ctx, pcm, delta, iters, conf_min, rule = fctx.ec3r
+        xyz, conf, link_off, src, tgt, pcm = fctx.saved_tensors
+        ctx, delta, iters, conf_min, rule, token = fctx.ec3r
+        if token != ctx.align_token():
+            token = 0        # another registration ran on this context since
         if gS is None:
             gS = torch.zeros((int(link_off.numel()) - 1, 13), dtype=torch.float64,
                              device=xyz.device)
         gx, gc = ctx.align_submaps_backward(xyz, conf, link_off, src, tgt,
                                             gS.to(torch.float64), gcost, pcm, delta=delta,
-                                            iters=iters, conf_min=conf_min, rule=rule)
+                                            iters=iters, conf_min=conf_min, rule=rule,
+                                            fwd_token=token)
         return None, gx, gc, None, None, None, None, None, None, None, None

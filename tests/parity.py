@@ -21,3 +21,21 @@ def assert_sim3_close(row, S_or, extent, what=""):
     assert rot <= ROT_TOL and sc <= SCALE_TOL and tr <= TRANS_TOL, \
         f"{what}: rot {rot:.2e} scale {sc:.2e} trans/extent {tr:.2e}"
     return rot, sc, tr
+
+
+def sub_pairset(ps, k):
+    """Pair k of a (device) PairSet as a one-pair PairSet on the host: only
+    its own frames are copied, so the oracle can recompute sampled pairs of
+    batches whose whole frame bank is too large to move."""
+    import torch
+    from paper_2510_02080_b300 import synth
+    lo, hi = int(ps.link_off[k]), int(ps.link_off[k + 1])
+    s = ps.src[lo:hi].long()
+    t = ps.tgt[lo:hi].long()
+    f = hi - lo
+    i32 = dict(dtype=torch.int32)
+    pcm = None if ps.pair_conf_min is None else ps.pair_conf_min[k:k + 1].cpu()
+    return synth.PairSet(torch.cat([ps.xyz[s], ps.xyz[t]]).cpu(),
+                         torch.cat([ps.conf[s], ps.conf[t]]).cpu(),
+                         torch.tensor([0, f], **i32), torch.arange(f, **i32),
+                         torch.arange(f, 2 * f, **i32), ps.H, ps.W, pair_conf_min=pcm)

@@ -9,7 +9,7 @@ import torch
 
 from oracle import register as reg
 from paper_2510_02080_b300 import ec3r, synth
-from parity import assert_sim3_close
+from parity import assert_sim3_close, sub_pairset
 
 pytestmark = pytest.mark.gpu
 
@@ -193,3 +193,151 @@ def test_full_size_chain_sampled_pairs(ctx):
         r = reg.align_pairs(sub)[0]
         assert r["status"] == 0
         assert_sim3_close(S[k], r["S"], r["extent"], f"chain pair {k}")
+
+
+def test_malformed_offsets_mark_every_pair(ctx):
+    """Offsets [0, 3, 2, 5] are no CSR array: pairs 0 and 2 would both claim
+    link 2 and pair 1 runs backwards.  Every pair of the call is marked (no
+    pair is solved from a link that another pair claims), the error is raised
+    at sync, and a well-formed call right after is unaffected.  Offsets whose
+    last value is not the link count are refused the same way."""
+    ps = to_cuda(synth.make_pair(synth.SEED_BASE + 5, H=40, W=60))
+    i32 = dict(dtype=torch.int32, device="cuda")
+    src, tgt = torch.zeros(5, **i32), torch.ones(5, **i32)
+    for off in ([0, 3, 2, 5],          # pairs 0 and 2 share link 2
+                [0, 2, 4]):            # the last offset is not the link count (5)
+        S, st, _ = ctx.align_submaps(ps.xyz, ps.conf, torch.tensor(off, **i32), src, tgt)
+        assert ctx.sync_status() == 1, off
+        assert st.tolist() == [ec3r.PAIR_BAD_INPUT] * (len(off) - 1), off
+        assert (S[:, 0] == 1.0).all() and (S[:, 10:] == 0.0).all()
+    S, st, _ = ctx.align_submaps(ps.xyz, ps.conf, torch.tensor([0, 2, 3, 5], **i32), src, tgt)
+    assert ctx.sync_status() == 0 and st.tolist() == [0, 0, 0]
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_config1_pair_at_full_size(ctx, precision):
+    """The single-pair configuration at its stated size: one shared 294 x 518
+    frame (152,292 points), sigma 0.005, 10 % outliers, delta 0.02, 10
+    iterations, in both accumulation modes."""
+    ps = synth.make_pair(synth.SEED_BASE + 1, H=294, W=518, sigma=0.005)
+    S, st, cost = run(ctx, to_cuda(ps), precision=precision, want_cost=True)
+    ref = check_against_oracle(ps, S, st, cost)
+    assert ref[0]["status"] == 0
+
+
+def check_sampled(S, st, cost, ps, sample, what):
+    for k in sample:
+        r = reg.align_pairs(sub_pairset(ps, k))[0]
+        assert int(st[k]) == r["status"], (what, k)
+        if r["status"] == 0:
+            assert_sim3_close(S[k], r["S"], r["extent"], f"{what} pair {k}")
+            if cost is not None:
+                assert abs(cost[k] - r["cost"]) <= 1e-5 * r["cost"] + 1e-12, (k, cost[k])
+
+
+@pytest.mark.timeout(1200)
+def test_config3_loop_batch_full_size_sampled_pairs(ctx):
+    """512 loop candidates with 1-5 shared 294 x 518 frames each and per-pair
+    thresholds for U[20k, 760k] valid points, registered in one call (the
+    launch that is benchmarked); the oracle recomputes 12 sampled pairs: the
+    first and last, the ones with the most and fewest links, and 8 at random."""
+    ps = synth.make_loop_batch(synth.SEED_BASE + 3, n_pairs=512, H=294, W=518, device="cuda")
+    S, st, cost = run(ctx, ps, want_cost=True)
+    assert ctx.sync_status() == 0 and (st == 0).all()
+    frames = np.asarray(ps.meta["frames"])
+    rng = np.random.default_rng(3)
+    sample = sorted({0, 511, int(frames.argmax()), int(frames.argmin())} |
+                    {int(k) for k in rng.choice(512, 8, replace=False)})
+    check_sampled(S, st, cost, ps, sample, "loop batch")
+
+
+@pytest.mark.timeout(1800)
+def test_config5_map_registration_sampled_pairs(ctx):
+    """The large map at 392 x 518: 1000 submaps of 5 frames, 999 chain pairs
+    plus 300 loop pairs (1-5 shared frames) in one call; the oracle recomputes
+    sampled chain and loop pairs."""
+    M = 1000
+    ch = synth.make_chain(synth.SEED_BASE + 5, M=M, F=5, H=392, W=518, device="cuda")
+    lb = synth.make_loop_batch(synth.SEED_BASE + 55, n_pairs=300, H=392, W=518,
+                               max_valid=760_000, device="cuda")
+    cp = ch.pairs()
+    del ch
+    nf = cp.xyz.shape[0]
+    dev = cp.xyz.device
+    bank = synth.PairSet(torch.cat([cp.xyz, lb.xyz]), torch.cat([cp.conf, lb.conf]),
+                         torch.cat([cp.link_off[:-1], lb.link_off + int(cp.link_off[-1])]),
+                         torch.cat([cp.src, lb.src + nf]), torch.cat([cp.tgt, lb.tgt + nf]),
+                         392, 518,
+                         pair_conf_min=torch.cat([torch.zeros(cp.n_pairs, device=dev),
+                                                  lb.pair_conf_min]))
+    del cp, lb
+    S, st, cost = run(ctx, bank, want_cost=True)
+    assert ctx.sync_status() == 0 and (st == 0).all()
+    check_sampled(S, st, cost, bank, [0, 500, 998], "map chain")
+    rng = np.random.default_rng(55)
+    check_sampled(S, st, cost, bank, [999 + int(k) for k in rng.choice(300, 4, replace=False)],
+                  "map loop")
+
+
+def test_persistent_wait_runs_out_and_the_context_recovers(cuda_lib):
+    """The persistent registration's waits on a pair's solve are bounded.  With
+    the test injection no solve publishes its epoch, so the second sweep's
+    waits run out: EC3R_ERR_TIMEOUT at sync, every CTA stops, no fault.  The
+    same context then registers the batch correctly."""
+    c = ec3r.Context()
+    ps = synth.make_loop_batch(synth.SEED_BASE + 4, n_pairs=4, H=50, W=80, min_valid=300,
+                               max_valid=15000)
+    d = to_cuda(ps)
+    c.set_wait_limit(0.005)
+    c.inject(ec3r.INJECT_ALIGN_NO_EPOCH)
+    run(c, d)
+    assert c.sync_status() == 6                      # EC3R_ERR_TIMEOUT
+    c.inject(0)
+    c.set_wait_limit(0)
+    S, st, cost = run(c, d, want_cost=True)
+    assert c.sync_status() == 0
+    check_against_oracle(ps, S, st, cost)
+    c.close()
+
+
+@pytest.mark.parametrize("v", range(9))
+def test_every_sweep_variant_matches_oracle_and_is_deterministic(ctx, v):
+    """Every variant of the persistent registration (pixels per tile x CTAs per
+    SM) against the oracle, on a batch of 1-5 shared 150 x 240 frames per pair
+    (36,000 pixels: ragged tiles of 4096, 8192 and 16384 pixels) with a
+    degenerate pair; a rerun is bitwise identical."""
+    ps = synth.make_loop_batch(synth.SEED_BASE + 4, n_pairs=6, H=150, W=240, min_valid=2000,
+                               max_valid=100000)
+    xyz = ps.xyz.clone()
+    xyz[ps.src[ps.link_off[2]:ps.link_off[3]].long(), :, 1:] = 0.0   # pair 2: collinear
+    ps = synth.PairSet(xyz, ps.conf, ps.link_off, ps.src, ps.tgt, ps.H, ps.W, ps.S_gt,
+                       ps.pair_conf_min)
+    d = to_cuda(ps)
+    ctx.set_align_variant(v)
+    try:
+        S, st, cost = run(ctx, d, want_cost=True)
+        S2, st2, cost2 = run(ctx, d, want_cost=True)
+        assert ctx.last_align_variant()[0] == v
+    finally:
+        ctx.set_align_variant(-1)
+    assert np.array_equal(S, S2) and np.array_equal(st, st2) and np.array_equal(cost, cost2)
+    assert ctx.sync_status() == 0
+    ref = check_against_oracle(ps, S, st, cost)
+    assert ref[2]["status"] == reg.DEG_RANK and sum(r["status"] == 0 for r in ref) == 5
+
+
+def test_autotuner_times_each_variant_once_per_size_bucket(cuda_lib):
+    """The first call of a size bucket times every variant and keeps the
+    fastest; later calls of the bucket reuse it without timing again."""
+    c = ec3r.Context()
+    d = to_cuda(synth.make_loop_batch(synth.SEED_BASE + 4, n_pairs=5, H=50, W=80,
+                                      min_valid=300, max_valid=15000))
+    run(c, d)
+    v, ms = c.last_align_variant()
+    assert sorted(ms) == list(range(ec3r.align_variant_count()))
+    assert all(t > 0 for t in ms.values()) and v == min(ms, key=ms.get)
+    S1 = run(c, d)[0]
+    v2, ms2 = c.last_align_variant()
+    assert v2 == v and ms2 == ms
+    assert np.array_equal(S1, run(c, d)[0])
+    c.close()

@@ -138,6 +138,17 @@ def test_bad_links_and_arguments(ctx):
     S, st, _ = run(ctx, bad)
     assert int(st[1]) == 16 and int(st[0]) == 0            # EC3R_PAIR_BAD_INPUT
     assert ctx.sync_status() == 1                          # EC3R_ERR_INVALID_ARG (bad index)
+    # offsets that are no CSR array: with [0, 2, 1, 3] pairs 0 and 2 would both
+    # claim link 1 and pair 1 runs backwards; every pair of the call is marked
+    d4 = synth.make_depth_chain(synth.SEED_BASE + 45, M=4, F=2, H=20, W=24, overlap=1).pairs()
+    overlap = synth.DepthPairSet(d4.depth, d4.conf, d4.cams,
+                                 torch.tensor([0, 2, 1, 3], dtype=torch.int32), d4.src, d4.tgt,
+                                 d4.H, d4.W)
+    S, st, _ = run(ctx, overlap)
+    assert st.tolist() == [16, 16, 16]
+    assert ctx.sync_status() == 1
+    S, st, _ = run(ctx, d4)
+    assert st.tolist() == [0, 0, 0] and ctx.sync_status() == 0
     with pytest.raises(ValueError):
         ctx.align_submaps_depth(dps.depth.cuda(), dps.conf.cuda(), dps.cams[:1].cuda(),
                                 dps.link_off.cuda(), dps.src.cuda(), dps.tgt.cuda())

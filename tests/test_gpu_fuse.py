@@ -178,3 +178,34 @@ def test_count_arguments(ctx):
     st = ctx._lib.ec3r_fuse_count(ctx._h, 2, 100, ec3r._ptr(conf), 1.0, ec3r._ptr(counts), None,
                                   ec3r._stream(None))
     assert st == 1  # EC3R_ERR_INVALID_ARG: no mask buffer
+
+
+@pytest.mark.timeout(1800)
+def test_config5_map_fusion_sampled_submaps(ctx):
+    """The large map: all 1000 x 5 x 392 x 518 = 1,015,280,000 points fused in
+    one call under the submaps' true poses; the oracle recomputes sampled
+    submaps, whose output offsets come from keep counts taken on the host."""
+    ch = synth.make_chain(synth.SEED_BASE + 5, M=1000, F=5, H=392, W=518, device="cuda")
+    M = ch.M
+    n = ch.F * ch.H * ch.W
+    s, R, t = (v.cpu().numpy() for v in (ch.T_gt.s, ch.T_gt.R, ch.T_gt.t))
+    rows = np.concatenate([s[:, None], R.reshape(M, 9), t], 1)
+    xyz = ch.xyz.reshape(M, n, 3)
+    conf = ch.conf.reshape(M, n)
+    counts = np.array([int((conf[m].cpu().numpy() > 1.0).sum()) for m in range(M)])
+    K = int(counts.sum())
+    out_xyz = torch.empty((K, 3), device="cuda")
+    out_idx = torch.empty((K,), dtype=torch.int64, device="cuda")
+    cursor = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ctx.fuse_points(xyz, conf, torch.tensor(rows, device="cuda"), out_xyz, out_idx, cursor)
+    assert ctx.sync_status() == 0 and int(cursor) == K
+    before = np.concatenate([[0], np.cumsum(counts)])
+    for m in (0, 437, 998, 999):
+        start = int(before[m])
+        ox, oi = ofuse.fuse_points(xyz[m:m + 1].cpu().numpy(), conf[m:m + 1].cpu().numpy(),
+                                   [(s[m], R[m], t[m])], 1.0, index_base=m * n)
+        assert len(oi) == counts[m]
+        gi = out_idx[start:start + len(oi)].cpu().numpy()
+        gx = out_xyz[start:start + len(oi)].cpu().numpy()
+        assert np.array_equal(gi, oi)
+        assert np.abs(gx - ox).max() <= POINT_TOL * extent(ox)

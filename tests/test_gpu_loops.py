@@ -110,3 +110,80 @@ def test_full_size_sampled_rows_and_candidates(ctx):
         best, bi, bj = olp.best_neighbour(U, a * stride, b * stride, kw["radius"], kw["gap"])
         assert abs(s - best) <= 1e-5
         assert (bi, bj) == (i, j) or abs(float(U[i] @ U[j]) - best) <= 1e-5
+
+
+U_BF16 = 2.0 ** -8          # unit roundoff of BF16's 8-bit significand
+U_FP32 = 2.0 ** -24
+
+
+def exact_cosine_bound(d):
+    """|S_bf16 - cos| for unit rows a, b of dimension d: each entry of a and b
+    is rounded once to BF16, a_i (1 + e_i), |e_i| <= u, so the exact product of
+    the rounded rows differs from a.b by at most (2u + u^2) sum |a_i b_i| <=
+    2u + u^2; FP32 accumulation of the d products adds at most d u32 times
+    sum |a'_i b'_i| <= (1 + u)^2; the FP32 normalisation before rounding adds
+    a few u32."""
+    u = U_BF16
+    return 2 * u + u * u + (d + 4) * U_FP32 * (1 + u) ** 2
+
+
+@pytest.mark.timeout(900)
+def test_full_size_similarity_against_exact_cosines(ctx):
+    """What tau_global thresholds is the cosine of two embeddings (Sec. III-D).
+    At the benchmarked size (32,768 keyframes x 1024, every 2nd sampled), 256
+    sampled rows of the tensor-core matrix are compared with the FP64 cosines
+    of the FP32 embeddings as they are: every entry within the rounding bound
+    above; and the coarse decisions at tau_global = 0.93 that the BF16
+    contraction takes differently from the exact cosines are counted (each of
+    them within the bound of the threshold)."""
+    n, d, stride, tau = 32768, 1024, 2, 0.93
+    E = synth.make_keyframe_embeddings(synth.SEED_BASE + 62, n=n, d=d)
+    rows, scores, counts, S = ctx.loop_candidates(E.cuda(), stride=stride, radius=2,
+                                                  gap=n // 5, tau_global=tau, tau_local=0.96,
+                                                  capacity=1 << 18, with_sim=True)
+    assert ctx.sync_status() == 0
+    En = E.numpy()
+    m = S.shape[0]
+    rng = np.random.default_rng(9)
+    sample = np.sort(rng.choice(m, 256, replace=False))
+    cos = olp.cosine_rows(En, stride, sample)
+    got = S[torch.as_tensor(sample, device="cuda")].cpu().numpy().astype(np.float64)
+    bound = exact_cosine_bound(d)
+    flips = near = 0
+    worst = 0.0
+    for r, a in enumerate(sample):
+        g, c = got[r, a:], cos[r, a:]
+        err = np.abs(g - c)
+        worst = max(worst, float(err.max()))
+        assert err.max() <= bound, (a, float(err.max()), bound)
+        b = np.arange(a, m)
+        far = (b - a) * stride >= n // 5
+        flip = far & ((g > tau) != (c > tau))
+        assert np.all(np.abs(c[flip] - tau) <= bound)
+        flips += int(flip.sum())
+        near += int((far & (np.abs(c - tau) <= bound)).sum())
+    print(f"exact-cosine check: max |S - cos| {worst:.3e} (bound {bound:.3e}); "
+          f"{flips} flipped decisions at tau {tau} among {near} entries within the bound of it")
+
+
+def test_bounded_wait_runs_out_and_the_context_recovers(cuda_lib):
+    """The similarity kernel's waits are bounded.  With the test injection the
+    TMA producer starts no copy, so the MMA thread's first wait on its stage's
+    mbarrier runs out (no copy is ever in flight): EC3R_ERR_TIMEOUT at sync, no
+    fault.  The same context then runs the normal call correctly."""
+    c = ec3r.Context()
+    rng = np.random.default_rng(0)
+    E = torch.tensor(rng.normal(size=(700, 256)).astype(np.float32), device="cuda")
+    kw = dict(stride=2, radius=1, gap=4, tau_global=0.5, tau_local=0.6, with_sim=True)
+    c.set_wait_limit(0.01)
+    c.inject(ec3r.INJECT_LOOPS_NO_COPY)
+    c.loop_candidates(E, **kw)
+    assert c.sync_status() == 6                      # EC3R_ERR_TIMEOUT
+    c.inject(0)
+    c.set_wait_limit(0)
+    rows, scores, counts, S = c.loop_candidates(E, **kw)
+    assert c.sync_status() == 0
+    ref = olp.coarse_similarity(E.cpu().numpy(), 2)
+    iu = np.triu_indices(ref.shape[0])
+    assert np.abs(S.cpu().numpy()[iu] - ref[iu]).max() <= MARGIN
+    c.close()

@@ -120,18 +120,21 @@ def test_invalid_edges_rejected(ctx):
         ctx.pose_graph_correct(nodes, [0], [3], T)
 
 
-@pytest.mark.timeout(900)
-def test_large_loop_graph_one_iteration_matches_oracle(ctx):
-    """1000 nodes, 300 random loops (minimum-degree ordering, a dense trailing
-    supernode in the factor): one Gauss-Newton step against the oracle's dense
-    FP64 solve."""
+@pytest.mark.timeout(1800)
+def test_large_loop_graph_converges_to_the_oracle(ctx):
+    """The large map's graph: 1000 nodes, 999 odometry and 300 random loop
+    edges (minimum-degree ordering, a dense trailing supernode in the factor),
+    all 10 Gauss-Newton iterations, against the oracle's dense FP64 solves:
+    the chi^2 history iterate by iterate, and the poses at convergence (the
+    oracle's last step is below 1e-8)."""
     n = 1000
     g = synth.make_pose_graph(synth.SEED_BASE + 5, n, 300)
     ei, ej, Tij = graph_from_synth(g)
     init = opg.chain_init(n, ei, ej, Tij)
-    ref, hist, _ = opg.gauss_newton(init, ei, ej, Tij, iters=1)
+    ref, hist, steps = opg.gauss_newton(init, ei, ej, Tij, iters=10)
+    assert steps[-1] < 1e-8 and hist[-1] < hist[0]
     nodes = rows([sim3.identity()] * n)
-    chi2 = ctx.pose_graph_correct(nodes, ei, ej, rows(Tij), iters=1)
+    chi2 = ctx.pose_graph_correct(nodes, ei, ej, rows(Tij), iters=10)
     assert ctx.sync_status() == 0
     np.testing.assert_allclose(chi2.cpu().numpy(), np.array(hist), rtol=TOL)
     assert_poses_close(tuples(nodes), ref)

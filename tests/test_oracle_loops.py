@@ -67,3 +67,28 @@ def test_sampled_rows_and_neighbourhood_helpers_agree_with_the_whole_matrix():
         assert loops.best_neighbour(En, 3 * a, 3 * b, 1, 20) == (s, i, j)
     # a neighbourhood with no pair far enough apart
     assert loops.best_neighbour(En, 0, 3, 1, 20) == (-np.inf, -1, -1)
+
+
+def test_exact_cosines_of_scaled_embeddings_on_a_circle():
+    """cosine_rows is the cosine itself: embeddings (r_k cos th_k, r_k sin th_k, 0...)
+    with arbitrary lengths r_k have cosines cos(th_a - th_b), whatever the
+    lengths; the BF16 similarity differs from it by at most the rounding bound
+    2u + u^2 (u = 2^-8, unit roundoff of an 8-bit significand) for unit rows."""
+    rng = np.random.default_rng(3)
+    n, d, stride = 40, 128, 3
+    th = rng.uniform(0, 2 * np.pi, n)
+    r = rng.uniform(0.1, 30.0, n)
+    E = np.zeros((n, d), np.float32)
+    E[:, 0] = r * np.cos(th)
+    E[:, 1] = r * np.sin(th)
+    rows = [0, 4, 13]
+    got = loops.cosine_rows(E, stride, rows)
+    ths = th[::stride].astype(np.float32).astype(np.float64)
+    e32 = E[::stride].astype(np.float64)
+    ang = np.arctan2(e32[:, 1], e32[:, 0])
+    want = np.cos(ang[rows][:, None] - ang[None, :])
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-14)
+    assert ths.shape[0] == got.shape[1]
+    u = 2.0 ** -8
+    bf = loops.coarse_similarity_rows(E, stride, rows)
+    assert np.abs(bf - got).max() <= 2 * u + u * u

@@ -103,3 +103,22 @@ def test_noalloc_refuses_sizes_beyond_its_scratch():
     big = synth.PairSet(ps.xyz, ps.conf, big_off, ps.src, ps.tgt, ps.H, ps.W)
     rc, *_ = call_noalloc(big, n_pairs=MAX_PAIRS + 1)
     assert rc == 1                      # EC3R_ERR_INVALID_ARG
+
+
+def test_noalloc_marks_every_pair_of_malformed_offsets():
+    """Offsets [0, 3, 2, 5] would let pairs 0 and 2 both claim link 2.  The
+    no-allocation entry point has no context to raise an error through, so
+    every pair of the call comes back marked EC3R_PAIR_BAD_INPUT (none is
+    solved from a link that two pairs claim), and the next call is clean."""
+    ps = cuda_set(synth.make_pair(synth.SEED_BASE + 5, H=40, W=60))
+    i32 = dict(dtype=torch.int32, device="cuda")
+    src, tgt = torch.zeros(5, **i32), torch.ones(5, **i32)
+    bad = synth.PairSet(ps.xyz, ps.conf, torch.tensor([0, 3, 2, 5], **i32), src, tgt, ps.H, ps.W)
+    rc, S, st, _ = call_noalloc(bad)
+    assert rc == 0
+    assert st.tolist() == [16, 16, 16]                  # EC3R_PAIR_BAD_INPUT
+    assert (S[:, 0] == 1.0).all()
+    good = synth.PairSet(ps.xyz, ps.conf, torch.tensor([0, 2, 3, 5], **i32), src, tgt, ps.H,
+                         ps.W)
+    rc, S, st, _ = call_noalloc(good)
+    assert rc == 0 and st.tolist() == [0, 0, 0]
