@@ -39,10 +39,12 @@ PG_ITERS = 10
 SEED_CORRECT = 2510020800 + 56
 SWEEP_BYTES_PER_PIXEL = 32          # p, q (2 x 12 B) + c_p, c_q (2 x 4 B) per sweep
 # DRAM bytes (read + write) per link pixel and sweep of the persistent
-# registration launch, from an ncu capture on the 40-submap chain; the traffic
-# scales with the pixels of a launch.  None until captured for the current
-# kernel.
-REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP = None
+# registration launch, by sweep variant: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of each variant's first timing launch on the 40-submap
+# chain (39 links x 152,292 px, 10 sweeps; the traffic scales with the pixels of
+# a launch).  Empty once the kernel changes.
+REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP = {0: 32.18, 1: 31.75, 2: 31.60, 3: 32.29, 4: 31.67,
+                                          5: 31.64, 6: 32.09, 7: 31.80, 8: 31.75}
 
 
 def peaks():
@@ -366,6 +368,170 @@ def oracle_check(args, ch, ps, S, poses, out_xyz, out_idx, M):
     return cpu, {"registration": registration, "fusion": fusion, "pose_graph": pose_graph}
 
 
+def _host_pair(ps, k):
+    """Pair k of a device PairSet as a one-pair host PairSet (its frames only)."""
+    import torch
+    from paper_2510_02080_b300 import synth
+    lo, hi = int(ps.link_off[k]), int(ps.link_off[k + 1])
+    s, t = ps.src[lo:hi].long(), ps.tgt[lo:hi].long()
+    f = hi - lo
+    i32 = dict(dtype=torch.int32)
+    pcm = None if ps.pair_conf_min is None else ps.pair_conf_min[k:k + 1].cpu()
+    return synth.PairSet(torch.cat([ps.xyz[s], ps.xyz[t]]).cpu(),
+                         torch.cat([ps.conf[s], ps.conf[t]]).cpu(),
+                         torch.tensor([0, f], **i32), torch.arange(f, **i32),
+                         torch.arange(f, 2 * f, **i32), ps.H, ps.W, pair_conf_min=pcm)
+
+
+def registration_error(S, st, host_pairs, ks):
+    """Error of the GPU's rows S[k] (and statuses) against the oracle on each
+    listed pair's own frames."""
+    from oracle import register as reg
+    Sh, sth = S.cpu().numpy(), st.cpu().numpy()
+    rot = sc = tr = 0.0
+    same = True
+    for k, hp in zip(ks, host_pairs):
+        r = reg.align_pairs(hp, delta=DELTA, iters=ITERS)[0]
+        same &= int(sth[k]) == r["status"]
+        if r["status"] == 0:
+            e = sim3_error(Sh[k], r["S"])
+            rot, sc = max(rot, e[0]), max(sc, e[1])
+            tr = max(tr, e[2] / max(r["extent"], 1e-30))
+    return {"pairs": [int(k) for k in ks], "statuses_equal": bool(same),
+            "max_rotation_rad": rot, "max_relative_scale": sc,
+            "max_translation_over_extent": tr,
+            "within_tolerances": bool(same and rot <= 1e-5 and sc <= 1e-6 and tr <= 1e-6)}
+
+
+def pose_graph_error(ctx, ei, ej, Tij_rows, n, iters):
+    """The GPU's pose graph (chaining + `iters` Gauss-Newton steps) against the
+    oracle's on the same edges: chi^2 history and poses (relative to the
+    trajectory's extent)."""
+    import numpy as np
+    import torch
+    from oracle import pose_graph as opg
+    nodes = torch.zeros((n, 13), dtype=torch.float64, device=Tij_rows.device)
+    nodes[:, 0] = 1.0
+    nodes[:, [1, 5, 9]] = 1.0
+    chi2 = ctx.pose_graph_correct(nodes, ei, ej, Tij_rows, iters=iters).cpu().numpy()
+    R = Tij_rows.cpu().numpy()
+    Tij = [(float(r[0]), r[1:10].reshape(3, 3), r[10:13]) for r in R]
+    ref, hist, _ = opg.gauss_newton(opg.chain_init(n, ei, ej, Tij), ei, ej, Tij, iters=iters)
+    got = nodes.cpu().numpy()
+    pe = [sim3_error(got[v], ref[v]) for v in range(n)]
+    traj = np.stack([np.asarray(T[2]) for T in ref])
+    text = max(float(np.linalg.norm(traj.max(0) - traj.min(0))), 1.0)
+    return {"nodes": n, "gn_iters": iters,
+            "max_chi2_relative": float(np.max(np.abs(chi2 - np.asarray(hist)) /
+                                              np.maximum(np.abs(np.asarray(hist)), 1e-300))),
+            "max_rotation": max(e[0] for e in pe), "max_relative_scale": max(e[1] for e in pe),
+            "max_translation_over_extent": max(e[2] for e in pe) / text}
+
+
+def _host_depth_pair(dps, k):
+    """Pair k of a device depth pair set as a one-pair host PairSet of the
+    oracle's pointmaps (its frames unprojected in FP64)."""
+    import torch
+    from oracle import unproject as oup
+    from paper_2510_02080_b300 import synth
+    lo, hi = int(dps.link_off[k]), int(dps.link_off[k + 1])
+    fr = torch.cat([dps.src[lo:hi], dps.tgt[lo:hi]]).long()
+    xyz = oup.unproject(dps.depth[fr].double().cpu().numpy(), dps.cams[fr].cpu().numpy())
+    f = hi - lo
+    i32 = dict(dtype=torch.int32)
+    return synth.PairSet(torch.from_numpy(xyz), dps.conf[fr].reshape(2 * f, -1).cpu(),
+                         torch.tensor([0, f], **i32), torch.arange(f, **i32),
+                         torch.arange(f, 2 * f, **i32), dps.H, dps.W)
+
+
+def map_fusion_error(xyz, conf, ox, oi, pts, refs, m=7):
+    """The map's fusion (identity poses) on submap m and the point correction of
+    the sampled references into submaps 0..m, against the oracle."""
+    import numpy as np
+    from oracle import fuse as ofuse
+    eye = (1.0, np.eye(3), np.zeros(3))
+    ch = conf[:m + 1].cpu().numpy()
+    n = ch.shape[1]
+    start = int((ch[:m] > 1.0).sum())
+    xm = xyz[:m + 1].cpu().numpy()
+    rx, ri = ofuse.fuse_points(xm[m:m + 1], ch[m:m + 1], [eye], 1.0, index_base=m * n)
+    gi = oi[start:start + len(ri)].cpu().numpy()
+    gx = ox[start:start + len(ri)].cpu().numpy().astype(np.float64)
+    ext = max(float(np.linalg.norm(rx.max(0) - rx.min(0))), float(np.abs(rx).max()))
+    fusion = {"submap": m, "points": int(len(ri)), "indices_equal": bool(np.array_equal(gi, ri)),
+              "max_point_error_over_extent": float(np.abs(gx - rx).max() / ext)}
+    r = refs.cpu().numpy()
+    sel = np.flatnonzero((r >= 0) & (r < (m + 1) * n))
+    before = np.zeros((len(sel), 3))
+    ref_pts = ofuse.correct_points(before, r[sel], xm, ch, [eye] * (m + 1), 1.0)[0]
+    got = pts[torch_index(sel, pts)].cpu().numpy().astype(np.float64)
+    cext = max(float(np.abs(ref_pts).max()), 1.0)
+    correction = {"references": int(len(sel)),
+                  "max_point_error_over_extent": float(np.abs(got - ref_pts).max() / cext)}
+    return fusion, correction
+
+
+def torch_index(idx, like):
+    import torch
+    return torch.as_tensor(idx, dtype=torch.int64, device=like.device)
+
+
+def similarity_error(ctx, E, kw, n_rows=64):
+    """The BF16 tensor-core similarity on sampled rows against the exact FP64
+    cosines of the FP32 embeddings, and the coarse decisions at tau_global that
+    differ (far pairs only)."""
+    import numpy as np
+    import torch
+    from oracle import loops as olp
+    _, _, _, S = ctx.loop_candidates(E, with_sim=True, **kw)
+    En = E.cpu().numpy()
+    stride, tau, gap = kw["stride"], kw["tau_global"], kw["gap"]
+    m = S.shape[0]
+    rows = np.sort(np.random.default_rng(9).choice(m, min(n_rows, m), replace=False))
+    cos = olp.cosine_rows(En, stride, rows)
+    got = S[torch.as_tensor(rows, device=S.device)].cpu().numpy().astype(np.float64)
+    worst, flips = 0.0, 0
+    for r, a in enumerate(rows):
+        g, c = got[r, a:], cos[r, a:]
+        worst = max(worst, float(np.abs(g - c).max()))
+        far = (np.arange(a, m) - a) * stride >= gap
+        flips += int((far & ((g > tau) != (c > tau))).sum())
+    return {"rows": int(len(rows)), "max_abs_error_vs_exact_cosine": worst,
+            "flipped_coarse_decisions": flips}
+
+
+def adjoint_error(ctx, ps, gS, gc, delta=DELTA, iters=ITERS):
+    """The backward call's gradients against the oracle's FP64 reverse mode
+    (element by element, |d| <= 2e-3 |g| + 1e-5 max|g|, points away from the
+    Huber kink): the largest ratio of error to bound per gradient."""
+    import numpy as np
+    from oracle import adjoint as oadj
+    from oracle import register as reg
+    gx, gcf = ctx.align_submaps_backward(ps.xyz, ps.conf, ps.link_off, ps.src, ps.tgt, gS, gc)
+    xyz, conf = ps.xyz.double().cpu().numpy(), ps.conf.double().cpu().numpy()
+    P, Q, cp, cq, valid = reg.pair_correspondences(xyz, conf, [0, 1], [0], [1], 0, 0.0)
+    w = cp[valid] * cq[valid]
+    Sh, tape, _ = oadj.irls_forward(P[valid], Q[valid], w, delta, iters)
+    g = gS.cpu().numpy()[0]
+    gP, gQ, gw = oadj.irls_backward(P[valid], Q[valid], w, delta, tape, Sh, g[0],
+                                    g[1:10].reshape(3, 3), g[10:13], float(gc[0]))
+    gcp, gcq = oadj.weight_grads(gw, cp[valid], cq[valid])
+    far = np.ones(int(valid.sum()), bool)
+    for rec in tape[1:]:
+        far &= np.abs(rec["r"] - delta) >= 1e-4
+    gxh, gch = gx.cpu().double().numpy(), gcf.cpu().double().numpy()
+
+    def ratio(got, ref):
+        b = 2e-3 * np.abs(ref) + 1e-5 * np.abs(ref).max()
+        return float((np.abs(got - ref) / b).max())
+    return {"points": int(far.sum()),
+            "dxyz_error_over_bound": max(ratio(gxh[0][valid][far], gP[far]),
+                                         ratio(gxh[1][valid][far], gQ[far])),
+            "dconf_error_over_bound": max(ratio(gch[0][valid][far], gcp[far]),
+                                          ratio(gch[1][valid][far], gcq[far])),
+            "bound": "|GPU - oracle| <= 2e-3 |oracle| + 1e-5 max|oracle| per element"}
+
+
 def run_reference(args):
     """The oracle as it stands, one process per host core, on consecutive pairs
     of a chain of the benchmark's recipe generated on the host (one pair per
@@ -655,9 +821,9 @@ def run_ours(args):
         return
 
     peak, peak_kind = peaks()
-    # the dominant kernel: the persistent registration launch (every sweep and
-    # solve of the call), 32 B per link pixel per sweep, 11 sweeps with the cost
-    sweeps = ITERS + 1
+    # the dominant kernel: the persistent registration launch (the 10 Huber-IRLS
+    # sweeps and every per-pair solve of the call), 32 B per link pixel per sweep
+    sweeps = ITERS
     reg_k = prof.get("irls_register", (0.0, 0))
     reg_launch_ms = reg_k[0] / max(reg_k[1], 1)
     reg_bytes = SWEEP_BYTES_PER_PIXEL * pix * sweeps
@@ -668,8 +834,13 @@ def run_ours(args):
     fuse_ms = sum(prof.get(k, (0.0, 0))[0] for k in ("fuse_count", "fuse_scan", "fuse_scatter"))
     pg_ms = sum(v[0] for k, v in prof.items() if k.startswith("pg_"))
     adj_ms = sum(v[0] for k, v in prof.items() if k.startswith("adj_"))
-    reg_ms = sum(prof.get(k, (0.0, 0))[0] for k in ("align_setup", "irls_register"))
+    # the whole registration call: set-up, the persistent launch, and the cost
+    # sweep and cost that the adjoint needs; and the same without the cost
+    reg_ms = sum(prof.get(k, (0.0, 0))[0]
+                 for k in ("align_setup", "irls_register", "irls_cost_sweep", "irls_cost"))
     reg_rate = n_valid * ITERS * args.steps / (reg_ms * 1e-3) if reg_ms else None
+    reg10_ms = sum(prof.get(k, (0.0, 0))[0] for k in ("align_setup", "irls_register"))
+    reg10_rate = n_valid * ITERS * args.steps / (reg10_ms * 1e-3) if reg10_ms else None
     fuse_gbs = 26.0 * n_fuse * args.steps / (fuse_ms * 1e-3) / 1e9 if fuse_ms else None
     variant, tune_ms = ctx.last_align_variant()
     vt, vc = ec3r.align_variant_info(variant) if variant >= 0 else (None, None)
@@ -693,12 +864,12 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "irls_register", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP * pix * sweeps
-                                 if REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP else None),
+                     "traffic": (REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP[variant] * pix * sweeps
+                                 if variant in REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP else None),
                      "algorithmic_bytes_per_launch": reg_bytes,
                      "launch_ms": reg_launch_ms,
-                     "note": "one persistent launch per call: 10 IRLS sweeps, the cost sweep "
-                             "and every per-pair FP64 solve; 32 B per link pixel per sweep",
+                     "note": "one persistent launch per call: the 10 Huber-IRLS sweeps and "
+                             "every per-pair FP64 solve; 32 B per link pixel per sweep",
                      "registration": {
                          "pt_iter_per_s": reg_rate,
                          "bytes_per_pt_iter": SWEEP_BYTES_PER_PIXEL,
@@ -706,10 +877,13 @@ def run_ours(args):
                                       if reg_rate else None),
                          "frac": (SWEEP_BYTES_PER_PIXEL * reg_rate / 1e9 / peak
                                   if reg_rate else None),
-                         "note": "the whole registration call (set-up + persistent launch) "
+                         "frac_without_cost_sweep": (SWEEP_BYTES_PER_PIXEL * reg10_rate / 1e9 /
+                                                     peak if reg10_rate else None),
+                         "note": "the whole registration call (set-up, persistent launch, and "
+                                 "the cost sweep + cost the adjoint needs: 11 sweeps streamed) "
                                  "against the metric's 10 iterations at 32 B per "
-                                 "correspondence; the call also streams the cost sweep that "
-                                 "the adjoint needs (11 sweeps)"}},
+                                 "correspondence; frac_without_cost_sweep: the call without "
+                                 "want_cost (set-up + persistent launch)"}},
         "sweep_variant": {"variant": variant, "tile_pixels": vt, "ctas_per_sm": vc,
                           "tuning_ms": {str(k): v for k, v in tune_ms.items()}},
         "kernels": kernels,
@@ -877,6 +1051,12 @@ def run_workload(args):
                                              ps.pair_conf_min, delta=DELTA, iters=ITERS,
                                              precision=precision, out=S, status=st), reps)
         assert ctx.sync_status() == 0, ctx.last_error()
+        v, tms = ctx.last_align_variant()
+        if v >= 0:
+            t, c = ec3r.align_variant_info(v)
+            out.setdefault("sweep_variants", []).append(
+                {"pairs": ps.n_pairs, "variant": v, "tile_pixels": t, "ctas_per_sm": c,
+                 "tuning_ms": {str(k): x for k, x in tms.items()}})
         return n_valid, ms, S, st
 
     if args.workload == "pair1":
@@ -886,6 +1066,11 @@ def run_workload(args):
             out[prec] = {"pt_iter_per_s": n * ITERS / (ms * 1e-3), "ms_per_call": ms,
                          "valid": n}
         out["note"] = "one 294x518 pair, 10 IRLS solves: latency-bound (4.9 MB, L2-resident)"
+        host = [_host_pair(ps, 0)]
+        out["oracle_error"] = {}
+        for prec in ("fp64", "fp32c"):
+            n, ms, S, st = reg_rate(ps, prec, reps=1)
+            out["oracle_error"][prec] = registration_error(S, st, host, [0])
     elif args.workload == "adjoint1":
         ps = synth.make_pair(synth.SEED_BASE + 4, H=294, W=518, sigma=0.005, device=dev)
         n, ms_f, S, st = reg_rate(ps, reps=50)
@@ -901,11 +1086,14 @@ def run_workload(args):
         ms = _time(fwd_bwd, 20)
         out.update({"forward_ms": ms_f, "forward_backward_ms": ms, "valid": n,
                     "note": "config-1 pair, 10 checkpointed IRLS iterations differentiated"})
+        out["oracle_error"] = adjoint_error(ctx, ps, gS, gc)
     elif args.workload == "loops512":
-        ps = synth.make_loop_batch(synth.SEED_BASE + 3, n_pairs=512, H=294, W=518, device=dev)
+        npairs = args.loop_pairs
+        ps = synth.make_loop_batch(synth.SEED_BASE + 3, n_pairs=npairs, H=294, W=518,
+                                   device=dev)
         n, ms, S, st = reg_rate(ps, reps=5)
         px = int(ps.link_off[-1]) * ps.hw
-        out["registration"] = {"pairs": 512, "valid": n, "ms": ms,
+        out["registration"] = {"pairs": npairs, "valid": n, "ms": ms,
                                "pt_iter_per_s": n * ITERS / (ms * 1e-3),
                                "gbs_at_32B_per_pixel": 32.0 * px * ITERS / (ms * 1e-3) / 1e9}
         g = synth.make_pose_graph(synth.SEED_BASE + 3, 200, 40, device="cpu")
@@ -916,6 +1104,10 @@ def run_workload(args):
         pg_ms = _time(lambda: ctx.pose_graph_correct(nodes, g.ei.numpy(), g.ej.numpy(), Tij,
                                                      iters=10), 5)
         out["pose_graph"] = {"nodes": 200, "edges": len(g.ei), "gn_iters": 10, "ms": pg_ms}
+        ks = [0, npairs // 2, npairs - 1]
+        out["oracle_error"] = {
+            "registration": registration_error(S, st, [_host_pair(ps, k) for k in ks], ks),
+            "pose_graph": pose_graph_error(ctx, g.ei.numpy(), g.ej.numpy(), Tij, 200, 2)}
     elif args.workload == "map1000":
         M = 1000
         ch = synth.make_chain(synth.SEED_BASE + 5, M=M, F=5, H=392, W=518, device=dev)
@@ -935,6 +1127,8 @@ def run_workload(args):
         out["registration"] = {"pairs": bank.n_pairs, "valid": n, "ms": ms,
                                "pt_iter_per_s": n * ITERS / (ms * 1e-3),
                                "gbs_at_32B_per_pixel": 32.0 * px * ITERS / (ms * 1e-3) / 1e9}
+        ks = [0, 500, 998, 1000, 1150, 1298]
+        err = {"registration": registration_error(S, st, [_host_pair(bank, k) for k in ks], ks)}
         del bank
         g = synth.make_pose_graph(synth.SEED_BASE + 5, M, 300, device="cpu")
         Tij = ec3r.sim3_rows(g.T_meas.s, g.T_meas.R, g.T_meas.t).to(dev)
@@ -944,6 +1138,7 @@ def run_workload(args):
         pg_ms = _time(lambda: ctx.pose_graph_correct(nodes, g.ei.numpy(), g.ej.numpy(), Tij,
                                                      iters=10), 1, warm=1)
         out["pose_graph"] = {"nodes": M, "edges": len(g.ei), "gn_iters": 10, "ms": pg_ms}
+        err["pose_graph"] = pose_graph_error(ctx, g.ei.numpy(), g.ej.numpy(), Tij, M, 1)
         xyz = ch.xyz.view(M, -1, 3)
         conf = ch.conf.view(M, -1)
         kept = int((conf > 1.0).sum())
@@ -972,6 +1167,8 @@ def run_workload(args):
         cms = _time(lambda: ctx.correct_points(pts, refs, xyz, conf, poses, threshold=1.0,
                                                n_corrected=ncor), 5)
         assert ctx.sync_status() == 0
+        err["fusion"], err["point_correction"] = map_fusion_error(xyz, conf, ox, oi, pts, refs)
+        out["oracle_error"] = err
         out["point_correction"] = {"points": n_sp, "ms": cms,
                                    "points_per_s": n_sp / (cms * 1e-3),
                                    "note": "random references: 16 B gathered per point"}
@@ -992,6 +1189,9 @@ def run_workload(args):
                                                    dps.src, dps.tgt, delta=DELTA, iters=ITERS,
                                                    out=S, status=st), 10)
         assert ctx.sync_status() == 0 and int((st != 0).sum()) == 0
+        ks = [0, 99, 198]
+        out["oracle_error"] = {"registration": registration_error(
+            S, st, [_host_depth_pair(dps, k) for k in ks], ks)}
         ctx.profile(True)
         ctx.profile_read()
         ctx.align_submaps_depth(dps.depth, dps.conf, dps.cams, dps.link_off, dps.src, dps.tgt,
@@ -1058,6 +1258,7 @@ def run_workload(args):
             "similarity_tflops": flops / (tc_ms * 1e-3) / 1e12,
             "similarity_frac_of_bf16_peak": flops / (tc_ms * 1e-3) / 1e12 / bf16_peak,
             "bf16_peak_tflops": bf16_peak}
+        out["oracle_error"] = similarity_error(ctx, E, kw)
     out["peak_gbs"] = peak
     out["peak_kind"] = peak_kind
     if not args.no_oracle:
@@ -1087,6 +1288,9 @@ def main():
                          "strong: one map split over the ranks")
     ap.add_argument("--variant", type=int, default=-1,
                     help="force registration sweep variant V (default: chosen by timing)")
+    ap.add_argument("--loop-pairs", type=int, default=512,
+                    help="pairs of loops512 (default 512); smaller values are for profiling "
+                         "only")
     ap.add_argument("--keyframes", type=int, default=32768,
                     help="keyframes of loops32k (default 32768); smaller values are for "
                          "profiling only")
