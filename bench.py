@@ -502,8 +502,11 @@ def similarity_error(ctx, E, kw, n_rows=64):
 
 def adjoint_error(ctx, ps, gS, gc, delta=DELTA, iters=ITERS):
     """The backward call's gradients against the oracle's FP64 reverse mode
-    (element by element, |d| <= 2e-3 |g| + 1e-5 max|g|, points away from the
-    Huber kink): the largest ratio of error to bound per gradient."""
+    (element by element, |d| <= 2e-3 |g| + 1e-5 max|g| + f32, points away from
+    the Huber kink; f32 = twice the largest change of the oracle's gradient
+    when its weighting estimate is rounded to FP32, the FP32-residual design's
+    own effect): the largest ratio of error to bound per gradient, and the
+    ratio without f32."""
     import numpy as np
     from oracle import adjoint as oadj
     from oracle import register as reg
@@ -516,20 +519,33 @@ def adjoint_error(ctx, ps, gS, gc, delta=DELTA, iters=ITERS):
     gP, gQ, gw = oadj.irls_backward(P[valid], Q[valid], w, delta, tape, Sh, g[0],
                                     g[1:10].reshape(3, 3), g[10:13], float(gc[0]))
     gcp, gcq = oadj.weight_grads(gw, cp[valid], cq[valid])
+    S32, tape32, _ = oadj.irls_forward(P[valid], Q[valid], w, delta, iters,
+                                       estimate_dtype=np.float32)
+    gP32, gQ32, gw32 = oadj.irls_backward(P[valid], Q[valid], w, delta, tape32, S32, g[0],
+                                          g[1:10].reshape(3, 3), g[10:13], float(gc[0]))
+    gcp32, gcq32 = oadj.weight_grads(gw32, cp[valid], cq[valid])
     far = np.ones(int(valid.sum()), bool)
     for rec in tape[1:]:
         far &= np.abs(rec["r"] - delta) >= 1e-4
     gxh, gch = gx.cpu().double().numpy(), gcf.cpu().double().numpy()
+    f32x = 2.0 * max(np.abs(gP32 - gP)[far].max(), np.abs(gQ32 - gQ)[far].max())
+    f32c = 2.0 * max(np.abs(gcp32 - gcp)[far].max(), np.abs(gcq32 - gcq)[far].max())
 
-    def ratio(got, ref):
-        b = 2e-3 * np.abs(ref) + 1e-5 * np.abs(ref).max()
+    def ratio(got, ref, f32):
+        b = 2e-3 * np.abs(ref) + 1e-5 * np.abs(ref).max() + f32
         return float((np.abs(got - ref) / b).max())
+
+    def both(a, b, c, d, f32):
+        return max(ratio(a, b, f32), ratio(c, d, f32)), max(ratio(a, b, 0.0), ratio(c, d, 0.0))
+    dx = both(gxh[0][valid][far], gP[far], gxh[1][valid][far], gQ[far], f32x)
+    dc = both(gch[0][valid][far], gcp[far], gch[1][valid][far], gcq[far], f32c)
     return {"points": int(far.sum()),
-            "dxyz_error_over_bound": max(ratio(gxh[0][valid][far], gP[far]),
-                                         ratio(gxh[1][valid][far], gQ[far])),
-            "dconf_error_over_bound": max(ratio(gch[0][valid][far], gcp[far]),
-                                          ratio(gch[1][valid][far], gcq[far])),
-            "bound": "|GPU - oracle| <= 2e-3 |oracle| + 1e-5 max|oracle| per element"}
+            "dxyz_error_over_bound": dx[0], "dconf_error_over_bound": dc[0],
+            "dxyz_error_over_bound_without_f32": dx[1],
+            "dconf_error_over_bound_without_f32": dc[1],
+            "f32_over_max": {"dxyz": f32x / max(np.abs(gP).max(), np.abs(gQ).max()),
+                             "dconf": f32c / max(np.abs(gcp).max(), np.abs(gcq).max())},
+            "bound": "|GPU - oracle| <= 2e-3 |oracle| + 1e-5 max|oracle| + f32 per element"}
 
 
 def run_reference(args):
@@ -821,9 +837,11 @@ def run_ours(args):
         return
 
     peak, peak_kind = peaks()
-    # the dominant kernel: the persistent registration launch (the 10 Huber-IRLS
-    # sweeps and every per-pair solve of the call), 32 B per link pixel per sweep
-    sweeps = ITERS
+    # the dominant kernel: the persistent registration launch (the Huber-IRLS
+    # sweeps and per-pair solves of the call but the last sweep and solve,
+    # which run in the final-sweep launch when the adjoint needs the cost),
+    # 32 B per link pixel per sweep
+    sweeps = ITERS - 1 if "irls_final_sweep" in prof else ITERS
     reg_k = prof.get("irls_register", (0.0, 0))
     reg_launch_ms = reg_k[0] / max(reg_k[1], 1)
     reg_bytes = SWEEP_BYTES_PER_PIXEL * pix * sweeps
@@ -834,16 +852,16 @@ def run_ours(args):
     fuse_ms = sum(prof.get(k, (0.0, 0))[0] for k in ("fuse_count", "fuse_scan", "fuse_scatter"))
     pg_ms = sum(v[0] for k, v in prof.items() if k.startswith("pg_"))
     adj_ms = sum(v[0] for k, v in prof.items() if k.startswith("adj_"))
-    # the whole registration call: set-up, the persistent launch, and the cost
-    # sweep and cost that the adjoint needs; and the same without the cost
+    # the whole registration call: set-up, the persistent launch, and the final
+    # sweep with the last solve and the cost that the adjoint needs (or, for
+    # the grid variant, every sweep, solve and the cost sweep as grids)
     reg_ms = sum(prof.get(k, (0.0, 0))[0]
-                 for k in ("align_setup", "irls_register", "irls_cost_sweep", "irls_cost"))
+                 for k in ("align_setup", "irls_register", "irls_final_sweep", "irls_cost",
+                           "irls_sweep_fp32", "sim3_solve"))
     reg_rate = n_valid * ITERS * args.steps / (reg_ms * 1e-3) if reg_ms else None
-    reg10_ms = sum(prof.get(k, (0.0, 0))[0] for k in ("align_setup", "irls_register"))
-    reg10_rate = n_valid * ITERS * args.steps / (reg10_ms * 1e-3) if reg10_ms else None
     fuse_gbs = 26.0 * n_fuse * args.steps / (fuse_ms * 1e-3) / 1e9 if fuse_ms else None
     variant, tune_ms = ctx.last_align_variant()
-    vt, vc = ec3r.align_variant_info(variant) if variant >= 0 else (None, None)
+    vt, vc, vp = ec3r.align_variant_info(variant) if variant >= 0 else (None, None, None)
     # ---- the oracle on sampled pairs of this workload, on every host core:
     # its rate (cpu_baseline) and each result's error against it (oracle_error)
     cpu_base = oracle_error = None
@@ -868,8 +886,10 @@ def run_ours(args):
                                  if variant in REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP else None),
                      "algorithmic_bytes_per_launch": reg_bytes,
                      "launch_ms": reg_launch_ms,
-                     "note": "one persistent launch per call: the 10 Huber-IRLS sweeps and "
-                             "every per-pair FP64 solve; 32 B per link pixel per sweep",
+                     "sweeps_per_launch": sweeps,
+                     "note": "one persistent launch per call: the Huber-IRLS sweeps and "
+                             "per-pair FP64 solves but the last (which the final-sweep launch "
+                             "runs with the cost); 32 B per link pixel per sweep",
                      "registration": {
                          "pt_iter_per_s": reg_rate,
                          "bytes_per_pt_iter": SWEEP_BYTES_PER_PIXEL,
@@ -877,14 +897,12 @@ def run_ours(args):
                                       if reg_rate else None),
                          "frac": (SWEEP_BYTES_PER_PIXEL * reg_rate / 1e9 / peak
                                   if reg_rate else None),
-                         "frac_without_cost_sweep": (SWEEP_BYTES_PER_PIXEL * reg10_rate / 1e9 /
-                                                     peak if reg10_rate else None),
-                         "note": "the whole registration call (set-up, persistent launch, and "
-                                 "the cost sweep + cost the adjoint needs: 11 sweeps streamed) "
-                                 "against the metric's 10 iterations at 32 B per "
-                                 "correspondence; frac_without_cost_sweep: the call without "
-                                 "want_cost (set-up + persistent launch)"}},
+                         "note": "the whole registration call (set-up, persistent launch, "
+                                 "final sweep with the last solve and the cost the adjoint "
+                                 "needs: 10 sweeps streamed) against the metric's 10 "
+                                 "iterations at 32 B per correspondence"}},
         "sweep_variant": {"variant": variant, "tile_pixels": vt, "ctas_per_sm": vc,
+                          "persistent": vp,
                           "tuning_ms": {str(k): v for k, v in tune_ms.items()}},
         "kernels": kernels,
         "profiled_pass": {"ms_per_step": ms_profiled / args.steps,
@@ -1053,9 +1071,10 @@ def run_workload(args):
         assert ctx.sync_status() == 0, ctx.last_error()
         v, tms = ctx.last_align_variant()
         if v >= 0:
-            t, c = ec3r.align_variant_info(v)
+            t, c, pers = ec3r.align_variant_info(v)
             out.setdefault("sweep_variants", []).append(
                 {"pairs": ps.n_pairs, "variant": v, "tile_pixels": t, "ctas_per_sm": c,
+                 "persistent": pers,
                  "tuning_ms": {str(k): x for k, x in tms.items()}})
         return n_valid, ms, S, st
 

@@ -179,11 +179,16 @@ void ec3r_align_opts_default(ec3r_align_opts* o);
  * by iteration to resident CTAs, the CTA that completes a pair's tiles of an
  * iteration solves that pair, and a pair's next sweep waits only for its own
  * solve (a bounded wait: one that runs out raises EC3R_ERR_TIMEOUT at
- * ec3r_sync_status).  With FP64 accumulation, `iters` x (sweep, solve) grids.
+ * ec3r_sync_status).  With want_cost the last sweep is a second launch that
+ * starts as the first one's CTAs retire and also accumulates the sums from
+ * which the cost under the last solve follows exactly (no extra pass over the
+ * correspondences).  With FP64 accumulation, `iters` x (sweep, solve) grids
+ * and, with want_cost, a cost sweep.
  * Replayed from a CUDA graph cached per argument set when `stream` is not
  * itself being captured.
  *
- * Variants.  The FP32 launch has variants (pixels per tile x CTAs per SM,
+ * Variants.  The FP32 path has variants (pixels per tile x CTAs per SM of the
+ * persistent launch, and one grid per sweep and per solve instead:
  * ec3r_align_variant_info).  The tile size groups the FP32 sums, so results
  * of different variants differ at FP32 rounding level; each variant is
  * deterministic.  Unless one is forced (ec3r_align_set_variant), the first
@@ -195,7 +200,7 @@ void ec3r_align_opts_default(ec3r_align_opts* o);
  * captured first call uses variant 0 untimed).  Other pointmaps use one fixed
  * configuration.
  *
- * Workspace: 152 bytes per 4096 link pixels, 4 bytes per link, and per pair
+ * Workspace: 300 bytes per 4096 link pixels, 4 bytes per link, and per pair
  * 444 bytes plus 448 bytes per iteration (the checkpoints that
  * ec3r_align_submaps_backward reuses).
  */
@@ -262,8 +267,9 @@ ec3r_status ec3r_align_submaps_backward(ec3r_ctx* ctx, const float* d_xyz, const
 
 /*
  * Sweep variants of ec3r_align_submaps (FP32 moments): their count, and for
- * variant v its tile size (pixels) and CTAs per SM (EC3R_ERR_INVALID_ARG for v
- * out of range).  ec3r_align_set_variant forces variant v for every later
+ * variant v its tile size (pixels), CTAs per SM and whether it is the
+ * persistent launch (1) or one grid per sweep and per solve (0)
+ * (EC3R_ERR_INVALID_ARG for v out of range).  ec3r_align_set_variant forces variant v for every later
  * call on the context, or, with v = -1 (the default), lets each size bucket
  * use the variant its first call timed fastest.  ec3r_align_last_variant gives
  * the variant of the last call (-1: a mode without variants) and, if ms is not
@@ -271,7 +277,8 @@ ec3r_status ec3r_align_submaps_backward(ec3r_ctx* ctx, const float* d_xyz, const
  * from the timing of that call's bucket (-1 where none was measured).
  */
 int ec3r_align_variant_count(void);
-ec3r_status ec3r_align_variant_info(int v, int* tile_pixels, int* ctas_per_sm);
+ec3r_status ec3r_align_variant_info(int v, int* tile_pixels, int* ctas_per_sm,
+                                    int* persistent);
 ec3r_status ec3r_align_set_variant(ec3r_ctx* ctx, int v);
 ec3r_status ec3r_align_last_variant(const ec3r_ctx* ctx, int* variant, float* ms);
 

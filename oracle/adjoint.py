@@ -93,24 +93,44 @@ def _solve_bwd(f, P, Q, om, gs, gR, gt):
     return g_om, gP, gQ
 
 
-def irls_forward(P, Q, w, delta, iters):
-    """Forward pass keeping what the reverse pass needs."""
+def _residual(S, P, Q, estimate_dtype):
+    """e = s R p + t - q; with estimate_dtype, the estimate as a path that
+    holds it in that type uses it: A = s R and b = t + A m_p - m_q around the
+    means m of P and Q, rounded to estimate_dtype, e = A (p - m_p) + b - (q - m_q)
+    (everything else in FP64)."""
+    if estimate_dtype is None:
+        return sim3.act(S, P) - Q
+    s, R, t = S
+    mp, mq = P.mean(0), Q.mean(0)
+    A = s * R
+    b = t + A @ mp - mq
+    A = A.astype(estimate_dtype).astype(np.float64)
+    b = b.astype(estimate_dtype).astype(np.float64)
+    return (P - mp) @ A.T + b - (Q - mq)
+
+
+def irls_forward(P, Q, w, delta, iters, estimate_dtype=None):
+    """Forward pass keeping what the reverse pass needs.  estimate_dtype
+    (default None: FP64 throughout) rounds the estimate that weights the next
+    iteration, as ``_residual`` describes: a model of a path that keeps it in
+    FP32, used to size that rounding's effect on the gradients."""
     P = np.asarray(P, np.float64)
     Q = np.asarray(Q, np.float64)
     w = np.asarray(w, np.float64)
     tape = []
     S = None
     for k in range(1, iters + 1):
+        e = None
         if k == 1:
             r = None
             h = np.ones_like(w)
         else:
-            e = sim3.act(S, P) - Q
+            e = _residual(S, P, Q, estimate_dtype)
             r = np.linalg.norm(e, axis=1)
             h = np.where(r <= delta, 1.0, delta / np.where(r > 0, r, 1.0))
         om = w * h
         f = _solve_fwd(P, Q, om)
-        tape.append(dict(f=f, r=r, h=h, om=om, S_prev=S))
+        tape.append(dict(f=f, r=r, h=h, om=om, S_prev=S, e=e))
         if not f["ok"]:
             return None, tape, 0.0
         S = (f["s"], f["R"], f["t"])
@@ -161,7 +181,7 @@ def irls_backward(P, Q, w, delta, tape, S, gs, gR, gt, gcost):
         r = rec["r"]
         gr = np.where(r > delta, -gh * delta / np.where(r > 0, r * r, 1.0), 0.0)
         sp, Rp, tp = rec["S_prev"]
-        e = sim3.act(rec["S_prev"], P) - Q
+        e = rec["e"]
         ge = (gr / np.where(r > 0, r, 1.0))[:, None] * e
         gP += sp * (ge @ Rp)
         gQ -= ge

@@ -29,7 +29,11 @@ namespace align {
 // --------------------------------------------------------------------------
 // set-up
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(THREADS) k_setup(
+// One thread per sampled correspondence: the 1024 pivot samples are one
+// round of loads instead of four.
+constexpr int SETUP_THREADS = 1024;
+
+__global__ void __launch_bounds__(SETUP_THREADS) k_setup(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t n_frames, int64_t hw,
     int n_pairs, int64_t n_links, const int32_t* __restrict__ link_off,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
@@ -39,13 +43,13 @@ __global__ void __launch_bounds__(THREADS) k_setup(
     double* __restrict__ cost_sums) {
   const int k = blockIdx.x;
   __shared__ int bad;
-  __shared__ float red[THREADS / 32][7];
+  __shared__ float red[SETUP_THREADS / 32][7];
   // a malformed offset array (k_check_offsets) marks every pair of the batch
   const int64_t l0 = *malformed ? 0 : link_off[k], l1 = *malformed ? 0 : link_off[k + 1];
   if (threadIdx.x == 0) bad = *malformed;
   __syncthreads();
   if (!bad) {
-    for (int64_t l = l0 + threadIdx.x; l < l1; l += THREADS) {
+    for (int64_t l = l0 + threadIdx.x; l < l1; l += SETUP_THREADS) {
       const int a = src[l], b = tgt[l];
       if (a < 0 || a >= n_frames || b < 0 || b >= n_frames) bad = 1;
     }
@@ -53,13 +57,13 @@ __global__ void __launch_bounds__(THREADS) k_setup(
   __syncthreads();
   const float cmin = pair_cmin ? pair_cmin[k] : cmin_default;
   if (!bad) {
-    for (int64_t l = l0 + threadIdx.x; l < l1; l += THREADS) link_pair[l] = k;
+    for (int64_t l = l0 + threadIdx.x; l < l1; l += SETUP_THREADS) link_pair[l] = k;
   }
   // pivot: mean of up to 1024 valid correspondences sampled evenly
   float acc[7] = {0, 0, 0, 0, 0, 0, 0};
   if (!bad && l1 > l0) {
     const int64_t npix = (l1 - l0) * hw;
-    for (int j = threadIdx.x; j < 1024; j += THREADS) {
+    for (int j = threadIdx.x; j < 1024; j += SETUP_THREADS) {
       int64_t f = (int64_t)((double)j * (double)npix / 1024.0);
       if (f >= npix) f = npix - 1;
       const int64_t l = l0 + f / hw, px = f % hw;
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(THREADS) k_setup(
   __syncthreads();
   if (threadIdx.x == 0) {
     float s[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int w = 0; w < THREADS / 32; ++w)
+    for (int w = 0; w < SETUP_THREADS / 32; ++w)
       for (int m = 0; m < 7; ++m) s[m] += red[w][m];
     PairState& S = st[k];
     const float inv = s[6] > 0.f ? 1.f / s[6] : 0.f;
@@ -311,7 +315,7 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "problem too large for one call");
   EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  void *p_state, *p_part, *p_lp, *p_ck, *p_cs, *p_ctl;
+  void *p_state, *p_part, *p_lp, *p_ck, *p_cs, *p_ctl, *p_cp;
   ec3r_status st;
   const size_t ctl_bytes = reg_ctl_bytes(n_pairs);
   if ((st = ensure_buf(ctx, "align.state", sizeof(PairState) * (size_t)n_pairs, s, &p_state)) ||
@@ -324,7 +328,11 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
                        sizeof(double) * CKPT * (size_t)n_pairs * (size_t)opts->iters, s, &p_ck)) ||
       (st = ensure_buf(ctx, "align.cost_sums", sizeof(double) * CS_STRIDE * (size_t)n_pairs, s,
                        &p_cs)) ||
-      (st = ensure_buf(ctx, "align.ctl", ctl_bytes, s, &p_ctl)))
+      (st = ensure_buf(ctx, "align.ctl", ctl_bytes, s, &p_ctl)) ||
+      (st = ensure_buf(ctx, "align.final_partials",
+                       sizeof(double) * FINAL_VALUES *
+                           (size_t)(n_links * ((hw + TILE - 1) / TILE) + 1),
+                       s, &p_cp)))
     return st;
   // (buffers that grew dropped the graphs holding older ones; re-read them all)
   PairState* state = (PairState*)ctx->bufs["align.state"].ptr;
@@ -333,6 +341,7 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
   double* ckpt = (double*)ctx->bufs["align.ckpt"].ptr;
   double* cost_sums = (double*)ctx->bufs["align.cost_sums"].ptr;
   void* ctl = ctx->bufs["align.ctl"].ptr;
+  double* final_partials = (double*)ctx->bufs["align.final_partials"].ptr;
   const bool vec =
       (hw % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0) && ((uintptr_t)d_conf % 16 == 0);
   const bool fp64 = opts->precision == EC3R_PREC_FP64;
@@ -347,56 +356,54 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
                                        cs));
     traced(ctx, cs, "align_setup", [&] {
       k_check_offsets<<<1, 1024, 0, cs>>>(d_link_off, n_pairs, n_links, malformed);
-      k_setup<<<n_pairs, THREADS, 0, cs>>>(d_xyz, d_conf, n_frames, hw, n_pairs, n_links,
+      k_setup<<<n_pairs, SETUP_THREADS, 0, cs>>>(d_xyz, d_conf, n_frames, hw, n_pairs, n_links,
                                            d_link_off, d_src, d_tgt, d_pair_conf_min,
                                            o.conf_min, link_pair, malformed, state,
                                            ctx->d_flags, d_out, d_pair_status,
                                            o.want_cost ? d_pair_cost : nullptr, cost_sums);
     });
-    if (!fp64) {
+    if (!fp64 && !(vec && v == reg_grid_variant())) {
+      // With the cost, the last Huber sweep runs as its own grid that also
+      // forms the cost and its sums (k_final_sweep, overlapping the
+      // persistent launch's tail); without, the persistent launch runs all.
+      const int n_sweeps = o.want_cost ? o.iters - 1 : o.iters;
       ec3r_status r = EC3R_OK;
       traced(ctx, cs, "irls_register", [&] {
         r = launch_register(ctx, cs, v, vec, d_xyz, d_conf, hw, n_pairs, n_links, d_link_off,
                             d_src, d_tgt, link_pair, state, partials, o.huber_delta,
-                            o.weight_rule, o.iters, d_out, d_pair_status,
+                            o.weight_rule, o.iters, n_sweeps, d_out, d_pair_status,
                             o.want_cost ? d_pair_cost : nullptr, cost_sums, ckpt, ctl,
                             ctl_bytes);
       });
       if (r != EC3R_OK) return r;
       if (o.want_cost) {
-        // the cost sweep (weights of S_{K-1}, residuals under S_K) as its own
-        // grid, then the cost and the adjoint's cost-term sums per pair
-        const int64_t tpl = (hw + TILE - 1) / TILE;
-        const int64_t n_tiles = n_links * tpl;
-        const float dl = o.iters == 1 ? FLT_MAX : o.huber_delta;
-        if (n_tiles > 0) traced(ctx, cs, "irls_cost_sweep", [&] {
-          if (vec)
-            launch_sweep<float, true>(COST, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
-                                      d_tgt, link_pair, state, dl, o.weight_rule, partials);
-          else
-            launch_sweep<float, false>(COST, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
-                                       d_tgt, link_pair, state, dl, o.weight_rule, partials);
+        traced(ctx, cs, "irls_final_sweep", [&] {
+          r = launch_final(ctx, cs, vec, n_sweeps > 0 && !ctx->profiling, d_xyz, d_conf, hw,
+                           n_pairs, n_links, d_link_off, d_src, d_tgt, link_pair, state,
+                           final_partials, o.huber_delta, o.weight_rule, o.iters, d_out,
+                           d_pair_status, d_pair_cost, cost_sums, ckpt, ctl);
         });
-        traced(ctx, cs, "irls_cost", [&] {
-          k_cost<<<n_pairs, 32, 0, cs>>>(n_pairs, d_link_off, (int)tpl, partials, state,
-                                         d_pair_cost, cost_sums);
-        });
+        if (r != EC3R_OK) return r;
       }
     } else {
-      // FP64 accumulation (the plain baseline): one grid per sweep and per solve
+      // one grid per sweep and per solve: the FP64-accumulation mode (the plain
+      // baseline), and with FP32 moments the autotuner's grid variant
       const int64_t tpl = (hw + TILE - 1) / TILE;
       const int64_t n_tiles = n_links * tpl;
       for (int it = 1; it <= o.iters + (o.want_cost ? 1 : 0); ++it) {
         const int kind = it == 1 ? FIRST : (it > o.iters ? COST : IRLS);
         // the cost of a single solve uses h = 1, which a huge delta reproduces
         const float dl = (kind == COST && o.iters == 1) ? FLT_MAX : o.huber_delta;
-        if (n_tiles > 0) traced(ctx, cs, "irls_sweep_fp64", [&] {
-          if (vec)
+        if (n_tiles > 0) traced(ctx, cs, fp64 ? "irls_sweep_fp64" : "irls_sweep_fp32", [&] {
+          if (fp64 && vec)
             launch_sweep<double, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
                                        d_tgt, link_pair, state, dl, o.weight_rule, partials);
-          else
+          else if (fp64)
             launch_sweep<double, false>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
                                         d_tgt, link_pair, state, dl, o.weight_rule, partials);
+          else
+            launch_sweep<float, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
+                                      d_tgt, link_pair, state, dl, o.weight_rule, partials);
         });
         if (kind == COST)
           traced(ctx, cs, "irls_cost", [&] {
@@ -499,8 +506,10 @@ ec3r_status ec3r_align_set_variant(ec3r_ctx* ctx, int v) {
 
 int ec3r_align_variant_count(void) { return reg_variant_count(); }
 
-ec3r_status ec3r_align_variant_info(int v, int* tile_pixels, int* ctas_per_sm) {
-  if (!tile_pixels || !ctas_per_sm || !reg_variant_info(v, tile_pixels, ctas_per_sm))
+ec3r_status ec3r_align_variant_info(int v, int* tile_pixels, int* ctas_per_sm,
+                                    int* persistent) {
+  if (!tile_pixels || !ctas_per_sm || !persistent ||
+      !reg_variant_info(v, tile_pixels, ctas_per_sm, persistent))
     return EC3R_ERR_INVALID_ARG;
   return EC3R_OK;
 }
@@ -619,7 +628,7 @@ extern "C" ec3r_status ec3r_align_submaps_noalloc(
   }
   int32_t* malformed = link_pair + n_links + 1;
   k_check_offsets<<<1, 1024, 0, cs>>>(d_link_off, n_pairs, n_links, malformed);
-  k_setup<<<n_pairs, THREADS, 0, cs>>>(d_xyz, d_conf, n_frames, hw, n_pairs, n_links,
+  k_setup<<<n_pairs, SETUP_THREADS, 0, cs>>>(d_xyz, d_conf, n_frames, hw, n_pairs, n_links,
                                        d_link_off, d_src, d_tgt, d_pair_conf_min, o.conf_min,
                                        link_pair, malformed, state, flags, d_out, d_pair_status,
                                        o.want_cost ? d_pair_cost : nullptr, nullptr);

@@ -440,12 +440,67 @@ static __global__ void __launch_bounds__(1024) k_check_offsets(
   if (threadIdx.x == 0) *malformed = bad ? 1 : 0;
 }
 
+// --------------------------------------------------------------------------
+// persistent launches: per-pair epochs (release / acquire) and bounded waits
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Epoch of a pair that no later sweep works on (degenerate): every wait passes.
+constexpr unsigned EPOCH_DONE = 0xffffffffu;
+
+// Waits until *ep >= want.  Gives up after `limit` cycles or 2^22 polls,
+// whichever comes first, or as soon as another CTA has given up (*abort):
+// then raises FLAG_TIMEOUT, sets *abort so that every other CTA stops too, and
+// returns false.
+static __device__ __noinline__ bool wait_epoch(const unsigned* ep, unsigned want, unsigned* abort,
+                                        unsigned* flags, long long limit) {
+  if (ld_acquire_u32(ep) >= want) return true;
+  const long long t0 = clock64();
+  unsigned ns = 32;
+  for (int poll = 0; poll < (1 << 22); ++poll) {
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+    if (ld_acquire_u32(ep) >= want) return true;
+    if (ld_acquire_u32(abort) || clock64() - t0 > limit) break;
+  }
+  atomicOr(flags, FLAG_TIMEOUT);
+  atomicExch(abort, 1u);
+  return false;
+}
+
+// FP64 tile sums from L2 (the partials were written by other CTAs during
+// this launch): four accumulators, fixed order, as tile_sum.
+template <int NV>
+__device__ __forceinline__ double tile_sum_cg(const double* partials, int64_t t0, int64_t t1,
+                                              int v) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t t = t0;
+#pragma unroll 2
+  for (; t + 4 <= t1; t += 4) {
+    s0 += __ldcg(&partials[t * NV + v]);
+    s1 += __ldcg(&partials[(t + 1) * NV + v]);
+    s2 += __ldcg(&partials[(t + 2) * NV + v]);
+    s3 += __ldcg(&partials[(t + 3) * NV + v]);
+  }
+  for (; t < t1; ++t) s0 += __ldcg(&partials[t * NV + v]);
+  return (s0 + s1) + (s2 + s3);
+}
+
 // The persistent registration with FP32 moments (align_persist.cu): the
 // autotuner's variants and the launch.  Variant v < 0 or out of range means
 // the first (8192-pixel tiles, four CTAs per SM); unaligned pointmaps have one
 // fixed configuration.
 int reg_variant_count();
-bool reg_variant_info(int v, int* tile, int* ctas);
+int reg_grid_variant();  // the variant that runs separate grids per sweep and solve
+bool reg_variant_info(int v, int* tile, int* ctas, int* persistent);
 int reg_min_tile();
 size_t reg_ctl_bytes(int n_pairs);
 ec3r_status launch_register(ec3r_ctx* ctx, cudaStream_t s, int v, bool vec,
@@ -453,8 +508,18 @@ ec3r_status launch_register(ec3r_ctx* ctx, cudaStream_t s, int v, bool vec,
                             int64_t n_links, const int32_t* link_off, const int32_t* src,
                             const int32_t* tgt, const int32_t* link_pair, PairState* st,
                             double* partials, float delta, int rule, int iters,
-                            ec3r_sim3* out, int32_t* status_out, double* cost,
+                            int n_sweeps, ec3r_sim3* out, int32_t* status_out, double* cost,
                             double* cost_sums, double* ckpt, void* ctl, size_t ctl_bytes);
+// Values per final-sweep tile (the partials buffer of launch_final holds
+// this many doubles per TILE-pixel tile).
+constexpr int FINAL_VALUES = NMOM + 18;
+ec3r_status launch_final(ec3r_ctx* ctx, cudaStream_t s, bool vec, bool after_register,
+                         const float* xyz, const float* conf, int64_t hw, int n_pairs,
+                         int64_t n_links, const int32_t* link_off, const int32_t* src,
+                         const int32_t* tgt, const int32_t* link_pair, PairState* st,
+                         double* partials, float delta, int rule, int iters, ec3r_sim3* out,
+                         int32_t* status_out, double* cost, double* cost_sums, double* ckpt,
+                         void* ctl);
 
 }  // namespace align
 }  // namespace ec3r

@@ -34,44 +34,12 @@
 namespace ec3r {
 namespace align {
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Epoch of a pair that no later sweep works on (degenerate): every wait passes.
-constexpr unsigned EPOCH_DONE = 0xffffffffu;
-
-// Waits until *ep >= want.  Gives up after `limit` cycles or 2^22 polls,
-// whichever comes first, or as soon as another CTA has given up (*abort):
-// then raises FLAG_TIMEOUT, sets *abort so that every other CTA stops too, and
-// returns false.
-__device__ __noinline__ bool wait_epoch(const unsigned* ep, unsigned want, unsigned* abort,
-                                        unsigned* flags, long long limit) {
-  if (ld_acquire_u32(ep) >= want) return true;
-  const long long t0 = clock64();
-  unsigned ns = 32;
-  for (int poll = 0; poll < (1 << 22); ++poll) {
-    __nanosleep(ns);
-    if (ns < 1024) ns <<= 1;
-    if (ld_acquire_u32(ep) >= want) return true;
-    if (ld_acquire_u32(abort) || clock64() - t0 > limit) break;
-  }
-  atomicOr(flags, FLAG_TIMEOUT);
-  atomicExch(abort, 1u);
-  return false;
-}
-
 // One point's contribution to the moments of Huber-IRLS sweep j: weights
 // from the current estimate S_{j-1} (A, b) around the pair's pivots; moments
 // W, Sp, Sq, Spp, Sqp and the count (the solve uses no cost moment).
 // delta = +inf gives h = 1 exactly (the first sweep: plain weighted moments).
 struct HuberOp {
+  static constexpr int NV = NMOM;
   float A[9], b[3], pp[3], pq[3], delta, cmin;
   int rule;
 
@@ -122,16 +90,17 @@ __device__ __forceinline__ void load_op(const PairState* S, int j, float delta, 
 // One tile of TP pixels of one link: per-thread sums of 4 consecutive pixels
 // at a time, then a pairwise warp butterfly; lane 0 of warp w leaves the warp's
 // sums in red[w] (the caller adds the warps in FP64).
-template <bool VEC, int TP>
-__device__ __forceinline__ void sweep_tile(const HuberOp& op, const float* __restrict__ P,
+template <bool VEC, int TP, class OP, int UNROLL = 2>
+__device__ __forceinline__ void sweep_tile(const OP& op, const float* __restrict__ P,
                                            const float* __restrict__ Q,
                                            const float* __restrict__ CP,
                                            const float* __restrict__ CQ, int npx,
-                                           double (*red)[NMOM]) {
-  float acc[NMOM];
+                                           double (*red)[OP::NV]) {
+  constexpr int NV = OP::NV;
+  float acc[NV];
 #pragma unroll
-  for (int m = 0; m < NMOM; ++m) acc[m] = 0.f;
-#pragma unroll 2
+  for (int m = 0; m < NV; ++m) acc[m] = 0.f;
+#pragma unroll UNROLL
   for (int g = threadIdx.x; g < TP / 4; g += THREADS) {
     const int i0 = 4 * g;
     if (i0 >= npx) break;
@@ -156,13 +125,13 @@ __device__ __forceinline__ void sweep_tile(const HuberOp& op, const float* __res
     }
   }
 #pragma unroll
-  for (int m = 0; m < NMOM; ++m)
+  for (int m = 0; m < NV; ++m)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
   const int warp = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0)
 #pragma unroll
-    for (int m = 0; m < NMOM; ++m) red[warp][m] = (double)acc[m];
+    for (int m = 0; m < NV; ++m) red[warp][m] = (double)acc[m];
 }
 
 struct RegArgs {
@@ -179,7 +148,8 @@ struct RegArgs {
   double* partials;    // [n_tiles][NMOM]
   float delta;
   int rule;
-  int iters;           // Huber-IRLS solves (= sweeps)
+  int iters;           // Huber-IRLS solves of the call
+  int n_sweeps;        // sweeps of this launch: iters, or iters - 1 before k_final_sweep
   ec3r_sim3* out;
   int32_t* status_out;
   double* cost;        // nullable: zeroed for pairs that turn degenerate
@@ -193,24 +163,6 @@ struct RegArgs {
   long long wait_cycles;
   int no_epoch;        // test injection: solves publish no epoch
 };
-
-// FP64 tile sums from L2 (the partials were written by other CTAs during
-// this launch): four accumulators, fixed order, as tile_sum.
-template <int NV>
-__device__ __forceinline__ double tile_sum_cg(const double* partials, int64_t t0, int64_t t1,
-                                              int v) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int64_t t = t0;
-#pragma unroll 2
-  for (; t + 4 <= t1; t += 4) {
-    s0 += __ldcg(&partials[t * NV + v]);
-    s1 += __ldcg(&partials[(t + 1) * NV + v]);
-    s2 += __ldcg(&partials[(t + 2) * NV + v]);
-    s3 += __ldcg(&partials[(t + 3) * NV + v]);
-  }
-  for (; t < t1; ++t) s0 += __ldcg(&partials[t * NV + v]);
-  return (s0 + s1) + (s2 + s3);
-}
 
 // Warp 0 of the CTA that completed pair k's sweep j: the solve of iteration j,
 // then the pair's epoch j (EPOCH_DONE if the pair turned degenerate).
@@ -245,12 +197,15 @@ __device__ __noinline__ void finish_pair(const RegArgs& a, int k, int j, double*
 
 template <bool VEC, int TP, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_register(const __grid_constant__ RegArgs a) {
+  // the cost sweep (a programmatic dependent launch) may be scheduled as soon
+  // as this grid's CTAs are resident: it waits per pair on the epochs
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ double red[THREADS / 32][NMOM];
   __shared__ double mom[NMOM];
   __shared__ long long s_item;
   __shared__ int s_k, s_go, s_last;
   __shared__ long long s_pre;  // the next item, fetched while this one is reduced
-  const long long total = (long long)a.iters * a.n_tiles;
+  const long long total = (long long)a.n_sweeps * a.n_tiles;
   if (threadIdx.x == 0) s_pre = -1;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -289,7 +244,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_register(const __grid_constan
         const int64_t rem = a.hw - px0;
         HuberOp op;
         load_op(a.st + k, j, a.delta, a.rule, op);
-        sweep_tile<VEC, TP>(op, a.xyz + (fs * a.hw + px0) * 3, a.xyz + (ft * a.hw + px0) * 3,
+        sweep_tile<VEC, TP, HuberOp>(op, a.xyz + (fs * a.hw + px0) * 3, a.xyz + (ft * a.hw + px0) * 3,
                             a.conf + fs * a.hw + px0, a.conf + ft * a.hw + px0,
                             rem < TP ? (int)rem : TP, red);
       }
@@ -326,6 +281,219 @@ __global__ void __launch_bounds__(THREADS, MINB) k_register(const __grid_constan
 }
 
 // --------------------------------------------------------------------------
+// the last Huber sweep with the cost, overlapping the persistent launch's tail
+// --------------------------------------------------------------------------
+// The cost the adjoint needs, J = sum om |r_K|^2 / sum om (weights om of the
+// last sweep, from S_{K-1}; residual r_K under the returned S_K), and its
+// sums sum om r_K p'^T, sum om r_K, come out of the last Huber sweep itself
+// instead of one more pass over every correspondence.  With r = r_{K-1} and
+// D = S_K - S_{K-1} in the (A, b) form, r_K = r + D_A p' + D_b exactly, so
+//   sum om |r_K|^2 = E + 2 <D_A, G> + 2 D_b . g + <D_A C, D_A> + 2 D_b . D_A Sp + W |D_b|^2
+//   sum om r_K p'^T = G + D_A C + D_b Sp^T,     sum om r_K = g + D_A Sp + W D_b
+// with E = sum om |r|^2, G = sum om r p'^T, g = sum om r, C = sum om p' p'^T
+// accumulated by the sweep beside the moments (Sp = sum om p', W = sum om).
+// Once the IRLS has settled D is small, so the terms that carry it are
+// corrections to sums accumulated directly (no cancellation of large terms).
+constexpr int F_G = NMOM;        // G, row-major (9)
+constexpr int F_GV = NMOM + 9;   // g (3)
+constexpr int F_C = NMOM + 12;   // C: xx, xy, xz, yy, yz, zz (6)
+constexpr int NFIN = FINAL_VALUES;
+
+struct FinalOp {
+  static constexpr int NV = NFIN;
+  float A[9], b[3], pp[3], pq[3], delta, cmin;
+  int rule;
+
+  // the moments exactly as HuberOp forms them, then E (in the M_COST slot), G, g, C
+  __device__ __forceinline__ void operator()(float p0, float p1, float p2, float q0, float q1,
+                                             float q2, float cp, float cq, float* acc) const {
+    const bool v = finitef(p0) && finitef(p1) && finitef(p2) && finitef(q0) && finitef(q1) &&
+                   finitef(q2) && finitef(cp) && finitef(cq) && cp > cmin && cq > cmin;
+    const float x0 = v ? p0 - pp[0] : 0.f, x1 = v ? p1 - pp[1] : 0.f, x2 = v ? p2 - pp[2] : 0.f;
+    const float y0 = v ? q0 - pq[0] : 0.f, y1 = v ? q1 - pq[1] : 0.f, y2 = v ? q2 - pq[2] : 0.f;
+    float w = rule == 0 ? cp * cq : cp;
+    w = v ? w : 0.f;
+    const float e0 = A[0] * x0 + A[1] * x1 + A[2] * x2 + b[0] - y0;
+    const float e1 = A[3] * x0 + A[4] * x1 + A[5] * x2 + b[1] - y1;
+    const float e2 = A[6] * x0 + A[7] * x1 + A[8] * x2 + b[2] - y2;
+    const float rr = e0 * e0 + e1 * e1 + e2 * e2;
+    const float om = w * fminf(1.f, delta * rsqrtf(rr));
+    acc[M_W] += om;
+    acc[M_CNT] += v ? 1.f : 0.f;
+    const float wx0 = om * x0, wx1 = om * x1, wx2 = om * x2;
+    const float wy0 = om * y0, wy1 = om * y1, wy2 = om * y2;
+    acc[M_SP + 0] += wx0; acc[M_SP + 1] += wx1; acc[M_SP + 2] += wx2;
+    acc[M_SQ + 0] += wy0; acc[M_SQ + 1] += wy1; acc[M_SQ + 2] += wy2;
+    acc[M_PP] += wx0 * x0 + wx1 * x1 + wx2 * x2;
+    acc[M_QP + 0] += wy0 * x0; acc[M_QP + 1] += wy0 * x1; acc[M_QP + 2] += wy0 * x2;
+    acc[M_QP + 3] += wy1 * x0; acc[M_QP + 4] += wy1 * x1; acc[M_QP + 5] += wy1 * x2;
+    acc[M_QP + 6] += wy2 * x0; acc[M_QP + 7] += wy2 * x1; acc[M_QP + 8] += wy2 * x2;
+    acc[M_COST] += om * rr;
+    const float g0 = om * e0, g1 = om * e1, g2 = om * e2;
+    acc[F_G + 0] += g0 * x0; acc[F_G + 1] += g0 * x1; acc[F_G + 2] += g0 * x2;
+    acc[F_G + 3] += g1 * x0; acc[F_G + 4] += g1 * x1; acc[F_G + 5] += g1 * x2;
+    acc[F_G + 6] += g2 * x0; acc[F_G + 7] += g2 * x1; acc[F_G + 8] += g2 * x2;
+    acc[F_GV + 0] += g0; acc[F_GV + 1] += g1; acc[F_GV + 2] += g2;
+    acc[F_C + 0] += wx0 * x0; acc[F_C + 1] += wx0 * x1; acc[F_C + 2] += wx0 * x2;
+    acc[F_C + 3] += wx1 * x1; acc[F_C + 4] += wx1 * x2; acc[F_C + 5] += wx2 * x2;
+  }
+};
+
+struct FinalArgs {
+  const float* xyz;
+  const float* conf;
+  int64_t hw;
+  int tpl;              // tiles of TILE pixels per link
+  const int32_t* link_off;
+  const int32_t* src;
+  const int32_t* tgt;
+  const int32_t* link_pair;
+  PairState* st;
+  double* partials;     // [n_tiles][NFIN], its own buffer
+  float delta;
+  int rule;
+  int iters;
+  ec3r_sim3* out;
+  int32_t* status_out;
+  double* cost;         // [n_pairs]
+  double* cost_sums;    // [n_pairs][CS_STRIDE]
+  double* ckpt;
+  unsigned long long* done;  // per pair: final tiles completed
+  const unsigned* epoch;     // the persistent launch's per-pair epochs
+  unsigned* abort;
+  unsigned* flags;
+  long long wait_cycles;
+};
+
+// Warp 0 of the CTA that completed pair k's final tiles: the last solve (as
+// finish_pair), then the cost and the cost term's sums from the identities above.
+__device__ __noinline__ void finish_final(const FinalArgs& a, int k, double* f) {
+  const int lane = threadIdx.x & 31;
+  __threadfence();
+  const int64_t t0 = (int64_t)a.link_off[k] * a.tpl, t1 = (int64_t)a.link_off[k + 1] * a.tpl;
+  f[lane] = tile_sum_cg<NFIN>(a.partials, t0, t1, lane);
+  if (lane + 32 < NFIN) f[lane + 32] = tile_sum_cg<NFIN>(a.partials, t0, t1, lane + 32);
+  __syncwarp();
+  if (lane != 0) return;
+  double R[9], s = 1.0, b[3] = {0, 0, 0}, dV[12];
+  const unsigned status = umeyama_from_moments(f, R, s, b, dV);
+  double* ck = a.ckpt + ((size_t)k * a.iters + (a.iters - 1)) * CKPT;
+  for (int m = 0; m < NMOM; ++m) ck[CK_MOM + m] = f[m];
+  for (int i = 0; i < 9; ++i) ck[CK_A + i] = s * R[i];
+  for (int i = 0; i < 3; ++i) ck[CK_B + i] = b[i];
+  ck[CK_STATUS] = (double)status;
+  ck[CK_S] = s;
+  for (int i = 0; i < 9; ++i) ck[CK_R + i] = R[i];
+  for (int i = 0; i < 12; ++i) ck[CK_D + i] = status ? 0.0 : dV[i];
+  PairState& S = a.st[k];
+  commit_estimate(S, status, R, s, b, true, a.out[k], a.status_out[k]);
+  double* cs = a.cost_sums + (size_t)k * CS_STRIDE;
+  if (status) {  // a degenerate pair reports no cost
+    a.cost[k] = 0.0;
+    for (int i = 0; i < CS_STRIDE; ++i) cs[i] = 0.0;
+    return;
+  }
+  // D between the FP32 estimates that the residuals use (S_K now in A, b;
+  // S_{K-1}, which weighted this sweep, in Ap, bp)
+  double DA[9], Db[3], C[9];
+  for (int i = 0; i < 9; ++i) DA[i] = (double)S.A[i] - (double)S.Ap[i];
+  for (int i = 0; i < 3; ++i) Db[i] = (double)S.b[i] - (double)S.bp[i];
+  C[0] = f[F_C + 0]; C[1] = C[3] = f[F_C + 1]; C[2] = C[6] = f[F_C + 2];
+  C[4] = f[F_C + 3]; C[5] = C[7] = f[F_C + 4]; C[8] = f[F_C + 5];
+  const double W = f[M_W];
+  const double* Sp = f + M_SP;
+  double J = f[M_COST];
+  for (int i = 0; i < 3; ++i) {
+    const double dAs = DA[3 * i] * Sp[0] + DA[3 * i + 1] * Sp[1] + DA[3 * i + 2] * Sp[2];
+    double gi = f[F_GV + i] + dAs + W * Db[i];
+    J += 2.0 * Db[i] * (f[F_GV + i] + dAs) + W * Db[i] * Db[i];
+    for (int j = 0; j < 3; ++j) {
+      const double dAC = DA[3 * i] * C[j] + DA[3 * i + 1] * C[3 + j] + DA[3 * i + 2] * C[6 + j];
+      const double G = f[F_G + 3 * i + j];
+      J += DA[3 * i + j] * (2.0 * G + dAC);
+      cs[3 * i + j] = G + dAC + Db[i] * Sp[j];
+    }
+    cs[9 + i] = gi;
+  }
+  const double v = W > 0.0 ? J / W : 0.0;
+  a.cost[k] = v;
+  cs[CS_COST] = v;
+}
+
+// One CTA per tile of TILE pixels (a programmatic dependent launch after
+// k_register, which ran sweeps 1 .. K-1): waits for its pair's solve K-1
+// (epoch K-1), runs the pair's last Huber sweep with the cost sums, and the
+// CTA that completes a pair's tiles solves, checkpoints and commits S_K and
+// forms the cost.  Every CTA ends by waiting for k_register to complete, so
+// that the work after this launch in the stream also follows k_register.
+// (37 accumulators: three CTAs of 256 threads per SM, 80 registers)
+constexpr int FIN_MINB = 3, FIN_UNROLL = 2;
+
+template <bool VEC>
+__global__ void __launch_bounds__(THREADS, FIN_MINB)
+    k_final_sweep(const __grid_constant__ FinalArgs a) {
+  __shared__ double red[THREADS / 32][NFIN];
+  __shared__ double fin[NFIN];
+  __shared__ int s_go, s_last;
+  const int64_t t = blockIdx.x;
+  const int64_t l = t / a.tpl;
+  const int c = (int)(t - l * a.tpl);
+  const int k = a.link_pair[l];
+  if (threadIdx.x == 0) {
+    int go = 0;
+    if (k >= 0) {
+      go = a.iters < 2 ? 1
+                       : (int)wait_epoch(a.epoch + k, (unsigned)(a.iters - 1), a.abort, a.flags,
+                                         a.wait_cycles);
+      if (go) go = __ldcg(&a.st[k].active);
+    }
+    s_go = go;
+  }
+  __syncthreads();
+  if (s_go) {
+    const PairState* S = a.st + k;
+    FinalOp op;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) op.A[i] = __ldcg(&S->A[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      op.b[i] = __ldcg(&S->b[i]);
+      op.pp[i] = __ldcg(&S->piv_p[i]);
+      op.pq[i] = __ldcg(&S->piv_q[i]);
+    }
+    // a single solve has unit Huber weights (its sweep starts from the identity)
+    op.delta = a.iters == 1 ? INFINITY : a.delta;
+    op.cmin = __ldcg(&S->cmin);
+    op.rule = a.rule;
+    const int64_t fs = a.src[l], ft = a.tgt[l];
+    const int64_t px0 = (int64_t)c * TILE;
+    const int64_t rem = a.hw - px0;
+    sweep_tile<VEC, TILE, FinalOp, FIN_UNROLL>(
+        op, a.xyz + (fs * a.hw + px0) * 3, a.xyz + (ft * a.hw + px0) * 3,
+        a.conf + fs * a.hw + px0, a.conf + ft * a.hw + px0, rem < TILE ? (int)rem : TILE, red);
+    __syncthreads();
+    for (int m = threadIdx.x; m < NFIN; m += THREADS) {
+      double sum = 0.0;
+#pragma unroll
+      for (int w = 0; w < THREADS / 32; ++w) sum += red[w][m];
+      a.partials[t * NFIN + m] = sum;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned long long nt =
+          (unsigned long long)(a.link_off[k + 1] - a.link_off[k]) * (unsigned long long)a.tpl;
+      s_last = atomicAdd(a.done + k, 1ull) + 1ull == nt;
+      if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) finish_final(a, k, fin);
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// --------------------------------------------------------------------------
 // host side: variants, occupancy, launch
 // --------------------------------------------------------------------------
 typedef void (*RegKernel)(const RegArgs);
@@ -335,25 +503,36 @@ struct RegVariant {
   RegKernel fn;
 };
 
-// 16-byte aligned pointmaps: the autotuner's candidates (tile pixels, CTAs
-// per SM; 64, 80 and 128 registers per thread).
+// 16-byte aligned pointmaps: the autotuner's persistent candidates (tile
+// pixels, CTAs per SM; 64, 80 and 128 registers per thread).  One more
+// variant, the last, runs every sweep and solve as separate grids (align.cu).
 static const RegVariant kTuned[] = {
     {8192, 4, k_register<true, 8192, 4>},   {8192, 3, k_register<true, 8192, 3>},
     {8192, 2, k_register<true, 8192, 2>},   {4096, 4, k_register<true, 4096, 4>},
     {4096, 3, k_register<true, 4096, 3>},   {4096, 2, k_register<true, 4096, 2>},
     {16384, 4, k_register<true, 16384, 4>}, {16384, 3, k_register<true, 16384, 3>},
-    {16384, 2, k_register<true, 16384, 2>},
+    {16384, 2, k_register<true, 16384, 2>}, {32768, 4, k_register<true, 32768, 4>},
+    {32768, 3, k_register<true, 32768, 3>}, {32768, 2, k_register<true, 32768, 2>},
 };
 constexpr int N_TUNED = sizeof(kTuned) / sizeof(kTuned[0]);
 // Unaligned pointmaps or hw not a multiple of 4: scalar loads, one configuration.
 static const RegVariant kScalar = {8192, 3, k_register<false, 8192, 3>};
 
-int reg_variant_count() { return N_TUNED; }
+int reg_variant_count() { return N_TUNED + 1; }
 
-bool reg_variant_info(int v, int* tile, int* ctas) {
+int reg_grid_variant() { return N_TUNED; }
+
+bool reg_variant_info(int v, int* tile, int* ctas, int* persistent) {
+  if (v == N_TUNED) {  // separate grids: k_sweep and k_solve
+    *tile = TILE;
+    *ctas = 4;
+    *persistent = 0;
+    return true;
+  }
   if (v < 0 || v >= N_TUNED) return false;
   *tile = kTuned[v].tile;
   *ctas = kTuned[v].ctas;
+  *persistent = 1;
   return true;
 }
 
@@ -383,7 +562,7 @@ ec3r_status launch_register(ec3r_ctx* ctx, cudaStream_t s, int v, bool vec,
                             int64_t n_links, const int32_t* link_off, const int32_t* src,
                             const int32_t* tgt, const int32_t* link_pair, PairState* st,
                             double* partials, float delta, int rule, int iters,
-                            ec3r_sim3* out, int32_t* status_out, double* cost,
+                            int n_sweeps, ec3r_sim3* out, int32_t* status_out, double* cost,
                             double* cost_sums, double* ckpt, void* ctl, size_t ctl_bytes) {
   const RegVariant& rv = pick(v, vec);
   const int64_t tpl = (hw + rv.tile - 1) / rv.tile;
@@ -402,6 +581,7 @@ ec3r_status launch_register(ec3r_ctx* ctx, cudaStream_t s, int v, bool vec,
   a.delta = delta;
   a.rule = rule;
   a.iters = iters;
+  a.n_sweeps = n_sweeps;
   a.out = out;
   a.status_out = status_out;
   a.cost = cost;
@@ -416,8 +596,8 @@ ec3r_status launch_register(ec3r_ctx* ctx, cudaStream_t s, int v, bool vec,
   a.wait_cycles = wait_limit_cycles(ctx);
   a.no_epoch = (ctx->inject & EC3R_INJECT_ALIGN_NO_EPOCH) ? 1 : 0;
   EC3R_CUDA_TRY(ctx, cudaMemsetAsync(ctl, 0, ctl_bytes, s));
-  if (a.n_tiles == 0) return EC3R_OK;
-  const long long total = (long long)a.iters * a.n_tiles;
+  const long long total = (long long)n_sweeps * a.n_tiles;
+  if (total == 0) return EC3R_OK;
   long long grid = resident_ctas(rv, ctx->sm_count);
   if (grid > total) grid = total;
   rv.fn<<<(unsigned)grid, THREADS, 0, s>>>(a);
@@ -425,9 +605,65 @@ ec3r_status launch_register(ec3r_ctx* ctx, cudaStream_t s, int v, bool vec,
   return EC3R_OK;
 }
 
-// Work counter, abort word, per-pair completion counters and epochs.
+// The final sweep as a programmatic dependent launch after launch_register's
+// (same stream, same control block; a plain launch when `after_register` is
+// false, i.e. no sweep ran before it): its tiles start as the persistent CTAs
+// retire and wait only for their own pair's solve K-1.
+ec3r_status launch_final(ec3r_ctx* ctx, cudaStream_t s, bool vec, bool after_register,
+                         const float* xyz, const float* conf, int64_t hw, int n_pairs,
+                         int64_t n_links, const int32_t* link_off, const int32_t* src,
+                         const int32_t* tgt, const int32_t* link_pair, PairState* st,
+                         double* partials, float delta, int rule, int iters, ec3r_sim3* out,
+                         int32_t* status_out, double* cost, double* cost_sums, double* ckpt,
+                         void* ctl) {
+  const int64_t tpl = (hw + TILE - 1) / TILE;
+  const int64_t n_tiles = n_links * tpl;
+  if (n_tiles == 0) return EC3R_OK;
+  FinalArgs a;
+  a.xyz = xyz;
+  a.conf = conf;
+  a.hw = hw;
+  a.tpl = (int)tpl;
+  a.link_off = link_off;
+  a.src = src;
+  a.tgt = tgt;
+  a.link_pair = link_pair;
+  a.st = st;
+  a.partials = partials;
+  a.delta = delta;
+  a.rule = rule;
+  a.iters = iters;
+  a.out = out;
+  a.status_out = status_out;
+  a.cost = cost;
+  a.cost_sums = cost_sums;
+  a.ckpt = ckpt;
+  unsigned long long* c = (unsigned long long*)ctl;
+  a.abort = (unsigned*)(c + 1);
+  a.epoch = (const unsigned*)(c + 2 + n_pairs);
+  a.done = (unsigned long long*)((unsigned*)(c + 2 + n_pairs) + n_pairs + (n_pairs & 1));
+  a.flags = ctx->d_flags;
+  a.wait_cycles = wait_limit_cycles(ctx);
+  const dim3 grid((unsigned)n_tiles), block(THREADS);
+  cudaError_t e;
+  if (after_register)
+    e = vec ? launch_pdl(k_final_sweep<true>, grid, block, 0, s, a)
+            : launch_pdl(k_final_sweep<false>, grid, block, 0, s, a);
+  else if (vec)
+    k_final_sweep<true><<<grid, block, 0, s>>>(a), e = cudaGetLastError();
+  else
+    k_final_sweep<false><<<grid, block, 0, s>>>(a), e = cudaGetLastError();
+  EC3R_CUDA_TRY(ctx, e);
+  return EC3R_OK;
+}
+
+// Work counter, abort word, per pair the completion counters and epochs of
+// the persistent launch, then (8-byte aligned) the final sweep's completion
+// counters.
 size_t reg_ctl_bytes(int n_pairs) {
-  return sizeof(unsigned long long) * (2 + (size_t)n_pairs) + sizeof(unsigned) * (size_t)n_pairs;
+  return sizeof(unsigned long long) * (2 + (size_t)n_pairs) +
+         sizeof(unsigned) * ((size_t)n_pairs + (size_t)(n_pairs & 1)) +
+         sizeof(unsigned long long) * (size_t)n_pairs;
 }
 
 }  // namespace align

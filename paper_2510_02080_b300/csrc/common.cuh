@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ec3r.h"
@@ -229,6 +230,25 @@ inline long long wait_limit_cycles(const ec3r_ctx* ctx) {
   const double s = ctx->wait_limit_s > 0.0 ? ctx->wait_limit_s : 2.0;
   const double khz = ctx->clock_khz > 0 ? (double)ctx->clock_khz : 2.0e6;
   return (long long)(s * khz * 1e3);
+}
+
+// Launches `kernel` with programmatic stream serialization: it may be
+// scheduled before the previous kernel in the stream finishes (the kernel
+// itself must wait for it, griddepcontrol.wait, before touching memory).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 inline std::string key_of(const char* tag, std::initializer_list<uint64_t> vals) {

@@ -132,12 +132,23 @@ __device__ __forceinline__ s3::Sim3d edge_error_T(const s3::Sim3d& Ti, const s3:
 // --------------------------------------------------------------------------
 // chaining initialisation: pointer jumping along the spanning tree (one CTA)
 // --------------------------------------------------------------------------
+// Programmatic dependent launch (PDL): every pose-graph kernel is launched so
+// that the next can be scheduled before it finishes.  Each kernel first waits
+// for the previous one to complete (its results visible) - before any memory
+// access - and only then lets its own dependent launch, so that at most one
+// kernel waits ahead (launched without the attribute, both are no-ops).
+__device__ __forceinline__ void pdl_prologue() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(1024) k_pg_init(int n, int fixed, const int* __restrict__ parent,
                                                   const int* __restrict__ tedge,
                                                   const int* __restrict__ tdir,
                                                   const ec3r_sim3* __restrict__ Tij,
                                                   ec3r_sim3* nodes, ec3r_sim3* W0, ec3r_sim3* W1,
                                                   int* anc0, int* anc1, int rounds) {
+  pdl_prologue();
   for (int v = threadIdx.x; v < n; v += blockDim.x) {
     s3::Sim3d w;
     int a = -1;
@@ -556,6 +567,7 @@ __device__ __forceinline__ void update_node(int k, const PgDev& p) {
 // multi-launch schedule: one launch per phase and per tree level
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(64) k_pg_linearize(PgDev p, int jacobians) {
+  pdl_prologue();
   __shared__ WarpScratch w;
   if (threadIdx.x < 32) linearize_edge(blockIdx.x, threadIdx.x, w, p, jacobians);
   else linearize_adjoint(blockIdx.x, threadIdx.x - 32, w, p, jacobians);
@@ -563,6 +575,7 @@ __global__ void __launch_bounds__(64) k_pg_linearize(PgDev p, int jacobians) {
 
 __global__ void __launch_bounds__(32) k_pg_assemble(PgDev p, int n_blocks, int nf,
                                                     double* chi2_out, int trial) {
+  pdl_prologue();
   assemble_unit(blockIdx.x, threadIdx.x, n_blocks, nf, p, chi2_out, trial);
 }
 
@@ -572,14 +585,19 @@ __global__ void __launch_bounds__(32) k_pg_assemble(PgDev p, int n_blocks, int n
 // lambda stays in [LM_MIN, LM_MAX].
 constexpr double LM_MIN = 1e-10, LM_MAX = 1e10;
 
-__global__ void k_pg_lm_start(PgDev p, double lambda0) { p.lm[0] = lambda0; }
+__global__ void k_pg_lm_start(PgDev p, double lambda0) {
+  pdl_prologue();
+  p.lm[0] = lambda0;
+}
 
 __global__ void k_pg_backup(PgDev p) {
+  pdl_prologue();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < p.n) p.backup[k] = p.nodes[k];
 }
 
 __global__ void k_pg_decide(PgDev p) {
+  pdl_prologue();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const bool accept = !ldc(p.fail) && ldc(p.lm + 2) < ldc(p.lm + 1);
   if (!accept && k < p.n) p.nodes[k] = p.backup[k];
@@ -676,6 +694,7 @@ __device__ void factor_staged(const ColMeta& c, int tid, double* CB, double* fpa
 
 // One column per CTA: the staged schedule, else factor_column.
 __global__ void __launch_bounds__(32 * FWARPS) k_pg_factor(PgDev p, int lstart) {
+  pdl_prologue();
   __shared__ double CB[CB_MAX * NB], fpart[FS_MAX * 7], inv[7], y[7];
   const ColMeta c = load_meta(p.col_meta, lstart + blockIdx.x);
   if (c.fast) factor_staged(c, threadIdx.x, CB, fpart, inv, y, p);
@@ -731,12 +750,14 @@ struct WarpSolve {
 
 // One column per warp (one warp per CTA).
 __global__ void __launch_bounds__(32) k_pg_backsolve(PgDev p, int lstart) {
+  pdl_prologue();
   __shared__ WarpSolve w;
   backsolve_staged(load_meta(p.col_meta, lstart + blockIdx.x), threadIdx.x, w.D, w.part, w.id,
                    w.x, p);
 }
 
 __global__ void k_pg_update(PgDev p) {
+  pdl_prologue();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= p.nf || ldc(p.fail)) return;
   update_node(k, p);
@@ -749,6 +770,7 @@ __global__ void k_pg_update(PgDev p) {
 // per destination block.
 __global__ void __launch_bounds__(32) k_pg_sn_assemble(const int* __restrict__ grp,
                                                        const int* __restrict__ upd_ab, double* L) {
+  pdl_prologue();
   const int g = blockIdx.x;
   apply_group(L, grp[3 * g], upd_ab + 2 * grp[3 * g + 1], grp[3 * g + 2], threadIdx.x);
 }
@@ -816,6 +838,7 @@ __device__ void sn_panel_cta(int k, int nf, const int* __restrict__ col_ptr,
 __global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_panel_first(
     int k, int nf, const int* __restrict__ col_ptr, const int* __restrict__ off_blk, double* L,
     double* idiag, unsigned* flags, int* fail) {
+  pdl_prologue();
   __shared__ double D[NB], inv[7];
   sn_panel_cta(k, nf, col_ptr, off_blk, L, idiag, flags, fail, D, inv);
 }
@@ -829,6 +852,7 @@ __global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_panel_first(
 __global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_update_panel(
     int k, int nf, const int* __restrict__ col_ptr, const int* __restrict__ off_blk, double* L,
     double* idiag, unsigned* flags, int* fail, int* cnt) {
+  pdl_prologue();
   __shared__ double D[NB], inv[7];
   __shared__ int mine, last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -882,6 +906,7 @@ __global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_update_panel(
 __global__ void __launch_bounds__(32) k_pg_sn_rhs(int sn0, const int* __restrict__ row_ptr,
                                                   const int* __restrict__ row_it,
                                                   const double* __restrict__ L, double* bvec) {
+  pdl_prologue();
   const int k = sn0 + blockIdx.x, lane = threadIdx.x;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int p = row_ptr[k] + lane; p < row_ptr[k + 1]; p += 32) {
@@ -923,6 +948,7 @@ __global__ void __launch_bounds__(SN_THREADS) k_pg_sn_dense_solve(int sn0, int n
                                                                  const double* __restrict__ L,
                                                                  const double* __restrict__ idiag,
                                                                  double* bvec) {
+  pdl_prologue();
   extern __shared__ double sn_b[];  // [ns * 7]
   __shared__ double D[2][NB], inv[2][7], v[7];
   const int ns = nf - sn0, tid = threadIdx.x;
@@ -1699,88 +1725,90 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
   return run_graph(ctx, gkey, s, [&](cudaStream_t cs) -> ec3r_status {
     if (o.init_by_chaining)
       traced(ctx, cs, "pg_init", [&] {
-        k_pg_init<<<1, 1024, 0, cs>>>(n_nodes, o.fixed_node, P->d_parent, P->d_tedge, P->d_tdir,
-                                      d_Tij, d_nodes, P->d_W0, P->d_W1, P->d_anc0, P->d_anc1,
-                                      P->rounds);
+        launch_pdl(k_pg_init, 1, 1024, 0, cs, n_nodes, o.fixed_node, P->d_parent, P->d_tedge,
+                   P->d_tdir, d_Tij, d_nodes, P->d_W0, P->d_W1, P->d_anc0, P->d_anc1,
+                   P->rounds);
       });
     const int nlev = P->nlev;
     if (lm)
-      traced(ctx, cs, "pg_lm", [&] { k_pg_lm_start<<<1, 1, 0, cs>>>(dv, o.lm_lambda); });
+      traced(ctx, cs, "pg_lm", [&] { launch_pdl(k_pg_lm_start, 1, 1, 0, cs, dv, o.lm_lambda); });
     for (int itn = 0; itn <= o.iters; ++itn) {
       const bool last = itn == o.iters;  // last pass only evaluates chi^2
       if (n_edges > 0)
         traced(ctx, cs, "pg_linearize", [&] {
-          k_pg_linearize<<<n_edges, 64, 0, cs>>>(dv, last ? 0 : 1);
+          launch_pdl(k_pg_linearize, n_edges, 64, 0, cs, dv, last ? 0 : 1);
         });
       if (last) {
         if (d_chi2)
           traced(ctx, cs, "pg_assemble", [&] {
-            k_pg_assemble<<<1, 32, 0, cs>>>(dv, 0, 0, d_chi2 + itn, 0);
+            launch_pdl(k_pg_assemble, 1, 32, 0, cs, dv, 0, 0, d_chi2 + itn, 0);
           });
         break;
       }
       traced(ctx, cs, "pg_assemble", [&] {
-        k_pg_assemble<<<P->n_blocks + P->nf + 1, 32, 0, cs>>>(
-            dv, P->n_blocks, P->nf, d_chi2 ? d_chi2 + itn : nullptr, 0);
+        launch_pdl(k_pg_assemble, P->n_blocks + P->nf + 1, 32, 0, cs, dv, P->n_blocks, P->nf,
+                   d_chi2 ? d_chi2 + itn : nullptr, 0);
       });
       if (P->nf == 0) continue;
       for (int l = 0; l < nlev; ++l)
         traced(ctx, cs, "pg_factor", [&] {
-          k_pg_factor<<<P->level_ptr[l + 1] - P->level_ptr[l], 32 * FWARPS, 0, cs>>>(
-              dv, P->level_ptr[l]);
+          launch_pdl(k_pg_factor, P->level_ptr[l + 1] - P->level_ptr[l], 32 * FWARPS, 0, cs, dv,
+                     P->level_ptr[l]);
         });
       if (P->sn0 < P->nf) {
         const int nf = P->nf;
         if (P->n_sn_groups > 0)
           traced(ctx, cs, "pg_sn_assemble", [&] {
-            k_pg_sn_assemble<<<P->n_sn_groups, 32, 0, cs>>>(P->d_sn_grp, P->d_upd_ab, P->d_L);
+            launch_pdl(k_pg_sn_assemble, P->n_sn_groups, 32, 0, cs, P->d_sn_grp, P->d_upd_ab,
+                       P->d_L);
           });
         // panel sn0, then per column k one launch: its trailing update and,
         // in the CTA that completes column k + 1, panel k + 1
         EC3R_CUDA_TRY(ctx, cudaMemsetAsync(P->d_sn_cnt, 0, sizeof(int) * (size_t)nf, cs));
         traced(ctx, cs, "pg_sn_panel", [&] {
-          k_pg_sn_panel_first<<<1, SN_UPD_THREADS, 0, cs>>>(
-              P->sn0, nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, dv.flags, P->d_fail);
+          launch_pdl(k_pg_sn_panel_first, 1, SN_UPD_THREADS, 0, cs, P->sn0, nf, P->d_col_ptr,
+                     P->d_off_blk, P->d_L, P->d_idiag, dv.flags, P->d_fail);
         });
         for (int k = P->sn0; k + 1 < nf; ++k) {
           const int64_t mrem = nf - 1 - k;
           const int64_t blocks = (mrem * (mrem + 1) / 2 + SN_UPD_THREADS / 32 - 1) /
                                  (SN_UPD_THREADS / 32);
           traced(ctx, cs, "pg_sn_update", [&] {
-            k_pg_sn_update_panel<<<(unsigned)blocks, SN_UPD_THREADS, 0, cs>>>(
-                k, nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, dv.flags, P->d_fail,
-                P->d_sn_cnt);
+            launch_pdl(k_pg_sn_update_panel, (unsigned)blocks, SN_UPD_THREADS, 0, cs, k, nf,
+                       P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, dv.flags, P->d_fail,
+                       P->d_sn_cnt);
           });
         }
         traced(ctx, cs, "pg_sn_solve", [&] {
           const int ns = nf - P->sn0;
-          k_pg_sn_rhs<<<ns, 32, 0, cs>>>(P->sn0, P->d_row_ptr, P->d_row, P->d_L, P->d_b);
-          k_pg_sn_dense_solve<<<1, SN_THREADS, sizeof(double) * 7 * ns, cs>>>(
-              P->sn0, nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, P->d_b);
+          launch_pdl(k_pg_sn_rhs, ns, 32, 0, cs, P->sn0, P->d_row_ptr, P->d_row, P->d_L,
+                     P->d_b);
+          launch_pdl(k_pg_sn_dense_solve, 1, SN_THREADS, sizeof(double) * 7 * ns, cs, P->sn0,
+                     nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, P->d_b);
         });
       }
       for (int l = nlev - 1; l >= 0; --l)
         traced(ctx, cs, "pg_backsolve", [&] {
-          k_pg_backsolve<<<P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs>>>(
-              dv, P->level_ptr[l]);
+          launch_pdl(k_pg_backsolve, P->level_ptr[l + 1] - P->level_ptr[l], 32, 0, cs, dv,
+                     P->level_ptr[l]);
         });
       if (lm)
         traced(ctx, cs, "pg_lm", [&] {
-          k_pg_backup<<<(n_nodes + 127) / 128, 128, 0, cs>>>(dv);
+          launch_pdl(k_pg_backup, (n_nodes + 127) / 128, 128, 0, cs, dv);
         });
       traced(ctx, cs, "pg_update", [&] {
-        k_pg_update<<<(P->nf + 63) / 64, 64, 0, cs>>>(dv);
+        launch_pdl(k_pg_update, (P->nf + 63) / 64, 64, 0, cs, dv);
       });
       if (lm) {  // chi^2 of the tentative step, then keep it or restore
         if (n_edges > 0)
           traced(ctx, cs, "pg_linearize", [&] {
-            k_pg_linearize<<<n_edges, 64, 0, cs>>>(dv, 0);
+            launch_pdl(k_pg_linearize, n_edges, 64, 0, cs, dv, 0);
           });
         traced(ctx, cs, "pg_assemble", [&] {
-          k_pg_assemble<<<1, 32, 0, cs>>>(dv, 0, 0, nullptr, 1);
+          launch_pdl(k_pg_assemble, 1, 32, 0, cs, dv, 0, 0, nullptr, 1);
         });
         traced(ctx, cs, "pg_lm", [&] {
-          k_pg_decide<<<(n_nodes + 127) / 128, 128, 0, cs>>>(dv);
+          launch_pdl(k_pg_decide, (n_nodes + 127) / 128, 128, 0, cs, dv);
         });
       }
     }

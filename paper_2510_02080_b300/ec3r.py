@@ -92,7 +92,8 @@ def _declare(l):
     l.ec3r_align_token.restype = C.c_uint64
     l.ec3r_align_variant_count.argtypes = []
     l.ec3r_align_variant_count.restype = C.c_int
-    l.ec3r_align_variant_info.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    l.ec3r_align_variant_info.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                          C.POINTER(C.c_int)]
     l.ec3r_align_set_variant.argtypes = [_P, C.c_int]
     l.ec3r_align_last_variant.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_float)]
     l.ec3r_set_wait_limit.argtypes = [_P, C.c_double]
@@ -507,12 +508,13 @@ def align_variant_count():
 
 
 def align_variant_info(v):
-    """(pixels per tile, CTAs per SM) of registration sweep variant v."""
-    t, c = C.c_int(), C.c_int()
-    st = lib().ec3r_align_variant_info(int(v), C.byref(t), C.byref(c))
+    """(pixels per tile, CTAs per SM, persistent: bool) of registration sweep
+    variant v (persistent False: one grid per sweep and per solve)."""
+    t, c, p = C.c_int(), C.c_int(), C.c_int()
+    st = lib().ec3r_align_variant_info(int(v), C.byref(t), C.byref(c), C.byref(p))
     if st != OK:
         raise Ec3rError(st, f"no variant {v}")
-    return t.value, c.value
+    return t.value, c.value, bool(p.value)
 
 
 def sim3_row(row):

@@ -8,14 +8,28 @@ Huber kink at any iteration are excluded (the loss is not differentiable
 there, and the FP32 and FP64 residuals may take different branches).
 
 Tolerance, element by element: |GPU - oracle| <= A_REL |oracle| + B_ABS
-max|oracle| per gradient array.  The GPU evaluates every per-point gradient in
-FP32 from the FP32 estimates of the forward (FP32 moments, so S_k differs from
-the oracle's by up to ~1e-6 relative) and from moment adjoints rounded to FP32;
-each element is a short sum of products whose terms carry relative errors of a
-few FP32 roundings (u = 2^-24) amplified by the conditioning of the 3x3 solves,
-which A_REL covers; where the terms cancel (a small gradient of a point whose
-terms are large), the error is a few roundings of the terms' scale, which B_ABS
-covers."""
+max|oracle| + F32_EST per gradient array.  The GPU evaluates every per-point
+gradient in FP32 from the FP32 estimates of the forward (FP32 moments, so S_k
+differs from the oracle's by up to ~1e-6 relative) and from moment adjoints
+rounded to FP32; each element is a short sum of products whose terms carry
+relative errors of a few FP32 roundings (u = 2^-24) amplified by the
+conditioning of the 3x3 solves, which A_REL covers; where the terms cancel (a
+small gradient of a point whose terms are large), the error is a few roundings
+of the terms' scale, which B_ABS covers.
+
+F32_EST: the registration weights iteration k by residuals under S_{k-1} held
+in FP32 (the FP32-residual design), and the gradient is far more sensitive to
+that estimate than the result is: through the Huber weight's curvature
+(d^2 h / dr^2 = 2 delta / r^3 at r ~ delta, against point offsets of metres)
+a relative change eps of S_{K-1} moves the gradient by some 10^2 - 10^3 eps
+of its largest element (measured on the oracle; the last estimate and the
+earlier ones matter far less).  So rounding the estimate to FP32 alone moves
+the exact FP64 gradient by up to a few 1e-5 of max|oracle| on the 294x518
+pair: the oracle measures this itself, as the difference between its
+gradient and that of the same forward with the weighting estimate rounded to
+FP32 (oracle.adjoint.irls_forward(estimate_dtype=float32)), and F32_EST is
+twice that difference's largest element (the GPU's rounding pattern is not
+the model's; the factor covers a different pattern of the same size)."""
 import numpy as np
 import pytest
 import torch
@@ -29,6 +43,7 @@ from parity import sub_pairset
 pytestmark = pytest.mark.gpu
 DELTA, ITERS = 0.02, 10
 A_REL, B_ABS = 2e-3, 1e-5
+F32_FACTOR = 2.0        # F32_EST = F32_FACTOR x the oracle's own FP32-estimate effect
 FD_RTOL = 2e-3          # finite differences: h = 1e-6 central differences of FP64
 
 
@@ -49,13 +64,16 @@ def oracle_grads(ps, S_gt_list=None, gS_rows=None, delta=DELTA, iters=ITERS, lam
     """The oracle's FP64 input gradients mapped to the frame bank, for the
     upstream gradient of the geodesic loss at the oracle's estimate (S_gt_list)
     or a given one (gS_rows [n_pairs, 13]); dL/dcost = lam.  Also returns the
-    upstream rows and the mask of pixels near the Huber kink."""
+    upstream rows, the mask of pixels near the Huber kink, and F32_EST per
+    array (dict x, c: absolute)."""
     xyz = ps.xyz.double().numpy()
     conf = ps.conf.double().numpy()
     lo, src, tgt = ps.link_off.numpy(), ps.src.numpy(), ps.tgt.numpy()
     hw = xyz.shape[1]
     gx = np.zeros_like(xyz)
     gc = np.zeros_like(conf)
+    gx32 = np.zeros_like(xyz)
+    gc32 = np.zeros_like(conf)
     gS = np.zeros((len(lo) - 1, 13))
     kink = np.zeros(xyz.shape[:2], bool)
     for k in range(len(lo) - 1):
@@ -70,6 +88,11 @@ def oracle_grads(ps, S_gt_list=None, gS_rows=None, delta=DELTA, iters=ITERS, lam
         gs, gR, gt = gS[k][0], gS[k][1:10].reshape(3, 3), gS[k][10:13]
         gP, gQ, gw = oadj.irls_backward(P[valid], Q[valid], w, delta, tape, S, gs, gR, gt, lam)
         gcp, gcq = oadj.weight_grads(gw, cp[valid], cq[valid])
+        S32, tape32, _ = oadj.irls_forward(P[valid], Q[valid], w, delta, iters,
+                                           estimate_dtype=np.float32)
+        gP32, gQ32, gw32 = oadj.irls_backward(P[valid], Q[valid], w, delta, tape32, S32, gs, gR,
+                                              gt, lam)
+        gcp32, gcq32 = oadj.weight_grads(gw32, cp[valid], cq[valid])
         near = np.zeros(valid.sum(), bool)
         for rec in tape[1:]:
             near |= np.abs(rec["r"] - delta) < 1e-4
@@ -78,24 +101,34 @@ def oracle_grads(ps, S_gt_list=None, gS_rows=None, delta=DELTA, iters=ITERS, lam
         fcp = np.zeros(valid.size); fcp[valid] = gcp
         fcq = np.zeros(valid.size); fcq[valid] = gcq
         fnear = np.zeros(valid.size, bool); fnear[valid] = near
+        f32 = [np.zeros((valid.size, 3)), np.zeros((valid.size, 3)), np.zeros(valid.size),
+               np.zeros(valid.size)]
+        for a, v in zip(f32, (gP32, gQ32, gcp32, gcq32)):
+            a[valid] = v
         for j, l in enumerate(range(lo[k], lo[k + 1])):
             sl = slice(j * hw, (j + 1) * hw)
             gx[src[l]] += fullP[sl]
             gx[tgt[l]] += fullQ[sl]
             gc[src[l]] += fcp[sl]
             gc[tgt[l]] += fcq[sl]
+            gx32[src[l]] += f32[0][sl]
+            gx32[tgt[l]] += f32[1][sl]
+            gc32[src[l]] += f32[2][sl]
+            gc32[tgt[l]] += f32[3][sl]
             kink[src[l]] |= fnear[sl]
             kink[tgt[l]] |= fnear[sl]
-    return gS, gx, gc, kink
+    allow = {"x": F32_FACTOR * float(np.abs(gx32 - gx)[~kink].max(initial=0.0)),
+             "c": F32_FACTOR * float(np.abs(gc32 - gc)[~kink].max(initial=0.0))}
+    return gS, gx, gc, kink, allow
 
 
-def compare(g_gpu, g_or, keep, what):
+def compare(g_gpu, g_or, keep, what, f32_est):
     """Element-by-element bound; returns the largest error / bound ratio."""
     a = np.asarray(g_gpu)[keep]
     b = np.asarray(g_or)[keep]
     scale = np.abs(b).max()
     err = np.abs(a - b)
-    bound = A_REL * np.abs(b) + B_ABS * scale
+    bound = A_REL * np.abs(b) + B_ABS * scale + f32_est
     worst = float((err / bound).max())
     i = int((err / bound).argmax())
     assert worst <= 1.0, (f"{what}: element {i}: |GPU - oracle| {err.ravel()[i]:.3e}, "
@@ -111,15 +144,15 @@ def truth_list(ps):
 @pytest.mark.parametrize("H,W", [(64, 96), (294, 518)])
 def test_adjoint_matches_oracle_reverse_mode(ctx, H, W):
     ps = synth.make_pair(synth.SEED_BASE + 4, H=H, W=W, sigma=0.005)
-    gS, gx_or, gc_or, kink = oracle_grads(ps, truth_list(ps))
+    gS, gx_or, gc_or, kink, allow = oracle_grads(ps, truth_list(ps))
     d = cuda_set(ps)
     gx, gc = ctx.align_submaps_backward(d.xyz, d.conf, d.link_off, d.src, d.tgt,
                                         torch.tensor(gS, device="cuda"),
                                         torch.ones(1, dtype=torch.float64, device="cuda"))
     gx, gc = gx.cpu().double().numpy(), gc.cpu().double().numpy()
     keep = ~kink
-    compare(gx, gx_or, keep, "dL/dxyz")
-    compare(gc, gc_or, keep, "dL/dconf")
+    compare(gx, gx_or, keep, "dL/dxyz", allow["x"])
+    compare(gc, gc_or, keep, "dL/dconf", allow["c"])
 
 
 def test_adjoint_shared_frames_accumulate(ctx):
@@ -132,20 +165,20 @@ def test_adjoint_shared_frames_accumulate(ctx):
     ps = synth.PairSet(xyz, conf, torch.tensor([0, 1, 2], dtype=i32),
                        torch.tensor([0, 0], dtype=i32), torch.tensor([1, 2], dtype=i32), 40, 60)
     truths = truth_list(a) + truth_list(a)
-    gS, gx_or, gc_or, kink = oracle_grads(ps, truths)
+    gS, gx_or, gc_or, kink, allow = oracle_grads(ps, truths)
     d = cuda_set(ps)
     gx, gc = ctx.align_submaps_backward(d.xyz, d.conf, d.link_off, d.src, d.tgt,
                                         torch.tensor(gS, device="cuda"),
                                         torch.ones(2, dtype=torch.float64, device="cuda"))
-    compare(gx.cpu().double().numpy(), gx_or, ~kink, "dL/dxyz")
-    compare(gc.cpu().double().numpy(), gc_or, ~kink, "dL/dconf")
+    compare(gx.cpu().double().numpy(), gx_or, ~kink, "dL/dxyz", allow["x"])
+    compare(gc.cpu().double().numpy(), gc_or, ~kink, "dL/dconf", allow["c"])
 
 
 def test_adjoint_against_fp64_finite_differences_2k_subset(ctx):
     """2048-point pair; FP64 central differences of the oracle forward loss."""
     ps = synth.make_pair(synth.SEED_BASE + 8, H=32, W=64, sigma=0.005)
     S_gt = truth_list(ps)[0]
-    gS, _, _, kink = oracle_grads(ps, [S_gt])
+    gS, _, _, kink, _ = oracle_grads(ps, [S_gt])
     d = cuda_set(ps)
     gx, gc = ctx.align_submaps_backward(d.xyz, d.conf, d.link_off, d.src, d.tgt,
                                         torch.tensor(gS, device="cuda"),
@@ -231,17 +264,22 @@ def test_autograd_rejects_inputs_modified_in_place(ctx):
         loss.backward()
 
 
-def test_backward_token_rules(ctx):
+def test_backward_token_rules(ctx, request):
     """fwd_token = 0 recomputes the checkpoints, so the gradients follow frames
     rewritten in place at the same address; the token of the last forward call
     reuses its checkpoints (bitwise the same gradients); a stale token, or the
     token of a call with other options, is refused before anything runs; a
-    forward without the cost sweep serves a backward without a cost gradient."""
+    forward without the cost sweep serves a backward without a cost gradient.
+    Both contexts use one sweep variant (each context's autotuner chooses by
+    its own timing, and variants differ at FP32 rounding level)."""
     a = cuda_set(synth.make_pair(synth.SEED_BASE + 9, H=48, W=64, sigma=0.005))
     b = cuda_set(synth.make_pair(synth.SEED_BASE + 10, H=48, W=64, sigma=0.01))
     gS = torch.linspace(-1, 1, 13, dtype=torch.float64, device="cuda").reshape(1, 13)
     gc = torch.ones(1, dtype=torch.float64, device="cuda")
+    ctx.set_align_variant(0)
+    request.addfinalizer(lambda: ctx.set_align_variant(-1))
     fresh = ec3r.Context()
+    fresh.set_align_variant(0)
     gx_b, gc_b = fresh.align_submaps_backward(b.xyz, b.conf, b.link_off, b.src, b.tgt, gS, gc)
     gx_bn, gc_bn = fresh.align_submaps_backward(b.xyz, b.conf, b.link_off, b.src, b.tgt, gS)
     fresh.close()
@@ -295,8 +333,8 @@ def test_chain_adjoint_full_size_sampled_pairs(ctx):
     for k in (0, 99, 198):
         fa, fb = int(ps.src[k]), int(ps.tgt[k])
         sub = sub_pairset(ps, k)
-        _, gx_or, gc_or, kink = oracle_grads(sub, gS_rows=gS_h[k:k + 1])
+        _, gx_or, gc_or, kink, allow = oracle_grads(sub, gS_rows=gS_h[k:k + 1])
         g_x = torch.stack([gx[fa], gx[fb]]).cpu().double().numpy()
         g_c = torch.stack([gc[fa], gc[fb]]).cpu().double().numpy()
-        compare(g_x, gx_or, ~kink, f"pair {k} dL/dxyz")
-        compare(g_c, gc_or, ~kink, f"pair {k} dL/dconf")
+        compare(g_x, gx_or, ~kink, f"pair {k} dL/dxyz", allow["x"])
+        compare(g_c, gc_or, ~kink, f"pair {k} dL/dconf", allow["c"])

@@ -300,12 +300,17 @@ def test_persistent_wait_runs_out_and_the_context_recovers(cuda_lib):
     c.close()
 
 
-@pytest.mark.parametrize("v", range(9))
+N_VARIANTS = 13   # ec3r_align_variant_count(): 12 persistent, then separate grids
+
+
+@pytest.mark.parametrize("v", range(N_VARIANTS))
 def test_every_sweep_variant_matches_oracle_and_is_deterministic(ctx, v):
-    """Every variant of the persistent registration (pixels per tile x CTAs per
-    SM) against the oracle, on a batch of 1-5 shared 150 x 240 frames per pair
-    (36,000 pixels: ragged tiles of 4096, 8192 and 16384 pixels) with a
-    degenerate pair; a rerun is bitwise identical."""
+    """Every registration variant (the persistent launch's pixels per tile x
+    CTAs per SM, and one grid per sweep and per solve) against the oracle, on a
+    batch of 1-5 shared 150 x 240 frames per pair (36,000 pixels: ragged tiles
+    of 4096, 8192, 16384 and 32768 pixels) with a degenerate pair; a rerun is
+    bitwise identical."""
+    assert ec3r.align_variant_count() == N_VARIANTS
     ps = synth.make_loop_batch(synth.SEED_BASE + 4, n_pairs=6, H=150, W=240, min_valid=2000,
                                max_valid=100000)
     xyz = ps.xyz.clone()

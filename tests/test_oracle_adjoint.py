@@ -178,3 +178,47 @@ def test_depth_gradient_is_zero_where_a_pixel_has_no_point():
     g = unp.unproject_backward(np.ones((1, d[0].size, 3)), d, camp)
     assert g[0, 1, 2] == 0.0 and g[0, 3, 4] == 0.0 and g[0, 5, 9] == 0.0
     assert np.count_nonzero(g) == d[0].size - 3
+
+
+def test_estimate_dtype_float64_is_the_plain_forward():
+    """The pivot-relative residual of the estimate_dtype model, without
+    rounding (float64), is algebraically the plain residual: same estimates,
+    costs and gradients to rounding."""
+    P, Q, cp, cq, S_gt = problem(5, n=200, outliers=20)
+    w = cp * cq
+    S, tape, cost = adj.irls_forward(P, Q, w, 0.05, 10)
+    S2, tape2, cost2 = adj.irls_forward(P, Q, w, 0.05, 10, estimate_dtype=np.float64)
+    assert abs(S2[0] - S[0]) < 1e-12 and np.abs(S2[1] - S[1]).max() < 1e-12
+    assert np.abs(S2[2] - S[2]).max() < 1e-11 and abs(cost2 - cost) < 1e-12 * cost
+    L, gs, gR, gt = adj.geodesic_loss_grad(S, S_gt)
+    g = adj.irls_backward(P, Q, w, 0.05, tape, S, gs, gR, gt, 1.0)
+    g2 = adj.irls_backward(P, Q, w, 0.05, tape2, S2, gs, gR, gt, 1.0)
+    for a, b in zip(g, g2):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
+
+
+def test_gradient_is_far_more_sensitive_to_the_weighting_estimate_than_the_result():
+    """Rounding the estimate that weights the next iteration to FP32 (relative
+    change <= 2^-24 per element) moves the registration's result by about that
+    much, but its gradient by three to four orders of magnitude more (relative
+    to the largest gradient element): the curvature of the Huber weight at
+    r ~ delta amplifies point offsets of O(1) by O(1 / delta).  This is the
+    effect the GPU parity tests allow for on top of their rounding bound."""
+    rng = np.random.default_rng(11)
+    n = 20000
+    P = rng.normal(size=(n, 3)) * np.array([2.0, 1.5, 1.0]) + np.array([3.0, -1.0, 6.0])
+    S0 = (1.3, Rotation.random(random_state=rng).as_matrix(), rng.normal(size=3))
+    Q = sim3.act(S0, P) + 0.01 * rng.normal(size=(n, 3))
+    Q[:2000] += 0.2 * rng.normal(size=(2000, 3))
+    w = rng.lognormal(0, 0.3, n)
+    delta = 0.02
+    S, tape, _ = adj.irls_forward(P, Q, w, delta, 10)
+    S32, tape32, _ = adj.irls_forward(P, Q, w, delta, 10, estimate_dtype=np.float32)
+    ds = max(abs(S32[0] - S[0]) / S[0], np.abs(S32[1] - S[1]).max())
+    L, gs, gR, gt = adj.geodesic_loss_grad(S, S0)
+    gP = adj.irls_backward(P, Q, w, delta, tape, S, gs, gR, gt, 1.0)[0]
+    gP32 = adj.irls_backward(P, Q, w, delta, tape32, S32, gs, gR, gt, 1.0)[0]
+    dg = np.abs(gP32 - gP).max() / np.abs(gP).max()
+    assert ds < 2.0 ** -23
+    assert 0.0 < dg < 1e-3
+    assert dg > 1e3 * ds
