@@ -40,11 +40,11 @@ SEED_CORRECT = 2510020800 + 56
 SWEEP_BYTES_PER_PIXEL = 32          # p, q (2 x 12 B) + c_p, c_q (2 x 4 B) per sweep
 # DRAM bytes (read + write) per link pixel and sweep of the persistent
 # registration launch, by sweep variant: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of each variant's first timing launch on the 40-submap
-# chain (39 links x 152,292 px, 10 sweeps; the traffic scales with the pixels of
-# a launch).  Empty once the kernel changes.
-REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP = {0: 32.18, 1: 31.75, 2: 31.60, 3: 32.29, 4: 31.67,
-                                          5: 31.64, 6: 32.09, 7: 31.80, 8: 31.75}
+# dram__bytes_write.sum of one launch per variant on the 40-submap chain with
+# the cost wanted (39 links x 152,292 px, 9 sweeps; the traffic scales with the
+# pixels and sweeps of a launch).  Variants without a capture of this build
+# report null.  Empty once the kernel changes.
+REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP = {0: 32.20, 6: 32.06, 9: 31.95, 10: 31.82}
 
 
 def peaks():
