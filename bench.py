@@ -1058,6 +1058,8 @@ def run_workload(args):
     dev = torch.device("cuda", 0)
     build.build()
     ctx = ec3r.Context(0)
+    if args.variant >= 0:
+        ctx.set_align_variant(args.variant)
     peak, peak_kind = peaks()
     out = {"workload": args.workload, "unit": UNIT, "data": "synthetic"}
 
