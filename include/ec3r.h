@@ -269,12 +269,13 @@ ec3r_status ec3r_align_submaps_backward(ec3r_ctx* ctx, const float* d_xyz, const
  * Sweep variants of ec3r_align_submaps (FP32 moments): their count, and for
  * variant v its tile size (pixels), CTAs per SM and whether it is the
  * persistent launch (1) or one grid per sweep and per solve (0)
- * (EC3R_ERR_INVALID_ARG for v out of range).  ec3r_align_set_variant forces variant v for every later
- * call on the context, or, with v = -1 (the default), lets each size bucket
- * use the variant its first call timed fastest.  ec3r_align_last_variant gives
- * the variant of the last call (-1: a mode without variants) and, if ms is not
- * NULL (float [ec3r_align_variant_count()]), every variant's median time in ms
- * from the timing of that call's bucket (-1 where none was measured).
+ * (EC3R_ERR_INVALID_ARG for v out of range).  ec3r_align_set_variant forces
+ * variant v for every later call on the context, or, with v = -1 (the
+ * default), lets each size bucket use the variant its first call timed
+ * fastest.  ec3r_align_last_variant gives the variant of the last call (-1: a
+ * mode without variants) and, if ms is not NULL (float
+ * [ec3r_align_variant_count()]), every variant's median time in ms from the
+ * timing of that call's bucket (-1 where none was measured).
  */
 int ec3r_align_variant_count(void);
 ec3r_status ec3r_align_variant_info(int v, int* tile_pixels, int* ctas_per_sm,

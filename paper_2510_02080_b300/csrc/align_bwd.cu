@@ -102,7 +102,8 @@ __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ck
   const double* g = gS + (size_t)k * 13;
   // t = b + piv_q - s R piv_p
   double Rp[3];
-  for (int i = 0; i < 3; ++i) Rp[i] = R[3 * i] * pp[0] + R[3 * i + 1] * pp[1] + R[3 * i + 2] * pp[2];
+  for (int i = 0; i < 3; ++i)
+    Rp[i] = R[3 * i] * pp[0] + R[3 * i + 1] * pp[1] + R[3 * i + 2] * pp[2];
   a.gs = g[0] - (g[10] * Rp[0] + g[11] * Rp[1] + g[12] * Rp[2]);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) a.gR[3 * i + j] = g[1 + 3 * i + j] - s * g[10 + i] * pp[j];

@@ -198,8 +198,8 @@ struct DepthOp {
 
   __device__ __forceinline__ void operator()(float dp, float dq, float cp, float cq, float u,
                                              float v, float* acc) const {
-    const bool ok = link_ok && dp > 0.f && dq > 0.f && dp <= FLT_MAX && dq <= FLT_MAX && cp > cmin &&
-                    cq > cmin && cp <= FLT_MAX && cq <= FLT_MAX;
+    const bool ok = link_ok && dp > 0.f && dq > 0.f && dp <= FLT_MAX && dq <= FLT_MAX &&
+                    cp > cmin && cq > cmin && cp <= FLT_MAX && cq <= FLT_MAX;
     const float zp = ok ? dp : 0.f, zq = ok ? dq : 0.f;
     const float x0 = zp * ((u - kp[2]) * kp[0]) - px[0];
     const float x1 = zp * ((v - kp[3]) * kp[1]) - px[1];

@@ -244,9 +244,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_register(const __grid_constan
         const int64_t rem = a.hw - px0;
         HuberOp op;
         load_op(a.st + k, j, a.delta, a.rule, op);
-        sweep_tile<VEC, TP, HuberOp>(op, a.xyz + (fs * a.hw + px0) * 3, a.xyz + (ft * a.hw + px0) * 3,
-                            a.conf + fs * a.hw + px0, a.conf + ft * a.hw + px0,
-                            rem < TP ? (int)rem : TP, red);
+        sweep_tile<VEC, TP, HuberOp>(op, a.xyz + (fs * a.hw + px0) * 3,
+                                     a.xyz + (ft * a.hw + px0) * 3, a.conf + fs * a.hw + px0,
+                                     a.conf + ft * a.hw + px0, rem < TP ? (int)rem : TP, red);
       }
       // the next item's round trip to the counter overlaps this one's reduction
       if (threadIdx.x == 0) s_pre = (long long)atomicAdd(a.next, 1ull);

@@ -1569,7 +1569,8 @@ static void bernoulli_table(double* c) {
     long double z = 0.0L;
     for (int i = N - 1; i >= 1; --i) z += powl((long double)i, -s);
     const long double Nn = N;
-    z += powl(Nn, 1 - s) / (s - 1) + 0.5L * powl(Nn, -s) + (long double)s / 12.0L * powl(Nn, -s - 1) -
+    z += powl(Nn, 1 - s) / (s - 1) + 0.5L * powl(Nn, -s) +
+         (long double)s / 12.0L * powl(Nn, -s - 1) -
          (long double)s * (s + 1) * (s + 2) / 720.0L * powl(Nn, -s - 3);
     const long double v = 2.0L * z / powl(2.0L * pi, s);
     c[k - 1] = (double)((k % 2 == 1) ? v : -v);
