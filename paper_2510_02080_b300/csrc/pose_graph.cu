@@ -28,7 +28,8 @@
 //   k_pg_update      one thread per node: T <- T Exp(delta)
 // The trailing dense supernode (the top of the elimination tree):
 //   k_pg_sn_assemble      updates of its blocks by the sparse columns
-//   k_pg_sn_panel_first   7x7 Cholesky and triangular solves of its first column
+//   k_pg_sn_panel_first   7x7 Cholesky, its inverse and the triangular solves
+//                         of its first column
 //   k_pg_sn_update_panel  per column: the right-looking update of the
 //                         remaining blocks over all SMs, and the next column's
 //                         panel in the CTA that completes that column
@@ -780,13 +781,17 @@ __device__ __forceinline__ int sn_block(const int* col_ptr, const int* off_blk, 
 }
 
 // Panel work of supernode column k by a CTA of SN_UPD_THREADS threads: 7x7
-// Cholesky of the diagonal block (warp 0), then the triangular solve of every
-// block below it (one block row per thread).  The column was written by other
-// CTAs of the same launch: its loads bypass L1.
+// Cholesky of the diagonal block and its inverse (warp 0; lane j forms column
+// j of L_kk^-1 by forward substitution, kept for the dense substitution too),
+// then X = A L_kk^-T for every block below it, one block row per thread: seven
+// independent dot products with the inverse instead of a chain of seven
+// dependent steps.  The column was written by other CTAs of the same launch:
+// its loads bypass L1.
 constexpr int SN_UPD_THREADS = 256;
-__device__ void sn_panel_cta(int k, int nf, const int* __restrict__ col_ptr,
+__device__ void sn_panel_cta(int k, int sn0, int nf, const int* __restrict__ col_ptr,
                              const int* __restrict__ off_blk, double* L, double* idiag,
-                             unsigned* flags, int* fail, double* D, double* inv) {
+                             double* linv, unsigned* flags, int* fail, double* D, double* inv,
+                             double* Li) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* Lkk = L + (size_t)k * NB;
   if (warp == 0) {
@@ -815,32 +820,49 @@ __device__ void sn_panel_cta(int k, int nf, const int* __restrict__ col_ptr,
       atomicExch(fail, 1);
     }
     for (int idx = lane; idx < NB; idx += 32) Lkk[idx] = (idx % 7 <= idx / 7) ? D[idx] : 0.0;
-    if (lane < 7) idiag[7 * k + lane] = inv[lane];
+    if (lane < 7) {
+      idiag[7 * k + lane] = inv[lane];
+      const int j = lane;  // column j of L^-1: L z = e_j
+      double z[7];
+#pragma unroll
+      for (int r = 0; r < 7; ++r) {
+        double v = r == j ? 1.0 : 0.0;
+#pragma unroll
+        for (int t = 0; t < r; ++t) v -= D[7 * r + t] * z[t];
+        z[r] = r < j ? 0.0 : v * inv[r];
+      }
+      double* Lg = linv + (size_t)(k - sn0) * NB;
+#pragma unroll
+      for (int r = 0; r < 7; ++r) {
+        Li[7 * r + j] = z[r];
+        Lg[7 * r + j] = z[r];
+      }
+    }
   }
   __syncthreads();
   const int nrows = (nf - 1 - k) * 7;
   for (int q = threadIdx.x; q < nrows; q += SN_UPD_THREADS) {
     double* X = L + (size_t)off_blk[col_ptr[k] + q / 7] * NB + 7 * (q % 7);
-    double x[7];
+    double v[7];
+#pragma unroll
+    for (int t = 0; t < 7; ++t) v[t] = __ldcg(X + t);
 #pragma unroll
     for (int c = 0; c < 7; ++c) {
-      double v = __ldcg(X + c);
+      double x = 0.0;
 #pragma unroll
-      for (int t = 0; t < c; ++t) v -= x[t] * D[7 * c + t];
-      x[c] = v * inv[c];
+      for (int t = 0; t <= c; ++t) x = fma(Li[7 * c + t], v[t], x);
+      X[c] = x;
     }
-#pragma unroll
-    for (int c = 0; c < 7; ++c) X[c] = x[c];
   }
 }
 
 // First panel of the supernode.
 __global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_panel_first(
     int k, int nf, const int* __restrict__ col_ptr, const int* __restrict__ off_blk, double* L,
-    double* idiag, unsigned* flags, int* fail) {
+    double* idiag, double* linv, unsigned* flags, int* fail) {
   pdl_prologue();
-  __shared__ double D[NB], inv[7];
-  sn_panel_cta(k, nf, col_ptr, off_blk, L, idiag, flags, fail, D, inv);
+  __shared__ double D[NB], inv[7], Li[NB];
+  sn_panel_cta(k, k, nf, col_ptr, off_blk, L, idiag, linv, flags, fail, D, inv, Li);
 }
 
 // Trailing update after panel k, L_ij -= L_ik L_jk^T for k < j <= i < nf (one
@@ -850,10 +872,10 @@ __global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_panel_first(
 // of column k + 1 updated) factors column k + 1 while the later columns are
 // still being updated.  No CTA waits on another.
 __global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_update_panel(
-    int k, int nf, const int* __restrict__ col_ptr, const int* __restrict__ off_blk, double* L,
-    double* idiag, unsigned* flags, int* fail, int* cnt) {
+    int k, int sn0, int nf, const int* __restrict__ col_ptr, const int* __restrict__ off_blk,
+    double* L, double* idiag, double* linv, unsigned* flags, int* fail, int* cnt) {
   pdl_prologue();
-  __shared__ double D[NB], inv[7];
+  __shared__ double D[NB], inv[7], Li[NB];
   __shared__ int mine, last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mrem = nf - 1 - k;
@@ -897,7 +919,7 @@ __global__ void __launch_bounds__(SN_UPD_THREADS) k_pg_sn_update_panel(
   __syncthreads();
   if (!last) return;
   __threadfence();
-  sn_panel_cta(k + 1, nf, col_ptr, off_blk, L, idiag, flags, fail, D, inv);
+  sn_panel_cta(k + 1, sn0, nf, col_ptr, off_blk, L, idiag, linv, flags, fail, D, inv, Li);
 }
 
 // Right-hand side of the supernode's forward substitution: b_k -= sum_j
@@ -934,45 +956,40 @@ constexpr int SN_THREADS = 512;
 // right-looking, the supernode's right-hand side in shared memory):
 //   forward, k ascending:  y_k = Lkk^-1 b_k, then b_i -= L_ik y_k for i > k;
 //   backward, k descending: x_k = Lkk^-T y_k, then y_i -= L_ki^T x_k for i < k.
-// One thread per row of each update; the next diagonal block is staged while
-// the current update runs.
-__device__ __forceinline__ void sn_stage_diag(int kk, const double* L, const double* idiag,
-                                              double* D, double* inv, int tid) {
-  if (tid < NB) D[tid] = ldc(L + (size_t)kk * NB + tid);
-  else if (tid < NB + 7) inv[tid - NB] = ldc(idiag + 7 * kk + tid - NB);
+// The inverses of the diagonal blocks come from the factorisation, so each
+// diagonal solve is seven independent dot products (lanes 0-6); one thread per
+// row of each update; the next inverse is staged while the current update runs.
+__device__ __forceinline__ void sn_stage_inv(int s, const double* linv, double* Li, int tid) {
+  if (tid < NB) Li[tid] = ldc(linv + (size_t)s * NB + tid);
 }
 
 __global__ void __launch_bounds__(SN_THREADS) k_pg_sn_dense_solve(int sn0, int nf,
                                                                  const int* __restrict__ col_ptr,
                                                                  const int* __restrict__ off_blk,
                                                                  const double* __restrict__ L,
-                                                                 const double* __restrict__ idiag,
+                                                                 const double* __restrict__ linv,
                                                                  double* bvec) {
   pdl_prologue();
   extern __shared__ double sn_b[];  // [ns * 7]
-  __shared__ double D[2][NB], inv[2][7], v[7];
+  __shared__ double Li[2][NB], v[7];
   const int ns = nf - sn0, tid = threadIdx.x;
   for (int i = tid; i < ns * 7; i += SN_THREADS) sn_b[i] = ldc(bvec + 7 * sn0 + i);
-  sn_stage_diag(sn0, L, idiag, D[0], inv[0], tid);
+  sn_stage_inv(0, linv, Li[0], tid);
   __syncthreads();
   // forward
   for (int k = 0; k < ns; ++k) {
     const int cur = k & 1;
-    if (tid == 0) {
-      double y[7];
+    if (tid < 7) {
+      double y = 0.0;
 #pragma unroll
-      for (int c = 0; c < 7; ++c) {
-        double a = sn_b[7 * k + c];
-#pragma unroll
-        for (int t = 0; t < c; ++t) a -= D[cur][7 * c + t] * y[t];
-        y[c] = a * inv[cur][c];
-      }
-#pragma unroll
-      for (int c = 0; c < 7; ++c) v[c] = sn_b[7 * k + c] = y[c];
+      for (int t = 0; t < 7; ++t)
+        if (t <= tid) y = fma(Li[cur][7 * tid + t], sn_b[7 * k + t], y);
+      v[tid] = y;
     } else if (tid >= 32 && k + 1 < ns) {
-      sn_stage_diag(sn0 + k + 1, L, idiag, D[cur ^ 1], inv[cur ^ 1], tid - 32);
+      sn_stage_inv(k + 1, linv, Li[cur ^ 1], tid - 32);
     }
     __syncthreads();
+    if (tid < 7) sn_b[7 * k + tid] = v[tid];
     const int kk = sn0 + k;
     for (int it = tid; it < (ns - 1 - k) * 7; it += SN_THREADS) {
       const int i = k + 1 + it / 7, r = it % 7;
@@ -986,24 +1003,20 @@ __global__ void __launch_bounds__(SN_THREADS) k_pg_sn_dense_solve(int sn0, int n
     }
     __syncthreads();
   }
-  // backward (the last diagonal block is staged: ns - 1 has parity (ns - 1) & 1)
+  // backward (the last inverse is staged: ns - 1 has parity (ns - 1) & 1)
   for (int k = ns - 1; k >= 0; --k) {
     const int cur = k & 1;
-    if (tid == 0) {
-      double x[7];
+    if (tid < 7) {
+      double x = 0.0;
 #pragma unroll
-      for (int c = 6; c >= 0; --c) {
-        double a = sn_b[7 * k + c];
-#pragma unroll
-        for (int t = 6; t > c; --t) a -= D[cur][7 * t + c] * x[t];
-        x[c] = a * inv[cur][c];
-      }
-#pragma unroll
-      for (int c = 0; c < 7; ++c) v[c] = sn_b[7 * k + c] = x[c];
+      for (int t = 0; t < 7; ++t)
+        if (t >= tid) x = fma(Li[cur][7 * t + tid], sn_b[7 * k + t], x);
+      v[tid] = x;
     } else if (tid >= 32 && k > 0) {
-      sn_stage_diag(sn0 + k - 1, L, idiag, D[cur ^ 1], inv[cur ^ 1], tid - 32);
+      sn_stage_inv(k - 1, linv, Li[cur ^ 1], tid - 32);
     }
     __syncthreads();
+    if (tid < 7) sn_b[7 * k + tid] = v[tid];
     for (int it = tid; it < k * 7; it += SN_THREADS) {
       const int i = it / 7, r = it % 7;  // block (k, i) of column i, its column r
       const double* Lki = L + (size_t)off_blk[col_ptr[sn0 + i] + (k - i - 1)] * NB + r;
@@ -1023,6 +1036,7 @@ __global__ void __launch_bounds__(SN_THREADS) k_pg_sn_dense_solve(int sn0, int n
 // shared memory during the substitution.
 constexpr int SN_DENSE_MAX = 3200;  // 3200 x 7 doubles = 175 KB
 
+
 // --------------------------------------------------------------------------
 // host: planning
 // --------------------------------------------------------------------------
@@ -1038,7 +1052,8 @@ struct Plan : Extension {
   int *d_row_ptr = nullptr, *d_row = nullptr;
   int *d_level_cols = nullptr, *d_level_ptr = nullptr, *d_asm_ptr = nullptr, *d_asm = nullptr;
   int *d_col_meta = nullptr, *d_grp_slot = nullptr;
-  int* d_sn_cnt = nullptr;  // per supernode column: its blocks updated so far
+  int* d_sn_cnt = nullptr;       // per supernode column: its blocks updated so far
+  double* d_sn_linv = nullptr;   // per supernode column: L_kk^-1 (7 x 7)
   int nlev = 0;
   int *d_g_ptr = nullptr, *d_g = nullptr;
   int *d_parent = nullptr, *d_tedge = nullptr, *d_tdir = nullptr;
@@ -1530,6 +1545,7 @@ static ec3r_status build_plan(ec3r_ctx* ctx, int n, int m, const int32_t* hi, co
   chk(upload(P, &P.d_col_meta, col_meta));
   chk(upload(P, &P.d_grp_slot, grp_slot));
   chk(alloc(P, &P.d_sn_cnt, (size_t)nf));
+  chk(alloc(P, &P.d_sn_linv, (size_t)std::max(nf - P.sn0, 1) * NB));
   chk(upload(P, &P.d_level_ptr, P.level_ptr));
   chk(upload(P, &P.d_asm_ptr, asm_ptr));
   chk(upload(P, &P.d_asm, asm_it));
@@ -1768,16 +1784,16 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
         EC3R_CUDA_TRY(ctx, cudaMemsetAsync(P->d_sn_cnt, 0, sizeof(int) * (size_t)nf, cs));
         traced(ctx, cs, "pg_sn_panel", [&] {
           launch_pdl(k_pg_sn_panel_first, 1, SN_UPD_THREADS, 0, cs, P->sn0, nf, P->d_col_ptr,
-                     P->d_off_blk, P->d_L, P->d_idiag, dv.flags, P->d_fail);
+                     P->d_off_blk, P->d_L, P->d_idiag, P->d_sn_linv, dv.flags, P->d_fail);
         });
         for (int k = P->sn0; k + 1 < nf; ++k) {
           const int64_t mrem = nf - 1 - k;
           const int64_t blocks = (mrem * (mrem + 1) / 2 + SN_UPD_THREADS / 32 - 1) /
                                  (SN_UPD_THREADS / 32);
           traced(ctx, cs, "pg_sn_update", [&] {
-            launch_pdl(k_pg_sn_update_panel, (unsigned)blocks, SN_UPD_THREADS, 0, cs, k, nf,
-                       P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, dv.flags, P->d_fail,
-                       P->d_sn_cnt);
+            launch_pdl(k_pg_sn_update_panel, (unsigned)blocks, SN_UPD_THREADS, 0, cs, k,
+                       P->sn0, nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag,
+                       P->d_sn_linv, dv.flags, P->d_fail, P->d_sn_cnt);
           });
         }
         traced(ctx, cs, "pg_sn_solve", [&] {
@@ -1785,7 +1801,7 @@ ec3r_status ec3r_pose_graph_correct(ec3r_ctx* ctx, int n_nodes, ec3r_sim3* d_nod
           launch_pdl(k_pg_sn_rhs, ns, 32, 0, cs, P->sn0, P->d_row_ptr, P->d_row, P->d_L,
                      P->d_b);
           launch_pdl(k_pg_sn_dense_solve, 1, SN_THREADS, sizeof(double) * 7 * ns, cs, P->sn0,
-                     nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_idiag, P->d_b);
+                     nf, P->d_col_ptr, P->d_off_blk, P->d_L, P->d_sn_linv, P->d_b);
         });
       }
       for (int l = nlev - 1; l >= 0; --l)
