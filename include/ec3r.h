@@ -172,7 +172,10 @@ void ec3r_align_opts_default(ec3r_align_opts* o);
  * d_pair_status[k] (int32, device) the EC3R_PAIR_* bits (0 = solved; a
  * degenerate pair gets the identity).  d_pair_cost (nullable, float64
  * [n_pairs]) receives sum omega r(S)^2 / sum omega with the last weights
- * when opts->want_cost is set.
+ * when opts->want_cost is set.  With FP32 moments the last sweep and solve
+ * then run in a second kernel that also forms the cost's sums, so the results
+ * with and without want_cost differ at FP32 rounding level, as between sweep
+ * variants.
  *
  * Launches.  A set-up kernel, then, with FP32 moments, one persistent launch
  * that runs every sweep and solve: tiles of pixels are handed out iteration
@@ -229,7 +232,8 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
  * estimate and the moments of every solve, each pair's final status and its
  * cost, and issues a new token (ec3r_align_token).  With fwd_token = 0 the
  * backward call first runs the forward pass itself (into context-owned
- * outputs) and uses its checkpoints: always correct.  With fwd_token = the
+ * outputs, with want_cost = 1 exactly when d_grad_cost is given) and uses its
+ * checkpoints: always correct.  With fwd_token = the
  * token of the last ec3r_align_submaps call on this context, the backward
  * call reuses that call's checkpoints instead; that call must have had the
  * same inputs (pointers and sizes) and options, and want_cost = 1 if
@@ -240,7 +244,7 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
  * may have been freed or reused.
  * It then differentiates all `iters` solves, unrolled (the Huber weights of
  * solve k depend on solve k-1): one reduction sweep per Huber iteration
- * (iters - 1 of them; the sums of the cost term come from the forward's cost
+ * (iters - 1 of them; the sums of the cost term come from the forward's last
  * sweep) and one final sweep that writes the per-point gradients.  The rotation is
  * differentiated in its polar form, with 1/(d_i + d_j) factors.  The Huber
  * weight has a kink at r = delta; there the one-sided derivative of the

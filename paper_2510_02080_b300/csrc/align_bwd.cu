@@ -701,8 +701,11 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "the backward pass supports FP32 moments only");
   if (n_pairs <= 0) return n_pairs == 0 ? EC3R_OK : EC3R_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  // the forward that the caller's call would be: with the cost only when the
+  // cost has a gradient (the last sweep and solve then run in another kernel,
+  // so the two differ at FP32 rounding level)
   ec3r_align_opts fo = *opts;
-  fo.want_cost = 1;
+  fo.want_cost = d_grad_cost ? 1 : 0;
   ec3r_status st;
   if (fwd_token != 0) {
     // Reuse the checkpoints of the forward call that issued this token: it must
