@@ -191,6 +191,11 @@ def _oracle_workload_inproc(name):
                    fusion_points_per_s=xyz.shape[1] / fdt,
                    pose_graph_ms_per_iteration_200_nodes=pg_iteration_ms(
                        synth.SEED_BASE + 3, 200, 40))
+    elif name == "pg1000":
+        ms = pg_iteration_ms(synth.SEED_BASE + 3, 200, 40)
+        out.update(value=ms, unit="ms per Gauss-Newton iteration", seconds=ms * 1e-3,
+                   sample="one Gauss-Newton iteration of a 200-node / 40-loop graph (the "
+                          "1000-node graph's dense FP64 normal equations would take minutes)")
     elif name == "depth200":
         ch = synth.make_depth_chain(synth.SEED_BASE + 46, M=3, F=5, H=294, W=518, device="cpu")
         dps = ch.pairs()
@@ -1193,6 +1198,30 @@ def run_workload(args):
         out["point_correction"] = {"points": n_sp, "ms": cms,
                                    "points_per_s": n_sp / (cms * 1e-3),
                                    "note": "random references: 16 B gathered per point"}
+    elif args.workload == "pg1000":
+        # config 5's pose graph alone: 1000 nodes, 999 odometry + 300 loop edges,
+        # chaining + 10 Gauss-Newton iterations (block Cholesky with the
+        # minimum-degree ordering and the dense trailing supernode)
+        M = 1000
+        g = synth.make_pose_graph(synth.SEED_BASE + 5, M, 300, device="cpu")
+        Tij = ec3r.sim3_rows(g.T_meas.s, g.T_meas.R, g.T_meas.t).to(dev)
+        nodes = torch.zeros((M, 13), dtype=torch.float64, device=dev)
+        nodes[:, 0] = 1.0
+        nodes[:, [1, 5, 9]] = 1.0
+        pg_ms = _time(lambda: ctx.pose_graph_correct(nodes, g.ei.numpy(), g.ej.numpy(), Tij,
+                                                     iters=10), 5, warm=2)
+        assert ctx.sync_status() == 0, ctx.last_error()
+        ctx.profile(True)
+        ctx.profile_read()
+        ctx.pose_graph_correct(nodes, g.ei.numpy(), g.ej.numpy(), Tij, iters=10)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        out["pose_graph"] = {"nodes": M, "edges": len(g.ei), "gn_iters": 10, "ms": pg_ms,
+                             "kernels_ms_event_pass": {k: v[0] for k, v in prof.items()},
+                             "launches": {k: v[1] for k, v in prof.items()}}
+        if not args.no_oracle:
+            out["oracle_error"] = {"pose_graph": pose_graph_error(
+                ctx, g.ei.numpy(), g.ej.numpy(), Tij, M, 1)}
     elif args.workload == "depth200":
         # the 200-submap chain given as depth maps + cameras (the paper's submaps
         # are unprojected depths): registration straight from depth, 16 B per
@@ -1298,7 +1327,7 @@ def main():
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--workload", default="chain200",
                     choices=["chain200", "pair1", "loops512", "adjoint1", "map1000",
-                             "depth200", "loops32k"],
+                             "pg1000", "depth200", "loops32k"],
                     help="chain200 is the benchmark; the others measure the other workloads")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="leave the adjoint out of the step (profiling only)")

@@ -10,7 +10,7 @@
 //
 //   k_adj_init     per pair: upstream dL/d(s, R, t) -> pivot-relative (s, R, b)
 //   cost term      (dL/dcost != 0) sum om e p'^T, sum om e at the last
-//                  estimate: accumulated by the forward's cost sweep
+//                  estimate: accumulated by the forward's last sweep
 //   k_adj_solve    one warp per pair: back through one weighted-Umeyama solve
 //                  (covariance, polar rotation with the (d_i + d_j) form from
 //                  the checkpointed d, V, scale, translation) to the gradient
@@ -117,7 +117,7 @@ __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ck
 
 // Reduction sweep of the Huber path of iteration k (S_{k-1} and the
 // moments' gradient of k).  (The cost term's sums come from the forward's
-// cost sweep.)
+// last sweep.)
 template <bool LASTK, bool VEC>
 __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
 }
 
 // One warp per pair.  First folds the reduced sums (scaled by `scale`: 2 dL/dJ
-// for the cost sweep, 1 for a Huber sweep) into the adjoint of estimate j as
+// for the cost term, 1 for a Huber sweep) into the adjoint of estimate j as
 // dL/dA and dL/db, then differentiates solve j and stores the gradient of its
 // moments in gM[j].
 __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j,
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
   const int wib = threadIdx.x >> 5;
   const double* ck = ckpt + ((size_t)warp * iters + (j - 1)) * CKPT;
   if (have_partials && lane < NRED) {
-    if (pair_sums) {  // summed per pair already (the forward's cost sweep)
+    if (pair_sums) {  // summed per pair already (the forward's last sweep)
       red[wib][lane] = pair_sums[(size_t)warp * CS_STRIDE + lane];
     } else {
       const int64_t t0 = (int64_t)link_off[warp] * tpl, t1 = (int64_t)link_off[warp + 1] * tpl;
@@ -710,7 +710,7 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
   if (fwd_token != 0) {
     // Reuse the checkpoints of the forward call that issued this token: it must
     // be the last registration call on this context, with these inputs and
-    // options, and with the cost sweep if the cost has a gradient.
+    // options, and with the cost if the cost has a gradient.
     const std::string want = key_of(
         "fwd", {(uint64_t)d_xyz, (uint64_t)d_conf, (uint64_t)n_frames, (uint64_t)hw,
                 (uint64_t)n_pairs, (uint64_t)n_links, (uint64_t)d_link_off, (uint64_t)d_src,
@@ -785,7 +785,7 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
                      (uint64_t)d_grad_S, (uint64_t)gcost, (uint64_t)d_grad_xyz,
                      (uint64_t)d_grad_conf, (uint64_t)vec});
   // the cost term's sums (sum g p'^T, sum g at the returned estimate with the
-  // last weights) and the cost come from the forward's cost sweep, per pair
+  // last weights) and the cost come from the forward's last sweep, per pair
   const double* cost_sums = (const double*)ctx->bufs["align.cost_sums"].ptr;
   return run_graph(ctx, gkey, s, [&](cudaStream_t cs) -> ec3r_status {
     traced(ctx, cs, "adj_init", [&] {

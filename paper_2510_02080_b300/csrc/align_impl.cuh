@@ -14,10 +14,11 @@ constexpr int THREADS = 256;
 constexpr int NMOM = 19;
 // moment slots
 enum { M_W = 0, M_SP = 1, M_SQ = 4, M_PP = 7, M_QP = 8, M_COST = 17, M_CNT = 18 };
-// The cost sweep leaves slots 1..16 free and stores there, from CS_SLOT on,
-// the 12 sums of the adjoint's cost term (sum g p'^T row-major, sum g).
-// Per pair the context keeps those 12 sums and then the cost itself
-// (CS_STRIDE doubles), so the backward never reads the caller's outputs.
+// The grid schedule's cost sweep leaves slots 1..16 free and stores there,
+// from CS_SLOT on, the 12 sums of the adjoint's cost term (sum g p'^T
+// row-major, sum g); the final sweep forms the same 12 sums.  Per pair the
+// context keeps those 12 sums and then the cost itself (CS_STRIDE doubles),
+// so the backward never reads the caller's outputs.
 constexpr int CS_SLOT = 1, NCS = 12, CS_COST = NCS, CS_STRIDE = NCS + 1;
 constexpr double RANK_REL_TOL = 1e-4;
 

@@ -20,10 +20,11 @@
 //
 // So each pair's solve runs while other pairs' tiles stream, and only the
 // last pair's last solve is exposed.  Every wait is bounded: past the limit
-// the CTA raises FLAG_TIMEOUT and skips its tile.  The cost sweep (weights
-// from one estimate, residuals under another: twelve more live registers than
-// a Huber sweep) runs after this launch as its own grid, so that the
-// persistent loop fits the register budget of four CTAs per SM.
+// the CTA raises FLAG_TIMEOUT and skips its tile.  When the cost is wanted,
+// the last sweep runs after this launch as its own grid (k_final_sweep): it
+// also accumulates the sums from which the cost under the last solve follows
+// exactly (37 sums per pixel instead of 19, which would not fit the persistent
+// loop's register budget of four CTAs per SM).
 //
 // Variants (tile pixels x CTAs per SM) are instantiated for the autotuner;
 // the tile size groups the FP32 sums, so variants differ at FP32 rounding
@@ -197,7 +198,7 @@ __device__ __noinline__ void finish_pair(const RegArgs& a, int k, int j, double*
 
 template <bool VEC, int TP, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_register(const __grid_constant__ RegArgs a) {
-  // the cost sweep (a programmatic dependent launch) may be scheduled as soon
+  // the final sweep (a programmatic dependent launch) may be scheduled as soon
   // as this grid's CTAs are resident: it waits per pair on the epochs
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ double red[THREADS / 32][NMOM];

@@ -69,7 +69,7 @@ struct ec3r_ctx {
   std::map<std::string, ec3r::Extension*> ext;
   uint64_t clock = 0;
   // The last registration call: its token (0: none, or it failed), the key of
-  // its inputs and options, and whether it ran the cost sweep.  Its
+  // its inputs and options, and whether it formed the cost.  Its
   // checkpoints, per-pair activity and cost live in the align.* workspace;
   // a backward call given this token reuses them.
   uint64_t align_token = 0;
