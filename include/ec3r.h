@@ -251,9 +251,10 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
  * branch taken by the FP32 forward is used.
  *
  * Errors: EC3R_ERR_INVALID_ARG (nothing enqueued) for a NULL context, opts,
- * d_grad_S, d_grad_xyz or d_grad_conf, n_pairs < 0, opts->precision other
+ * d_grad_xyz or d_grad_conf, a NULL d_grad_S with n_pairs > 0, n_pairs < 0,
+ * opts->precision other
  * than EC3R_PREC_FP32C, or a fwd_token that does not qualify (above);
- * n_pairs = 0 does nothing.  The forward call's own checks apply when it is
+ * n_pairs = 0 only zeroes d_grad_xyz and d_grad_conf.  The forward call's own checks apply when it is
  * run with fwd_token = 0.
  * Workspace (context-owned, beyond the forward's): 96 bytes per tile of 8192
  * pixels, 32 bytes per link pixel (per-link gradients, summed into frames

@@ -695,12 +695,21 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
     uint64_t fwd_token, const double* d_grad_S, const double* d_grad_cost, float* d_grad_xyz,
     float* d_grad_conf, void* stream) {
   if (!ctx) return EC3R_ERR_INVALID_ARG;
-  if (!opts || !d_grad_S || !d_grad_xyz || !d_grad_conf)
+  if (!opts || (n_pairs > 0 && !d_grad_S) || !d_grad_xyz || !d_grad_conf)
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "a required pointer is NULL");
   if (opts->precision != EC3R_PREC_FP32C)
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "the backward pass supports FP32 moments only");
-  if (n_pairs <= 0) return n_pairs == 0 ? EC3R_OK : EC3R_ERR_INVALID_ARG;
+  if (n_pairs < 0) return set_error(ctx, EC3R_ERR_INVALID_ARG, "n_pairs < 0");
   cudaStream_t s = (cudaStream_t)stream;
+  if (n_pairs == 0) {  // no pair: every point's gradient is zero
+    if (n_frames < 0 || hw < 0)
+      return set_error(ctx, EC3R_ERR_INVALID_ARG, "negative frame bank size");
+    const size_t px = (size_t)n_frames * (size_t)hw;
+    EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    EC3R_CUDA_TRY(ctx, cudaMemsetAsync(d_grad_xyz, 0, sizeof(float) * 3 * px, s));
+    EC3R_CUDA_TRY(ctx, cudaMemsetAsync(d_grad_conf, 0, sizeof(float) * px, s));
+    return EC3R_OK;
+  }
   // the forward that the caller's call would be: with the cost only when the
   // cost has a gradient (the last sweep and solve then run in another kernel,
   // so the two differ at FP32 rounding level)

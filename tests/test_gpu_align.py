@@ -346,3 +346,30 @@ def test_autotuner_times_each_variant_once_per_size_bucket(cuda_lib):
     assert v2 == v and ms2 == ms
     assert np.array_equal(S1, run(c, d)[0])
     c.close()
+
+
+def test_zero_sized_calls(ctx):
+    """No pair, no submap: the registration writes nothing and succeeds; the
+    backward call zeroes the gradients of every frame (each point's gradient is
+    zero when no pair uses it); fusion of no submap keeps nothing."""
+    xyz = torch.randn((2, 16, 3), device="cuda")
+    conf = torch.ones((2, 16), device="cuda")
+    lo = torch.zeros(1, dtype=torch.int32, device="cuda")
+    none = torch.zeros(0, dtype=torch.int32, device="cuda")
+    S, st, cost = ctx.align_submaps(xyz, conf, lo, none, none, want_cost=True)
+    assert S.shape == (0, 13) and st.shape == (0,) and cost.shape == (0,)
+    gx, gc = ctx.align_submaps_backward(xyz, conf, lo, none, none,
+                                        torch.zeros((0, 13), dtype=torch.float64,
+                                                    device="cuda"))
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    assert torch.count_nonzero(gx) == 0 and torch.count_nonzero(gc) == 0
+    out_xyz = torch.full((4, 3), float("nan"), device="cuda")
+    out_idx = torch.full((4,), -7, dtype=torch.int64, device="cuda")
+    cursor = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ctx.fuse_points(torch.zeros((0, 16, 3), device="cuda"), torch.zeros((0, 16), device="cuda"),
+                    torch.zeros((0, 13), dtype=torch.float64, device="cuda"), out_xyz,
+                    out_idx, cursor)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    assert int(cursor) == 0 and int((out_idx == -7).sum()) == 4
