@@ -37,14 +37,22 @@ M_SUBMAPS, F_FRAMES, H, W = 200, 5, 294, 518   # the chain workload
 ITERS, DELTA = 10, 0.02
 PG_ITERS = 10
 SEED_CORRECT = 2510020800 + 56
-SWEEP_BYTES_PER_PIXEL = 32          # p, q (2 x 12 B) + c_p, c_q (2 x 4 B) per sweep
-# DRAM bytes (read + write) per link pixel and sweep of the persistent
-# registration launch, by sweep variant: ncu dram__bytes_read.sum +
+# Algorithmic bytes per link pixel of one Huber-IRLS sweep.  Sweep 1 reads p,
+# q (2 x 12 B) and c_p, c_q (2 x 4 B) and writes the pixel's weight (4 B);
+# every later sweep (and the final sweep with the cost) reads p, q and that
+# weight.
+SWEEP1_BYTES_PER_PIXEL = 36
+SWEEP_BYTES_PER_PIXEL = 28
+# The metric's own count: one correspondence of one iteration read as p, q,
+# c_p and c_q.
+METRIC_BYTES_PER_PT_ITER = 32
+# DRAM bytes (read + write) per link pixel and sweep of the persistent launch
+# of sweeps 2 .. 9, by sweep variant: ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch per variant on the 40-submap chain with
-# the cost wanted (39 links x 152,292 px, 9 sweeps; the traffic scales with the
+# the cost wanted (39 links x 152,292 px, 8 sweeps; the traffic scales with the
 # pixels and sweeps of a launch).  Variants without a capture of this build
 # report null.  Empty once the kernel changes.
-REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP = {0: 32.20, 6: 32.06, 9: 31.95, 10: 31.82}
+REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP = {}
 
 
 def peaks():
@@ -842,11 +850,11 @@ def run_ours(args):
         return
 
     peak, peak_kind = peaks()
-    # the dominant kernel: the persistent registration launch (the Huber-IRLS
-    # sweeps and per-pair solves of the call but the last sweep and solve,
-    # which run in the final-sweep launch when the adjoint needs the cost),
-    # 32 B per link pixel per sweep
-    sweeps = ITERS - 1 if "irls_final_sweep" in prof else ITERS
+    # the dominant kernel: the persistent registration launch of sweeps 2 ..
+    # K-1 (sweep 1 runs in its own launch before it; the last sweep and solve
+    # in the final-sweep launch, since the adjoint needs the cost), 28 B per
+    # link pixel per sweep
+    sweeps = (ITERS - 1 if "irls_final_sweep" in prof else ITERS) - 1
     reg_k = prof.get("irls_register", (0.0, 0))
     reg_launch_ms = reg_k[0] / max(reg_k[1], 1)
     reg_bytes = SWEEP_BYTES_PER_PIXEL * pix * sweeps
@@ -861,9 +869,11 @@ def run_ours(args):
     # sweep with the last solve and the cost that the adjoint needs (or, for
     # the grid variant, every sweep, solve and the cost sweep as grids)
     reg_ms = sum(prof.get(k, (0.0, 0))[0]
-                 for k in ("align_setup", "irls_register", "irls_final_sweep", "irls_cost",
-                           "irls_sweep_fp32", "sim3_solve"))
+                 for k in ("align_setup", "irls_sweep1", "irls_register", "irls_final_sweep",
+                           "irls_cost", "irls_sweep_fp32", "sim3_solve"))
     reg_rate = n_valid * ITERS * args.steps / (reg_ms * 1e-3) if reg_ms else None
+    # bytes the registration call streams per correspondence and iteration
+    call_bytes_pt_iter = (SWEEP1_BYTES_PER_PIXEL + SWEEP_BYTES_PER_PIXEL * (ITERS - 1)) / ITERS
     fuse_gbs = 26.0 * n_fuse * args.steps / (fuse_ms * 1e-3) / 1e9 if fuse_ms else None
     variant, tune_ms = ctx.last_align_variant()
     vt, vc, vp = ec3r.align_variant_info(variant) if variant >= 0 else (None, None, None)
@@ -892,20 +902,24 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": reg_bytes,
                      "launch_ms": reg_launch_ms,
                      "sweeps_per_launch": sweeps,
-                     "note": "one persistent launch per call: the Huber-IRLS sweeps and "
-                             "per-pair FP64 solves but the last (which the final-sweep launch "
-                             "runs with the cost); 32 B per link pixel per sweep",
+                     "note": "the persistent launch of Huber-IRLS sweeps 2 .. K-1 and their "
+                             "per-pair FP64 solves (sweep 1 has its own launch before it, "
+                             "the last sweep and solve the final-sweep launch after it); "
+                             "28 B per link pixel per sweep: p, q and the stored weight",
                      "registration": {
                          "pt_iter_per_s": reg_rate,
-                         "bytes_per_pt_iter": SWEEP_BYTES_PER_PIXEL,
-                         "achieved": (SWEEP_BYTES_PER_PIXEL * reg_rate / 1e9
+                         "bytes_per_pt_iter": call_bytes_pt_iter,
+                         "achieved": (call_bytes_pt_iter * reg_rate / 1e9
                                       if reg_rate else None),
-                         "frac": (SWEEP_BYTES_PER_PIXEL * reg_rate / 1e9 / peak
+                         "frac": (call_bytes_pt_iter * reg_rate / 1e9 / peak
                                   if reg_rate else None),
-                         "note": "the whole registration call (set-up, persistent launch, "
-                                 "final sweep with the last solve and the cost the adjoint "
-                                 "needs: 10 sweeps streamed) against the metric's 10 "
-                                 "iterations at 32 B per correspondence"}},
+                         "effective_gbs_at_32B": (METRIC_BYTES_PER_PT_ITER * reg_rate / 1e9
+                                                  if reg_rate else None),
+                         "note": "the whole registration call (set-up, sweep-1 launch, "
+                                 "persistent launch, final sweep with the last solve and the "
+                                 "cost the adjoint needs: 10 sweeps streamed, 36 B per pixel "
+                                 "in the first and 28 B in each other); effective_gbs_at_32B "
+                                 "counts the metric's 32 B per correspondence and iteration"}},
         "sweep_variant": {"variant": variant, "tile_pixels": vt, "ctas_per_sm": vc,
                           "persistent": vp,
                           "tuning_ms": {str(k): v for k, v in tune_ms.items()}},

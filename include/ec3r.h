@@ -177,16 +177,19 @@ void ec3r_align_opts_default(ec3r_align_opts* o);
  * with and without want_cost differ at FP32 rounding level, as between sweep
  * variants.
  *
- * Launches.  A set-up kernel, then, with FP32 moments, one persistent launch
- * that runs every sweep and solve: tiles of pixels are handed out iteration
- * by iteration to resident CTAs, the CTA that completes a pair's tiles of an
- * iteration solves that pair, and a pair's next sweep waits only for its own
- * solve (a bounded wait: one that runs out raises EC3R_ERR_TIMEOUT at
- * ec3r_sync_status).  With want_cost the last sweep is a second launch that
- * starts as the first one's CTAs retire and also accumulates the sums from
- * which the cost under the last solve follows exactly (no extra pass over the
- * correspondences).  With FP64 accumulation, `iters` x (sweep, solve) grids
- * and, with want_cost, a cost sweep.
+ * Launches.  A set-up kernel, then, with FP32 moments, two persistent
+ * launches that run every sweep and solve: the first sweep, which also stores
+ * each correspondence's weight (NaN where it is invalid), then the later
+ * sweeps, which read that weight in place of both confidences (28 instead of
+ * 32 bytes per correspondence) and start as the first launch's CTAs retire.
+ * Tiles of pixels are handed out iteration by iteration to resident CTAs, the
+ * CTA that completes a pair's tiles of an iteration solves that pair, and a
+ * pair's next sweep waits only for its own solve (a bounded wait: one that
+ * runs out raises EC3R_ERR_TIMEOUT at ec3r_sync_status).  With want_cost the
+ * last sweep is one more launch that starts as the persistent CTAs retire and
+ * also accumulates the sums from which the cost under the last solve follows
+ * exactly (no extra pass over the correspondences).  With FP64 accumulation,
+ * `iters` x (sweep, solve) grids and, with want_cost, a cost sweep.
  * Replayed from a CUDA graph cached per argument set when `stream` is not
  * itself being captured.
  *
@@ -203,7 +206,9 @@ void ec3r_align_opts_default(ec3r_align_opts* o);
  * captured first call uses variant 0 untimed).  Other pointmaps use one fixed
  * configuration.
  *
- * Workspace: 300 bytes per 4096 link pixels, 4 bytes per link, and per pair
+ * Workspace: 4 bytes per link pixel (the stored weights, which
+ * ec3r_align_submaps_backward also reads), 300 bytes per 4096 link pixels,
+ * 4 bytes per link, and per pair
  * 444 bytes plus 448 bytes per iteration (the checkpoints that
  * ec3r_align_submaps_backward reuses).
  */

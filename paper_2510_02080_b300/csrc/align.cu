@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2) k_sweep(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
     const int32_t* __restrict__ link_pair, const PairState* __restrict__ st, float delta,
-    int rule, double* __restrict__ partials) {
+    int rule, double* __restrict__ partials, float* __restrict__ wout) {
   const int64_t t = blockIdx.x;
   const int64_t l = t / tpl;
   const int c = (int)(t - l * tpl);
@@ -160,6 +160,11 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2) k_sweep(
   const float* CQ = conf + ft * hw + px0;
   const int64_t rem = hw - px0;
   const int npx = rem < TILE ? (int)rem : TILE;
+  // the first FP32 sweep leaves every link pixel's weight for the later sweeps
+  // and the backward pass (pixel_weight: NaN marks an invalid correspondence)
+  constexpr bool STORE_W = sizeof(T) == 4 && KIND == FIRST;
+  float* WO = STORE_W && wout ? wout + l * hw + px0 : nullptr;
+  const float cmin = S.cmin;
 
   T acc[NMOM];
 #pragma unroll
@@ -180,12 +185,22 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2) k_sweep(
       op(pa.w, pb.x, pb.y, qa.w, qb.x, qb.y, cp.y, cq.y, acc);
       op(pb.z, pb.w, pc.x, qb.z, qb.w, qc.x, cp.z, cq.z, acc);
       op(pc.y, pc.z, pc.w, qc.y, qc.z, qc.w, cp.w, cq.w, acc);
+      if (STORE_W && WO)
+        __stcs(reinterpret_cast<float4*>(WO + i0),
+               make_float4(
+                   pixel_weight(pa.x, pa.y, pa.z, qa.x, qa.y, qa.z, cp.x, cq.x, cmin, rule),
+                   pixel_weight(pa.w, pb.x, pb.y, qa.w, qb.x, qb.y, cp.y, cq.y, cmin, rule),
+                   pixel_weight(pb.z, pb.w, pc.x, qb.z, qb.w, qc.x, cp.z, cq.z, cmin, rule),
+                   pixel_weight(pc.y, pc.z, pc.w, qc.y, qc.z, qc.w, cp.w, cq.w, cmin, rule)));
     } else {
       const int n = min(4, npx - i0);
       for (int j = 0; j < n; ++j) {
         const int i = i0 + j;
         op(P[3 * i], P[3 * i + 1], P[3 * i + 2], Q[3 * i], Q[3 * i + 1], Q[3 * i + 2], CP[i],
            CQ[i], acc);
+        if (STORE_W && WO)
+          __stcs(WO + i, pixel_weight(P[3 * i], P[3 * i + 1], P[3 * i + 2], Q[3 * i],
+                                      Q[3 * i + 1], Q[3 * i + 2], CP[i], CQ[i], cmin, rule));
       }
     }
   }
@@ -256,17 +271,17 @@ template <typename T, bool VEC>
 void launch_sweep(int kind, int64_t n_tiles, cudaStream_t s, const float* xyz, const float* conf,
                   int64_t hw, int tpl, const int32_t* src, const int32_t* tgt,
                   const int32_t* link_pair, const PairState* st, float delta, int rule,
-                  double* partials) {
+                  double* partials, float* wout) {
   const dim3 grid((unsigned)n_tiles);
   if (kind == FIRST)
     k_sweep<T, FIRST, VEC><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt, link_pair, st,
-                                                    delta, rule, partials);
+                                                    delta, rule, partials, wout);
   else if (kind == IRLS)
     k_sweep<T, IRLS, VEC><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt, link_pair, st,
-                                                   delta, rule, partials);
+                                                   delta, rule, partials, nullptr);
   else
     k_sweep<T, COST, VEC><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt, link_pair, st,
-                                                   delta, rule, partials);
+                                                   delta, rule, partials, nullptr);
 }
 
 }  // namespace align
@@ -315,7 +330,7 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "problem too large for one call");
   EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  void *p_state, *p_part, *p_lp, *p_ck, *p_cs, *p_ctl, *p_cp;
+  void *p_state, *p_part, *p_lp, *p_ck, *p_cs, *p_ctl, *p_cp, *p_w;
   ec3r_status st;
   const size_t ctl_bytes = reg_ctl_bytes(n_pairs);
   if ((st = ensure_buf(ctx, "align.state", sizeof(PairState) * (size_t)n_pairs, s, &p_state)) ||
@@ -332,7 +347,10 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
       (st = ensure_buf(ctx, "align.final_partials",
                        sizeof(double) * FINAL_VALUES *
                            (size_t)(n_links * ((hw + TILE - 1) / TILE) + 1),
-                       s, &p_cp)))
+                       s, &p_cp)) ||
+      // every link pixel's weight (NaN: invalid), written by the first sweep
+      (st = ensure_buf(ctx, "align.weights", sizeof(float) * ((size_t)n_links * hw + 4), s,
+                       &p_w)))
     return st;
   // (buffers that grew dropped the graphs holding older ones; re-read them all)
   PairState* state = (PairState*)ctx->bufs["align.state"].ptr;
@@ -341,6 +359,7 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
   double* ckpt = (double*)ctx->bufs["align.ckpt"].ptr;
   double* cost_sums = (double*)ctx->bufs["align.cost_sums"].ptr;
   void* ctl = ctx->bufs["align.ctl"].ptr;
+  float* weights = (float*)ctx->bufs["align.weights"].ptr;
   double* final_partials = (double*)ctx->bufs["align.final_partials"].ptr;
   const bool vec =
       (hw % 4 == 0) && ((uintptr_t)d_xyz % 16 == 0) && ((uintptr_t)d_conf % 16 == 0);
@@ -368,19 +387,22 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
       // persistent launch's tail); without, the persistent launch runs all.
       const int n_sweeps = o.want_cost ? o.iters - 1 : o.iters;
       ec3r_status r = EC3R_OK;
-      traced(ctx, cs, "irls_register", [&] {
-        r = launch_register(ctx, cs, v, vec, d_xyz, d_conf, hw, n_pairs, n_links, d_link_off,
-                            d_src, d_tgt, link_pair, state, partials, o.huber_delta,
-                            o.weight_rule, o.iters, n_sweeps, d_out, d_pair_status,
-                            o.want_cost ? d_pair_cost : nullptr, cost_sums, ckpt, ctl,
-                            ctl_bytes);
-      });
-      if (r != EC3R_OK) return r;
+      // sweep 1 (confidences in, pixel weights out), then sweeps 2 .. n_sweeps
+      for (const bool first : {true, false}) {
+        traced(ctx, cs, first ? "irls_sweep1" : "irls_register", [&] {
+          r = launch_register(ctx, cs, v, vec, first, d_xyz, d_conf, hw, n_pairs, n_links,
+                              d_link_off, d_src, d_tgt, link_pair, weights, state, partials,
+                              o.huber_delta, o.weight_rule, o.iters, n_sweeps, d_out,
+                              d_pair_status, o.want_cost ? d_pair_cost : nullptr, cost_sums,
+                              ckpt, ctl, ctl_bytes);
+        });
+        if (r != EC3R_OK) return r;
+      }
       if (o.want_cost) {
         traced(ctx, cs, "irls_final_sweep", [&] {
           r = launch_final(ctx, cs, vec, n_sweeps > 0 && !ctx->profiling, d_xyz, d_conf, hw,
-                           n_pairs, n_links, d_link_off, d_src, d_tgt, link_pair, state,
-                           final_partials, o.huber_delta, o.weight_rule, o.iters, d_out,
+                           n_pairs, n_links, d_link_off, d_src, d_tgt, link_pair, weights,
+                           state, final_partials, o.huber_delta, o.weight_rule, o.iters, d_out,
                            d_pair_status, d_pair_cost, cost_sums, ckpt, ctl);
         });
         if (r != EC3R_OK) return r;
@@ -397,13 +419,16 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
         if (n_tiles > 0) traced(ctx, cs, fp64 ? "irls_sweep_fp64" : "irls_sweep_fp32", [&] {
           if (fp64 && vec)
             launch_sweep<double, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
-                                       d_tgt, link_pair, state, dl, o.weight_rule, partials);
+                                       d_tgt, link_pair, state, dl, o.weight_rule, partials,
+                                       weights);
           else if (fp64)
             launch_sweep<double, false>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
-                                        d_tgt, link_pair, state, dl, o.weight_rule, partials);
+                                        d_tgt, link_pair, state, dl, o.weight_rule, partials,
+                                        weights);
           else
             launch_sweep<float, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
-                                      d_tgt, link_pair, state, dl, o.weight_rule, partials);
+                                      d_tgt, link_pair, state, dl, o.weight_rule, partials,
+                                      weights);
         });
         if (kind == COST)
           traced(ctx, cs, "irls_cost", [&] {
@@ -640,17 +665,21 @@ extern "C" ec3r_status ec3r_align_submaps_noalloc(
       if (fp64) {
         if (vec)
           launch_sweep<double, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
-                                     d_tgt, link_pair, state, dl, o.weight_rule, partials);
+                                     d_tgt, link_pair, state, dl, o.weight_rule, partials,
+                                     nullptr);
         else
           launch_sweep<double, false>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
-                                      d_tgt, link_pair, state, dl, o.weight_rule, partials);
+                                      d_tgt, link_pair, state, dl, o.weight_rule, partials,
+                                      nullptr);
       } else {
         if (vec)
           launch_sweep<float, true>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
-                                    d_tgt, link_pair, state, dl, o.weight_rule, partials);
+                                    d_tgt, link_pair, state, dl, o.weight_rule, partials,
+                                    nullptr);
         else
           launch_sweep<float, false>(kind, n_tiles, cs, d_xyz, d_conf, hw, (int)tpl, d_src,
-                                     d_tgt, link_pair, state, dl, o.weight_rule, partials);
+                                     d_tgt, link_pair, state, dl, o.weight_rule, partials,
+                                     nullptr);
       }
     }
     if (kind == COST)

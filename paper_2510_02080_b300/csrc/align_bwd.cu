@@ -117,12 +117,13 @@ __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ck
 
 // Reduction sweep of the Huber path of iteration k (S_{k-1} and the
 // moments' gradient of k).  (The cost term's sums come from the forward's
-// last sweep.)
+// last sweep.)  The pixels' weights are the ones the forward's first sweep
+// stored (NaN: invalid), so a pixel costs 28 bytes, not 32.
 template <bool LASTK, bool VEC>
 __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
-    const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
+    const float* __restrict__ xyz, const float* __restrict__ weights, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
-    const int32_t* __restrict__ link_pair, const RedParams* __restrict__ rp, int rule,
+    const int32_t* __restrict__ link_pair, const RedParams* __restrict__ rp,
     double* __restrict__ partials) {
   const int64_t t = blockIdx.x;
   const int64_t l = t / tpl;
@@ -146,29 +147,23 @@ __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
   constexpr bool lastk = LASTK;  // the cost residual at S_K enters the last Huber sweep
   const float pp0 = RP.pp[0], pp1 = RP.pp[1], pp2 = RP.pp[2];
   const float pq0 = RP.pq[0], pq1 = RP.pq[1], pq2 = RP.pq[2];
-  const float cmin = RP.cmin;
   const float dl = RP.dl;
 
   const int64_t fs = src[l], ft = tgt[l];
   const int64_t px0 = (int64_t)c * TILE;
   const float* P = xyz + (fs * hw + px0) * 3;
   const float* Q = xyz + (ft * hw + px0) * 3;
-  const float* CP = conf + fs * hw + px0;
-  const float* CQ = conf + ft * hw + px0;
+  const float* WL = weights + l * hw + px0;
   const int64_t rem = hw - px0;
   const int npx = rem < TILE ? (int)rem : TILE;
   float acc[NRED];
 #pragma unroll
   for (int m = 0; m < NRED; ++m) acc[m] = 0.f;
 
-  auto point = [&](float p0, float p1, float p2, float q0, float q1, float q2, float cp,
-                   float cq) {
-    const bool v = finitef(p0) && finitef(p1) && finitef(p2) && finitef(q0) && finitef(q1) &&
-                   finitef(q2) && finitef(cp) && finitef(cq) && cp > cmin && cq > cmin;
-    if (!v) return;
+  auto point = [&](float p0, float p1, float p2, float q0, float q1, float q2, float w) {
+    if (!(w == w)) return;
     const float x0 = p0 - pp0, x1 = p1 - pp1, x2 = p2 - pp2;
     const float y0 = q0 - pq0, y1 = q1 - pq1, y2 = q2 - pq2;
-    const float w = rule == 0 ? cp * cq : cp;
     const float e0 = Ap[0] * x0 + Ap[1] * x1 + Ap[2] * x2 + bp[0] - y0;
     const float e1 = Ap[3] * x0 + Ap[4] * x1 + Ap[5] * x2 + bp[1] - y1;
     const float e2 = Ap[6] * x0 + Ap[7] * x1 + Ap[8] * x2 + bp[2] - y2;
@@ -207,18 +202,16 @@ __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
       const float4* Q4 = reinterpret_cast<const float4*>(Q + 3 * i0);
       const float4 pa = __ldcs(P4), pb = __ldcs(P4 + 1), pc = __ldcs(P4 + 2);
       const float4 qa = __ldcs(Q4), qb = __ldcs(Q4 + 1), qc = __ldcs(Q4 + 2);
-      const float4 cp = __ldcs(reinterpret_cast<const float4*>(CP + i0));
-      const float4 cq = __ldcs(reinterpret_cast<const float4*>(CQ + i0));
-      point(pa.x, pa.y, pa.z, qa.x, qa.y, qa.z, cp.x, cq.x);
-      point(pa.w, pb.x, pb.y, qa.w, qb.x, qb.y, cp.y, cq.y);
-      point(pb.z, pb.w, pc.x, qb.z, qb.w, qc.x, cp.z, cq.z);
-      point(pc.y, pc.z, pc.w, qc.y, qc.z, qc.w, cp.w, cq.w);
+      const float4 w = __ldcs(reinterpret_cast<const float4*>(WL + i0));
+      point(pa.x, pa.y, pa.z, qa.x, qa.y, qa.z, w.x);
+      point(pa.w, pb.x, pb.y, qa.w, qb.x, qb.y, w.y);
+      point(pb.z, pb.w, pc.x, qb.z, qb.w, qc.x, w.z);
+      point(pc.y, pc.z, pc.w, qc.y, qc.z, qc.w, w.w);
     } else {
       const int n = min(4, npx - i0);
       for (int j = 0; j < n; ++j) {
         const int i = i0 + j;
-        point(P[3 * i], P[3 * i + 1], P[3 * i + 2], Q[3 * i], Q[3 * i + 1], Q[3 * i + 2], CP[i],
-              CQ[i]);
+        point(P[3 * i], P[3 * i + 1], P[3 * i + 2], Q[3 * i], Q[3 * i + 1], Q[3 * i + 2], WL[i]);
       }
     }
   }
@@ -770,6 +763,7 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
   PairState* state = (PairState*)ctx->bufs["align.state"].ptr;
   double* ckpt = (double*)ctx->bufs["align.ckpt"].ptr;
   int32_t* link_pair = (int32_t*)ctx->bufs["align.link_pair"].ptr;
+  const float* weights = (const float*)ctx->bufs["align.weights"].ptr;
   AdjState* adj = (AdjState*)p_adj;
   RedParams* rp = (RedParams*)p_rp;
   double* gM = (double*)p_gm;
@@ -813,16 +807,16 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
           const bool last = k == iters;
           if (vec && last)
             k_adj_reduce<true, true><<<grid, THREADS, 0, cs>>>(
-                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
+                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part);
           else if (vec)
             k_adj_reduce<false, true><<<grid, THREADS, 0, cs>>>(
-                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
+                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part);
           else if (last)
             k_adj_reduce<true, false><<<grid, THREADS, 0, cs>>>(
-                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
+                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part);
           else
             k_adj_reduce<false, false><<<grid, THREADS, 0, cs>>>(
-                d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, rp, rule, part);
+                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part);
         });
       traced(ctx, cs, "adj_solve", [&] {
         k_adj_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, iters, k - 1, d_link_off, (int)tpl,

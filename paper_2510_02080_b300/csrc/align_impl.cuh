@@ -38,6 +38,20 @@ struct PairState {
 
 __device__ __forceinline__ bool finitef(float x) { return fabsf(x) <= FLT_MAX; }
 
+// A link pixel's weight as the first FP32 sweep leaves it for the later
+// sweeps and the backward pass (4 B per link pixel instead of both 4-byte
+// confidences): w = c_p c_q (rule 0) or c_p when the correspondence is valid
+// (p, q, c_p, c_q finite and both confidences above cmin), NaN when it is not.
+// (A valid weight can be <= 0 only under a negative threshold, so validity
+// cannot be read from the sign.)
+__device__ __forceinline__ float pixel_weight(float p0, float p1, float p2, float q0, float q1,
+                                              float q2, float cp, float cq, float cmin,
+                                              int rule) {
+  const bool v = finitef(p0) && finitef(p1) && finitef(p2) && finitef(q0) && finitef(q1) &&
+                 finitef(q2) && finitef(cp) && finitef(cq) && cp > cmin && cq > cmin;
+  return v ? (rule == 0 ? cp * cq : cp) : __int_as_float(0x7fc00000);
+}
+
 // Per pair and iteration, the forward solve keeps (for the backward pass) the
 // 19 moments, A = s R (9) and b (3) of its estimate, its status, s and R
 // themselves, and the singular values d (3) and right singular vectors V (9)
@@ -504,11 +518,11 @@ int reg_grid_variant();  // the variant that runs separate grids per sweep and s
 bool reg_variant_info(int v, int* tile, int* ctas, int* persistent);
 int reg_min_tile();
 size_t reg_ctl_bytes(int n_pairs);
-ec3r_status launch_register(ec3r_ctx* ctx, cudaStream_t s, int v, bool vec,
+ec3r_status launch_register(ec3r_ctx* ctx, cudaStream_t s, int v, bool vec, bool first,
                             const float* xyz, const float* conf, int64_t hw, int n_pairs,
                             int64_t n_links, const int32_t* link_off, const int32_t* src,
-                            const int32_t* tgt, const int32_t* link_pair, PairState* st,
-                            double* partials, float delta, int rule, int iters,
+                            const int32_t* tgt, const int32_t* link_pair, float* weights,
+                            PairState* st, double* partials, float delta, int rule, int iters,
                             int n_sweeps, ec3r_sim3* out, int32_t* status_out, double* cost,
                             double* cost_sums, double* ckpt, void* ctl, size_t ctl_bytes);
 // Values per final-sweep tile (the partials buffer of launch_final holds
@@ -517,8 +531,9 @@ constexpr int FINAL_VALUES = NMOM + 18;
 ec3r_status launch_final(ec3r_ctx* ctx, cudaStream_t s, bool vec, bool after_register,
                          const float* xyz, const float* conf, int64_t hw, int n_pairs,
                          int64_t n_links, const int32_t* link_off, const int32_t* src,
-                         const int32_t* tgt, const int32_t* link_pair, PairState* st,
-                         double* partials, float delta, int rule, int iters, ec3r_sim3* out,
+                         const int32_t* tgt, const int32_t* link_pair, float* weights,
+                         PairState* st, double* partials, float delta, int rule, int iters,
+                         ec3r_sim3* out,
                          int32_t* status_out, double* cost, double* cost_sums, double* ckpt,
                          void* ctl);
 
