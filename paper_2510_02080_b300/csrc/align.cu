@@ -125,13 +125,16 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup(
 // --------------------------------------------------------------------------
 // Per-tile partial moments.  Each thread sums its 32 pixels (8 groups of 4
 // consecutive pixels); warps combine by a pairwise butterfly in T; the eight
-// warp sums are added in FP64 in a fixed order.
-template <typename T, int KIND, bool VEC>
+// warp sums are added in FP64 in a fixed order.  `wbuf` ([n_links][hw],
+// nullable): the first FP32 sweep writes every link pixel's weight there;
+// with WGT a later sweep reads it instead of both confidences (28 B per pixel
+// instead of 32).
+template <typename T, int KIND, bool VEC, bool WGT>
 __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2) k_sweep(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
     const int32_t* __restrict__ link_pair, const PairState* __restrict__ st, float delta,
-    int rule, double* __restrict__ partials, float* __restrict__ wout) {
+    int rule, double* __restrict__ partials, float* __restrict__ wbuf) {
   const int64_t t = blockIdx.x;
   const int64_t l = t / tpl;
   const int c = (int)(t - l * tpl);
@@ -163,7 +166,8 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2) k_sweep(
   // the first FP32 sweep leaves every link pixel's weight for the later sweeps
   // and the backward pass (pixel_weight: NaN marks an invalid correspondence)
   constexpr bool STORE_W = sizeof(T) == 4 && KIND == FIRST;
-  float* WO = STORE_W && wout ? wout + l * hw + px0 : nullptr;
+  float* WO = STORE_W && wbuf ? wbuf + l * hw + px0 : nullptr;
+  const float* WI = WGT ? wbuf + l * hw + px0 : nullptr;
   const float cmin = S.cmin;
 
   T acc[NMOM];
@@ -179,6 +183,14 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2) k_sweep(
       const float4* Q4 = reinterpret_cast<const float4*>(Q + 3 * i0);
       const float4 pa = __ldcs(P4), pb = __ldcs(P4 + 1), pc = __ldcs(P4 + 2);
       const float4 qa = __ldcs(Q4), qb = __ldcs(Q4 + 1), qc = __ldcs(Q4 + 2);
+      if constexpr (WGT) {
+        const float4 w = __ldcs(reinterpret_cast<const float4*>(WI + i0));
+        op(pa.x, pa.y, pa.z, qa.x, qa.y, qa.z, w.x, acc);
+        op(pa.w, pb.x, pb.y, qa.w, qb.x, qb.y, w.y, acc);
+        op(pb.z, pb.w, pc.x, qb.z, qb.w, qc.x, w.z, acc);
+        op(pc.y, pc.z, pc.w, qc.y, qc.z, qc.w, w.w, acc);
+        continue;
+      }
       const float4 cp = __ldcs(reinterpret_cast<const float4*>(CP + i0));
       const float4 cq = __ldcs(reinterpret_cast<const float4*>(CQ + i0));
       op(pa.x, pa.y, pa.z, qa.x, qa.y, qa.z, cp.x, cq.x, acc);
@@ -196,6 +208,11 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 4 : 2) k_sweep(
       const int n = min(4, npx - i0);
       for (int j = 0; j < n; ++j) {
         const int i = i0 + j;
+        if constexpr (WGT) {
+          op(P[3 * i], P[3 * i + 1], P[3 * i + 2], Q[3 * i], Q[3 * i + 1], Q[3 * i + 2],
+             __ldcs(WI + i), acc);
+          continue;
+        }
         op(P[3 * i], P[3 * i + 1], P[3 * i + 2], Q[3 * i], Q[3 * i + 1], Q[3 * i + 2], CP[i],
            CQ[i], acc);
         if (STORE_W && WO)
@@ -271,17 +288,36 @@ template <typename T, bool VEC>
 void launch_sweep(int kind, int64_t n_tiles, cudaStream_t s, const float* xyz, const float* conf,
                   int64_t hw, int tpl, const int32_t* src, const int32_t* tgt,
                   const int32_t* link_pair, const PairState* st, float delta, int rule,
-                  double* partials, float* wout) {
+                  double* partials, float* wbuf) {
   const dim3 grid((unsigned)n_tiles);
-  if (kind == FIRST)
-    k_sweep<T, FIRST, VEC><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt, link_pair, st,
-                                                    delta, rule, partials, wout);
-  else if (kind == IRLS)
-    k_sweep<T, IRLS, VEC><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt, link_pair, st,
-                                                   delta, rule, partials, nullptr);
+  if (kind == FIRST) {
+    k_sweep<T, FIRST, VEC, false><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt,
+                                                           link_pair, st, delta, rule, partials,
+                                                           wbuf);
+    return;
+  }
+  // FP32 sweeps after the first read the weights it stored (when it stored them)
+  if constexpr (sizeof(T) == 4) {
+    if (wbuf) {
+      if (kind == IRLS)
+        k_sweep<T, IRLS, VEC, true><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt,
+                                                             link_pair, st, delta, rule, partials,
+                                                             wbuf);
+      else
+        k_sweep<T, COST, VEC, true><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt,
+                                                             link_pair, st, delta, rule, partials,
+                                                             wbuf);
+      return;
+    }
+  }
+  if (kind == IRLS)
+    k_sweep<T, IRLS, VEC, false><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt,
+                                                          link_pair, st, delta, rule, partials,
+                                                          nullptr);
   else
-    k_sweep<T, COST, VEC><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt, link_pair, st,
-                                                   delta, rule, partials, nullptr);
+    k_sweep<T, COST, VEC, false><<<grid, THREADS, 0, s>>>(xyz, conf, hw, tpl, src, tgt,
+                                                          link_pair, st, delta, rule, partials,
+                                                          nullptr);
 }
 
 }  // namespace align

@@ -240,16 +240,29 @@ struct PointOp {
   float cmin;
   int rule;
 
+  // from both confidences
   __device__ __forceinline__ void operator()(float p0, float p1, float p2, float q0, float q1,
                                              float q2, float cp, float cq, T* acc) const {
     const bool v = finitef(p0) && finitef(p1) && finitef(p2) && finitef(q0) && finitef(q1) &&
                    finitef(q2) && finitef(cp) && finitef(cq) && cp > cmin && cq > cmin;
+    const T w = rule == 0 ? (T)cp * (T)cq : (T)cp;
+    point(p0, p1, p2, q0, q1, q2, v, v ? w : T(0), acc);
+  }
+
+  // from the pixel weight that the first FP32 sweep stored (NaN: invalid;
+  // the same FP32 product as above)
+  __device__ __forceinline__ void operator()(float p0, float p1, float p2, float q0, float q1,
+                                             float q2, float wv, T* acc) const {
+    const bool v = wv == wv;
+    point(p0, p1, p2, q0, q1, q2, v, v ? (T)wv : T(0), acc);
+  }
+
+  __device__ __forceinline__ void point(float p0, float p1, float p2, float q0, float q1,
+                                        float q2, bool v, T w, T* acc) const {
     const T x0 = v ? (T)p0 - pp[0] : T(0), x1 = v ? (T)p1 - pp[1] : T(0),
             x2 = v ? (T)p2 - pp[2] : T(0);
     const T y0 = v ? (T)q0 - pq[0] : T(0), y1 = v ? (T)q1 - pq[1] : T(0),
             y2 = v ? (T)q2 - pq[2] : T(0);
-    T w = rule == 0 ? (T)cp * (T)cq : (T)cp;
-    w = v ? w : T(0);
     T h = T(1), r2 = T(0), f0 = T(0), f1 = T(0), f2 = T(0);
     if (KIND != FIRST) {
       const T* a = (KIND == COST) ? Ap : A;
