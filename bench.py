@@ -48,11 +48,10 @@ SWEEP_BYTES_PER_PIXEL = 28
 METRIC_BYTES_PER_PT_ITER = 32
 # DRAM bytes (read + write) per link pixel and sweep of the persistent launch
 # of sweeps 2 .. 9, by sweep variant: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch per variant on the 40-submap chain with
-# the cost wanted (39 links x 152,292 px, 8 sweeps; the traffic scales with the
-# pixels and sweeps of a launch).  Variants without a capture of this build
-# report null.  Empty once the kernel changes.
-REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP = {}
+# dram__bytes_write.sum of that launch on this workload at full size (one-pass
+# counters; 199 links x 152,292 px, 8 sweeps).  Variants without a capture of
+# this build report null.  Emptied whenever the kernel changes.
+REGISTER_TRAFFIC_BYTES_PER_PIXEL_SWEEP = {6: 28.10, 9: 28.07}
 
 
 def peaks():
