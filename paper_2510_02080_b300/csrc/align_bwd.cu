@@ -391,6 +391,72 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
+// One iteration of the scatter for a packed pixel pair.  S: estimate it-1
+// (A, b) and gM of iteration it; Sp: the estimate whose residual weights
+// iteration it (HUBER: it > 1; iteration 1 has h = 1); COSTK: the last
+// iteration, which also carries the cost terms of the returned estimate.
+template <bool HUBER, bool COSTK>
+__device__ __forceinline__ void scatter_iter(const float2* S, const float2* Sp, const float2 (&X)[3],
+                                             const float2 (&Y)[3], const float2 (&nY)[3],
+                                             float2 W, float2 XX, float delta, float d2,
+                                             float gJ, float gOm, float2 (&gp)[3],
+                                             float2 (&gq)[3], float2& gw, float2 (&Gt)[NGM]) {
+  float2 h = f2(1.f), e[3] = {f2(0.f), f2(0.f), f2(0.f)}, rr = f2(0.f), rs = f2(0.f);
+  if (HUBER) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      e[r] = fma2(Sp[3 * r], X[0],
+                  fma2(Sp[3 * r + 1], X[1], fma2(Sp[3 * r + 2], X[2], add2(Sp[9 + r], nY[r]))));
+    rr = fma2(e[0], e[0], fma2(e[1], e[1], mul2(e[2], e[2])));
+    rs = make_float2(rsqrtf(rr.x), rsqrtf(rr.y));
+    const float2 dr = mul2(f2(delta), rs);
+    h = make_float2(fminf(1.f, dr.x), fminf(1.f, dr.y));
+  }
+  const float2 om = mul2(W, h);
+  const float2* G = S + 12;
+  float2 gom = fma2(G[G_PP], XX, G[G_W]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float2 Gx = fma2(G[G_QP + 3 * r], X[0],
+                           fma2(G[G_QP + 3 * r + 1], X[1], fma2(G[G_QP + 3 * r + 2], X[2], G[G_SQ + r])));
+    gom = fma2(G[G_SP + r], X[r], gom);
+    gom = fma2(Y[r], Gx, gom);
+  }
+#pragma unroll
+  for (int i = 0; i < NGM; ++i) Gt[i] = fma2(om, G[i], Gt[i]);
+  if (COSTK) {  // cost terms of the returned estimate
+    float2 f[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      f[r] = fma2(S[3 * r], X[0],
+                  fma2(S[3 * r + 1], X[1], fma2(S[3 * r + 2], X[2], add2(S[9 + r], nY[r]))));
+    const float2 ff = fma2(f[0], f[0], fma2(f[1], f[1], mul2(f[2], f[2])));
+    gom = add2(gom, fma2(f2(gJ), ff, f2(gOm)));
+    const float2 s2 = mul2(f2(2.f * gJ), om);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float2 ge = mul2(s2, f[r]);
+      gq[r] = fma2(f2(-1.f), ge, gq[r]);
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) gp[cc] = fma2(S[3 * r + cc], ge, gp[cc]);
+    }
+  }
+  gw = fma2(gom, h, gw);
+  if (HUBER) {
+    // Huber branch (|r| > delta): d h / d e = -delta e / |r|^3
+    float2 u = mul2(mul2(gom, W), mul2(f2(-delta), mul2(rs, mul2(rs, rs))));
+    u.x = rr.x > d2 ? u.x : 0.f;
+    u.y = rr.y > d2 ? u.y : 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float2 ge = mul2(u, e[r]);
+      gq[r] = fma2(f2(-1.f), ge, gq[r]);
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) gp[cc] = fma2(Sp[3 * r + cc], ge, gp[cc]);
+    }
+  }
+}
+
 template <bool VEC>
 __global__ void __launch_bounds__(THREADS, 2) k_adj_scatter(
     const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
@@ -499,68 +565,23 @@ __global__ void __launch_bounds__(THREADS, 2) k_adj_scatter(
 #pragma unroll
     for (int i = 0; i < NGM; ++i) Gt[i] = f2(0.f);
     if (active) {
-      // two iterations per trip: the next one's shared-memory constants load while
-      // this one computes (3 % faster, bit-identical)
+      // iteration 1 (unit Huber weights) and the last one (cost terms) peeled,
+      // so that the iterations between run without branches, two per trip
+      // (the next one's shared-memory constants load while this one computes)
+      if (iters == 1) {
+        scatter_iter<false, true>(sh2, sh2, X, Y, nY, W, XX, delta, d2, gJ, gOm, gp, gq, gw, Gt);
+      } else {
+        scatter_iter<false, false>(sh2, sh2, X, Y, nY, W, XX, delta, d2, gJ, gOm, gp, gq, gw,
+                                   Gt);
 #pragma unroll 2
-      for (int it = 1; it <= iters; ++it) {
-        const float2* S = sh2 + (it - 1) * SC_PAIRS;  // estimate it-1 (A, b) and gM of it
-        const float2* Sp = S - (it > 1 ? SC_PAIRS : 0);  // estimate the weights of it use
-        float2 h = f2(1.f), e[3] = {f2(0.f), f2(0.f), f2(0.f)}, rr = f2(0.f), rs = f2(0.f);
-        if (it > 1) {
-#pragma unroll
-          for (int r = 0; r < 3; ++r)
-            e[r] = fma2(Sp[3 * r], X[0],
-                        fma2(Sp[3 * r + 1], X[1],
-                             fma2(Sp[3 * r + 2], X[2], add2(Sp[9 + r], nY[r]))));
-          rr = fma2(e[0], e[0], fma2(e[1], e[1], mul2(e[2], e[2])));
-          rs = make_float2(rsqrtf(rr.x), rsqrtf(rr.y));
-          const float2 dr = mul2(f2(delta), rs);
-          h = make_float2(fminf(1.f, dr.x), fminf(1.f, dr.y));
+        for (int it = 2; it < iters; ++it) {
+          const float2* S = sh2 + (it - 1) * SC_PAIRS;
+          scatter_iter<true, false>(S, S - SC_PAIRS, X, Y, nY, W, XX, delta, d2, gJ, gOm, gp, gq,
+                                    gw, Gt);
         }
-        const float2 om = mul2(W, h);
-        const float2* G = S + 12;
-        float2 gom = fma2(G[G_PP], XX, G[G_W]);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const float2 Gx = fma2(G[G_QP + 3 * r], X[0],
-                                 fma2(G[G_QP + 3 * r + 1], X[1],
-                                      fma2(G[G_QP + 3 * r + 2], X[2], G[G_SQ + r])));
-          gom = fma2(G[G_SP + r], X[r], gom);
-          gom = fma2(Y[r], Gx, gom);
-        }
-#pragma unroll
-        for (int i = 0; i < NGM; ++i) Gt[i] = fma2(om, G[i], Gt[i]);
-        if (it == iters) {  // cost terms of the returned estimate
-          float2 f[3];
-#pragma unroll
-          for (int r = 0; r < 3; ++r)
-            f[r] = fma2(S[3 * r], X[0],
-                        fma2(S[3 * r + 1], X[1], fma2(S[3 * r + 2], X[2], add2(S[9 + r], nY[r]))));
-          const float2 ff = fma2(f[0], f[0], fma2(f[1], f[1], mul2(f[2], f[2])));
-          gom = add2(gom, fma2(f2(gJ), ff, f2(gOm)));
-          const float2 s2 = mul2(f2(2.f * gJ), om);
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            const float2 ge = mul2(s2, f[r]);
-            gq[r] = fma2(f2(-1.f), ge, gq[r]);
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) gp[cc] = fma2(S[3 * r + cc], ge, gp[cc]);
-          }
-        }
-        gw = fma2(gom, h, gw);
-        if (it > 1) {
-          // Huber branch (|r| > delta): d h / d e = -delta e / |r|^3
-          float2 u = mul2(mul2(gom, W), mul2(f2(-delta), mul2(rs, mul2(rs, rs))));
-          u.x = rr.x > d2 ? u.x : 0.f;
-          u.y = rr.y > d2 ? u.y : 0.f;
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            const float2 ge = mul2(u, e[r]);
-            gq[r] = fma2(f2(-1.f), ge, gq[r]);
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) gp[cc] = fma2(Sp[3 * r + cc], ge, gp[cc]);
-          }
-        }
+        const float2* S = sh2 + (iters - 1) * SC_PAIRS;
+        scatter_iter<true, true>(S, S - SC_PAIRS, X, Y, nY, W, XX, delta, d2, gJ, gOm, gp, gq, gw,
+                                 Gt);
       }
       // the fixed-weight part: d<Gt, phi>/dp and d<Gt, phi>/dq
 #pragma unroll
