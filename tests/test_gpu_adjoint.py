@@ -174,6 +174,32 @@ def test_adjoint_shared_frames_accumulate(ctx):
     compare(gc.cpu().double().numpy(), gc_or, ~kink, "dL/dconf", allow["c"])
 
 
+def test_adjoint_scalar_path_with_invalid_pixels(ctx):
+    """hw = 31 x 39 = 1209, not a multiple of 4: the scalar load paths of the
+    forward sweeps and of the backward's reduction sweeps.  Invalid pixels (NaN
+    and infinite coordinates, zero and negative confidences) carry the stored
+    weight NaN; their gradients are zero and the rest match the oracle's."""
+    ps = synth.make_pair(synth.SEED_BASE + 9, H=31, W=39, sigma=0.005)
+    xyz, conf = ps.xyz.clone(), ps.conf.clone()
+    xyz[0, 7, 1] = float("nan")
+    xyz[0, 300, 0] = float("inf")
+    xyz[1, 512, 2] = -float("inf")
+    conf[0, 40] = 0.0
+    conf[1, 41] = -1.0
+    conf[1, 1208] = float("nan")
+    ps = synth.PairSet(xyz, conf, ps.link_off, ps.src, ps.tgt, ps.H, ps.W, ps.S_gt)
+    gS, gx_or, gc_or, kink, allow = oracle_grads(ps, truth_list(ps))
+    d = cuda_set(ps)
+    gx, gc = ctx.align_submaps_backward(d.xyz, d.conf, d.link_off, d.src, d.tgt,
+                                        torch.tensor(gS, device="cuda"),
+                                        torch.ones(1, dtype=torch.float64, device="cuda"))
+    gx, gc = gx.cpu().double().numpy(), gc.cpu().double().numpy()
+    for f, i in ((0, 7), (0, 300), (1, 512), (0, 40), (1, 41), (1, 1208)):
+        assert np.all(gx[f, i] == 0.0) and gc[f, i] == 0.0, (f, i)
+    compare(gx, gx_or, ~kink, "dL/dxyz", allow["x"])
+    compare(gc, gc_or, ~kink, "dL/dconf", allow["c"])
+
+
 def test_adjoint_against_fp64_finite_differences_2k_subset(ctx):
     """2048-point pair; FP64 central differences of the oracle forward loss."""
     ps = synth.make_pair(synth.SEED_BASE + 8, H=32, W=64, sigma=0.005)
