@@ -1254,7 +1254,7 @@ def run_workload(args):
                                                    dps.src, dps.tgt, delta=DELTA, iters=ITERS,
                                                    out=S, status=st), 10)
         assert ctx.sync_status() == 0 and int((st != 0).sum()) == 0
-        ks = [0, 99, 198]
+        ks = sorted({0, dps.n_pairs // 2, dps.n_pairs - 1})
         out["oracle_error"] = {"registration": registration_error(
             S, st, [_host_depth_pair(dps, k) for k in ks], ks)}
         ctx.profile(True)
