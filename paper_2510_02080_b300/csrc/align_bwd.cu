@@ -457,14 +457,48 @@ __device__ __forceinline__ void scatter_iter(const float2* S, const float2* Sp, 
   }
 }
 
+// The frame zeroing that the scatter's CTAs share: the frame bank's pixels
+// (frame-major, n_frames x hw) split into equal runs of a multiple of four
+// pixels, one per CTA; a run's pixels of a frame that no scatter writes
+// directly (references 0 or > 1) are zeroed.  The stores drain while the
+// CTA computes: the scatter is bound by FP32 latency, not by HBM.
+template <bool VEC>
+__device__ __forceinline__ void zero_share(int64_t n_frames, int64_t hw,
+                                           const int32_t* __restrict__ refs,
+                                           float* __restrict__ gxyz, float* __restrict__ gconf) {
+  const int64_t U = n_frames * hw, G = gridDim.x;
+  const int64_t per = (((U + G - 1) / G) + 3) & ~(int64_t)3;
+  int64_t u0 = (int64_t)blockIdx.x * per;
+  const int64_t u1 = min(U, u0 + per);
+  while (u0 < u1) {
+    const int64_t f = u0 / hw;
+    const int64_t fe = min(u1, (f + 1) * hw);
+    if (refs[f] != 1) {
+      if (VEC) {  // hw and the run boundaries are multiples of 4 pixels
+        float4* x4 = reinterpret_cast<float4*>(gxyz + 3 * u0);
+        float4* c4 = reinterpret_cast<float4*>(gconf + u0);
+        const int64_t n4 = (fe - u0) / 4;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t i = threadIdx.x; i < 3 * n4; i += THREADS) __stcs(x4 + i, z);
+        for (int64_t i = threadIdx.x; i < n4; i += THREADS) __stcs(c4 + i, z);
+      } else {
+        for (int64_t i = 3 * u0 + threadIdx.x; i < 3 * fe; i += THREADS) gxyz[i] = 0.f;
+        for (int64_t i = u0 + threadIdx.x; i < fe; i += THREADS) gconf[i] = 0.f;
+      }
+    }
+    u0 = fe;
+  }
+}
+
 template <bool VEC>
 __global__ void __launch_bounds__(THREADS, 2) k_adj_scatter(
-    const float* __restrict__ xyz, const float* __restrict__ conf, int64_t hw, int tpl,
-    const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
+    const float* __restrict__ xyz, const float* __restrict__ conf, int64_t n_frames, int64_t hw,
+    int tpl, const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
     const int32_t* __restrict__ link_pair, const PairState* __restrict__ st,
     const AdjState* __restrict__ adj, const double* __restrict__ ckpt,
     const double* __restrict__ gM, int iters, float delta, int rule, float* __restrict__ lg,
     const int32_t* __restrict__ refs, float* __restrict__ gxyz, float* __restrict__ gconf) {
+  zero_share<VEC>(n_frames, hw, refs, gxyz, gconf);
   const int64_t t = blockIdx.x;
   const int64_t l = t / tpl;
   const int c = (int)(t - l * tpl);
@@ -851,33 +885,29 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
         k_adj_refcount<<<(unsigned)((n_links + 255) / 256), 256, 0, cs>>>(
             n_links, n_frames, d_src, d_tgt, link_pair, refs, any_shared);
       });
-    // Branch: zeroing every frame that the scatter does not write directly
-    // (HBM-bound) runs beside the ALU-bound scatter, which writes only the
-    // other frames; both join before the shared frames are summed.
-    // (Under per-kernel profiling everything stays on one stream.)
-    cudaStream_t side = ctx->profiling ? cs : ctx->side_stream;
-    if (side != cs) {
-      EC3R_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, cs));
-      EC3R_CUDA_TRY(ctx, cudaStreamWaitEvent(side, ctx->ev_fork, 0));
-    }
-    traced(ctx, side, "adj_zero_frames", [&] {
-      k_adj_zero_frames<<<(unsigned)n_frames, 512, 0, side>>>(hw, refs, d_grad_xyz, d_grad_conf);
-    });
-    if (side != cs) EC3R_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, side));
+    // The scatter writes the frames that exactly one link references; its CTAs
+    // also zero every other frame (zero_share: HBM stores beside FP32-bound
+    // work, where a separate zeroing kernel could not run beside the scatter,
+    // whose two CTAs per SM hold the whole register file).
     if (n_tiles > 0) {
       const size_t shm = sizeof(float2) * SC_PAIRS * (size_t)iters;
+      const bool vz = vec && ((uintptr_t)d_grad_xyz % 16 == 0) &&
+                      ((uintptr_t)d_grad_conf % 16 == 0);
       traced(ctx, cs, "adj_scatter", [&] {
-        if (vec)
+        if (vz)
           k_adj_scatter<true><<<grid, THREADS, shm, cs>>>(
-              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
-              delta, rule, lg, refs, d_grad_xyz, d_grad_conf);
+              d_xyz, d_conf, n_frames, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt,
+              gM, iters, delta, rule, lg, refs, d_grad_xyz, d_grad_conf);
         else
           k_adj_scatter<false><<<grid, THREADS, shm, cs>>>(
-              d_xyz, d_conf, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt, gM, iters,
-              delta, rule, lg, refs, d_grad_xyz, d_grad_conf);
+              d_xyz, d_conf, n_frames, hw, (int)tpl, d_src, d_tgt, link_pair, state, adj, ckpt,
+              gM, iters, delta, rule, lg, refs, d_grad_xyz, d_grad_conf);
+      });
+    } else {
+      traced(ctx, cs, "adj_zero_frames", [&] {
+        k_adj_zero_frames<<<(unsigned)n_frames, 512, 0, cs>>>(hw, refs, d_grad_xyz, d_grad_conf);
       });
     }
-    if (side != cs) EC3R_CUDA_TRY(ctx, cudaStreamWaitEvent(cs, ctx->ev_join, 0));
     if (n_tiles > 0)
       traced(ctx, cs, "adj_frames", [&] {
         k_adj_frames<<<(unsigned)((hw + 255) / 256), 256, 0, cs>>>(hw, n_links, d_src, d_tgt,

@@ -39,10 +39,7 @@ ec3r_status ec3r_create(ec3r_ctx** out, int device) {
       cudaMalloc(&c->d_flags, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(c->d_flags, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&c->h_flags, sizeof(unsigned)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     ec3r_destroy(c);
     return EC3R_ERR_CUDA;
@@ -67,9 +64,6 @@ void ec3r_destroy(ec3r_ctx* c) {
   if (c->d_flags) cudaFree(c->d_flags);
   if (c->h_flags) cudaFreeHost(c->h_flags);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
-  if (c->side_stream) cudaStreamDestroy(c->side_stream);
-  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
 }
 

@@ -61,9 +61,6 @@ struct ec3r_ctx {
   unsigned* d_flags = nullptr;  // device status word
   unsigned* h_flags = nullptr;  // pinned mirror
   cudaStream_t capture_stream = nullptr;
-  // second stream and fork/join events for independent branches inside one call
-  cudaStream_t side_stream = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::map<std::string, ec3r::DevBuf> bufs;
   std::map<std::string, ec3r::GraphEntry> graphs;
   std::map<std::string, ec3r::Extension*> ext;

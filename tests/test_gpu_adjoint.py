@@ -352,9 +352,19 @@ def test_chain_adjoint_full_size_sampled_pairs(ctx):
     gS = torch.randn((ps.n_pairs, 13), generator=gen, dtype=torch.float64, device="cuda")
     gcost = torch.ones((ps.n_pairs,), dtype=torch.float64, device="cuda")
     S, st, _ = ctx.align_submaps(ps.xyz, ps.conf, ps.link_off, ps.src, ps.tgt, want_cost=True)
+    # the gradient buffers come from the caching allocator: hand it blocks full
+    # of NaN first, so that a frame the call fails to write would show
+    junk = [torch.full_like(ps.xyz, float("nan")), torch.full_like(ps.conf, float("nan"))]
+    del junk
     gx, gc = ctx.align_submaps_backward(ps.xyz, ps.conf, ps.link_off, ps.src, ps.tgt, gS, gcost,
                                         fwd_token=ctx.align_token())
     assert ctx.sync_status() == 0 and int((st != 0).sum()) == 0
+    # frames that no link references (three of every five) get exact zeros
+    ref = torch.zeros(gc.shape[0], dtype=torch.bool, device="cuda")
+    ref[ps.src.long()] = True
+    ref[ps.tgt.long()] = True
+    assert int((~ref).sum()) > 0
+    assert bool((gx[~ref] == 0).all()) and bool((gc[~ref] == 0).all())
     gS_h = gS.cpu().numpy()
     for k in (0, 99, 198):
         fa, fb = int(ps.src[k]), int(ps.tgt[k])
