@@ -459,22 +459,27 @@ __device__ __forceinline__ void scatter_iter(const float2* S, const float2* Sp, 
 
 // The frame zeroing that the scatter's CTAs share: the frame bank's pixels
 // (frame-major, n_frames x hw) split into equal runs of a multiple of four
-// pixels, one per CTA; a run's pixels of a frame that no scatter writes
+// pixels, one per CTA, and each run into ZS slices, one per trip of the
+// CTA's pixel loop; a slice's pixels of a frame that no scatter writes
 // directly (references 0 or > 1) are zeroed.  The stores drain while the
 // CTA computes: the scatter is bound by FP32 latency, not by HBM.
+constexpr int ZS = TILE / 2 / THREADS;  // trips of the scatter's pixel loop
+
 template <bool VEC>
-__device__ __forceinline__ void zero_share(int64_t n_frames, int64_t hw,
+__device__ __forceinline__ void zero_slice(int64_t n_frames, int64_t hw, int slice,
                                            const int32_t* __restrict__ refs,
                                            float* __restrict__ gxyz, float* __restrict__ gconf) {
   const int64_t U = n_frames * hw, G = gridDim.x;
   const int64_t per = (((U + G - 1) / G) + 3) & ~(int64_t)3;
-  int64_t u0 = (int64_t)blockIdx.x * per;
-  const int64_t u1 = min(U, u0 + per);
+  const int64_t r0 = min(U, (int64_t)blockIdx.x * per), r1 = min(U, r0 + per);
+  const int64_t sub = (((r1 - r0) / 4 + ZS - 1) / ZS) * 4;
+  int64_t u0 = min(r1, r0 + slice * sub);
+  const int64_t u1 = min(r1, u0 + sub);
   while (u0 < u1) {
     const int64_t f = u0 / hw;
     const int64_t fe = min(u1, (f + 1) * hw);
     if (refs[f] != 1) {
-      if (VEC) {  // hw and the run boundaries are multiples of 4 pixels
+      if (VEC) {  // hw and the slice boundaries are multiples of 4 pixels
         float4* x4 = reinterpret_cast<float4*>(gxyz + 3 * u0);
         float4* c4 = reinterpret_cast<float4*>(gconf + u0);
         const int64_t n4 = (fe - u0) / 4;
@@ -498,12 +503,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_adj_scatter(
     const AdjState* __restrict__ adj, const double* __restrict__ ckpt,
     const double* __restrict__ gM, int iters, float delta, int rule, float* __restrict__ lg,
     const int32_t* __restrict__ refs, float* __restrict__ gxyz, float* __restrict__ gconf) {
-  zero_share<VEC>(n_frames, hw, refs, gxyz, gconf);
   const int64_t t = blockIdx.x;
   const int64_t l = t / tpl;
   const int c = (int)(t - l * tpl);
   const int k = link_pair[l];
-  if (k < 0) return;  // pair rejected at set-up: its frames were not counted
+  if (k < 0) {  // pair rejected at set-up: its frames were not counted
+    for (int z = 0; z < ZS; ++z) zero_slice<VEC>(n_frames, hw, z, refs, gxyz, gconf);
+    return;
+  }
   const int64_t px0 = (int64_t)c * TILE;
   const int64_t rem = hw - px0;
   const int npx = rem < TILE ? (int)rem : TILE;
@@ -538,9 +545,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_adj_scatter(
   const float* Q = xyz + (ft * hw + px0) * 3;
   const float* CP = conf + fs * hw + px0;
   const float* CQ = conf + ft * hw + px0;
+  int zs = 0;  // zeroing slices done by this thread
   for (int g = threadIdx.x; g < TILE / 2; g += THREADS) {
     const int i0 = 2 * g;
     if (i0 >= npx) break;
+    zero_slice<VEC>(n_frames, hw, zs++, refs, gxyz, gconf);
     const int n = min(2, npx - i0);
     float pr[6], qr[6], cpr[2], cqr[2];
     if (VEC && n == 2) {
@@ -678,6 +687,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_adj_scatter(
       }
     }
   }
+  // the slices of the trips a ragged tile does not make
+  for (; zs < ZS; ++zs) zero_slice<VEC>(n_frames, hw, zs, refs, gxyz, gconf);
 }
 
 // References of every frame by the links of valid pairs.
@@ -886,7 +897,7 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
             n_links, n_frames, d_src, d_tgt, link_pair, refs, any_shared);
       });
     // The scatter writes the frames that exactly one link references; its CTAs
-    // also zero every other frame (zero_share: HBM stores beside FP32-bound
+    // also zero every other frame (zero_slice: HBM stores beside FP32-bound
     // work, where a separate zeroing kernel could not run beside the scatter,
     // whose two CTAs per SM hold the whole register file).
     if (n_tiles > 0) {
