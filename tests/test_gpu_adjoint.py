@@ -200,6 +200,28 @@ def test_adjoint_scalar_path_with_invalid_pixels(ctx):
     compare(gc, gc_or, ~kink, "dL/dconf", allow["c"])
 
 
+@pytest.mark.parametrize("variant", [0, 9, 12])
+def test_backward_after_each_forward_schedule(ctx, request, variant):
+    """The backward's reduction sweeps read the pixel weights that the forward's
+    first sweep stored: by the persistent launch (variants 0 and 9) or by the
+    separate-grid schedule (variant 12).  Each forward followed by the backward
+    on its token matches the oracle."""
+    ps = synth.make_pair(synth.SEED_BASE + 4, H=64, W=96, sigma=0.005)
+    gS, gx_or, gc_or, kink, allow = oracle_grads(ps, truth_list(ps))
+    d = cuda_set(ps)
+    ctx.set_align_variant(variant)
+    request.addfinalizer(lambda: ctx.set_align_variant(-1))
+    ctx.align_submaps(d.xyz, d.conf, d.link_off, d.src, d.tgt, want_cost=True)
+    assert ctx.last_align_variant()[0] == variant
+    gx, gc = ctx.align_submaps_backward(d.xyz, d.conf, d.link_off, d.src, d.tgt,
+                                        torch.tensor(gS, device="cuda"),
+                                        torch.ones(1, dtype=torch.float64, device="cuda"),
+                                        fwd_token=ctx.align_token())
+    assert ctx.sync_status() == 0
+    compare(gx.cpu().double().numpy(), gx_or, ~kink, "dL/dxyz", allow["x"])
+    compare(gc.cpu().double().numpy(), gc_or, ~kink, "dL/dconf", allow["c"])
+
+
 def test_adjoint_against_fp64_finite_differences_2k_subset(ctx):
     """2048-point pair; FP64 central differences of the oracle forward loss."""
     ps = synth.make_pair(synth.SEED_BASE + 8, H=32, W=64, sigma=0.005)
