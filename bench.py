@@ -1291,7 +1291,12 @@ def run_workload(args):
         assert ctx.sync_status() == 0 and int(cur) == kept
         out["fusion"] = {"points": npts, "kept": kept, "ms": fms,
                          "gbs_at_16B_plus_20B_per_kept":
-                             (16.0 * npts + 20.0 * kept) / (fms * 1e-3) / 1e9}
+                             (16.0 * npts + 20.0 * kept) / (fms * 1e-3) / 1e9,
+                         # the bytes moved: the count reads depth and confidence
+                         # and writes a 1-bit keep mask; the scatter reads the
+                         # depth and the mask and writes 20 B per kept point
+                         "gbs": ((12.25 * npts + 20.0 * kept) / (fms * 1e-3) / 1e9),
+                         "bytes_per_point_read": 12.25}
     elif args.workload == "loops32k":
         # global loop retrieval over 32,768 keyframe embeddings of 1,024 dimensions
         # (two laps of a 1.6 km route, a keyframe every 0.1 m), every 2nd keyframe

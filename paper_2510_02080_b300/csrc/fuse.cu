@@ -259,12 +259,15 @@ __device__ __forceinline__ bool keepz(float d, float c, float thr) {
   return d > 0.f && d <= FLT_MAX && c > thr;
 }
 
+// Kept points per tile and the tile's keep mask, in k_fuse_count's layout
+// (an unusable camera keeps nothing).
 template <bool VEC>
 __global__ void __launch_bounds__(THREADS) k_fusez_count(const float* __restrict__ depth,
                                                          const float* __restrict__ conf,
                                                          const ec3r_camera* __restrict__ cams,
                                                          int64_t hw, int tpf, float thr,
-                                                         int32_t* __restrict__ tile_count) {
+                                                         int32_t* __restrict__ tile_count,
+                                                         uint32_t* __restrict__ mask) {
   const int64_t t = blockIdx.x;
   const int64_t fr = t / tpf;
   const int c = (int)(t - fr * tpf);
@@ -272,20 +275,34 @@ __global__ void __launch_bounds__(THREADS) k_fusez_count(const float* __restrict
   const int64_t rem = hw - (int64_t)c * TILE;
   const int npx = rem < TILE ? (int)rem : TILE;
   const bool usable = cam_usable(cams[fr]);
+  const int lane = threadIdx.x & 31;
   int cnt = 0;
-  if (usable) {
-    for (int i0 = 4 * threadIdx.x; i0 < npx; i0 += 4 * THREADS) {
+  for (int r0 = 0; r0 < npx; r0 += 4 * THREADS) {  // every lane takes every round
+    const int i0 = r0 + 4 * threadIdx.x;
+    unsigned nib = 0;
+    if (usable) {
       if (VEC && i0 + 4 <= npx) {
         const float4 d = __ldcs(reinterpret_cast<const float4*>(depth + base + i0));
         const float4 v = __ldcs(reinterpret_cast<const float4*>(conf + base + i0));
-        cnt += keepz(d.x, v.x, thr) + keepz(d.y, v.y, thr) + keepz(d.z, v.z, thr) +
-               keepz(d.w, v.w, thr);
+        nib = (unsigned)keepz(d.x, v.x, thr) | (unsigned)keepz(d.y, v.y, thr) << 1 |
+              (unsigned)keepz(d.z, v.z, thr) << 2 | (unsigned)keepz(d.w, v.w, thr) << 3;
       } else {
-        for (int j = i0; j < min(i0 + 4, npx); ++j)
-          cnt += keepz(depth[base + j], conf[base + j], thr);
+        for (int j = 0; j < 4; ++j)
+          if (i0 + j < npx && keepz(depth[base + i0 + j], conf[base + i0 + j], thr))
+            nib |= 1u << j;
       }
     }
+    cnt += __popc(nib);
+    unsigned w = nib << (4 * (lane & 7));
+    w |= __shfl_xor_sync(0xffffffffu, w, 1);
+    w |= __shfl_xor_sync(0xffffffffu, w, 2);
+    w |= __shfl_xor_sync(0xffffffffu, w, 4);
+    if ((lane & 7) == 0) mask[t * MASK_WORDS + (r0 >> 5) + (threadIdx.x >> 3)] = w;
   }
+  // words past the last round of a short tile
+  for (int w = ((npx + 4 * THREADS - 1) / (4 * THREADS)) * (4 * THREADS / 32) + threadIdx.x;
+       w < MASK_WORDS; w += THREADS)
+    mask[t * MASK_WORDS + w] = 0u;
   cnt = __reduce_add_sync(0xffffffffu, cnt);
   __shared__ int red[THREADS / 32];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
@@ -302,9 +319,9 @@ __global__ void __launch_bounds__(THREADS) k_fusez_count(const float* __restrict
 // with the camera pose, formed in FP64 and rounded to FP32 once per CTA.
 template <bool VEC>
 __global__ void __launch_bounds__(THREADS) k_fusez_scatter(
-    const float* __restrict__ depth, const float* __restrict__ conf,
+    const float* __restrict__ depth, const uint32_t* __restrict__ mask,
     const ec3r_camera* __restrict__ cams, int W, int64_t hw, int tpf, int frames,
-    const ec3r_sim3* __restrict__ poses, float thr, int64_t index_base,
+    const ec3r_sim3* __restrict__ poses, int64_t index_base,
     const int64_t* __restrict__ tile_off, float* __restrict__ out_xyz,
     int64_t* __restrict__ out_idx, int64_t capacity, unsigned* flags) {
   const int64_t t = blockIdx.x;
@@ -315,7 +332,6 @@ __global__ void __launch_bounds__(THREADS) k_fusez_scatter(
   const int64_t rem = hw - tile0;
   const int npx = rem < TILE ? (int)rem : TILE;
   __shared__ float A[16];
-  __shared__ int usable;
   __shared__ int wcnt[THREADS / 32];
   __shared__ float sx[3 * ROUND];
   __shared__ int64_t sidx[ROUND];
@@ -332,45 +348,39 @@ __global__ void __launch_bounds__(THREADS) k_fusez_scatter(
     A[13] = 1.f / cam.fy;
     A[14] = cam.cx;
     A[15] = cam.cy;
-    usable = cam_usable(cam);
   }
   __syncthreads();
   const float a00 = A[0], a01 = A[1], a02 = A[2], a03 = A[3];
   const float a10 = A[4], a11 = A[5], a12 = A[6], a13 = A[7];
   const float a20 = A[8], a21 = A[9], a22 = A[10], a23 = A[11];
   const float ifx = A[12], ify = A[13], cx = A[14], cy = A[15];
-  const bool ok = usable != 0;
   int64_t pos = tile_off[t];
   bool overflow = false;
 
-  float cf[4], dd[4];
+  // the keep decision from the count pass's mask (1 bit per point instead of
+  // a 4-byte confidence); the depth is read for the kept points' coordinates
+  const uint32_t* tmask = mask + t * MASK_WORDS;
+  unsigned nb;
+  float dd[4];
   auto load = [&](int r0) {
     const int i0 = r0 + 4 * threadIdx.x;
+    nb = (tmask[(r0 >> 5) + (threadIdx.x >> 3)] >> (4 * (threadIdx.x & 7))) & 0xFu;
     if (VEC && i0 + 4 <= npx) {
-      const float4 v = __ldcs(reinterpret_cast<const float4*>(conf + base + i0));
       const float4 d = __ldcs(reinterpret_cast<const float4*>(depth + base + i0));
-      cf[0] = v.x; cf[1] = v.y; cf[2] = v.z; cf[3] = v.w;
       dd[0] = d.x; dd[1] = d.y; dd[2] = d.z; dd[3] = d.w;
     } else {
-      for (int j = 0; j < 4; ++j) {
-        const bool in = i0 + j < npx;
-        cf[j] = in ? conf[base + i0 + j] : -FLT_MAX;
-        dd[j] = in ? depth[base + i0 + j] : 0.f;
-      }
+      for (int j = 0; j < 4; ++j) dd[j] = i0 + j < npx ? depth[base + i0 + j] : 0.f;
     }
   };
   if (npx > 0) load(0);
   for (int r0 = 0; r0 < npx; r0 += ROUND) {
     const int i0 = r0 + 4 * threadIdx.x;
-    float ccf[4], cd[4];
-    for (int j = 0; j < 4; ++j) {
-      ccf[j] = cf[j];
-      cd[j] = dd[j];
-    }
+    float cd[4];
+    const unsigned cnb = nb;
+    for (int j = 0; j < 4; ++j) cd[j] = dd[j];
     if (r0 + ROUND < npx) load(r0 + ROUND);  // next round in flight
     unsigned km = 0;
-    for (int j = 0; j < 4; ++j)
-      km |= (ok && i0 + j < npx && keepz(cd[j], ccf[j], thr)) ? (1u << j) : 0u;
+    for (int j = 0; j < 4; ++j) km |= (i0 + j < npx && ((cnb >> j) & 1u)) ? (1u << j) : 0u;
     const unsigned pix0 = (unsigned)(tile0 + i0);  // < 2^31
     const unsigned v0 = pix0 / (unsigned)W;
     const unsigned u0 = pix0 - v0 * (unsigned)W;
@@ -542,33 +552,38 @@ extern "C" ec3r_status ec3r_fuse_points_depth(ec3r_ctx* ctx, int n_submaps, int 
     return set_error(ctx, EC3R_ERR_INVALID_ARG, "problem too large for one call");
   EC3R_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  void *p_cnt, *p_off;
+  void *p_cnt, *p_off, *p_mask;
   ec3r_status st;
   if ((st = ensure_buf(ctx, "fuse.count", sizeof(int32_t) * (size_t)n_tiles, s, &p_cnt))) return st;
   if ((st = ensure_buf(ctx, "fuse.off", sizeof(int64_t) * (size_t)n_tiles, s, &p_off))) return st;
-  int32_t* cnt = (int32_t*)p_cnt;
-  int64_t* off = (int64_t*)p_off;
+  if ((st = ensure_buf(ctx, "fuse.mask", sizeof(uint32_t) * MASK_WORDS * (size_t)n_tiles, s,
+                       &p_mask)))
+    return st;
+  // (buffers that grew dropped the graphs holding older ones; re-read them all)
+  int32_t* cnt = (int32_t*)ctx->bufs["fuse.count"].ptr;
+  int64_t* off = (int64_t*)ctx->bufs["fuse.off"].ptr;
+  uint32_t* mask = (uint32_t*)ctx->bufs["fuse.mask"].ptr;
   const bool vec = (hw % 4 == 0) && ((uintptr_t)d_depth % 16 == 0) &&
                    ((uintptr_t)d_conf % 16 == 0);
   const dim3 grid((unsigned)n_tiles);
   traced(ctx, s, "fusez_count", [&] {
     if (vec)
       k_fusez_count<true><<<grid, THREADS, 0, s>>>(d_depth, d_conf, d_cams, hw, (int)tpf,
-                                                   conf_threshold, cnt);
+                                                   conf_threshold, cnt, mask);
     else
       k_fusez_count<false><<<grid, THREADS, 0, s>>>(d_depth, d_conf, d_cams, hw, (int)tpf,
-                                                    conf_threshold, cnt);
+                                                    conf_threshold, cnt, mask);
   });
   traced(ctx, s, "fuse_scan", [&] { k_fuse_scan<<<1, 1024, 0, s>>>(cnt, n_tiles, off, d_cursor); });
   traced(ctx, s, "fusez_scatter", [&] {
     if (vec)
       k_fusez_scatter<true><<<grid, THREADS, 0, s>>>(
-          d_depth, d_conf, d_cams, W, hw, (int)tpf, frames, d_poses, conf_threshold, index_base,
-          off, d_out_xyz, d_out_idx, capacity, ctx->d_flags);
+          d_depth, mask, d_cams, W, hw, (int)tpf, frames, d_poses, index_base, off, d_out_xyz,
+          d_out_idx, capacity, ctx->d_flags);
     else
       k_fusez_scatter<false><<<grid, THREADS, 0, s>>>(
-          d_depth, d_conf, d_cams, W, hw, (int)tpf, frames, d_poses, conf_threshold, index_base,
-          off, d_out_xyz, d_out_idx, capacity, ctx->d_flags);
+          d_depth, mask, d_cams, W, hw, (int)tpf, frames, d_poses, index_base, off, d_out_xyz,
+          d_out_idx, capacity, ctx->d_flags);
   });
   EC3R_CUDA_TRY(ctx, cudaGetLastError());
   return EC3R_OK;
