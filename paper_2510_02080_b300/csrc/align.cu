@@ -405,7 +405,7 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
   // This call overwrites the workspace that an earlier token refers to.
   ctx->align_token = 0;
 
-  // set-up, then every sweep and solve in one persistent launch
+  // set-up, then every sweep and solve: the persistent launches (or separate grids)
   auto enqueue = [&](cudaStream_t cs, int v) -> ec3r_status {
     EC3R_CUDA_TRY(ctx, cudaMemsetAsync(link_pair, 0xff, sizeof(int32_t) * (size_t)(n_links + 1),
                                        cs));
