@@ -51,17 +51,36 @@ struct RedParams {
   int pad[3];
 };
 
-__device__ inline void write_red_params(RedParams& P, const double* ckb, int k_it, bool cur,
+// The checkpointed estimates that write_red_params needs, loaded ahead so that
+// their latency overlaps the solve's arithmetic: "prev" = estimate k_it - 1,
+// "cur" = estimate k_it (A = s R, b).
+struct RedCk {
+  double Ap[9], bp[3], Ac[9], bc[3];
+};
+
+__device__ inline void load_red_ck(RedCk& c, const double* ckb, int k_it, bool cur) {
+  const bool first = k_it == 1;
+  for (int i = 0; i < 9; ++i) {
+    c.Ap[i] = first ? ((i % 4 == 0) ? 1.0 : 0.0) : ckb[(k_it - 2) * CKPT + CK_A + i];
+    c.Ac[i] = cur ? ckb[(k_it - 1) * CKPT + CK_A + i] : 0.0;
+  }
+  for (int i = 0; i < 3; ++i) {
+    c.bp[i] = first ? 0.0 : ckb[(k_it - 2) * CKPT + CK_B + i];
+    c.bc[i] = cur ? ckb[(k_it - 1) * CKPT + CK_B + i] : 0.0;
+  }
+}
+
+__device__ inline void write_red_params(RedParams& P, const RedCk& c, int k_it,
                                         const double* G, const AdjState& a, const PairState& S,
                                         float delta) {
   const bool first = k_it == 1;
   for (int i = 0; i < 9; ++i) {
-    P.Ap[i] = first ? ((i % 4 == 0) ? 1.f : 0.f) : (float)ckb[(k_it - 2) * CKPT + CK_A + i];
-    P.Ac[i] = cur ? (float)ckb[(k_it - 1) * CKPT + CK_A + i] : 0.f;
+    P.Ap[i] = (float)c.Ap[i];
+    P.Ac[i] = (float)c.Ac[i];
   }
   for (int i = 0; i < 3; ++i) {
-    P.bp[i] = first ? 0.f : (float)ckb[(k_it - 2) * CKPT + CK_B + i];
-    P.bc[i] = cur ? (float)ckb[(k_it - 1) * CKPT + CK_B + i] : 0.f;
+    P.bp[i] = (float)c.bp[i];
+    P.bc[i] = (float)c.bc[i];
     P.pp[i] = S.piv_p[i];
     P.pq[i] = S.piv_q[i];
   }
@@ -249,8 +268,7 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
   const int lane = threadIdx.x & 31;
   __shared__ double red[8][NRED];
   if (warp >= n_pairs) return;
-  AdjState& a = adj[warp];
-  if (!a.active) return;
+  if (!adj[warp].active) return;
   const int wib = threadIdx.x >> 5;
   const double* ck = ckpt + ((size_t)warp * iters + (j - 1)) * CKPT;
   if (have_partials && lane < NRED) {
@@ -263,8 +281,19 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
   }
   __syncwarp();
   if (lane != 0) return;
-  double s, R[9];
+  // Every checkpoint value and the pair's adjoint state first, so that their
+  // loads are in flight together; the three reciprocals 1/(d_a + d_b) of the
+  // polar factor's derivative start at once, off the dependent chain.
+  double s, R[9], M[NMOM], d[3], V[9];
   ck_sR(ck, &s, R);
+  for (int m = 0; m < NMOM; ++m) M[m] = ck[CK_MOM + m];
+  for (int i = 0; i < 3; ++i) d[i] = ck[CK_D + i];
+  for (int i = 0; i < 9; ++i) V[i] = ck[CK_V + i];
+  RedCk rc;
+  if (j >= 2) load_red_ck(rc, ckpt + (size_t)warp * iters * CKPT, j, j == iters);
+  AdjState& ag = adj[warp];
+  AdjState a = ag;
+  const double idd[3] = {1.0 / (d[0] + d[1]), 1.0 / (d[0] + d[2]), 1.0 / (d[1] + d[2])};
   if (have_partials) {
     const double f = scale_by_gJ ? 2.0 * a.gJ : 1.0;
     // dL/dA = f X, dL/db = f y; A = s R -> dL/ds = <dL/dA, R>, dL/dR = s dL/dA
@@ -278,7 +307,6 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
     for (int i = 0; i < 3; ++i) a.gb[i] += f * red[wib][9 + i];
   }
   // forward quantities of solve j from its moments
-  const double* M = ck + CK_MOM;
   const double W = M[M_W], iw = 1.0 / W;
   const double mp[3] = {M[M_SP] * iw, M[M_SP + 1] * iw, M[M_SP + 2] * iw};
   const double mq[3] = {M[M_SQ] * iw, M[M_SQ + 1] * iw, M[M_SQ + 2] * iw};
@@ -288,9 +316,6 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
   const double var = M[M_PP] * iw - (mp[0] * mp[0] + mp[1] * mp[1] + mp[2] * mp[2]);
   // the forward solve's polar factor R = U' V^T of Sig and its d, V
   const double* Rr = R;
-  double d[3], V[9];
-  for (int i = 0; i < 3; ++i) d[i] = ck[CK_D + i];
-  for (int i = 0; i < 9; ++i) V[i] = ck[CK_V + i];
   double tau = 0.0;
   for (int i = 0; i < 9; ++i) tau += Rr[i] * Sig[i];
   // b = mq - s R mp
@@ -307,8 +332,9 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
   for (int k = 0; k < 3; ++k)
     gmp[k] = -s * (Rr[k] * a.gb[0] + Rr[3 + k] * a.gb[1] + Rr[6 + k] * a.gb[2]);
   // s = tau / var, d tau / dSig = R
-  const double gtau = gs / var;
-  const double gvar = -gs * tau / (var * var);
+  const double ivar = 1.0 / var;
+  const double gtau = gs * ivar;
+  const double gvar = -gs * tau * ivar * ivar;
   double gSig[9];
   for (int i = 0; i < 9; ++i) gSig[i] = gtau * Rr[i];
   // R = U' V^T, U' = R V: dL/dSig += U' K V^T, K_ab = (G'_ab - G'_ba) / (d_a + d_b)
@@ -324,7 +350,7 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
       G2[3 * r + c] = G1[3 * r] * V[c] + G1[3 * r + 1] * V[3 + c] + G1[3 * r + 2] * V[6 + c];
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c)
-      Kx[3 * r + c] = r == c ? 0.0 : (G2[3 * r + c] - G2[3 * c + r]) / (d[r] + d[c]);
+      Kx[3 * r + c] = r == c ? 0.0 : (G2[3 * r + c] - G2[3 * c + r]) * idd[r + c - 1];
   for (int r = 0; r < 3; ++r)  // G1 = U K
     for (int c = 0; c < 3; ++c)
       G1[3 * r + c] = U[3 * r] * Kx[c] + U[3 * r + 1] * Kx[3 + c] + U[3 * r + 2] * Kx[6 + c];
@@ -356,13 +382,11 @@ __global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j
   // parameters of the Huber sweep of iteration j (it rebuilds the adjoint of
   // estimate j-1); iteration 1 starts from the identity with unit weights and
   // has none
-  if (j >= 2)
-    write_red_params(rp[warp], ckpt + (size_t)warp * iters * CKPT, j, j == iters, out, a,
-                     st[warp], delta);
+  if (j >= 2) write_red_params(rp[warp], rc, j, out, a, st[warp], delta);
   // the adjoint of estimate j-1 is rebuilt by the next Huber sweep
-  a.gs = 0.0;
-  for (int i = 0; i < 9; ++i) a.gR[i] = 0.0;
-  for (int i = 0; i < 3; ++i) a.gb[i] = 0.0;
+  ag.gs = 0.0;
+  for (int i = 0; i < 9; ++i) ag.gR[i] = 0.0;
+  for (int i = 0; i < 3; ++i) ag.gb[i] = 0.0;
 }
 
 // Per-correspondence gradients, all iterations in one pass (link layout,
