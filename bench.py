@@ -666,10 +666,10 @@ def run_ours(args):
     # (which needs the registered edges) runs on a second, high-priority
     # stream while the adjoint runs on the main one; the latency-bound
     # pose-graph launches then fill the gaps of the HBM-bound adjoint sweeps.
-    # The fusion's keep counts (no pose needed) run on the second stream
-    # before the pose graph; its scan and scatter (HBM-bound, they need the
-    # corrected poses) follow the adjoint on the main stream once the pose
-    # graph is done.
+    # Beside the adjoint the pose graph is the longer branch, so the fusion's
+    # keep counts (no pose needed) follow the adjoint on the main stream; its
+    # scan and scatter (HBM-bound, they need the corrected poses) follow them
+    # once the pose graph is done.
     side = torch.cuda.Stream(device=dev, priority=-1)
     tile_counts = torch.empty((M * ((n_frames // M * hw + 8191) // 8192),), dtype=torch.int32,
                               device=dev)
@@ -684,8 +684,6 @@ def run_ours(args):
                           want_cost=True, cost=cost, stream=main)
         ev_reg.record(main)
         sec.wait_event(ev_reg)
-        # the fusion's keep counts need no pose: beside the pose graph
-        ctx.fuse_count(conf_in.view(M, -1), tile_counts, keep_mask, stream=sec)
         ctx.pose_graph_correct(poses, ei, ej, S, iters=PG_ITERS, chi2=chi2, stream=sec)
         ev_side.record(sec)
         if not args.no_adjoint:
@@ -696,6 +694,8 @@ def run_ours(args):
                 int(ps.src.numel()), ec3r._ptr(ps.link_off), ec3r._ptr(ps.src),
                 ec3r._ptr(ps.tgt), None, ec3r.C.byref(o), ctx.align_token(), ec3r._ptr(gS),
                 ec3r._ptr(gcost), ec3r._ptr(gxyz), ec3r._ptr(gconf), ec3r._stream(main)))
+        # the fusion's keep counts need no pose: in the adjoint branch's slack
+        ctx.fuse_count(conf_in.view(M, -1), tile_counts, keep_mask, stream=main)
         main.wait_event(ev_side)
         c = cursors[ci[0] % n_cursor:ci[0] % n_cursor + 1]
         ci[0] += 1

@@ -51,46 +51,6 @@ struct RedParams {
   int pad[3];
 };
 
-// The checkpointed estimates that write_red_params needs, loaded ahead so that
-// their latency overlaps the solve's arithmetic: "prev" = estimate k_it - 1,
-// "cur" = estimate k_it (A = s R, b).
-struct RedCk {
-  double Ap[9], bp[3], Ac[9], bc[3];
-};
-
-__device__ inline void load_red_ck(RedCk& c, const double* ckb, int k_it, bool cur) {
-  const bool first = k_it == 1;
-  for (int i = 0; i < 9; ++i) {
-    c.Ap[i] = first ? ((i % 4 == 0) ? 1.0 : 0.0) : ckb[(k_it - 2) * CKPT + CK_A + i];
-    c.Ac[i] = cur ? ckb[(k_it - 1) * CKPT + CK_A + i] : 0.0;
-  }
-  for (int i = 0; i < 3; ++i) {
-    c.bp[i] = first ? 0.0 : ckb[(k_it - 2) * CKPT + CK_B + i];
-    c.bc[i] = cur ? ckb[(k_it - 1) * CKPT + CK_B + i] : 0.0;
-  }
-}
-
-__device__ inline void write_red_params(RedParams& P, const RedCk& c, int k_it,
-                                        const double* G, const AdjState& a, const PairState& S,
-                                        float delta) {
-  const bool first = k_it == 1;
-  for (int i = 0; i < 9; ++i) {
-    P.Ap[i] = (float)c.Ap[i];
-    P.Ac[i] = (float)c.Ac[i];
-  }
-  for (int i = 0; i < 3; ++i) {
-    P.bp[i] = (float)c.bp[i];
-    P.bc[i] = (float)c.bc[i];
-    P.pp[i] = S.piv_p[i];
-    P.pq[i] = S.piv_q[i];
-  }
-  for (int i = 0; i < NGM; ++i) P.G[i] = G ? (float)G[i] : 0.f;
-  P.gJ = (float)a.gJ;
-  P.gOm = (float)a.gOm;
-  P.cmin = S.cmin;
-  P.dl = first ? FLT_MAX : delta;
-}
-
 __device__ inline void ck_sR(const double* ck, double* s, double* R) {
   *s = ck[CK_S];
   for (int i = 0; i < 9; ++i) R[i] = ck[CK_R + i];
@@ -250,143 +210,189 @@ __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
   }
 }
 
-// One warp per pair.  First folds the reduced sums (scaled by `scale`: 2 dL/dJ
-// for the cost term, 1 for a Huber sweep) into the adjoint of estimate j as
-// dL/dA and dL/db, then differentiates solve j and stores the gradient of its
-// moments in gM[j].
-__global__ void __launch_bounds__(256) k_adj_solve(int n_pairs, int iters, int j,
-                                                   const int32_t* __restrict__ link_off, int tpl,
-                                                   const double* __restrict__ partials,
-                                                   int have_partials, int scale_by_gJ,
-                                                   const double* __restrict__ ckpt,
-                                                   AdjState* __restrict__ adj,
-                                                   double* __restrict__ gM,
-                                                   const PairState* __restrict__ st,
-                                                   float delta, RedParams* __restrict__ rp,
-                                                   const double* __restrict__ pair_sums) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  __shared__ double red[8][NRED];
-  if (warp >= n_pairs) return;
-  if (!adj[warp].active) return;
-  const int wib = threadIdx.x >> 5;
-  const double* ck = ckpt + ((size_t)warp * iters + (j - 1)) * CKPT;
+// One warp per pair (one warp per CTA).  First folds the reduced sums (scaled
+// by `scale`: 2 dL/dJ for the cost term, 1 for a Huber sweep) into the adjoint
+// of estimate j as dL/dA and dL/db, then differentiates solve j and stores the
+// gradient of its moments in gM[j].
+//
+// The FP64 pipe costs about the same per warp instruction whatever the number
+// of active lanes, so the 3x3 algebra runs element-parallel: lane e < 9 (and
+// its copy e + 16) owns element (e / 3, e % 3) of each matrix, the matrices
+// pass between products through shared memory, and 9-term sums are
+// fixed-order butterflies over the 16-lane half-warp (lanes 9..15 add zeros).
+// Scalars every lane needs are computed redundantly by all lanes, at the cost
+// of one instruction each.
+__device__ __forceinline__ double half_warp_sum(double x) {
+  x += __shfl_xor_sync(0xffffffffu, x, 8);
+  x += __shfl_xor_sync(0xffffffffu, x, 4);
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  return x;
+}
+
+__device__ __forceinline__ double pick3(int i, double a0, double a1, double a2) {
+  return i == 0 ? a0 : (i == 1 ? a1 : a2);
+}
+
+static_assert(sizeof(AdjState) == 16 * sizeof(double), "AdjState is 15 doubles + 2 ints");
+enum { AG_S = 0, AG_R = 1, AG_B = 10, AG_J = 13, AG_OM = 14, AG_N = 15 };
+
+__global__ void __launch_bounds__(32) k_adj_solve(int n_pairs, int iters, int j,
+                                                  const int32_t* __restrict__ link_off, int tpl,
+                                                  const double* __restrict__ partials,
+                                                  int have_partials, int scale_by_gJ,
+                                                  const double* __restrict__ ckpt,
+                                                  AdjState* __restrict__ adj,
+                                                  double* __restrict__ gM,
+                                                  const PairState* __restrict__ st,
+                                                  float delta, RedParams* __restrict__ rp,
+                                                  const double* __restrict__ pair_sums) {
+  const int k = blockIdx.x;
+  const int lane = threadIdx.x;
+  if (k >= n_pairs) return;
+  if (!adj[k].active) return;
+  __shared__ double ck[CKPT];   // checkpoint of solve j: moments, A, b, s, R, d, V
+  __shared__ double ckp[12];    // A, b of estimate j - 1 (the next sweep's weights)
+  __shared__ double ag[AG_N];   // adjoint state: gs, gR, gb, gJ, gOm
+  __shared__ double red[NRED];  // reduced sums of the sweep that ran last
+  __shared__ double X[9], Y[9], Z[9];
+  const double* ckb = ckpt + (size_t)k * iters * CKPT;
+  for (int i = lane; i < CKPT; i += 32) ck[i] = ckb[(size_t)(j - 1) * CKPT + i];
+  if (j >= 2 && lane < 12) ckp[lane] = ckb[(size_t)(j - 2) * CKPT + CK_A + lane];
+  double* agd = reinterpret_cast<double*>(adj + k);
+  if (lane < AG_N) ag[lane] = agd[lane];
   if (have_partials && lane < NRED) {
     if (pair_sums) {  // summed per pair already (the forward's last sweep)
-      red[wib][lane] = pair_sums[(size_t)warp * CS_STRIDE + lane];
+      red[lane] = pair_sums[(size_t)k * CS_STRIDE + lane];
     } else {
-      const int64_t t0 = (int64_t)link_off[warp] * tpl, t1 = (int64_t)link_off[warp + 1] * tpl;
-      red[wib][lane] = tile_sum<NRED>(partials, t0, t1, lane);
+      const int64_t t0 = (int64_t)link_off[k] * tpl, t1 = (int64_t)link_off[k + 1] * tpl;
+      red[lane] = tile_sum<NRED>(partials, t0, t1, lane);
     }
   }
   __syncwarp();
-  if (lane != 0) return;
-  // Every checkpoint value and the pair's adjoint state first, so that their
-  // loads are in flight together; the three reciprocals 1/(d_a + d_b) of the
-  // polar factor's derivative start at once, off the dependent chain.
-  double s, R[9], M[NMOM], d[3], V[9];
-  ck_sR(ck, &s, R);
-  for (int m = 0; m < NMOM; ++m) M[m] = ck[CK_MOM + m];
-  for (int i = 0; i < 3; ++i) d[i] = ck[CK_D + i];
-  for (int i = 0; i < 9; ++i) V[i] = ck[CK_V + i];
-  RedCk rc;
-  if (j >= 2) load_red_ck(rc, ckpt + (size_t)warp * iters * CKPT, j, j == iters);
-  AdjState& ag = adj[warp];
-  AdjState a = ag;
-  const double idd[3] = {1.0 / (d[0] + d[1]), 1.0 / (d[0] + d[2]), 1.0 / (d[1] + d[2])};
+  const int e = lane & 15;
+  const bool own = e < 9;
+  const int r = own ? e / 3 : 0, c = own ? e % 3 : 0;
+  const double* M = ck + CK_MOM;
+  const double* R = ck + CK_R;
+  const double* V = ck + CK_V;
+  const double s = ck[CK_S];
+  const double W = M[M_W], iw = 1.0 / W;
+  // this lane's reciprocal of the polar factor's derivative: 1/(d_r + d_c)
+  const int da = r < c ? r : c, db = r < c ? c : r;
+  const double idd = 1.0 / (ck[CK_D + (own && r != c ? da : 0)] +
+                            ck[CK_D + (own && r != c ? db : 1)]);
+  const double Re = R[3 * r + c];
+  // dL/dA = f X, dL/db = f y; A = s R -> dL/ds = <dL/dA, R>, dL/dR = s dL/dA
+  double gs = ag[AG_S];
+  double gRe = own ? ag[AG_R + e] : 0.0;
+  double gb0 = ag[AG_B], gb1 = ag[AG_B + 1], gb2 = ag[AG_B + 2];
   if (have_partials) {
-    const double f = scale_by_gJ ? 2.0 * a.gJ : 1.0;
-    // dL/dA = f X, dL/db = f y; A = s R -> dL/ds = <dL/dA, R>, dL/dR = s dL/dA
-    double gs = 0.0;
-    for (int i = 0; i < 9; ++i) {
-      const double gA = f * red[wib][i];
-      gs += gA * R[i];
-      a.gR[i] += s * gA;
-    }
-    a.gs += gs;
-    for (int i = 0; i < 3; ++i) a.gb[i] += f * red[wib][9 + i];
+    const double f = scale_by_gJ ? 2.0 * ag[AG_J] : 1.0;
+    const double gA = f * red[3 * r + c];
+    gRe = own ? fma(s, gA, gRe) : 0.0;
+    gb0 = fma(f, red[9], gb0);
+    gb1 = fma(f, red[10], gb1);
+    gb2 = fma(f, red[11], gb2);
+    gs += half_warp_sum(own ? gA * Re : 0.0);
   }
   // forward quantities of solve j from its moments
-  const double W = M[M_W], iw = 1.0 / W;
-  const double mp[3] = {M[M_SP] * iw, M[M_SP + 1] * iw, M[M_SP + 2] * iw};
-  const double mq[3] = {M[M_SQ] * iw, M[M_SQ + 1] * iw, M[M_SQ + 2] * iw};
-  double Sig[9];
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 3; ++k) Sig[3 * i + k] = M[M_QP + 3 * i + k] * iw - mq[i] * mp[k];
-  const double var = M[M_PP] * iw - (mp[0] * mp[0] + mp[1] * mp[1] + mp[2] * mp[2]);
-  // the forward solve's polar factor R = U' V^T of Sig and its d, V
-  const double* Rr = R;
-  double tau = 0.0;
-  for (int i = 0; i < 9; ++i) tau += Rr[i] * Sig[i];
-  // b = mq - s R mp
-  double gmq[3], gmp[3], gs = a.gs, gR[9];
-  double Rmp[3];
-  for (int i = 0; i < 3; ++i)
-    Rmp[i] = Rr[3 * i] * mp[0] + Rr[3 * i + 1] * mp[1] + Rr[3 * i + 2] * mp[2];
-  for (int i = 0; i < 3; ++i) {
-    gmq[i] = a.gb[i];
-    gs -= a.gb[i] * Rmp[i];
-  }
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 3; ++k) gR[3 * i + k] = a.gR[3 * i + k] - s * a.gb[i] * mp[k];
-  for (int k = 0; k < 3; ++k)
-    gmp[k] = -s * (Rr[k] * a.gb[0] + Rr[3 + k] * a.gb[1] + Rr[6 + k] * a.gb[2]);
+  const double mp0 = M[M_SP] * iw, mp1 = M[M_SP + 1] * iw, mp2 = M[M_SP + 2] * iw;
+  const double mq0 = M[M_SQ] * iw, mq1 = M[M_SQ + 1] * iw, mq2 = M[M_SQ + 2] * iw;
+  const double mpc = pick3(c, mp0, mp1, mp2), mqr = pick3(r, mq0, mq1, mq2);
+  const double gbr = pick3(r, gb0, gb1, gb2);
+  const double Sige = fma(-mqr, mpc, M[M_QP + 3 * r + c] * iw);
+  const double var = M[M_PP] * iw - (mp0 * mp0 + mp1 * mp1 + mp2 * mp2);
+  // tau = tr(R^T Sig), the scale's numerator
+  const double tau = half_warp_sum(own ? Re * Sige : 0.0);
+  // b = mq - s R mp: dL/ds -= gb^T R mp, dL/dR -= s gb mp^T,
+  // dL/dmp = -s R^T gb, dL/dmq = gb
+  gs -= half_warp_sum(own ? gbr * Re * mpc : 0.0);
+  const double gR2 = own ? gRe - s * gbr * mpc : 0.0;
   // s = tau / var, d tau / dSig = R
   const double ivar = 1.0 / var;
   const double gtau = gs * ivar;
   const double gvar = -gs * tau * ivar * ivar;
-  double gSig[9];
-  for (int i = 0; i < 9; ++i) gSig[i] = gtau * Rr[i];
+  double gSig = gtau * Re;
   // R = U' V^T, U' = R V: dL/dSig += U' K V^T, K_ab = (G'_ab - G'_ba) / (d_a + d_b)
-  double U[9], G1[9], G2[9], Kx[9];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c)
-      U[3 * r + c] = Rr[3 * r] * V[c] + Rr[3 * r + 1] * V[3 + c] + Rr[3 * r + 2] * V[6 + c];
-  for (int r = 0; r < 3; ++r)  // G1 = U^T gR
-    for (int c = 0; c < 3; ++c)
-      G1[3 * r + c] = U[r] * gR[c] + U[3 + r] * gR[3 + c] + U[6 + r] * gR[6 + c];
-  for (int r = 0; r < 3; ++r)  // G2 = G1 V
-    for (int c = 0; c < 3; ++c)
-      G2[3 * r + c] = G1[3 * r] * V[c] + G1[3 * r + 1] * V[3 + c] + G1[3 * r + 2] * V[6 + c];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c)
-      Kx[3 * r + c] = r == c ? 0.0 : (G2[3 * r + c] - G2[3 * c + r]) * idd[r + c - 1];
-  for (int r = 0; r < 3; ++r)  // G1 = U K
-    for (int c = 0; c < 3; ++c)
-      G1[3 * r + c] = U[3 * r] * Kx[c] + U[3 * r + 1] * Kx[3 + c] + U[3 * r + 2] * Kx[6 + c];
-  for (int r = 0; r < 3; ++r)  // += G1 V^T
-    for (int c = 0; c < 3; ++c)
-      gSig[3 * r + c] += G1[3 * r] * V[3 * c] + G1[3 * r + 1] * V[3 * c + 1] +
-                         G1[3 * r + 2] * V[3 * c + 2];
-  // Sig = Sqp/W - mq mp^T, var = Spp/W - |mp|^2, mp = Sp/W, mq = Sq/W
-  double* out = gM + ((size_t)warp * iters + (j - 1)) * NGM;
-  double gW = 0.0;
-  for (int i = 0; i < 9; ++i) {
-    out[G_QP + i] = gSig[i] * iw;
-    gW -= gSig[i] * M[M_QP + i] * iw * iw;
+  if (lane < 9) {
+    X[e] = R[3 * r] * V[c] + R[3 * r + 1] * V[3 + c] + R[3 * r + 2] * V[6 + c];  // U
+    Y[e] = gR2;
   }
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 3; ++k) {
-      gmq[i] -= gSig[3 * i + k] * mp[k];
-      gmp[k] -= gSig[3 * i + k] * mq[i];
+  __syncwarp();
+  if (lane < 9) Z[e] = X[r] * Y[c] + X[3 + r] * Y[3 + c] + X[6 + r] * Y[6 + c];  // U^T gR
+  __syncwarp();
+  if (lane < 9) Y[e] = Z[3 * r] * V[c] + Z[3 * r + 1] * V[3 + c] + Z[3 * r + 2] * V[6 + c];  // G2
+  __syncwarp();
+  if (lane < 9) Z[e] = r == c ? 0.0 : (Y[e] - Y[3 * c + r]) * idd;  // K
+  __syncwarp();
+  if (lane < 9) Y[e] = X[3 * r] * Z[c] + X[3 * r + 1] * Z[3 + c] + X[3 * r + 2] * Z[6 + c];  // U K
+  __syncwarp();
+  gSig += Y[3 * r] * V[3 * c] + Y[3 * r + 1] * V[3 * c + 1] + Y[3 * r + 2] * V[3 * c + 2];
+  if (lane < 9) X[e] = gSig;
+  __syncwarp();
+  // Sig = Sqp/W - mq mp^T, var = Spp/W - |mp|^2, mp = Sp/W, mq = Sq/W.
+  // Lanes 0-2: dL/dmq_i (row i of gSig against mp); lanes 3-5: dL/dmp_m
+  // (column m against mq, the b and var terms).
+  double gv = 0.0;
+  if (e < 3) {
+    gv = pick3(e, gb0, gb1, gb2) - (X[3 * e] * mp0 + X[3 * e + 1] * mp1 + X[3 * e + 2] * mp2);
+  } else if (e < 6) {
+    const int m = e - 3;
+    const double mpm = pick3(m, mp0, mp1, mp2);
+    gv = -s * (R[m] * gb0 + R[3 + m] * gb1 + R[6 + m] * gb2) -
+         (X[m] * mq0 + X[3 + m] * mq1 + X[6 + m] * mq2) - 2.0 * gvar * mpm;
+  }
+  // dL/dW = -(sum gSig Sqp + gvar Spp + gmp Sp + gmq Sq) / W^2
+  double cw = own ? gSig * M[M_QP + e] : 0.0;
+  if (e < 3) cw += gv * M[M_SQ + e];
+  else if (e < 6) cw += gv * M[M_SP + e - 3];
+  const double gW = -(half_warp_sum(cw) + gvar * M[M_PP]) * iw * iw;
+  double* out = gM + ((size_t)k * iters + (j - 1)) * NGM;
+  // The Huber sweep of iteration j rebuilds the adjoint of estimate j-1 from
+  // these parameters; iteration 1 starts from the identity with unit weights
+  // and has none.
+  RedParams& P = rp[k];
+  const bool params = j >= 2;
+  if (lane < 9) {
+    const double o = gSig * iw;
+    out[G_QP + e] = o;
+    if (params) P.G[G_QP + e] = (float)o;
+  }
+  if (e < 6 && lane < 16) {
+    const double o = gv * iw;
+    const int slot = e < 3 ? G_SQ + e : G_SP + e - 3;
+    out[slot] = o;
+    if (params) P.G[slot] = (float)o;
+  }
+  if (lane == 16) {
+    out[G_PP] = gvar * iw;
+    out[G_W] = gW;
+    if (params) {
+      P.G[G_PP] = (float)(gvar * iw);
+      P.G[G_W] = (float)gW;
     }
-  out[G_PP] = gvar * iw;
-  gW -= gvar * M[M_PP] * iw * iw;
-  for (int k = 0; k < 3; ++k) gmp[k] -= 2.0 * gvar * mp[k];
-  for (int k = 0; k < 3; ++k) {
-    out[G_SP + k] = gmp[k] * iw;
-    out[G_SQ + k] = gmq[k] * iw;
-    gW -= (gmp[k] * M[M_SP + k] + gmq[k] * M[M_SQ + k]) * iw * iw;
   }
-  out[G_W] = gW;
-  // parameters of the Huber sweep of iteration j (it rebuilds the adjoint of
-  // estimate j-1); iteration 1 starts from the identity with unit weights and
-  // has none
-  if (j >= 2) write_red_params(rp[warp], rc, j, out, a, st[warp], delta);
+  if (params) {
+    const bool cur = j == iters;
+    if (lane < 9) {
+      P.Ap[lane] = (float)ckp[lane];
+      P.Ac[lane] = cur ? (float)ck[CK_A + lane] : 0.f;
+    } else if (lane < 12) {
+      P.bp[lane - 9] = (float)ckp[lane];
+      P.bc[lane - 9] = cur ? (float)ck[CK_A + lane] : 0.f;
+    } else if (lane < 15) {
+      P.pp[lane - 12] = st[k].piv_p[lane - 12];
+      P.pq[lane - 12] = st[k].piv_q[lane - 12];
+    } else if (lane == 15) {
+      P.gJ = (float)ag[AG_J];
+      P.gOm = (float)ag[AG_OM];
+      P.cmin = st[k].cmin;
+      P.dl = delta;
+    }
+  }
   // the adjoint of estimate j-1 is rebuilt by the next Huber sweep
-  ag.gs = 0.0;
-  for (int i = 0; i < 9; ++i) ag.gR[i] = 0.0;
-  for (int i = 0; i < 3; ++i) ag.gb[i] = 0.0;
+  if (lane < AG_J) agd[lane] = 0.0;
 }
 
 // Per-correspondence gradients, all iterations in one pass (link layout,
