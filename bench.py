@@ -622,6 +622,7 @@ def run_ours(args):
     ctx = ec3r.Context(local)
     if args.variant >= 0:
         ctx.set_align_variant(args.variant)
+    ctx.set_backward_ctas_per_sm(args.bwd_ctas_per_sm)
 
     # per-rank synthetic chain (weak scaling: every rank owns its own map)
     M = args.submaps
@@ -1351,6 +1352,9 @@ def main():
                     choices=["chain200", "pair1", "loops512", "adjoint1", "map1000",
                              "pg1000", "depth200", "loops32k"],
                     help="chain200 is the benchmark; the others measure the other workloads")
+    ap.add_argument("--bwd-ctas-per-sm", type=int, default=0,
+                    help="CTAs per SM of the backward's reduction sweeps in the step "
+                         "(0: one CTA per tile)")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="leave the adjoint out of the step (profiling only)")
     ap.add_argument("--submaps", type=int, default=M_SUBMAPS,

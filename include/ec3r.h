@@ -287,6 +287,21 @@ ec3r_status ec3r_align_submaps_backward(ec3r_ctx* ctx, const float* d_xyz, const
  * [ec3r_align_variant_count()]), every variant's median time in ms from the
  * timing of that call's bucket (-1 where none was measured).
  */
+/*
+ * Share of the SMs that the backward call's reduction sweeps take (the
+ * HBM-bound part of ec3r_align_submaps_backward).  With ctas_per_sm = 0 (the
+ * default) each sweep launches one CTA per tile of 8192 link pixels, as many
+ * resident per SM as fit (four): the fastest sweep when nothing else runs.
+ * With 1..4 each sweep launches ctas_per_sm CTAs per SM that stride over the
+ * tiles, which leaves room on every SM for latency-bound work that the caller
+ * runs beside the backward call on another stream (for instance the pose
+ * graph).  The gradients are bit-identical for every value (each tile's
+ * partial sums have a fixed slot).  Later calls of this context use the
+ * value; a change drops the context's cached graphs.  EC3R_ERR_INVALID_ARG for
+ * a NULL context or a value outside 0..4.
+ */
+ec3r_status ec3r_align_backward_set_ctas_per_sm(ec3r_ctx* ctx, int ctas_per_sm);
+
 int ec3r_align_variant_count(void);
 ec3r_status ec3r_align_variant_info(int v, int* tile_pixels, int* ctas_per_sm,
                                     int* persistent);

@@ -97,14 +97,14 @@ __global__ void k_adj_init(int n_pairs, int iters, const double* __restrict__ ck
 // Reduction sweep of the Huber path of iteration k (S_{k-1} and the
 // moments' gradient of k).  (The cost term's sums come from the forward's
 // last sweep.)  The pixels' weights are the ones the forward's first sweep
-// stored (NaN: invalid), so a pixel costs 28 bytes, not 32.
+// stored (NaN: invalid), so a pixel costs 28 bytes, not 32.  One tile of it:
+// the tile's 12 partial sums go to slot t.
 template <bool LASTK, bool VEC>
-__global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
+__device__ __forceinline__ void reduce_tile(
     const float* __restrict__ xyz, const float* __restrict__ weights, int64_t hw, int tpl,
     const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
     const int32_t* __restrict__ link_pair, const RedParams* __restrict__ rp,
-    double* __restrict__ partials) {
-  const int64_t t = blockIdx.x;
+    double* __restrict__ partials, int64_t t, double (*red)[NRED]) {
   const int64_t l = t / tpl;
   const int c = (int)(t - l * tpl);
   const int k = link_pair[l];
@@ -198,7 +198,6 @@ __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
   for (int m = 0; m < NRED; ++m)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
-  __shared__ double red[THREADS / 32][NRED];
   const int warp = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0)
     for (int m = 0; m < NRED; ++m) red[warp][m] = (double)acc[m];
@@ -207,6 +206,21 @@ __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
     double s = 0.0;
     for (int w = 0; w < THREADS / 32; ++w) s += red[w][threadIdx.x];
     partials[t * NRED + threadIdx.x] = s;
+  }
+}
+
+// The sweep: a CTA per tile (grid = the tile count), or ctas_per_sm CTAs per
+// SM striding over the tiles (ec3r_align_backward_set_ctas_per_sm).
+template <bool LASTK, bool VEC>
+__global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
+    const float* __restrict__ xyz, const float* __restrict__ weights, int64_t hw, int tpl,
+    const int32_t* __restrict__ src, const int32_t* __restrict__ tgt,
+    const int32_t* __restrict__ link_pair, const RedParams* __restrict__ rp,
+    double* __restrict__ partials, int64_t n_tiles) {
+  __shared__ double red[THREADS / 32][NRED];
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    reduce_tile<LASTK, VEC>(xyz, weights, hw, tpl, src, tgt, link_pair, rp, partials, t, red);
+    __syncthreads();  // red is reused by the CTA's next tile
   }
 }
 
@@ -870,6 +884,9 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
   const float delta = opts->huber_delta;
   const int rule = opts->weight_rule;
   const dim3 grid((unsigned)(n_tiles > 0 ? n_tiles : 1));
+  // the reduction sweeps' grid: one CTA per tile, or a share of the SMs
+  const int64_t cap = (int64_t)ctx->bwd_ctas_per_sm * ctx->sm_count;
+  const dim3 grid_red((unsigned)(cap > 0 && cap < n_tiles ? cap : (n_tiles > 0 ? n_tiles : 1)));
   const int solve_blocks = n_pairs;  // one warp per CTA: pairs spread over all SMs' FP64 pipes
   void* p_refs;
   if ((st = ensure_buf(ctx, "adj.refs", sizeof(int32_t) * (size_t)(n_frames + 1), s, &p_refs)))
@@ -882,7 +899,7 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
                      (uint64_t)n_pairs, (uint64_t)n_links, (uint64_t)d_link_off, (uint64_t)d_src,
                      (uint64_t)d_tgt, fbits(delta), (uint64_t)iters, (uint64_t)rule,
                      (uint64_t)d_grad_S, (uint64_t)gcost, (uint64_t)d_grad_xyz,
-                     (uint64_t)d_grad_conf, (uint64_t)vec});
+                     (uint64_t)d_grad_conf, (uint64_t)vec, (uint64_t)grid_red.x});
   // the cost term's sums (sum g p'^T, sum g at the returned estimate with the
   // last weights) and the cost come from the forward's last sweep, per pair
   const double* cost_sums = (const double*)ctx->bufs["align.cost_sums"].ptr;
@@ -902,17 +919,17 @@ extern "C" ec3r_status ec3r_align_submaps_backward(
         traced(ctx, cs, "adj_reduce", [&] {
           const bool last = k == iters;
           if (vec && last)
-            k_adj_reduce<true, true><<<grid, THREADS, 0, cs>>>(
-                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part);
+            k_adj_reduce<true, true><<<grid_red, THREADS, 0, cs>>>(
+                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part, n_tiles);
           else if (vec)
-            k_adj_reduce<false, true><<<grid, THREADS, 0, cs>>>(
-                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part);
+            k_adj_reduce<false, true><<<grid_red, THREADS, 0, cs>>>(
+                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part, n_tiles);
           else if (last)
-            k_adj_reduce<true, false><<<grid, THREADS, 0, cs>>>(
-                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part);
+            k_adj_reduce<true, false><<<grid_red, THREADS, 0, cs>>>(
+                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part, n_tiles);
           else
-            k_adj_reduce<false, false><<<grid, THREADS, 0, cs>>>(
-                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part);
+            k_adj_reduce<false, false><<<grid_red, THREADS, 0, cs>>>(
+                d_xyz, weights, hw, (int)tpl, d_src, d_tgt, link_pair, rp, part, n_tiles);
         });
       traced(ctx, cs, "adj_solve", [&] {
         k_adj_solve<<<solve_blocks, 32, 0, cs>>>(n_pairs, iters, k - 1, d_link_off, (int)tpl,

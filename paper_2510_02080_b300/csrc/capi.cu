@@ -97,6 +97,13 @@ ec3r_status ec3r_set_wait_limit(ec3r_ctx* c, double seconds) {
   return EC3R_OK;
 }
 
+ec3r_status ec3r_align_backward_set_ctas_per_sm(ec3r_ctx* c, int ctas_per_sm) {
+  if (!c || ctas_per_sm < 0 || ctas_per_sm > 4) return EC3R_ERR_INVALID_ARG;
+  if (c->bwd_ctas_per_sm != ctas_per_sm) drop_graphs(c);  // the grid is in the graphs
+  c->bwd_ctas_per_sm = ctas_per_sm;
+  return EC3R_OK;
+}
+
 ec3r_status ec3r_inject(ec3r_ctx* c, unsigned what) {
   if (!c || (what & ~(unsigned)(EC3R_INJECT_LOOPS_NO_COPY | EC3R_INJECT_ALIGN_NO_EPOCH)))
     return EC3R_ERR_INVALID_ARG;

@@ -86,6 +86,9 @@ struct ec3r_ctx {
   double wait_limit_s = 0.0;
   int clock_khz = 0;
   unsigned inject = 0;
+  // CTAs per SM of the backward call's reduction sweeps (0: one CTA per tile,
+  // as many resident as fit)
+  int bwd_ctas_per_sm = 0;
 };
 
 namespace ec3r {

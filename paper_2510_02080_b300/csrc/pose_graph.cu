@@ -135,9 +135,10 @@ __device__ __forceinline__ s3::Sim3d edge_error_T(const s3::Sim3d& Ti, const s3:
 // --------------------------------------------------------------------------
 // Programmatic dependent launch (PDL): every pose-graph kernel is launched so
 // that the next can be scheduled before it finishes.  Each kernel first waits
-// for the previous one to complete (its results visible) - before any memory
-// access - and only then lets its own dependent launch, so that at most one
-// kernel waits ahead (launched without the attribute, both are no-ops).
+// for the previous one to complete (its results visible) - before any access
+// to data that a launch writes; only the plan's static index arrays may be
+// read earlier - and only then lets its own dependent launch, so that at most
+// one kernel waits ahead (launched without the attribute, both are no-ops).
 __device__ __forceinline__ void pdl_prologue() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -213,6 +214,22 @@ struct PgDev {
 // coherent loads, never the read-only data path.
 __device__ __forceinline__ double ldc(const double* p) { return *p; }
 __device__ __forceinline__ int ldc(const int* p) { return *p; }
+
+// The plan's index arrays are written by the host before a call and by no
+// kernel, so a launch may touch them before griddepcontrol.wait: it reads its
+// column's metadata and prefetches the column's index ranges into L1 there,
+// while the launch before it still runs.  Beside HBM-saturating work an L2
+// round trip costs several times its unloaded latency, and the factor and
+// back-substitution launches, one per tree level, are chains of such trips.
+__device__ __forceinline__ void prefetch_bytes(const void* base, size_t bytes, int tid,
+                                               int nthreads) {
+  const uintptr_t a0 = (uintptr_t)base & ~(uintptr_t)127, a1 = (uintptr_t)base + bytes;
+  for (uintptr_t a = a0 + (uintptr_t)tid * 128; a < a1; a += (uintptr_t)nthreads * 128)
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+}
+__device__ __forceinline__ void prefetch_range(const int* base, int n, int tid, int nthreads) {
+  prefetch_bytes(base, sizeof(int) * (size_t)(n > 0 ? n : 0), tid, nthreads);
+}
 
 __device__ __forceinline__ s3::Sim3d load_cg(const ec3r_sim3* a) { return s3::load(*a); }
 
@@ -568,6 +585,13 @@ __device__ __forceinline__ void update_node(int k, const PgDev& p) {
 // multi-launch schedule: one launch per phase and per tree level
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(64) k_pg_linearize(PgDev p, int jacobians) {
+  {  // the edge's static data, before the wait
+    const int e = blockIdx.x, t = threadIdx.x;
+    prefetch_range(p.ei + e, 1, t, 64);
+    prefetch_range(p.ej + e, 1, t, 64);
+    prefetch_bytes(p.Tij + e, sizeof(ec3r_sim3), t, 64);
+    if (p.info) prefetch_bytes(p.info + (size_t)e * NB, sizeof(double) * NB, t, 64);
+  }
   pdl_prologue();
   __shared__ WarpScratch w;
   if (threadIdx.x < 32) linearize_edge(blockIdx.x, threadIdx.x, w, p, jacobians);
@@ -576,6 +600,16 @@ __global__ void __launch_bounds__(64) k_pg_linearize(PgDev p, int jacobians) {
 
 __global__ void __launch_bounds__(32) k_pg_assemble(PgDev p, int n_blocks, int nf,
                                                     double* chi2_out, int trial) {
+  {  // the unit's static index ranges, before the wait
+    const int b = blockIdx.x;
+    if (b < n_blocks) {
+      const int p0 = p.asm_ptr[b], p1 = p.asm_ptr[b + 1];
+      prefetch_range(p.asm_it + p0, p1 - p0, threadIdx.x, 32);
+    } else if (b < n_blocks + nf) {
+      const int k = b - n_blocks, q0 = p.g_ptr[k], q1 = p.g_ptr[k + 1];
+      prefetch_range(p.g_it + q0, q1 - q0, threadIdx.x, 32);
+    }
+  }
   pdl_prologue();
   assemble_unit(blockIdx.x, threadIdx.x, n_blocks, nf, p, chi2_out, trial);
 }
@@ -695,9 +729,16 @@ __device__ void factor_staged(const ColMeta& c, int tid, double* CB, double* fpa
 
 // One column per CTA: the staged schedule, else factor_column.
 __global__ void __launch_bounds__(32 * FWARPS) k_pg_factor(PgDev p, int lstart) {
-  pdl_prologue();
   __shared__ double CB[CB_MAX * NB], fpart[FS_MAX * 7], inv[7], y[7];
-  const ColMeta c = load_meta(p.col_meta, lstart + blockIdx.x);
+  const ColMeta c = load_meta(p.col_meta, lstart + blockIdx.x);  // static: before the wait
+  if (c.fast) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    prefetch_range(p.off_blk + c.o0, c.o1 - c.o0, t, nt);
+    prefetch_range(p.grp + 3 * c.g0, 3 * (c.g1 - c.g0), t, nt);
+    prefetch_range(p.grp_slot + c.g0, c.g1 - c.g0, t, nt);
+    prefetch_range(p.row + 2 * c.r0, 2 * (c.r1 - c.r0), t, nt);
+  }
+  pdl_prologue();
   if (c.fast) factor_staged(c, threadIdx.x, CB, fpart, inv, y, p);
   else factor_column<FWARPS>(c.k, threadIdx.x, CB, inv, y, p);
 }
@@ -751,10 +792,12 @@ struct WarpSolve {
 
 // One column per warp (one warp per CTA).
 __global__ void __launch_bounds__(32) k_pg_backsolve(PgDev p, int lstart) {
-  pdl_prologue();
   __shared__ WarpSolve w;
-  backsolve_staged(load_meta(p.col_meta, lstart + blockIdx.x), threadIdx.x, w.D, w.part, w.id,
-                   w.x, p);
+  const ColMeta c = load_meta(p.col_meta, lstart + blockIdx.x);  // static: before the wait
+  prefetch_range(p.off_blk + c.o0, c.o1 - c.o0, threadIdx.x, 32);
+  prefetch_range(p.off_row + c.o0, c.o1 - c.o0, threadIdx.x, 32);
+  pdl_prologue();
+  backsolve_staged(c, threadIdx.x, w.D, w.part, w.id, w.x, p);
 }
 
 __global__ void k_pg_update(PgDev p) {

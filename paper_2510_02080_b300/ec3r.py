@@ -33,7 +33,7 @@ EXPORTS = ("ec3r_create", "ec3r_destroy", "ec3r_last_error", "ec3r_status_string
            "ec3r_fuse_points_depth", "ec3r_loop_candidates", "ec3r_fuse_count",
            "ec3r_fuse_points_counted", "ec3r_align_token", "ec3r_align_variant_count",
            "ec3r_align_variant_info", "ec3r_align_set_variant", "ec3r_align_last_variant",
-           "ec3r_set_wait_limit", "ec3r_inject")
+           "ec3r_set_wait_limit", "ec3r_inject", "ec3r_align_backward_set_ctas_per_sm")
 
 
 class Sim3(C.Structure):
@@ -98,6 +98,7 @@ def _declare(l):
     l.ec3r_align_last_variant.argtypes = [_P, C.POINTER(C.c_int), C.POINTER(C.c_float)]
     l.ec3r_set_wait_limit.argtypes = [_P, C.c_double]
     l.ec3r_inject.argtypes = [_P, C.c_uint]
+    l.ec3r_align_backward_set_ctas_per_sm.argtypes = [_P, C.c_int]
     l.ec3r_align_submaps_depth.argtypes = [_P, _P, _P, _P, _I64, C.c_int, C.c_int, C.c_int,
                                            _I64, _P, _P, _P, _P, C.POINTER(AlignOpts), _P, _P,
                                            _P, _P]
@@ -119,7 +120,8 @@ def _declare(l):
                  "ec3r_align_submaps_backward", "ec3r_align_submaps_depth", "ec3r_correct_points",
                  "ec3r_fuse_points_depth", "ec3r_loop_candidates", "ec3r_fuse_count",
                  "ec3r_fuse_points_counted", "ec3r_align_variant_info", "ec3r_align_set_variant",
-                 "ec3r_align_last_variant", "ec3r_set_wait_limit", "ec3r_inject"):
+                 "ec3r_align_last_variant", "ec3r_set_wait_limit", "ec3r_inject",
+                 "ec3r_align_backward_set_ctas_per_sm"):
         getattr(l, name).restype = C.c_int
 
 
@@ -214,6 +216,10 @@ class Context:
     def set_wait_limit(self, seconds):
         """Limit of the kernels' bounded waits in seconds (0: the default, 2 s)."""
         self._check(self._lib.ec3r_set_wait_limit(self._h, float(seconds)))
+
+    def set_backward_ctas_per_sm(self, ctas_per_sm):
+        """CTAs per SM of the backward call's reduction sweeps (0: one per tile)."""
+        self._check(self._lib.ec3r_align_backward_set_ctas_per_sm(self._h, int(ctas_per_sm)))
 
     def inject(self, what):
         """Test-only: make a bounded wait run out (INJECT_* bits; 0 = off)."""

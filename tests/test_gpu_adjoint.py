@@ -396,3 +396,33 @@ def test_chain_adjoint_full_size_sampled_pairs(ctx):
         g_c = torch.stack([gc[fa], gc[fb]]).cpu().double().numpy()
         compare(g_x, gx_or, ~kink, f"pair {k} dL/dxyz", allow["x"])
         compare(g_c, gc_or, ~kink, f"pair {k} dL/dconf", allow["c"])
+
+
+def test_reduction_share_of_sms_bit_identical(ctx, request):
+    """ec3r_align_backward_set_ctas_per_sm: the reduction sweeps as 1 or 3 CTAs
+    per SM striding over the tiles (a 40-submap chain at 294 x 518: 741 tiles,
+    more than either grid) give the same gradients, bit for bit, as one CTA per
+    tile; values outside 0..4 are rejected."""
+    ch = synth.make_chain(synth.SEED_BASE + 2, M=40, F=5, H=294, W=518, device="cuda")
+    ps = ch.pairs()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    gS = torch.randn((ps.n_pairs, 13), generator=gen, dtype=torch.float64, device="cuda")
+    gcost = torch.ones((ps.n_pairs,), dtype=torch.float64, device="cuda")
+    _, st, _ = ctx.align_submaps(ps.xyz, ps.conf, ps.link_off, ps.src, ps.tgt, want_cost=True)
+    tok = ctx.align_token()
+    request.addfinalizer(lambda: ctx.set_backward_ctas_per_sm(0))
+    out = {}
+    for c in (0, 1, 3):
+        ctx.set_backward_ctas_per_sm(c)
+        gx, gc = ctx.align_submaps_backward(ps.xyz, ps.conf, ps.link_off, ps.src, ps.tgt, gS,
+                                            gcost, fwd_token=tok)
+        assert ctx.sync_status() == 0
+        out[c] = (gx.clone(), gc.clone())
+    assert int((st != 0).sum()) == 0
+    assert bool(out[0][0].abs().sum() > 0)
+    for c in (1, 3):
+        assert torch.equal(out[c][0], out[0][0]) and torch.equal(out[c][1], out[0][1])
+    lib = ec3r.lib()
+    for bad in (-1, 5):
+        assert lib.ec3r_align_backward_set_ctas_per_sm(ctx._h, bad) == 1  # EC3R_ERR_INVALID_ARG
