@@ -229,13 +229,13 @@ __global__ void __launch_bounds__(THREADS, 4) k_adj_reduce(
 // of estimate j as dL/dA and dL/db, then differentiates solve j and stores the
 // gradient of its moments in gM[j].
 //
-// The FP64 pipe costs about the same per warp instruction whatever the number
-// of active lanes, so the 3x3 algebra runs element-parallel: lane e < 9 (and
-// its copy e + 16) owns element (e / 3, e % 3) of each matrix, the matrices
-// pass between products through shared memory, and 9-term sums are
+// On B300 a dependent FP64 operation takes about the same time whether one
+// lane or a few carry it, so the 3x3 algebra runs element-parallel: lane e < 9
+// (and its copy e + 16) owns element (e / 3, e % 3) of each matrix, the
+// matrices pass between products through shared memory, and 9-term sums are
 // fixed-order butterflies over the 16-lane half-warp (lanes 9..15 add zeros).
-// Scalars every lane needs are computed redundantly by all lanes, at the cost
-// of one instruction each.
+// Scalars every lane needs are computed redundantly by all lanes, one
+// instruction each.
 __device__ __forceinline__ double half_warp_sum(double x) {
   x += __shfl_xor_sync(0xffffffffu, x, 8);
   x += __shfl_xor_sync(0xffffffffu, x, 4);
