@@ -73,3 +73,27 @@ def test_noalloc_limits_are_enforced_before_any_device_work():
     assert call(1, 1, 64, bad) == 1
     bad.iters, bad.want_cost = 10, 1                               # cost wanted, no buffer
     assert call(1, 1, 64, bad) == 1
+
+
+def test_context_settings_reject_bad_arguments_on_the_host():
+    """The context settings and the variant table validate their arguments
+    before any device work: a NULL context is EC3R_ERR_INVALID_ARG (1) for
+    every setter, the token of a NULL context is 0, and the variant table
+    answers every index in range and rejects the rest."""
+    l = ec3r.lib()
+    assert l.ec3r_set_wait_limit(None, 1.0) == 1
+    assert l.ec3r_inject(None, 0) == 1
+    assert l.ec3r_align_set_variant(None, 0) == 1
+    assert l.ec3r_align_backward_set_ctas_per_sm(None, 0) == 1
+    assert l.ec3r_align_token(None) == 0
+    n = l.ec3r_align_variant_count()
+    assert n >= 2
+    t, c, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    persistent = []
+    for v in range(n):
+        assert l.ec3r_align_variant_info(v, ctypes.byref(t), ctypes.byref(c), ctypes.byref(p)) == 0
+        assert t.value % 4096 == 0 and 1 <= c.value <= 4 and p.value in (0, 1)
+        persistent.append(p.value)
+    assert 0 in persistent and 1 in persistent
+    for v in (-1, n):
+        assert l.ec3r_align_variant_info(v, ctypes.byref(t), ctypes.byref(c), ctypes.byref(p)) == 1
