@@ -372,7 +372,7 @@ ec3r_status ec3r_align_submaps(ec3r_ctx* ctx, const float* d_xyz, const float* d
   if ((st = ensure_buf(ctx, "align.state", sizeof(PairState) * (size_t)n_pairs, s, &p_state)) ||
       (st = ensure_buf(ctx, "align.partials", sizeof(double) * NMOM * (size_t)(n_tiles_max + 1),
                        s, &p_part)) ||
-      // link -> pair map, then one word for the verdict of k_check_offsets
+      // link -> pair map, then one word for the result of k_check_offsets
       (st = ensure_buf(ctx, "align.link_pair", sizeof(int32_t) * (size_t)(n_links + 2), s,
                        &p_lp)) ||
       (st = ensure_buf(ctx, "align.ckpt",

@@ -539,7 +539,7 @@ extern "C" ec3r_status ec3r_align_submaps_depth(
   if ((st = ensure_buf(ctx, "depth.partials", sizeof(double) * NMOM * (size_t)(n_tiles + 1), s,
                        &p_part)))
     return st;
-  // link -> pair map, then one word for the verdict of k_check_offsets
+  // link -> pair map, then one word for the result of k_check_offsets
   if ((st = ensure_buf(ctx, "depth.link_pair", sizeof(int32_t) * (size_t)(n_links + 2), s,
                        &p_lp)))
     return st;

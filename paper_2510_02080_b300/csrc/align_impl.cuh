@@ -454,7 +454,7 @@ static __global__ void __launch_bounds__(32) k_cost(int n_pairs,
 // Checks the link offsets as one CSR array (link_off[0] = 0, non-decreasing,
 // link_off[n_pairs] = n_links) and writes 1 to *malformed if they are not, else
 // 0.  One CTA reads every offset, so that the set-up of every pair sees the
-// same verdict: a malformed batch marks all its pairs, and no two pairs of an
+// same answer: a malformed batch marks all its pairs, and no two pairs of an
 // accepted batch can claim the same link.
 static __global__ void __launch_bounds__(1024) k_check_offsets(
     const int32_t* __restrict__ link_off, int n_pairs, int64_t n_links, int32_t* malformed) {
